@@ -1,0 +1,165 @@
+/*
+ * dts.h -- C ABI of the GB300 Domain Transform Solver library (libdts.so).
+ *
+ * The Domain Transform Solver (Bapat & Frahm, "The Domain Transform Solver",
+ * ECCV 2018) minimises, for a target t with per-pixel confidence c under a
+ * C-channel guide image I,
+ *     F(z) = lambda/2 sum_i (z_i - zbar_i)^2 + sum_i c_i (z_i - t_i)^2      (Eq. 1-2)
+ * where zbar = A z is the edge-aware mean (Eq. 10) computed with the domain
+ * transform (§3.2): distances between neighbouring pixels (Eq. 8-9) feed a
+ * recursive filter (causal then anti-causal first-order recurrence along every
+ * row, then every column, for N passes with a halving sigma schedule).  The
+ * solver iterates the gradient step of Eq. 3 with step 0.99 (§4) or the fixed
+ * point of Eq. 4.
+ *
+ * Conventions for every entry point
+ *  - All image pointers are DEVICE pointers owned by the caller; the library
+ *    never allocates, frees or keeps them.  Scratch memory is the caller's
+ *    workspace (size from dts_workspace_size), at least 256-byte aligned.
+ *  - Single-channel images (target, confidence, z, gradients) are dense H x W
+ *    row-major (row stride W elements).  The guide is planar C x H x W with
+ *    the strides given in dts_guide.
+ *  - Calls are asynchronous on `stream` (NULL = the legacy default stream).
+ *    Argument errors are returned synchronously and launch nothing.  Errors
+ *    detected on the device (a bounded wait that gave up) are recorded in a
+ *    per-device status word that dts_last_status() returns.  No kernel traps.
+ *  - Return value: a dts_status code (DTS_OK = 0).
+ */
+#ifndef DTS_H
+#define DTS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t / CUstream. */
+typedef struct CUstream_st* dts_stream;
+
+typedef enum dts_status {
+    DTS_OK = 0,
+    DTS_ERR_INVALID_ARG = 1, /* a size, pointer, alignment or parameter is out of range */
+    DTS_ERR_UNSUPPORTED = 2, /* valid but not implemented (e.g. a line longer than the kernels hold) */
+    DTS_ERR_WORKSPACE = 3,   /* workspace missing, too small or misaligned */
+    DTS_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    DTS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (reported by dts_last_status) */
+    DTS_ERR_NONFINITE = 6    /* reserved: non-finite values detected */
+} dts_status;
+
+typedef enum dts_dtype { DTS_F32 = 0, DTS_BF16 = 1, DTS_F16 = 2 } dts_dtype;
+typedef enum dts_norm { DTS_NORM_L1 = 0, DTS_NORM_L2 = 1 } dts_norm;
+typedef enum dts_update { DTS_UPDATE_GD = 0, DTS_UPDATE_JACOBI = 1 } dts_update;
+typedef enum dts_conf_mode { DTS_CONF_PLAIN = 0, DTS_CONF_SUPPORT = 1 } dts_conf_mode;
+
+/* Planar guide image I: channel k, row y, column x is element
+ * k * ch_stride + y * row_stride + x of `data` (dtype F32, BF16 or F16).
+ * row_stride = 0 means W; ch_stride = 0 means H * row_stride.
+ * Requires C >= 1, H >= 1, W >= 1, row_stride >= W, ch_stride >= H * row_stride. */
+typedef struct dts_guide {
+    int C, H, W;
+    int dtype;              /* dts_dtype */
+    const void* data;       /* device pointer */
+    long long ch_stride;    /* elements */
+    long long row_stride;   /* elements */
+} dts_guide;
+
+/* Solver parameters (names follow the paper).
+ *  lambda      weight of the edge-aware regulariser (Eq. 1), >= 0
+ *  sigma_s     spatial standard deviation in pixels (sigma_x = sigma_y, §4), > 0
+ *  sigma_r     range standard deviation in guide units (§4: colours in [0, 1]), > 0
+ *  step        gradient step eta of Eq. 3 (§4 uses 0.99), > 0
+ *  iterations  solver iterations K >= 0 (§4: 3000 for stereo, 10 for depth SR)
+ *  passes      recursive-filter passes N per edge-aware mean, 1..16 (3 by default)
+ *  norm        distance norm: DTS_NORM_L1 (1 + sigma_s/sigma_r sum_k |dI_k|) or
+ *              DTS_NORM_L2 (sqrt(1 + (sigma_s/sigma_r)^2 sum_k dI_k^2), §3.2)
+ *  update      DTS_UPDATE_GD (Eq. 3) or DTS_UPDATE_JACOBI (Eq. 4)
+ *  conf_mode   DTS_CONF_PLAIN (c as given) or DTS_CONF_SUPPORT (c weighted by
+ *              S_flat / sum_j W_ij, §3.1 after Eq. 6)
+ *  dist_dtype  storage of the distance planes: DTS_F32 or DTS_F16
+ *  save_checkpoints  1: dts_solve keeps z_0 .. z_{K-1} in the workspace for
+ *              dts_solve_backward (workspace sized with with_backward = 1) */
+typedef struct dts_params {
+    float lambda, sigma_s, sigma_r, step;
+    int iterations, passes;
+    int norm, update, conf_mode;
+    int dist_dtype;
+    int save_checkpoints;
+} dts_params;
+
+/* Human-readable name of a status code (static string). */
+const char* dts_status_string(int status);
+
+/* Library version string (static). */
+const char* dts_version(void);
+
+/* Bytes of workspace that dts_filter / dts_solve (with_backward = 0) or
+ * dts_solve with save_checkpoints plus dts_solve_backward (with_backward = 1)
+ * need for this guide and these parameters.  0 on invalid arguments. */
+size_t dts_workspace_size(const dts_guide* guide, const dts_params* params, int with_backward);
+
+/* Domain-transform distances (§3.2, Eq. 8-9) between neighbouring pixels:
+ *   dX[y][x] between (y, x-1) and (y, x), dY[y][x] between (y-1, x) and (y, x),
+ *   L1: 1 + (sigma_s/sigma_r) sum_k |I_k(p) - I_k(q)|;  L2: sqrt(1 + (sigma_s/sigma_r)^2 sum_k (I_k(p) - I_k(q))^2).
+ * dX[y][0] and dY[0][x] have no neighbour and are written as 1.
+ * Outputs are dense H x W planes of params->dist_dtype (F32 or F16).
+ * Uses params->sigma_s, sigma_r, norm, dist_dtype only. */
+int dts_domain_transform(const dts_guide* guide, const dts_params* params, void* dX, void* dY, dts_stream stream);
+
+/* Edge-aware mean dst = A src (Eq. 10 with the recursive-filter kernel of §3.2):
+ * A = V(a_N) H(a_N) ... V(a_1) H(a_1), the horizontal pass first; pass i uses
+ * sigma_i = sigma_s sqrt(3) 2^(N-i) / sqrt(4^N - 1) and a_i = exp(-sqrt(2)/sigma_i),
+ * and each 1-D pass runs J[n] = (1 - w) x[n] + w J[n-1] with w = a_i^d forward and
+ * then backward along the line.  src and dst are dense H x W FP32 and may alias. */
+int dts_filter(const dts_guide* guide, const dts_params* params, const float* src, float* dst, void* ws,
+               size_t ws_bytes, dts_stream stream);
+
+/* The solver (§3.1): z_0 = z_init (or the target when z_init is NULL), then K times
+ *   zbar = A z_k;  z_{k+1} = z_k - step (lambda (z_k - zbar) + c (z_k - t))       (GD, Eq. 3)
+ *                  or (lambda zbar + c t) / (lambda + c)                           (Jacobi, Eq. 4)
+ * target: dense H x W of target_dtype (F32, BF16 or F16); conf: dense H x W FP32
+ * (c >= 0); z_out: dense H x W FP32 (may alias z_init, not target/conf).
+ * With save_checkpoints = 1 the iterates z_0 .. z_{K-1} stay in the workspace. */
+int dts_solve(const dts_guide* guide, const void* target, int target_dtype, const float* conf, const float* z_init,
+              const dts_params* params, float* z_out, void* ws, size_t ws_bytes, dts_stream stream);
+
+/* Reverse mode of dts_solve (the paper has no backward; the adjoint of each
+ * recurrence is the same recurrence run in the opposite direction).  Must follow
+ * a dts_solve with the same arguments, save_checkpoints = 1 and this workspace
+ * (sized with with_backward = 1), which holds the checkpoints it reads.
+ * grad_z: dL/dz_K (H x W FP32).  Outputs (each may be NULL, all FP32 dense):
+ *   grad_target H x W (includes the z_0 = target path when z_init is NULL),
+ *   grad_conf H x W, grad_guide C x H x W (through the distances; L1 uses sign(0) = 0),
+ *   grad_z_init H x W (only meaningful when z_init was given).
+ * Supports conf_mode = DTS_CONF_PLAIN only. */
+int dts_solve_backward(const dts_guide* guide, const void* target, int target_dtype, const float* conf,
+                       const float* z_init, const dts_params* params, void* ws, size_t ws_bytes, const float* grad_z,
+                       float* grad_target, float* grad_conf, float* grad_guide, float* grad_z_init,
+                       dts_stream stream);
+
+/* Synchronises `stream`, then returns and clears the device-side status word of
+ * the current device (DTS_OK, or e.g. DTS_ERR_TIMEOUT), or DTS_ERR_CUDA if the
+ * synchronisation itself failed. */
+int dts_last_status(dts_stream stream);
+
+/* ---- per-launch kernel timing (a tracing aid; not part of the paper's method) ----
+ * dts_profile(1) clears the record and, until dts_profile(0), brackets every kernel the
+ * library launches with two CUDA events on that launch's stream.  Host-side only; it does
+ * not change what the kernels compute. */
+int dts_profile(int enable);
+
+/* Copies up to max_records records of the launches made since dts_profile(1), in launch
+ * order: kernel id (see dts_kernel_name), pixels the launch covered, flags (bit 0: FP16
+ * distance planes, bit 1: 16-bit target) and the event-timed duration in milliseconds.
+ * Any output pointer may be NULL.  Waits for the recorded events.  Returns the number of
+ * records copied, or minus a dts_status. */
+int dts_profile_read(int max_records, int* kernel, long long* pixels, int* flags, float* ms);
+
+/* Name of a kernel id reported by dts_profile_read (static string). */
+const char* dts_kernel_name(int kernel);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DTS_H */

@@ -1,0 +1,384 @@
+// C ABI of libdts (declared in include/dts.h): argument checks, workspace layout,
+// the per-pass sigma schedule and the launch sequence of each entry point.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "dts_internal.cuh"
+
+namespace dts {
+
+// Device-side status word (one per device that loads the library).
+__device__ int g_status = 0;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_prep_mutex;
+bool g_prepared[kMaxDevices] = {};
+
+int ensure_prepared() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DTS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_prep_mutex);
+    if (!g_prepared[dev]) {
+        if (prepare_kernels() != cudaSuccess) return DTS_ERR_CUDA;
+        g_prepared[dev] = true;
+    }
+    return DTS_OK;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool valid_dtype(int d) { return d == DTS_F32 || d == DTS_BF16 || d == DTS_F16; }
+
+int check_guide(const dts_guide* g) {
+    if (!g || !g->data) return DTS_ERR_INVALID_ARG;
+    if (g->C < 1 || g->H < 1 || g->W < 1 || !valid_dtype(g->dtype)) return DTS_ERR_INVALID_ARG;
+    const long long rs = g->row_stride ? g->row_stride : g->W;
+    const long long cs = g->ch_stride ? g->ch_stride : (long long)g->H * rs;
+    if (rs < g->W || (g->C > 1 && cs < (long long)g->H * rs) || cs < 0) return DTS_ERR_INVALID_ARG;
+    return DTS_OK;
+}
+
+int check_params(const dts_params* p) {
+    if (!p) return DTS_ERR_INVALID_ARG;
+    if (!(p->lambda >= 0.f) || !isfinite(p->lambda)) return DTS_ERR_INVALID_ARG;
+    if (!(p->sigma_s > 0.f) || !isfinite(p->sigma_s)) return DTS_ERR_INVALID_ARG;
+    if (!(p->sigma_r > 0.f) || !isfinite(p->sigma_r)) return DTS_ERR_INVALID_ARG;
+    if (!(p->step > 0.f) || !isfinite(p->step)) return DTS_ERR_INVALID_ARG;
+    if (p->iterations < 0 || p->passes < 1 || p->passes > kMaxPasses) return DTS_ERR_INVALID_ARG;
+    if (p->norm != DTS_NORM_L1 && p->norm != DTS_NORM_L2) return DTS_ERR_INVALID_ARG;
+    if (p->update != DTS_UPDATE_GD && p->update != DTS_UPDATE_JACOBI) return DTS_ERR_INVALID_ARG;
+    if (p->conf_mode != DTS_CONF_PLAIN && p->conf_mode != DTS_CONF_SUPPORT) return DTS_ERR_INVALID_ARG;
+    if (p->dist_dtype != DTS_F32 && p->dist_dtype != DTS_F16) return DTS_ERR_INVALID_ARG;
+    return DTS_OK;
+}
+
+// Workspace layout (byte offsets from the workspace base).
+struct Layout {
+    long long pitch;
+    size_t plane_f32;   // bytes of one FP32 plane
+    size_t plane_d;     // bytes of one distance plane
+    size_t dX, dY, u, chat, z;  // offsets
+    int z_planes;       // 1 (in place) or K checkpoints
+    size_t fwd_end;     // bytes used by the forward
+    // backward scratch
+    size_t xin;         // 2N pass-input planes
+    size_t g0, g1;      // adjoint ping-pong planes
+    size_t gz;          // adjoint of the iterate
+    size_t dXb, dYb;    // distance gradients
+    size_t total;
+};
+
+Layout make_layout(int H, int W, const dts_params* p, int with_backward) {
+    Layout L = {};
+    L.pitch = pitch_for(W);
+    L.plane_f32 = align_up((size_t)H * (size_t)L.pitch * 4, kPlaneAlign);
+    L.plane_d = align_up((size_t)H * (size_t)L.pitch * (p->dist_dtype == DTS_F16 ? 2 : 4), kPlaneAlign);
+    size_t off = 0;
+    L.dX = off; off += L.plane_d;
+    L.dY = off; off += L.plane_d;
+    L.u = off; off += L.plane_f32;
+    L.chat = off;
+    if (p->conf_mode == DTS_CONF_SUPPORT) off += L.plane_f32;
+    L.z = off;
+    const bool keep = p->save_checkpoints || with_backward;
+    L.z_planes = keep ? (p->iterations > 0 ? p->iterations : 1) : 1;
+    off += (size_t)L.z_planes * L.plane_f32;
+    L.fwd_end = off;
+    if (with_backward) {
+        L.xin = off; off += (size_t)(2 * p->passes) * L.plane_f32;
+        L.g0 = off; off += L.plane_f32;
+        L.g1 = off; off += L.plane_f32;
+        L.gz = off; off += L.plane_f32;
+        L.dXb = off; off += L.plane_f32;
+        L.dYb = off; off += L.plane_f32;
+    }
+    L.total = off;
+    return L;
+}
+
+// Per-pass feedback of the recursive filter: sigma_i = sigma_s sqrt(3) 2^(N-i) / sqrt(4^N - 1),
+// a_i = exp(-sqrt(2) / sigma_i); the kernels take log2(a_i) so that w = exp2(log2(a_i) * d).
+void pass_log2a(double sigma_s, int N, float* k2) {
+    for (int i = 1; i <= N; ++i) {
+        const double sig = sigma_s * sqrt(3.0) * ldexp(1.0, N - i) / sqrt(ldexp(1.0, 2 * N) - 1.0);
+        k2[i - 1] = (float)(-sqrt(2.0) / (sig * log(2.0)));
+    }
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return DTS_OK;
+    if (getenv("DTS_LOG")) fprintf(stderr, "libdts: CUDA error %s\n", cudaGetErrorString(e));
+    return DTS_ERR_CUDA;
+}
+
+struct Plans {
+    RowPlan rows;
+    ColPlan cols;
+};
+
+int make_plans(int H, int W, Plans* pl) {
+    if (!plan_rows(W, &pl->rows)) return DTS_ERR_UNSUPPORTED;
+    if (!plan_cols(H, &pl->cols)) return DTS_ERR_UNSUPPORTED;
+    return DTS_OK;
+}
+
+char* ws_at(void* ws, size_t off) { return static_cast<char*>(ws) + off; }
+
+// distances into the workspace, plus an optional fused copy of `src` into plane `dst`
+int run_distances(const dts_guide* g, const dts_params* p, const Layout& L, void* ws, const void* src, int src_dtype,
+                  float* dst, cudaStream_t s) {
+    DistArgs a = {};
+    a.guide = g->data;
+    a.row_stride = g->row_stride ? g->row_stride : g->W;
+    a.ch_stride = g->ch_stride ? g->ch_stride : (long long)g->H * a.row_stride;
+    a.C = g->C;
+    a.H = g->H;
+    a.W = g->W;
+    a.gdtype = g->dtype;
+    a.norm = p->norm;
+    a.dhalf = p->dist_dtype == DTS_F16;
+    a.k = p->sigma_s / p->sigma_r;
+    a.dX = ws_at(ws, L.dX);
+    a.dY = ws_at(ws, L.dY);
+    a.pitch = L.pitch;
+    a.src = src;
+    a.src_dtype = src_dtype;
+    a.dst = dst;
+    return cuda_status(launch_distances(a, s));
+}
+
+PassArgs base_pass(const dts_guide* g, const Layout& L) {
+    PassArgs a = {};
+    a.H = g->H;
+    a.W = g->W;
+    a.pitch = L.pitch;
+    a.dst_pitch = L.pitch;
+    return a;
+}
+
+// effective confidence for DTS_CONF_SUPPORT: chat = c * S_flat / S (written to L.chat)
+int run_support(const dts_guide* g, const dts_params* p, const Layout& L, void* ws, const float* conf,
+                const Plans& pl, cudaStream_t s) {
+    const int dh = p->dist_dtype == DTS_F16;
+    const double a = exp(-sqrt(2.0) / (double)p->sigma_s);
+    float* u = reinterpret_cast<float*>(ws_at(ws, L.u));
+    PassArgs r = base_pass(g, L);
+    r.src = u;
+    r.dst = u;
+    r.d = ws_at(ws, L.dX);
+    r.k2 = (float)log2(a);
+    int st = cuda_status(launch_row_pass(r, dh, PASS_SUPPORT, pl.rows, s));
+    if (st) return st;
+    PassArgs c = base_pass(g, L);
+    c.src = u;
+    c.dst = u;
+    c.d = ws_at(ws, L.dY);
+    c.k2 = (float)log2(a);
+    c.c = conf;
+    c.zout = reinterpret_cast<float*>(ws_at(ws, L.chat));
+    c.zout_pitch = L.pitch;
+    c.s_flat = (float)(((1.0 + a) / (1.0 - a)) * ((1.0 + a) / (1.0 - a)));
+    return cuda_status(launch_col_pass(c, dh, PASS_SUPPORT_CONF, pl.cols, s));
+}
+
+}  // namespace
+}  // namespace dts
+
+namespace dts {
+namespace {
+int solve_forward(const dts_guide* g, const void* target, int tdt, const float* conf, const float* z_init,
+                       const dts_params* p, float* z_out, void* ws, const Layout& L, const Plans& pl,
+                       cudaStream_t s) {
+    int st;
+    const int K = p->iterations;
+    const int W = g->W;
+    if (K == 0) {
+        if (z_init) return cuda_status(launch_copy_plane(z_init, DTS_F32, W, z_out, W, g->H, W, s));
+        return cuda_status(launch_copy_plane(target, tdt, W, z_out, W, g->H, W, s));
+    }
+    const bool keep = L.z_planes > 1 || p->save_checkpoints;
+    auto zslot = [&](int k) -> float* {
+        return reinterpret_cast<float*>(ws_at(ws, L.z + (keep ? (size_t)k * L.plane_f32 : 0)));
+    };
+    // distances, and z_0 = z_init (or the target) into the first iterate plane
+    if (z_init) st = run_distances(g, p, L, ws, z_init, DTS_F32, zslot(0), s);
+    else st = run_distances(g, p, L, ws, target, tdt, zslot(0), s);
+    if (st) return st;
+    const bool support = p->conf_mode == DTS_CONF_SUPPORT;
+    if (support && (st = run_support(g, p, L, ws, conf, pl, s))) return st;
+    float k2[kMaxPasses];
+    pass_log2a(p->sigma_s, p->passes, k2);
+    const int dh = p->dist_dtype == DTS_F16;
+    float* u = reinterpret_cast<float*>(ws_at(ws, L.u));
+    for (int k = 0; k < K; ++k) {
+        float* zin = zslot(k);
+        for (int i = 0; i < p->passes; ++i) {
+            PassArgs r = base_pass(g, L);
+            r.src = i == 0 ? zin : u;
+            r.dst = u;
+            r.d = ws_at(ws, L.dX);
+            r.k2 = k2[i];
+            if ((st = cuda_status(launch_row_pass(r, dh, PASS_PLAIN, pl.rows, s)))) return st;
+            PassArgs c = base_pass(g, L);
+            c.src = u;
+            c.dst = u;
+            c.d = ws_at(ws, L.dY);
+            c.k2 = k2[i];
+            int kind = PASS_PLAIN;
+            if (i == p->passes - 1) {
+                kind = PASS_UPDATE;
+                c.zk = zin;
+                c.t = target;
+                c.t_dtype = tdt;
+                c.c = support ? reinterpret_cast<const float*>(ws_at(ws, L.chat)) : conf;
+                c.c_pitched = support;
+                c.clamp_step = support;
+                c.lambda = p->lambda;
+                c.step = p->step;
+                c.update = p->update;
+                if (k == K - 1) {
+                    c.zout = z_out;
+                    c.zout_pitch = W;
+                } else {
+                    c.zout = zslot(k + 1);
+                    c.zout_pitch = L.pitch;
+                }
+            }
+            if ((st = cuda_status(launch_col_pass(c, dh, kind, pl.cols, s)))) return st;
+        }
+    }
+    return DTS_OK;
+}
+
+}  // namespace
+}  // namespace dts
+
+using namespace dts;
+
+extern "C" const char* dts_status_string(int s) {
+    switch (s) {
+        case DTS_OK: return "DTS_OK";
+        case DTS_ERR_INVALID_ARG: return "DTS_ERR_INVALID_ARG";
+        case DTS_ERR_UNSUPPORTED: return "DTS_ERR_UNSUPPORTED";
+        case DTS_ERR_WORKSPACE: return "DTS_ERR_WORKSPACE";
+        case DTS_ERR_CUDA: return "DTS_ERR_CUDA";
+        case DTS_ERR_TIMEOUT: return "DTS_ERR_TIMEOUT";
+        case DTS_ERR_NONFINITE: return "DTS_ERR_NONFINITE";
+        default: return "DTS_ERR_UNKNOWN";
+    }
+}
+
+extern "C" const char* dts_version(void) { return "dts-gb300 0.1 (sm_103a)"; }
+
+extern "C" size_t dts_workspace_size(const dts_guide* guide, const dts_params* params, int with_backward) {
+    if (check_guide(guide) || check_params(params)) return 0;
+    return make_layout(guide->H, guide->W, params, with_backward).total;
+}
+
+extern "C" int dts_domain_transform(const dts_guide* guide, const dts_params* params, void* dX, void* dY,
+                                    dts_stream stream) {
+    int st = check_guide(guide);
+    if (!st) st = check_params(params);
+    if (st) return st;
+    if (!dX || !dY) return DTS_ERR_INVALID_ARG;
+    DistArgs a = {};
+    a.guide = guide->data;
+    a.row_stride = guide->row_stride ? guide->row_stride : guide->W;
+    a.ch_stride = guide->ch_stride ? guide->ch_stride : (long long)guide->H * a.row_stride;
+    a.C = guide->C;
+    a.H = guide->H;
+    a.W = guide->W;
+    a.gdtype = guide->dtype;
+    a.norm = params->norm;
+    a.dhalf = params->dist_dtype == DTS_F16;
+    a.k = params->sigma_s / params->sigma_r;
+    a.dX = dX;
+    a.dY = dY;
+    a.pitch = guide->W;
+    return cuda_status(launch_distances(a, (cudaStream_t)stream));
+}
+
+extern "C" int dts_filter(const dts_guide* guide, const dts_params* params, const float* src, float* dst, void* ws,
+                          size_t ws_bytes, dts_stream stream) {
+    int st = check_guide(guide);
+    if (!st) st = check_params(params);
+    if (st) return st;
+    if (!src || !dst) return DTS_ERR_INVALID_ARG;
+    Plans pl;
+    if ((st = make_plans(guide->H, guide->W, &pl))) return st;
+    dts_params p = *params;
+    p.conf_mode = DTS_CONF_PLAIN;
+    p.save_checkpoints = 0;
+    const Layout L = make_layout(guide->H, guide->W, &p, 0);
+    if (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.fwd_end) return DTS_ERR_WORKSPACE;
+    if ((st = ensure_prepared())) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    float* u = reinterpret_cast<float*>(ws_at(ws, L.u));
+    if ((st = run_distances(guide, &p, L, ws, src, DTS_F32, u, s))) return st;
+    float k2[kMaxPasses];
+    pass_log2a(p.sigma_s, p.passes, k2);
+    const int dh = p.dist_dtype == DTS_F16;
+    for (int i = 0; i < p.passes; ++i) {
+        PassArgs r = base_pass(guide, L);
+        r.src = u;
+        r.dst = u;
+        r.d = ws_at(ws, L.dX);
+        r.k2 = k2[i];
+        if ((st = cuda_status(launch_row_pass(r, dh, PASS_PLAIN, pl.rows, s)))) return st;
+        PassArgs c = base_pass(guide, L);
+        c.src = u;
+        c.d = ws_at(ws, L.dY);
+        c.k2 = k2[i];
+        if (i == p.passes - 1) {
+            c.dst = dst;
+            c.dst_pitch = guide->W;
+        } else {
+            c.dst = u;
+        }
+        if ((st = cuda_status(launch_col_pass(c, dh, PASS_PLAIN, pl.cols, s)))) return st;
+    }
+    return DTS_OK;
+}
+
+extern "C" int dts_solve(const dts_guide* guide, const void* target, int target_dtype, const float* conf,
+                         const float* z_init, const dts_params* params, float* z_out, void* ws, size_t ws_bytes,
+                         dts_stream stream) {
+    int st = check_guide(guide);
+    if (!st) st = check_params(params);
+    if (st) return st;
+    if (!target || !conf || !z_out || !valid_dtype(target_dtype)) return DTS_ERR_INVALID_ARG;
+    Plans pl;
+    if ((st = make_plans(guide->H, guide->W, &pl))) return st;
+    const Layout L = make_layout(guide->H, guide->W, params, 0);
+    if (params->iterations > 0 && (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.fwd_end))
+        return DTS_ERR_WORKSPACE;
+    if ((st = ensure_prepared())) return st;
+    return solve_forward(guide, target, target_dtype, conf, z_init, params, z_out, ws, L, pl, (cudaStream_t)stream);
+}
+
+extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, int target_dtype, const float* conf,
+                                  const float* z_init, const dts_params* params, void* ws, size_t ws_bytes,
+                                  const float* grad_z, float* grad_target, float* grad_conf, float* grad_guide,
+                                  float* grad_z_init, dts_stream stream) {
+    (void)guide; (void)target; (void)target_dtype; (void)conf; (void)z_init; (void)params; (void)ws;
+    (void)ws_bytes; (void)grad_z; (void)grad_target; (void)grad_conf; (void)grad_guide; (void)grad_z_init;
+    (void)stream;
+    return DTS_ERR_UNSUPPORTED;
+}
+
+extern "C" int dts_last_status(dts_stream stream) {
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return DTS_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_status, sizeof(int)) != cudaSuccess) return DTS_ERR_CUDA;
+    if (v != 0) {
+        const int zero = 0;
+        if (cudaMemcpyToSymbol(g_status, &zero, sizeof(int)) != cudaSuccess) return DTS_ERR_CUDA;
+    }
+    return v;
+}

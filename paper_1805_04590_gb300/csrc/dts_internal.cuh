@@ -1,0 +1,124 @@
+// Internal declarations shared by the libdts translation units (not installed).
+//
+// Data layout inside the workspace: every plane (distances, working buffer,
+// iterates) is H rows of `pitch` elements, pitch = W rounded up to 64, each
+// plane starting on a 256-byte boundary.  Rows are therefore 16-byte aligned
+// and the kernels load and store them with 16-byte vector accesses; the
+// padding columns [W, pitch) may hold anything and are masked on load.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/dts.h"
+
+namespace dts {
+
+constexpr int kPitchAlign = 64;     // elements
+constexpr size_t kPlaneAlign = 256; // bytes
+constexpr int kMaxPasses = 16;
+
+inline long long pitch_for(int W) { return ((long long)W + kPitchAlign - 1) / kPitchAlign * kPitchAlign; }
+
+// ---------------------------------------------------------------- device helpers
+template <typename T> __device__ __forceinline__ float to_f32(T v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+
+// Element of a dense plane of runtime dtype (target storage).
+__device__ __forceinline__ float load_any(const void* p, long long i, int dtype) {
+    if (dtype == DTS_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+    if (dtype == DTS_F16) return __half2float(static_cast<const __half*>(p)[i]);
+    return static_cast<const float*>(p)[i];
+}
+
+// ---------------------------------------------------------------- kernel arguments
+struct DistArgs {
+    const void* guide;
+    long long ch_stride, row_stride;
+    int C, H, W, gdtype, norm;
+    int dhalf;              // distance planes stored as FP16
+    float k;                // sigma_s / sigma_r
+    void* dX;
+    void* dY;
+    long long pitch;        // element pitch of dX/dY
+    // optional fused copy of an H x W plane (pitch W, dtype src_dtype) into dst (pitch `pitch`, FP32)
+    const void* src;
+    int src_dtype;
+    float* dst;
+};
+
+// One directional pass over lines of a plane held in the workspace.
+struct PassArgs {
+    const float* src;       // pass input (pitch `pitch`)
+    float* dst;             // pass output (may equal src)
+    long long dst_pitch;    // pitch of dst (vertical passes; horizontal passes use `pitch`)
+    const void* d;          // distances along the pass direction (pitch `pitch`)
+    int H, W;
+    long long pitch;
+    float k2;               // log2(a_i): w = exp2(k2 * d)
+    // update epilogue (last vertical pass of an iteration only)
+    const float* zk;        // z_k (pitch `pitch`)
+    const void* t;          // target (dense, pitch W, dtype t_dtype)
+    int t_dtype;
+    const float* c;         // confidence (dense pitch W) -- or chat (pitch `pitch`) when c_pitched
+    int c_pitched;
+    float* zout;            // z_{k+1}
+    long long zout_pitch;
+    float lambda, step;
+    int update;             // DTS_UPDATE_GD / DTS_UPDATE_JACOBI
+    int clamp_step;         // SUPPORT mode: step_i = min(step, 1 / (lambda + c_i))
+    // support mode: S -> chat = c * s_flat / S (written to zout)
+    float s_flat;
+};
+
+struct ColPlan {
+    int items;   // rows per thread
+    int warps;   // warps per CTA
+    int cluster; // CTAs per cluster along the column
+};
+
+struct RowPlan {
+    int items;   // elements per thread
+    int tpr;     // threads per row (multiple of 32)
+    int rpb;     // rows per CTA
+};
+
+enum PassKind { PASS_PLAIN = 0, PASS_UPDATE = 1, PASS_SUPPORT = 2, PASS_SUPPORT_CONF = 3 };
+
+// Kernel ids reported by the per-launch timer (dts_profile / dts_kernel_name).
+enum KernelId {
+    KID_DISTANCES = 0,
+    KID_COPY = 1,
+    KID_ROW_PLAIN = 2,
+    KID_ROW_SUPPORT = 3,
+    KID_COL_PLAIN = 4,
+    KID_COL_UPDATE = 5,
+    KID_COL_SUPPORT = 6,
+};
+// flags of a timing record
+constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
+constexpr int kFlagTarget16 = 2;   // target stored in 16 bits
+
+// per-launch timer (dts_profile.cu): returns a handle for prof_end, or -1 when off
+int prof_begin(int kernel, long long pixels, int flags, cudaStream_t s);
+void prof_end(int handle, cudaStream_t s);
+
+// launchers (dts_forward.cu); return cudaGetLastError() after the launch
+cudaError_t launch_distances(const DistArgs& a, cudaStream_t s);
+cudaError_t launch_copy_plane(const void* src, int src_dtype, long long src_pitch, float* dst, long long dst_pitch,
+                              int H, int W, cudaStream_t s);
+cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const RowPlan& p, cudaStream_t s);
+cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s);
+bool plan_rows(int W, RowPlan* p);
+bool plan_cols(int H, ColPlan* p);
+cudaError_t prepare_kernels();
+
+}  // namespace dts

@@ -1,0 +1,101 @@
+// Per-launch kernel timing: while enabled, every kernel libdts launches is bracketed
+// by two CUDA events recorded on the launch stream.  Used by the benchmark to take
+// the duration of each kernel inside the timed region.
+#include <mutex>
+#include <vector>
+
+#include "dts_internal.cuh"
+
+namespace dts {
+
+namespace {
+
+struct Record {
+    int kernel;
+    long long pixels;
+    int flags;
+    cudaEvent_t start, stop;
+};
+
+std::mutex g_mu;
+bool g_enabled = false;
+std::vector<Record> g_records;
+std::vector<cudaEvent_t> g_pool;
+constexpr size_t kMaxRecords = 1 << 16;
+
+cudaEvent_t take_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void recycle_all() {
+    for (auto& r : g_records) {
+        if (r.start) g_pool.push_back(r.start);
+        if (r.stop) g_pool.push_back(r.stop);
+    }
+    g_records.clear();
+}
+
+}  // namespace
+
+int prof_begin(int kernel, long long pixels, int flags, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_enabled || g_records.size() >= kMaxRecords) return -1;
+    Record r = {kernel, pixels, flags, take_event(), take_event()};
+    if (!r.start || !r.stop) return -1;
+    cudaEventRecord(r.start, s);
+    g_records.push_back(r);
+    return (int)g_records.size() - 1;
+}
+
+void prof_end(int handle, cudaStream_t s) {
+    if (handle < 0) return;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (handle < (int)g_records.size()) cudaEventRecord(g_records[handle].stop, s);
+}
+
+}  // namespace dts
+
+using namespace dts;
+
+extern "C" int dts_profile(int enable) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (enable) recycle_all();
+    g_enabled = enable != 0;
+    return DTS_OK;
+}
+
+extern "C" int dts_profile_read(int max_records, int* kernel, long long* pixels, int* flags, float* ms) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    const int n = (int)g_records.size() < max_records ? (int)g_records.size() : max_records;
+    for (int i = 0; i < n; ++i) {
+        const Record& r = g_records[i];
+        if (cudaEventSynchronize(r.stop) != cudaSuccess) return -DTS_ERR_CUDA;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.start, r.stop) != cudaSuccess) return -DTS_ERR_CUDA;
+        if (kernel) kernel[i] = r.kernel;
+        if (pixels) pixels[i] = r.pixels;
+        if (flags) flags[i] = r.flags;
+        if (ms) ms[i] = t;
+    }
+    return n;
+}
+
+extern "C" const char* dts_kernel_name(int kernel) {
+    switch (kernel) {
+        case KID_DISTANCES: return "distance_kernel";
+        case KID_COPY: return "copy_plane_kernel";
+        case KID_ROW_PLAIN: return "row_pass_kernel";
+        case KID_ROW_SUPPORT: return "row_pass_kernel<support>";
+        case KID_COL_PLAIN: return "col_pass_kernel";
+        case KID_COL_UPDATE: return "col_pass_kernel<update>";
+        case KID_COL_SUPPORT: return "col_pass_kernel<support>";
+        default: return "unknown";
+    }
+}

@@ -1,0 +1,257 @@
+"""Thin Python binding of libdts.so (the C ABI in include/dts.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA kernels
+of the library.  Functions take CUDA torch tensors (device memory and the
+current stream come from PyTorch) and keep the C entry-point names.  If the
+library is missing or cannot be loaded, every call raises; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional
+
+import torch
+
+from . import build as _build
+
+F32, BF16, F16 = 0, 1, 2
+NORM_L1, NORM_L2 = 0, 1
+UPDATE_GD, UPDATE_JACOBI = 0, 1
+CONF_PLAIN, CONF_SUPPORT = 0, 1
+
+STATUS = {0: "DTS_OK", 1: "DTS_ERR_INVALID_ARG", 2: "DTS_ERR_UNSUPPORTED", 3: "DTS_ERR_WORKSPACE",
+          4: "DTS_ERR_CUDA", 5: "DTS_ERR_TIMEOUT", 6: "DTS_ERR_NONFINITE"}
+
+_TORCH_DTYPE = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
+
+
+class DTSError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class CGuide(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int), ("dtype", ctypes.c_int),
+                ("data", ctypes.c_void_p), ("ch_stride", ctypes.c_longlong), ("row_stride", ctypes.c_longlong)]
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_float), ("sigma_s", ctypes.c_float), ("sigma_r", ctypes.c_float),
+                ("step", ctypes.c_float), ("iterations", ctypes.c_int), ("passes", ctypes.c_int),
+                ("norm", ctypes.c_int), ("update", ctypes.c_int), ("conf_mode", ctypes.c_int),
+                ("dist_dtype", ctypes.c_int), ("save_checkpoints", ctypes.c_int)]
+
+
+@dataclasses.dataclass
+class Params:
+    """Mirror of ``dts_params`` (see include/dts.h for the meaning of each field)."""
+    lam: float = 1.0
+    sigma_s: float = 8.0
+    sigma_r: float = 0.2
+    step: float = 0.99
+    iterations: int = 10
+    passes: int = 3
+    norm: int = NORM_L1
+    update: int = UPDATE_GD
+    conf_mode: int = CONF_PLAIN
+    dist_dtype: int = F32
+    save_checkpoints: int = 0
+
+    def c(self) -> CParams:
+        return CParams(self.lam, self.sigma_s, self.sigma_r, self.step, self.iterations, self.passes, self.norm,
+                       self.update, self.conf_mode, self.dist_dtype, self.save_checkpoints)
+
+
+_lib = None
+EXPORTS = ("dts_status_string", "dts_version", "dts_workspace_size", "dts_domain_transform", "dts_filter",
+           "dts_solve", "dts_solve_backward", "dts_last_status", "dts_profile", "dts_profile_read",
+           "dts_kernel_name")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Open libdts.so (building it first if it is missing); raises on failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"libdts.so not built ({path}); run paper_1805_04590_gb300.build")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    lib.dts_status_string.argtypes = [i]
+    lib.dts_status_string.restype = ctypes.c_char_p
+    lib.dts_version.restype = ctypes.c_char_p
+    lib.dts_workspace_size.argtypes = [P(CGuide), P(CParams), i]
+    lib.dts_workspace_size.restype = sz
+    lib.dts_domain_transform.argtypes = [P(CGuide), P(CParams), vp, vp, vp]
+    lib.dts_filter.argtypes = [P(CGuide), P(CParams), vp, vp, vp, sz, vp]
+    lib.dts_solve.argtypes = [P(CGuide), vp, i, vp, vp, P(CParams), vp, vp, sz, vp]
+    lib.dts_solve_backward.argtypes = [P(CGuide), vp, i, vp, vp, P(CParams), vp, sz, vp, vp, vp, vp, vp, vp]
+    lib.dts_last_status.argtypes = [vp]
+    lib.dts_profile.argtypes = [i]
+    lib.dts_profile_read.argtypes = [i, P(ctypes.c_int), P(ctypes.c_longlong), P(ctypes.c_int), P(ctypes.c_float)]
+    lib.dts_kernel_name.argtypes = [i]
+    lib.dts_kernel_name.restype = ctypes.c_char_p
+    for name in ("dts_domain_transform", "dts_filter", "dts_solve", "dts_solve_backward", "dts_last_status",
+                 "dts_profile", "dts_profile_read"):
+        getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise DTSError(status, what)
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else t.data_ptr()
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("libdts takes CUDA tensors")
+
+
+def guide_desc(guide: torch.Tensor) -> CGuide:
+    """Describe a (C, H, W) or (H, W) CUDA tensor (row-contiguous) as a dts_guide."""
+    if guide.dim() == 2:
+        guide = guide.unsqueeze(0)
+    if guide.dim() != 3 or guide.dtype not in _TORCH_DTYPE:
+        raise ValueError("guide must be (C, H, W) float32/bfloat16/float16")
+    if guide.stride(2) != 1:
+        raise ValueError("guide rows must be contiguous")
+    C, H, W = guide.shape
+    return CGuide(C, H, W, _TORCH_DTYPE[guide.dtype], guide.data_ptr(), guide.stride(0), guide.stride(1))
+
+
+def _dense(t: torch.Tensor, name: str, dtypes=(torch.float32,)):
+    if t.dtype not in dtypes or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {'/'.join(str(d) for d in dtypes)} tensor")
+
+
+def workspace_size(guide: torch.Tensor, params: Params, with_backward: bool = False) -> int:
+    g = guide_desc(guide)
+    p = params.c()
+    return load().dts_workspace_size(ctypes.byref(g), ctypes.byref(p), int(with_backward))
+
+
+def workspace(guide: torch.Tensor, params: Params, with_backward: bool = False) -> torch.Tensor:
+    """A caller-owned workspace tensor of the size libdts asks for."""
+    n = workspace_size(guide, params, with_backward)
+    if n == 0:
+        raise DTSError(1, "dts_workspace_size")
+    return torch.empty(n, dtype=torch.uint8, device=guide.device)
+
+
+def dts_domain_transform(guide: torch.Tensor, params: Params, stream=None):
+    """(dX, dY) distance planes of the guide, dtype float32 or float16 per params.dist_dtype."""
+    _need_cuda(guide)
+    g = guide_desc(guide)
+    H, W = g.H, g.W
+    dt = torch.float16 if params.dist_dtype == F16 else torch.float32
+    dX = torch.empty((H, W), dtype=dt, device=guide.device)
+    dY = torch.empty((H, W), dtype=dt, device=guide.device)
+    p = params.c()
+    _check(load().dts_domain_transform(ctypes.byref(g), ctypes.byref(p), dX.data_ptr(), dY.data_ptr(),
+                                       _stream(stream)), "dts_domain_transform")
+    return dX, dY
+
+
+def dts_filter(guide: torch.Tensor, src: torch.Tensor, params: Params, out: Optional[torch.Tensor] = None,
+               ws: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Edge-aware mean A src (H x W float32)."""
+    _need_cuda(guide, src)
+    _dense(src, "src")
+    g = guide_desc(guide)
+    out = torch.empty_like(src) if out is None else out
+    ws = workspace(guide, params) if ws is None else ws
+    p = params.c()
+    _check(load().dts_filter(ctypes.byref(g), ctypes.byref(p), src.data_ptr(), out.data_ptr(), ws.data_ptr(),
+                             ws.numel(), _stream(stream)), "dts_filter")
+    return out
+
+
+def dts_solve(guide: torch.Tensor, target: torch.Tensor, conf: torch.Tensor, params: Params,
+              z_init: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+              ws: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """The solver: returns z_K (H x W float32)."""
+    _need_cuda(guide, target, conf, z_init)
+    _dense(target, "target", tuple(_TORCH_DTYPE))
+    _dense(conf, "conf")
+    if z_init is not None:
+        _dense(z_init, "z_init")
+    g = guide_desc(guide)
+    out = torch.empty(target.shape, dtype=torch.float32, device=target.device) if out is None else out
+    ws = workspace(guide, params, bool(params.save_checkpoints)) if ws is None else ws
+    p = params.c()
+    _check(load().dts_solve(ctypes.byref(g), target.data_ptr(), _TORCH_DTYPE[target.dtype], conf.data_ptr(),
+                            _ptr(z_init), ctypes.byref(p), out.data_ptr(), ws.data_ptr(), ws.numel(),
+                            _stream(stream)), "dts_solve")
+    return out
+
+
+def dts_solve_backward(guide: torch.Tensor, target: torch.Tensor, conf: torch.Tensor, params: Params,
+                       ws: torch.Tensor, grad_z: torch.Tensor, z_init: Optional[torch.Tensor] = None,
+                       need_guide: bool = True, stream=None):
+    """Gradients (target, conf, guide or None, z_init or None) given dL/dz_K.
+
+    Must follow ``dts_solve`` with ``save_checkpoints=1`` on the same workspace."""
+    _need_cuda(guide, target, conf, grad_z, z_init)
+    _dense(grad_z, "grad_z")
+    g = guide_desc(guide)
+    dev = target.device
+    gt = torch.empty(target.shape, dtype=torch.float32, device=dev)
+    gc = torch.empty(target.shape, dtype=torch.float32, device=dev)
+    gg = torch.empty((g.C, g.H, g.W), dtype=torch.float32, device=dev) if need_guide else None
+    gz0 = torch.empty(target.shape, dtype=torch.float32, device=dev) if z_init is not None else None
+    p = params.c()
+    _check(load().dts_solve_backward(ctypes.byref(g), target.data_ptr(), _TORCH_DTYPE[target.dtype],
+                                     conf.data_ptr(), _ptr(z_init), ctypes.byref(p), ws.data_ptr(), ws.numel(),
+                                     grad_z.data_ptr(), gt.data_ptr(), gc.data_ptr(), _ptr(gg), _ptr(gz0),
+                                     _stream(stream)), "dts_solve_backward")
+    return gt, gc, gg, gz0
+
+
+def dts_last_status(stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device-side status word."""
+    return load().dts_last_status(_stream(stream))
+
+
+def dts_profile(enable: bool) -> None:
+    """Start (clearing earlier records) or stop per-launch event timing in libdts."""
+    _check(load().dts_profile(int(enable)), "dts_profile")
+
+
+def dts_profile_read(max_records: int = 1 << 16):
+    """Records [(kernel name, kernel id, pixels, flags, ms)] since dts_profile(True)."""
+    lib = load()
+    k = (ctypes.c_int * max_records)()
+    px = (ctypes.c_longlong * max_records)()
+    fl = (ctypes.c_int * max_records)()
+    ms = (ctypes.c_float * max_records)()
+    n = lib.dts_profile_read(max_records, k, px, fl, ms)
+    if n < 0:
+        raise DTSError(-n, "dts_profile_read")
+    return [(lib.dts_kernel_name(k[i]).decode(), k[i], px[i], fl[i], ms[i]) for i in range(n)]
+
+
+def version() -> str:
+    return load().dts_version().decode()

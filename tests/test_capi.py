@@ -1,0 +1,114 @@
+"""Host-side checks of the C ABI: the library loads, exports every function that
+include/dts.h declares, sizes workspaces and rejects bad arguments before any
+device work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1805_04590_gb300 import dts
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(dts_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_function():
+    lib = dts.load()
+    names = declared_functions()
+    assert "dts_solve" in names and "dts_filter" in names and "dts_solve_backward" in names
+    assert "dts_domain_transform" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(dts.EXPORTS) <= set(names)
+
+
+def test_version_and_status_strings():
+    lib = dts.load()
+    assert b"sm_103a" in lib.dts_version()
+    assert lib.dts_status_string(0) == b"DTS_OK"
+    assert lib.dts_status_string(5) == b"DTS_ERR_TIMEOUT"
+
+
+def _guide(C=3, H=40, W=50, dtype=dts.F32):
+    return dts.CGuide(C, H, W, dtype, 0x1000, 0, 0)
+
+
+def test_workspace_size_layout():
+    lib = dts.load()
+    p = dts.Params(iterations=5).c()
+    g = _guide(H=40, W=50)
+    n0 = lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p), 0)
+    pitch = 64
+    plane = 40 * pitch * 4
+    assert n0 == 4 * plane  # dX, dY, working buffer, iterate
+    n1 = lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p), 1)
+    assert n1 == (3 + 5 + 2 * 3 + 5) * plane  # + K checkpoints, 2N pass inputs, adjoint buffers
+    p16 = dts.Params(iterations=5, dist_dtype=dts.F16).c()
+    assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p16), 0) == 2 * (40 * pitch * 2) + 2 * plane
+    bad = dts.Params(sigma_s=-1.0).c()
+    assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(bad), 0) == 0
+
+
+@pytest.mark.parametrize("field,value", [("sigma_s", 0.0), ("sigma_r", -1.0), ("lam", -0.5), ("step", 0.0),
+                                         ("iterations", -1), ("passes", 0), ("passes", 17), ("norm", 2),
+                                         ("update", 3), ("conf_mode", 2), ("dist_dtype", 1)])
+def test_invalid_params_rejected_synchronously(field, value):
+    lib = dts.load()
+    prm = dts.Params()
+    setattr(prm, field, value)
+    p = prm.c()
+    g = _guide()
+    rc = lib.dts_solve(ctypes.byref(g), 0x2000, 0, 0x3000, None, ctypes.byref(p), 0x4000, 0x5000, 1 << 30, None)
+    assert rc == 1
+
+
+def test_invalid_guide_and_pointers_rejected():
+    lib = dts.load()
+    p = dts.Params().c()
+    for g in (_guide(C=0), _guide(H=0), _guide(W=0), _guide(dtype=7), dts.CGuide(3, 4, 5, 0, 0, 0, 0),
+              dts.CGuide(3, 4, 5, 0, 0x1000, 0, 4), dts.CGuide(3, 4, 5, 0, 0x1000, 10, 5)):
+        assert lib.dts_solve(ctypes.byref(g), 0x2000, 0, 0x3000, None, ctypes.byref(p), 0x4000, 0x5000,
+                             1 << 30, None) == 1
+        assert lib.dts_filter(ctypes.byref(g), ctypes.byref(p), 0x2000, 0x3000, 0x5000, 1 << 30, None) == 1
+    g = _guide()
+    assert lib.dts_solve(ctypes.byref(g), None, 0, 0x3000, None, ctypes.byref(p), 0x4000, 0x5000, 1 << 30,
+                         None) == 1
+    assert lib.dts_solve(ctypes.byref(g), 0x2000, 9, 0x3000, None, ctypes.byref(p), 0x4000, 0x5000, 1 << 30,
+                         None) == 1
+    assert lib.dts_domain_transform(ctypes.byref(g), ctypes.byref(p), None, 0x10, None) == 1
+
+
+def test_workspace_errors_and_size_limits():
+    lib = dts.load()
+    p = dts.Params(iterations=2).c()
+    g = _guide()
+    # too small, misaligned, missing
+    assert lib.dts_solve(ctypes.byref(g), 0x2000, 0, 0x3000, None, ctypes.byref(p), 0x4000, 0x5000, 16, None) == 3
+    assert lib.dts_solve(ctypes.byref(g), 0x2000, 0, 0x3000, None, ctypes.byref(p), 0x4000, 0x5010, 1 << 30,
+                         None) == 3
+    assert lib.dts_solve(ctypes.byref(g), 0x2000, 0, 0x3000, None, ctypes.byref(p), 0x4000, None, 1 << 30,
+                         None) == 3
+    # rows longer than the horizontal kernels hold, columns taller than a cluster holds
+    for gg in (_guide(H=4, W=20000), _guide(H=20000, W=4)):
+        assert lib.dts_solve(ctypes.byref(gg), 0x2000, 0, 0x3000, None, ctypes.byref(p), 0x4000, 0x5000,
+                             1 << 40, None) == 2
+
+
+def test_product_path_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1805_04590_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                src = open(os.path.join(dirpath, fn)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), fn
+                assert "dts_oracle" not in src and "liborc" not in src, fn

@@ -1,0 +1,188 @@
+"""GPU parity of the forward path (through the C ABI) against the FP64 oracle.
+
+Tolerance (FP32 arithmetic on the GPU, FP64 in the oracle): the solve and the
+filter must agree to max |gpu - oracle| <= 1e-4 * (max t - min t), the bound
+stated for this solver; distances to 2e-6 relative (FP32 rounding of a sum
+of C absolute differences).  Reduced-precision storage is checked against the
+oracle run on the same rounded inputs, with the same bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1805_04590_gb300 import dts, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+NP_DT = {torch.float32: np.float32, torch.float16: np.float16}
+
+
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def to_dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev()).to(dtype)
+
+
+def rounded(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def oracle_solve(prob_guide, t, c, prm, **kw):
+    return oracle.solve(prob_guide, t, c, lam=prm.lam, sigma_s=prm.sigma_s, sigma_r=prm.sigma_r, step=prm.step,
+                        iterations=prm.iterations, passes=prm.passes, norm=prm.norm, update=prm.update,
+                        conf_mode=prm.conf_mode, **kw)
+
+
+def assert_close(z, ref, t, what=""):
+    rng = float(np.max(t) - np.min(t)) or 1.0
+    err = float(np.abs(z - ref).max()) if z.size else 0.0
+    assert err <= TOL * rng, f"{what}: max|gpu-oracle| = {err:.3e} > {TOL * rng:.3e}"
+
+
+# ---------------------------------------------------------------- distances
+@pytest.mark.parametrize("gdt", [torch.float32, torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("norm", [dts.NORM_L1, dts.NORM_L2])
+def test_distances(gdt, norm):
+    prob = workloads.random_problem(37, 53, C=4, seed=2)
+    g = to_dev(prob.guide, gdt)
+    prm = dts.Params(sigma_s=8.0, sigma_r=0.2, norm=norm)
+    dX, dY = dts.dts_domain_transform(g, prm)
+    rX, rY = oracle.distances(rounded(g), 8.0, 0.2, norm)
+    np.testing.assert_allclose(dX.cpu().numpy(), rX, rtol=2e-6, atol=0)
+    np.testing.assert_allclose(dY.cpu().numpy(), rY, rtol=2e-6, atol=0)
+    prm.dist_dtype = dts.F16
+    hX, hY = dts.dts_domain_transform(g, prm)
+    np.testing.assert_allclose(hX.float().cpu().numpy(), rX, rtol=2 ** -10, atol=0)
+    np.testing.assert_allclose(hY.float().cpu().numpy(), rY, rtol=2 ** -10, atol=0)
+
+
+def test_distances_strided_guide():
+    prob = workloads.random_problem(20, 30, C=3, seed=4)
+    big = torch.zeros((3, 25, 40), device=dev())
+    big[:, :20, :30] = to_dev(prob.guide)
+    view = big[:, :20, :30]
+    dX, dY = dts.dts_domain_transform(view, dts.Params())
+    rX, rY = oracle.distances(prob.guide, 8.0, 0.2)
+    np.testing.assert_allclose(dX.cpu().numpy(), rX, rtol=2e-6)
+    np.testing.assert_allclose(dY.cpu().numpy(), rY, rtol=2e-6)
+
+
+# ---------------------------------------------------------------- filter
+FILTER_SHAPES = [(1, 1), (1, 17), (19, 1), (7, 13), (33, 257), (300, 517), (257, 64), (1000, 77), (2100, 40),
+                 (3, 9000), (4100, 9), (64, 8193)]
+
+
+@pytest.mark.parametrize("H,W", FILTER_SHAPES)
+def test_filter(H, W):
+    prob = workloads.random_problem(H, W, C=3, seed=H * 7 + W)
+    prm = dts.Params(sigma_s=12.0, sigma_r=0.3, passes=3)
+    g = to_dev(prob.guide)
+    src = to_dev(prob.target)
+    out = dts.dts_filter(g, src, prm)
+    ref = oracle.filter(prob.guide, prob.target, 12.0, 0.3, passes=3)
+    assert_close(out.cpu().numpy(), ref, prob.target, f"filter {H}x{W}")
+
+
+def test_filter_preserves_constants_and_aliases():
+    prob = workloads.random_problem(120, 333, C=3, seed=8)
+    g = to_dev(prob.guide)
+    x = torch.full((120, 333), 0.75, device=dev())
+    dts.dts_filter(g, x, dts.Params(), out=x)
+    assert float((x - 0.75).abs().max()) <= 1e-6
+
+
+# ---------------------------------------------------------------- solve
+def test_solve_plain_workload():
+    wl = workloads.make(0)
+    p = wl.problems[0]
+    prm = dts.Params(lam=wl.params.lam, sigma_s=wl.params.sigma_s, sigma_r=wl.params.sigma_r,
+                     iterations=wl.params.iterations, passes=wl.params.passes)
+    z = dts.dts_solve(to_dev(p.guide), to_dev(p.target), to_dev(p.conf), prm)
+    ref = oracle_solve(p.guide, p.target, p.conf, prm)
+    assert_close(z.cpu().numpy(), ref, p.target, "plain 256x256")
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 40), (40, 1), (31, 45), (129, 300), (700, 263), (1100, 90)])
+@pytest.mark.parametrize("update", [dts.UPDATE_GD, dts.UPDATE_JACOBI])
+def test_solve_shapes(H, W, update):
+    prob = workloads.random_problem(H, W, C=3, seed=H + 3 * W + update)
+    prm = dts.Params(lam=0.99, sigma_s=16.0, sigma_r=0.1, iterations=5, update=update)
+    z = dts.dts_solve(to_dev(prob.guide), to_dev(prob.target), to_dev(prob.conf), prm)
+    ref = oracle_solve(prob.guide, prob.target, prob.conf, prm)
+    assert_close(z.cpu().numpy(), ref, prob.target, f"solve {H}x{W} update={update}")
+
+
+@pytest.mark.parametrize("variant", ["l2", "support", "zinit", "k0", "checkpoints", "passes1", "passes5"])
+def test_solve_variants(variant):
+    prob = workloads.random_problem(150, 211, C=3, seed=11)
+    prm = dts.Params(lam=1.0, sigma_s=8.0, sigma_r=0.2, iterations=6)
+    kw = {}
+    z_init = None
+    if variant == "l2":
+        prm.norm = dts.NORM_L2
+    elif variant == "support":
+        prm.conf_mode = dts.CONF_SUPPORT
+    elif variant == "zinit":
+        z_init = np.random.default_rng(3).random(prob.target.shape).astype(np.float32)
+        kw["z_init"] = z_init.astype(np.float64)
+    elif variant == "k0":
+        prm.iterations = 0
+    elif variant == "checkpoints":
+        prm.save_checkpoints = 1
+    elif variant == "passes1":
+        prm.passes = 1
+    elif variant == "passes5":
+        prm.passes = 5
+    z = dts.dts_solve(to_dev(prob.guide), to_dev(prob.target), to_dev(prob.conf), prm,
+                      z_init=None if z_init is None else to_dev(z_init))
+    ref = oracle_solve(prob.guide, prob.target, prob.conf, prm, **kw)
+    assert_close(z.cpu().numpy(), ref, prob.target, variant)
+
+
+@pytest.mark.parametrize("sdt", [torch.bfloat16, torch.float16])
+def test_solve_reduced_precision_storage(sdt):
+    """Guide and target stored in 16 bits, FP32 arithmetic: against the oracle on
+    the same rounded inputs the FP32 bound still holds."""
+    prob = workloads.random_problem(200, 300, C=3, seed=12)
+    g = to_dev(prob.guide, sdt)
+    t = to_dev(prob.target, sdt)
+    prm = dts.Params(lam=1.0, sigma_s=8.0, sigma_r=0.2, iterations=8)
+    z = dts.dts_solve(g, t, to_dev(prob.conf), prm)
+    ref = oracle_solve(rounded(g), rounded(t), prob.conf, prm)
+    assert_close(z.cpu().numpy(), ref, rounded(t), f"storage {sdt}")
+
+
+def test_solve_fp16_distances():
+    """FP16 distance planes: checked against the oracle solving on its own FP64
+    distances rounded to FP16."""
+    prob = workloads.random_problem(180, 260, C=3, seed=13)
+    prm = dts.Params(lam=1.0, sigma_s=8.0, sigma_r=0.2, iterations=8, dist_dtype=dts.F16)
+    z = dts.dts_solve(to_dev(prob.guide), to_dev(prob.target), to_dev(prob.conf), prm)
+    dX, dY = oracle.distances(prob.guide, 8.0, 0.2)
+    dX = dX.astype(np.float16).astype(np.float64)
+    dY = dY.astype(np.float16).astype(np.float64)
+    ref = oracle.solve_d(dX, dY, prob.target, prob.conf, lam=1.0, sigma_s=8.0, iterations=8)
+    assert_close(z.cpu().numpy(), ref, prob.target, "fp16 distances")
+
+
+def test_solve_full_stereo_workload():
+    """The 2880 x 1988, 20-iteration stereo-shaped solve at full size, all outputs."""
+    wl = workloads.make(1)
+    p = wl.problems[0]
+    q = wl.params
+    prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes)
+    z = dts.dts_solve(to_dev(p.guide), to_dev(p.target), to_dev(p.conf), prm)
+    assert dts.dts_last_status() == 0
+    ref = oracle_solve(p.guide, p.target, p.conf, prm)
+    assert_close(z.cpu().numpy(), ref, p.target, "stereo 2880x1988")
+
+
+def test_last_status_clean():
+    assert dts.dts_last_status() == 0
