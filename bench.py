@@ -40,6 +40,7 @@ if ROOT not in sys.path:
 METRIC = "megapixels/sec per DTS solve (fwd, fwd+bwd) and % of GB300 HBM roofline at stated error"
 UNIT = "MP/s"
 TOL = 1e-4
+PROFILE_EVERY = 10
 
 # algorithmic bytes per pixel of each kernel (s_d distance storage, s_t target storage, C guide
 # channels of s_g bytes): every input element read once, every output element written once
@@ -215,9 +216,12 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         clk.start()
         time.sleep(0.15)
-        dts.dts_profile(True)
+        dts.dts_profile(1)
+        dts.dts_profile(0)
         wall0 = time.perf_counter()
-        for e0, e1 in evs:
+        for i, (e0, e1) in enumerate(evs):
+            # per-kernel events on every PROFILE_EVERY-th step (events between kernels cost a little)
+            dts.dts_profile(2 if i % PROFILE_EVERY == 0 else 0)
             flush.zero_()
             e0.record(stream)
             dts.dts_solve(g, t, c, prm, out=out, ws=ws)
@@ -225,7 +229,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         barrier()
-        dts.dts_profile(False)
+        dts.dts_profile(0)
         clk.stop()
         ms = [a.elapsed_time(b) for a, b in evs]
         return ms, wall, clk.summary(), dts.dts_profile_read()
@@ -243,7 +247,9 @@ def run_ours(args, rank, world, local_rank):
     if dts.dts_last_status() != 0:
         raise RuntimeError("device status not clean after the timed region")
 
-    # per-kernel durations inside the timed region
+    # per-kernel durations inside the timed region (sampled steps)
+    profiled_steps = len(range(0, args.steps, PROFILE_EVERY))
+    launches_per_step = len(recs) // profiled_steps
     kern = {}
     for name, _, px, fl, t_ms in recs:
         k = kern.setdefault(name, {"launches": 0, "ms": 0.0, "pixels": 0})
@@ -304,7 +310,8 @@ def run_ours(args, rank, world, local_rank):
                                              "l2": "flushed between steps (512 MiB write)",
                                              "parallelism": f"replicas x{world}"}),
             "roofline": roof, "kernels": kernels, "e2e": e2e,
-            "gpu_launches": len(recs), "clocks": clk, "wall_s_timed_region": round(wall, 4)}
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk, "wall_s_timed_region": round(wall, 4),
+            "kernel_timing": f"CUDA events around each kernel on every {PROFILE_EVERY}th timed step"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle

@@ -143,10 +143,11 @@ int dts_solve_backward(const dts_guide* guide, const void* target, int target_dt
 int dts_last_status(dts_stream stream);
 
 /* ---- per-launch kernel timing (a tracing aid; not part of the paper's method) ----
- * dts_profile(1) clears the record and, until dts_profile(0), brackets every kernel the
- * library launches with two CUDA events on that launch's stream.  Host-side only; it does
- * not change what the kernels compute. */
-int dts_profile(int enable);
+ * mode 1: clear the record and start bracketing every kernel the library launches with two
+ * CUDA events on that launch's stream; mode 2: resume without clearing; mode 0: stop.
+ * Host-side only; it does not change what the kernels compute (events between kernels do
+ * prevent the programmatic early launch of the next kernel).  DTS_ERR_INVALID_ARG for other modes. */
+int dts_profile(int mode);
 
 /* Copies up to max_records records of the launches made since dts_profile(1), in launch
  * order: kernel id (see dts_kernel_name), pixels the launch covered, flags (bit 0: FP16

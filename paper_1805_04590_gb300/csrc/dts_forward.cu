@@ -5,13 +5,31 @@
 //  col_pass_kernel   one vertical pass; the last one of an iteration also applies the
 //                    data-term update of Eq. 3 (gradient step) or Eq. 4 (fixed point)
 //
-// Every 1-D sweep J[n] = (1 - w_n) x[n] + w_n J[n-1] (w_n = a^d_n) is an affine map of
-// J[n-1].  A thread owns ITEMS consecutive elements of a line in registers, folds them
-// into one affine map, the maps of all threads of the line are combined by a scan
-// (warp shuffles, then shared memory, then distributed shared memory across the CTAs
-// of a cluster for columns), and each thread then replays its elements from the exact
-// carry-in.  A line is read once and written once per pass: 2 s_z + s_d bytes per pixel.
+// A pass runs, along every line, the causal sweep J[n] = (1 - w_n) x[n] + w_n J[n-1] and then
+// the anti-causal sweep K[n] = (1 - w_{n+1}) J[n] + w_{n+1} K[n+1] on its result, with
+// w_n = a^(d_n) the feedback across the distance d_n between positions n-1 and n.
+//
+// Parallel form.  A thread owns a segment of ITEMS consecutive positions of a line in
+// registers.  For the carry c entering the segment from the left and the anti-causal value k
+// entering from the right, the segment satisfies
+//     c_out   = A c + B                      (causal value leaving on the right)
+//     k_start = al k + be c + ga             (anti-causal value at its first position)
+// with A = prod w, B = causal sweep from 0, al = prod w', and
+//     be = sum_n r_n (1 - w'_n) P_n,  ga = sum_n r_n (1 - w'_n) Q_n
+// where P_n = prod_{m<=n} w_m, Q_n = causal sweep from 0 at n, r_n = prod_{m<n} w'_m: all of it
+// accumulates in ONE forward sweep over the segment.  Adjacent groups compose associatively
+// (CoupledMode::suf_compose), so a single exchange of these five numbers between the segments
+// of a line -- warp shuffles, shared memory, and distributed shared memory between the CTAs of
+// a cluster for columns -- gives every segment its exact carries in both directions, after
+// which it replays its positions once each way.  A line is read once and written once per
+// pass: 2 s_z + s_d bytes per pixel.
 #include <cooperative_groups.h>
+
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <type_traits>
+#include <utility>
 
 #include "dts_internal.cuh"
 
@@ -23,34 +41,171 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// v -> A v + B
+// 2^x with the SFU instruction (PTX ex2.approx.ftz.f32; relative error ~2^-22, results below
+// the normal range flush to zero, which is harmless for a feedback weight).
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Programmatic dependent launch: a kernel launched with the programmatic-serialization
+// attribute may start while its predecessor drains; it must wait for the predecessor's
+// completion (and memory) before touching global data, and it lets its own successor start
+// launching once it no longer needs the SM slots it would free.  Both are no-ops otherwise.
+__device__ __forceinline__ void wait_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void release_successor() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// v -> A v + B, the causal carry map of a group of positions
 struct Aff {
     float A, B;
 };
 
-// apply `first`, then `second`
-__device__ __forceinline__ Aff compose(Aff first, Aff second) {
-    return Aff{first.A * second.A, fmaf(second.A, first.B, second.B)};
+__device__ __forceinline__ Aff aff_identity() { return Aff{1.f, 0.f}; }
+
+// first `f`, then `s`
+__device__ __forceinline__ Aff aff_compose(const Aff& f, const Aff& s) {
+    return Aff{f.A * s.A, fmaf(s.A, f.B, s.B)};
 }
 
-// inclusive scan over lanes 0..lane (lane 0 applied first)
-__device__ __forceinline__ Aff warp_scan_up(Aff v, int lane) {
+template <typename T>
+__device__ __forceinline__ T shfl_up_t(const T& v, int off) {
+    constexpr int n = sizeof(T) / 4;
+    T r;
+    const float* s = reinterpret_cast<const float*>(&v);
+    float* d = reinterpret_cast<float*>(&r);
+#pragma unroll
+    for (int i = 0; i < n; ++i) d[i] = __shfl_up_sync(kFull, s[i], off);
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_down_t(const T& v, int off) {
+    constexpr int n = sizeof(T) / 4;
+    T r;
+    const float* s = reinterpret_cast<const float*>(&v);
+    float* d = reinterpret_cast<float*>(&r);
+#pragma unroll
+    for (int i = 0; i < n; ++i) d[i] = __shfl_down_sync(kFull, s[i], off);
+    return r;
+}
+
+// ---------------------------------------------------------------- segment algebra
+// Normalised pass: causal sweep, then the anti-causal sweep on its result.
+struct CoupledMode {
+    struct Suf {
+        float A, B, al, be, ga;
+    };
+    static __device__ __forceinline__ Suf suf_identity() { return Suf{1.f, 0.f, 1.f, 0.f, 0.f}; }
+    // group `f` followed by group `s` (s to the right of f)
+    static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) {
+        Suf o;
+        o.A = f.A * s.A;
+        o.B = fmaf(s.A, f.B, s.B);
+        o.al = f.al * s.al;
+        o.be = fmaf(f.al * s.be, f.A, f.be);
+        o.ga = fmaf(f.al, fmaf(s.be, f.B, s.ga), f.ga);
+        return o;
+    }
+    template <int N>
+    static __device__ __forceinline__ void local(const float (&x)[N], const float (&w)[N], float wn, Aff& pre,
+                                                 Suf& suf) {
+        float P = 1.f, Q = 0.f, r = 1.f, be = 0.f, ga = 0.f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            P *= w[j];
+            Q = fmaf(w[j], Q - x[j], x[j]);
+            const float wp = (j + 1 < N) ? w[j + 1] : wn;
+            const float coef = fmaf(-r, wp, r);
+            be = fmaf(coef, P, be);
+            ga = fmaf(coef, Q, ga);
+            r *= wp;
+        }
+        pre = Aff{P, Q};
+        suf = Suf{P, Q, r, be, ga};
+    }
+    // c: causal value entering on the left; c_out: leaving on the right; after: all groups to the right
+    template <int N>
+    static __device__ __forceinline__ void apply(float (&x)[N], const float (&w)[N], float wn, float c, float c_out,
+                                                 const Suf& after) {
+        float J = c;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            J = fmaf(w[j], J - x[j], x[j]);
+            x[j] = J;
+        }
+        float K = fmaf(after.be, c_out, after.ga);
+#pragma unroll
+        for (int j = N - 1; j >= 0; --j) {
+            const float wp = (j + 1 < N) ? w[j + 1] : wn;
+            K = fmaf(wp, K - x[j], x[j]);
+            x[j] = K;
+        }
+    }
+};
+
+// Support of the unnormalised kernel (confidence weighting): causal P[n] = x[n] + w_n P[n-1] and
+// anti-causal Q[n] = x[n] + w'_n Q[n+1], both on x; the result is P + Q - x.
+struct SupportMode {
+    struct Suf {
+        float al, de;
+    };
+    static __device__ __forceinline__ Suf suf_identity() { return Suf{1.f, 0.f}; }
+    static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) {
+        return Suf{f.al * s.al, fmaf(f.al, s.de, f.de)};
+    }
+    template <int N>
+    static __device__ __forceinline__ void local(const float (&x)[N], const float (&w)[N], float wn, Aff& pre,
+                                                 Suf& suf) {
+        float A = 1.f, B = 0.f, r = 1.f, de = 0.f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            A *= w[j];
+            B = fmaf(w[j], B, x[j]);
+            de = fmaf(r, x[j], de);
+            r *= (j + 1 < N) ? w[j + 1] : wn;
+        }
+        pre = Aff{A, B};
+        suf = Suf{r, de};
+    }
+    template <int N>
+    static __device__ __forceinline__ void apply(float (&x)[N], const float (&w)[N], float wn, float c, float c_out,
+                                                 const Suf& after) {
+        (void)c_out;
+        float Pv[N];
+        float Pc = c;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            Pc = fmaf(w[j], Pc, x[j]);
+            Pv[j] = Pc;
+        }
+        float Qc = after.de;
+#pragma unroll
+        for (int j = N - 1; j >= 0; --j) {
+            const float wp = (j + 1 < N) ? w[j + 1] : wn;
+            Qc = fmaf(wp, Qc, x[j]);
+            x[j] = Pv[j] + Qc - x[j];
+        }
+    }
+};
+
+__device__ __forceinline__ Aff scan_pre(Aff v, int lane) {
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        float A = __shfl_up_sync(kFull, v.A, off);
-        float B = __shfl_up_sync(kFull, v.B, off);
-        if (lane >= off) v = compose(Aff{A, B}, v);
+        const Aff o = shfl_up_t(v, off);
+        if (lane >= off) v = aff_compose(o, v);
     }
     return v;
 }
 
-// inclusive scan over lanes lane..31 (lane 31 applied first)
-__device__ __forceinline__ Aff warp_scan_down(Aff v, int lane) {
+template <class M>
+__device__ __forceinline__ typename M::Suf scan_suf(typename M::Suf v, int lane) {
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        float A = __shfl_down_sync(kFull, v.A, off);
-        float B = __shfl_down_sync(kFull, v.B, off);
-        if (lane + off < 32) v = compose(Aff{A, B}, v);
+        const typename M::Suf o = shfl_down_t(v, off);
+        if (lane + off < 32) v = M::suf_compose(v, o);
     }
     return v;
 }
@@ -76,205 +231,193 @@ __device__ __forceinline__ float load1_d(const void* base, long long idx) {
 }
 
 // ---------------------------------------------------------------- distances
+// Thread = one column x and kDistRows consecutive rows; a warp covers 32 consecutive columns,
+// so every guide row segment is one coalesced access and the left neighbour comes from the
+// adjacent lane.
+constexpr int kDistRows = 8;
+
 template <typename GT, typename DT>
 __global__ void __launch_bounds__(256) distance_kernel(DistArgs a) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= a.W) return;
+    wait_predecessor();
+    const int lane = threadIdx.x & 31;
+    const int x = blockIdx.x * 32 + lane;
+    const int y0 = (blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kDistRows;
+    const bool xok = x < a.W;
     const GT* I = static_cast<const GT*>(a.guide);
-    const long long p = (long long)y * a.row_stride + x;
-    float sx = 0.f, sy = 0.f;
+    float sx[kDistRows], sy[kDistRows];
+#pragma unroll
+    for (int r = 0; r < kDistRows; ++r) sx[r] = sy[r] = 0.f;
+    const bool l2 = a.norm == DTS_NORM_L2;
     for (int c = 0; c < a.C; ++c) {
         const GT* Ic = I + (long long)c * a.ch_stride;
-        const float v = to_f32<GT>(Ic[p]);
-        if (x > 0) {
-            const float dv = v - to_f32<GT>(Ic[p - 1]);
-            sx += a.norm == DTS_NORM_L2 ? dv * dv : fabsf(dv);
-        }
-        if (y > 0) {
-            const float dv = v - to_f32<GT>(Ic[p - a.row_stride]);
-            sy += a.norm == DTS_NORM_L2 ? dv * dv : fabsf(dv);
+        float prev = (xok && y0 > 0 && y0 - 1 < a.H) ? to_f32<GT>(Ic[(long long)(y0 - 1) * a.row_stride + x]) : 0.f;
+#pragma unroll
+        for (int r = 0; r < kDistRows; ++r) {
+            const int y = y0 + r;
+            const bool ok = xok && y < a.H;
+            const long long p = (long long)y * a.row_stride + x;
+            const float v = ok ? to_f32<GT>(Ic[p]) : 0.f;
+            float left = __shfl_up_sync(kFull, v, 1);
+            if (lane == 0) left = (ok && x > 0) ? to_f32<GT>(Ic[p - 1]) : 0.f;
+            const float dxv = v - left, dyv = v - prev;
+            sx[r] += l2 ? dxv * dxv : fabsf(dxv);
+            sy[r] += l2 ? dyv * dyv : fabsf(dyv);
+            prev = v;
         }
     }
-    float dx, dy;
-    if (a.norm == DTS_NORM_L2) {
-        dx = sqrtf(fmaf(a.k * a.k, sx, 1.f));
-        dy = sqrtf(fmaf(a.k * a.k, sy, 1.f));
-    } else {
-        dx = fmaf(a.k, sx, 1.f);
-        dy = fmaf(a.k, sy, 1.f);
+#pragma unroll
+    for (int r = 0; r < kDistRows; ++r) {
+        const int y = y0 + r;
+        if (!(xok && y < a.H)) continue;
+        float dx, dy;
+        if (l2) {
+            dx = sqrtf(fmaf(a.k * a.k, sx[r], 1.f));
+            dy = sqrtf(fmaf(a.k * a.k, sy[r], 1.f));
+        } else {
+            dx = fmaf(a.k, sx[r], 1.f);
+            dy = fmaf(a.k, sy[r], 1.f);
+        }
+        if (x == 0) dx = 1.f;
+        if (y == 0) dy = 1.f;
+        const long long q = (long long)y * a.pitch + x;
+        static_cast<DT*>(a.dX)[q] = from_f32<DT>(dx);
+        static_cast<DT*>(a.dY)[q] = from_f32<DT>(dy);
+        if (a.dst) a.dst[q] = load_any(a.src, (long long)y * a.W + x, a.src_dtype);
     }
-    const long long q = (long long)y * a.pitch + x;
-    static_cast<DT*>(a.dX)[q] = from_f32<DT>(dx);
-    static_cast<DT*>(a.dY)[q] = from_f32<DT>(dy);
-    if (a.dst) a.dst[q] = load_any(a.src, (long long)y * a.W + x, a.src_dtype);
 }
 
 __global__ void __launch_bounds__(256) copy_plane_kernel(const void* src, int src_dtype, long long sp, float* dst,
                                                          long long dp, int H, int W) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
+    wait_predecessor();
     if (x >= W || y >= H) return;
     dst[(long long)y * dp + x] = load_any(src, (long long)y * sp + x, src_dtype);
 }
 
 // ---------------------------------------------------------------- horizontal pass
-// CTA = rpb rows x tpr threads; thread t of a row owns elements [t*ITEMS, t*ITEMS+ITEMS).
-// KIND: PASS_PLAIN (normalised causal then anti-causal on the causal result) or
-//       PASS_SUPPORT (unnormalised sweeps of the constant 1: out = P + Q - 1).
+// CTA = rpb rows x tpr threads (tpr a multiple of 32, so a warp never spans two rows); thread t
+// of a row owns positions [t*ITEMS, t*ITEMS + ITEMS).  The segments of a row exchange their
+// aggregates through warp shuffles and one shared-memory round.
+// KIND: PASS_PLAIN (CoupledMode on the plane) or PASS_SUPPORT (SupportMode on the constant 1).
 template <int ITEMS, bool DHALF, int KIND>
 __global__ void __launch_bounds__(1024) row_pass_kernel(PassArgs a, int tpr) {
     static_assert(ITEMS % 4 == 0, "ITEMS must be a multiple of 4");
-    __shared__ Aff s_fwd[32];
-    __shared__ Aff s_bwd[32];
+    using M = typename std::conditional<KIND == PASS_SUPPORT, SupportMode, CoupledMode>::type;
+    using Suf = typename M::Suf;
+    __shared__ Aff s_pre[32];
+    __shared__ Suf s_suf[32];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const int rloc = tid / tpr;
     const int t = tid - rloc * tpr;
-    const int wpr = tpr >> 5;           // warps per row
-    const int wrow = t >> 5;            // warp index within the row
-    const int wbase = warp - wrow;      // first warp of this row
+    const int wpr = tpr >> 5;       // warps per row
+    const int wrow = t >> 5;        // warp index within the row
+    const int wbase = warp - wrow;  // first warp of this row
     const int rpb = blockDim.x / tpr;
     const int row = blockIdx.x * rpb + rloc;
     const bool row_ok = row < a.H;
     const int e0 = t * ITEMS;
     const long long P = a.pitch;
-    const bool in_row = row_ok && e0 < P;
+    const long long base = (long long)row * P + e0;
+    const bool live = row_ok && e0 < P;
 
+    wait_predecessor();
     float x[ITEMS], w[ITEMS];
-    if (in_row) {
-        const long long base = (long long)row * P + e0;
+    if (live) {
 #pragma unroll
         for (int q = 0; q < ITEMS / 4; ++q) {
             if constexpr (KIND == PASS_SUPPORT) {
                 x[4 * q] = x[4 * q + 1] = x[4 * q + 2] = x[4 * q + 3] = 1.f;
             } else {
-                float4 v = *reinterpret_cast<const float4*>(a.src + base + 4 * q);
+                const float4 v = *reinterpret_cast<const float4*>(a.src + base + 4 * q);
                 x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
             }
             load4_d<DHALF>(a.d, base + 4 * q, &w[4 * q]);
         }
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) w[j] = ex2(a.k2 * w[j]);
+        if (e0 + ITEMS > a.W) {  // the segment holding the row end: clear the padding
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j)
+                if (e0 + j >= a.W) x[j] = w[j] = 0.f;
+        }
+        if (e0 == 0) w[0] = 0.f;  // the row starts here
     } else {
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) x[j] = w[j] = 0.f;
     }
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const int e = e0 + j;
-        const bool ok = row_ok && e < a.W;
-        x[j] = ok ? x[j] : 0.f;
-        w[j] = (ok && e > 0) ? exp2f(a.k2 * w[j]) : 0.f;
-    }
-    // weight between the last owned element and the next one (anti-causal needs w[e+1])
+    // weight between this segment's last position and the next segment's first
     float wn = __shfl_down_sync(kFull, w[0], 1);
     if (lane == 31) {
         const int en = e0 + ITEMS;
-        wn = (row_ok && en < a.W) ? exp2f(a.k2 * load1_d<DHALF>(a.d, (long long)row * P + en)) : 0.f;
+        wn = (row_ok && en < a.W) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)row * P + en)) : 0.f;
     }
 
-    // ---- causal sweep
-    Aff m{1.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        if constexpr (KIND == PASS_SUPPORT) m.B = fmaf(w[j], m.B, x[j]);
-        else m.B = fmaf(w[j], m.B - x[j], x[j]);
-        m.A *= w[j];
+    Aff own_pre;
+    Suf own_suf;
+    M::local(x, w, wn, own_pre, own_suf);
+    const Aff inc_pre = scan_pre(own_pre, lane);
+    const Suf inc_suf = scan_suf<M>(own_suf, lane);
+    Aff pre = shfl_up_t(inc_pre, 1);
+    Suf suf = shfl_down_t(inc_suf, 1);
+    if (lane == 0) pre = aff_identity();
+    if (lane == 31) suf = M::suf_identity();
+    if (wpr > 1) {
+        if (lane == 31) s_pre[warp] = inc_pre;
+        if (lane == 0) s_suf[warp] = inc_suf;
+        __syncthreads();
+        Aff wpre = aff_identity();
+        for (int q = 0; q < wrow; ++q) wpre = aff_compose(wpre, s_pre[wbase + q]);
+        Suf wsuf = M::suf_identity();
+        for (int q = wrow + 1; q < wpr; ++q) wsuf = M::suf_compose(wsuf, s_suf[wbase + q]);
+        pre = aff_compose(wpre, pre);
+        suf = M::suf_compose(suf, wsuf);
     }
-    Aff inc = warp_scan_up(m, lane);
-    if (lane == 31) s_fwd[warp] = inc;
-    float eA = __shfl_up_sync(kFull, inc.A, 1), eB = __shfl_up_sync(kFull, inc.B, 1);
-    if (lane == 0) { eA = 1.f; eB = 0.f; }
-    // ---- anti-causal local maps need the causal results first; for SUPPORT the
-    // anti-causal sweep runs on x itself, so its reduction can start now.
-    float Pv[KIND == PASS_SUPPORT ? ITEMS : 1];
-    __syncthreads();
-    float carry = 0.f;
-    for (int q = 0; q < wrow; ++q) carry = fmaf(s_fwd[wbase + q].A, carry, s_fwd[wbase + q].B);
-    carry = fmaf(eA, carry, eB);
-    {
-        float J = carry;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if constexpr (KIND == PASS_SUPPORT) {
-                J = fmaf(w[j], J, x[j]);
-                Pv[j] = J;
-            } else {
-                J = fmaf(w[j], J - x[j], x[j]);
-                x[j] = J;
-            }
-        }
-    }
+    release_successor();
+    const float c = pre.B;
+    const float c_out = fmaf(own_pre.A, c, own_pre.B);
+    M::apply(x, w, wn, c, c_out, suf);
 
-    // ---- anti-causal sweep (right to left), w'_j = w_{j+1}
-    m = Aff{1.f, 0.f};
+    if (live) {
 #pragma unroll
-    for (int j = ITEMS - 1; j >= 0; --j) {
-        const float wp = (j == ITEMS - 1) ? wn : w[j + 1];
-        if constexpr (KIND == PASS_SUPPORT) m.B = fmaf(wp, m.B, x[j]);
-        else m.B = fmaf(wp, m.B - x[j], x[j]);
-        m.A *= wp;
-    }
-    inc = warp_scan_down(m, lane);
-    if (lane == 0) s_bwd[warp] = inc;
-    eA = __shfl_down_sync(kFull, inc.A, 1);
-    eB = __shfl_down_sync(kFull, inc.B, 1);
-    if (lane == 31) { eA = 1.f; eB = 0.f; }
-    __syncthreads();
-    carry = 0.f;
-    for (int q = wpr - 1; q > wrow; --q) carry = fmaf(s_bwd[wbase + q].A, carry, s_bwd[wbase + q].B);
-    carry = fmaf(eA, carry, eB);
-    {
-        float K = carry;
-#pragma unroll
-        for (int j = ITEMS - 1; j >= 0; --j) {
-            const float wp = (j == ITEMS - 1) ? wn : w[j + 1];
-            if constexpr (KIND == PASS_SUPPORT) {
-                K = fmaf(wp, K, x[j]);
-                // P + Q - x; padding elements stay 0
-                const bool ok = row_ok && (e0 + j) < a.W;
-                Pv[j] = ok ? Pv[j] + K - x[j] : 0.f;
-            } else {
-                K = fmaf(wp, K - x[j], x[j]);
-                x[j] = K;
-            }
-        }
-    }
-    if (in_row) {
-        const long long base = (long long)row * P + e0;
-#pragma unroll
-        for (int q = 0; q < ITEMS / 4; ++q) {
-            float4 v;
-            if constexpr (KIND == PASS_SUPPORT) v = make_float4(Pv[4 * q], Pv[4 * q + 1], Pv[4 * q + 2], Pv[4 * q + 3]);
-            else v = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-            *reinterpret_cast<float4*>(a.dst + base + 4 * q) = v;
-        }
+        for (int q = 0; q < ITEMS / 4; ++q)
+            *reinterpret_cast<float4*>(a.dst + base + 4 * q) =
+                make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
     }
 }
 
 // ---------------------------------------------------------------- vertical pass
-// Grid (ceil(W/32), cluster, 1) with cluster dims (1, cluster, 1): one cluster per strip
-// of 32 columns covering all H rows.  Lane = column (coalesced 128-byte row segments),
-// warp q of CTA r owns rows [(r*NW + q)*ITEMS, +ITEMS).  Carries cross warps through
-// shared memory and CTAs through distributed shared memory.
-// KIND: PASS_PLAIN, PASS_UPDATE (z_{k+1} from z_k, t, c and zbar) or
-//       PASS_SUPPORT_CONF (unnormalised sweeps of the row support s: S = P + Q - s,
-//       then chat = c * s_flat / S).
-// Largest CTA a vertical-pass shape uses (bounds the registers per thread).
+// Grid (ceil(W/32), cluster) with cluster dims (1, cluster, 1): one cluster per strip of 32
+// columns covering all H rows.  Lane = column (128-byte coalesced row segments); warp q of CTA
+// r owns rows [(r*NW + q)*ITEMS, +ITEMS).  The segments of a column are the warps of all CTAs of
+// the cluster: one shared-memory round inside a CTA, one distributed-shared-memory round
+// across CTAs.
+// KIND: PASS_PLAIN (CoupledMode, store), PASS_UPDATE (CoupledMode, then z_{k+1} from z_k, t, c
+// and zbar) or PASS_SUPPORT_CONF (SupportMode on the row support s, then chat = c s_flat / S).
 template <int ITEMS>
 constexpr int col_max_threads() {
     return ITEMS <= 8 ? 1024 : 512;
 }
+// resident CTAs of the largest shape the register budget must allow (the update epilogue keeps
+// its operand loads in flight and gets the larger budget)
+template <int ITEMS, int KIND>
+constexpr int col_min_blocks() {
+    return (ITEMS == 16 && KIND != PASS_UPDATE) ? 2 : 1;
+}
 
 template <int ITEMS, bool DHALF, int KIND>
-__global__ void __launch_bounds__(col_max_threads<ITEMS>()) col_pass_kernel(PassArgs a) {
+__global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS, KIND>()) col_pass_kernel(PassArgs a) {
+    using M = typename std::conditional<KIND == PASS_SUPPORT_CONF, SupportMode, CoupledMode>::type;
+    using Suf = typename M::Suf;
     cg::cluster_group cluster = cg::this_cluster();
-    __shared__ Aff s_wf[32][32];
-    __shared__ Aff s_wb[32][32];
-    __shared__ Aff s_cf[32];
-    __shared__ Aff s_cb[32];
-    __shared__ float s_carry_f[32];
-    __shared__ float s_carry_b[32];
+    __shared__ Aff s_pre[32][32];
+    __shared__ Suf s_suf[32][32];
+    __shared__ Aff s_cta_pre[32];
+    __shared__ Suf s_cta_suf[32];
+    __shared__ Aff s_cl_pre[32];
+    __shared__ Suf s_cl_suf[32];
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -286,110 +429,90 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>()) col_pass_kernel(Pass
     const int row0 = (rank * NW + warp) * ITEMS;
     const long long P = a.pitch;
 
+    wait_predecessor();
+    if constexpr (KIND == PASS_UPDATE) {
+        // the update operands are read only at the end: start bringing them into L2 now
+        if ((lane == 0 || lane == 31) && col_ok) {
+            const int tsz = a.t_dtype == DTS_F32 ? 4 : 2;
+#pragma unroll 1
+            for (int j = 0; j < ITEMS; ++j) {
+                const int r = row0 + j;
+                if (r < a.H) {
+                    prefetch_l2(a.zk + (long long)r * P + col);
+                    prefetch_l2(static_cast<const char*>(a.t) + ((long long)r * a.W + col) * tsz);
+                    prefetch_l2(a.c + (a.c_pitched ? (long long)r * P : (long long)r * a.W) + col);
+                }
+            }
+        }
+    }
+
     float x[ITEMS], w[ITEMS];
+    const bool full = col_ok && row0 + ITEMS <= a.H;
+    {
+        const float* src = a.src + (long long)row0 * P + col;
+        const long long d0 = (long long)row0 * P + col;
+        if (full) {
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const int r = row0 + j;
-        const bool ok = col_ok && r < a.H;
-        const long long idx = (long long)r * P + col;
-        x[j] = ok ? a.src[idx] : 0.f;
-        w[j] = ok ? load1_d<DHALF>(a.d, idx) : 0.f;
+            for (int j = 0; j < ITEMS; ++j) {
+                x[j] = src[j * P];
+                w[j] = load1_d<DHALF>(a.d, d0 + j * P);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const bool ok = col_ok && row0 + j < a.H;
+                x[j] = ok ? src[j * P] : 0.f;
+                w[j] = ok ? load1_d<DHALF>(a.d, d0 + j * P) : 0.f;
+            }
+        }
     }
     float wn;
     {
         const int rn = row0 + ITEMS;
-        wn = (col_ok && rn < a.H) ? exp2f(a.k2 * load1_d<DHALF>(a.d, (long long)rn * P + col)) : 0.f;
+        wn = (col_ok && rn < a.H) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)rn * P + col)) : 0.f;
     }
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const int r = row0 + j;
-        w[j] = (col_ok && r > 0 && r < a.H) ? exp2f(a.k2 * w[j]) : 0.f;
+    for (int j = 0; j < ITEMS; ++j) w[j] = ex2(a.k2 * w[j]);
+    if (!full) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j)
+            if (!(col_ok && row0 + j < a.H)) w[j] = 0.f;
     }
+    if (row0 == 0) w[0] = 0.f;  // the column starts here
 
-    // ---- causal (top to bottom)
-    Aff m{1.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        if constexpr (KIND == PASS_SUPPORT_CONF) m.B = fmaf(w[j], m.B, x[j]);
-        else m.B = fmaf(w[j], m.B - x[j], x[j]);
-        m.A *= w[j];
-    }
-    s_wf[warp][lane] = m;
+    Aff own_pre;
+    Suf own_suf;
+    M::local(x, w, wn, own_pre, own_suf);
+    s_pre[warp][lane] = own_pre;
+    s_suf[warp][lane] = own_suf;
     __syncthreads();
-    if (warp == 0) {
-        Aff tot{1.f, 0.f};
-        for (int q = 0; q < NW; ++q) tot = compose(tot, s_wf[q][lane]);
-        s_cf[lane] = tot;
-    }
-    cluster.sync();
-    if (warp == 0) {
-        float c = 0.f;
-        for (int q = 0; q < rank; ++q) {
-            const Aff o = *cluster.map_shared_rank(&s_cf[lane], q);
-            c = fmaf(o.A, c, o.B);
+    Aff wpre = aff_identity();
+    for (int q = 0; q < warp; ++q) wpre = aff_compose(wpre, s_pre[q][lane]);
+    Suf wsuf = M::suf_identity();
+    for (int q = warp + 1; q < NW; ++q) wsuf = M::suf_compose(wsuf, s_suf[q][lane]);
+    if (CS > 1) {
+        // CTA totals: the last warp holds the full prefix, the first warp the full suffix
+        if (warp == NW - 1) s_cta_pre[lane] = aff_compose(wpre, own_pre);
+        if (warp == 0) s_cta_suf[lane] = M::suf_compose(own_suf, wsuf);
+        cluster.sync();
+        if (warp == 0) {
+            Aff cp = aff_identity();
+            for (int q = 0; q < rank; ++q) cp = aff_compose(cp, *cluster.map_shared_rank(&s_cta_pre[lane], q));
+            Suf cs = M::suf_identity();
+            for (int q = rank + 1; q < CS; ++q) cs = M::suf_compose(cs, *cluster.map_shared_rank(&s_cta_suf[lane], q));
+            s_cl_pre[lane] = cp;
+            s_cl_suf[lane] = cs;
         }
-        s_carry_f[lane] = c;
+        __syncthreads();
+        wpre = aff_compose(s_cl_pre[lane], wpre);
+        wsuf = M::suf_compose(wsuf, s_cl_suf[lane]);
     }
-    __syncthreads();
-    float Pv[KIND == PASS_SUPPORT_CONF ? ITEMS : 1];
-    {
-        float J = s_carry_f[lane];
-        for (int q = 0; q < warp; ++q) J = fmaf(s_wf[q][lane].A, J, s_wf[q][lane].B);
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if constexpr (KIND == PASS_SUPPORT_CONF) {
-                J = fmaf(w[j], J, x[j]);
-                Pv[j] = J;
-            } else {
-                J = fmaf(w[j], J - x[j], x[j]);
-                x[j] = J;
-            }
-        }
-    }
-
-    // ---- anti-causal (bottom to top), w'_r = w_{r+1}
-    m = Aff{1.f, 0.f};
-#pragma unroll
-    for (int j = ITEMS - 1; j >= 0; --j) {
-        const float wp = (j == ITEMS - 1) ? wn : w[j + 1];
-        if constexpr (KIND == PASS_SUPPORT_CONF) m.B = fmaf(wp, m.B, x[j]);
-        else m.B = fmaf(wp, m.B - x[j], x[j]);
-        m.A *= wp;
-    }
-    s_wb[warp][lane] = m;
-    __syncthreads();
-    if (warp == 0) {
-        Aff tot{1.f, 0.f};
-        for (int q = NW - 1; q >= 0; --q) tot = compose(tot, s_wb[q][lane]);
-        s_cb[lane] = tot;
-    }
-    cluster.sync();
-    if (warp == 0) {
-        float c = 0.f;
-        for (int q = CS - 1; q > rank; --q) {
-            const Aff o = *cluster.map_shared_rank(&s_cb[lane], q);
-            c = fmaf(o.A, c, o.B);
-        }
-        s_carry_b[lane] = c;
-    }
-    __syncthreads();
-    // all remote reads of this CTA are done: peers may exit once everyone arrived
+    // every remote read of this CTA is done: peers may exit once all have arrived
     cluster.barrier_arrive();
-    {
-        float K = s_carry_b[lane];
-        for (int q = NW - 1; q > warp; --q) K = fmaf(s_wb[q][lane].A, K, s_wb[q][lane].B);
-#pragma unroll
-        for (int j = ITEMS - 1; j >= 0; --j) {
-            const float wp = (j == ITEMS - 1) ? wn : w[j + 1];
-            if constexpr (KIND == PASS_SUPPORT_CONF) {
-                K = fmaf(wp, K, x[j]);
-                Pv[j] = Pv[j] + K - x[j];
-            } else {
-                K = fmaf(wp, K - x[j], x[j]);
-                x[j] = K;
-            }
-        }
-    }
+    release_successor();
+    const float c = wpre.B;
+    const float c_out = fmaf(own_pre.A, c, own_pre.B);
+    M::apply(x, w, wn, c, c_out, wsuf);
 
     // ---- epilogue
 #pragma unroll
@@ -404,40 +527,56 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>()) col_pass_kernel(Pass
             const float zb = x[j];
             const float z = a.zk[idx];
             const float t = load_any(a.t, di, a.t_dtype);
-            const float c = a.c_pitched ? a.c[idx] : a.c[di];
+            const float cf = a.c_pitched ? a.c[idx] : a.c[di];
             float zn;
             if (a.update == DTS_UPDATE_JACOBI) {
-                const float den = a.lambda + c;
-                zn = den != 0.f ? (a.lambda * zb + c * t) / den : z;
+                const float den = a.lambda + cf;
+                zn = den != 0.f ? (a.lambda * zb + cf * t) / den : z;
             } else {
                 float eta = a.step;
-                if (a.clamp_step && a.lambda + c > 0.f) eta = fminf(eta, 1.f / (a.lambda + c));
-                zn = z - eta * (a.lambda * (z - zb) + c * (z - t));
+                if (a.clamp_step && a.lambda + cf > 0.f) eta = fminf(eta, 1.f / (a.lambda + cf));
+                zn = z - eta * (a.lambda * (z - zb) + cf * (z - t));
             }
             a.zout[(long long)r * a.zout_pitch + col] = zn;
         } else {
-            const float c = a.c[(long long)r * a.W + col];
-            a.zout[idx] = c * a.s_flat / Pv[j];
+            a.zout[idx] = a.c[(long long)r * a.W + col] * a.s_flat / x[j];
         }
     }
     cluster.barrier_wait();
 }
 
-template <int ITEMS, bool DHALF, int KIND>
-cudaError_t launch_col_t(const PassArgs& a, const ColPlan& p, cudaStream_t s) {
+// launch with programmatic stream serialization (unless disabled) and an optional cluster shape
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, int cluster_y, cudaStream_t s,
+                      Args&&... args) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)((a.W + 31) / 32), (unsigned)p.cluster, 1);
-    cfg.blockDim = dim3((unsigned)(32 * p.warps), 1, 1);
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = (unsigned)p.cluster;
-    attr[0].val.clusterDim.z = 1;
+    cudaLaunchAttribute attr[2];
+    int n = 0;
+    if (cluster_y > 0) {
+        attr[n].id = cudaLaunchAttributeClusterDimension;
+        attr[n].val.clusterDim.x = 1;
+        attr[n].val.clusterDim.y = (unsigned)cluster_y;
+        attr[n].val.clusterDim.z = 1;
+        ++n;
+    }
+    if (pdl_enabled()) {
+        attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[n].val.programmaticStreamSerializationAllowed = 1;
+        ++n;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, col_pass_kernel<ITEMS, DHALF, KIND>, a);
+    cfg.numAttrs = n;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+template <int ITEMS, bool DHALF, int KIND>
+cudaError_t launch_col_t(const PassArgs& a, const ColPlan& p, cudaStream_t s) {
+    return launch_ex(col_pass_kernel<ITEMS, DHALF, KIND>, dim3((unsigned)((a.W + 31) / 32), (unsigned)p.cluster, 1),
+                     dim3((unsigned)(32 * p.warps), 1, 1), p.cluster, s, a);
 }
 
 template <int ITEMS, bool DHALF>
@@ -454,21 +593,18 @@ template <int ITEMS, bool DHALF>
 cudaError_t launch_row_k(const PassArgs& a, int kind, const RowPlan& p, cudaStream_t s) {
     const dim3 grid((unsigned)((a.H + p.rpb - 1) / p.rpb));
     const dim3 block((unsigned)(p.tpr * p.rpb));
-    if (kind == PASS_SUPPORT) row_pass_kernel<ITEMS, DHALF, PASS_SUPPORT><<<grid, block, 0, s>>>(a, p.tpr);
-    else row_pass_kernel<ITEMS, DHALF, PASS_PLAIN><<<grid, block, 0, s>>>(a, p.tpr);
-    return cudaGetLastError();
+    if (kind == PASS_SUPPORT) return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_SUPPORT>, grid, block, 0, s, a, p.tpr);
+    return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_PLAIN>, grid, block, 0, s, a, p.tpr);
 }
 
 template <int ITEMS, bool DHALF>
 cudaError_t allow_clusters() {
     cudaError_t e = cudaSuccess;
-    const int kinds[3] = {PASS_PLAIN, PASS_UPDATE, PASS_SUPPORT_CONF};
-    for (int k : kinds) {
-        const void* f = nullptr;
-        if (k == PASS_PLAIN) f = (const void*)col_pass_kernel<ITEMS, DHALF, PASS_PLAIN>;
-        if (k == PASS_UPDATE) f = (const void*)col_pass_kernel<ITEMS, DHALF, PASS_UPDATE>;
-        if (k == PASS_SUPPORT_CONF) f = (const void*)col_pass_kernel<ITEMS, DHALF, PASS_SUPPORT_CONF>;
-        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    const void* fs[3] = {(const void*)col_pass_kernel<ITEMS, DHALF, PASS_PLAIN>,
+                         (const void*)col_pass_kernel<ITEMS, DHALF, PASS_UPDATE>,
+                         (const void*)col_pass_kernel<ITEMS, DHALF, PASS_SUPPORT_CONF>};
+    for (const void* f : fs) {
+        const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (r != cudaSuccess) e = r;
     }
     return e;
@@ -480,19 +616,19 @@ cudaError_t allow_clusters() {
 cudaError_t launch_col_dispatch(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s);
 
 cudaError_t launch_distances(const DistArgs& a, cudaStream_t s) {
-    const dim3 block(256);
-    const dim3 grid((unsigned)((a.W + 255) / 256), (unsigned)a.H);
+    const dim3 block(256);  // 8 warps x kDistRows rows
+    const dim3 grid((unsigned)((a.W + 31) / 32), (unsigned)((a.H + 8 * kDistRows - 1) / (8 * kDistRows)));
     const int h = prof_begin(KID_DISTANCES, (long long)a.H * a.W, a.dhalf ? kFlagDistHalf : 0, s);
+    cudaError_t e;
     if (a.dhalf) {
-        if (a.gdtype == DTS_BF16) distance_kernel<__nv_bfloat16, __half><<<grid, block, 0, s>>>(a);
-        else if (a.gdtype == DTS_F16) distance_kernel<__half, __half><<<grid, block, 0, s>>>(a);
-        else distance_kernel<float, __half><<<grid, block, 0, s>>>(a);
+        if (a.gdtype == DTS_BF16) e = launch_ex(distance_kernel<__nv_bfloat16, __half>, grid, block, 0, s, a);
+        else if (a.gdtype == DTS_F16) e = launch_ex(distance_kernel<__half, __half>, grid, block, 0, s, a);
+        else e = launch_ex(distance_kernel<float, __half>, grid, block, 0, s, a);
     } else {
-        if (a.gdtype == DTS_BF16) distance_kernel<__nv_bfloat16, float><<<grid, block, 0, s>>>(a);
-        else if (a.gdtype == DTS_F16) distance_kernel<__half, float><<<grid, block, 0, s>>>(a);
-        else distance_kernel<float, float><<<grid, block, 0, s>>>(a);
+        if (a.gdtype == DTS_BF16) e = launch_ex(distance_kernel<__nv_bfloat16, float>, grid, block, 0, s, a);
+        else if (a.gdtype == DTS_F16) e = launch_ex(distance_kernel<__half, float>, grid, block, 0, s, a);
+        else e = launch_ex(distance_kernel<float, float>, grid, block, 0, s, a);
     }
-    const cudaError_t e = cudaGetLastError();
     prof_end(h, s);
     return e;
 }
@@ -502,8 +638,7 @@ cudaError_t launch_copy_plane(const void* src, int src_dtype, long long src_pitc
     const dim3 block(256);
     const dim3 grid((unsigned)((W + 255) / 256), (unsigned)H);
     const int h = prof_begin(KID_COPY, (long long)H * W, 0, s);
-    copy_plane_kernel<<<grid, block, 0, s>>>(src, src_dtype, src_pitch, dst, dst_pitch, H, W);
-    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e = launch_ex(copy_plane_kernel, grid, block, 0, s, src, src_dtype, src_pitch, dst, dst_pitch, H, W);
     prof_end(h, s);
     return e;
 }
@@ -538,9 +673,11 @@ cudaError_t launch_col_dispatch(const PassArgs& a, int dist_half, int kind, cons
 // Horizontal plan: ITEMS elements per thread, one row per tpr threads (<= 1024).
 bool plan_rows(int W, RowPlan* p) {
     int items;
-    if (W <= 8 * 1024) items = 8;
+    if (W <= 256) items = 8;
     else if (W <= 16 * 1024) items = 16;
     else return false;
+    static const char* env = getenv("DTS_ROW_ITEMS");  // tuning aid: force 8 or 16
+    if (env && (atoi(env) == 8 || atoi(env) == 16) && (W + atoi(env) - 1) / atoi(env) <= 1024) items = atoi(env);
     int tpr = (W + items - 1) / items;
     tpr = (tpr + 31) / 32 * 32;
     int rpb = 256 / tpr;
@@ -551,16 +688,32 @@ bool plan_rows(int W, RowPlan* p) {
     return true;
 }
 
-// Vertical plan: the first (items, warps) shape whose cluster holds the whole column
-// with at most 8 CTAs, else at most 16 (non-portable cluster size).
+// Vertical plan: columns up to 256 rows in one CTA; else the first (items, warps) shape whose
+// cluster holds the whole column with at most 8 CTAs, else at most 16 (non-portable size).
 bool plan_cols(int H, ColPlan* p) {
+    // DTS_COL_PLAN="items,warps" overrides the shape (tuning aid)
+    static const char* env = getenv("DTS_COL_PLAN");
+    if (env) {
+        int it = 0, nw = 0;
+        if (sscanf(env, "%d,%d", &it, &nw) == 2 && (it == 8 || it == 16 || it == 32 || it == 40) && nw >= 1 &&
+            nw * 32 <= (it <= 8 ? 1024 : 512)) {
+            const int cs = (H + it * nw - 1) / (it * nw);
+            if (cs <= 16) {
+                p->items = it;
+                p->warps = nw;
+                p->cluster = cs;
+                return true;
+            }
+        }
+    }
     if (H <= 256) {
         p->items = 8;
         p->warps = (H + 7) / 8;
         p->cluster = 1;
         return true;
     }
-    static const int cand[][2] = {{8, 8}, {16, 8}, {16, 16}, {32, 16}, {40, 16}};
+    // measured on the 2880 x 1988 stereo workload: 32 rows x 8 warps per CTA is fastest
+    static const int cand[][2] = {{32, 8}, {16, 16}, {32, 16}, {40, 16}};
     for (int limit : {8, 16}) {
         for (const auto& c : cand) {
             const int rows = c[0] * c[1];

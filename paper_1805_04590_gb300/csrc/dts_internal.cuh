@@ -11,6 +11,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "../../include/dts.h"
 
@@ -19,6 +20,12 @@ namespace dts {
 constexpr int kPitchAlign = 64;     // elements
 constexpr size_t kPlaneAlign = 256; // bytes
 constexpr int kMaxPasses = 16;
+
+// Programmatic dependent launch between consecutive kernels (off when DTS_NO_PDL is set).
+inline bool pdl_enabled() {
+    static const bool on = getenv("DTS_NO_PDL") == nullptr;
+    return on;
+}
 
 inline long long pitch_for(int W) { return ((long long)W + kPitchAlign - 1) / kPitchAlign * kPitchAlign; }
 

@@ -64,10 +64,11 @@ void prof_end(int handle, cudaStream_t s) {
 
 using namespace dts;
 
-extern "C" int dts_profile(int enable) {
+extern "C" int dts_profile(int mode) {
+    if (mode < 0 || mode > 2) return DTS_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (enable) recycle_all();
-    g_enabled = enable != 0;
+    if (mode == 1) recycle_all();
+    g_enabled = mode != 0;
     return DTS_OK;
 }
 

@@ -235,9 +235,9 @@ def dts_last_status(stream=None) -> int:
     return load().dts_last_status(_stream(stream))
 
 
-def dts_profile(enable: bool) -> None:
-    """Start (clearing earlier records) or stop per-launch event timing in libdts."""
-    _check(load().dts_profile(int(enable)), "dts_profile")
+def dts_profile(mode: int) -> None:
+    """Per-launch event timing in libdts: 1 start (clearing earlier records), 2 resume, 0 stop."""
+    _check(load().dts_profile(int(mode)), "dts_profile")
 
 
 def dts_profile_read(max_records: int = 1 << 16):
