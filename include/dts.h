@@ -137,6 +137,27 @@ int dts_solve_backward(const dts_guide* guide, const void* target, int target_dt
                        float* grad_target, float* grad_conf, float* grad_guide, float* grad_z_init,
                        dts_stream stream);
 
+/* dts_solve without a caller workspace.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory (code inside a host framework that owns every
+ * device allocation, or a latency-critical loop where an allocation could block, fail or break
+ * a fixed memory budget) and so cannot pass a workspace.  Arguments and results are those of
+ * dts_solve; inputs and outputs are still the caller's.  The scratch is a 16 MiB device array
+ * inside the library (dts_noalloc_max_workspace() bytes), held by every GPU that loads the
+ * library until the process exits; problems whose dts_workspace_size(with_backward = 0)
+ * exceeds it return DTS_ERR_WORKSPACE (16 bytes per padded pixel with FP32 distances: about
+ * one megapixel), and
+ * save_checkpoints = 1 returns DTS_ERR_UNSUPPORTED.  It allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library call.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last call's contents
+ * (every plane a solve reads is written by that solve first): calls that overlap on the GPU,
+ * on any streams, race and give wrong results. */
+int dts_solve_noalloc(const dts_guide* guide, const void* target, int target_dtype, const float* conf,
+                      const float* z_init, const dts_params* params, float* z_out, dts_stream stream);
+
+/* Size in bytes of the scratch array dts_solve_noalloc uses. */
+size_t dts_noalloc_max_workspace(void);
+
 /* Synchronises `stream`, then returns and clears the device-side status word of
  * the current device (DTS_OK, or e.g. DTS_ERR_TIMEOUT), or DTS_ERR_CUDA if the
  * synchronisation itself failed. */

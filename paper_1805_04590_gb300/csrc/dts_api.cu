@@ -362,6 +362,56 @@ extern "C" int dts_solve(const dts_guide* guide, const void* target, int target_
     return solve_forward(guide, target, target_dtype, conf, z_init, params, z_out, ws, L, pl, (cudaStream_t)stream);
 }
 
+// ---------------------------------------------------------------- solve without allocation
+// Callers that cannot allocate device memory (for example code running inside a host
+// framework that owns every device allocation, or a latency-critical loop where an allocation
+// could block, fail or exceed a fixed memory budget) cannot provide a workspace.  For them the
+// solve can use this library-owned scratch array instead.  It is a file-scope device array, so
+// every GPU that loads the library holds it until the process exits; all calls share it.
+namespace dts {
+namespace {
+constexpr size_t kStaticWorkspaceBytes = (size_t)16 << 20;  // 16 MiB
+__device__ __align__(256) unsigned char g_static_workspace[kStaticWorkspaceBytes];
+std::mutex g_static_mutex;
+void* g_static_workspace_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  Host code cannot use the
+// array's name as a device address; it is looked up once per device, with that device current.
+int static_workspace(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DTS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_workspace_ptr[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_workspace);
+        if (e != cudaSuccess || ptr == nullptr) return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
+        g_static_workspace_ptr[dev] = ptr;
+    }
+    *out = g_static_workspace_ptr[dev];
+    return DTS_OK;
+}
+}  // namespace
+}  // namespace dts
+
+extern "C" size_t dts_noalloc_max_workspace(void) { return kStaticWorkspaceBytes; }
+
+extern "C" int dts_solve_noalloc(const dts_guide* guide, const void* target, int target_dtype, const float* conf,
+                                 const float* z_init, const dts_params* params, float* z_out, dts_stream stream) {
+    int st = check_guide(guide);
+    if (!st) st = check_params(params);
+    if (st) return st;
+    if (!target || !conf || !z_out || !valid_dtype(target_dtype)) return DTS_ERR_INVALID_ARG;
+    if (params->save_checkpoints) return DTS_ERR_UNSUPPORTED;  // checkpoints must outlive the call
+    Plans pl;
+    if ((st = make_plans(guide->H, guide->W, &pl))) return st;
+    const Layout L = make_layout(guide->H, guide->W, params, 0);
+    if (L.fwd_end > kStaticWorkspaceBytes) return DTS_ERR_WORKSPACE;
+    if ((st = ensure_prepared())) return st;
+    void* ws = nullptr;
+    if ((st = static_workspace(&ws))) return st;
+    return solve_forward(guide, target, target_dtype, conf, z_init, params, z_out, ws, L, pl, (cudaStream_t)stream);
+}
+
 extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, int target_dtype, const float* conf,
                                   const float* z_init, const dts_params* params, void* ws, size_t ws_bytes,
                                   const float* grad_z, float* grad_target, float* grad_conf, float* grad_guide,

@@ -69,7 +69,7 @@ class Params:
 _lib = None
 EXPORTS = ("dts_status_string", "dts_version", "dts_workspace_size", "dts_domain_transform", "dts_filter",
            "dts_solve", "dts_solve_backward", "dts_last_status", "dts_profile", "dts_profile_read",
-           "dts_kernel_name")
+           "dts_kernel_name", "dts_solve_noalloc", "dts_noalloc_max_workspace")
 
 
 def library_path() -> str:
@@ -99,12 +99,14 @@ def load(build_if_missing: bool = True):
     lib.dts_solve.argtypes = [P(CGuide), vp, i, vp, vp, P(CParams), vp, vp, sz, vp]
     lib.dts_solve_backward.argtypes = [P(CGuide), vp, i, vp, vp, P(CParams), vp, sz, vp, vp, vp, vp, vp, vp]
     lib.dts_last_status.argtypes = [vp]
+    lib.dts_solve_noalloc.argtypes = [P(CGuide), vp, i, vp, vp, P(CParams), vp, vp]
+    lib.dts_noalloc_max_workspace.restype = sz
     lib.dts_profile.argtypes = [i]
     lib.dts_profile_read.argtypes = [i, P(ctypes.c_int), P(ctypes.c_longlong), P(ctypes.c_int), P(ctypes.c_float)]
     lib.dts_kernel_name.argtypes = [i]
     lib.dts_kernel_name.restype = ctypes.c_char_p
     for name in ("dts_domain_transform", "dts_filter", "dts_solve", "dts_solve_backward", "dts_last_status",
-                 "dts_profile", "dts_profile_read"):
+                 "dts_profile", "dts_profile_read", "dts_solve_noalloc"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -205,6 +207,24 @@ def dts_solve(guide: torch.Tensor, target: torch.Tensor, conf: torch.Tensor, par
     _check(load().dts_solve(ctypes.byref(g), target.data_ptr(), _TORCH_DTYPE[target.dtype], conf.data_ptr(),
                             _ptr(z_init), ctypes.byref(p), out.data_ptr(), ws.data_ptr(), ws.numel(),
                             _stream(stream)), "dts_solve")
+    return out
+
+
+def dts_solve_noalloc(guide: torch.Tensor, target: torch.Tensor, conf: torch.Tensor, params: Params,
+                      z_init: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+                      stream=None) -> torch.Tensor:
+    """dts_solve on the library's own scratch array, for callers that cannot allocate device
+    memory for a workspace (sizes up to dts_noalloc_max_workspace() bytes of workspace; calls
+    that overlap on the GPU race on the shared array)."""
+    _need_cuda(guide, target, conf, z_init)
+    _dense(target, "target", tuple(_TORCH_DTYPE))
+    _dense(conf, "conf")
+    g = guide_desc(guide)
+    out = torch.empty(target.shape, dtype=torch.float32, device=target.device) if out is None else out
+    p = params.c()
+    _check(load().dts_solve_noalloc(ctypes.byref(g), target.data_ptr(), _TORCH_DTYPE[target.dtype],
+                                    conf.data_ptr(), _ptr(z_init), ctypes.byref(p), out.data_ptr(),
+                                    _stream(stream)), "dts_solve_noalloc")
     return out
 
 
