@@ -25,7 +25,7 @@ int ensure_prepared() {
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DTS_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_prep_mutex);
     if (!g_prepared[dev]) {
-        if (prepare_kernels() != cudaSuccess) return DTS_ERR_CUDA;
+        if (prepare_kernels() != cudaSuccess || prepare_backward_kernels() != cudaSuccess) return DTS_ERR_CUDA;
         g_prepared[dev] = true;
     }
     return DTS_OK;
@@ -416,10 +416,118 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
                                   const float* z_init, const dts_params* params, void* ws, size_t ws_bytes,
                                   const float* grad_z, float* grad_target, float* grad_conf, float* grad_guide,
                                   float* grad_z_init, dts_stream stream) {
-    (void)guide; (void)target; (void)target_dtype; (void)conf; (void)z_init; (void)params; (void)ws;
-    (void)ws_bytes; (void)grad_z; (void)grad_target; (void)grad_conf; (void)grad_guide; (void)grad_z_init;
-    (void)stream;
-    return DTS_ERR_UNSUPPORTED;
+    int st = check_guide(guide);
+    if (!st) st = check_params(params);
+    if (st) return st;
+    if (!target || !conf || !grad_z || !valid_dtype(target_dtype)) return DTS_ERR_INVALID_ARG;
+    if (params->conf_mode != DTS_CONF_PLAIN) return DTS_ERR_UNSUPPORTED;
+    Plans pl;
+    if ((st = make_plans(guide->H, guide->W, &pl))) return st;
+    RowPlan rb;
+    ColPlan cb;
+    if (!plan_rows_bwd(guide->W, &rb) || !plan_cols_bwd(guide->H, &cb)) return DTS_ERR_UNSUPPORTED;
+    const Layout L = make_layout(guide->H, guide->W, params, 1);
+    if (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.total) return DTS_ERR_WORKSPACE;
+    if ((st = ensure_prepared())) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int H = guide->H, W = guide->W, K = params->iterations, N = params->passes;
+    const long long P = L.pitch;
+    const int dh = params->dist_dtype == DTS_F16;
+    auto plane = [&](size_t off) { return reinterpret_cast<float*>(ws_at(ws, off)); };
+    float* gz = plane(L.gz);
+    float* dXb = plane(L.dXb);
+    float* dYb = plane(L.dYb);
+    const size_t dense = (size_t)H * W * sizeof(float);
+    if (grad_target && cudaMemsetAsync(grad_target, 0, dense, s) != cudaSuccess) return DTS_ERR_CUDA;
+    if (grad_conf && cudaMemsetAsync(grad_conf, 0, dense, s) != cudaSuccess) return DTS_ERR_CUDA;
+    if (cudaMemsetAsync(dXb, 0, L.plane_f32, s) != cudaSuccess) return DTS_ERR_CUDA;
+    if (cudaMemsetAsync(dYb, 0, L.plane_f32, s) != cudaSuccess) return DTS_ERR_CUDA;
+    if ((st = cuda_status(launch_axpy_plane(grad_z, W, gz, P, H, W, 0, s)))) return st;
+    float k2[kMaxPasses];
+    pass_log2a(params->sigma_s, N, k2);
+    float* U[2 * kMaxPasses];
+    for (int p = 1; p < 2 * N; ++p) U[p] = plane(L.xin + (size_t)p * L.plane_f32);
+    float* gbuf[2] = {plane(L.g0), plane(L.g1)};
+    for (int k = K - 1; k >= 0; --k) {
+        U[0] = plane(L.z + (size_t)k * L.plane_f32);
+        // recompute the inputs of passes 1 .. 2N-1 from the checkpoint z_k
+        for (int p = 0; p + 1 < 2 * N; ++p) {
+            PassArgs a = base_pass(guide, L);
+            a.src = U[p];
+            a.dst = U[p + 1];
+            a.k2 = k2[p / 2];
+            if (p % 2 == 0) {
+                a.d = ws_at(ws, L.dX);
+                if ((st = cuda_status(launch_row_pass(a, dh, PASS_PLAIN, pl.rows, s)))) return st;
+            } else {
+                a.d = ws_at(ws, L.dY);
+                if ((st = cuda_status(launch_col_pass(a, dh, PASS_PLAIN, pl.cols, s)))) return st;
+            }
+        }
+        // adjoint passes in reverse order
+        int cur = 0;
+        for (int p = 2 * N - 1; p >= 0; --p) {
+            BwdArgs b = {};
+            b.x = U[p];
+            b.H = H;
+            b.W = W;
+            b.pitch = P;
+            b.k2 = k2[p / 2];
+            b.lna = (float)((double)k2[p / 2] * log(2.0));
+            b.gin = gbuf[cur];
+            b.gout = gbuf[cur ^ 1];
+            b.gz = gz;
+            if (p % 2 == 1) {
+                b.d = ws_at(ws, L.dY);
+                b.dbar = dYb;
+                const bool upd = p == 2 * N - 1;
+                if (upd) {
+                    b.t = target;
+                    b.t_dtype = target_dtype;
+                    b.c = conf;
+                    b.zk = U[0];
+                    b.gt = grad_target;
+                    b.gc = grad_conf;
+                    b.lambda = params->lambda;
+                    b.step = params->step;
+                    b.update = params->update;
+                }
+                if ((st = cuda_status(launch_col_bwd(b, dh, upd, cb, s)))) return st;
+            } else {
+                b.d = ws_at(ws, L.dX);
+                b.dbar = dXb;
+                if ((st = cuda_status(launch_row_bwd(b, dh, p == 0, rb, s)))) return st;
+            }
+            cur ^= 1;
+        }
+    }
+    // z_0: the target itself (z_init NULL) or the caller's z_init
+    if (!z_init) {
+        if (grad_target && (st = cuda_status(launch_axpy_plane(gz, P, grad_target, W, H, W, 1, s)))) return st;
+    } else if (grad_z_init) {
+        if ((st = cuda_status(launch_axpy_plane(gz, P, grad_z_init, W, H, W, 0, s)))) return st;
+    }
+    if (grad_guide) {
+        GuideGradArgs gg = {};
+        gg.guide = guide->data;
+        gg.row_stride = guide->row_stride ? guide->row_stride : W;
+        gg.ch_stride = guide->ch_stride ? guide->ch_stride : (long long)H * gg.row_stride;
+        gg.C = guide->C;
+        gg.H = H;
+        gg.W = W;
+        gg.gdtype = guide->dtype;
+        gg.norm = params->norm;
+        gg.dhalf = dh;
+        gg.k = params->sigma_s / params->sigma_r;
+        gg.dX = ws_at(ws, L.dX);
+        gg.dY = ws_at(ws, L.dY);
+        gg.dXb = dXb;
+        gg.dYb = dYb;
+        gg.pitch = P;
+        gg.out = grad_guide;
+        if ((st = cuda_status(launch_guide_grad(gg, s)))) return st;
+    }
+    return DTS_OK;
 }
 
 extern "C" int dts_last_status(dts_stream stream) {

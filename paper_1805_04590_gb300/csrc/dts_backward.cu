@@ -1,0 +1,456 @@
+// Reverse mode of the solver for sm_103a (the paper has no backward; these kernels follow from
+// the forward recurrences by the chain rule).
+//
+// One horizontal or vertical pass computes, along every line, J = causal(x) and K = anticausal(J)
+//     J[n] = (1 - w_n) x[n] + w_n J[n-1],   K[n] = (1 - w_{n+1}) J[n] + w_{n+1} K[n+1].
+// Given G = dL/dK, its adjoint is a left-to-right then right-to-left pair as well:
+//     h[n]  = G[n] + w_n h[n-1]                          (total gradient of K[n])
+//     gJ[n] = (1 - w_{n+1}) h[n] + w_{n+1} gJ[n+1]       (total gradient of J[n])
+//     dL/dx[n] = (1 - w_n) gJ[n]
+//     dL/dw_n  = gJ[n] (J[n-1] - x[n]) + h[n-1] (K[n] - J[n-1]),   dL/dd_n = ln(a) w_n dL/dw_n.
+// The pair (h, gJ) has the same coupled structure as (J, K) (unnormalised on the way out), so a
+// pass adjoint exchanges TWO coupled five-tuples in one round: one to recompute J and K from the
+// saved pass input, one for the carries of h and gJ.  The last vertical pass of an iteration also
+// takes the adjoint of the data-term update (Eq. 3 or Eq. 4); the first horizontal pass adds the
+// filter's adjoint into the gradient of the iterate.
+#include "dts_scan.cuh"
+
+namespace dts {
+
+namespace {
+
+using namespace scan;
+
+struct Pre2 {
+    Aff jk, hg;
+};
+struct Suf2 {
+    Coupled jk, hg;
+};
+
+struct BackwardMode {
+    using Pre = Pre2;
+    using Suf = Suf2;
+    static __device__ __forceinline__ Pre pre_identity() { return Pre{aff_identity(), aff_identity()}; }
+    static __device__ __forceinline__ Pre pre_compose(const Pre& f, const Pre& s) {
+        return Pre{aff_compose(f.jk, s.jk), aff_compose(f.hg, s.hg)};
+    }
+    static __device__ __forceinline__ Suf suf_identity() { return Suf{coupled_identity(), coupled_identity()}; }
+    static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) {
+        return Suf{coupled_compose(f.jk, s.jk), coupled_compose(f.hg, s.hg)};
+    }
+};
+
+// Replays one segment given its carries; on return x holds dL/dx and db holds ln(a) w dL/dw.
+// jin: J entering from the left, kin: K entering from the right, hin: h entering from the left,
+// gin: gJ entering from the right.  On return K holds the recomputed pass output.
+template <int N>
+__device__ __forceinline__ void segment_adjoint(float (&x)[N], const float (&w)[N], float wn, const float (&G)[N],
+                                                float (&K)[N], float (&db)[N], float jin, float kin, float hin,
+                                                float gin, float lna) {
+    float J[N];
+    float v = jin;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        v = fmaf(w[j], v - x[j], x[j]);
+        J[j] = v;
+    }
+    v = kin;
+#pragma unroll
+    for (int j = N - 1; j >= 0; --j) {
+        const float wp = (j + 1 < N) ? w[j + 1] : wn;
+        v = fmaf(wp, v - J[j], J[j]);
+        K[j] = v;
+    }
+    float h[N];
+    float hp = hin;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const float Jp = j ? J[j - 1] : jin;
+        db[j] = hp * (K[j] - Jp);
+        hp = fmaf(w[j], hp, G[j]);
+        h[j] = hp;
+    }
+    float g = gin;
+#pragma unroll
+    for (int j = N - 1; j >= 0; --j) {
+        const float wp = (j + 1 < N) ? w[j + 1] : wn;
+        g = fmaf(wp, g - h[j], h[j]);  // (1 - w') h + w' g
+        const float Jp = j ? J[j - 1] : jin;
+        db[j] = lna * w[j] * fmaf(g, Jp - x[j], db[j]);
+        x[j] = fmaf(-w[j], g, g);  // (1 - w) g
+    }
+}
+
+// ---------------------------------------------------------------- horizontal pass adjoint
+// Same thread layout as the forward horizontal pass.  FINAL: the first pass of the filter; its
+// input gradient is added into a.gz instead of written to a.gout.
+template <int ITEMS, bool DHALF, bool FINAL>
+__global__ void __launch_bounds__(1024) row_bwd_kernel(BwdArgs a, int tpr) {
+    static_assert(ITEMS % 4 == 0, "ITEMS must be a multiple of 4");
+    using M = BackwardMode;
+    __shared__ M::Pre s_pre[32];
+    __shared__ M::Suf s_suf[32];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int rloc = tid / tpr;
+    const int t = tid - rloc * tpr;
+    const int wpr = tpr >> 5;
+    const int wrow = t >> 5;
+    const int wbase = warp - wrow;
+    const int rpb = blockDim.x / tpr;
+    const int row = blockIdx.x * rpb + rloc;
+    const bool row_ok = row < a.H;
+    const int e0 = t * ITEMS;
+    const long long P = a.pitch;
+    const long long base = (long long)row * P + e0;
+    const bool live = row_ok && e0 < P;
+
+    wait_predecessor();
+    float x[ITEMS], w[ITEMS], G[ITEMS];
+    if (live) {
+#pragma unroll
+        for (int q = 0; q < ITEMS / 4; ++q) {
+            load4_f(a.x, base + 4 * q, &x[4 * q]);
+            load4_f(a.gin, base + 4 * q, &G[4 * q]);
+            load4_d<DHALF>(a.d, base + 4 * q, &w[4 * q]);
+        }
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) w[j] = ex2(a.k2 * w[j]);
+        if (e0 + ITEMS > a.W) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j)
+                if (e0 + j >= a.W) x[j] = w[j] = G[j] = 0.f;
+        }
+        if (e0 == 0) w[0] = 0.f;
+    } else {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) x[j] = w[j] = G[j] = 0.f;
+    }
+    float wn = __shfl_down_sync(kFull, w[0], 1);
+    if (lane == 31) {
+        const int en = e0 + ITEMS;
+        wn = (row_ok && en < a.W) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)row * P + en)) : 0.f;
+    }
+
+    M::Pre own_pre, pre;
+    M::Suf own_suf, suf;
+    own_suf.jk = coupled_local<true>(x, w, wn);
+    own_suf.hg = coupled_local<false>(G, w, wn);
+    own_pre = M::Pre{Aff{own_suf.jk.A, own_suf.jk.B}, Aff{own_suf.hg.A, own_suf.hg.B}};
+    row_exchange<M>(own_pre, own_suf, lane, warp, wrow, wbase, wpr, s_pre, s_suf, pre, suf);
+    release_successor();
+    const float jin = pre.jk.B;
+    const float kin = k_entering(suf.jk, fmaf(own_pre.jk.A, jin, own_pre.jk.B));
+    const float hin = pre.hg.B;
+    const float gin = k_entering(suf.hg, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
+    float K[ITEMS], db[ITEMS];
+    segment_adjoint(x, w, wn, G, K, db, jin, kin, hin, gin, a.lna);
+
+    if (live) {
+#pragma unroll
+        for (int q = 0; q < ITEMS / 4; ++q) {
+            float acc[4];
+            load4_f(a.dbar, base + 4 * q, acc);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] += (e0 + 4 * q + i < a.W) ? db[4 * q + i] : 0.f;
+            store4_f(a.dbar, base + 4 * q, acc);
+            if constexpr (FINAL) {
+                float gz[4];
+                load4_f(a.gz, base + 4 * q, gz);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) gz[i] += x[4 * q + i];
+                store4_f(a.gz, base + 4 * q, gz);
+            } else {
+                store4_f(a.gout, base + 4 * q, &x[4 * q]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- vertical pass adjoint
+// Same layout as the forward vertical pass.  UPDATE: the last pass of an iteration; its output
+// gradient is the adjoint of the data-term update, computed from a.gz = dL/dz_{k+1}:
+//   GD      z' = z - eta (lambda (z - zbar) + c (z - t)):
+//           dzbar = eta lambda g,  dt += eta c g,  dc += eta (t - z) g,  dz (direct) = (1 - eta lambda - eta c) g
+//   Jacobi  z' = (lambda zbar + c t) / (lambda + c):
+//           dzbar = lambda g / den,  dt += c g / den,  dc += lambda (t - zbar) g / den^2,  dz (direct) = 0
+// and a.gz is overwritten with the direct part (the filter's adjoint is added later).
+template <int ITEMS>
+constexpr int bwd_col_max_threads() {
+    return ITEMS <= 8 ? 512 : 256;
+}
+
+template <int ITEMS, bool DHALF, bool UPDATE>
+__global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>()) col_bwd_kernel(BwdArgs a) {
+    using M = BackwardMode;
+    __shared__ ColShared<M, 16> sh;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int NW = blockDim.x >> 5;
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int col = blockIdx.x * 32 + lane;
+    const bool col_ok = col < a.W;
+    const int row0 = (rank * NW + warp) * ITEMS;
+    const long long P = a.pitch;
+
+    wait_predecessor();
+    float x[ITEMS], w[ITEMS], G[ITEMS], g1[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int r = row0 + j;
+        const bool ok = col_ok && r < a.H;
+        const long long idx = (long long)r * P + col;
+        x[j] = ok ? a.x[idx] : 0.f;
+        w[j] = ok ? load1_d<DHALF>(a.d, idx) : 0.f;
+        if constexpr (UPDATE) {
+            g1[j] = ok ? a.gz[idx] : 0.f;
+            float gb = 0.f;
+            if (ok) {
+                const float cf = a.c[(long long)r * a.W + col];
+                if (a.update == DTS_UPDATE_JACOBI) {
+                    const float den = a.lambda + cf;
+                    gb = den != 0.f ? a.lambda / den * g1[j] : 0.f;
+                } else {
+                    gb = a.step * a.lambda * g1[j];
+                }
+            }
+            G[j] = gb;
+        } else {
+            G[j] = ok ? a.gin[idx] : 0.f;
+        }
+    }
+    float wn;
+    {
+        const int rn = row0 + ITEMS;
+        wn = (col_ok && rn < a.H) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)rn * P + col)) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int r = row0 + j;
+        w[j] = (col_ok && r > 0 && r < a.H) ? ex2(a.k2 * w[j]) : 0.f;
+    }
+
+    M::Pre own_pre, pre;
+    M::Suf own_suf, suf;
+    own_suf.jk = coupled_local<true>(x, w, wn);
+    own_suf.hg = coupled_local<false>(G, w, wn);
+    own_pre = M::Pre{Aff{own_suf.jk.A, own_suf.jk.B}, Aff{own_suf.hg.A, own_suf.hg.B}};
+    col_exchange<M, 16>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
+    release_successor();
+    const float jin = pre.jk.B;
+    const float kin = k_entering(suf.jk, fmaf(own_pre.jk.A, jin, own_pre.jk.B));
+    const float hin = pre.hg.B;
+    const float gin = k_entering(suf.hg, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
+    float K[ITEMS], db[ITEMS];
+    segment_adjoint(x, w, wn, G, K, db, jin, kin, hin, gin, a.lna);
+
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int r = row0 + j;
+        if (!(col_ok && r < a.H)) continue;
+        const long long idx = (long long)r * P + col;
+        a.dbar[idx] += db[j];
+        a.gout[idx] = x[j];
+        if constexpr (UPDATE) {
+            const long long di = (long long)r * a.W + col;
+            const float g = g1[j];
+            const float cf = a.c[di];
+            const float t = load_any(a.t, di, a.t_dtype);
+            float dt, dc, dz;
+            if (a.update == DTS_UPDATE_JACOBI) {
+                const float den = a.lambda + cf;
+                if (den != 0.f) {
+                    dt = cf / den * g;
+                    dc = a.lambda * (t - K[j]) / (den * den) * g;
+                    dz = 0.f;
+                } else {
+                    dt = dc = 0.f;
+                    dz = g;
+                }
+            } else {
+                dt = a.step * cf * g;
+                dc = a.step * (t - a.zk[idx]) * g;
+                dz = (1.f - a.step * a.lambda - a.step * cf) * g;
+            }
+            if (a.gt) a.gt[di] += dt;
+            if (a.gc) a.gc[di] += dc;
+            a.gz[idx] = dz;
+        }
+    }
+    cluster_exit();
+}
+
+// ---------------------------------------------------------------- guide gradient
+// dL/dI_c[y][x] gathers the four distances that involve pixel (y, x):
+//   L1 d = 1 + k sum |D|:          dd/dD = k sign(D)
+//   L2 d = sqrt(1 + k^2 sum D^2):  dd/dD = k^2 D / d
+// with D = I(p) - I(q) for the neighbour q on the left / above.
+template <typename GT, bool DHALF>
+__global__ void __launch_bounds__(256) guide_grad_kernel(GuideGradArgs a) {
+    wait_predecessor();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= a.W || y >= a.H) return;
+    const GT* I = static_cast<const GT*>(a.guide);
+    const long long P = a.pitch;
+    const long long q = (long long)y * P + x;
+    const bool l2 = a.norm == DTS_NORM_L2;
+    auto slope = [&](float D, long long qi, bool vertical) -> float {
+        if (l2) return a.k * a.k * D / load1_d<DHALF>(vertical ? a.dY : a.dX, qi);
+        return a.k * (float)((D > 0.f) - (D < 0.f));
+    };
+    const float gl = x > 0 ? a.dXb[q] : 0.f;
+    const float gr = x + 1 < a.W ? a.dXb[q + 1] : 0.f;
+    const float gu = y > 0 ? a.dYb[q] : 0.f;
+    const float gd = y + 1 < a.H ? a.dYb[q + P] : 0.f;
+    for (int c = 0; c < a.C; ++c) {
+        const GT* Ic = I + (long long)c * a.ch_stride + (long long)y * a.row_stride + x;
+        const float v = to_f32<GT>(Ic[0]);
+        float g = 0.f;
+        if (x > 0) g += gl * slope(v - to_f32<GT>(Ic[-1]), q, false);
+        if (x + 1 < a.W) g -= gr * slope(to_f32<GT>(Ic[1]) - v, q + 1, false);
+        if (y > 0) g += gu * slope(v - to_f32<GT>(Ic[-a.row_stride]), q, true);
+        if (y + 1 < a.H) g -= gd * slope(to_f32<GT>(Ic[a.row_stride]) - v, q + P, true);
+        a.out[((long long)c * a.H + y) * a.W + x] = g;
+    }
+}
+
+// dst[y][x] (pitch dp) += src[y][x] (pitch sp), or = when accumulate is 0
+__global__ void __launch_bounds__(256) axpy_plane_kernel(const float* src, long long sp, float* dst, long long dp,
+                                                         int H, int W, int accumulate) {
+    wait_predecessor();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const float v = src[(long long)y * sp + x];
+    float* d = dst + (long long)y * dp + x;
+    *d = accumulate ? *d + v : v;
+}
+
+template <int ITEMS, bool DHALF>
+cudaError_t launch_row_bwd_t(const BwdArgs& a, bool final_pass, const RowPlan& p, cudaStream_t s) {
+    const dim3 grid((unsigned)((a.H + p.rpb - 1) / p.rpb));
+    const dim3 block((unsigned)(p.tpr * p.rpb));
+    if (final_pass) return launch_ex(row_bwd_kernel<ITEMS, DHALF, true>, grid, block, 0, s, a, p.tpr);
+    return launch_ex(row_bwd_kernel<ITEMS, DHALF, false>, grid, block, 0, s, a, p.tpr);
+}
+
+template <int ITEMS, bool DHALF>
+cudaError_t launch_col_bwd_t(const BwdArgs& a, bool update, const ColPlan& p, cudaStream_t s) {
+    const dim3 grid((unsigned)((a.W + 31) / 32), (unsigned)p.cluster, 1);
+    const dim3 block((unsigned)(32 * p.warps));
+    if (update) return launch_ex(col_bwd_kernel<ITEMS, DHALF, true>, grid, block, p.cluster, s, a);
+    return launch_ex(col_bwd_kernel<ITEMS, DHALF, false>, grid, block, p.cluster, s, a);
+}
+
+template <int ITEMS, bool DHALF>
+cudaError_t allow_bwd_clusters() {
+    cudaError_t e = cudaSuccess;
+    const void* fs[2] = {(const void*)col_bwd_kernel<ITEMS, DHALF, true>,
+                         (const void*)col_bwd_kernel<ITEMS, DHALF, false>};
+    for (const void* f : fs) {
+        const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (r != cudaSuccess) e = r;
+    }
+    return e;
+}
+
+}  // namespace
+
+// Backward plans: 8 positions per thread (five arrays of them live at once).
+bool plan_rows_bwd(int W, RowPlan* p) {
+    const int items = 8;
+    int tpr = (W + items - 1) / items;
+    if (tpr > 1024) return false;
+    tpr = (tpr + 31) / 32 * 32;
+    int rpb = 256 / tpr;
+    if (rpb < 1) rpb = 1;
+    p->items = items;
+    p->tpr = tpr;
+    p->rpb = rpb;
+    return true;
+}
+
+// Backward vertical plan (CTA at most bwd_col_max_threads): columns up to 2048 rows.
+bool plan_cols_bwd(int H, ColPlan* p) {
+    static const int cand[][2] = {{8, 8}, {8, 16}, {16, 8}};
+    if (H <= 128) {
+        p->items = 8;
+        p->warps = (H + 7) / 8;
+        p->cluster = 1;
+        return true;
+    }
+    for (int limit : {8, 16}) {
+        for (const auto& c : cand) {
+            const int rows = c[0] * c[1];
+            const int cs = (H + rows - 1) / rows;
+            if (cs <= limit) {
+                p->items = c[0];
+                p->warps = c[1];
+                p->cluster = cs;
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+cudaError_t launch_row_bwd(const BwdArgs& a, int dist_half, bool final_pass, const RowPlan& p, cudaStream_t s) {
+    const int h = prof_begin(final_pass ? KID_ROW_BWD_FINAL : KID_ROW_BWD, (long long)a.H * a.W,
+                             dist_half ? kFlagDistHalf : 0, s);
+    cudaError_t e = cudaErrorInvalidValue;
+    if (p.items == 8) e = dist_half ? launch_row_bwd_t<8, true>(a, final_pass, p, s) : launch_row_bwd_t<8, false>(a, final_pass, p, s);
+    prof_end(h, s);
+    return e;
+}
+
+cudaError_t launch_col_bwd(const BwdArgs& a, int dist_half, bool update, const ColPlan& p, cudaStream_t s) {
+    const int h = prof_begin(update ? KID_COL_BWD_UPDATE : KID_COL_BWD, (long long)a.H * a.W,
+                             (dist_half ? kFlagDistHalf : 0) | (update && a.t_dtype != DTS_F32 ? kFlagTarget16 : 0), s);
+    cudaError_t e = cudaErrorInvalidValue;
+    if (p.items == 8) e = dist_half ? launch_col_bwd_t<8, true>(a, update, p, s) : launch_col_bwd_t<8, false>(a, update, p, s);
+    if (p.items == 16) e = dist_half ? launch_col_bwd_t<16, true>(a, update, p, s) : launch_col_bwd_t<16, false>(a, update, p, s);
+    prof_end(h, s);
+    return e;
+}
+
+cudaError_t launch_guide_grad(const GuideGradArgs& a, cudaStream_t s) {
+    const int h = prof_begin(KID_GUIDE_GRAD, (long long)a.H * a.W, a.dhalf ? kFlagDistHalf : 0, s);
+    const dim3 block(256);
+    const dim3 grid((unsigned)((a.W + 255) / 256), (unsigned)a.H);
+    cudaError_t e;
+    if (a.dhalf) {
+        if (a.gdtype == DTS_BF16) e = launch_ex(guide_grad_kernel<__nv_bfloat16, true>, grid, block, 0, s, a);
+        else if (a.gdtype == DTS_F16) e = launch_ex(guide_grad_kernel<__half, true>, grid, block, 0, s, a);
+        else e = launch_ex(guide_grad_kernel<float, true>, grid, block, 0, s, a);
+    } else {
+        if (a.gdtype == DTS_BF16) e = launch_ex(guide_grad_kernel<__nv_bfloat16, false>, grid, block, 0, s, a);
+        else if (a.gdtype == DTS_F16) e = launch_ex(guide_grad_kernel<__half, false>, grid, block, 0, s, a);
+        else e = launch_ex(guide_grad_kernel<float, false>, grid, block, 0, s, a);
+    }
+    prof_end(h, s);
+    return e;
+}
+
+cudaError_t launch_axpy_plane(const float* src, long long sp, float* dst, long long dp, int H, int W, int accumulate,
+                              cudaStream_t s) {
+    const int h = prof_begin(KID_AXPY, (long long)H * W, 0, s);
+    const dim3 block(256);
+    const dim3 grid((unsigned)((W + 255) / 256), (unsigned)H);
+    const cudaError_t e = launch_ex(axpy_plane_kernel, grid, block, 0, s, src, sp, dst, dp, H, W, accumulate);
+    prof_end(h, s);
+    return e;
+}
+
+cudaError_t prepare_backward_kernels() {
+    cudaError_t e = cudaSuccess, r;
+    if ((r = allow_bwd_clusters<8, false>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_clusters<8, true>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_clusters<16, false>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_clusters<16, true>()) != cudaSuccess) e = r;
+    return e;
+}
+
+}  // namespace dts

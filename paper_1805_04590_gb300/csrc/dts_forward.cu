@@ -23,120 +23,43 @@
 // a cluster for columns -- gives every segment its exact carries in both directions, after
 // which it replays its positions once each way.  A line is read once and written once per
 // pass: 2 s_z + s_d bytes per pixel.
-#include <cooperative_groups.h>
-
 #include <stdio.h>
 #include <stdlib.h>
 
-#include <type_traits>
-#include <utility>
-
-#include "dts_internal.cuh"
-
-namespace cg = cooperative_groups;
+#include "dts_scan.cuh"
 
 namespace dts {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+using namespace scan;
 
-// 2^x with the SFU instruction (PTX ex2.approx.ftz.f32; relative error ~2^-22, results below
-// the normal range flush to zero, which is harmless for a feedback weight).
-__device__ __forceinline__ float ex2(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
-// Programmatic dependent launch: a kernel launched with the programmatic-serialization
-// attribute may start while its predecessor drains; it must wait for the predecessor's
-// completion (and memory) before touching global data, and it lets its own successor start
-// launching once it no longer needs the SM slots it would free.  Both are no-ops otherwise.
-__device__ __forceinline__ void wait_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void release_successor() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// v -> A v + B, the causal carry map of a group of positions
-struct Aff {
-    float A, B;
-};
-
-__device__ __forceinline__ Aff aff_identity() { return Aff{1.f, 0.f}; }
-
-// first `f`, then `s`
-__device__ __forceinline__ Aff aff_compose(const Aff& f, const Aff& s) {
-    return Aff{f.A * s.A, fmaf(s.A, f.B, s.B)};
-}
-
-template <typename T>
-__device__ __forceinline__ T shfl_up_t(const T& v, int off) {
-    constexpr int n = sizeof(T) / 4;
-    T r;
-    const float* s = reinterpret_cast<const float*>(&v);
-    float* d = reinterpret_cast<float*>(&r);
-#pragma unroll
-    for (int i = 0; i < n; ++i) d[i] = __shfl_up_sync(kFull, s[i], off);
-    return r;
-}
-
-template <typename T>
-__device__ __forceinline__ T shfl_down_t(const T& v, int off) {
-    constexpr int n = sizeof(T) / 4;
-    T r;
-    const float* s = reinterpret_cast<const float*>(&v);
-    float* d = reinterpret_cast<float*>(&r);
-#pragma unroll
-    for (int i = 0; i < n; ++i) d[i] = __shfl_down_sync(kFull, s[i], off);
-    return r;
-}
-
-// ---------------------------------------------------------------- segment algebra
+// ---------------------------------------------------------------- modes
 // Normalised pass: causal sweep, then the anti-causal sweep on its result.
 struct CoupledMode {
-    struct Suf {
-        float A, B, al, be, ga;
-    };
-    static __device__ __forceinline__ Suf suf_identity() { return Suf{1.f, 0.f, 1.f, 0.f, 0.f}; }
-    // group `f` followed by group `s` (s to the right of f)
-    static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) {
-        Suf o;
-        o.A = f.A * s.A;
-        o.B = fmaf(s.A, f.B, s.B);
-        o.al = f.al * s.al;
-        o.be = fmaf(f.al * s.be, f.A, f.be);
-        o.ga = fmaf(f.al, fmaf(s.be, f.B, s.ga), f.ga);
-        return o;
-    }
+    using Pre = Aff;
+    using Suf = Coupled;
+    static __device__ __forceinline__ Pre pre_identity() { return aff_identity(); }
+    static __device__ __forceinline__ Pre pre_compose(const Pre& f, const Pre& s) { return aff_compose(f, s); }
+    static __device__ __forceinline__ Suf suf_identity() { return coupled_identity(); }
+    static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) { return coupled_compose(f, s); }
     template <int N>
-    static __device__ __forceinline__ void local(const float (&x)[N], const float (&w)[N], float wn, Aff& pre,
+    static __device__ __forceinline__ void local(const float (&x)[N], const float (&w)[N], float wn, Pre& pre,
                                                  Suf& suf) {
-        float P = 1.f, Q = 0.f, r = 1.f, be = 0.f, ga = 0.f;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            P *= w[j];
-            Q = fmaf(w[j], Q - x[j], x[j]);
-            const float wp = (j + 1 < N) ? w[j + 1] : wn;
-            const float coef = fmaf(-r, wp, r);
-            be = fmaf(coef, P, be);
-            ga = fmaf(coef, Q, ga);
-            r *= wp;
-        }
-        pre = Aff{P, Q};
-        suf = Suf{P, Q, r, be, ga};
+        suf = coupled_local<true>(x, w, wn);
+        pre = Aff{suf.A, suf.B};
     }
-    // c: causal value entering on the left; c_out: leaving on the right; after: all groups to the right
+    // c: causal value entering on the left; after: composition of every segment to the right
     template <int N>
-    static __device__ __forceinline__ void apply(float (&x)[N], const float (&w)[N], float wn, float c, float c_out,
-                                                 const Suf& after) {
+    static __device__ __forceinline__ void apply(float (&x)[N], const float (&w)[N], float wn, const Pre& own,
+                                                 float c, const Suf& after) {
         float J = c;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             J = fmaf(w[j], J - x[j], x[j]);
             x[j] = J;
         }
-        float K = fmaf(after.be, c_out, after.ga);
+        float K = k_entering(after, fmaf(own.A, c, own.B));
 #pragma unroll
         for (int j = N - 1; j >= 0; --j) {
             const float wp = (j + 1 < N) ? w[j + 1] : wn;
@@ -147,17 +70,22 @@ struct CoupledMode {
 };
 
 // Support of the unnormalised kernel (confidence weighting): causal P[n] = x[n] + w_n P[n-1] and
-// anti-causal Q[n] = x[n] + w'_n Q[n+1], both on x; the result is P + Q - x.
+// anti-causal Q[n] = x[n] + w'_n Q[n+1], both on x; the result is P + Q - x.  The two sweeps are
+// independent: Suf carries (al, de) with Q_start = al Q_in + de.
+struct SupSuf {
+    float al, de;
+};
 struct SupportMode {
-    struct Suf {
-        float al, de;
-    };
+    using Pre = Aff;
+    using Suf = SupSuf;
+    static __device__ __forceinline__ Pre pre_identity() { return aff_identity(); }
+    static __device__ __forceinline__ Pre pre_compose(const Pre& f, const Pre& s) { return aff_compose(f, s); }
     static __device__ __forceinline__ Suf suf_identity() { return Suf{1.f, 0.f}; }
     static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) {
         return Suf{f.al * s.al, fmaf(f.al, s.de, f.de)};
     }
     template <int N>
-    static __device__ __forceinline__ void local(const float (&x)[N], const float (&w)[N], float wn, Aff& pre,
+    static __device__ __forceinline__ void local(const float (&x)[N], const float (&w)[N], float wn, Pre& pre,
                                                  Suf& suf) {
         float A = 1.f, B = 0.f, r = 1.f, de = 0.f;
 #pragma unroll
@@ -171,9 +99,9 @@ struct SupportMode {
         suf = Suf{r, de};
     }
     template <int N>
-    static __device__ __forceinline__ void apply(float (&x)[N], const float (&w)[N], float wn, float c, float c_out,
-                                                 const Suf& after) {
-        (void)c_out;
+    static __device__ __forceinline__ void apply(float (&x)[N], const float (&w)[N], float wn, const Pre& own,
+                                                 float c, const Suf& after) {
+        (void)own;
         float Pv[N];
         float Pc = c;
 #pragma unroll
@@ -190,45 +118,6 @@ struct SupportMode {
         }
     }
 };
-
-__device__ __forceinline__ Aff scan_pre(Aff v, int lane) {
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const Aff o = shfl_up_t(v, off);
-        if (lane >= off) v = aff_compose(o, v);
-    }
-    return v;
-}
-
-template <class M>
-__device__ __forceinline__ typename M::Suf scan_suf(typename M::Suf v, int lane) {
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const typename M::Suf o = shfl_down_t(v, off);
-        if (lane + off < 32) v = M::suf_compose(v, o);
-    }
-    return v;
-}
-
-template <bool DHALF>
-__device__ __forceinline__ void load4_d(const void* base, long long idx, float* out) {
-    if constexpr (DHALF) {
-        uint2 v = *reinterpret_cast<const uint2*>(static_cast<const __half*>(base) + idx);
-        __half2 h0 = *reinterpret_cast<__half2*>(&v.x);
-        __half2 h1 = *reinterpret_cast<__half2*>(&v.y);
-        float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
-        out[0] = f0.x; out[1] = f0.y; out[2] = f1.x; out[3] = f1.y;
-    } else {
-        float4 v = *reinterpret_cast<const float4*>(static_cast<const float*>(base) + idx);
-        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
-    }
-}
-
-template <bool DHALF>
-__device__ __forceinline__ float load1_d(const void* base, long long idx) {
-    if constexpr (DHALF) return __half2float(static_cast<const __half*>(base)[idx]);
-    else return static_cast<const float*>(base)[idx];
-}
 
 // ---------------------------------------------------------------- distances
 // Thread = one column x and kDistRows consecutive rows; a warp covers 32 consecutive columns,
@@ -304,9 +193,8 @@ template <int ITEMS, bool DHALF, int KIND>
 __global__ void __launch_bounds__(1024) row_pass_kernel(PassArgs a, int tpr) {
     static_assert(ITEMS % 4 == 0, "ITEMS must be a multiple of 4");
     using M = typename std::conditional<KIND == PASS_SUPPORT, SupportMode, CoupledMode>::type;
-    using Suf = typename M::Suf;
-    __shared__ Aff s_pre[32];
-    __shared__ Suf s_suf[32];
+    __shared__ typename M::Pre s_pre[32];
+    __shared__ typename M::Suf s_suf[32];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
@@ -331,8 +219,7 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(PassArgs a, int tpr) {
             if constexpr (KIND == PASS_SUPPORT) {
                 x[4 * q] = x[4 * q + 1] = x[4 * q + 2] = x[4 * q + 3] = 1.f;
             } else {
-                const float4 v = *reinterpret_cast<const float4*>(a.src + base + 4 * q);
-                x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
+                load4_f(a.src, base + 4 * q, &x[4 * q]);
             }
             load4_d<DHALF>(a.d, base + 4 * q, &w[4 * q]);
         }
@@ -355,36 +242,16 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(PassArgs a, int tpr) {
         wn = (row_ok && en < a.W) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)row * P + en)) : 0.f;
     }
 
-    Aff own_pre;
-    Suf own_suf;
+    typename M::Pre own_pre, pre;
+    typename M::Suf own_suf, suf;
     M::local(x, w, wn, own_pre, own_suf);
-    const Aff inc_pre = scan_pre(own_pre, lane);
-    const Suf inc_suf = scan_suf<M>(own_suf, lane);
-    Aff pre = shfl_up_t(inc_pre, 1);
-    Suf suf = shfl_down_t(inc_suf, 1);
-    if (lane == 0) pre = aff_identity();
-    if (lane == 31) suf = M::suf_identity();
-    if (wpr > 1) {
-        if (lane == 31) s_pre[warp] = inc_pre;
-        if (lane == 0) s_suf[warp] = inc_suf;
-        __syncthreads();
-        Aff wpre = aff_identity();
-        for (int q = 0; q < wrow; ++q) wpre = aff_compose(wpre, s_pre[wbase + q]);
-        Suf wsuf = M::suf_identity();
-        for (int q = wrow + 1; q < wpr; ++q) wsuf = M::suf_compose(wsuf, s_suf[wbase + q]);
-        pre = aff_compose(wpre, pre);
-        suf = M::suf_compose(suf, wsuf);
-    }
+    row_exchange<M>(own_pre, own_suf, lane, warp, wrow, wbase, wpr, s_pre, s_suf, pre, suf);
     release_successor();
-    const float c = pre.B;
-    const float c_out = fmaf(own_pre.A, c, own_pre.B);
-    M::apply(x, w, wn, c, c_out, suf);
+    M::apply(x, w, wn, own_pre, pre.B, suf);
 
     if (live) {
 #pragma unroll
-        for (int q = 0; q < ITEMS / 4; ++q)
-            *reinterpret_cast<float4*>(a.dst + base + 4 * q) =
-                make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+        for (int q = 0; q < ITEMS / 4; ++q) store4_f(a.dst, base + 4 * q, &x[4 * q]);
     }
 }
 
@@ -410,20 +277,11 @@ constexpr int col_min_blocks() {
 template <int ITEMS, bool DHALF, int KIND>
 __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS, KIND>()) col_pass_kernel(PassArgs a) {
     using M = typename std::conditional<KIND == PASS_SUPPORT_CONF, SupportMode, CoupledMode>::type;
-    using Suf = typename M::Suf;
-    cg::cluster_group cluster = cg::this_cluster();
-    __shared__ Aff s_pre[32][32];
-    __shared__ Suf s_suf[32][32];
-    __shared__ Aff s_cta_pre[32];
-    __shared__ Suf s_cta_suf[32];
-    __shared__ Aff s_cl_pre[32];
-    __shared__ Suf s_cl_suf[32];
-
+    __shared__ ColShared<M, 32> sh;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int NW = blockDim.x >> 5;
-    const int rank = (int)cluster.block_rank();
-    const int CS = (int)cluster.num_blocks();
+    const int rank = (int)cg::this_cluster().block_rank();
     const int col = blockIdx.x * 32 + lane;
     const bool col_ok = col < a.W;
     const int row0 = (rank * NW + warp) * ITEMS;
@@ -480,39 +338,12 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
     }
     if (row0 == 0) w[0] = 0.f;  // the column starts here
 
-    Aff own_pre;
-    Suf own_suf;
+    typename M::Pre own_pre, pre;
+    typename M::Suf own_suf, suf;
     M::local(x, w, wn, own_pre, own_suf);
-    s_pre[warp][lane] = own_pre;
-    s_suf[warp][lane] = own_suf;
-    __syncthreads();
-    Aff wpre = aff_identity();
-    for (int q = 0; q < warp; ++q) wpre = aff_compose(wpre, s_pre[q][lane]);
-    Suf wsuf = M::suf_identity();
-    for (int q = warp + 1; q < NW; ++q) wsuf = M::suf_compose(wsuf, s_suf[q][lane]);
-    if (CS > 1) {
-        // CTA totals: the last warp holds the full prefix, the first warp the full suffix
-        if (warp == NW - 1) s_cta_pre[lane] = aff_compose(wpre, own_pre);
-        if (warp == 0) s_cta_suf[lane] = M::suf_compose(own_suf, wsuf);
-        cluster.sync();
-        if (warp == 0) {
-            Aff cp = aff_identity();
-            for (int q = 0; q < rank; ++q) cp = aff_compose(cp, *cluster.map_shared_rank(&s_cta_pre[lane], q));
-            Suf cs = M::suf_identity();
-            for (int q = rank + 1; q < CS; ++q) cs = M::suf_compose(cs, *cluster.map_shared_rank(&s_cta_suf[lane], q));
-            s_cl_pre[lane] = cp;
-            s_cl_suf[lane] = cs;
-        }
-        __syncthreads();
-        wpre = aff_compose(s_cl_pre[lane], wpre);
-        wsuf = M::suf_compose(wsuf, s_cl_suf[lane]);
-    }
-    // every remote read of this CTA is done: peers may exit once all have arrived
-    cluster.barrier_arrive();
+    col_exchange<M, 32>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
     release_successor();
-    const float c = wpre.B;
-    const float c_out = fmaf(own_pre.A, c, own_pre.B);
-    M::apply(x, w, wn, c, c_out, wsuf);
+    M::apply(x, w, wn, own_pre, pre.B, suf);
 
     // ---- epilogue
 #pragma unroll
@@ -542,35 +373,7 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
             a.zout[idx] = a.c[(long long)r * a.W + col] * a.s_flat / x[j];
         }
     }
-    cluster.barrier_wait();
-}
-
-// launch with programmatic stream serialization (unless disabled) and an optional cluster shape
-template <typename... KArgs, typename... Args>
-cudaError_t launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, int cluster_y, cudaStream_t s,
-                      Args&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[2];
-    int n = 0;
-    if (cluster_y > 0) {
-        attr[n].id = cudaLaunchAttributeClusterDimension;
-        attr[n].val.clusterDim.x = 1;
-        attr[n].val.clusterDim.y = (unsigned)cluster_y;
-        attr[n].val.clusterDim.z = 1;
-        ++n;
-    }
-    if (pdl_enabled()) {
-        attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[n].val.programmaticStreamSerializationAllowed = 1;
-        ++n;
-    }
-    cfg.attrs = attr;
-    cfg.numAttrs = n;
-    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    cluster_exit();
 }
 
 template <int ITEMS, bool DHALF, int KIND>

@@ -86,6 +86,43 @@ struct PassArgs {
     float s_flat;
 };
 
+// One directional pass adjoint (see dts_backward.cu).
+struct BwdArgs {
+    const float* x;         // the pass input recomputed from the checkpoint (pitch `pitch`)
+    const void* d;          // distances along the pass direction
+    const float* gin;       // dL/d(pass output) (not read by the update variant)
+    float* gout;            // dL/d(pass input)
+    float* dbar;            // += dL/d(distances)
+    float* gz;              // dL/dz of the iterate (update variant: read then overwritten;
+                            // final horizontal pass: += dL/d(pass input))
+    int H, W;
+    long long pitch;
+    float k2;               // log2(a_i)
+    float lna;              // ln(a_i)
+    // data-term update adjoint (last vertical pass)
+    const void* t;
+    int t_dtype;
+    const float* c;         // dense pitch W
+    const float* zk;        // checkpoint z_k (pitch `pitch`)
+    float* gt;              // += dL/dt (dense, may be null)
+    float* gc;              // += dL/dc (dense, may be null)
+    float lambda, step;
+    int update;
+};
+
+struct GuideGradArgs {
+    const void* guide;
+    long long ch_stride, row_stride;
+    int C, H, W, gdtype, norm, dhalf;
+    float k;                // sigma_s / sigma_r
+    const void* dX;
+    const void* dY;
+    const float* dXb;
+    const float* dYb;
+    long long pitch;
+    float* out;             // C x H x W dense
+};
+
 struct ColPlan {
     int items;   // rows per thread
     int warps;   // warps per CTA
@@ -109,6 +146,12 @@ enum KernelId {
     KID_COL_PLAIN = 4,
     KID_COL_UPDATE = 5,
     KID_COL_SUPPORT = 6,
+    KID_ROW_BWD = 7,
+    KID_ROW_BWD_FINAL = 8,
+    KID_COL_BWD = 9,
+    KID_COL_BWD_UPDATE = 10,
+    KID_GUIDE_GRAD = 11,
+    KID_AXPY = 12,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
@@ -127,5 +170,15 @@ cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const Co
 bool plan_rows(int W, RowPlan* p);
 bool plan_cols(int H, ColPlan* p);
 cudaError_t prepare_kernels();
+
+// backward launchers (dts_backward.cu)
+bool plan_rows_bwd(int W, RowPlan* p);
+bool plan_cols_bwd(int H, ColPlan* p);
+cudaError_t launch_row_bwd(const BwdArgs& a, int dist_half, bool final_pass, const RowPlan& p, cudaStream_t s);
+cudaError_t launch_col_bwd(const BwdArgs& a, int dist_half, bool update, const ColPlan& p, cudaStream_t s);
+cudaError_t launch_guide_grad(const GuideGradArgs& a, cudaStream_t s);
+cudaError_t launch_axpy_plane(const float* src, long long sp, float* dst, long long dp, int H, int W, int accumulate,
+                              cudaStream_t s);
+cudaError_t prepare_backward_kernels();
 
 }  // namespace dts

@@ -97,6 +97,12 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_COL_PLAIN: return "col_pass_kernel";
         case KID_COL_UPDATE: return "col_pass_kernel<update>";
         case KID_COL_SUPPORT: return "col_pass_kernel<support>";
+        case KID_ROW_BWD: return "row_bwd_kernel";
+        case KID_ROW_BWD_FINAL: return "row_bwd_kernel<final>";
+        case KID_COL_BWD: return "col_bwd_kernel";
+        case KID_COL_BWD_UPDATE: return "col_bwd_kernel<update>";
+        case KID_GUIDE_GRAD: return "guide_grad_kernel";
+        case KID_AXPY: return "axpy_plane_kernel";
         default: return "unknown";
     }
 }

@@ -1,0 +1,288 @@
+// Segment algebra and line exchanges shared by the forward and backward pass kernels.
+//
+// A pass (forward or adjoint) runs two first-order recurrences along every line: one from left
+// to right and one from right to left on the result of the first.  A thread owns a segment of
+// consecutive positions.  With c the value entering the segment from the left and k the value
+// entering from the right, any such pair satisfies
+//     c_out   = A c + B                      (left-to-right value leaving on the right)
+//     k_start = al k + be c + ga             (right-to-left value at the segment's first position)
+// and these five numbers of adjacent groups compose associatively (coupled_compose).  A "mode"
+// bundles what one exchange carries:
+//     Pre          what the exclusive prefix needs (the left-to-right maps)
+//     Suf          what the exclusive suffix needs
+//     pre_identity / pre_compose, suf_identity / suf_compose   (f first, s to its right)
+// row_exchange (warp shuffles + one shared-memory round) and col_exchange (shared memory + one
+// distributed-shared-memory round across the CTAs of a cluster) return, for every segment, the
+// composition of all segments before it (pre) and after it (suf) on its line.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include <type_traits>
+#include <utility>
+
+#include "dts_internal.cuh"
+
+namespace dts {
+namespace scan {
+
+namespace cg = cooperative_groups;
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// 2^x with the SFU instruction (PTX ex2.approx.ftz.f32; relative error ~2^-22, results below
+// the normal range flush to zero, which is harmless for a feedback weight).
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Programmatic dependent launch: a kernel launched with the programmatic-serialization
+// attribute may start while its predecessor drains; it must wait for the predecessor's
+// completion (and memory) before touching global data, and it lets its own successor start
+// launching once it no longer needs the SM slots it would free.  Both are no-ops otherwise.
+__device__ __forceinline__ void wait_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void release_successor() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// v -> A v + B: the left-to-right map of a group of positions
+struct Aff {
+    float A, B;
+};
+__device__ __forceinline__ Aff aff_identity() { return Aff{1.f, 0.f}; }
+__device__ __forceinline__ Aff aff_compose(const Aff& f, const Aff& s) { return Aff{f.A * s.A, fmaf(s.A, f.B, s.B)}; }
+
+// the coupled five numbers of a group
+struct Coupled {
+    float A, B, al, be, ga;
+};
+__device__ __forceinline__ Coupled coupled_identity() { return Coupled{1.f, 0.f, 1.f, 0.f, 0.f}; }
+// group f followed by group s:  c_mid = A_f c + B_f,  k_mid = al_s k + be_s c_mid + ga_s,
+// k_start = al_f k_mid + be_f c + ga_f
+__device__ __forceinline__ Coupled coupled_compose(const Coupled& f, const Coupled& s) {
+    Coupled o;
+    o.A = f.A * s.A;
+    o.B = fmaf(s.A, f.B, s.B);
+    o.al = f.al * s.al;
+    o.be = fmaf(f.al * s.be, f.A, f.be);
+    o.ga = fmaf(f.al, fmaf(s.be, f.B, s.ga), f.ga);
+    return o;
+}
+
+// One forward walk over a segment gives its coupled numbers.  The left-to-right recurrence is
+//     u[n] = w[n] u[n-1] + (NORM ? (1 - w[n]) : 1) y[n]
+// and the right-to-left one, on u, is v[n] = w'[n] v[n+1] + (1 - w'[n]) u[n] with w'[n] = w[n+1]
+// (wn for the last position).  P_n = prod_{m<=n} w_m is the weight of the entering value in
+// u[n], Q_n the value of u[n] from a zero carry, r_n = prod_{m<n} w'_m the weight of u[n]'s
+// contribution path to v at the segment start:  be = sum r_n (1-w'_n) P_n,  ga = sum r_n (1-w'_n) Q_n.
+template <bool NORM, int N>
+__device__ __forceinline__ Coupled coupled_local(const float (&y)[N], const float (&w)[N], float wn) {
+    float P = 1.f, Q = 0.f, r = 1.f, be = 0.f, ga = 0.f;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        P *= w[j];
+        if constexpr (NORM) Q = fmaf(w[j], Q - y[j], y[j]);
+        else Q = fmaf(w[j], Q, y[j]);
+        const float wp = (j + 1 < N) ? w[j + 1] : wn;
+        const float coef = fmaf(-r, wp, r);
+        be = fmaf(coef, P, be);
+        ga = fmaf(coef, Q, ga);
+        r *= wp;
+    }
+    return Coupled{P, Q, r, be, ga};
+}
+
+// value entering a segment from the right, given the composition of everything after it and
+// the left-to-right value leaving it
+__device__ __forceinline__ float k_entering(const Coupled& after, float c_out) {
+    return fmaf(after.be, c_out, after.ga);
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_up_t(const T& v, int off) {
+    constexpr int n = sizeof(T) / 4;
+    T r;
+    const float* s = reinterpret_cast<const float*>(&v);
+    float* d = reinterpret_cast<float*>(&r);
+#pragma unroll
+    for (int i = 0; i < n; ++i) d[i] = __shfl_up_sync(kFull, s[i], off);
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_down_t(const T& v, int off) {
+    constexpr int n = sizeof(T) / 4;
+    T r;
+    const float* s = reinterpret_cast<const float*>(&v);
+    float* d = reinterpret_cast<float*>(&r);
+#pragma unroll
+    for (int i = 0; i < n; ++i) d[i] = __shfl_down_sync(kFull, s[i], off);
+    return r;
+}
+
+// ---------------------------------------------------------------- exchanges
+template <class M>
+__device__ __forceinline__ typename M::Pre warp_scan_pre(typename M::Pre v, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const typename M::Pre o = shfl_up_t(v, off);
+        if (lane >= off) v = M::pre_compose(o, v);
+    }
+    return v;
+}
+
+template <class M>
+__device__ __forceinline__ typename M::Suf warp_scan_suf(typename M::Suf v, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const typename M::Suf o = shfl_down_t(v, off);
+        if (lane + off < 32) v = M::suf_compose(v, o);
+    }
+    return v;
+}
+
+// Segments of one row are consecutive threads (a row never shares a warp with another row):
+// warp `wrow` of the row's `wpr` warps, the row's first warp being CTA warp `wbase`.
+// s_pre / s_suf: shared arrays of at least 32 entries.  Contains __syncthreads when wpr > 1
+// (wpr must then be uniform across the CTA).
+template <class M>
+__device__ __forceinline__ void row_exchange(const typename M::Pre& own_pre, const typename M::Suf& own_suf,
+                                             int lane, int warp, int wrow, int wbase, int wpr,
+                                             typename M::Pre* s_pre, typename M::Suf* s_suf,
+                                             typename M::Pre& pre, typename M::Suf& suf) {
+    const typename M::Pre inc_pre = warp_scan_pre<M>(own_pre, lane);
+    const typename M::Suf inc_suf = warp_scan_suf<M>(own_suf, lane);
+    pre = shfl_up_t(inc_pre, 1);
+    suf = shfl_down_t(inc_suf, 1);
+    if (lane == 0) pre = M::pre_identity();
+    if (lane == 31) suf = M::suf_identity();
+    if (wpr > 1) {
+        if (lane == 31) s_pre[warp] = inc_pre;
+        if (lane == 0) s_suf[warp] = inc_suf;
+        __syncthreads();
+        typename M::Pre wpre = M::pre_identity();
+        for (int q = 0; q < wrow; ++q) wpre = M::pre_compose(wpre, s_pre[wbase + q]);
+        typename M::Suf wsuf = M::suf_identity();
+        for (int q = wrow + 1; q < wpr; ++q) wsuf = M::suf_compose(wsuf, s_suf[wbase + q]);
+        pre = M::pre_compose(wpre, pre);
+        suf = M::suf_compose(suf, wsuf);
+    }
+}
+
+// Shared state of a column exchange: NWMAX warps per CTA.
+template <class M, int NWMAX>
+struct ColShared {
+    typename M::Pre pre[NWMAX][32];
+    typename M::Suf suf[NWMAX][32];
+    typename M::Pre cta_pre[32];
+    typename M::Suf cta_suf[32];
+    typename M::Pre cl_pre[32];
+    typename M::Suf cl_suf[32];
+};
+
+// Segments of a column: warp q of cluster CTA r is segment r*NW + q (lane = column).  Ends with
+// barrier.cluster.arrive: the caller must execute cluster_exit() before returning, after which
+// no CTA of the cluster reads another's shared memory.
+template <class M, int NWMAX>
+__device__ __forceinline__ void col_exchange(const typename M::Pre& own_pre, const typename M::Suf& own_suf,
+                                             int lane, int warp, int NW, ColShared<M, NWMAX>& sh,
+                                             typename M::Pre& pre, typename M::Suf& suf) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int CS = (int)cluster.num_blocks();
+    sh.pre[warp][lane] = own_pre;
+    sh.suf[warp][lane] = own_suf;
+    __syncthreads();
+    typename M::Pre wpre = M::pre_identity();
+    for (int q = 0; q < warp; ++q) wpre = M::pre_compose(wpre, sh.pre[q][lane]);
+    typename M::Suf wsuf = M::suf_identity();
+    for (int q = warp + 1; q < NW; ++q) wsuf = M::suf_compose(wsuf, sh.suf[q][lane]);
+    if (CS > 1) {
+        // CTA totals: the last warp holds the full prefix, the first warp the full suffix
+        if (warp == NW - 1) sh.cta_pre[lane] = M::pre_compose(wpre, own_pre);
+        if (warp == 0) sh.cta_suf[lane] = M::suf_compose(own_suf, wsuf);
+        cluster.sync();
+        if (warp == 0) {
+            typename M::Pre cp = M::pre_identity();
+            for (int q = 0; q < rank; ++q) cp = M::pre_compose(cp, *cluster.map_shared_rank(&sh.cta_pre[lane], q));
+            typename M::Suf cs = M::suf_identity();
+            for (int q = rank + 1; q < CS; ++q) cs = M::suf_compose(cs, *cluster.map_shared_rank(&sh.cta_suf[lane], q));
+            sh.cl_pre[lane] = cp;
+            sh.cl_suf[lane] = cs;
+        }
+        __syncthreads();
+        wpre = M::pre_compose(sh.cl_pre[lane], wpre);
+        wsuf = M::suf_compose(wsuf, sh.cl_suf[lane]);
+    }
+    pre = wpre;
+    suf = wsuf;
+    // every remote read of this CTA is done: peers may exit once all have arrived
+    cluster.barrier_arrive();
+}
+
+__device__ __forceinline__ void cluster_exit() { cg::this_cluster().barrier_wait(); }
+
+// ---------------------------------------------------------------- loads
+template <bool DHALF>
+__device__ __forceinline__ void load4_d(const void* base, long long idx, float* out) {
+    if constexpr (DHALF) {
+        uint2 v = *reinterpret_cast<const uint2*>(static_cast<const __half*>(base) + idx);
+        __half2 h0 = *reinterpret_cast<__half2*>(&v.x);
+        __half2 h1 = *reinterpret_cast<__half2*>(&v.y);
+        float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+        out[0] = f0.x; out[1] = f0.y; out[2] = f1.x; out[3] = f1.y;
+    } else {
+        float4 v = *reinterpret_cast<const float4*>(static_cast<const float*>(base) + idx);
+        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    }
+}
+
+template <bool DHALF>
+__device__ __forceinline__ float load1_d(const void* base, long long idx) {
+    if constexpr (DHALF) return __half2float(static_cast<const __half*>(base)[idx]);
+    else return static_cast<const float*>(base)[idx];
+}
+
+__device__ __forceinline__ void load4_f(const float* base, long long idx, float* out) {
+    const float4 v = *reinterpret_cast<const float4*>(base + idx);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+
+__device__ __forceinline__ void store4_f(float* base, long long idx, const float* v) {
+    *reinterpret_cast<float4*>(base + idx) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// ---------------------------------------------------------------- launch
+// Launch with programmatic stream serialization (unless disabled) and an optional cluster shape
+// (1, cluster_y, 1).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, int cluster_y, cudaStream_t s,
+                      Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    int n = 0;
+    if (cluster_y > 0) {
+        attr[n].id = cudaLaunchAttributeClusterDimension;
+        attr[n].val.clusterDim.x = 1;
+        attr[n].val.clusterDim.y = (unsigned)cluster_y;
+        attr[n].val.clusterDim.z = 1;
+        ++n;
+    }
+    if (pdl_enabled()) {
+        attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[n].val.programmaticStreamSerializationAllowed = 1;
+        ++n;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = n;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+}  // namespace scan
+}  // namespace dts

@@ -275,3 +275,44 @@ def dts_profile_read(max_records: int = 1 << 16):
 
 def version() -> str:
     return load().dts_version().decode()
+
+
+class DTSSolve(torch.autograd.Function):
+    """z_K = dts_solve(guide, target, conf, z_init) with the hand-written CUDA backward.
+
+    The forward keeps the iterates z_0 .. z_{K-1} in its workspace; the backward
+    (dts_solve_backward) recomputes each iteration's pass inputs from them and runs the
+    reversed recurrences, giving gradients for the target, the confidence, the guide
+    (through the distances) and z_init."""
+
+    @staticmethod
+    def forward(ctx, guide, target, conf, z_init, params: Params):
+        p = dataclasses.replace(params, save_checkpoints=1)
+        ws = workspace(guide, p, with_backward=True)
+        z = dts_solve(guide, target, conf, p, z_init=z_init, ws=ws)
+        zi = z_init if z_init is not None else torch.empty(0, device=target.device)
+        ctx.save_for_backward(guide, target, conf, zi)
+        ctx.ws = ws
+        ctx.params = p
+        ctx.has_zinit = z_init is not None
+        return z
+
+    @staticmethod
+    def backward(ctx, grad_z):
+        guide, target, conf, zi = ctx.saved_tensors
+        gt, gc, gg, gz0 = dts_solve_backward(guide, target, conf, ctx.params, ctx.ws,
+                                             grad_z.contiguous().float(),
+                                             z_init=zi if ctx.has_zinit else None,
+                                             need_guide=ctx.needs_input_grad[0])
+        ctx.ws = None
+        return (gg.to(guide.dtype).reshape(guide.shape) if ctx.needs_input_grad[0] else None,
+                gt.to(target.dtype) if ctx.needs_input_grad[1] else None,
+                gc if ctx.needs_input_grad[2] else None,
+                gz0 if (ctx.has_zinit and ctx.needs_input_grad[3]) else None,
+                None)
+
+
+def solve(guide: torch.Tensor, target: torch.Tensor, conf: torch.Tensor, params: Params,
+          z_init: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Differentiable DTS solve (autograd through the CUDA backward)."""
+    return DTSSolve.apply(guide, target, conf, z_init, params)

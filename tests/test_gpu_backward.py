@@ -1,0 +1,137 @@
+"""GPU parity of dts_solve_backward (through the C ABI and the autograd Function)
+against the FP64 oracle's reverse mode, itself pinned by finite differences and
+an autograd restatement.  Tolerance (FP32 arithmetic, long reversed recurrences):
+max |g_gpu - g_oracle| <= 1e-3 * max |g_oracle| for every gradient."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1805_04590_gb300 import dts, workloads
+
+pytestmark = pytest.mark.gpu
+
+GTOL = 1e-3
+
+
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def T(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev()).to(dtype)
+
+
+def guide_noisy(H, W, C, seed):
+    rng = np.random.default_rng(seed)
+    return rng.random((C, H, W)).astype(np.float32)
+
+
+def close(gpu, ref, what):
+    scale = float(np.abs(ref).max()) or 1.0
+    err = float(np.abs(gpu - ref).max())
+    assert err <= GTOL * scale, f"{what}: {err:.3e} > {GTOL * scale:.3e}"
+
+
+def run_case(H, W, C=3, K=4, update=dts.UPDATE_GD, norm=dts.NORM_L1, zinit=False, seed=0, passes=3,
+             sigma_s=8.0, sigma_r=0.3, dist=dts.F32):
+    rng = np.random.default_rng(seed)
+    I = guide_noisy(H, W, C, seed)
+    t = rng.normal(size=(H, W)).astype(np.float32)
+    c = rng.uniform(0.1, 1.0, (H, W)).astype(np.float32)
+    gz = rng.normal(size=(H, W)).astype(np.float32)
+    z0 = rng.normal(size=(H, W)).astype(np.float32) if zinit else None
+    prm = dts.Params(lam=0.9, sigma_s=sigma_s, sigma_r=sigma_r, iterations=K, passes=passes, update=update,
+                     norm=norm, dist_dtype=dist, save_checkpoints=1)
+    g, tt, cc = T(I), T(t), T(c)
+    zi = T(z0) if zinit else None
+    ws = dts.workspace(g, prm, with_backward=True)
+    z = dts.dts_solve(g, tt, cc, prm, z_init=zi, ws=ws)
+    gt, gc, gg, gz0 = dts.dts_solve_backward(g, tt, cc, prm, ws, T(gz), z_init=zi)
+    assert dts.dts_last_status() == 0
+    kw = dict(lam=0.9, sigma_s=sigma_s, sigma_r=sigma_r, iterations=K, passes=passes, update=update, norm=norm)
+    if dist == dts.F16:
+        return z, gt, gc, gg, gz0, None
+    ref = oracle.solve_backward(I, t, c, gz, z_init=z0, **kw)
+    zr = oracle.solve(I, t, c, z_init=z0, **kw)
+    np.testing.assert_allclose(z.cpu().numpy(), zr, atol=1e-4 * float(np.ptp(t)))
+    close(gt.cpu().numpy(), ref["t"], "grad target")
+    close(gc.cpu().numpy(), ref["c"], "grad conf")
+    close(gg.cpu().numpy(), ref["guide"], "grad guide")
+    if zinit:
+        close(gz0.cpu().numpy(), ref["z_init"], "grad z_init")
+    return z, gt, gc, gg, gz0, ref
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 23), (29, 1), (17, 31), (64, 80), (130, 70), (45, 300), (300, 45)])
+def test_backward_shapes(H, W):
+    run_case(H, W, seed=H * 31 + W)
+
+
+@pytest.mark.parametrize("update,norm,zinit", [(dts.UPDATE_JACOBI, dts.NORM_L1, False),
+                                               (dts.UPDATE_GD, dts.NORM_L2, False),
+                                               (dts.UPDATE_JACOBI, dts.NORM_L2, True),
+                                               (dts.UPDATE_GD, dts.NORM_L1, True)])
+def test_backward_variants(update, norm, zinit):
+    run_case(70, 90, update=update, norm=norm, zinit=zinit, seed=5 + update + 2 * norm)
+
+
+def test_backward_iterations_and_passes():
+    run_case(50, 60, K=0, seed=1)
+    run_case(50, 60, K=1, passes=1, seed=2)
+    run_case(50, 60, K=7, passes=5, seed=3)
+
+
+def test_backward_larger_multi_cluster():
+    run_case(600, 420, K=3, seed=9, sigma_s=20.0)
+
+
+def test_autograd_function_matches_oracle():
+    H, W = 40, 52
+    rng = np.random.default_rng(77)
+    I = guide_noisy(H, W, 3, 77)
+    t = rng.normal(size=(H, W)).astype(np.float32)
+    c = rng.uniform(0.1, 1.0, (H, W)).astype(np.float32)
+    gz = rng.normal(size=(H, W)).astype(np.float32)
+    prm = dts.Params(lam=0.9, sigma_s=8.0, sigma_r=0.3, iterations=3)
+    g = T(I).requires_grad_(True)
+    tt = T(t).requires_grad_(True)
+    cc = T(c).requires_grad_(True)
+    z = dts.solve(g, tt, cc, prm)
+    (z * T(gz)).sum().backward()
+    ref = oracle.solve_backward(I, t, c, gz, lam=0.9, sigma_s=8.0, sigma_r=0.3, iterations=3)
+    close(tt.grad.cpu().numpy(), ref["t"], "autograd t")
+    close(cc.grad.cpu().numpy(), ref["c"], "autograd c")
+    close(g.grad.cpu().numpy(), ref["guide"], "autograd guide")
+
+
+def test_backward_fp16_distances_runs_and_agrees_roughly():
+    z, gt, gc, gg, _, _ = run_case(64, 96, dist=dts.F16, seed=4)
+    _, gt32, gc32, gg32, _, _ = run_case(64, 96, seed=4)
+    for a, b in ((gt, gt32), (gc, gc32)):
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        assert np.abs(a - b).max() <= 2e-2 * np.abs(b).max()
+
+
+def test_backward_depth_sr_batch_full_size():
+    """The x16 depth super-resolution workload (8 x 2048 x 1536, K = 10) at full size: every
+    gradient of every image against the oracle's reverse mode."""
+    wl = workloads.make(2)
+    q = wl.params
+    prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes,
+                     save_checkpoints=1)
+    rng = np.random.default_rng(2002)
+    for i, p in enumerate(wl.problems):
+        gz = rng.normal(size=p.target.shape).astype(np.float32)
+        g, tt, cc = T(p.guide), T(p.target), T(p.conf)
+        ws = dts.workspace(g, prm, with_backward=True)
+        dts.dts_solve(g, tt, cc, prm, ws=ws)
+        gt, gc, gg, _ = dts.dts_solve_backward(g, tt, cc, prm, ws, T(gz))
+        ref = oracle.solve_backward(p.guide, p.target, p.conf, gz, lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r,
+                                    iterations=q.iterations, passes=q.passes)
+        close(gt.cpu().numpy(), ref["t"], f"image {i} grad target")
+        close(gc.cpu().numpy(), ref["c"], f"image {i} grad conf")
+        close(gg.cpu().numpy(), ref["guide"], f"image {i} grad guide")
+        del ws
