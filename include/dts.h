@@ -163,6 +163,16 @@ size_t dts_noalloc_max_workspace(void);
  * synchronisation itself failed. */
 int dts_last_status(dts_stream stream);
 
+/* ---- fault injection for tests (host-requested, one-shot; nothing faults or traps) ----
+ * DTS_INJECT_TMA_SKIP: the next vertical pass runs on the kernel that stages its tiles with
+ * TMA (the one path with device-side waits) and, when it covers its columns in a single round,
+ * skips the first tile load of its first CTA; that CTA's bounded wait (about a millisecond under
+ * injection) gives up, computes on unfilled shared memory and records DTS_ERR_TIMEOUT, which
+ * dts_last_status() then returns.  kind 0 cancels.
+ * DTS_ERR_INVALID_ARG for unknown kinds. */
+#define DTS_INJECT_TMA_SKIP 1
+int dts_debug_inject(int kind);
+
 /* ---- per-launch kernel timing (a tracing aid; not part of the paper's method) ----
  * mode 1: clear the record and start bracketing every kernel the library launches with two
  * CUDA events on that launch's stream; mode 2: resume without clearing; mode 0: stop.

@@ -17,6 +17,8 @@ __device__ int g_status = 0;
 namespace {
 
 constexpr int kMaxDevices = 64;
+int* g_status_ptr[kMaxDevices] = {};
+bool g_inject_tma_skip = false;
 std::mutex g_prep_mutex;
 bool g_prepared[kMaxDevices] = {};
 
@@ -30,6 +32,33 @@ int ensure_prepared() {
     }
     return DTS_OK;
 }
+
+}  // namespace
+
+int* status_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    if (!g_status_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+        g_status_ptr[dev] = static_cast<int*>(p);
+    }
+    return g_status_ptr[dev];
+}
+
+bool injected_tma_skip_pending() {
+    std::lock_guard<std::mutex> lock(g_prep_mutex);
+    return g_inject_tma_skip;
+}
+
+bool take_injected_tma_skip() {
+    std::lock_guard<std::mutex> lock(g_prep_mutex);
+    const bool v = g_inject_tma_skip;
+    g_inject_tma_skip = false;
+    return v;
+}
+
+namespace {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -64,6 +93,9 @@ struct Layout {
     size_t plane_f32;   // bytes of one FP32 plane
     size_t plane_d;     // bytes of one distance plane
     size_t dX, dY, u, chat, z;  // offsets
+    size_t agg, carry, counters;  // split vertical pass scratch
+    long long agg_pitch, agg_plane;
+    int nstrips128;
     int z_planes;       // 1 (in place) or K checkpoints
     size_t fwd_end;     // bytes used by the forward
     // backward scratch
@@ -85,6 +117,13 @@ Layout make_layout(int H, int W, const dts_params* p, int with_backward) {
     L.u = off; off += L.plane_f32;
     L.chat = off;
     if (p->conf_mode == DTS_CONF_SUPPORT) off += L.plane_f32;
+    split_col_scratch(H, W, &L.agg_pitch, &L.agg_plane, &L.nstrips128);
+    L.agg = off;
+    off += align_up((size_t)L.agg_plane * 5 * sizeof(float), kPlaneAlign);
+    L.carry = off;
+    off += align_up((size_t)L.agg_plane * 2 * sizeof(float), kPlaneAlign);
+    L.counters = off;
+    off += align_up((size_t)L.nstrips128 * sizeof(unsigned), kPlaneAlign);
     L.z = off;
     const bool keep = p->save_checkpoints || with_backward;
     L.z_planes = keep ? (p->iterations > 0 ? p->iterations : 1) : 1;
@@ -153,13 +192,34 @@ int run_distances(const dts_guide* g, const dts_params* p, const Layout& L, void
     return cuda_status(launch_distances(a, s));
 }
 
+// workspace base of the pass arguments (set by the entry points before building passes)
+thread_local void* t_ws = nullptr;
+
 PassArgs base_pass(const dts_guide* g, const Layout& L) {
     PassArgs a = {};
     a.H = g->H;
     a.W = g->W;
     a.pitch = L.pitch;
     a.dst_pitch = L.pitch;
+    a.status = status_word();
+    if (t_ws) {
+        a.agg = reinterpret_cast<float*>(static_cast<char*>(t_ws) + L.agg);
+        a.carry = reinterpret_cast<float*>(static_cast<char*>(t_ws) + L.carry);
+        a.counters = reinterpret_cast<unsigned*>(static_cast<char*>(t_ws) + L.counters);
+        a.agg_pitch = L.agg_pitch;
+        a.agg_plane = L.agg_plane;
+    }
     return a;
+}
+
+// Binds the workspace for base_pass and zeroes the split pass's ticket counters (each strip's
+// last CTA resets its own counter, so one clear per call suffices).
+int bind_workspace(void* ws, const Layout& L, cudaStream_t s) {
+    t_ws = ws;
+    if (cudaMemsetAsync(static_cast<char*>(ws) + L.counters, 0, (size_t)L.nstrips128 * sizeof(unsigned), s) !=
+        cudaSuccess)
+        return DTS_ERR_CUDA;
+    return DTS_OK;
 }
 
 // effective confidence for DTS_CONF_SUPPORT: chat = c * S_flat / S (written to L.chat)
@@ -202,6 +262,7 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
         if (z_init) return cuda_status(launch_copy_plane(z_init, DTS_F32, W, z_out, W, g->H, W, s));
         return cuda_status(launch_copy_plane(target, tdt, W, z_out, W, g->H, W, s));
     }
+    if ((st = bind_workspace(ws, L, s))) return st;
     const bool keep = L.z_planes > 1 || p->save_checkpoints;
     auto zslot = [&](int k) -> float* {
         return reinterpret_cast<float*>(ws_at(ws, L.z + (keep ? (size_t)k * L.plane_f32 : 0)));
@@ -319,6 +380,7 @@ extern "C" int dts_filter(const dts_guide* guide, const dts_params* params, cons
     if (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.fwd_end) return DTS_ERR_WORKSPACE;
     if ((st = ensure_prepared())) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if ((st = bind_workspace(ws, L, s))) return st;
     float* u = reinterpret_cast<float*>(ws_at(ws, L.u));
     if ((st = run_distances(guide, &p, L, ws, src, DTS_F32, u, s))) return st;
     float k2[kMaxPasses];
@@ -430,6 +492,7 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
     if (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.total) return DTS_ERR_WORKSPACE;
     if ((st = ensure_prepared())) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if ((st = bind_workspace(ws, L, s))) return st;
     const int H = guide->H, W = guide->W, K = params->iterations, N = params->passes;
     const long long P = L.pitch;
     const int dh = params->dist_dtype == DTS_F16;
@@ -527,6 +590,13 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
         gg.out = grad_guide;
         if ((st = cuda_status(launch_guide_grad(gg, s)))) return st;
     }
+    return DTS_OK;
+}
+
+extern "C" int dts_debug_inject(int kind) {
+    if (kind != 0 && kind != DTS_INJECT_TMA_SKIP) return DTS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_prep_mutex);
+    g_inject_tma_skip = kind == DTS_INJECT_TMA_SKIP;
     return DTS_OK;
 }
 

@@ -23,8 +23,13 @@
 // a cluster for columns -- gives every segment its exact carries in both directions, after
 // which it replays its positions once each way.  A line is read once and written once per
 // pass: 2 s_z + s_d bytes per pixel.
+#include <cuda.h>  // CUtensorMap and its enums; the encoder comes from the runtime's driver entry point
 #include <stdio.h>
 #include <stdlib.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "dts_scan.cuh"
 
@@ -271,7 +276,7 @@ constexpr int col_max_threads() {
 // its operand loads in flight and gets the larger budget)
 template <int ITEMS, int KIND>
 constexpr int col_min_blocks() {
-    return (ITEMS == 16 && KIND != PASS_UPDATE) ? 2 : 1;
+    return ITEMS == 16 ? 2 : 1;
 }
 
 template <int ITEMS, bool DHALF, int KIND>
@@ -289,17 +294,16 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
 
     wait_predecessor();
     if constexpr (KIND == PASS_UPDATE) {
-        // the update operands are read only at the end: start bringing them into L2 now
-        if ((lane == 0 || lane == 31) && col_ok) {
-            const int tsz = a.t_dtype == DTS_F32 ? 4 : 2;
-#pragma unroll 1
-            for (int j = 0; j < ITEMS; ++j) {
-                const int r = row0 + j;
-                if (r < a.H) {
-                    prefetch_l2(a.zk + (long long)r * P + col);
-                    prefetch_l2(static_cast<const char*>(a.t) + ((long long)r * a.W + col) * tsz);
-                    prefetch_l2(a.c + (a.c_pitched ? (long long)r * P : (long long)r * a.W) + col);
-                }
+        // the update operands are read only at the end: start bringing them into L2 now, lane j
+        // taking row j of the warp's rows (each prefetch covers the warp's 128-byte row segment)
+        const int c0 = blockIdx.x * 32;
+        const int tsz = a.t_dtype == DTS_F32 ? 4 : 2;
+        for (int j = lane; j < ITEMS; j += 32) {
+            const int r = row0 + j;
+            if (r < a.H) {
+                prefetch_l2(a.zk + (long long)r * P + c0);
+                prefetch_l2(static_cast<const char*>(a.t) + ((long long)r * a.W + c0) * tsz);
+                prefetch_l2(a.c + (a.c_pitched ? (long long)r * P : (long long)r * a.W) + c0);
             }
         }
     }
@@ -376,6 +380,238 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
     cluster_exit();
 }
 
+// ---------------------------------------------------------------- persistent horizontal pass
+// Persistent CTAs loop over groups of rpb rows; the next group's positions and distances are
+// loaded into a second register set while the current group is exchanged and replayed, so the
+// memory pipe stays busy through the compute.  Same thread layout as row_pass_kernel.
+// largest CTA of the persistent horizontal pass (the prefetch registers double the data)
+template <int ITEMS>
+constexpr int row_persist_max_threads() {
+    return ITEMS <= 8 ? 1024 : 512;
+}
+
+template <int ITEMS, bool DHALF, int KIND, bool PREFETCH>
+__global__ void __launch_bounds__(PREFETCH ? row_persist_max_threads<ITEMS>() : 1024) row_persist_kernel(PassArgs a, int tpr, int ngroups) {
+    static_assert(ITEMS % 4 == 0, "ITEMS must be a multiple of 4");
+    using M = typename std::conditional<KIND == PASS_SUPPORT, SupportMode, CoupledMode>::type;
+    __shared__ typename M::Pre s_pre[2][32];
+    __shared__ typename M::Suf s_suf[2][32];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int rloc = tid / tpr;
+    const int t = tid - rloc * tpr;
+    const int wpr = tpr >> 5;
+    const int wrow = t >> 5;
+    const int wbase = warp - wrow;
+    const int rpb = blockDim.x / tpr;
+    const int e0 = t * ITEMS;
+    const long long P = a.pitch;
+
+    float xn[ITEMS], dn[ITEMS];
+    auto load = [&](int grp) {
+        const int row = grp * rpb + rloc;
+        if (row < a.H && e0 < P) {
+            const long long base = (long long)row * P + e0;
+#pragma unroll
+            for (int q = 0; q < ITEMS / 4; ++q) {
+                if constexpr (KIND != PASS_SUPPORT) load4_f(a.src, base + 4 * q, &xn[4 * q]);
+                load4_d<DHALF>(a.d, base + 4 * q, &dn[4 * q]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) xn[j] = dn[j] = 0.f;
+        }
+    };
+
+    wait_predecessor();
+    int g = blockIdx.x;
+    if (PREFETCH && g < ngroups) load(g);
+    for (int it = 0; g < ngroups; g += gridDim.x, ++it) {
+        if (!PREFETCH) load(g);
+        float x[ITEMS], w[ITEMS];
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            x[j] = KIND == PASS_SUPPORT ? 1.f : xn[j];
+            w[j] = dn[j];
+        }
+        const int gnext = g + gridDim.x;
+        if (PREFETCH && gnext < ngroups) load(gnext);
+        if (gnext >= ngroups) release_successor();
+
+        const int row = g * rpb + rloc;
+        const bool row_ok = row < a.H;
+        const long long base = (long long)row * P + e0;
+        const bool live = row_ok && e0 < P;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) w[j] = ex2(a.k2 * w[j]);
+        if (!live || e0 + ITEMS > a.W) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j)
+                if (!live || e0 + j >= a.W) x[j] = w[j] = 0.f;
+        }
+        if (e0 == 0) w[0] = 0.f;
+        float wn = __shfl_down_sync(kFull, w[0], 1);
+        if (lane == 31) {
+            const int en = e0 + ITEMS;
+            wn = (row_ok && en < a.W) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)row * P + en)) : 0.f;
+        }
+        typename M::Pre own_pre, pre;
+        typename M::Suf own_suf, suf;
+        M::local(x, w, wn, own_pre, own_suf);
+        row_exchange<M>(own_pre, own_suf, lane, warp, wrow, wbase, wpr, s_pre[it & 1], s_suf[it & 1], pre, suf);
+        M::apply(x, w, wn, own_pre, pre.B, suf);
+        if (live) {
+#pragma unroll
+            for (int q = 0; q < ITEMS / 4; ++q) store4_f(a.dst, base + 4 * q, &x[4 * q]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- persistent TMA vertical pass
+// One cluster of CS CTAs per strip of 32 columns, looping over strips (persistent grid).  CTA r
+// owns rows [r R, r R + R) of the strip, R = NW * ITEMS; its tile of the pass input and of the
+// distances arrives by 2-D TMA into one of two shared-memory stages, the next strip's tile
+// streaming in while the current one is exchanged and replayed.  Lane = column, warp q holds rows
+// [q ITEMS, q ITEMS + ITEMS) of the tile: every shared-memory row read is 128 contiguous bytes.
+// Waits on the stage barriers are bounded (a.timeout cycles); a wait that gives up records
+// DTS_ERR_TIMEOUT in the status word and the CTA carries on (every barrier is still executed).
+// KIND: PASS_PLAIN or PASS_UPDATE (as in col_pass_kernel).
+constexpr int kTmaColMaxWarps = 8;
+
+template <int ITEMS, bool DHALF>
+constexpr size_t tma_stage_bytes(int NW) {
+    return (size_t)NW * ITEMS * 32 * (4 + (DHALF ? 2 : 4));
+}
+
+// register budget: three resident CTAs of 8 warps up to 16 rows per thread, two beyond
+template <int ITEMS>
+constexpr int tma_col_min_blocks() {
+    return ITEMS <= 16 ? 3 : 2;
+}
+
+template <int ITEMS, bool DHALF, int KIND>
+__global__ void __launch_bounds__(32 * kTmaColMaxWarps, tma_col_min_blocks<ITEMS>()) col_tma_kernel(const __grid_constant__ CUtensorMap tm_x,
+                                                                      const __grid_constant__ CUtensorMap tm_d,
+                                                                      PassArgs a, int nstrips, long long timeout,
+                                                                      int skip_first) {
+    using M = CoupledMode;
+    using DT = typename std::conditional<DHALF, __half, float>::type;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ ColShared<M, kTmaColMaxWarps> sh;
+    __shared__ __align__(8) uint64_t bar[2];
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int NW = blockDim.x >> 5;
+    const int R = NW * ITEMS;
+    const int rank = (int)cluster.block_rank();
+    const int CS = (int)cluster.num_blocks();
+    const int tile_row = rank * R;
+    const int row0 = tile_row + warp * ITEMS;
+    const long long P = a.pitch;
+    const size_t xbytes = (size_t)R * 32 * 4;
+    const size_t stage_bytes = (size_t)R * 32 * (4 + sizeof(DT));
+    const uint32_t tx = (uint32_t)stage_bytes;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    wait_predecessor();
+    auto issue = [&](int stage, int strip) {
+        unsigned char* st = dsm + (size_t)stage * stage_bytes;
+        mbar_arrive_expect_tx(&bar[stage], tx);
+        tma_load_2d(st, &tm_x, strip * 32, tile_row, &bar[stage]);
+        tma_load_2d(st + xbytes, &tm_d, strip * 32, tile_row, &bar[stage]);
+    };
+    if (threadIdx.x == 0 && (int)blockIdx.x < nstrips) {
+        // fault injection for tests (single-strip grids only): leave the first stage unfilled
+        if (!(skip_first && blockIdx.x == 0 && rank == 0 && nstrips <= (int)gridDim.x)) issue(0, blockIdx.x);
+    }
+    int it = 0;
+    for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x, ++it) {
+        const int stage = it & 1;
+        const uint32_t parity = (it >> 1) & 1;
+        const int next = strip + gridDim.x;
+        if (threadIdx.x == 0 && next < nstrips) issue(stage ^ 1, next);
+        const int col = strip * 32 + lane;
+        const bool col_ok = col < a.W;
+        if constexpr (KIND == PASS_UPDATE) {
+            if ((lane == 0 || lane == 31) && col_ok) {
+                const int tsz = a.t_dtype == DTS_F32 ? 4 : 2;
+#pragma unroll 1
+                for (int j = 0; j < ITEMS; ++j) {
+                    const int r = row0 + j;
+                    if (r < a.H) {
+                        prefetch_l2(a.zk + (long long)r * P + col);
+                        prefetch_l2(static_cast<const char*>(a.t) + ((long long)r * a.W + col) * tsz);
+                        prefetch_l2(a.c + (a.c_pitched ? (long long)r * P : (long long)r * a.W) + col);
+                    }
+                }
+            }
+        }
+        if (!mbar_wait_bounded(&bar[stage], parity, timeout)) atomicExch(a.status, DTS_ERR_TIMEOUT);
+        const float* sx = reinterpret_cast<const float*>(dsm + (size_t)stage * stage_bytes);
+        const DT* sd = reinterpret_cast<const DT*>(dsm + (size_t)stage * stage_bytes + xbytes);
+        float x[ITEMS], w[ITEMS];
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            x[j] = sx[(warp * ITEMS + j) * 32 + lane];
+            w[j] = to_f32<DT>(sd[(warp * ITEMS + j) * 32 + lane]);
+        }
+        float dnext = 0.f;
+        if (warp + 1 < NW) dnext = to_f32<DT>(sd[((warp + 1) * ITEMS) * 32 + lane]);
+        __syncthreads();  // this stage is free again: the next-but-one tile may land in it
+        {
+            const int rn = row0 + ITEMS;
+            if (warp + 1 == NW && col_ok && rn < a.H) dnext = load1_d<DHALF>(a.d, (long long)rn * P + col);
+        }
+        const float wn = (col_ok && row0 + ITEMS < a.H) ? ex2(a.k2 * dnext) : 0.f;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int r = row0 + j;
+            w[j] = (col_ok && r > 0 && r < a.H) ? ex2(a.k2 * w[j]) : 0.f;
+            if (!(col_ok && r < a.H)) x[j] = 0.f;
+        }
+        typename M::Pre own_pre, pre;
+        typename M::Suf own_suf, suf;
+        M::local(x, w, wn, own_pre, own_suf);
+        col_exchange_iter<M, kTmaColMaxWarps>(own_pre, own_suf, lane, warp, NW, sh, it == 0, pre, suf);
+        if (next >= nstrips) release_successor();
+        M::apply(x, w, wn, own_pre, pre.B, suf);
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int r = row0 + j;
+            if (!(col_ok && r < a.H)) continue;
+            if constexpr (KIND == PASS_PLAIN) {
+                a.dst[(long long)r * a.dst_pitch + col] = x[j];
+            } else {
+                const long long idx = (long long)r * P + col;
+                const long long di = (long long)r * a.W + col;
+                const float zb = x[j];
+                const float z = a.zk[idx];
+                const float t = load_any(a.t, di, a.t_dtype);
+                const float cf = a.c_pitched ? a.c[idx] : a.c[di];
+                float zn;
+                if (a.update == DTS_UPDATE_JACOBI) {
+                    const float den = a.lambda + cf;
+                    zn = den != 0.f ? (a.lambda * zb + cf * t) / den : z;
+                } else {
+                    float eta = a.step;
+                    if (a.clamp_step && a.lambda + cf > 0.f) eta = fminf(eta, 1.f / (a.lambda + cf));
+                    zn = z - eta * (a.lambda * (z - zb) + cf * (z - t));
+                }
+                a.zout[(long long)r * a.zout_pitch + col] = zn;
+            }
+        }
+    }
+    if (CS > 1 && it > 0) cluster_exit();
+}
+
 template <int ITEMS, bool DHALF, int KIND>
 cudaError_t launch_col_t(const PassArgs& a, const ColPlan& p, cudaStream_t s) {
     return launch_ex(col_pass_kernel<ITEMS, DHALF, KIND>, dim3((unsigned)((a.W + 31) / 32), (unsigned)p.cluster, 1),
@@ -411,6 +647,143 @@ cudaError_t allow_clusters() {
         if (r != cudaSuccess) e = r;
     }
     return e;
+}
+
+
+// ---------------------------------------------------------------- host: TMA descriptors, persistent grids
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Tiles of 32 columns x box_rows rows of an H x W plane with row pitch `pitch` elements.
+bool make_tile_map(CUtensorMap* m, const void* base, bool half, int W, int H, long long pitch, int box_rows) {
+    EncodeTiledFn fn = tensor_map_encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * (half ? 2 : 4)};
+    const cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base),
+              dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// resident CTAs per SM of a kernel (cached per kernel and block size)
+int blocks_per_sm(const void* kernel, int block, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, size_t>, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(kernel, block, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess) n = 0;
+    cache[key] = n;
+    return n;
+}
+
+// clusters of `cs` CTAs that fit at once (cached)
+int max_clusters(const void* kernel, int block, int cs, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int, size_t>, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(kernel, block, cs, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, (unsigned)cs, 1);
+    cfg.blockDim = dim3((unsigned)block, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = (unsigned)cs;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess) n = 0;
+    cache[key] = n;
+    return n;
+}
+
+// persistent grid over `units` work items with `slots` concurrent workers: equal rounds
+int balanced_grid(int units, int slots) {
+    if (slots < 1) slots = 1;
+    const int rounds = (units + slots - 1) / slots;
+    return (units + rounds - 1) / rounds;
+}
+
+long long default_timeout_cycles() { return 2000000000LL; }  // ~1 s at the boost clock
+
+template <int ITEMS, bool DHALF, int KIND>
+cudaError_t launch_col_tma_t(const PassArgs& a, const ColPlan& p, cudaStream_t s) {
+    auto kernel = col_tma_kernel<ITEMS, DHALF, KIND>;
+    const int NW = p.warps;
+    const int R = NW * ITEMS;
+    // DTS_TMA_GRID=full: one cluster per strip, no persistence and a single stage (tuning aid)
+    static const bool full_grid = getenv("DTS_TMA_GRID") && getenv("DTS_TMA_GRID")[0] == 'f';
+    const size_t smem = (full_grid ? 1 : 2) * tma_stage_bytes<ITEMS, DHALF>(NW);
+    if (cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return cudaErrorInvalidConfiguration;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        configured = true;
+    }
+    CUtensorMap tx, td;
+    if (!make_tile_map(&tx, a.src, false, a.W, a.H, a.pitch, R)) return cudaErrorInvalidValue;
+    if (!make_tile_map(&td, a.d, DHALF, a.W, a.H, a.pitch, R)) return cudaErrorInvalidValue;
+    const int nstrips = (a.W + 31) / 32;
+    const int mc = max_clusters((const void*)kernel, 32 * NW, p.cluster, smem);
+    if (mc < 1) return cudaErrorInvalidConfiguration;
+    const int gx = full_grid ? nstrips : balanced_grid(nstrips, mc);
+    const int skip = take_injected_tma_skip() ? 1 : 0;
+    const long long timeout = skip ? 2000000LL : default_timeout_cycles();
+    return launch_ex_smem(kernel, dim3((unsigned)gx, (unsigned)p.cluster, 1), dim3((unsigned)(32 * NW)), p.cluster,
+                          smem, s, tx, td, a, nstrips, timeout, skip);
+}
+
+// DTS_ROW_PREFETCH=1: the register-prefetch variant (tuning aid)
+bool row_prefetch() {
+    static const bool on = getenv("DTS_ROW_PREFETCH") != nullptr;
+    return on;
+}
+
+template <int ITEMS, bool DHALF, int KIND>
+cudaError_t launch_row_persist_t(const PassArgs& a, const RowPlan& p, cudaStream_t s) {
+    auto kernel = row_prefetch() ? row_persist_kernel<ITEMS, DHALF, KIND, true> : row_persist_kernel<ITEMS, DHALF, KIND, false>;
+    const int block = p.tpr * p.rpb;
+    const int ngroups = (a.H + p.rpb - 1) / p.rpb;
+    const int per_sm = blocks_per_sm((const void*)kernel, block, 0);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = balanced_grid(ngroups, per_sm * sm_count());
+    return launch_ex(kernel, dim3((unsigned)grid), dim3((unsigned)block), 0, s, a, p.tpr, ngroups);
 }
 
 }  // namespace
@@ -450,13 +823,27 @@ cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const Ro
     const int h = prof_begin(kind == PASS_SUPPORT ? KID_ROW_SUPPORT : KID_ROW_PLAIN, (long long)a.H * a.W,
                              dist_half ? kFlagDistHalf : 0, s);
     cudaError_t e = cudaErrorInvalidValue;
-    if (p.items == 8) e = dist_half ? launch_row_k<8, true>(a, kind, p, s) : launch_row_k<8, false>(a, kind, p, s);
-    if (p.items == 16) e = dist_half ? launch_row_k<16, true>(a, kind, p, s) : launch_row_k<16, false>(a, kind, p, s);
+    if (use_row_persistent() && (!row_prefetch() || p.tpr * p.rpb <= (p.items <= 8 ? 1024 : 512))) {
+        const bool sup = kind == PASS_SUPPORT;
+        if (p.items == 8)
+            e = dist_half ? (sup ? launch_row_persist_t<8, true, PASS_SUPPORT>(a, p, s) : launch_row_persist_t<8, true, PASS_PLAIN>(a, p, s))
+                          : (sup ? launch_row_persist_t<8, false, PASS_SUPPORT>(a, p, s) : launch_row_persist_t<8, false, PASS_PLAIN>(a, p, s));
+        if (p.items == 16)
+            e = dist_half ? (sup ? launch_row_persist_t<16, true, PASS_SUPPORT>(a, p, s) : launch_row_persist_t<16, true, PASS_PLAIN>(a, p, s))
+                          : (sup ? launch_row_persist_t<16, false, PASS_SUPPORT>(a, p, s) : launch_row_persist_t<16, false, PASS_PLAIN>(a, p, s));
+    } else {
+        if (p.items == 8) e = dist_half ? launch_row_k<8, true>(a, kind, p, s) : launch_row_k<8, false>(a, kind, p, s);
+        if (p.items == 16) e = dist_half ? launch_row_k<16, true>(a, kind, p, s) : launch_row_k<16, false>(a, kind, p, s);
+    }
     prof_end(h, s);
     return e;
 }
 
 cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
+    ColPlan tp_probe;
+    const bool inject = injected_tma_skip_pending() && kind != PASS_SUPPORT_CONF && plan_cols_tma(a.H, &tp_probe);
+    if (!inject && use_col_split() && kind != PASS_SUPPORT_CONF && a.agg && a.carry && a.counters)
+        return launch_col_split(a, dist_half, kind, s);
     const int kid = kind == PASS_UPDATE ? KID_COL_UPDATE : kind == PASS_SUPPORT_CONF ? KID_COL_SUPPORT : KID_COL_PLAIN;
     const int flags = (dist_half ? kFlagDistHalf : 0) | (kind == PASS_UPDATE && a.t_dtype != DTS_F32 ? kFlagTarget16 : 0);
     const int h = prof_begin(kid, (long long)a.H * a.W, flags, s);
@@ -466,6 +853,23 @@ cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const Co
 }
 
 cudaError_t launch_col_dispatch(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
+    // a pending fault injection exercises the bounded waits of the TMA kernel
+    const bool inject = injected_tma_skip_pending();
+    if (!inject && use_col_split() && kind != PASS_SUPPORT_CONF && a.agg && a.carry && a.counters)
+        return launch_col_split(a, dist_half, kind, s);
+    ColPlan tp;
+    if ((inject || use_col_tma()) && kind != PASS_SUPPORT_CONF && plan_cols_tma(a.H, &tp)) {
+        const bool up = kind == PASS_UPDATE;
+        if (tp.items == 8)
+            return dist_half ? (up ? launch_col_tma_t<8, true, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<8, true, PASS_PLAIN>(a, tp, s))
+                             : (up ? launch_col_tma_t<8, false, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<8, false, PASS_PLAIN>(a, tp, s));
+        if (tp.items == 16)
+            return dist_half ? (up ? launch_col_tma_t<16, true, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<16, true, PASS_PLAIN>(a, tp, s))
+                             : (up ? launch_col_tma_t<16, false, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<16, false, PASS_PLAIN>(a, tp, s));
+        if (tp.items == 32)
+            return dist_half ? (up ? launch_col_tma_t<32, true, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<32, true, PASS_PLAIN>(a, tp, s))
+                             : (up ? launch_col_tma_t<32, false, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<32, false, PASS_PLAIN>(a, tp, s));
+    }
     if (p.items == 8) return dist_half ? launch_col_k<8, true>(a, kind, p, s) : launch_col_k<8, false>(a, kind, p, s);
     if (p.items == 16) return dist_half ? launch_col_k<16, true>(a, kind, p, s) : launch_col_k<16, false>(a, kind, p, s);
     if (p.items == 32) return dist_half ? launch_col_k<32, true>(a, kind, p, s) : launch_col_k<32, false>(a, kind, p, s);
@@ -515,8 +919,9 @@ bool plan_cols(int H, ColPlan* p) {
         p->cluster = 1;
         return true;
     }
-    // measured on the 2880 x 1988 stereo workload: 32 rows x 8 warps per CTA is fastest
-    static const int cand[][2] = {{32, 8}, {16, 16}, {32, 16}, {40, 16}};
+    // measured on the 2880 x 1988 stereo workload: 16 rows x 16 warps per CTA at 64 registers
+    // (two CTAs, 32 warps per SM) is fastest
+    static const int cand[][2] = {{16, 16}, {32, 8}, {32, 16}, {40, 16}};
     for (int limit : {8, 16}) {
         for (const auto& c : cand) {
             const int rows = c[0] * c[1];
@@ -530,6 +935,67 @@ bool plan_cols(int H, ColPlan* p) {
         }
     }
     return false;
+}
+
+// Alternative kernels kept for tuning (measured slower on the stereo workload, off by default):
+// DTS_ROW_PERSIST=1 persistent horizontal pass, DTS_COL_TMA=1 persistent TMA vertical pass.
+bool use_persistent() {
+    static const bool on = getenv("DTS_NO_PERSIST") == nullptr;
+    return on;
+}
+bool use_row_persistent() {
+    static const bool on = getenv("DTS_ROW_PERSIST") != nullptr;
+    return on;
+}
+bool use_col_tma() {
+    static const bool on = getenv("DTS_COL_TMA") != nullptr;
+    return on;
+}
+// split (two-kernel, cluster-free) vertical pass, measured slower than the cluster kernel on the
+// stereo workload; DTS_COL_SPLIT=1 selects it (tuning aid)
+bool use_col_split() {
+    static const bool on = getenv("DTS_COL_SPLIT") != nullptr;
+    return on;
+}
+
+// TMA vertical plan: tiles of R = items x warps rows (R <= 256, one TMA box), clusters of at most
+// 16 CTAs: columns up to 4096 rows.  DTS_TMA_COL_PLAN="items,warps" overrides (tuning aid).
+bool plan_cols_tma(int H, ColPlan* p) {
+    static const char* env = getenv("DTS_TMA_COL_PLAN");
+    int it = 16, nw = 8;
+    if (env) {
+        int a = 0, b = 0;
+        if (sscanf(env, "%d,%d", &a, &b) == 2 && (a == 8 || a == 16 || a == 32) && b >= 1 &&
+            b <= kTmaColMaxWarps) {
+            it = a;
+            nw = b;
+        }
+    } else if (H <= 64) {
+        it = 8;
+        nw = (H + 7) / 8;
+    } else if (H <= 128) {
+        it = 16;
+        nw = (H + 15) / 16;
+    }
+    if (nw > kTmaColMaxWarps) return false;
+    const int R = it * nw;
+    const int cs = (H + R - 1) / R;
+    if (cs > 16) {
+        if (env) return false;
+        // taller columns: the largest tile
+        it = 32;
+        nw = 8;
+        const int cs2 = (H + 255) / 256;
+        if (cs2 > 16) return false;
+        p->items = it;
+        p->warps = nw;
+        p->cluster = cs2;
+        return true;
+    }
+    p->items = it;
+    p->warps = nw;
+    p->cluster = cs;
+    return true;
 }
 
 cudaError_t prepare_kernels() {

@@ -84,6 +84,14 @@ struct PassArgs {
     int clamp_step;         // SUPPORT mode: step_i = min(step, 1 / (lambda + c_i))
     // support mode: S -> chat = c * s_flat / S (written to zout)
     float s_flat;
+    // device status word (bounded waits that give up write DTS_ERR_TIMEOUT here)
+    int* status;
+    // scratch of the split vertical pass (dts_vertical.cu): five aggregate planes and two carry
+    // planes of agg_plane floats each (row pitch agg_pitch), one ticket counter per 128 columns
+    float* agg;
+    float* carry;
+    unsigned* counters;
+    long long agg_pitch, agg_plane;
 };
 
 // One directional pass adjoint (see dts_backward.cu).
@@ -152,6 +160,7 @@ enum KernelId {
     KID_COL_BWD_UPDATE = 10,
     KID_GUIDE_GRAD = 11,
     KID_AXPY = 12,
+    KID_COL_AGG = 13,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
@@ -161,6 +170,13 @@ constexpr int kFlagTarget16 = 2;   // target stored in 16 bits
 int prof_begin(int kernel, long long pixels, int flags, cudaStream_t s);
 void prof_end(int handle, cudaStream_t s);
 
+// device status word of the current device (dts_api.cu)
+int* status_word();
+// one-shot fault injection for tests: the next TMA vertical pass skips its first tile load in
+// its first CTA, so that CTA's bounded wait gives up (dts_api.cu)
+bool take_injected_tma_skip();
+bool injected_tma_skip_pending();
+
 // launchers (dts_forward.cu); return cudaGetLastError() after the launch
 cudaError_t launch_distances(const DistArgs& a, cudaStream_t s);
 cudaError_t launch_copy_plane(const void* src, int src_dtype, long long src_pitch, float* dst, long long dst_pitch,
@@ -169,7 +185,16 @@ cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const Ro
 cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s);
 bool plan_rows(int W, RowPlan* p);
 bool plan_cols(int H, ColPlan* p);
+bool plan_cols_tma(int H, ColPlan* p);
+bool use_persistent();
+bool use_row_persistent();
+bool use_col_tma();
 cudaError_t prepare_kernels();
+
+// split vertical pass (dts_vertical.cu)
+void split_col_scratch(int H, int W, long long* agg_pitch, long long* agg_plane, int* nstrips128);
+cudaError_t launch_col_split(const PassArgs& a, int dist_half, int kind, cudaStream_t s);
+bool use_col_split();
 
 // backward launchers (dts_backward.cu)
 bool plan_rows_bwd(int W, RowPlan* p);

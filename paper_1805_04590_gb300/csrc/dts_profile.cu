@@ -103,6 +103,7 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_COL_BWD_UPDATE: return "col_bwd_kernel<update>";
         case KID_GUIDE_GRAD: return "guide_grad_kernel";
         case KID_AXPY: return "axpy_plane_kernel";
+        case KID_COL_AGG: return "col_agg_kernel";
         default: return "unknown";
     }
 }

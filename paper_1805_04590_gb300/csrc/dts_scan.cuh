@@ -180,7 +180,30 @@ struct ColShared {
     typename M::Suf cta_suf[32];
     typename M::Pre cl_pre[32];
     typename M::Suf cl_suf[32];
+    typename M::Pre rem_pre[16][32];  // totals of the other CTAs of the cluster, gathered in parallel
+    typename M::Suf rem_suf[16][32];
 };
+
+// Gather every peer's CTA totals (one DSMEM round, spread over the warps), then warp 0 folds
+// them from local shared memory into the cluster prefix and suffix of this CTA.
+template <class M, int NWMAX>
+__device__ __forceinline__ void gather_cluster_totals(cg::cluster_group& cluster, int rank, int CS, int lane,
+                                                      int warp, int NW, ColShared<M, NWMAX>& sh) {
+    for (int q = warp; q < CS; q += NW) {
+        if (q == rank) continue;
+        if (q < rank) sh.rem_pre[q][lane] = *cluster.map_shared_rank(&sh.cta_pre[lane], q);
+        else sh.rem_suf[q][lane] = *cluster.map_shared_rank(&sh.cta_suf[lane], q);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        typename M::Pre cp = M::pre_identity();
+        for (int q = 0; q < rank; ++q) cp = M::pre_compose(cp, sh.rem_pre[q][lane]);
+        typename M::Suf cs = M::suf_identity();
+        for (int q = rank + 1; q < CS; ++q) cs = M::suf_compose(cs, sh.rem_suf[q][lane]);
+        sh.cl_pre[lane] = cp;
+        sh.cl_suf[lane] = cs;
+    }
+}
 
 // Segments of a column: warp q of cluster CTA r is segment r*NW + q (lane = column).  Ends with
 // barrier.cluster.arrive: the caller must execute cluster_exit() before returning, after which
@@ -204,14 +227,7 @@ __device__ __forceinline__ void col_exchange(const typename M::Pre& own_pre, con
         if (warp == NW - 1) sh.cta_pre[lane] = M::pre_compose(wpre, own_pre);
         if (warp == 0) sh.cta_suf[lane] = M::suf_compose(own_suf, wsuf);
         cluster.sync();
-        if (warp == 0) {
-            typename M::Pre cp = M::pre_identity();
-            for (int q = 0; q < rank; ++q) cp = M::pre_compose(cp, *cluster.map_shared_rank(&sh.cta_pre[lane], q));
-            typename M::Suf cs = M::suf_identity();
-            for (int q = rank + 1; q < CS; ++q) cs = M::suf_compose(cs, *cluster.map_shared_rank(&sh.cta_suf[lane], q));
-            sh.cl_pre[lane] = cp;
-            sh.cl_suf[lane] = cs;
-        }
+        gather_cluster_totals<M, NWMAX>(cluster, rank, CS, lane, warp, NW, sh);
         __syncthreads();
         wpre = M::pre_compose(sh.cl_pre[lane], wpre);
         wsuf = M::suf_compose(wsuf, sh.cl_suf[lane]);
@@ -223,6 +239,83 @@ __device__ __forceinline__ void col_exchange(const typename M::Pre& own_pre, con
 }
 
 __device__ __forceinline__ void cluster_exit() { cg::this_cluster().barrier_wait(); }
+
+// The same exchange for a kernel that loops over several lines per cluster (persistent grid).
+// Before a CTA overwrites its totals it waits until every peer has finished reading the
+// previous iteration's (the arrive at the end of that iteration); `first` skips that wait.
+// After the last iteration the caller executes cluster_exit() if any iteration ran with CS > 1.
+template <class M, int NWMAX>
+__device__ __forceinline__ void col_exchange_iter(const typename M::Pre& own_pre, const typename M::Suf& own_suf,
+                                                  int lane, int warp, int NW, ColShared<M, NWMAX>& sh, bool first,
+                                                  typename M::Pre& pre, typename M::Suf& suf) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int CS = (int)cluster.num_blocks();
+    sh.pre[warp][lane] = own_pre;
+    sh.suf[warp][lane] = own_suf;
+    __syncthreads();
+    typename M::Pre wpre = M::pre_identity();
+    for (int q = 0; q < warp; ++q) wpre = M::pre_compose(wpre, sh.pre[q][lane]);
+    typename M::Suf wsuf = M::suf_identity();
+    for (int q = warp + 1; q < NW; ++q) wsuf = M::suf_compose(wsuf, sh.suf[q][lane]);
+    if (CS > 1) {
+        if (!first) cluster.barrier_wait();
+        if (warp == NW - 1) sh.cta_pre[lane] = M::pre_compose(wpre, own_pre);
+        if (warp == 0) sh.cta_suf[lane] = M::suf_compose(own_suf, wsuf);
+        cluster.sync();
+        gather_cluster_totals<M, NWMAX>(cluster, rank, CS, lane, warp, NW, sh);
+        __syncthreads();
+        wpre = M::pre_compose(sh.cl_pre[lane], wpre);
+        wsuf = M::suf_compose(wsuf, sh.cl_suf[lane]);
+        cluster.barrier_arrive();
+    }
+    pre = wpre;
+    suf = wsuf;
+}
+
+// ---------------------------------------------------------------- TMA and mbarriers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make the initialised barriers visible to the asynchronous (TMA) proxy
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity; gives up after `limit` clock cycles (false).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > limit) return false;
+    }
+    return true;
+}
+
+// 2-D tiled TMA load of the box at (x, y) (x in elements, a multiple of 16 bytes) into shared
+// memory, completing `bytes` on `bar`.  Rows or columns outside the tensor read as zero.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
 
 // ---------------------------------------------------------------- loads
 template <bool DHALF>
@@ -258,12 +351,12 @@ __device__ __forceinline__ void store4_f(float* base, long long idx, const float
 // Launch with programmatic stream serialization (unless disabled) and an optional cluster shape
 // (1, cluster_y, 1).
 template <typename... KArgs, typename... Args>
-cudaError_t launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, int cluster_y, cudaStream_t s,
-                      Args&&... args) {
+cudaError_t launch_ex_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, int cluster_y, size_t smem,
+                           cudaStream_t s, Args&&... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
     int n = 0;
@@ -282,6 +375,12 @@ cudaError_t launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, int clust
     cfg.attrs = attr;
     cfg.numAttrs = n;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, int cluster_y, cudaStream_t s,
+                      Args&&... args) {
+    return launch_ex_smem(kernel, grid, block, cluster_y, 0, s, std::forward<Args>(args)...);
 }
 
 }  // namespace scan

@@ -50,11 +50,14 @@ def test_workspace_size_layout():
     n0 = lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p), 0)
     pitch = 64
     plane = 40 * pitch * 4
-    assert n0 == 4 * plane  # dX, dY, working buffer, iterate
+    # split vertical pass: 5 aggregate + 2 carry planes of (W rounded to 128) x ceil(H/32) floats,
+    # and one ticket counter per 128 columns, each region 256-byte aligned
+    split = 5 * 128 * 2 * 4 + 2 * 128 * 2 * 4 + 256
+    assert n0 == 4 * plane + split  # dX, dY, working buffer, iterate
     n1 = lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p), 1)
-    assert n1 == (3 + 5 + 2 * 3 + 5) * plane  # + K checkpoints, 2N pass inputs, adjoint buffers
+    assert n1 == (3 + 5 + 2 * 3 + 5) * plane + split  # + K checkpoints, 2N pass inputs, adjoint buffers
     p16 = dts.Params(iterations=5, dist_dtype=dts.F16).c()
-    assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p16), 0) == 2 * (40 * pitch * 2) + 2 * plane
+    assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p16), 0) == 2 * (40 * pitch * 2) + 2 * plane + split
     bad = dts.Params(sigma_s=-1.0).c()
     assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(bad), 0) == 0
 
