@@ -277,6 +277,25 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
     pass_log2a(p->sigma_s, p->passes, k2);
     const int dh = p->dist_dtype == DTS_F16;
     float* u = reinterpret_cast<float*>(ws_at(ws, L.u));
+    const float* cplane = support ? reinterpret_cast<const float*>(ws_at(ws, L.chat)) : conf;
+    auto set_update = [&](PassArgs& a, const float* zk) {
+        a.zk = zk;
+        a.t = target;
+        a.t_dtype = tdt;
+        a.c = cplane;
+        a.c_pitched = support;
+        a.clamp_step = support;
+        a.lambda = p->lambda;
+        a.step = p->step;
+        a.update = p->update;
+        const int tsz = tdt == DTS_F32 ? 4 : 2;
+        a.tc_vec = (W % 4 == 0) && ((uintptr_t)target % (4 * tsz) == 0) && ((uintptr_t)conf % 16 == 0);
+    };
+    // The data-term update of iteration k is applied by the first horizontal pass of iteration
+    // k + 1 (reading z_k, zbar, t and c as vectors along rows and writing z_{k+1}); after the
+    // last iteration a standalone kernel applies it.  Rows too long for that kernel keep the
+    // update in the last vertical pass.
+    const bool row_update = row_update_fits(pl.rows);
     for (int k = 0; k < K; ++k) {
         float* zin = zslot(k);
         for (int i = 0; i < p->passes; ++i) {
@@ -285,24 +304,24 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
             r.dst = u;
             r.d = ws_at(ws, L.dX);
             r.k2 = k2[i];
-            if ((st = cuda_status(launch_row_pass(r, dh, PASS_PLAIN, pl.rows, s)))) return st;
+            int rkind = PASS_PLAIN;
+            if (row_update && i == 0 && k > 0) {
+                rkind = PASS_UPDATE_ROW;
+                r.src = u;  // zbar of iteration k - 1
+                set_update(r, zslot(k - 1));
+                r.zout = zin;  // z_k
+                r.zout_pitch = L.pitch;
+            }
+            if ((st = cuda_status(launch_row_pass(r, dh, rkind, pl.rows, s)))) return st;
             PassArgs c = base_pass(g, L);
             c.src = u;
             c.dst = u;
             c.d = ws_at(ws, L.dY);
             c.k2 = k2[i];
             int kind = PASS_PLAIN;
-            if (i == p->passes - 1) {
+            if (!row_update && i == p->passes - 1) {
                 kind = PASS_UPDATE;
-                c.zk = zin;
-                c.t = target;
-                c.t_dtype = tdt;
-                c.c = support ? reinterpret_cast<const float*>(ws_at(ws, L.chat)) : conf;
-                c.c_pitched = support;
-                c.clamp_step = support;
-                c.lambda = p->lambda;
-                c.step = p->step;
-                c.update = p->update;
+                set_update(c, zin);
                 if (k == K - 1) {
                     c.zout = z_out;
                     c.zout_pitch = W;
@@ -313,6 +332,14 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
             }
             if ((st = cuda_status(launch_col_pass(c, dh, kind, pl.cols, s)))) return st;
         }
+    }
+    if (row_update) {
+        PassArgs a = base_pass(g, L);
+        a.src = u;
+        set_update(a, zslot(K - 1));
+        a.zout = z_out;
+        a.zout_pitch = W;
+        if ((st = cuda_status(launch_update(a, s)))) return st;
     }
     return DTS_OK;
 }

@@ -194,8 +194,36 @@ __global__ void __launch_bounds__(256) copy_plane_kernel(const void* src, int sr
 // of a row owns positions [t*ITEMS, t*ITEMS + ITEMS).  The segments of a row exchange their
 // aggregates through warp shuffles and one shared-memory round.
 // KIND: PASS_PLAIN (CoupledMode on the plane) or PASS_SUPPORT (SupportMode on the constant 1).
+// KIND PASS_UPDATE_ROW: the first pass of an iteration also applies the previous iteration's
+// data-term update: it reads zbar (a.src), z_k (a.zk), t and c, writes z_{k+1} to a.zout and
+// filters z_{k+1}.
+template <int ITEMS, int KIND>
+constexpr int row_max_threads() {
+    return KIND == PASS_UPDATE_ROW ? 512 : 1024;
+}
+
+// four consecutive target / confidence values at dense index i (16-byte vectors when allowed)
+__device__ __forceinline__ void load4_t(const PassArgs& a, long long i, bool vec, float* out) {
+    if (vec) {
+        if (a.t_dtype == DTS_F32) {
+            load4_f(static_cast<const float*>(a.t), i, out);
+        } else {
+            const uint2 v = *reinterpret_cast<const uint2*>(static_cast<const unsigned short*>(a.t) + i);
+            const unsigned short h[4] = {(unsigned short)(v.x & 0xffff), (unsigned short)(v.x >> 16),
+                                         (unsigned short)(v.y & 0xffff), (unsigned short)(v.y >> 16)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                out[k] = a.t_dtype == DTS_BF16 ? __bfloat162float(__ushort_as_bfloat16(h[k]))
+                                               : __half2float(__ushort_as_half(h[k]));
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = load_any(a.t, i + k, a.t_dtype);
+    }
+}
+
 template <int ITEMS, bool DHALF, int KIND>
-__global__ void __launch_bounds__(1024) row_pass_kernel(PassArgs a, int tpr) {
+__global__ void __launch_bounds__(row_max_threads<ITEMS, KIND>()) row_pass_kernel(PassArgs a, int tpr) {
     static_assert(ITEMS % 4 == 0, "ITEMS must be a multiple of 4");
     using M = typename std::conditional<KIND == PASS_SUPPORT, SupportMode, CoupledMode>::type;
     __shared__ typename M::Pre s_pre[32];
@@ -227,6 +255,39 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(PassArgs a, int tpr) {
                 load4_f(a.src, base + 4 * q, &x[4 * q]);
             }
             load4_d<DHALF>(a.d, base + 4 * q, &w[4 * q]);
+        }
+        if constexpr (KIND == PASS_UPDATE_ROW) {
+            // z_{k+1} from z_k, zbar (already in x), t and c; padding positions stay 0
+            const long long di = (long long)row * a.W + e0;
+            const bool full_seg = e0 + ITEMS <= a.W;
+#pragma unroll
+            for (int q = 0; q < ITEMS / 4; ++q) {
+                float zk[4], tt[4], cc[4];
+                load4_f(a.zk, base + 4 * q, zk);
+                if (full_seg) {
+                    load4_t(a, di + 4 * q, a.tc_vec, tt);
+                    if (a.c_pitched) load4_f(a.c, base + 4 * q, cc);
+                    else if (a.tc_vec) load4_f(a.c, di + 4 * q, cc);
+                    else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) cc[k] = a.c[di + 4 * q + k];
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const bool ok = e0 + 4 * q + k < a.W;
+                        tt[k] = ok ? load_any(a.t, di + 4 * q + k, a.t_dtype) : 0.f;
+                        cc[k] = ok ? (a.c_pitched ? a.c[base + 4 * q + k] : a.c[di + 4 * q + k]) : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float zn = dts_update_value(zk[k], x[4 * q + k], tt[k], cc[k], a.lambda, a.step, a.update,
+                                                      a.clamp_step);
+                    x[4 * q + k] = (e0 + 4 * q + k < a.W) ? zn : 0.f;
+                }
+                store4_f(a.zout, base + 4 * q, &x[4 * q]);
+            }
         }
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) w[j] = ex2(a.k2 * w[j]);
@@ -633,6 +694,8 @@ cudaError_t launch_row_k(const PassArgs& a, int kind, const RowPlan& p, cudaStre
     const dim3 grid((unsigned)((a.H + p.rpb - 1) / p.rpb));
     const dim3 block((unsigned)(p.tpr * p.rpb));
     if (kind == PASS_SUPPORT) return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_SUPPORT>, grid, block, 0, s, a, p.tpr);
+    if (kind == PASS_UPDATE_ROW)
+        return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_UPDATE_ROW>, grid, block, 0, s, a, p.tpr);
     return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_PLAIN>, grid, block, 0, s, a, p.tpr);
 }
 
@@ -786,7 +849,31 @@ cudaError_t launch_row_persist_t(const PassArgs& a, const RowPlan& p, cudaStream
     return launch_ex(kernel, dim3((unsigned)grid), dim3((unsigned)block), 0, s, a, p.tpr, ngroups);
 }
 
+// z_out[y][x] (pitch zout_pitch) = update(z_k, zbar = src, t, c) for every pixel
+__global__ void __launch_bounds__(256) update_kernel(PassArgs a) {
+    wait_predecessor();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= a.W || y >= a.H) return;
+    const long long idx = (long long)y * a.pitch + x;
+    const long long di = (long long)y * a.W + x;
+    const float c = a.c_pitched ? a.c[idx] : a.c[di];
+    a.zout[(long long)y * a.zout_pitch + x] =
+        dts_update_value(a.zk[idx], a.src[idx], load_any(a.t, di, a.t_dtype), c, a.lambda, a.step, a.update,
+                         a.clamp_step);
+}
+
 }  // namespace
+
+bool row_update_fits(const RowPlan& p) { return p.tpr * p.rpb <= 512; }
+
+cudaError_t launch_update(const PassArgs& a, cudaStream_t s) {
+    const int h = prof_begin(KID_UPDATE, (long long)a.H * a.W, a.t_dtype != DTS_F32 ? kFlagTarget16 : 0, s);
+    const dim3 grid((unsigned)((a.W + 255) / 256), (unsigned)a.H);
+    const cudaError_t e = launch_ex(update_kernel, grid, dim3(256), 0, s, a);
+    prof_end(h, s);
+    return e;
+}
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_col_dispatch(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s);
@@ -820,10 +907,11 @@ cudaError_t launch_copy_plane(const void* src, int src_dtype, long long src_pitc
 }
 
 cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const RowPlan& p, cudaStream_t s) {
-    const int h = prof_begin(kind == PASS_SUPPORT ? KID_ROW_SUPPORT : KID_ROW_PLAIN, (long long)a.H * a.W,
-                             dist_half ? kFlagDistHalf : 0, s);
+    const int h = prof_begin(kind == PASS_SUPPORT ? KID_ROW_SUPPORT : kind == PASS_UPDATE_ROW ? KID_ROW_UPDATE : KID_ROW_PLAIN,
+                             (long long)a.H * a.W,
+                             (dist_half ? kFlagDistHalf : 0) | (kind == PASS_UPDATE_ROW && a.t_dtype != DTS_F32 ? kFlagTarget16 : 0), s);
     cudaError_t e = cudaErrorInvalidValue;
-    if (use_row_persistent() && (!row_prefetch() || p.tpr * p.rpb <= (p.items <= 8 ? 1024 : 512))) {
+    if (kind != PASS_UPDATE_ROW && use_row_persistent() && (!row_prefetch() || p.tpr * p.rpb <= (p.items <= 8 ? 1024 : 512))) {
         const bool sup = kind == PASS_SUPPORT;
         if (p.items == 8)
             e = dist_half ? (sup ? launch_row_persist_t<8, true, PASS_SUPPORT>(a, p, s) : launch_row_persist_t<8, true, PASS_PLAIN>(a, p, s))

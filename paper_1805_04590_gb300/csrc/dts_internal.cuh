@@ -46,6 +46,22 @@ __device__ __forceinline__ float load_any(const void* p, long long i, int dtype)
     return static_cast<const float*>(p)[i];
 }
 
+// One data-term update of the solver at a pixel: z = z_k, zb = zbar = A z_k, t, c (confidence,
+// or the support-weighted confidence).
+//   GD (Eq. 3):      z - step (lambda (z - zb) + c (z - t)), with the step limited to
+//                    1 / (lambda + c) when clamp is set
+//   Jacobi (Eq. 4):  (lambda zb + c t) / (lambda + c); z is kept where lambda + c = 0
+__device__ __forceinline__ float dts_update_value(float z, float zb, float t, float c, float lambda, float step,
+                                                  int update, int clamp) {
+    if (update == DTS_UPDATE_JACOBI) {
+        const float den = lambda + c;
+        return den != 0.f ? (lambda * zb + c * t) / den : z;
+    }
+    float eta = step;
+    if (clamp && lambda + c > 0.f) eta = fminf(eta, 1.f / (lambda + c));
+    return z - eta * (lambda * (z - zb) + c * (z - t));
+}
+
 // ---------------------------------------------------------------- kernel arguments
 struct DistArgs {
     const void* guide;
@@ -82,6 +98,7 @@ struct PassArgs {
     float lambda, step;
     int update;             // DTS_UPDATE_GD / DTS_UPDATE_JACOBI
     int clamp_step;         // SUPPORT mode: step_i = min(step, 1 / (lambda + c_i))
+    int tc_vec;             // t and c rows may be read with 16-byte vectors (W % 4 == 0, aligned)
     // support mode: S -> chat = c * s_flat / S (written to zout)
     float s_flat;
     // device status word (bounded waits that give up write DTS_ERR_TIMEOUT here)
@@ -143,7 +160,7 @@ struct RowPlan {
     int rpb;     // rows per CTA
 };
 
-enum PassKind { PASS_PLAIN = 0, PASS_UPDATE = 1, PASS_SUPPORT = 2, PASS_SUPPORT_CONF = 3 };
+enum PassKind { PASS_PLAIN = 0, PASS_UPDATE = 1, PASS_SUPPORT = 2, PASS_SUPPORT_CONF = 3, PASS_UPDATE_ROW = 4 };
 
 // Kernel ids reported by the per-launch timer (dts_profile / dts_kernel_name).
 enum KernelId {
@@ -161,6 +178,8 @@ enum KernelId {
     KID_GUIDE_GRAD = 11,
     KID_AXPY = 12,
     KID_COL_AGG = 13,
+    KID_ROW_UPDATE = 14,
+    KID_UPDATE = 15,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
@@ -184,6 +203,8 @@ cudaError_t launch_copy_plane(const void* src, int src_dtype, long long src_pitc
 cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const RowPlan& p, cudaStream_t s);
 cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s);
 bool plan_rows(int W, RowPlan* p);
+bool row_update_fits(const RowPlan& p);
+cudaError_t launch_update(const PassArgs& a, cudaStream_t s);
 bool plan_cols(int H, ColPlan* p);
 bool plan_cols_tma(int H, ColPlan* p);
 bool use_persistent();

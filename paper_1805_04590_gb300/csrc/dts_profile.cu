@@ -104,6 +104,8 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_GUIDE_GRAD: return "guide_grad_kernel";
         case KID_AXPY: return "axpy_plane_kernel";
         case KID_COL_AGG: return "col_agg_kernel";
+        case KID_ROW_UPDATE: return "row_pass_kernel<update>";
+        case KID_UPDATE: return "update_kernel";
         default: return "unknown";
     }
 }
