@@ -377,8 +377,10 @@ bool plan_rows_bwd(int W, RowPlan* p) {
 bool plan_cols_bwd(int H, ColPlan* p) {
     static const int cand[][2] = {{8, 8}, {8, 16}, {16, 8}};
     if (H <= 128) {
+        int nw = 1;
+        while (nw * 8 < H) nw <<= 1;  // a power of two (the CTA scan works in lane groups)
         p->items = 8;
-        p->warps = (H + 7) / 8;
+        p->warps = nw;
         p->cluster = 1;
         return true;
     }

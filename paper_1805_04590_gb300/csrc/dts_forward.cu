@@ -369,23 +369,28 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
         }
     }
 
+    using DT = typename std::conditional<DHALF, __half, float>::type;
     float x[ITEMS], w[ITEMS];
     const bool full = col_ok && row0 + ITEMS <= a.H;
     {
-        const float* src = a.src + (long long)row0 * P + col;
-        const long long d0 = (long long)row0 * P + col;
+        const float* ps = a.src + (long long)row0 * P + col;
+        const DT* pd = static_cast<const DT*>(a.d) + (long long)row0 * P + col;
         if (full) {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) {
-                x[j] = src[j * P];
-                w[j] = load1_d<DHALF>(a.d, d0 + j * P);
+                x[j] = *ps;
+                w[j] = to_f32<DT>(*pd);
+                ps += P;
+                pd += P;
             }
         } else {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) {
                 const bool ok = col_ok && row0 + j < a.H;
-                x[j] = ok ? src[j * P] : 0.f;
-                w[j] = ok ? load1_d<DHALF>(a.d, d0 + j * P) : 0.f;
+                x[j] = ok ? *ps : 0.f;
+                w[j] = ok ? to_f32<DT>(*pd) : 0.f;
+                ps += P;
+                pd += P;
             }
         }
     }
@@ -411,6 +416,24 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
     M::apply(x, w, wn, own_pre, pre.B, suf);
 
     // ---- epilogue
+    if constexpr (KIND == PASS_PLAIN) {
+        float* pdst = a.dst + (long long)row0 * a.dst_pitch + col;
+        if (full) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                *pdst = x[j];
+                pdst += a.dst_pitch;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if (col_ok && row0 + j < a.H) *pdst = x[j];
+                pdst += a.dst_pitch;
+            }
+        }
+        cluster_exit();
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int r = row0 + j;
@@ -991,7 +1014,7 @@ bool plan_cols(int H, ColPlan* p) {
     if (env) {
         int it = 0, nw = 0;
         if (sscanf(env, "%d,%d", &it, &nw) == 2 && (it == 8 || it == 16 || it == 32 || it == 40) && nw >= 1 &&
-            nw * 32 <= (it <= 8 ? 1024 : 512)) {
+            (nw & (nw - 1)) == 0 && nw * 32 <= (it <= 8 ? 1024 : 512)) {
             const int cs = (H + it * nw - 1) / (it * nw);
             if (cs <= 16) {
                 p->items = it;
@@ -1002,8 +1025,10 @@ bool plan_cols(int H, ColPlan* p) {
         }
     }
     if (H <= 256) {
+        int nw = 1;
+        while (nw * 8 < H) nw <<= 1;  // a power of two (the CTA scan works in lane groups)
         p->items = 8;
-        p->warps = (H + 7) / 8;
+        p->warps = nw;
         p->cluster = 1;
         return true;
     }

@@ -122,6 +122,28 @@ __device__ __forceinline__ T shfl_down_t(const T& v, int off) {
     return r;
 }
 
+template <typename T>
+__device__ __forceinline__ T shfl_up_w(const T& v, int off, int width) {
+    constexpr int n = sizeof(T) / 4;
+    T r;
+    const float* s = reinterpret_cast<const float*>(&v);
+    float* d = reinterpret_cast<float*>(&r);
+#pragma unroll
+    for (int i = 0; i < n; ++i) d[i] = __shfl_up_sync(kFull, s[i], off, width);
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_down_w(const T& v, int off, int width) {
+    constexpr int n = sizeof(T) / 4;
+    T r;
+    const float* s = reinterpret_cast<const float*>(&v);
+    float* d = reinterpret_cast<float*>(&r);
+#pragma unroll
+    for (int i = 0; i < n; ++i) d[i] = __shfl_down_sync(kFull, s[i], off, width);
+    return r;
+}
+
 // ---------------------------------------------------------------- exchanges
 template <class M>
 __device__ __forceinline__ typename M::Pre warp_scan_pre(typename M::Pre v, int lane) {
@@ -174,8 +196,9 @@ __device__ __forceinline__ void row_exchange(const typename M::Pre& own_pre, con
 // Shared state of a column exchange: NWMAX warps per CTA.
 template <class M, int NWMAX>
 struct ColShared {
-    typename M::Pre pre[NWMAX][32];
-    typename M::Suf suf[NWMAX][32];
+    // rows padded to 33 entries: the CTA scan reads a column across the warps' rows
+    typename M::Pre pre[NWMAX][33];
+    typename M::Suf suf[NWMAX][33];
     typename M::Pre cta_pre[32];
     typename M::Suf cta_suf[32];
     typename M::Pre cl_pre[32];
@@ -208,6 +231,38 @@ __device__ __forceinline__ void gather_cluster_totals(cg::cluster_group& cluster
 // Segments of a column: warp q of cluster CTA r is segment r*NW + q (lane = column).  Ends with
 // barrier.cluster.arrive: the caller must execute cluster_exit() before returning, after which
 // no CTA of the cluster reads another's shared memory.
+// Exclusive prefix / suffix over the NW warps of a CTA for each of the 32 columns, in parallel:
+// with NW a power of two, warp q scans columns [q*32/NW, (q+1)*32/NW), NW lanes per column, in
+// log2(NW) shuffle rounds, and writes the exclusive results back in place; the CTA totals go to
+// cta_pre / cta_suf.  Ends with __syncthreads.
+template <class M, int NWMAX>
+__device__ __forceinline__ void cta_scan(int lane, int warp, int NW, ColShared<M, NWMAX>& sh) {
+    const int q = lane & (NW - 1);         // the segment (warp) this lane stands for
+    const int cw = warp * (32 / NW) + lane / NW;  // the column it scans
+    typename M::Pre p = sh.pre[q][cw];
+    typename M::Suf f = sh.suf[q][cw];
+    for (int off = 1; off < NW; off <<= 1) {
+        const typename M::Pre op = shfl_up_w(p, off, NW);
+        const typename M::Suf of = shfl_down_w(f, off, NW);
+        if (q >= off) p = M::pre_compose(op, p);
+        if (q + off < NW) f = M::suf_compose(f, of);
+    }
+    if (q == NW - 1) sh.cta_pre[cw] = p;
+    if (q == 0) sh.cta_suf[cw] = f;
+    typename M::Pre pe = shfl_up_w(p, 1, NW);
+    typename M::Suf fe = shfl_down_w(f, 1, NW);
+    if (q == 0) pe = M::pre_identity();
+    if (q == NW - 1) fe = M::suf_identity();
+    sh.pre[q][cw] = pe;
+    sh.suf[q][cw] = fe;
+    __syncthreads();
+}
+
+// Segments of a column: warp q of cluster CTA r is segment r*NW + q (lane = column).  Each thread
+// folds the other warps' aggregates of its column from shared memory (measured faster than the
+// shuffle scan of cta_scan on the stereo workload).  Ends with barrier.cluster.arrive: the caller
+// must execute cluster_exit() before returning, after which no CTA of the cluster reads another's
+// shared memory.
 template <class M, int NWMAX>
 __device__ __forceinline__ void col_exchange(const typename M::Pre& own_pre, const typename M::Suf& own_suf,
                                              int lane, int warp, int NW, ColShared<M, NWMAX>& sh,
