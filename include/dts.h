@@ -158,6 +158,20 @@ int dts_solve_noalloc(const dts_guide* guide, const void* target, int target_dty
 /* Size in bytes of the scratch array dts_solve_noalloc uses. */
 size_t dts_noalloc_max_workspace(void);
 
+/* Workspace bytes for dts_solve_batched over these n guides (0 on invalid arguments). */
+size_t dts_batched_workspace_size(int n, const dts_guide* guides, const dts_params* params);
+
+/* n independent solves of uneven sizes (the same parameters) as ONE CUDA graph launch on `stream`:
+ * each image's launch sequence is captured on a few internal streams forked from one origin, so
+ * small images run side by side; the instantiated graph is cached per argument set (pointers,
+ * shapes, parameters) and later calls with the same arguments replay it.  If `stream` is being
+ * captured by the caller, the launches join the caller's graph instead.  guides, targets, confs
+ * and z_out are HOST arrays of n entries (device pointers, as in dts_solve; target_dtype shared);
+ * z_init is the target; save_checkpoints must be 0.  The workspace holds one slice per image. */
+int dts_solve_batched(int n, const dts_guide* guides, const void* const* targets, int target_dtype,
+                      const float* const* confs, const dts_params* params, float* const* z_out, void* ws,
+                      size_t ws_bytes, dts_stream stream);
+
 /* Synchronises `stream`, then returns and clears the device-side status word of
  * the current device (DTS_OK, or e.g. DTS_ERR_TIMEOUT), or DTS_ERR_CUDA if the
  * synchronisation itself failed. */

@@ -5,7 +5,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "dts_internal.cuh"
 
@@ -449,6 +451,174 @@ extern "C" int dts_solve(const dts_guide* guide, const void* target, int target_
         return DTS_ERR_WORKSPACE;
     if ((st = ensure_prepared())) return st;
     return solve_forward(guide, target, target_dtype, conf, z_init, params, z_out, ws, L, pl, (cudaStream_t)stream);
+}
+
+
+// ---------------------------------------------------------------- batched solve
+// Many images of uneven sizes as one CUDA graph: the per-image launch sequences are captured on
+// a few internal streams forked from one origin (so small images run side by side), the graph is
+// instantiated once per argument set and replayed with a single cudaGraphLaunch.
+namespace dts {
+namespace {
+
+constexpr int kBatchStreams = 8;
+
+struct BatchResources {
+    cudaStream_t capture = nullptr;
+    cudaStream_t side[kBatchStreams] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kBatchStreams] = {};
+    bool ready = false;
+};
+
+struct BatchGraph {
+    std::vector<unsigned long long> key;
+    cudaGraphExec_t exec = nullptr;
+};
+
+std::mutex g_batch_mutex;
+BatchResources g_batch_res[kMaxDevices];
+std::vector<BatchGraph> g_batch_graphs[kMaxDevices];
+constexpr size_t kBatchGraphCache = 8;
+
+int batch_resources(int dev, BatchResources** out) {
+    BatchResources& r = g_batch_res[dev];
+    if (!r.ready) {
+        if (cudaStreamCreateWithFlags(&r.capture, cudaStreamNonBlocking) != cudaSuccess) return DTS_ERR_CUDA;
+        for (int j = 0; j < kBatchStreams; ++j)
+            if (cudaStreamCreateWithFlags(&r.side[j], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&r.join[j], cudaEventDisableTiming) != cudaSuccess)
+                return DTS_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming) != cudaSuccess) return DTS_ERR_CUDA;
+        r.ready = true;
+    }
+    *out = &r;
+    return DTS_OK;
+}
+
+size_t batch_slice(const dts_guide& g, const dts_params* p) {
+    return align_up(make_layout(g.H, g.W, p, 0).fwd_end, kPlaneAlign);
+}
+
+// Issues every image's solve on the side streams, forked from and joined back into `origin`.
+int issue_batch(int n, const dts_guide* guides, const void* const* targets, int tdt, const float* const* confs,
+                const dts_params* p, float* const* z_out, void* ws, BatchResources& r, cudaStream_t origin) {
+    if (cudaEventRecord(r.fork, origin) != cudaSuccess) return DTS_ERR_CUDA;
+    for (int j = 0; j < kBatchStreams; ++j)
+        if (cudaStreamWaitEvent(r.side[j], r.fork, 0) != cudaSuccess) return DTS_ERR_CUDA;
+    // largest images first, each onto the least loaded stream
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long long)guides[a].H * guides[a].W > (long long)guides[b].H * guides[b].W;
+    });
+    std::vector<size_t> offset(n);
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        offset[i] = off;
+        off += batch_slice(guides[i], p);
+    }
+    long long load[kBatchStreams] = {};
+    for (int i : order) {
+        int j = 0;
+        for (int q = 1; q < kBatchStreams; ++q)
+            if (load[q] < load[j]) j = q;
+        load[j] += (long long)guides[i].H * guides[i].W;
+        Plans pl;
+        int st = make_plans(guides[i].H, guides[i].W, &pl);
+        if (st) return st;
+        const Layout L = make_layout(guides[i].H, guides[i].W, p, 0);
+        st = solve_forward(&guides[i], targets[i], tdt, confs[i], nullptr, p, z_out[i], ws_at(ws, offset[i]), L, pl,
+                           r.side[j]);
+        if (st) return st;
+    }
+    for (int j = 0; j < kBatchStreams; ++j) {
+        if (cudaEventRecord(r.join[j], r.side[j]) != cudaSuccess) return DTS_ERR_CUDA;
+        if (cudaStreamWaitEvent(origin, r.join[j], 0) != cudaSuccess) return DTS_ERR_CUDA;
+    }
+    return DTS_OK;
+}
+
+}  // namespace
+}  // namespace dts
+
+extern "C" size_t dts_batched_workspace_size(int n, const dts_guide* guides, const dts_params* params) {
+    if (n < 1 || !guides || check_params(params)) return 0;
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        if (check_guide(&guides[i])) return 0;
+        total += batch_slice(guides[i], params);
+    }
+    return total;
+}
+
+extern "C" int dts_solve_batched(int n, const dts_guide* guides, const void* const* targets, int target_dtype,
+                                 const float* const* confs, const dts_params* params, float* const* z_out, void* ws,
+                                 size_t ws_bytes, dts_stream stream) {
+    if (n < 1 || !guides || !targets || !confs || !z_out || !valid_dtype(target_dtype)) return DTS_ERR_INVALID_ARG;
+    int st = check_params(params);
+    if (st) return st;
+    if (params->save_checkpoints) return DTS_ERR_UNSUPPORTED;
+    for (int i = 0; i < n; ++i) {
+        if ((st = check_guide(&guides[i]))) return st;
+        if (!targets[i] || !confs[i] || !z_out[i]) return DTS_ERR_INVALID_ARG;
+        Plans pl;
+        if ((st = make_plans(guides[i].H, guides[i].W, &pl))) return st;
+    }
+    const size_t need = dts_batched_workspace_size(n, guides, params);
+    if (params->iterations > 0 && (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < need))
+        return DTS_ERR_WORKSPACE;
+    if ((st = ensure_prepared())) return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DTS_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    BatchResources* r = nullptr;
+    if ((st = batch_resources(dev, &r))) return st;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return DTS_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone)  // the caller is capturing: become part of its graph
+        return issue_batch(n, guides, targets, target_dtype, confs, params, z_out, ws, *r, s);
+    // key: every pointer, shape and parameter that the captured launches bake in
+    std::vector<unsigned long long> key;
+    key.push_back((unsigned long long)n);
+    key.push_back((unsigned long long)(uintptr_t)ws);
+    key.push_back((unsigned long long)target_dtype);
+    {
+        unsigned long long pw[(sizeof(dts_params) + 7) / 8] = {};
+        memcpy(pw, params, sizeof(dts_params));
+        for (unsigned long long v : pw) key.push_back(v);
+    }
+    for (int i = 0; i < n; ++i) {
+        const dts_guide& g = guides[i];
+        key.insert(key.end(), {(unsigned long long)g.C, (unsigned long long)g.H, (unsigned long long)g.W,
+                               (unsigned long long)g.dtype, (unsigned long long)(uintptr_t)g.data,
+                               (unsigned long long)g.ch_stride, (unsigned long long)g.row_stride,
+                               (unsigned long long)(uintptr_t)targets[i], (unsigned long long)(uintptr_t)confs[i],
+                               (unsigned long long)(uintptr_t)z_out[i]});
+    }
+    auto& cache = g_batch_graphs[dev];
+    for (auto& bg : cache)
+        if (bg.key == key) return cudaGraphLaunch(bg.exec, s) == cudaSuccess ? DTS_OK : DTS_ERR_CUDA;
+    if (cudaStreamBeginCapture(r->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DTS_ERR_CUDA;
+    st = issue_batch(n, guides, targets, target_dtype, confs, params, z_out, ws, *r, r->capture);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(r->capture, &graph);
+    if (st) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (ec != cudaSuccess || !graph) return DTS_ERR_CUDA;
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return DTS_ERR_CUDA;
+    if (cache.size() >= kBatchGraphCache) {
+        cudaGraphExecDestroy(cache.front().exec);
+        cache.erase(cache.begin());
+    }
+    cache.push_back(BatchGraph{key, exec});
+    return cudaGraphLaunch(exec, s) == cudaSuccess ? DTS_OK : DTS_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------- solve without allocation

@@ -47,6 +47,8 @@ void recycle_all() {
 int prof_begin(int kernel, long long pixels, int flags, cudaStream_t s) {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_enabled || g_records.size() >= kMaxRecords) return -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return -1;  // not in graphs
     Record r = {kernel, pixels, flags, take_event(), take_event()};
     if (!r.start || !r.stop) return -1;
     cudaEventRecord(r.start, s);

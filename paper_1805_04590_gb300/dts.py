@@ -69,7 +69,8 @@ class Params:
 _lib = None
 EXPORTS = ("dts_status_string", "dts_version", "dts_workspace_size", "dts_domain_transform", "dts_filter",
            "dts_solve", "dts_solve_backward", "dts_last_status", "dts_profile", "dts_profile_read",
-           "dts_kernel_name", "dts_solve_noalloc", "dts_noalloc_max_workspace")
+           "dts_kernel_name", "dts_solve_noalloc", "dts_noalloc_max_workspace", "dts_batched_workspace_size",
+           "dts_solve_batched", "dts_debug_inject")
 
 
 def library_path() -> str:
@@ -100,13 +101,17 @@ def load(build_if_missing: bool = True):
     lib.dts_solve_backward.argtypes = [P(CGuide), vp, i, vp, vp, P(CParams), vp, sz, vp, vp, vp, vp, vp, vp]
     lib.dts_last_status.argtypes = [vp]
     lib.dts_solve_noalloc.argtypes = [P(CGuide), vp, i, vp, vp, P(CParams), vp, vp]
+    lib.dts_batched_workspace_size.argtypes = [i, P(CGuide), P(CParams)]
+    lib.dts_batched_workspace_size.restype = sz
+    lib.dts_solve_batched.argtypes = [i, P(CGuide), P(vp), i, P(vp), P(CParams), P(vp), vp, sz, vp]
+    lib.dts_debug_inject.argtypes = [i]
     lib.dts_noalloc_max_workspace.restype = sz
     lib.dts_profile.argtypes = [i]
     lib.dts_profile_read.argtypes = [i, P(ctypes.c_int), P(ctypes.c_longlong), P(ctypes.c_int), P(ctypes.c_float)]
     lib.dts_kernel_name.argtypes = [i]
     lib.dts_kernel_name.restype = ctypes.c_char_p
     for name in ("dts_domain_transform", "dts_filter", "dts_solve", "dts_solve_backward", "dts_last_status",
-                 "dts_profile", "dts_profile_read", "dts_solve_noalloc"):
+                 "dts_profile", "dts_profile_read", "dts_solve_noalloc", "dts_solve_batched", "dts_debug_inject"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -208,6 +213,39 @@ def dts_solve(guide: torch.Tensor, target: torch.Tensor, conf: torch.Tensor, par
                             _ptr(z_init), ctypes.byref(p), out.data_ptr(), ws.data_ptr(), ws.numel(),
                             _stream(stream)), "dts_solve")
     return out
+
+
+def batched_workspace(guides, params: Params) -> torch.Tensor:
+    """Workspace tensor for dts_solve_batched over these guides."""
+    arr = (CGuide * len(guides))(*[guide_desc(g) for g in guides])
+    p = params.c()
+    n = load().dts_batched_workspace_size(len(guides), arr, ctypes.byref(p))
+    if n == 0:
+        raise DTSError(1, "dts_batched_workspace_size")
+    return torch.empty(n, dtype=torch.uint8, device=guides[0].device)
+
+
+def dts_solve_batched(guides, targets, confs, params: Params, outs=None, ws: Optional[torch.Tensor] = None,
+                      stream=None):
+    """Solves of uneven sizes (lists of CUDA tensors, same parameters) as one CUDA graph launch."""
+    n = len(guides)
+    if not (len(targets) == len(confs) == n) or n == 0:
+        raise ValueError("guides, targets and confs must be non-empty lists of equal length")
+    dt = targets[0].dtype
+    for t, c in zip(targets, confs):
+        _need_cuda(t, c)
+        _dense(t, "target", (dt,))
+        _dense(c, "conf")
+    outs = [torch.empty(t.shape, dtype=torch.float32, device=t.device) for t in targets] if outs is None else outs
+    garr = (CGuide * n)(*[guide_desc(g) for g in guides])
+    tarr = (ctypes.c_void_p * n)(*[t.data_ptr() for t in targets])
+    carr = (ctypes.c_void_p * n)(*[c.data_ptr() for c in confs])
+    oarr = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    ws = batched_workspace(guides, params) if ws is None else ws
+    p = params.c()
+    _check(load().dts_solve_batched(n, garr, tarr, _TORCH_DTYPE[dt], carr, ctypes.byref(p), oarr, ws.data_ptr(),
+                                    ws.numel(), _stream(stream)), "dts_solve_batched")
+    return outs
 
 
 def dts_solve_noalloc(guide: torch.Tensor, target: torch.Tensor, conf: torch.Tensor, params: Params,

@@ -1,0 +1,82 @@
+"""The batched entry point: images of uneven sizes solved as one CUDA graph launch,
+checked image by image against the FP64 oracle and against dts_solve, on repeated
+calls (graph replay) and after the arguments change (new capture)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1805_04590_gb300 import dts, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _batch(seed, n=7):
+    wl = workloads.workload_batched(seed=seed, n=n, hmin=17, hmax=300, wmin=9, wmax=400)
+    d = dev()
+    g = [torch.from_numpy(p.guide).to(d) for p in wl.problems]
+    t = [torch.from_numpy(p.target).to(d) for p in wl.problems]
+    c = [torch.from_numpy(p.conf).to(d) for p in wl.problems]
+    q = wl.params
+    prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes)
+    return wl, g, t, c, prm
+
+
+def test_batched_matches_oracle_and_single_solves():
+    wl, g, t, c, prm = _batch(5)
+    ws = dts.batched_workspace(g, prm)
+    outs = [torch.full_like(x, float("nan")) for x in t]
+    for rep in range(2):  # the second call replays the cached graph
+        for o in outs:
+            o.fill_(float("nan"))
+        dts.dts_solve_batched(g, t, c, prm, outs=outs, ws=ws)
+        torch.cuda.synchronize()
+        assert dts.dts_last_status() == 0
+        for i, p in enumerate(wl.problems):
+            z = outs[i].cpu().numpy()
+            ref = oracle.solve(p.guide, p.target, p.conf, lam=prm.lam, sigma_s=prm.sigma_s, sigma_r=prm.sigma_r,
+                               iterations=prm.iterations)
+            assert np.abs(z - ref).max() <= TOL * float(np.ptp(p.target)), (rep, i, p.target.shape)
+            single = dts.dts_solve(g[i], t[i], c[i], prm).cpu().numpy()
+            np.testing.assert_array_equal(z, single)
+
+
+def test_batched_recaptures_when_arguments_change():
+    wl, g, t, c, prm = _batch(6, n=4)
+    first = [x.clone() for x in dts.dts_solve_batched(g, t, c, prm)]
+    t2 = [x * 0.5 for x in t]
+    second = dts.dts_solve_batched(g, t2, c, prm)
+    torch.cuda.synchronize()
+    for i, p in enumerate(wl.problems):
+        ref = oracle.solve(p.guide, p.target * 0.5, p.conf, lam=prm.lam, sigma_s=prm.sigma_s, sigma_r=prm.sigma_r,
+                           iterations=prm.iterations)
+        assert np.abs(second[i].cpu().numpy() - ref).max() <= TOL * float(np.ptp(p.target))
+        assert not torch.equal(first[i], second[i])
+
+
+def test_batched_inside_a_caller_capture():
+    wl, g, t, c, prm = _batch(7, n=3)
+    ws = dts.batched_workspace(g, prm)
+    outs = [torch.empty_like(x) for x in t]
+    dts.dts_solve_batched(g, t, c, prm, outs=outs, ws=ws)  # warm (kernel attributes set outside capture)
+    torch.cuda.synchronize()
+    expect = [o.clone() for o in outs]
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for o in outs:
+            o.zero_()
+        with torch.cuda.graph(graph, stream=s):
+            dts.dts_solve_batched(g, t, c, prm, outs=outs, ws=ws, stream=s)
+    graph.replay()
+    torch.cuda.synchronize()
+    for o, e in zip(outs, expect):
+        torch.testing.assert_close(o, e, rtol=0, atol=0)
