@@ -172,6 +172,22 @@ int dts_solve_batched(int n, const dts_guide* guides, const void* const* targets
                       const float* const* confs, const dts_params* params, float* const* z_out, void* ws,
                       size_t ws_bytes, dts_stream stream);
 
+/* Autotuner (not part of the paper's method): for this guide's height and width, times each
+ * candidate vertical tile shape (rows per thread x warps per CTA x cluster size) and horizontal
+ * segment length with CUDA events on `stream`, using the workspace (sized for dts_filter) and the
+ * guide's real distances, and records the fastest; later calls for the same height / width use
+ * them.  Synchronises `stream`.  The results live in the process (see dts_autotune_export). */
+int dts_autotune(const dts_guide* guide, const dts_params* params, void* ws, size_t ws_bytes, dts_stream stream);
+
+/* Text of the recorded shapes ("row W items" and "col H items warps cluster" lines).  With
+ * buf == NULL returns the bytes needed (including the terminating 0); else copies and returns
+ * that count, or minus DTS_ERR_INVALID_ARG when len is too small. */
+int dts_autotune_export(char* buf, size_t len);
+
+/* Records shapes from text in the format of dts_autotune_export (shapes that are not valid
+ * candidates for their size are ignored).  DTS_ERR_INVALID_ARG on malformed text. */
+int dts_autotune_import(const char* text);
+
 /* Synchronises `stream`, then returns and clears the device-side status word of
  * the current device (DTS_OK, or e.g. DTS_ERR_TIMEOUT), or DTS_ERR_CUDA if the
  * synchronisation itself failed. */

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "dts_internal.cuh"
@@ -619,6 +620,125 @@ extern "C" int dts_solve_batched(int n, const dts_guide* guides, const void* con
     }
     cache.push_back(BatchGraph{key, exec});
     return cudaGraphLaunch(exec, s) == cudaSuccess ? DTS_OK : DTS_ERR_CUDA;
+}
+
+
+// ---------------------------------------------------------------- autotuner
+namespace dts {
+std::string tuned_export();
+}
+
+extern "C" int dts_autotune(const dts_guide* guide, const dts_params* params, void* ws, size_t ws_bytes,
+                            dts_stream stream) {
+    int st = check_guide(guide);
+    if (!st) st = check_params(params);
+    if (st) return st;
+    Plans pl;
+    if ((st = make_plans(guide->H, guide->W, &pl))) return st;
+    dts_params p = *params;
+    p.conf_mode = DTS_CONF_PLAIN;
+    p.save_checkpoints = 0;
+    const Layout L = make_layout(guide->H, guide->W, &p, 0);
+    if (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.fwd_end) return DTS_ERR_WORKSPACE;
+    if ((st = ensure_prepared())) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = bind_workspace(ws, L, s))) return st;
+    // real distances of this guide; the pass input is the iterate plane (any finite values)
+    float* u = reinterpret_cast<float*>(ws_at(ws, L.u));
+    if (cudaMemsetAsync(u, 0, L.plane_f32, s) != cudaSuccess) return DTS_ERR_CUDA;
+    if ((st = run_distances(guide, &p, L, ws, nullptr, DTS_F32, nullptr, s))) return st;
+    float k2[kMaxPasses];
+    pass_log2a(p.sigma_s, 1, k2);
+    const int dh = p.dist_dtype == DTS_F16;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return DTS_ERR_CUDA;
+    auto time_it = [&](auto&& launch) -> float {
+        for (int w = 0; w < 2; ++w)
+            if (launch() != cudaSuccess) return -1.f;
+        cudaEventRecord(e0, s);
+        const int reps = 5;
+        for (int r = 0; r < reps; ++r)
+            if (launch() != cudaSuccess) return -1.f;
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / reps;
+    };
+    // vertical shapes
+    ColPlan cand[16];
+    const int nc = col_candidates(guide->H, cand, 16);
+    float best = 1e30f;
+    ColPlan best_plan = pl.cols;
+    for (int i = 0; i < nc; ++i) {
+        PassArgs c = base_pass(guide, L);
+        c.src = u;
+        c.dst = u;
+        c.d = ws_at(ws, L.dY);
+        c.k2 = k2[0];
+        c.agg = nullptr;  // the cluster kernel, whose shape is being chosen
+        const float t = time_it([&] { return launch_col_pass(c, dh, PASS_PLAIN, cand[i], s); });
+        cudaGetLastError();
+        if (t > 0.f && t < best) {
+            best = t;
+            best_plan = cand[i];
+        }
+    }
+    set_tuned_col(guide->H, best_plan);
+    // horizontal items per thread
+    int best_items = pl.rows.items;
+    best = 1e30f;
+    for (int items : {8, 16}) {
+        RowPlan rp;
+        rp.items = items;
+        rp.tpr = ((guide->W + items - 1) / items + 31) / 32 * 32;
+        if (rp.tpr > 1024) continue;
+        rp.rpb = rp.tpr < 256 ? 256 / rp.tpr : 1;
+        PassArgs r = base_pass(guide, L);
+        r.src = u;
+        r.dst = u;
+        r.d = ws_at(ws, L.dX);
+        r.k2 = k2[0];
+        const float t = time_it([&] { return launch_row_pass(r, dh, PASS_PLAIN, rp, s); });
+        cudaGetLastError();
+        if (t > 0.f && t < best) {
+            best = t;
+            best_items = items;
+        }
+    }
+    set_tuned_row(guide->W, best_items);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return DTS_OK;
+}
+
+extern "C" int dts_autotune_export(char* buf, size_t len) {
+    const std::string t = tuned_export();
+    if (!buf) return (int)t.size() + 1;
+    if (len < t.size() + 1) return -DTS_ERR_INVALID_ARG;
+    memcpy(buf, t.c_str(), t.size() + 1);
+    return (int)t.size() + 1;
+}
+
+extern "C" int dts_autotune_import(const char* text) {
+    if (!text) return DTS_ERR_INVALID_ARG;
+    const char* p = text;
+    while (*p) {
+        int a = 0, b = 0, c = 0, d = 0, used = 0;
+        if (sscanf(p, "row %d %d %n", &a, &b, &used) == 2 && used > 0) {
+            if (a >= 1 && (b == 8 || b == 16)) set_tuned_row(a, b);
+        } else if (sscanf(p, "col %d %d %d %d %n", &a, &b, &c, &d, &used) == 4 && used > 0) {
+            ColPlan cp{b, c, d};
+            ColPlan cand[16];
+            const int nc = col_candidates(a, cand, 16);
+            for (int i = 0; i < nc; ++i)
+                if (cand[i].items == b && cand[i].warps == c && cand[i].cluster == d) set_tuned_col(a, cp);
+        } else {
+            return DTS_ERR_INVALID_ARG;
+        }
+        p += used;
+    }
+    return DTS_OK;
 }
 
 // ---------------------------------------------------------------- solve without allocation

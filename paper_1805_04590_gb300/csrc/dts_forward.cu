@@ -28,6 +28,7 @@
 #include <stdlib.h>
 
 #include <map>
+#include <string>
 #include <mutex>
 #include <tuple>
 
@@ -989,11 +990,69 @@ cudaError_t launch_col_dispatch(const PassArgs& a, int dist_half, int kind, cons
 }
 
 // Horizontal plan: ITEMS elements per thread, one row per tpr threads (<= 1024).
+// ---------------------------------------------------------------- tuned shapes
+// Shapes chosen by dts_autotune (measured per line length), consulted before the defaults.
+std::mutex g_tuned_mutex;
+std::map<int, int> g_tuned_row_items;      // W -> items per thread
+std::map<int, ColPlan> g_tuned_col_plans;  // H -> vertical shape
+
+void set_tuned_row(int W, int items) {
+    std::lock_guard<std::mutex> lock(g_tuned_mutex);
+    g_tuned_row_items[W] = items;
+}
+void set_tuned_col(int H, const ColPlan& p) {
+    std::lock_guard<std::mutex> lock(g_tuned_mutex);
+    g_tuned_col_plans[H] = p;
+}
+bool tuned_col(int H, ColPlan* p) {
+    std::lock_guard<std::mutex> lock(g_tuned_mutex);
+    auto it = g_tuned_col_plans.find(H);
+    if (it == g_tuned_col_plans.end()) return false;
+    *p = it->second;
+    return true;
+}
+int tuned_row(int W) {
+    std::lock_guard<std::mutex> lock(g_tuned_mutex);
+    auto it = g_tuned_row_items.find(W);
+    return it == g_tuned_row_items.end() ? 0 : it->second;
+}
+// "row W items" / "col H items warps cluster" lines
+std::string tuned_export() {
+    std::lock_guard<std::mutex> lock(g_tuned_mutex);
+    std::string out;
+    char line[96];
+    for (auto& kv : g_tuned_row_items) {
+        snprintf(line, sizeof(line), "row %d %d\n", kv.first, kv.second);
+        out += line;
+    }
+    for (auto& kv : g_tuned_col_plans) {
+        snprintf(line, sizeof(line), "col %d %d %d %d\n", kv.first, kv.second.items, kv.second.warps,
+                 kv.second.cluster);
+        out += line;
+    }
+    return out;
+}
+
+// vertical shapes the tuner tries: rows per thread x warps per CTA (clusters of at most 16)
+int col_candidates(int H, ColPlan* out, int max_out) {
+    static const int cand[][2] = {{8, 8}, {8, 16}, {8, 32}, {16, 8}, {16, 16}, {32, 8}, {32, 16}, {40, 16}};
+    int n = 0;
+    for (const auto& c : cand) {
+        const int rows = c[0] * c[1];
+        const int cs = (H + rows - 1) / rows;
+        if (cs > 16 || (cs > 1 && rows > 2 * H) || n >= max_out) continue;
+        out[n++] = ColPlan{c[0], c[1], cs};
+    }
+    return n;
+}
+
 bool plan_rows(int W, RowPlan* p) {
     int items;
     if (W <= 256) items = 8;
     else if (W <= 16 * 1024) items = 16;
     else return false;
+    const int tuned = tuned_row(W);
+    if ((tuned == 8 || tuned == 16) && (W + tuned - 1) / tuned <= 1024) items = tuned;
     static const char* env = getenv("DTS_ROW_ITEMS");  // tuning aid: force 8 or 16
     if (env && (atoi(env) == 8 || atoi(env) == 16) && (W + atoi(env) - 1) / atoi(env) <= 1024) items = atoi(env);
     int tpr = (W + items - 1) / items;
@@ -1009,6 +1068,7 @@ bool plan_rows(int W, RowPlan* p) {
 // Vertical plan: columns up to 256 rows in one CTA; else the first (items, warps) shape whose
 // cluster holds the whole column with at most 8 CTAs, else at most 16 (non-portable size).
 bool plan_cols(int H, ColPlan* p) {
+    if (tuned_col(H, p)) return true;
     // DTS_COL_PLAN="items,warps" overrides the shape (tuning aid)
     static const char* env = getenv("DTS_COL_PLAN");
     if (env) {

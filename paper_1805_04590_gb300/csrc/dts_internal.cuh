@@ -204,6 +204,10 @@ cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const Ro
 cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s);
 bool plan_rows(int W, RowPlan* p);
 bool row_update_fits(const RowPlan& p);
+// autotuner tables (dts_forward.cu)
+void set_tuned_row(int W, int items);
+void set_tuned_col(int H, const ColPlan& p);
+int col_candidates(int H, ColPlan* out, int max_out);
 cudaError_t launch_update(const PassArgs& a, cudaStream_t s);
 bool plan_cols(int H, ColPlan* p);
 bool plan_cols_tma(int H, ColPlan* p);

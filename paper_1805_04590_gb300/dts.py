@@ -70,7 +70,7 @@ _lib = None
 EXPORTS = ("dts_status_string", "dts_version", "dts_workspace_size", "dts_domain_transform", "dts_filter",
            "dts_solve", "dts_solve_backward", "dts_last_status", "dts_profile", "dts_profile_read",
            "dts_kernel_name", "dts_solve_noalloc", "dts_noalloc_max_workspace", "dts_batched_workspace_size",
-           "dts_solve_batched", "dts_debug_inject")
+           "dts_solve_batched", "dts_debug_inject", "dts_autotune", "dts_autotune_export", "dts_autotune_import")
 
 
 def library_path() -> str:
@@ -105,13 +105,17 @@ def load(build_if_missing: bool = True):
     lib.dts_batched_workspace_size.restype = sz
     lib.dts_solve_batched.argtypes = [i, P(CGuide), P(vp), i, P(vp), P(CParams), P(vp), vp, sz, vp]
     lib.dts_debug_inject.argtypes = [i]
+    lib.dts_autotune.argtypes = [P(CGuide), P(CParams), vp, sz, vp]
+    lib.dts_autotune_export.argtypes = [ctypes.c_char_p, sz]
+    lib.dts_autotune_import.argtypes = [ctypes.c_char_p]
     lib.dts_noalloc_max_workspace.restype = sz
     lib.dts_profile.argtypes = [i]
     lib.dts_profile_read.argtypes = [i, P(ctypes.c_int), P(ctypes.c_longlong), P(ctypes.c_int), P(ctypes.c_float)]
     lib.dts_kernel_name.argtypes = [i]
     lib.dts_kernel_name.restype = ctypes.c_char_p
     for name in ("dts_domain_transform", "dts_filter", "dts_solve", "dts_solve_backward", "dts_last_status",
-                 "dts_profile", "dts_profile_read", "dts_solve_noalloc", "dts_solve_batched", "dts_debug_inject"):
+                 "dts_profile", "dts_profile_read", "dts_solve_noalloc", "dts_solve_batched", "dts_debug_inject",
+                 "dts_autotune", "dts_autotune_export", "dts_autotune_import"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -225,10 +229,58 @@ def batched_workspace(guides, params: Params) -> torch.Tensor:
     return torch.empty(n, dtype=torch.uint8, device=guides[0].device)
 
 
+def dts_autotune(guide: torch.Tensor, params: Params, ws: Optional[torch.Tensor] = None, stream=None) -> None:
+    """Time the candidate tile shapes for this guide's height and width and record the fastest."""
+    g = guide_desc(guide)
+    ws = workspace(guide, params) if ws is None else ws
+    p = params.c()
+    _check(load().dts_autotune(ctypes.byref(g), ctypes.byref(p), ws.data_ptr(), ws.numel(), _stream(stream)),
+           "dts_autotune")
+
+
+def autotune_export() -> str:
+    lib = load()
+    n = lib.dts_autotune_export(None, 0)
+    buf = ctypes.create_string_buffer(n)
+    lib.dts_autotune_export(buf, n)
+    return buf.value.decode()
+
+
+def autotune_import(text: str) -> None:
+    _check(load().dts_autotune_import(text.encode()), "dts_autotune_import")
+
+
+def autotune_save(path: str) -> None:
+    """Write the recorded shapes to a JSON cache tagged with the device they were measured on."""
+    import json
+    dev = torch.cuda.get_device_properties(torch.cuda.current_device())
+    with open(path, "w") as f:
+        json.dump({"device": dev.name, "sm_count": dev.multi_processor_count, "shapes": autotune_export()}, f)
+
+
+def autotune_load(path: str) -> bool:
+    """Load a JSON cache written by autotune_save if it was measured on this kind of device."""
+    import json
+    with open(path) as f:
+        d = json.load(f)
+    dev = torch.cuda.get_device_properties(torch.cuda.current_device())
+    if d.get("device") != dev.name or d.get("sm_count") != dev.multi_processor_count:
+        return False
+    autotune_import(d["shapes"])
+    return True
+
+
 def dts_solve_batched(guides, targets, confs, params: Params, outs=None, ws: Optional[torch.Tensor] = None,
-                      stream=None):
-    """Solves of uneven sizes (lists of CUDA tensors, same parameters) as one CUDA graph launch."""
+                      stream=None, autotune: bool = False):
+    """Solves of uneven sizes (lists of CUDA tensors, same parameters) as one CUDA graph launch.
+    With autotune=True the tile shapes of every distinct size are measured first."""
     n = len(guides)
+    if autotune:
+        tuned = set()
+        for g in guides:
+            if tuple(g.shape) not in tuned:
+                dts_autotune(g, params, stream=stream)
+                tuned.add(tuple(g.shape))
     if not (len(targets) == len(confs) == n) or n == 0:
         raise ValueError("guides, targets and confs must be non-empty lists of equal length")
     dt = targets[0].dtype

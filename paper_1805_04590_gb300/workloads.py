@@ -49,11 +49,16 @@ class SolverParams:
 
 @dataclasses.dataclass
 class Problem:
-    """One image: guide (C, H, W), target (H, W), confidence (H, W), float32."""
+    """One image: guide (C, H, W), target (H, W), confidence (H, W), float32, C-contiguous."""
     guide: np.ndarray
     target: np.ndarray
     conf: np.ndarray
     truth: Optional[np.ndarray] = None
+
+    def __post_init__(self):
+        self.guide = np.ascontiguousarray(self.guide, dtype=np.float32)
+        self.target = np.ascontiguousarray(self.target, dtype=np.float32)
+        self.conf = np.ascontiguousarray(self.conf, dtype=np.float32)
 
     @property
     def shape(self):

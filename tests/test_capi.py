@@ -115,3 +115,16 @@ def test_product_path_never_imports_the_oracle():
                 src = open(os.path.join(dirpath, fn)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), fn
                 assert "dts_oracle" not in src and "liborc" not in src, fn
+
+
+def test_autotune_table_roundtrip_without_gpu():
+    lib = dts.load()
+    text = "row 2880 8\nrow 300 16\ncol 1988 16 16 8\ncol 500 32 8 2\n"
+    assert dts.autotune_import(text) is None
+    out = dts.autotune_export()
+    for line in ("row 2880 8", "row 300 16", "col 1988 16 16 8", "col 500 32 8 2"):
+        assert line in out
+    # a shape that is not a candidate for its height is ignored, malformed text rejected
+    dts.autotune_import("col 64 40 16 16\n")
+    assert "col 64 " not in dts.autotune_export()
+    assert lib.dts_autotune_import(b"bogus 1 2\n") == 1

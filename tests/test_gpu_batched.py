@@ -80,3 +80,16 @@ def test_batched_inside_a_caller_capture():
     torch.cuda.synchronize()
     for o, e in zip(outs, expect):
         torch.testing.assert_close(o, e, rtol=0, atol=0)
+
+
+def test_autotuned_shapes_are_used_and_exact():
+    wl, g, t, c, prm = _batch(8, n=3)
+    outs = dts.dts_solve_batched(g, t, c, prm, autotune=True)
+    torch.cuda.synchronize()
+    text = dts.autotune_export()
+    for x in g:
+        assert f"col {x.shape[1]} " in text and f"row {x.shape[2]} " in text
+    for i, p in enumerate(wl.problems):
+        ref = oracle.solve(p.guide, p.target, p.conf, lam=prm.lam, sigma_s=prm.sigma_s, sigma_r=prm.sigma_r,
+                           iterations=prm.iterations)
+        assert np.abs(outs[i].cpu().numpy() - ref).max() <= TOL * float(np.ptp(p.target))
