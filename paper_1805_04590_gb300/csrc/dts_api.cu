@@ -830,11 +830,15 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
     float* gbuf[2] = {plane(L.g0), plane(L.g1)};
     for (int k = K - 1; k >= 0; --k) {
         U[0] = plane(L.z + (size_t)k * L.plane_f32);
-        // recompute the inputs of passes 1 .. 2N-1 from the checkpoint z_k
-        for (int p = 0; p + 1 < 2 * N; ++p) {
+        // recompute the inputs of passes 1 .. 2N-1 from the checkpoint z_k; for Jacobi also zbar
+        // (the last pass's output, needed by the confidence gradient) into the free slot 0
+        const bool jacobi = params->update == DTS_UPDATE_JACOBI;
+        float* zbar = plane(L.xin);
+        for (int p = 0; p < 2 * N; ++p) {
+            if (p + 1 == 2 * N && !jacobi) break;
             PassArgs a = base_pass(guide, L);
             a.src = U[p];
-            a.dst = U[p + 1];
+            a.dst = p + 1 < 2 * N ? U[p + 1] : zbar;
             a.k2 = k2[p / 2];
             if (p % 2 == 0) {
                 a.d = ws_at(ws, L.dX);
@@ -843,6 +847,26 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
                 a.d = ws_at(ws, L.dY);
                 if ((st = cuda_status(launch_col_pass(a, dh, PASS_PLAIN, pl.cols, s)))) return st;
             }
+        }
+        // adjoint of the data-term update: dzbar into gbuf[0], the direct part stays in gz
+        {
+            BwdArgs b = {};
+            b.x = zbar;
+            b.H = H;
+            b.W = W;
+            b.pitch = P;
+            b.gz = gz;
+            b.gout = gbuf[0];
+            b.t = target;
+            b.t_dtype = target_dtype;
+            b.c = conf;
+            b.zk = U[0];
+            b.gt = grad_target;
+            b.gc = grad_conf;
+            b.lambda = params->lambda;
+            b.step = params->step;
+            b.update = params->update;
+            if ((st = cuda_status(launch_update_adjoint(b, s)))) return st;
         }
         // adjoint passes in reverse order
         int cur = 0;
@@ -860,19 +884,7 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
             if (p % 2 == 1) {
                 b.d = ws_at(ws, L.dY);
                 b.dbar = dYb;
-                const bool upd = p == 2 * N - 1;
-                if (upd) {
-                    b.t = target;
-                    b.t_dtype = target_dtype;
-                    b.c = conf;
-                    b.zk = U[0];
-                    b.gt = grad_target;
-                    b.gc = grad_conf;
-                    b.lambda = params->lambda;
-                    b.step = params->step;
-                    b.update = params->update;
-                }
-                if ((st = cuda_status(launch_col_bwd(b, dh, upd, cb, s)))) return st;
+                if ((st = cuda_status(launch_col_bwd(b, dh, false, cb, s)))) return st;
             } else {
                 b.d = ws_at(ws, L.dX);
                 b.dbar = dXb;

@@ -13,6 +13,9 @@
 // saved pass input, one for the carries of h and gJ.  The last vertical pass of an iteration also
 // takes the adjoint of the data-term update (Eq. 3 or Eq. 4); the first horizontal pass adds the
 // filter's adjoint into the gradient of the iterate.
+#include <stdio.h>
+#include <stdlib.h>
+
 #include "dts_scan.cuh"
 
 namespace dts {
@@ -45,9 +48,10 @@ struct BackwardMode {
 // jin: J entering from the left, kin: K entering from the right, hin: h entering from the left,
 // gin: gJ entering from the right.  On return K holds the recomputed pass output.
 template <int N>
-__device__ __forceinline__ void segment_adjoint(float (&x)[N], const float (&w)[N], float wn, const float (&G)[N],
-                                                float (&K)[N], float (&db)[N], float jin, float kin, float hin,
-                                                float gin, float lna) {
+__device__ __forceinline__ void segment_adjoint(float (&x)[N], const float (&w)[N], float wn, float (&G)[N],
+                                                float (&K)[N], float jin, float kin, float hin, float gin,
+                                                float lna) {
+    // live arrays: x (then dL/dx), w, J, K (then the weight gradient), G (then h)
     float J[N];
     float v = jin;
 #pragma unroll
@@ -62,22 +66,21 @@ __device__ __forceinline__ void segment_adjoint(float (&x)[N], const float (&w)[
         v = fmaf(wp, v - J[j], J[j]);
         K[j] = v;
     }
-    float h[N];
     float hp = hin;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         const float Jp = j ? J[j - 1] : jin;
-        db[j] = hp * (K[j] - Jp);
+        K[j] = hp * (K[j] - Jp);  // h[n-1] (K[n] - J[n-1]), the anti-causal share of dL/dw_n
         hp = fmaf(w[j], hp, G[j]);
-        h[j] = hp;
+        G[j] = hp;
     }
     float g = gin;
 #pragma unroll
     for (int j = N - 1; j >= 0; --j) {
         const float wp = (j + 1 < N) ? w[j + 1] : wn;
-        g = fmaf(wp, g - h[j], h[j]);  // (1 - w') h + w' g
+        g = fmaf(wp, g - G[j], G[j]);  // (1 - w') h + w' g
         const float Jp = j ? J[j - 1] : jin;
-        db[j] = lna * w[j] * fmaf(g, Jp - x[j], db[j]);
+        K[j] = lna * w[j] * fmaf(g, Jp - x[j], K[j]);
         x[j] = fmaf(-w[j], g, g);  // (1 - w) g
     }
 }
@@ -145,8 +148,9 @@ __global__ void __launch_bounds__(1024) row_bwd_kernel(BwdArgs a, int tpr) {
     const float kin = k_entering(suf.jk, fmaf(own_pre.jk.A, jin, own_pre.jk.B));
     const float hin = pre.hg.B;
     const float gin = k_entering(suf.hg, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
-    float K[ITEMS], db[ITEMS];
-    segment_adjoint(x, w, wn, G, K, db, jin, kin, hin, gin, a.lna);
+    float K[ITEMS];
+    segment_adjoint(x, w, wn, G, K, jin, kin, hin, gin, a.lna);
+    const float(&db)[ITEMS] = K;
 
     if (live) {
 #pragma unroll
@@ -179,11 +183,18 @@ __global__ void __launch_bounds__(1024) row_bwd_kernel(BwdArgs a, int tpr) {
 // and a.gz is overwritten with the direct part (the filter's adjoint is added later).
 template <int ITEMS>
 constexpr int bwd_col_max_threads() {
-    return ITEMS <= 8 ? 512 : 256;
+    return ITEMS <= 8 ? 512 : 512;
+}
+inline int bwd_col_max_threads_host(int items) { return items <= 8 ? 512 : 512; }
+
+// two resident CTAs of the largest plain shape (64 registers); the update variant keeps more live
+template <int ITEMS, bool UPDATE>
+constexpr int bwd_col_min_blocks() {
+    return (ITEMS <= 8 && !UPDATE) ? 2 : 1;
 }
 
-template <int ITEMS, bool DHALF, bool UPDATE>
-__global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>()) col_bwd_kernel(BwdArgs a) {
+template <int ITEMS, bool DHALF, bool UPDATE, bool FOLD = false>
+__global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_blocks<ITEMS, UPDATE>()) col_bwd_kernel(BwdArgs a) {
     using M = BackwardMode;
     __shared__ ColShared<M, 16> sh;
     const int lane = threadIdx.x & 31;
@@ -237,21 +248,40 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>()) col_bwd_kernel(B
     own_suf.jk = coupled_local<true>(x, w, wn);
     own_suf.hg = coupled_local<false>(G, w, wn);
     own_pre = M::Pre{Aff{own_suf.jk.A, own_suf.jk.B}, Aff{own_suf.hg.A, own_suf.hg.B}};
-    col_exchange<M, 16>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
+    if constexpr (FOLD) col_exchange<M, 16>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
+    else col_exchange_scan<M, 16>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
     release_successor();
     const float jin = pre.jk.B;
     const float kin = k_entering(suf.jk, fmaf(own_pre.jk.A, jin, own_pre.jk.B));
     const float hin = pre.hg.B;
     const float gin = k_entering(suf.hg, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
-    float K[ITEMS], db[ITEMS];
-    segment_adjoint(x, w, wn, G, K, db, jin, kin, hin, gin, a.lna);
+    float K[ITEMS];
+    float zbar[UPDATE ? ITEMS : 1];
+    if constexpr (UPDATE) {
+        // the Jacobi confidence gradient needs zbar = this pass's output: sweep it once more
+        float J = jin;
+        float Jv[ITEMS];
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            J = fmaf(w[j], J - x[j], x[j]);
+            Jv[j] = J;
+        }
+        float Kc = kin;
+#pragma unroll
+        for (int j = ITEMS - 1; j >= 0; --j) {
+            const float wp = (j + 1 < ITEMS) ? w[j + 1] : wn;
+            Kc = fmaf(wp, Kc - Jv[j], Jv[j]);
+            zbar[j] = Kc;
+        }
+    }
+    segment_adjoint(x, w, wn, G, K, jin, kin, hin, gin, a.lna);
 
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int r = row0 + j;
         if (!(col_ok && r < a.H)) continue;
         const long long idx = (long long)r * P + col;
-        a.dbar[idx] += db[j];
+        a.dbar[idx] += K[j];
         a.gout[idx] = x[j];
         if constexpr (UPDATE) {
             const long long di = (long long)r * a.W + col;
@@ -263,7 +293,7 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>()) col_bwd_kernel(B
                 const float den = a.lambda + cf;
                 if (den != 0.f) {
                     dt = cf / den * g;
-                    dc = a.lambda * (t - K[j]) / (den * den) * g;
+                    dc = a.lambda * (t - zbar[j]) / (den * den) * g;
                     dz = 0.f;
                 } else {
                     dt = dc = 0.f;
@@ -317,6 +347,45 @@ __global__ void __launch_bounds__(256) guide_grad_kernel(GuideGradArgs a) {
     }
 }
 
+// Adjoint of the data-term update at every pixel, given g = dL/dz_{k+1} in a.gz:
+//   GD      dzbar = eta lambda g,  dt += eta c g,  dc += eta (t - z_k) g,  a.gz <- (1 - eta lambda - eta c) g
+//   Jacobi  dzbar = lambda g / den,  dt += c g / den,  dc += lambda (t - zbar) g / den^2,  a.gz <- 0
+//           (den = lambda + c; where den = 0 the iterate was kept: a.gz <- g and nothing else)
+// dzbar goes to a.gout (the input gradient of the last pass's adjoint); a.x holds zbar (Jacobi).
+__global__ void __launch_bounds__(256) update_adjoint_kernel(BwdArgs a) {
+    wait_predecessor();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= a.W || y >= a.H) return;
+    const long long idx = (long long)y * a.pitch + x;
+    const long long di = (long long)y * a.W + x;
+    const float g = a.gz[idx];
+    const float cf = a.c[di];
+    const float t = load_any(a.t, di, a.t_dtype);
+    float dzb, dt, dc, dz;
+    if (a.update == DTS_UPDATE_JACOBI) {
+        const float den = a.lambda + cf;
+        if (den != 0.f) {
+            dzb = a.lambda / den * g;
+            dt = cf / den * g;
+            dc = a.lambda * (t - a.x[idx]) / (den * den) * g;
+            dz = 0.f;
+        } else {
+            dzb = dt = dc = 0.f;
+            dz = g;
+        }
+    } else {
+        dzb = a.step * a.lambda * g;
+        dt = a.step * cf * g;
+        dc = a.step * (t - a.zk[idx]) * g;
+        dz = (1.f - a.step * a.lambda - a.step * cf) * g;
+    }
+    a.gout[idx] = dzb;
+    a.gz[idx] = dz;
+    if (a.gt) a.gt[di] += dt;
+    if (a.gc) a.gc[di] += dc;
+}
+
 // dst[y][x] (pitch dp) += src[y][x] (pitch sp), or = when accumulate is 0
 __global__ void __launch_bounds__(256) axpy_plane_kernel(const float* src, long long sp, float* dst, long long dp,
                                                          int H, int W, int accumulate) {
@@ -341,15 +410,18 @@ template <int ITEMS, bool DHALF>
 cudaError_t launch_col_bwd_t(const BwdArgs& a, bool update, const ColPlan& p, cudaStream_t s) {
     const dim3 grid((unsigned)((a.W + 31) / 32), (unsigned)p.cluster, 1);
     const dim3 block((unsigned)(32 * p.warps));
+    static const bool fold = getenv("DTS_BWD_FOLD") != nullptr;  // tuning aid
     if (update) return launch_ex(col_bwd_kernel<ITEMS, DHALF, true>, grid, block, p.cluster, s, a);
+    if (fold) return launch_ex(col_bwd_kernel<ITEMS, DHALF, false, true>, grid, block, p.cluster, s, a);
     return launch_ex(col_bwd_kernel<ITEMS, DHALF, false>, grid, block, p.cluster, s, a);
 }
 
 template <int ITEMS, bool DHALF>
 cudaError_t allow_bwd_clusters() {
     cudaError_t e = cudaSuccess;
-    const void* fs[2] = {(const void*)col_bwd_kernel<ITEMS, DHALF, true>,
-                         (const void*)col_bwd_kernel<ITEMS, DHALF, false>};
+    const void* fs[3] = {(const void*)col_bwd_kernel<ITEMS, DHALF, true>,
+                         (const void*)col_bwd_kernel<ITEMS, DHALF, false>,
+                         (const void*)col_bwd_kernel<ITEMS, DHALF, false, true>};
     for (const void* f : fs) {
         const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (r != cudaSuccess) e = r;
@@ -373,9 +445,25 @@ bool plan_rows_bwd(int W, RowPlan* p) {
     return true;
 }
 
-// Backward vertical plan (CTA at most bwd_col_max_threads): columns up to 2048 rows.
+// Backward vertical plan (CTA at most bwd_col_max_threads): columns up to 4096 rows.
 bool plan_cols_bwd(int H, ColPlan* p) {
-    static const int cand[][2] = {{8, 8}, {8, 16}, {16, 8}};
+    // DTS_BWD_COL_PLAN="items,warps" overrides the shape (tuning aid)
+    static const char* env = getenv("DTS_BWD_COL_PLAN");
+    if (env) {
+        int it = 0, nw = 0;
+        if (sscanf(env, "%d,%d", &it, &nw) == 2 && (it == 8 || it == 16) && nw >= 1 && (nw & (nw - 1)) == 0 &&
+            nw * 32 <= bwd_col_max_threads_host(it)) {
+            const int cs = (H + it * nw - 1) / (it * nw);
+            if (cs <= 16) {
+                p->items = it;
+                p->warps = nw;
+                p->cluster = cs;
+                return true;
+            }
+        }
+    }
+    // measured on the 2880 x 1988 stereo workload: 16 rows x 16 warps (clusters of 8) is fastest
+    static const int cand[][2] = {{16, 16}, {8, 16}, {16, 8}, {8, 8}};
     if (H <= 128) {
         int nw = 1;
         while (nw * 8 < H) nw <<= 1;  // a power of two (the CTA scan works in lane groups)
@@ -432,6 +520,14 @@ cudaError_t launch_guide_grad(const GuideGradArgs& a, cudaStream_t s) {
         else if (a.gdtype == DTS_F16) e = launch_ex(guide_grad_kernel<__half, false>, grid, block, 0, s, a);
         else e = launch_ex(guide_grad_kernel<float, false>, grid, block, 0, s, a);
     }
+    prof_end(h, s);
+    return e;
+}
+
+cudaError_t launch_update_adjoint(const BwdArgs& a, cudaStream_t s) {
+    const int h = prof_begin(KID_UPDATE_ADJ, (long long)a.H * a.W, a.t_dtype != DTS_F32 ? kFlagTarget16 : 0, s);
+    const dim3 grid((unsigned)((a.W + 255) / 256), (unsigned)a.H);
+    const cudaError_t e = launch_ex(update_adjoint_kernel, grid, dim3(256), 0, s, a);
     prof_end(h, s);
     return e;
 }

@@ -180,6 +180,7 @@ enum KernelId {
     KID_COL_AGG = 13,
     KID_ROW_UPDATE = 14,
     KID_UPDATE = 15,
+    KID_UPDATE_ADJ = 16,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
@@ -227,6 +228,7 @@ bool plan_cols_bwd(int H, ColPlan* p);
 cudaError_t launch_row_bwd(const BwdArgs& a, int dist_half, bool final_pass, const RowPlan& p, cudaStream_t s);
 cudaError_t launch_col_bwd(const BwdArgs& a, int dist_half, bool update, const ColPlan& p, cudaStream_t s);
 cudaError_t launch_guide_grad(const GuideGradArgs& a, cudaStream_t s);
+cudaError_t launch_update_adjoint(const BwdArgs& a, cudaStream_t s);
 cudaError_t launch_axpy_plane(const float* src, long long sp, float* dst, long long dp, int H, int W, int accumulate,
                               cudaStream_t s);
 cudaError_t prepare_backward_kernels();

@@ -293,6 +293,34 @@ __device__ __forceinline__ void col_exchange(const typename M::Pre& own_pre, con
     cluster.barrier_arrive();
 }
 
+// col_exchange with the cross-warp part done by cta_scan (log2(NW) shuffle rounds instead of a
+// per-thread fold over the other warps): the better choice when the tuples are large.  NW must be
+// a power of two.  Same contract as col_exchange.
+template <class M, int NWMAX>
+__device__ __forceinline__ void col_exchange_scan(const typename M::Pre& own_pre, const typename M::Suf& own_suf,
+                                                  int lane, int warp, int NW, ColShared<M, NWMAX>& sh,
+                                                  typename M::Pre& pre, typename M::Suf& suf) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int CS = (int)cluster.num_blocks();
+    sh.pre[warp][lane] = own_pre;
+    sh.suf[warp][lane] = own_suf;
+    __syncthreads();
+    cta_scan<M, NWMAX>(lane, warp, NW, sh);
+    typename M::Pre wpre = sh.pre[warp][lane];
+    typename M::Suf wsuf = sh.suf[warp][lane];
+    if (CS > 1) {
+        cluster.sync();
+        gather_cluster_totals<M, NWMAX>(cluster, rank, CS, lane, warp, NW, sh);
+        __syncthreads();
+        wpre = M::pre_compose(sh.cl_pre[lane], wpre);
+        wsuf = M::suf_compose(wsuf, sh.cl_suf[lane]);
+    }
+    pre = wpre;
+    suf = wsuf;
+    cluster.barrier_arrive();
+}
+
 __device__ __forceinline__ void cluster_exit() { cg::this_cluster().barrier_wait(); }
 
 // The same exchange for a kernel that loops over several lines per cluster (persistent grid).
