@@ -50,6 +50,7 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4):
         "copy_plane_kernel": s_t + 4,
         "row_pass_kernel": 8 + s_d,
         "col_pass_kernel": 8 + s_d,
+        "col_strip_kernel": 8 + s_d,
         "col_pass_kernel<update>": 16 + s_d + s_t,
         "row_pass_kernel<support>": s_d + 4,
         "col_pass_kernel<support>": 12 + s_d,
@@ -62,6 +63,7 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4):
         "col_bwd_kernel<update>": 48 + s_d + s_t,
         "guide_grad_kernel": C * s_g + 2 * s_d + 8 + 4 * C,
         "axpy_plane_kernel": 12,
+        "update_adjoint_kernel": 36 + s_t,
     }.get(name)
 
 

@@ -173,13 +173,15 @@ int dts_solve_batched(int n, const dts_guide* guides, const void* const* targets
                       size_t ws_bytes, dts_stream stream);
 
 /* Autotuner (not part of the paper's method): for this guide's height and width, times each
- * candidate vertical tile shape (rows per thread x warps per CTA x cluster size) and horizontal
+ * candidate vertical tile shape (rows per thread x warps per CTA x cluster size, where cluster
+ * size 0 is the cluster-free kernel with one CTA per 8-column strip) and horizontal
  * segment length with CUDA events on `stream`, using the workspace (sized for dts_filter) and the
  * guide's real distances, and records the fastest; later calls for the same height / width use
  * them.  Synchronises `stream`.  The results live in the process (see dts_autotune_export). */
 int dts_autotune(const dts_guide* guide, const dts_params* params, void* ws, size_t ws_bytes, dts_stream stream);
 
-/* Text of the recorded shapes ("row W items" and "col H items warps cluster" lines).  With
+/* Text of the recorded shapes ("row W items" and "col H items warps cluster" lines; cluster 0:
+ * the strip kernel).  Batched solves take the cluster shapes for their vertical passes.  With
  * buf == NULL returns the bytes needed (including the terminating 0); else copies and returns
  * that count, or minus DTS_ERR_INVALID_ARG when len is too small. */
 int dts_autotune_export(char* buf, size_t len);

@@ -528,6 +528,9 @@ int issue_batch(int n, const dts_guide* guides, const void* const* targets, int 
         Plans pl;
         int st = make_plans(guides[i].H, guides[i].W, &pl);
         if (st) return st;
+        // solves that run side by side keep the cluster shapes for the vertical passes: their
+        // smaller CTAs pack several images onto an SM (measured on the 64-image batch)
+        if (pl.cols.cluster == 0 && !plan_cols_cluster(guides[i].H, &pl.cols)) return DTS_ERR_UNSUPPORTED;
         const Layout L = make_layout(guides[i].H, guides[i].W, p, 0);
         st = solve_forward(&guides[i], targets[i], tdt, confs[i], nullptr, p, z_out[i], ws_at(ws, offset[i]), L, pl,
                            r.side[j]);
@@ -676,7 +679,7 @@ extern "C" int dts_autotune(const dts_guide* guide, const dts_params* params, vo
         c.dst = u;
         c.d = ws_at(ws, L.dY);
         c.k2 = k2[0];
-        c.agg = nullptr;  // the cluster kernel, whose shape is being chosen
+        c.agg = nullptr;  // not the split kernel: the shape being chosen
         const float t = time_it([&] { return launch_col_pass(c, dh, PASS_PLAIN, cand[i], s); });
         cudaGetLastError();
         if (t > 0.f && t < best) {

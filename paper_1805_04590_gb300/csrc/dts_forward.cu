@@ -465,6 +465,261 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
     cluster_exit();
 }
 
+
+// ---------------------------------------------------------------- strip vertical pass (no cluster)
+// CTA = NW <= 32 warps over a strip of 8 columns and the whole column height.  Lane l of warp q
+// takes column l % 8 and segment 4q + l / 8 (ITEMS rows each): 4 NW segments per column.
+// Exchange: the 4 segments of a column inside a warp scan with shuffles at stride 8; the NW warp
+// totals of a column scan in one warp (lane = warp); two __syncthreads, no cluster barrier.
+constexpr int kStripCols = 8;
+constexpr int kStripWarps = 32;
+
+template <class M>
+struct StripShared {
+    typename M::Pre pre[kStripWarps][kStripCols + 1];
+    typename M::Suf suf[kStripWarps][kStripCols + 1];
+};
+
+// pre / suf: the transforms of everything above / below this thread's segment in its column
+template <class M>
+__device__ __forceinline__ void strip_exchange(const typename M::Pre& own_pre, const typename M::Suf& own_suf,
+                                               int lane, int warp, int NW, int cl, int sw, StripShared<M>& sh,
+                                               typename M::Pre& pre, typename M::Suf& suf) {
+    using Pre = typename M::Pre;
+    using Suf = typename M::Suf;
+    constexpr int SEGS = 32 / kStripCols;
+    // inside the warp: the column's segments are lanes cl, cl + 8, cl + 16, cl + 24
+    Pre ip = own_pre;
+    Suf is = own_suf;
+#pragma unroll
+    for (int off = 1; off < SEGS; off <<= 1) {
+        const Pre op = shfl_up_t(ip, off * kStripCols);
+        const Suf os = shfl_down_t(is, off * kStripCols);
+        if (sw >= off) ip = M::pre_compose(op, ip);
+        if (sw + off < SEGS) is = M::suf_compose(is, os);
+    }
+    Pre xp = shfl_up_t(ip, kStripCols);
+    Suf xs = shfl_down_t(is, kStripCols);
+    if (sw == 0) xp = M::pre_identity();
+    if (sw == SEGS - 1) xs = M::suf_identity();
+    if (sw == SEGS - 1) sh.pre[warp][cl] = ip;  // warp total, prefix direction
+    if (sw == 0) sh.suf[warp][cl] = is;         // warp total, suffix direction
+    __syncthreads();
+    // across the warps: warp c < 8 (or every warp of a smaller CTA, in turn) scans column c over
+    // the NW warp totals (lane = warp)
+    for (int c = warp; c < kStripCols; c += NW) {
+        const bool in = lane < NW;
+        const Pre p = in ? sh.pre[lane][c] : M::pre_identity();
+        const Suf f = in ? sh.suf[lane][c] : M::suf_identity();
+        const Pre ip2 = warp_scan_pre<M>(p, lane);
+        const Suf is2 = warp_scan_suf<M>(f, lane);
+        Pre pe = shfl_up_t(ip2, 1);
+        Suf fe = shfl_down_t(is2, 1);
+        if (lane == 0) pe = M::pre_identity();
+        if (lane == 31) fe = M::suf_identity();
+        if (in) {
+            sh.pre[lane][c] = pe;
+            sh.suf[lane][c] = fe;
+        }
+    }
+    __syncthreads();
+    pre = M::pre_compose(sh.pre[warp][cl], xp);
+    suf = M::suf_compose(xs, sh.suf[warp][cl]);
+}
+
+// Strip kernel with plain loads: each warp load covers four 32-byte row pieces.
+template <int ITEMS, bool DHALF>
+__global__ void __launch_bounds__(32 * kStripWarps) col_strip_kernel(PassArgs a) {
+    using M = CoupledMode;
+    using DT = typename std::conditional<DHALF, __half, float>::type;
+    __shared__ StripShared<M> sh;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int NW = blockDim.x >> 5;
+    const int cl = lane & (kStripCols - 1);  // column within the strip
+    const int sw = lane / kStripCols;        // segment within the warp (0..3)
+    const int col = blockIdx.x * kStripCols + cl;
+    const bool col_ok = col < a.W;
+    const int row0 = (warp * (32 / kStripCols) + sw) * ITEMS;
+    const long long P = a.pitch;
+
+    wait_predecessor();
+    float x[ITEMS], w[ITEMS];
+    const bool full = col_ok && row0 + ITEMS <= a.H;
+    {
+        const float* ps = a.src + (long long)row0 * P + col;
+        const DT* pd = static_cast<const DT*>(a.d) + (long long)row0 * P + col;
+        if (full) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                x[j] = *ps;
+                w[j] = to_f32<DT>(*pd);
+                ps += P;
+                pd += P;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const bool ok = col_ok && row0 + j < a.H;
+                x[j] = ok ? *ps : 0.f;
+                w[j] = ok ? to_f32<DT>(*pd) : 0.f;
+                ps += P;
+                pd += P;
+            }
+        }
+    }
+    float wn;
+    {
+        const int rn = row0 + ITEMS;
+        wn = (col_ok && rn < a.H) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)rn * P + col)) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) w[j] = ex2(a.k2 * w[j]);
+    if (!full) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j)
+            if (!(col_ok && row0 + j < a.H)) w[j] = 0.f;
+    }
+    if (row0 == 0) w[0] = 0.f;
+
+    typename M::Pre own_pre, pre;
+    typename M::Suf own_suf, suf;
+    M::local(x, w, wn, own_pre, own_suf);
+    strip_exchange<M>(own_pre, own_suf, lane, warp, NW, cl, sw, sh, pre, suf);
+    release_successor();
+    M::apply(x, w, wn, own_pre, pre.B, suf);
+
+    float* pdst = a.dst + (long long)row0 * a.dst_pitch + col;
+    if (full) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            *pdst = x[j];
+            pdst += a.dst_pitch;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (col_ok && row0 + j < a.H) *pdst = x[j];
+            pdst += a.dst_pitch;
+        }
+    }
+}
+
+// Strip kernel fed by TMA, persistent over strips.  Warp q owns the slab of rows
+// [4 q ITEMS, 4 (q + 1) ITEMS) of every strip the CTA processes: one lane loads the slab's
+// positions (8 x 4 ITEMS box) and distances (one row more: the weight entering the next slab)
+// into the warp's input region, completing on the warp's mbarrier (bounded waits).  As soon as
+// the warp holds a strip in registers it starts the loads of its next strip into the same
+// region, so they overlap the exchange and the replay.  The result goes out through a second
+// region and one TMA store per warp and strip.  ITEMS is odd, so the four segments of a warp
+// start on rows of different residue mod 4 (mod 8 for FP16 distances) and the column-wise
+// shared-memory accesses are free of bank conflicts.
+template <int ITEMS, bool DHALF>
+__host__ __device__ constexpr int strip_x_bytes() {
+    return 4 * ITEMS * kStripCols * 4;  // a multiple of 128 for odd ITEMS = 9, 17 (1152, 2176)
+}
+template <int ITEMS, bool DHALF>
+__host__ __device__ constexpr int strip_d_bytes() {
+    return ((4 * ITEMS + 1) * kStripCols * (DHALF ? 2 : 4) + 127) / 128 * 128;
+}
+// input positions, input distances, output
+template <int ITEMS, bool DHALF>
+__host__ __device__ constexpr int strip_slab_bytes() {
+    return 2 * strip_x_bytes<ITEMS, DHALF>() + strip_d_bytes<ITEMS, DHALF>();
+}
+
+template <int ITEMS, bool DHALF>
+__global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const __grid_constant__ CUtensorMap tm_x,
+                                                                          const __grid_constant__ CUtensorMap tm_d,
+                                                                          const __grid_constant__ CUtensorMap tm_o,
+                                                                          PassArgs a, int nstrips, long long timeout) {
+    static_assert(ITEMS % 2 == 1, "odd segment length (bank-conflict-free column accesses)");
+    static_assert(strip_x_bytes<ITEMS, DHALF>() % 128 == 0, "slab alignment");
+    using M = CoupledMode;
+    using DT = typename std::conditional<DHALF, __half, float>::type;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ StripShared<M> sh;
+    __shared__ __align__(8) uint64_t bar[kStripWarps];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int NW = blockDim.x >> 5;
+    const int cl = lane & (kStripCols - 1);
+    const int sw = lane / kStripCols;
+    const int slab_row = warp * 4 * ITEMS;
+    const int row0 = slab_row + sw * ITEMS;
+    unsigned char* slab = dsm + (size_t)warp * strip_slab_bytes<ITEMS, DHALF>();
+    float* sx = reinterpret_cast<float*>(slab);
+    const DT* sd = reinterpret_cast<const DT*>(slab + strip_x_bytes<ITEMS, DHALF>());
+    float* so = reinterpret_cast<float*>(slab + strip_x_bytes<ITEMS, DHALF>() + strip_d_bytes<ITEMS, DHALF>());
+    constexpr uint32_t kTx = 4 * ITEMS * kStripCols * 4 + (4 * ITEMS + 1) * kStripCols * (int)sizeof(DT);
+
+    if (lane == 0) {
+        mbar_init(&bar[warp], 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    wait_predecessor();
+    // full boxes count, the parts outside the plane included (they read as zero)
+    if (lane == 0 && (int)blockIdx.x < nstrips) {
+        mbar_arrive_expect_tx(&bar[warp], kTx);
+        tma_load_2d(sx, &tm_x, blockIdx.x * kStripCols, slab_row, &bar[warp]);
+        tma_load_2d((void*)sd, &tm_d, blockIdx.x * kStripCols, slab_row, &bar[warp]);
+    }
+    int it = 0;
+    for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x, ++it) {
+        const int next = strip + gridDim.x;
+        const int col = strip * kStripCols + cl;
+        const bool col_ok = col < a.W;
+        if (!mbar_wait_bounded(&bar[warp], (uint32_t)(it & 1), timeout) && lane == 0)
+            atomicExch(a.status, DTS_ERR_TIMEOUT);
+        float x[ITEMS], w[ITEMS];
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            x[j] = sx[(sw * ITEMS + j) * kStripCols + cl];
+            w[j] = to_f32<DT>(sd[(sw * ITEMS + j) * kStripCols + cl]);
+        }
+        const float dn = to_f32<DT>(sd[((sw + 1) * ITEMS) * kStripCols + cl]);
+        // the reads above come before the next strip's TMA writes into the same region
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0 && next < nstrips) {
+            mbar_arrive_expect_tx(&bar[warp], kTx);
+            tma_load_2d(sx, &tm_x, next * kStripCols, slab_row, &bar[warp]);
+            tma_load_2d((void*)sd, &tm_d, next * kStripCols, slab_row, &bar[warp]);
+        }
+        const float wn = (col_ok && row0 + ITEMS < a.H) ? ex2(a.k2 * dn) : 0.f;
+        const bool full = col_ok && row0 + ITEMS <= a.H;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) w[j] = ex2(a.k2 * w[j]);
+        if (!full) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j)
+                if (!(col_ok && row0 + j < a.H)) w[j] = 0.f;  // positions outside the plane read as 0
+        }
+        if (row0 == 0) w[0] = 0.f;
+
+        typename M::Pre own_pre, pre;
+        typename M::Suf own_suf, suf;
+        M::local(x, w, wn, own_pre, own_suf);
+        strip_exchange<M>(own_pre, own_suf, lane, warp, NW, cl, sw, sh, pre, suf);
+        if (next >= nstrips) release_successor();
+        M::apply(x, w, wn, own_pre, pre.B, suf);
+
+        // the previous strip's store must have read the output region before it is rewritten
+        if (lane == 0) bulk_wait_read();
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) so[(sw * ITEMS + j) * kStripCols + cl] = x[j];
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            tma_store_2d(&tm_o, strip * kStripCols, slab_row, so);
+            bulk_commit();
+        }
+    }
+    if (lane == 0) bulk_wait_read();
+}
+
 // ---------------------------------------------------------------- persistent horizontal pass
 // Persistent CTAs loop over groups of rpb rows; the next group's positions and distances are
 // loaded into a second register set while the current group is exchanged and replayed, so the
@@ -756,6 +1011,23 @@ EncodeTiledFn tensor_map_encoder() {
     return fn;
 }
 
+// Boxes of box_cols x box_rows elements of an H x W plane with row pitch `pitch` elements; false
+// when the plane breaks the tensor-map rules (16-byte aligned base and pitch) or encoding fails.
+bool make_box_map(CUtensorMap* m, const void* base, bool half, int W, int H, long long pitch, int box_cols,
+                  int box_rows) {
+    EncodeTiledFn fn = tensor_map_encoder();
+    if (!fn) return false;
+    const int es = half ? 2 : 4;
+    if ((uintptr_t)base % 16 != 0 || (pitch * es) % 16 != 0 || (box_cols * es) % 16 != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    const cuuint32_t elem[2] = {1, 1};
+    return fn(m, half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base),
+              dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Tiles of 32 columns x box_rows rows of an H x W plane with row pitch `pitch` elements.
 bool make_tile_map(CUtensorMap* m, const void* base, bool half, int W, int H, long long pitch, int box_rows) {
     EncodeTiledFn fn = tensor_map_encoder();
@@ -951,17 +1223,71 @@ cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const Ro
     return e;
 }
 
+cudaError_t launch_col_strip(const PassArgs& a, int dist_half, const ColPlan& p, cudaStream_t s);
+
 cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
     ColPlan tp_probe;
     const bool inject = injected_tma_skip_pending() && kind != PASS_SUPPORT_CONF && plan_cols_tma(a.H, &tp_probe);
     if (!inject && use_col_split() && kind != PASS_SUPPORT_CONF && a.agg && a.carry && a.counters)
         return launch_col_split(a, dist_half, kind, s);
-    const int kid = kind == PASS_UPDATE ? KID_COL_UPDATE : kind == PASS_SUPPORT_CONF ? KID_COL_SUPPORT : KID_COL_PLAIN;
+    // the strip kernel runs plain passes only; other kinds (and fault injection) take the cluster shape
+    ColPlan q = p;
+    if (q.cluster == 0 && (kind != PASS_PLAIN || inject) && !plan_cols_cluster(a.H, &q)) return cudaErrorInvalidValue;
+    const bool strip = q.cluster == 0;
+    const int kid = strip ? KID_COL_STRIP
+                  : kind == PASS_UPDATE ? KID_COL_UPDATE : kind == PASS_SUPPORT_CONF ? KID_COL_SUPPORT : KID_COL_PLAIN;
     const int flags = (dist_half ? kFlagDistHalf : 0) | (kind == PASS_UPDATE && a.t_dtype != DTS_F32 ? kFlagTarget16 : 0);
     const int h = prof_begin(kid, (long long)a.H * a.W, flags, s);
-    const cudaError_t e = launch_col_dispatch(a, dist_half, kind, p, s);
+    const cudaError_t e = strip ? launch_col_strip(a, dist_half, q, s) : launch_col_dispatch(a, dist_half, kind, q, s);
     prof_end(h, s);
     return e;
+}
+
+// strip kernel (no cluster): rows per segment (odd: 9, or 17 above 1152 rows) and warps of a
+// strip CTA, the fewest warps whose 4 NW segments cover the column (up to kStripMaxRows rows)
+constexpr int kStripMaxRows = 4 * kStripWarps * 17;
+
+void strip_shape(int H, int* items, int* warps) {
+    const int it = H <= 4 * kStripWarps * 9 ? 9 : 17;
+    const int segs = (H + it - 1) / it;
+    *items = it;
+    *warps = (segs + 3) / 4;
+}
+
+// DTS_STRIP_LSU=1: the plain-load strip kernel instead of the TMA one (tuning aid)
+bool strip_lsu() {
+    static const bool on = getenv("DTS_STRIP_LSU") != nullptr;
+    return on;
+}
+
+template <int ITEMS, bool DHALF>
+cudaError_t launch_col_strip_t(const PassArgs& a, int nw, cudaStream_t s) {
+    const dim3 grid((unsigned)((a.W + kStripCols - 1) / kStripCols));
+    const dim3 block((unsigned)(32 * nw));
+    CUtensorMap tx, td, to;
+    if (!strip_lsu() && make_box_map(&tx, a.src, false, a.W, a.H, a.pitch, kStripCols, 4 * ITEMS) &&
+        make_box_map(&td, a.d, DHALF, a.W, a.H, a.pitch, kStripCols, 4 * ITEMS + 1) &&
+        make_box_map(&to, a.dst, false, a.W, a.H, a.dst_pitch, kStripCols, 4 * ITEMS)) {
+        auto kernel = col_strip_tma_kernel<ITEMS, DHALF>;  // shared-memory limit raised in prepare_kernels
+        const size_t smem = (size_t)nw * strip_slab_bytes<ITEMS, DHALF>();
+        // persistent: as many CTAs as fit at once (each loops over strips), at most one per strip
+        const int nstrips = (int)grid.x;
+        const int per_sm = blocks_per_sm((const void*)kernel, 32 * nw, smem);
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        const int g = std::min(nstrips, per_sm * sm_count());
+        return launch_ex_smem(kernel, dim3((unsigned)g), block, 0, smem, s, tx, td, to, a, nstrips,
+                              default_timeout_cycles());
+    }
+    // planes that tensor maps cannot describe (e.g. a caller's unaligned output): plain loads
+    return launch_ex(col_strip_kernel<ITEMS, DHALF>, grid, block, 0, s, a);
+}
+
+cudaError_t launch_col_strip(const PassArgs& a, int dist_half, const ColPlan& p, cudaStream_t s) {
+    if (p.warps < 1 || p.warps > kStripWarps || (long long)4 * p.warps * p.items < a.H) return cudaErrorInvalidValue;
+    if (p.items == 9) return dist_half ? launch_col_strip_t<9, true>(a, p.warps, s) : launch_col_strip_t<9, false>(a, p.warps, s);
+    if (p.items == 17)
+        return dist_half ? launch_col_strip_t<17, true>(a, p.warps, s) : launch_col_strip_t<17, false>(a, p.warps, s);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_col_dispatch(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
@@ -1033,10 +1359,15 @@ std::string tuned_export() {
     return out;
 }
 
-// vertical shapes the tuner tries: rows per thread x warps per CTA (clusters of at most 16)
+// vertical shapes the tuner tries: the strip kernel (columns up to 2048 rows), then rows per
+// thread x warps per CTA in clusters of at most 16
 int col_candidates(int H, ColPlan* out, int max_out) {
     static const int cand[][2] = {{8, 8}, {8, 16}, {8, 32}, {16, 8}, {16, 16}, {32, 8}, {32, 16}, {40, 16}};
     int n = 0;
+    if (H <= kStripMaxRows && n < max_out) {
+        strip_shape(H, &out[n].items, &out[n].warps);
+        out[n++].cluster = 0;
+    }
     for (const auto& c : cand) {
         const int rows = c[0] * c[1];
         const int cs = (H + rows - 1) / rows;
@@ -1065,10 +1396,27 @@ bool plan_rows(int W, RowPlan* p) {
     return true;
 }
 
-// Vertical plan: columns up to 256 rows in one CTA; else the first (items, warps) shape whose
-// cluster holds the whole column with at most 8 CTAs, else at most 16 (non-portable size).
+bool use_col_tma();
+bool use_col_split();
+
+// Vertical plan: the strip kernel for columns up to 2048 rows (measured faster than clusters on
+// the stereo, depth and 256 x 256 workloads; DTS_NO_STRIP=1 keeps clusters, a tuning aid), else
+// the cluster plan.  A tuned shape comes first.
 bool plan_cols(int H, ColPlan* p) {
     if (tuned_col(H, p)) return true;
+    static const bool strip = getenv("DTS_NO_STRIP") == nullptr && getenv("DTS_COL_PLAN") == nullptr;
+    if (strip && !use_col_tma() && !use_col_split() && H <= kStripMaxRows) {
+        strip_shape(H, &p->items, &p->warps);
+        p->cluster = 0;
+        return true;
+    }
+    return plan_cols_cluster(H, p);
+}
+
+// Cluster plan: columns up to 256 rows in one CTA; else the first (items, warps) shape whose
+// cluster holds the whole column with at most 8 CTAs, else at most 16 (non-portable size).
+bool plan_cols_cluster(int H, ColPlan* p) {
+    if (tuned_col(H, p) && p->cluster > 0) return true;
     // DTS_COL_PLAN="items,warps" overrides the shape (tuning aid)
     static const char* env = getenv("DTS_COL_PLAN");
     if (env) {
@@ -1171,6 +1519,14 @@ bool plan_cols_tma(int H, ColPlan* p) {
     return true;
 }
 
+// dynamic shared memory of the TMA strip kernel: up to 32 slabs (208 KB at 17 rows, FP32)
+template <int ITEMS, bool DHALF>
+cudaError_t allow_strip_smem() {
+    return cudaFuncSetAttribute((const void*)col_strip_tma_kernel<ITEMS, DHALF>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kStripWarps * strip_slab_bytes<ITEMS, DHALF>());
+}
+
 cudaError_t prepare_kernels() {
     cudaError_t e = cudaSuccess, r;
     if ((r = allow_clusters<8, false>()) != cudaSuccess) e = r;
@@ -1181,6 +1537,10 @@ cudaError_t prepare_kernels() {
     if ((r = allow_clusters<32, true>()) != cudaSuccess) e = r;
     if ((r = allow_clusters<40, false>()) != cudaSuccess) e = r;
     if ((r = allow_clusters<40, true>()) != cudaSuccess) e = r;
+    if ((r = allow_strip_smem<9, false>()) != cudaSuccess) e = r;
+    if ((r = allow_strip_smem<9, true>()) != cudaSuccess) e = r;
+    if ((r = allow_strip_smem<17, false>()) != cudaSuccess) e = r;
+    if ((r = allow_strip_smem<17, true>()) != cudaSuccess) e = r;
     return e;
 }
 

@@ -151,7 +151,7 @@ struct GuideGradArgs {
 struct ColPlan {
     int items;   // rows per thread
     int warps;   // warps per CTA
-    int cluster; // CTAs per cluster along the column
+    int cluster; // CTAs per cluster along the column; 0: one CTA per 8-column strip (no cluster)
 };
 
 struct RowPlan {
@@ -181,6 +181,7 @@ enum KernelId {
     KID_ROW_UPDATE = 14,
     KID_UPDATE = 15,
     KID_UPDATE_ADJ = 16,
+    KID_COL_STRIP = 17,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
@@ -211,6 +212,7 @@ void set_tuned_col(int H, const ColPlan& p);
 int col_candidates(int H, ColPlan* out, int max_out);
 cudaError_t launch_update(const PassArgs& a, cudaStream_t s);
 bool plan_cols(int H, ColPlan* p);
+bool plan_cols_cluster(int H, ColPlan* p);
 bool plan_cols_tma(int H, ColPlan* p);
 bool use_persistent();
 bool use_row_persistent();

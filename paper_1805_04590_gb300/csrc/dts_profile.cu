@@ -109,6 +109,7 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_ROW_UPDATE: return "row_pass_kernel<update>";
         case KID_UPDATE: return "update_kernel";
         case KID_UPDATE_ADJ: return "update_adjoint_kernel";
+        case KID_COL_STRIP: return "col_strip_kernel";
         default: return "unknown";
     }
 }

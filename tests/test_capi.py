@@ -119,11 +119,16 @@ def test_product_path_never_imports_the_oracle():
 
 def test_autotune_table_roundtrip_without_gpu():
     lib = dts.load()
-    text = "row 2880 8\nrow 300 16\ncol 1988 16 16 8\ncol 500 32 8 2\n"
+    # cluster shapes "col H items warps cluster"; cluster 0 is the strip kernel (one CTA of
+    # `warps` warps per 8 columns, 4 * warps segments of `items` rows per column)
+    text = "row 2880 8\nrow 300 16\ncol 1988 16 16 8\ncol 500 32 8 2\ncol 1080 9 30 0\n"
     assert dts.autotune_import(text) is None
     out = dts.autotune_export()
-    for line in ("row 2880 8", "row 300 16", "col 1988 16 16 8", "col 500 32 8 2"):
+    for line in ("row 2880 8", "row 300 16", "col 1988 16 16 8", "col 500 32 8 2", "col 1080 9 30 0"):
         assert line in out
+    # a strip shape that does not cover the column is not a candidate
+    dts.autotune_import("col 1500 16 17 0\n")
+    assert "col 1500 " not in dts.autotune_export()
     # a shape that is not a candidate for its height is ignored, malformed text rejected
     dts.autotune_import("col 64 40 16 16\n")
     assert "col 64 " not in dts.autotune_export()

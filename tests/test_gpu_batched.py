@@ -45,8 +45,11 @@ def test_batched_matches_oracle_and_single_solves():
             ref = oracle.solve(p.guide, p.target, p.conf, lam=prm.lam, sigma_s=prm.sigma_s, sigma_r=prm.sigma_r,
                                iterations=prm.iterations)
             assert np.abs(z - ref).max() <= TOL * float(np.ptp(p.target)), (rep, i, p.target.shape)
+            # single solves of columns up to 2048 rows take the strip kernel for their vertical
+            # passes, batched solves the cluster kernel: the same recursion with another grouping
+            # of the segment exchange, so the two agree to FP32 rounding, not bit for bit
             single = dts.dts_solve(g[i], t[i], c[i], prm).cpu().numpy()
-            np.testing.assert_array_equal(z, single)
+            assert np.abs(z - single).max() <= TOL * float(np.ptp(p.target)), (rep, i)
 
 
 def test_batched_recaptures_when_arguments_change():

@@ -75,8 +75,13 @@ def test_distances_strided_guide():
 
 
 # ---------------------------------------------------------------- filter
-FILTER_SHAPES = [(1, 1), (1, 17), (19, 1), (7, 13), (33, 257), (300, 517), (257, 64), (1000, 77), (2100, 40),
-                 (3, 9000), (4100, 9), (64, 8193)]
+# vertical passes: strip CTAs (one per 8 columns, the warp count following the height) up to 2176
+# rows -- edges at 1152 / 1153 (segment length 9 -> 17), 1080 (30 warps), 2176 (32 warps) -- and
+# clusters above (2177, 4100).  The strip kernel loads and stores through tensor maps; an output
+# whose row pitch is not a multiple of 16 bytes (W = 77, 13, ...) takes its plain-load twin for
+# the last pass, W = 24 / 12 store through a tensor map into the caller's buffer.
+FILTER_SHAPES = [(1, 1), (1, 17), (19, 1), (7, 13), (33, 257), (300, 517), (257, 64), (1000, 77), (1152, 24),
+                 (1153, 13), (1080, 31), (2176, 12), (2177, 5), (2100, 40), (3, 9000), (4100, 9), (64, 8193)]
 
 
 @pytest.mark.parametrize("H,W", FILTER_SHAPES)
@@ -172,6 +177,21 @@ def test_solve_fp16_distances():
     assert_close(z.cpu().numpy(), ref, prob.target, "fp16 distances")
 
 
+@pytest.mark.parametrize("H,W", [(180, 260), (1500, 72)])
+def test_filter_fp16_distances(H, W):
+    """FP16 distance planes in the filter (segments of 9 and of 17 rows in the strip kernel):
+    against the oracle filtering with its own FP64 distances rounded to FP16."""
+    prob = workloads.random_problem(H, W, C=3, seed=H + W)
+    prm = dts.Params(sigma_s=12.0, sigma_r=0.3, passes=3, dist_dtype=dts.F16)
+    out = dts.dts_filter(to_dev(prob.guide), to_dev(prob.target), prm)
+    dX, dY = oracle.distances(prob.guide, 12.0, 0.3)
+    dX = dX.astype(np.float16).astype(np.float64)
+    dY = dY.astype(np.float16).astype(np.float64)
+    _, a = oracle.schedule(12.0, 3)
+    ref = oracle.filter_d(dX, dY, a, prob.target)
+    assert_close(out.cpu().numpy(), ref, prob.target, f"fp16 distances {H}x{W}")
+
+
 def test_solve_full_stereo_workload():
     """The 2880 x 1988, 20-iteration stereo-shaped solve at full size, all outputs."""
     wl = workloads.make(1)
@@ -185,4 +205,5 @@ def test_solve_full_stereo_workload():
 
 
 def test_last_status_clean():
+    dev()
     assert dts.dts_last_status() == 0
