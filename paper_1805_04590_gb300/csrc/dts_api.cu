@@ -296,9 +296,10 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
     };
     // The data-term update of iteration k is applied by the first horizontal pass of iteration
     // k + 1 (reading z_k, zbar, t and c as vectors along rows and writing z_{k+1}); after the
-    // last iteration a standalone kernel applies it.  Rows too long for that kernel keep the
-    // update in the last vertical pass.
-    const bool row_update = row_update_fits(pl.rows);
+    // last iteration a standalone kernel applies it.  Rows too long for that kernel (over 16384)
+    // keep the update in the last vertical pass.
+    RowPlan urows;
+    const bool row_update = plan_rows_update(W, pl.rows, &urows);
     for (int k = 0; k < K; ++k) {
         float* zin = zslot(k);
         for (int i = 0; i < p->passes; ++i) {
@@ -315,7 +316,7 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
                 r.zout = zin;  // z_k
                 r.zout_pitch = L.pitch;
             }
-            if ((st = cuda_status(launch_row_pass(r, dh, rkind, pl.rows, s)))) return st;
+            if ((st = cuda_status(launch_row_pass(r, dh, rkind, rkind == PASS_UPDATE_ROW ? urows : pl.rows, s)))) return st;
             PassArgs c = base_pass(g, L);
             c.src = u;
             c.dst = u;

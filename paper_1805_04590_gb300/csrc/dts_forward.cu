@@ -181,6 +181,105 @@ __global__ void __launch_bounds__(256) distance_kernel(DistArgs a) {
     }
 }
 
+// Four consecutive guide values of one row (16-byte load for FP32, 8-byte for 16-bit types).
+template <typename GT>
+__device__ __forceinline__ void load4_guide(const GT* p, float* out) {
+    if constexpr (sizeof(GT) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        out[0] = v.x;
+        out[1] = v.y;
+        out[2] = v.z;
+        out[3] = v.w;
+    } else {
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
+        const GT* h = reinterpret_cast<const GT*>(&v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = to_f32<GT>(h[k]);
+    }
+}
+
+template <typename DT>
+__device__ __forceinline__ void store4_dist(DT* p, const float* v) {
+    if constexpr (sizeof(DT) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        uint2 u;
+        DT* h = reinterpret_cast<DT*>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h[k] = from_f32<DT>(v[k]);
+        *reinterpret_cast<uint2*>(p) = u;
+    }
+}
+
+// Distances with four consecutive columns per thread (vector loads and stores), for guides whose
+// rows and channels start on 4-element boundaries and W % 4 == 0.  Thread = 4 columns x
+// kDistRows rows; a warp covers 128 columns.  The left neighbour of a thread's first column is
+// the previous lane's last one (lane 0 loads it); the upper neighbour is the previous row held
+// in registers.
+template <typename GT, typename DT>
+__global__ void __launch_bounds__(256) distance4_kernel(DistArgs a) {
+    wait_predecessor();
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * 32 + lane) * 4;
+    const int y0 = (blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kDistRows;
+    const bool xok = x0 < a.W;  // W % 4 == 0: the thread's four columns are all inside or all outside
+    const GT* I = static_cast<const GT*>(a.guide);
+    float sx[kDistRows][4], sy[kDistRows][4];
+#pragma unroll
+    for (int r = 0; r < kDistRows; ++r)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sx[r][k] = sy[r][k] = 0.f;
+    const bool l2 = a.norm == DTS_NORM_L2;
+    for (int c = 0; c < a.C; ++c) {
+        const GT* Ic = I + (long long)c * a.ch_stride;
+        float prev[4] = {0.f, 0.f, 0.f, 0.f};
+        if (xok && y0 > 0 && y0 - 1 < a.H) load4_guide<GT>(Ic + (long long)(y0 - 1) * a.row_stride + x0, prev);
+#pragma unroll
+        for (int r = 0; r < kDistRows; ++r) {
+            const int y = y0 + r;
+            const bool ok = xok && y < a.H;
+            const long long p = (long long)y * a.row_stride + x0;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            if (ok) load4_guide<GT>(Ic + p, v);
+            float left = __shfl_up_sync(kFull, v[3], 1);
+            if (lane == 0) left = (ok && x0 > 0) ? to_f32<GT>(Ic[p - 1]) : 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float dxv = v[k] - (k == 0 ? left : v[k - 1]);
+                const float dyv = v[k] - prev[k];
+                sx[r][k] += l2 ? dxv * dxv : fabsf(dxv);
+                sy[r][k] += l2 ? dyv * dyv : fabsf(dyv);
+                prev[k] = v[k];
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kDistRows; ++r) {
+        const int y = y0 + r;
+        if (!(xok && y < a.H)) continue;
+        float dx[4], dy[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (l2) {
+                dx[k] = sqrtf(fmaf(a.k * a.k, sx[r][k], 1.f));
+                dy[k] = sqrtf(fmaf(a.k * a.k, sy[r][k], 1.f));
+            } else {
+                dx[k] = fmaf(a.k, sx[r][k], 1.f);
+                dy[k] = fmaf(a.k, sy[r][k], 1.f);
+            }
+            if (y == 0) dy[k] = 1.f;
+        }
+        if (x0 == 0) dx[0] = 1.f;
+        const long long q = (long long)y * a.pitch + x0;
+        store4_dist<DT>(static_cast<DT*>(a.dX) + q, dx);
+        store4_dist<DT>(static_cast<DT*>(a.dY) + q, dy);
+        if (a.dst) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a.dst[q + k] = load_any(a.src, (long long)y * a.W + x0 + k, a.src_dtype);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) copy_plane_kernel(const void* src, int src_dtype, long long sp, float* dst,
                                                          long long dp, int H, int W) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1163,6 +1262,21 @@ __global__ void __launch_bounds__(256) update_kernel(PassArgs a) {
 
 bool row_update_fits(const RowPlan& p) { return p.tpr * p.rpb <= 512; }
 
+// Plan of the horizontal pass that also applies the data-term update (CTAs of at most 512
+// threads): the plain plan when it fits, else 32 positions per thread (rows up to 16384).
+bool plan_rows_update(int W, const RowPlan& plain, RowPlan* p) {
+    if (row_update_fits(plain)) {
+        *p = plain;
+        return true;
+    }
+    const int tpr = ((W + 31) / 32 + 31) / 32 * 32;
+    if (tpr > 512) return false;
+    p->items = 32;
+    p->tpr = tpr;
+    p->rpb = 1;
+    return true;
+}
+
 cudaError_t launch_update(const PassArgs& a, cudaStream_t s) {
     const int h = prof_begin(KID_UPDATE, (long long)a.H * a.W, a.t_dtype != DTS_F32 ? kFlagTarget16 : 0, s);
     const dim3 grid((unsigned)((a.W + 255) / 256), (unsigned)a.H);
@@ -1176,9 +1290,26 @@ cudaError_t launch_col_dispatch(const PassArgs& a, int dist_half, int kind, cons
 
 cudaError_t launch_distances(const DistArgs& a, cudaStream_t s) {
     const dim3 block(256);  // 8 warps x kDistRows rows
-    const dim3 grid((unsigned)((a.W + 31) / 32), (unsigned)((a.H + 8 * kDistRows - 1) / (8 * kDistRows)));
     const int h = prof_begin(KID_DISTANCES, (long long)a.H * a.W, a.dhalf ? kFlagDistHalf : 0, s);
     cudaError_t e;
+    const int gsz = a.gdtype == DTS_F32 ? 4 : 2;
+    const bool vec = a.W % 4 == 0 && a.row_stride % 4 == 0 && a.ch_stride % 4 == 0 &&
+                     (uintptr_t)a.guide % (4 * gsz) == 0 && a.pitch % 4 == 0;
+    if (vec) {
+        const dim3 grid((unsigned)((a.W + 127) / 128), (unsigned)((a.H + 8 * kDistRows - 1) / (8 * kDistRows)));
+        if (a.dhalf) {
+            if (a.gdtype == DTS_BF16) e = launch_ex(distance4_kernel<__nv_bfloat16, __half>, grid, block, 0, s, a);
+            else if (a.gdtype == DTS_F16) e = launch_ex(distance4_kernel<__half, __half>, grid, block, 0, s, a);
+            else e = launch_ex(distance4_kernel<float, __half>, grid, block, 0, s, a);
+        } else {
+            if (a.gdtype == DTS_BF16) e = launch_ex(distance4_kernel<__nv_bfloat16, float>, grid, block, 0, s, a);
+            else if (a.gdtype == DTS_F16) e = launch_ex(distance4_kernel<__half, float>, grid, block, 0, s, a);
+            else e = launch_ex(distance4_kernel<float, float>, grid, block, 0, s, a);
+        }
+        prof_end(h, s);
+        return e;
+    }
+    const dim3 grid((unsigned)((a.W + 31) / 32), (unsigned)((a.H + 8 * kDistRows - 1) / (8 * kDistRows)));
     if (a.dhalf) {
         if (a.gdtype == DTS_BF16) e = launch_ex(distance_kernel<__nv_bfloat16, __half>, grid, block, 0, s, a);
         else if (a.gdtype == DTS_F16) e = launch_ex(distance_kernel<__half, __half>, grid, block, 0, s, a);
@@ -1218,6 +1349,12 @@ cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const Ro
     } else {
         if (p.items == 8) e = dist_half ? launch_row_k<8, true>(a, kind, p, s) : launch_row_k<8, false>(a, kind, p, s);
         if (p.items == 16) e = dist_half ? launch_row_k<16, true>(a, kind, p, s) : launch_row_k<16, false>(a, kind, p, s);
+        if (p.items == 32 && kind == PASS_UPDATE_ROW) {  // long rows (plan_rows_update)
+            const dim3 grid((unsigned)((a.H + p.rpb - 1) / p.rpb));
+            const dim3 block((unsigned)(p.tpr * p.rpb));
+            e = dist_half ? launch_ex(row_pass_kernel<32, true, PASS_UPDATE_ROW>, grid, block, 0, s, a, p.tpr)
+                          : launch_ex(row_pass_kernel<32, false, PASS_UPDATE_ROW>, grid, block, 0, s, a, p.tpr);
+        }
     }
     prof_end(h, s);
     return e;

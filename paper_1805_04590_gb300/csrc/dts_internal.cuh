@@ -206,6 +206,7 @@ cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const Ro
 cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s);
 bool plan_rows(int W, RowPlan* p);
 bool row_update_fits(const RowPlan& p);
+bool plan_rows_update(int W, const RowPlan& plain, RowPlan* p);
 // autotuner tables (dts_forward.cu)
 void set_tuned_row(int W, int items);
 void set_tuned_col(int H, const ColPlan& p);

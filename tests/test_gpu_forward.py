@@ -47,10 +47,12 @@ def assert_close(z, ref, t, what=""):
 
 
 # ---------------------------------------------------------------- distances
+# W = 53: one column per thread; W = 52 (rows on 4-element boundaries): four columns per thread
+@pytest.mark.parametrize("W", [53, 52])
 @pytest.mark.parametrize("gdt", [torch.float32, torch.bfloat16, torch.float16])
 @pytest.mark.parametrize("norm", [dts.NORM_L1, dts.NORM_L2])
-def test_distances(gdt, norm):
-    prob = workloads.random_problem(37, 53, C=4, seed=2)
+def test_distances(gdt, norm, W):
+    prob = workloads.random_problem(37, W, C=4, seed=2)
     g = to_dev(prob.guide, gdt)
     prm = dts.Params(sigma_s=8.0, sigma_r=0.2, norm=norm)
     dX, dY = dts.dts_domain_transform(g, prm)
@@ -63,11 +65,12 @@ def test_distances(gdt, norm):
     np.testing.assert_allclose(hY.float().cpu().numpy(), rY, rtol=2 ** -10, atol=0)
 
 
-def test_distances_strided_guide():
-    prob = workloads.random_problem(20, 30, C=3, seed=4)
+@pytest.mark.parametrize("W", [30, 32])
+def test_distances_strided_guide(W):
+    prob = workloads.random_problem(20, W, C=3, seed=4)
     big = torch.zeros((3, 25, 40), device=dev())
-    big[:, :20, :30] = to_dev(prob.guide)
-    view = big[:, :20, :30]
+    big[:, :20, :W] = to_dev(prob.guide)
+    view = big[:, :20, :W]
     dX, dY = dts.dts_domain_transform(view, dts.Params())
     rX, rY = oracle.distances(prob.guide, 8.0, 0.2)
     np.testing.assert_allclose(dX.cpu().numpy(), rX, rtol=2e-6)
@@ -114,7 +117,10 @@ def test_solve_plain_workload():
     assert_close(z.cpu().numpy(), ref, p.target, "plain 256x256")
 
 
-@pytest.mark.parametrize("H,W", [(1, 1), (1, 40), (40, 1), (31, 45), (129, 300), (700, 263), (1100, 90)])
+# (3, 9000) and (2, 16384): rows longer than 8192 apply the update in a horizontal pass with 32
+# positions per thread
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 40), (40, 1), (31, 45), (129, 300), (700, 263), (1100, 90), (3, 9000),
+                                 (2, 16384)])
 @pytest.mark.parametrize("update", [dts.UPDATE_GD, dts.UPDATE_JACOBI])
 def test_solve_shapes(H, W, update):
     prob = workloads.random_problem(H, W, C=3, seed=H + 3 * W + update)
