@@ -106,6 +106,8 @@ struct Layout {
     size_t g0, g1;      // adjoint ping-pong planes
     size_t gz;          // adjoint of the iterate
     size_t dXb, dYb;    // distance gradients
+    size_t tot;         // chunk totals of the vertical adjoint (columns taller than one cluster)
+    int tot_chunks;
     size_t total;
 };
 
@@ -139,6 +141,9 @@ Layout make_layout(int H, int W, const dts_params* p, int with_backward) {
         L.gz = off; off += L.plane_f32;
         L.dXb = off; off += L.plane_f32;
         L.dYb = off; off += L.plane_f32;
+        L.tot_chunks = bwd_col_chunks(H);
+        L.tot = off;
+        off += align_up((size_t)L.tot_chunks * 14 * (size_t)L.pitch * sizeof(float), kPlaneAlign);
     }
     L.total = off;
     return L;
@@ -888,7 +893,10 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
             if (p % 2 == 1) {
                 b.d = ws_at(ws, L.dY);
                 b.dbar = dYb;
-                if ((st = cuda_status(launch_col_bwd(b, dh, false, cb, s)))) return st;
+                b.tot = plane(L.tot);
+                b.tot_chunks = L.tot_chunks;
+                b.tot_pitch = P;
+                if ((st = cuda_status(launch_col_bwd(b, dh, cb, s)))) return st;
             } else {
                 b.d = ws_at(ws, L.dX);
                 b.dbar = dXb;

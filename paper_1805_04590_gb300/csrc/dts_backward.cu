@@ -88,8 +88,14 @@ __device__ __forceinline__ void segment_adjoint(float (&x)[N], const float (&w)[
 // ---------------------------------------------------------------- horizontal pass adjoint
 // Same thread layout as the forward horizontal pass.  FINAL: the first pass of the filter; its
 // input gradient is added into a.gz instead of written to a.gout.
+// CTA limit: 1024 threads at 8 positions; 640 at 16 (rows up to 10240, registers for five arrays)
+template <int ITEMS>
+constexpr int row_bwd_max_threads() {
+    return ITEMS <= 8 ? 1024 : 640;
+}
+
 template <int ITEMS, bool DHALF, bool FINAL>
-__global__ void __launch_bounds__(1024) row_bwd_kernel(BwdArgs a, int tpr) {
+__global__ void __launch_bounds__(row_bwd_max_threads<ITEMS>()) row_bwd_kernel(BwdArgs a, int tpr) {
     static_assert(ITEMS % 4 == 0, "ITEMS must be a multiple of 4");
     using M = BackwardMode;
     __shared__ M::Pre s_pre[32];
@@ -174,40 +180,70 @@ __global__ void __launch_bounds__(1024) row_bwd_kernel(BwdArgs a, int tpr) {
 }
 
 // ---------------------------------------------------------------- vertical pass adjoint
-// Same layout as the forward vertical pass.  UPDATE: the last pass of an iteration; its output
-// gradient is the adjoint of the data-term update, computed from a.gz = dL/dz_{k+1}:
-//   GD      z' = z - eta (lambda (z - zbar) + c (z - t)):
-//           dzbar = eta lambda g,  dt += eta c g,  dc += eta (t - z) g,  dz (direct) = (1 - eta lambda - eta c) g
-//   Jacobi  z' = (lambda zbar + c t) / (lambda + c):
-//           dzbar = lambda g / den,  dt += c g / den,  dc += lambda (t - zbar) g / den^2,  dz (direct) = 0
-// and a.gz is overwritten with the direct part (the filter's adjoint is added later).
+// Same layout as the forward vertical pass (lane = column, one cluster per 32-column strip).
+// Columns taller than one cluster are cut into chunks of CS x NW x ITEMS rows, one cluster each
+// (grid.y = CS x chunks).  Then the pass runs twice: chunk mode 1 writes each chunk's total
+// transforms (prefix and suffix direction) to a.tot; chunk mode 2 composes the totals of the
+// chunks above and below into every segment's carries and replays.  Mode 0: a single chunk.
 template <int ITEMS>
 constexpr int bwd_col_max_threads() {
-    return ITEMS <= 8 ? 512 : 512;
+    return 512;
 }
-inline int bwd_col_max_threads_host(int items) { return items <= 8 ? 512 : 512; }
+inline int bwd_col_max_threads_host(int) { return 512; }
 
-// two resident CTAs of the largest plain shape (64 registers); the update variant keeps more live
-template <int ITEMS, bool UPDATE>
+// two resident CTAs of the 8-row shape (64 registers)
+template <int ITEMS>
 constexpr int bwd_col_min_blocks() {
-    return (ITEMS <= 8 && !UPDATE) ? 2 : 1;
+    return ITEMS <= 8 ? 2 : 1;
 }
 
-template <int ITEMS, bool DHALF, bool UPDATE, bool FOLD = false>
-__global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_blocks<ITEMS, UPDATE>()) col_bwd_kernel(BwdArgs a) {
+// chunk totals in a.tot: plane f of chunk c at (c * kTotFields + f) * tot_pitch
+constexpr int kTotFields = 14;  // prefix: 2 x (A, B); suffix: 2 x (A, B, al, be, ga)
+
+__device__ __forceinline__ void store_tot_pre(const BwdArgs& a, int chunk, int col, const Pre2& p) {
+    float* t = a.tot + (long long)chunk * kTotFields * a.tot_pitch + col;
+    const long long q = a.tot_pitch;
+    t[0] = p.jk.A;
+    t[q] = p.jk.B;
+    t[2 * q] = p.hg.A;
+    t[3 * q] = p.hg.B;
+}
+__device__ __forceinline__ void store_tot_suf(const BwdArgs& a, int chunk, int col, const Suf2& f) {
+    float* t = a.tot + (long long)chunk * kTotFields * a.tot_pitch + col + 4 * a.tot_pitch;
+    const long long q = a.tot_pitch;
+    const float v[10] = {f.jk.A, f.jk.B, f.jk.al, f.jk.be, f.jk.ga, f.hg.A, f.hg.B, f.hg.al, f.hg.be, f.hg.ga};
+#pragma unroll
+    for (int i = 0; i < 10; ++i) t[i * q] = v[i];
+}
+__device__ __forceinline__ Pre2 load_tot_pre(const BwdArgs& a, int chunk, int col) {
+    const float* t = a.tot + (long long)chunk * kTotFields * a.tot_pitch + col;
+    return Pre2{Aff{t[0], t[a.tot_pitch]}, Aff{t[2 * a.tot_pitch], t[3 * a.tot_pitch]}};
+}
+__device__ __forceinline__ Suf2 load_tot_suf(const BwdArgs& a, int chunk, int col) {
+    const float* t = a.tot + (long long)chunk * kTotFields * a.tot_pitch + col + 4 * a.tot_pitch;
+    const long long q = a.tot_pitch;
+    return Suf2{Coupled{t[0], t[q], t[2 * q], t[3 * q], t[4 * q]},
+                Coupled{t[5 * q], t[6 * q], t[7 * q], t[8 * q], t[9 * q]}};
+}
+
+template <int ITEMS, bool DHALF, bool FOLD = false, bool CHUNKED = false>
+__global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_blocks<ITEMS>()) col_bwd_kernel(BwdArgs a) {
     using M = BackwardMode;
     __shared__ ColShared<M, 16> sh;
+    cg::cluster_group cluster = cg::this_cluster();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int NW = blockDim.x >> 5;
-    const int rank = (int)cg::this_cluster().block_rank();
+    const int rank = (int)cluster.block_rank();
+    const int CS = (int)cluster.num_blocks();
+    const int chunk = CHUNKED ? (int)blockIdx.y / CS : 0;
     const int col = blockIdx.x * 32 + lane;
     const bool col_ok = col < a.W;
-    const int row0 = (rank * NW + warp) * ITEMS;
+    const int row0 = ((chunk * CS + rank) * NW + warp) * ITEMS;
     const long long P = a.pitch;
 
     wait_predecessor();
-    float x[ITEMS], w[ITEMS], G[ITEMS], g1[ITEMS];
+    float x[ITEMS], w[ITEMS], G[ITEMS];
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int r = row0 + j;
@@ -215,22 +251,7 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_bloc
         const long long idx = (long long)r * P + col;
         x[j] = ok ? a.x[idx] : 0.f;
         w[j] = ok ? load1_d<DHALF>(a.d, idx) : 0.f;
-        if constexpr (UPDATE) {
-            g1[j] = ok ? a.gz[idx] : 0.f;
-            float gb = 0.f;
-            if (ok) {
-                const float cf = a.c[(long long)r * a.W + col];
-                if (a.update == DTS_UPDATE_JACOBI) {
-                    const float den = a.lambda + cf;
-                    gb = den != 0.f ? a.lambda / den * g1[j] : 0.f;
-                } else {
-                    gb = a.step * a.lambda * g1[j];
-                }
-            }
-            G[j] = gb;
-        } else {
-            G[j] = ok ? a.gin[idx] : 0.f;
-        }
+        G[j] = ok ? a.gin[idx] : 0.f;
     }
     float wn;
     {
@@ -251,29 +272,27 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_bloc
     if constexpr (FOLD) col_exchange<M, 16>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
     else col_exchange_scan<M, 16>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
     release_successor();
+    if (CHUNKED && a.chunk_mode == 1) {
+        // this chunk's totals: the inclusive prefix at its last segment, the inclusive suffix at
+        // its first
+        if (col_ok && rank == CS - 1 && warp == NW - 1) store_tot_pre(a, chunk, col, M::pre_compose(pre, own_pre));
+        if (col_ok && rank == 0 && warp == 0) store_tot_suf(a, chunk, col, M::suf_compose(own_suf, suf));
+        cluster_exit();
+        return;
+    }
+    if (CHUNKED && a.chunk_mode == 2 && col_ok) {
+        M::Pre ep = M::pre_identity();
+        for (int c = 0; c < chunk; ++c) ep = M::pre_compose(ep, load_tot_pre(a, c, col));
+        M::Suf es = M::suf_identity();
+        for (int c = a.nchunks - 1; c > chunk; --c) es = M::suf_compose(load_tot_suf(a, c, col), es);
+        pre = M::pre_compose(ep, pre);
+        suf = M::suf_compose(suf, es);
+    }
     const float jin = pre.jk.B;
     const float kin = k_entering(suf.jk, fmaf(own_pre.jk.A, jin, own_pre.jk.B));
     const float hin = pre.hg.B;
     const float gin = k_entering(suf.hg, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
     float K[ITEMS];
-    float zbar[UPDATE ? ITEMS : 1];
-    if constexpr (UPDATE) {
-        // the Jacobi confidence gradient needs zbar = this pass's output: sweep it once more
-        float J = jin;
-        float Jv[ITEMS];
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            J = fmaf(w[j], J - x[j], x[j]);
-            Jv[j] = J;
-        }
-        float Kc = kin;
-#pragma unroll
-        for (int j = ITEMS - 1; j >= 0; --j) {
-            const float wp = (j + 1 < ITEMS) ? w[j + 1] : wn;
-            Kc = fmaf(wp, Kc - Jv[j], Jv[j]);
-            zbar[j] = Kc;
-        }
-    }
     segment_adjoint(x, w, wn, G, K, jin, kin, hin, gin, a.lna);
 
 #pragma unroll
@@ -283,31 +302,6 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_bloc
         const long long idx = (long long)r * P + col;
         a.dbar[idx] += K[j];
         a.gout[idx] = x[j];
-        if constexpr (UPDATE) {
-            const long long di = (long long)r * a.W + col;
-            const float g = g1[j];
-            const float cf = a.c[di];
-            const float t = load_any(a.t, di, a.t_dtype);
-            float dt, dc, dz;
-            if (a.update == DTS_UPDATE_JACOBI) {
-                const float den = a.lambda + cf;
-                if (den != 0.f) {
-                    dt = cf / den * g;
-                    dc = a.lambda * (t - zbar[j]) / (den * den) * g;
-                    dz = 0.f;
-                } else {
-                    dt = dc = 0.f;
-                    dz = g;
-                }
-            } else {
-                dt = a.step * cf * g;
-                dc = a.step * (t - a.zk[idx]) * g;
-                dz = (1.f - a.step * a.lambda - a.step * cf) * g;
-            }
-            if (a.gt) a.gt[di] += dt;
-            if (a.gc) a.gc[di] += dc;
-            a.gz[idx] = dz;
-        }
     }
     cluster_exit();
 }
@@ -407,20 +401,33 @@ cudaError_t launch_row_bwd_t(const BwdArgs& a, bool final_pass, const RowPlan& p
 }
 
 template <int ITEMS, bool DHALF>
-cudaError_t launch_col_bwd_t(const BwdArgs& a, bool update, const ColPlan& p, cudaStream_t s) {
-    const dim3 grid((unsigned)((a.W + 31) / 32), (unsigned)p.cluster, 1);
+cudaError_t launch_col_bwd_t(const BwdArgs& a, const ColPlan& p, cudaStream_t s) {
+    const int rows = ITEMS * p.warps * p.cluster;  // one chunk
+    const int nch = (a.H + rows - 1) / rows;
+    const dim3 grid((unsigned)((a.W + 31) / 32), (unsigned)(p.cluster * nch), 1);
     const dim3 block((unsigned)(32 * p.warps));
     static const bool fold = getenv("DTS_BWD_FOLD") != nullptr;  // tuning aid
-    if (update) return launch_ex(col_bwd_kernel<ITEMS, DHALF, true>, grid, block, p.cluster, s, a);
-    if (fold) return launch_ex(col_bwd_kernel<ITEMS, DHALF, false, true>, grid, block, p.cluster, s, a);
-    return launch_ex(col_bwd_kernel<ITEMS, DHALF, false>, grid, block, p.cluster, s, a);
+    if (nch == 1) {
+        auto kernel = fold ? col_bwd_kernel<ITEMS, DHALF, true> : col_bwd_kernel<ITEMS, DHALF, false>;
+        BwdArgs b = a;
+        b.chunk_mode = 0;
+        return launch_ex(kernel, grid, block, p.cluster, s, b);
+    }
+    if (!a.tot || a.tot_chunks < nch) return cudaErrorInvalidValue;
+    auto kernel = col_bwd_kernel<ITEMS, DHALF, false, true>;
+    BwdArgs b = a;
+    b.nchunks = nch;
+    b.chunk_mode = 1;
+    cudaError_t e = launch_ex(kernel, grid, block, p.cluster, s, b);
+    if (e != cudaSuccess) return e;
+    b.chunk_mode = 2;
+    return launch_ex(kernel, grid, block, p.cluster, s, b);
 }
 
 template <int ITEMS, bool DHALF>
 cudaError_t allow_bwd_clusters() {
     cudaError_t e = cudaSuccess;
-    const void* fs[3] = {(const void*)col_bwd_kernel<ITEMS, DHALF, true>,
-                         (const void*)col_bwd_kernel<ITEMS, DHALF, false>,
+    const void* fs[3] = {(const void*)col_bwd_kernel<ITEMS, DHALF, false>, (const void*)col_bwd_kernel<ITEMS, DHALF, true>,
                          (const void*)col_bwd_kernel<ITEMS, DHALF, false, true>};
     for (const void* f : fs) {
         const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -431,11 +438,12 @@ cudaError_t allow_bwd_clusters() {
 
 }  // namespace
 
-// Backward plans: 8 positions per thread (five arrays of them live at once).
+// Backward plans: 8 positions per thread (five arrays of them live at once), 16 for rows over
+// 8192 (up to 10240).
 bool plan_rows_bwd(int W, RowPlan* p) {
-    const int items = 8;
+    const int items = W <= 8192 ? 8 : 16;
     int tpr = (W + items - 1) / items;
-    if (tpr > 1024) return false;
+    if (tpr > (items <= 8 ? 1024 : 640)) return false;
     tpr = (tpr + 31) / 32 * 32;
     int rpb = 256 / tpr;
     if (rpb < 1) rpb = 1;
@@ -445,7 +453,8 @@ bool plan_rows_bwd(int W, RowPlan* p) {
     return true;
 }
 
-// Backward vertical plan (CTA at most bwd_col_max_threads): columns up to 4096 rows.
+// Backward vertical plan (CTA at most bwd_col_max_threads): one cluster for columns up to 4096
+// rows, chunks of 2048 rows above (bwd_col_chunks).
 bool plan_cols_bwd(int H, ColPlan* p) {
     // DTS_BWD_COL_PLAN="items,warps" overrides the shape (tuning aid)
     static const char* env = getenv("DTS_BWD_COL_PLAN");
@@ -484,6 +493,13 @@ bool plan_cols_bwd(int H, ColPlan* p) {
             }
         }
     }
+    // taller columns: chunks of 2048 rows (16 x 16 x 8), two launches per pass
+    if (H <= kBwdMaxRows) {
+        p->items = 16;
+        p->warps = 16;
+        p->cluster = 8;
+        return true;
+    }
     return false;
 }
 
@@ -492,16 +508,25 @@ cudaError_t launch_row_bwd(const BwdArgs& a, int dist_half, bool final_pass, con
                              dist_half ? kFlagDistHalf : 0, s);
     cudaError_t e = cudaErrorInvalidValue;
     if (p.items == 8) e = dist_half ? launch_row_bwd_t<8, true>(a, final_pass, p, s) : launch_row_bwd_t<8, false>(a, final_pass, p, s);
+    if (p.items == 16)
+        e = dist_half ? launch_row_bwd_t<16, true>(a, final_pass, p, s) : launch_row_bwd_t<16, false>(a, final_pass, p, s);
     prof_end(h, s);
     return e;
 }
 
-cudaError_t launch_col_bwd(const BwdArgs& a, int dist_half, bool update, const ColPlan& p, cudaStream_t s) {
-    const int h = prof_begin(update ? KID_COL_BWD_UPDATE : KID_COL_BWD, (long long)a.H * a.W,
-                             (dist_half ? kFlagDistHalf : 0) | (update && a.t_dtype != DTS_F32 ? kFlagTarget16 : 0), s);
+int bwd_col_chunks(int H) {
+    ColPlan p;
+    if (!plan_cols_bwd(H, &p)) return 0;
+    const int rows = p.items * p.warps * p.cluster;
+    const int n = (H + rows - 1) / rows;
+    return n > 1 ? n : 0;
+}
+
+cudaError_t launch_col_bwd(const BwdArgs& a, int dist_half, const ColPlan& p, cudaStream_t s) {
+    const int h = prof_begin(KID_COL_BWD, (long long)a.H * a.W, dist_half ? kFlagDistHalf : 0, s);
     cudaError_t e = cudaErrorInvalidValue;
-    if (p.items == 8) e = dist_half ? launch_col_bwd_t<8, true>(a, update, p, s) : launch_col_bwd_t<8, false>(a, update, p, s);
-    if (p.items == 16) e = dist_half ? launch_col_bwd_t<16, true>(a, update, p, s) : launch_col_bwd_t<16, false>(a, update, p, s);
+    if (p.items == 8) e = dist_half ? launch_col_bwd_t<8, true>(a, p, s) : launch_col_bwd_t<8, false>(a, p, s);
+    if (p.items == 16) e = dist_half ? launch_col_bwd_t<16, true>(a, p, s) : launch_col_bwd_t<16, false>(a, p, s);
     prof_end(h, s);
     return e;
 }

@@ -133,6 +133,12 @@ struct BwdArgs {
     float* gc;              // += dL/dc (dense, may be null)
     float lambda, step;
     int update;
+    // columns taller than one cluster (vertical adjoint in chunks): chunk_mode 0 single chunk,
+    // 1 write chunk totals, 2 apply with the totals of the other chunks; tot holds tot_chunks
+    // chunks of 14 planes of tot_pitch floats
+    int chunk_mode, nchunks, tot_chunks;
+    float* tot;
+    long long tot_pitch;
 };
 
 struct GuideGradArgs {
@@ -229,7 +235,11 @@ bool use_col_split();
 bool plan_rows_bwd(int W, RowPlan* p);
 bool plan_cols_bwd(int H, ColPlan* p);
 cudaError_t launch_row_bwd(const BwdArgs& a, int dist_half, bool final_pass, const RowPlan& p, cudaStream_t s);
-cudaError_t launch_col_bwd(const BwdArgs& a, int dist_half, bool update, const ColPlan& p, cudaStream_t s);
+cudaError_t launch_col_bwd(const BwdArgs& a, int dist_half, const ColPlan& p, cudaStream_t s);
+// tallest column of the backward (the forward's limit) and the chunks a column of H rows takes
+// in the vertical adjoint (0: one cluster holds it)
+constexpr int kBwdMaxRows = 10240;
+int bwd_col_chunks(int H);
 cudaError_t launch_guide_grad(const GuideGradArgs& a, cudaStream_t s);
 cudaError_t launch_update_adjoint(const BwdArgs& a, cudaStream_t s);
 cudaError_t launch_axpy_plane(const float* src, long long sp, float* dst, long long dp, int H, int W, int accumulate,

@@ -70,6 +70,26 @@ def test_backward_shapes(H, W):
     run_case(H, W, seed=H * 31 + W)
 
 
+# columns over 4096 rows: the vertical adjoint runs in chunks of 2048 rows (two launches, chunk
+# totals composed across chunks); rows over 8192: 16 positions per thread in the row adjoint
+@pytest.mark.parametrize("H,W,update", [(4500, 40, dts.UPDATE_GD), (9000, 9, dts.UPDATE_JACOBI),
+                                        (5, 9000, dts.UPDATE_GD), (3, 10240, dts.UPDATE_JACOBI)])
+def test_backward_tall_and_wide(H, W, update):
+    run_case(H, W, K=2, update=update, seed=H + W)
+
+
+def test_backward_limits():
+    # rows over 10240 have no backward plan; the forward still runs
+    dev()
+    prm = dts.Params(iterations=1, save_checkpoints=1)
+    g = torch.zeros((3, 2, 10300), device=dev())
+    t = torch.zeros((2, 10300), device=dev())
+    ws = dts.workspace(g, prm, with_backward=True)
+    dts.dts_solve(g, t, t, prm, ws=ws)
+    with pytest.raises(RuntimeError):
+        dts.dts_solve_backward(g, t, t, prm, ws, t)
+
+
 @pytest.mark.parametrize("update,norm,zinit", [(dts.UPDATE_JACOBI, dts.NORM_L1, False),
                                                (dts.UPDATE_GD, dts.NORM_L2, False),
                                                (dts.UPDATE_JACOBI, dts.NORM_L2, True),
