@@ -207,12 +207,15 @@ class Case:
         self.s_io = 2 if args.storage == "bf16" else 4
         self.prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, step=q.step, iterations=q.iterations,
                               passes=q.passes, dist_dtype=dts.F16 if self.s_d == 2 else dts.F32,
-                              save_checkpoints=1 if self.bwd else 0)
+                              save_checkpoints=0)
         probs = self.wl.problems
         self.mp = sum(p.target.size for p in probs) / 1e6
         self.g = [torch.from_numpy(p.guide).to(dev).to(self.sdt) for p in probs]
         self.t = [torch.from_numpy(p.target).to(dev).to(self.sdt) for p in probs]
         self.c = [torch.from_numpy(p.conf).to(dev) for p in probs]
+        if self.bwd:  # what the autograd path picks: every pass input kept when memory allows
+            big = max(range(len(probs)), key=lambda i: probs[i].target.size)
+            self.prm.save_checkpoints = dts.backward_checkpoint_mode(self.g[big], self.prm)
         self.out = [torch.empty(p.target.shape, dtype=torch.float32, device=dev) for p in probs]
         rng = np.random.default_rng(77)
         self.gz = [torch.from_numpy(rng.standard_normal(p.target.shape).astype(np.float32)).to(dev) for p in probs] \
@@ -258,6 +261,8 @@ class Case:
                 "iterations": q.iterations, "passes": q.passes, "megapixels_per_step": round(self.mp, 6),
                 "direction": self.args.direction, "storage": self.args.storage,
                 "distance_storage": self.args.dist_dtype, "l2": "flushed between steps (512 MiB write)",
+                "backward_checkpoints": ({1: "iterates (pass inputs recomputed)", 2: "every pass input"}
+                                         .get(self.prm.save_checkpoints) if self.bwd else None),
                 "parallelism": f"replicas x{world}"}
 
     def cpu_sample(self):

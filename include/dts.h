@@ -77,8 +77,12 @@ typedef struct dts_guide {
  *  conf_mode   DTS_CONF_PLAIN (c as given) or DTS_CONF_SUPPORT (c weighted by
  *              S_flat / sum_j W_ij, §3.1 after Eq. 6)
  *  dist_dtype  storage of the distance planes: DTS_F32 or DTS_F16
- *  save_checkpoints  1: dts_solve keeps z_0 .. z_{K-1} in the workspace for
- *              dts_solve_backward (workspace sized with with_backward = 1) */
+ *  save_checkpoints  0: nothing kept; 1: dts_solve keeps z_0 .. z_{K-1} in the
+ *              workspace for dts_solve_backward (workspace sized with with_backward = 1),
+ *              which recomputes each iteration's pass inputs from them; 2: it also keeps
+ *              every pass input and the filtered iterate of every iteration (K x 2N more
+ *              planes: the passes write them instead of overwriting one plane, at no extra
+ *              traffic), so the backward skips the recompute */
 typedef struct dts_params {
     float lambda, sigma_s, sigma_r, step;
     int iterations, passes;

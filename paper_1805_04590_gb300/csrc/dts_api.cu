@@ -87,6 +87,7 @@ int check_params(const dts_params* p) {
     if (p->update != DTS_UPDATE_GD && p->update != DTS_UPDATE_JACOBI) return DTS_ERR_INVALID_ARG;
     if (p->conf_mode != DTS_CONF_PLAIN && p->conf_mode != DTS_CONF_SUPPORT) return DTS_ERR_INVALID_ARG;
     if (p->dist_dtype != DTS_F32 && p->dist_dtype != DTS_F16) return DTS_ERR_INVALID_ARG;
+    if (p->save_checkpoints < 0 || p->save_checkpoints > 2) return DTS_ERR_INVALID_ARG;
     return DTS_OK;
 }
 
@@ -100,6 +101,7 @@ struct Layout {
     long long agg_pitch, agg_plane;
     int nstrips128;
     int z_planes;       // 1 (in place) or K checkpoints
+    size_t passes;      // save_checkpoints = 2: K x 2N planes, (k, 0) = zbar_k, (k, q) = input of pass q
     size_t fwd_end;     // bytes used by the forward
     // backward scratch
     size_t xin;         // 2N pass-input planes
@@ -133,9 +135,12 @@ Layout make_layout(int H, int W, const dts_params* p, int with_backward) {
     const bool keep = p->save_checkpoints || with_backward;
     L.z_planes = keep ? (p->iterations > 0 ? p->iterations : 1) : 1;
     off += (size_t)L.z_planes * L.plane_f32;
+    L.passes = off;
+    if (p->save_checkpoints == 2) off += (size_t)(p->iterations > 0 ? p->iterations : 1) * 2 * p->passes * L.plane_f32;
     L.fwd_end = off;
     if (with_backward) {
-        L.xin = off; off += (size_t)(2 * p->passes) * L.plane_f32;
+        // recompute scratch for the pass inputs (not needed when the forward kept them all)
+        L.xin = off; off += (p->save_checkpoints == 2 ? 0 : (size_t)(2 * p->passes)) * L.plane_f32;
         L.g0 = off; off += L.plane_f32;
         L.g1 = off; off += L.plane_f32;
         L.gz = off; off += L.plane_f32;
@@ -286,6 +291,14 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
     const int dh = p->dist_dtype == DTS_F16;
     float* u = reinterpret_cast<float*>(ws_at(ws, L.u));
     const float* cplane = support ? reinterpret_cast<const float*>(ws_at(ws, L.chat)) : conf;
+    // save_checkpoints = 2: every pass reads and writes its own plane of iteration k (the
+    // backward then reads the pass inputs instead of recomputing them); else all passes run in
+    // place on u
+    const bool keep_passes = p->save_checkpoints == 2;
+    const int NP = 2 * p->passes;
+    auto pslot = [&](int k, int q) -> float* {
+        return keep_passes ? reinterpret_cast<float*>(ws_at(ws, L.passes + ((size_t)k * NP + q) * L.plane_f32)) : u;
+    };
     auto set_update = [&](PassArgs& a, const float* zk) {
         a.zk = zk;
         a.t = target;
@@ -309,22 +322,22 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
         float* zin = zslot(k);
         for (int i = 0; i < p->passes; ++i) {
             PassArgs r = base_pass(g, L);
-            r.src = i == 0 ? zin : u;
-            r.dst = u;
+            r.src = i == 0 ? zin : pslot(k, 2 * i);
+            r.dst = pslot(k, 2 * i + 1);
             r.d = ws_at(ws, L.dX);
             r.k2 = k2[i];
             int rkind = PASS_PLAIN;
             if (row_update && i == 0 && k > 0) {
                 rkind = PASS_UPDATE_ROW;
-                r.src = u;  // zbar of iteration k - 1
+                r.src = pslot(k - 1, 0);  // zbar of iteration k - 1
                 set_update(r, zslot(k - 1));
                 r.zout = zin;  // z_k
                 r.zout_pitch = L.pitch;
             }
             if ((st = cuda_status(launch_row_pass(r, dh, rkind, rkind == PASS_UPDATE_ROW ? urows : pl.rows, s)))) return st;
             PassArgs c = base_pass(g, L);
-            c.src = u;
-            c.dst = u;
+            c.src = pslot(k, 2 * i + 1);
+            c.dst = pslot(k, (2 * i + 2) % NP);
             c.d = ws_at(ws, L.dY);
             c.k2 = k2[i];
             int kind = PASS_PLAIN;
@@ -344,7 +357,7 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
     }
     if (row_update) {
         PassArgs a = base_pass(g, L);
-        a.src = u;
+        a.src = pslot(K - 1, 0);
         set_update(a, zslot(K - 1));
         a.zout = z_out;
         a.zout_pitch = W;
@@ -809,6 +822,7 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
     if (st) return st;
     if (!target || !conf || !grad_z || !valid_dtype(target_dtype)) return DTS_ERR_INVALID_ARG;
     if (params->conf_mode != DTS_CONF_PLAIN) return DTS_ERR_UNSUPPORTED;
+    if (params->save_checkpoints == 0) return DTS_ERR_INVALID_ARG;  // the forward kept no iterates
     Plans pl;
     if ((st = make_plans(guide->H, guide->W, &pl))) return st;
     RowPlan rb;
@@ -837,13 +851,18 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
     float* U[2 * kMaxPasses];
     for (int p = 1; p < 2 * N; ++p) U[p] = plane(L.xin + (size_t)p * L.plane_f32);
     float* gbuf[2] = {plane(L.g0), plane(L.g1)};
+    const bool kept = params->save_checkpoints == 2;
     for (int k = K - 1; k >= 0; --k) {
         U[0] = plane(L.z + (size_t)k * L.plane_f32);
-        // recompute the inputs of passes 1 .. 2N-1 from the checkpoint z_k; for Jacobi also zbar
-        // (the last pass's output, needed by the confidence gradient) into the free slot 0
         const bool jacobi = params->update == DTS_UPDATE_JACOBI;
         float* zbar = plane(L.xin);
-        for (int p = 0; p < 2 * N; ++p) {
+        if (kept) {  // the forward kept every pass input of iteration k, and zbar_k
+            for (int p = 1; p < 2 * N; ++p) U[p] = plane(L.passes + ((size_t)k * 2 * N + p) * L.plane_f32);
+            zbar = plane(L.passes + (size_t)k * 2 * N * L.plane_f32);
+        }
+        // else recompute the inputs of passes 1 .. 2N-1 from the checkpoint z_k; for Jacobi also
+        // zbar (the last pass's output, needed by the confidence gradient) into the free slot 0
+        for (int p = 0; p < 2 * N && !kept; ++p) {
             if (p + 1 == 2 * N && !jacobi) break;
             PassArgs a = base_pass(guide, L);
             a.src = U[p];

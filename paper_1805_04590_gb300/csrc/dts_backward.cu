@@ -44,14 +44,13 @@ struct BackwardMode {
     }
 };
 
-// Replays one segment given its carries; on return x holds dL/dx and db holds ln(a) w dL/dw.
+// Replays one segment given its carries; on return x holds dL/dx and G holds ln(a) w dL/dw.
 // jin: J entering from the left, kin: K entering from the right, hin: h entering from the left,
-// gin: gJ entering from the right.  On return K holds the recomputed pass output.
+// gin: gJ entering from the right.  Four arrays stay live: x (then dL/dx), w, J, G (then h, then
+// the weight gradient); K is recomputed in the right-to-left sweep, where it is consumed.
 template <int N>
 __device__ __forceinline__ void segment_adjoint(float (&x)[N], const float (&w)[N], float wn, float (&G)[N],
-                                                float (&K)[N], float jin, float kin, float hin, float gin,
-                                                float lna) {
-    // live arrays: x (then dL/dx), w, J, K (then the weight gradient), G (then h)
+                                                float jin, float kin, float hin, float gin, float lna) {
     float J[N];
     float v = jin;
 #pragma unroll
@@ -59,28 +58,22 @@ __device__ __forceinline__ void segment_adjoint(float (&x)[N], const float (&w)[
         v = fmaf(w[j], v - x[j], x[j]);
         J[j] = v;
     }
-    v = kin;
-#pragma unroll
-    for (int j = N - 1; j >= 0; --j) {
-        const float wp = (j + 1 < N) ? w[j + 1] : wn;
-        v = fmaf(wp, v - J[j], J[j]);
-        K[j] = v;
-    }
     float hp = hin;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-        const float Jp = j ? J[j - 1] : jin;
-        K[j] = hp * (K[j] - Jp);  // h[n-1] (K[n] - J[n-1]), the anti-causal share of dL/dw_n
         hp = fmaf(w[j], hp, G[j]);
-        G[j] = hp;
+        G[j] = hp;  // h[j]
     }
-    float g = gin;
+    float K = kin, g = gin;
 #pragma unroll
     for (int j = N - 1; j >= 0; --j) {
         const float wp = (j + 1 < N) ? w[j + 1] : wn;
+        K = fmaf(wp, K - J[j], J[j]);
         g = fmaf(wp, g - G[j], G[j]);  // (1 - w') h + w' g
         const float Jp = j ? J[j - 1] : jin;
-        K[j] = lna * w[j] * fmaf(g, Jp - x[j], K[j]);
+        const float hprev = j ? G[j - 1] : hin;
+        const float t1 = hprev * (K - Jp);  // h[n-1] (K[n] - J[n-1]), the anti-causal share of dL/dw_n
+        G[j] = lna * w[j] * fmaf(g, Jp - x[j], t1);
         x[j] = fmaf(-w[j], g, g);  // (1 - w) g
     }
 }
@@ -154,9 +147,8 @@ __global__ void __launch_bounds__(row_bwd_max_threads<ITEMS>()) row_bwd_kernel(B
     const float kin = k_entering(suf.jk, fmaf(own_pre.jk.A, jin, own_pre.jk.B));
     const float hin = pre.hg.B;
     const float gin = k_entering(suf.hg, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
-    float K[ITEMS];
-    segment_adjoint(x, w, wn, G, K, jin, kin, hin, gin, a.lna);
-    const float(&db)[ITEMS] = K;
+    segment_adjoint(x, w, wn, G, jin, kin, hin, gin, a.lna);
+    const float(&db)[ITEMS] = G;
 
     if (live) {
 #pragma unroll
@@ -292,15 +284,14 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_bloc
     const float kin = k_entering(suf.jk, fmaf(own_pre.jk.A, jin, own_pre.jk.B));
     const float hin = pre.hg.B;
     const float gin = k_entering(suf.hg, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
-    float K[ITEMS];
-    segment_adjoint(x, w, wn, G, K, jin, kin, hin, gin, a.lna);
+    segment_adjoint(x, w, wn, G, jin, kin, hin, gin, a.lna);
 
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int r = row0 + j;
         if (!(col_ok && r < a.H)) continue;
         const long long idx = (long long)r * P + col;
-        a.dbar[idx] += K[j];
+        a.dbar[idx] += G[j];
         a.gout[idx] = x[j];
     }
     cluster_exit();

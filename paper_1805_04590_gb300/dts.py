@@ -323,7 +323,7 @@ def dts_solve_backward(guide: torch.Tensor, target: torch.Tensor, conf: torch.Te
                        need_guide: bool = True, stream=None):
     """Gradients (target, conf, guide or None, z_init or None) given dL/dz_K.
 
-    Must follow ``dts_solve`` with ``save_checkpoints=1`` on the same workspace."""
+    Must follow ``dts_solve`` with ``save_checkpoints`` 1 or 2 on the same workspace."""
     _need_cuda(guide, target, conf, grad_z, z_init)
     _dense(grad_z, "grad_z")
     g = guide_desc(guide)
@@ -367,17 +367,28 @@ def version() -> str:
     return load().dts_version().decode()
 
 
+def backward_checkpoint_mode(guide: torch.Tensor, params: Params) -> int:
+    """save_checkpoints for a solve that will be differentiated: 2 (keep every pass input,
+    no recompute in the backward) when its workspace takes at most a quarter of the free
+    device memory, else 1 (keep the iterates only)."""
+    g = guide_desc(guide)
+    p2 = dataclasses.replace(params, save_checkpoints=2).c()
+    need = load().dts_workspace_size(ctypes.byref(g), ctypes.byref(p2), 1)
+    free, _ = torch.cuda.mem_get_info(guide.device)
+    return 2 if need and need <= free // 4 else 1
+
+
 class DTSSolve(torch.autograd.Function):
     """z_K = dts_solve(guide, target, conf, z_init) with the hand-written CUDA backward.
 
-    The forward keeps the iterates z_0 .. z_{K-1} in its workspace; the backward
-    (dts_solve_backward) recomputes each iteration's pass inputs from them and runs the
-    reversed recurrences, giving gradients for the target, the confidence, the guide
-    (through the distances) and z_init."""
+    The forward keeps every pass input in its workspace when memory allows (else the
+    iterates z_0 .. z_{K-1}, from which the backward recomputes the pass inputs); the
+    backward (dts_solve_backward) runs the reversed recurrences, giving gradients for the
+    target, the confidence, the guide (through the distances) and z_init."""
 
     @staticmethod
     def forward(ctx, guide, target, conf, z_init, params: Params):
-        p = dataclasses.replace(params, save_checkpoints=1)
+        p = dataclasses.replace(params, save_checkpoints=backward_checkpoint_mode(guide, params))
         ws = workspace(guide, p, with_backward=True)
         z = dts_solve(guide, target, conf, p, z_init=z_init, ws=ws)
         zi = z_init if z_init is not None else torch.empty(0, device=target.device)

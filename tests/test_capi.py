@@ -60,6 +60,13 @@ def test_workspace_size_layout():
     assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p16), 0) == 2 * (40 * pitch * 2) + 2 * plane + split
     bad = dts.Params(sigma_s=-1.0).c()
     assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(bad), 0) == 0
+    # save_checkpoints = 2: K x 2N planes of kept pass inputs in the forward part, no recompute
+    # planes in the backward part
+    p2 = dts.Params(iterations=5, save_checkpoints=2).c()
+    assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p2), 1) == n1 + (5 * 6 - 6) * plane
+    assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p2), 0) == n0 + (5 - 1 + 5 * 6) * plane
+    p3 = dts.Params(save_checkpoints=3).c()
+    assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p3), 0) == 0
 
 
 @pytest.mark.parametrize("field,value", [("sigma_s", 0.0), ("sigma_r", -1.0), ("lam", -0.5), ("step", 0.0),

@@ -36,7 +36,7 @@ def close(gpu, ref, what):
 
 
 def run_case(H, W, C=3, K=4, update=dts.UPDATE_GD, norm=dts.NORM_L1, zinit=False, seed=0, passes=3,
-             sigma_s=8.0, sigma_r=0.3, dist=dts.F32):
+             sigma_s=8.0, sigma_r=0.3, dist=dts.F32, keep=1):
     rng = np.random.default_rng(seed)
     I = guide_noisy(H, W, C, seed)
     t = rng.normal(size=(H, W)).astype(np.float32)
@@ -44,7 +44,7 @@ def run_case(H, W, C=3, K=4, update=dts.UPDATE_GD, norm=dts.NORM_L1, zinit=False
     gz = rng.normal(size=(H, W)).astype(np.float32)
     z0 = rng.normal(size=(H, W)).astype(np.float32) if zinit else None
     prm = dts.Params(lam=0.9, sigma_s=sigma_s, sigma_r=sigma_r, iterations=K, passes=passes, update=update,
-                     norm=norm, dist_dtype=dist, save_checkpoints=1)
+                     norm=norm, dist_dtype=dist, save_checkpoints=keep)
     g, tt, cc = T(I), T(t), T(c)
     zi = T(z0) if zinit else None
     ws = dts.workspace(g, prm, with_backward=True)
@@ -68,6 +68,27 @@ def run_case(H, W, C=3, K=4, update=dts.UPDATE_GD, norm=dts.NORM_L1, zinit=False
 @pytest.mark.parametrize("H,W", [(1, 1), (1, 23), (29, 1), (17, 31), (64, 80), (130, 70), (45, 300), (300, 45)])
 def test_backward_shapes(H, W):
     run_case(H, W, seed=H * 31 + W)
+
+
+@pytest.mark.parametrize("update", [dts.UPDATE_GD, dts.UPDATE_JACOBI])
+def test_backward_kept_pass_inputs(update):
+    """save_checkpoints = 2 (every pass input kept, no recompute) gives the same forward and
+    the same gradients, bit for bit, as save_checkpoints = 1 (recompute from the iterates)."""
+    a = run_case(90, 130, K=3, update=update, seed=21 + update, keep=2)
+    b = run_case(90, 130, K=3, update=update, seed=21 + update, keep=1)
+    for x, y in zip(a[:5], b[:5]):
+        if x is not None:
+            assert torch.equal(x, y)
+
+
+def test_backward_needs_kept_iterates():
+    dev()
+    prm = dts.Params(iterations=2)
+    g = torch.rand((3, 20, 30), device=dev())
+    t = torch.rand((20, 30), device=dev())
+    ws = dts.workspace(g, prm, with_backward=True)
+    with pytest.raises(RuntimeError):
+        dts.dts_solve_backward(g, t, t, prm, ws, t)
 
 
 # columns over 4096 rows: the vertical adjoint runs in chunks of 2048 rows (two launches, chunk
