@@ -57,9 +57,9 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4):
         "row_pass_kernel<update>": 20 + s_t + s_d,
         "update_kernel": 16 + s_t,
         "col_agg_kernel": 4 + s_d,
-        "row_bwd_kernel": 20 + s_d,
-        "row_bwd_kernel<final>": 24 + s_d,
-        "col_bwd_kernel": 20 + s_d,
+        "row_bwd_kernel": 24 + s_d,
+        "row_bwd_kernel<final>": 28 + s_d,
+        "col_bwd_kernel": 24 + s_d,
         "col_bwd_kernel<update>": 48 + s_d + s_t,
         "guide_grad_kernel": C * s_g + 2 * s_d + 8 + 4 * C,
         "axpy_plane_kernel": 12,

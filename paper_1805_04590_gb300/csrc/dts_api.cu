@@ -148,7 +148,7 @@ Layout make_layout(int H, int W, const dts_params* p, int with_backward) {
         L.dYb = off; off += L.plane_f32;
         L.tot_chunks = bwd_col_chunks(H);
         L.tot = off;
-        off += align_up((size_t)L.tot_chunks * 14 * (size_t)L.pitch * sizeof(float), kPlaneAlign);
+        off += align_up((size_t)L.tot_chunks * 9 * (size_t)L.pitch * sizeof(float), kPlaneAlign);
     }
     L.total = off;
     return L;
@@ -854,16 +854,14 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
     const bool kept = params->save_checkpoints == 2;
     for (int k = K - 1; k >= 0; --k) {
         U[0] = plane(L.z + (size_t)k * L.plane_f32);
-        const bool jacobi = params->update == DTS_UPDATE_JACOBI;
         float* zbar = plane(L.xin);
         if (kept) {  // the forward kept every pass input of iteration k, and zbar_k
             for (int p = 1; p < 2 * N; ++p) U[p] = plane(L.passes + ((size_t)k * 2 * N + p) * L.plane_f32);
             zbar = plane(L.passes + (size_t)k * 2 * N * L.plane_f32);
         }
-        // else recompute the inputs of passes 1 .. 2N-1 from the checkpoint z_k; for Jacobi also
-        // zbar (the last pass's output, needed by the confidence gradient) into the free slot 0
+        // else recompute the inputs of passes 1 .. 2N-1 from the checkpoint z_k, and zbar (the last
+        // pass's output) into the free slot 0
         for (int p = 0; p < 2 * N && !kept; ++p) {
-            if (p + 1 == 2 * N && !jacobi) break;
             PassArgs a = base_pass(guide, L);
             a.src = U[p];
             a.dst = p + 1 < 2 * N ? U[p + 1] : zbar;
@@ -908,6 +906,7 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
             b.lna = (float)((double)k2[p / 2] * log(2.0));
             b.gin = gbuf[cur];
             b.gout = gbuf[cur ^ 1];
+            b.kout = p + 1 < 2 * N ? U[p + 1] : zbar;
             b.gz = gz;
             if (p % 2 == 1) {
                 b.d = ws_at(ws, L.dY);

@@ -8,11 +8,11 @@
 //     gJ[n] = (1 - w_{n+1}) h[n] + w_{n+1} gJ[n+1]       (total gradient of J[n])
 //     dL/dx[n] = (1 - w_n) gJ[n]
 //     dL/dw_n  = gJ[n] (J[n-1] - x[n]) + h[n-1] (K[n] - J[n-1]),   dL/dd_n = ln(a) w_n dL/dw_n.
-// The pair (h, gJ) has the same coupled structure as (J, K) (unnormalised on the way out), so a
-// pass adjoint exchanges TWO coupled five-tuples in one round: one to recompute J and K from the
-// saved pass input, one for the carries of h and gJ.  The last vertical pass of an iteration also
-// takes the adjoint of the data-term update (Eq. 3 or Eq. 4); the first horizontal pass adds the
-// filter's adjoint into the gradient of the iterate.
+// The pass output K is read back (it is the next pass's input, or zbar for the last pass), and J
+// is recomputed from the pass input with its causal map alone; the pair (h, gJ) has the same
+// coupled structure as (J, K) (unnormalised on the way out).  So a pass adjoint exchanges, per
+// segment, two affine maps (J and h left to right) and one coupled five-tuple (h, gJ) in one
+// round.  The first horizontal pass adds the filter's adjoint into the gradient of the iterate.
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -25,55 +25,56 @@ namespace {
 using namespace scan;
 
 struct Pre2 {
-    Aff jk, hg;
-};
-struct Suf2 {
-    Coupled jk, hg;
+    Aff jk, hg;  // causal maps of J and of h
 };
 
 struct BackwardMode {
     using Pre = Pre2;
-    using Suf = Suf2;
+    using Suf = Coupled;  // (h, gJ)
     static __device__ __forceinline__ Pre pre_identity() { return Pre{aff_identity(), aff_identity()}; }
     static __device__ __forceinline__ Pre pre_compose(const Pre& f, const Pre& s) {
         return Pre{aff_compose(f.jk, s.jk), aff_compose(f.hg, s.hg)};
     }
-    static __device__ __forceinline__ Suf suf_identity() { return Suf{coupled_identity(), coupled_identity()}; }
-    static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) {
-        return Suf{coupled_compose(f.jk, s.jk), coupled_compose(f.hg, s.hg)};
-    }
+    static __device__ __forceinline__ Suf suf_identity() { return coupled_identity(); }
+    static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) { return coupled_compose(f, s); }
 };
 
-// Replays one segment given its carries; on return x holds dL/dx and G holds ln(a) w dL/dw.
-// jin: J entering from the left, kin: K entering from the right, hin: h entering from the left,
-// gin: gJ entering from the right.  Four arrays stay live: x (then dL/dx), w, J, G (then h, then
-// the weight gradient); K is recomputed in the right-to-left sweep, where it is consumed.
+// A segment's own transforms: the causal map of J (normalised, on the pass input x), and the
+// coupled transform of (h, gJ) (unnormalised, on G = dL/dK); both share the weight product.
+template <int N>
+__device__ __forceinline__ void adjoint_local(const float (&x)[N], const float (&w)[N], float wn, const float (&G)[N],
+                                              Pre2& pre, Coupled& suf) {
+    suf = coupled_local<false>(G, w, wn);
+    float q = 0.f;
+#pragma unroll
+    for (int j = 0; j < N; ++j) q = fmaf(w[j], q - x[j], x[j]);
+    pre = Pre2{Aff{suf.A, q}, Aff{suf.A, suf.B}};
+}
+
+// Replays one segment given its carries: jin (J entering from the left), hin (h from the left),
+// gin (gJ from the right).  In: x the pass input, G = dL/dK, K the pass output.  Out: x holds
+// dL/dx and G holds ln(a) w dL/dw.  Left to right the sweep forms J and h and the two parts of
+// dL/dw_n that need J[n-1] and h[n-1]: b = J[n-1] - x[n] (into x) and h[n-1] (K[n] - J[n-1])
+// (into K); right to left it forms gJ and finishes both gradients.  Four arrays stay live.
 template <int N>
 __device__ __forceinline__ void segment_adjoint(float (&x)[N], const float (&w)[N], float wn, float (&G)[N],
-                                                float jin, float kin, float hin, float gin, float lna) {
-    float J[N];
-    float v = jin;
+                                                float (&K)[N], float jin, float hin, float gin, float lna) {
+    float Jp = jin, hp = hin;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-        v = fmaf(w[j], v - x[j], x[j]);
-        J[j] = v;
-    }
-    float hp = hin;
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
+        const float J = fmaf(w[j], Jp - x[j], x[j]);
+        K[j] = hp * (K[j] - Jp);
+        x[j] = Jp - x[j];
         hp = fmaf(w[j], hp, G[j]);
         G[j] = hp;  // h[j]
+        Jp = J;
     }
-    float K = kin, g = gin;
+    float g = gin;
 #pragma unroll
     for (int j = N - 1; j >= 0; --j) {
         const float wp = (j + 1 < N) ? w[j + 1] : wn;
-        K = fmaf(wp, K - J[j], J[j]);
         g = fmaf(wp, g - G[j], G[j]);  // (1 - w') h + w' g
-        const float Jp = j ? J[j - 1] : jin;
-        const float hprev = j ? G[j - 1] : hin;
-        const float t1 = hprev * (K - Jp);  // h[n-1] (K[n] - J[n-1]), the anti-causal share of dL/dw_n
-        G[j] = lna * w[j] * fmaf(g, Jp - x[j], t1);
+        G[j] = lna * w[j] * fmaf(g, x[j], K[j]);
         x[j] = fmaf(-w[j], g, g);  // (1 - w) g
     }
 }
@@ -110,12 +111,15 @@ __global__ void __launch_bounds__(row_bwd_max_threads<ITEMS>()) row_bwd_kernel(B
     const bool live = row_ok && e0 < P;
 
     wait_predecessor();
-    float x[ITEMS], w[ITEMS], G[ITEMS];
+    // the distance gradient is read-modified-written at the end: bring its lines into L2 now
+    if (live) prefetch_l2(a.dbar + base);
+    float x[ITEMS], w[ITEMS], G[ITEMS], K[ITEMS];
     if (live) {
 #pragma unroll
         for (int q = 0; q < ITEMS / 4; ++q) {
             load4_f(a.x, base + 4 * q, &x[4 * q]);
             load4_f(a.gin, base + 4 * q, &G[4 * q]);
+            load4_f(a.kout, base + 4 * q, &K[4 * q]);
             load4_d<DHALF>(a.d, base + 4 * q, &w[4 * q]);
         }
 #pragma unroll
@@ -123,12 +127,12 @@ __global__ void __launch_bounds__(row_bwd_max_threads<ITEMS>()) row_bwd_kernel(B
         if (e0 + ITEMS > a.W) {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j)
-                if (e0 + j >= a.W) x[j] = w[j] = G[j] = 0.f;
+                if (e0 + j >= a.W) x[j] = w[j] = G[j] = K[j] = 0.f;
         }
         if (e0 == 0) w[0] = 0.f;
     } else {
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) x[j] = w[j] = G[j] = 0.f;
+        for (int j = 0; j < ITEMS; ++j) x[j] = w[j] = G[j] = K[j] = 0.f;
     }
     float wn = __shfl_down_sync(kFull, w[0], 1);
     if (lane == 31) {
@@ -138,16 +142,13 @@ __global__ void __launch_bounds__(row_bwd_max_threads<ITEMS>()) row_bwd_kernel(B
 
     M::Pre own_pre, pre;
     M::Suf own_suf, suf;
-    own_suf.jk = coupled_local<true>(x, w, wn);
-    own_suf.hg = coupled_local<false>(G, w, wn);
-    own_pre = M::Pre{Aff{own_suf.jk.A, own_suf.jk.B}, Aff{own_suf.hg.A, own_suf.hg.B}};
+    adjoint_local(x, w, wn, G, own_pre, own_suf);
     row_exchange<M>(own_pre, own_suf, lane, warp, wrow, wbase, wpr, s_pre, s_suf, pre, suf);
     release_successor();
     const float jin = pre.jk.B;
-    const float kin = k_entering(suf.jk, fmaf(own_pre.jk.A, jin, own_pre.jk.B));
     const float hin = pre.hg.B;
-    const float gin = k_entering(suf.hg, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
-    segment_adjoint(x, w, wn, G, jin, kin, hin, gin, a.lna);
+    const float gin = k_entering(suf, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
+    segment_adjoint(x, w, wn, G, K, jin, hin, gin, a.lna);
     const float(&db)[ITEMS] = G;
 
     if (live) {
@@ -190,7 +191,7 @@ constexpr int bwd_col_min_blocks() {
 }
 
 // chunk totals in a.tot: plane f of chunk c at (c * kTotFields + f) * tot_pitch
-constexpr int kTotFields = 14;  // prefix: 2 x (A, B); suffix: 2 x (A, B, al, be, ga)
+constexpr int kTotFields = 9;  // prefix: 2 x (A, B); suffix: (A, B, al, be, ga)
 
 __device__ __forceinline__ void store_tot_pre(const BwdArgs& a, int chunk, int col, const Pre2& p) {
     float* t = a.tot + (long long)chunk * kTotFields * a.tot_pitch + col;
@@ -200,22 +201,23 @@ __device__ __forceinline__ void store_tot_pre(const BwdArgs& a, int chunk, int c
     t[2 * q] = p.hg.A;
     t[3 * q] = p.hg.B;
 }
-__device__ __forceinline__ void store_tot_suf(const BwdArgs& a, int chunk, int col, const Suf2& f) {
+__device__ __forceinline__ void store_tot_suf(const BwdArgs& a, int chunk, int col, const Coupled& f) {
     float* t = a.tot + (long long)chunk * kTotFields * a.tot_pitch + col + 4 * a.tot_pitch;
     const long long q = a.tot_pitch;
-    const float v[10] = {f.jk.A, f.jk.B, f.jk.al, f.jk.be, f.jk.ga, f.hg.A, f.hg.B, f.hg.al, f.hg.be, f.hg.ga};
-#pragma unroll
-    for (int i = 0; i < 10; ++i) t[i * q] = v[i];
+    t[0] = f.A;
+    t[q] = f.B;
+    t[2 * q] = f.al;
+    t[3 * q] = f.be;
+    t[4 * q] = f.ga;
 }
 __device__ __forceinline__ Pre2 load_tot_pre(const BwdArgs& a, int chunk, int col) {
     const float* t = a.tot + (long long)chunk * kTotFields * a.tot_pitch + col;
     return Pre2{Aff{t[0], t[a.tot_pitch]}, Aff{t[2 * a.tot_pitch], t[3 * a.tot_pitch]}};
 }
-__device__ __forceinline__ Suf2 load_tot_suf(const BwdArgs& a, int chunk, int col) {
+__device__ __forceinline__ Coupled load_tot_suf(const BwdArgs& a, int chunk, int col) {
     const float* t = a.tot + (long long)chunk * kTotFields * a.tot_pitch + col + 4 * a.tot_pitch;
     const long long q = a.tot_pitch;
-    return Suf2{Coupled{t[0], t[q], t[2 * q], t[3 * q], t[4 * q]},
-                Coupled{t[5 * q], t[6 * q], t[7 * q], t[8 * q], t[9 * q]}};
+    return Coupled{t[0], t[q], t[2 * q], t[3 * q], t[4 * q]};
 }
 
 template <int ITEMS, bool DHALF, bool FOLD = false, bool CHUNKED = false>
@@ -235,7 +237,11 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_bloc
     const long long P = a.pitch;
 
     wait_predecessor();
-    float x[ITEMS], w[ITEMS], G[ITEMS];
+    // the distance gradient is read-modified-written at the end: lane j brings row j of the
+    // warp's rows into L2 now (one 128-byte line per row of the strip)
+    if (lane < ITEMS && row0 + lane < a.H && blockIdx.x * 32 < a.W)
+        prefetch_l2(a.dbar + (long long)(row0 + lane) * P + blockIdx.x * 32);
+    float x[ITEMS], w[ITEMS], G[ITEMS], K[ITEMS];
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int r = row0 + j;
@@ -244,6 +250,7 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_bloc
         x[j] = ok ? a.x[idx] : 0.f;
         w[j] = ok ? load1_d<DHALF>(a.d, idx) : 0.f;
         G[j] = ok ? a.gin[idx] : 0.f;
+        K[j] = ok ? a.kout[idx] : 0.f;
     }
     float wn;
     {
@@ -258,9 +265,7 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_bloc
 
     M::Pre own_pre, pre;
     M::Suf own_suf, suf;
-    own_suf.jk = coupled_local<true>(x, w, wn);
-    own_suf.hg = coupled_local<false>(G, w, wn);
-    own_pre = M::Pre{Aff{own_suf.jk.A, own_suf.jk.B}, Aff{own_suf.hg.A, own_suf.hg.B}};
+    adjoint_local(x, w, wn, G, own_pre, own_suf);
     if constexpr (FOLD) col_exchange<M, 16>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
     else col_exchange_scan<M, 16>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
     release_successor();
@@ -281,10 +286,9 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_bloc
         suf = M::suf_compose(suf, es);
     }
     const float jin = pre.jk.B;
-    const float kin = k_entering(suf.jk, fmaf(own_pre.jk.A, jin, own_pre.jk.B));
     const float hin = pre.hg.B;
-    const float gin = k_entering(suf.hg, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
-    segment_adjoint(x, w, wn, G, jin, kin, hin, gin, a.lna);
+    const float gin = k_entering(suf, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
+    segment_adjoint(x, w, wn, G, K, jin, hin, gin, a.lna);
 
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {

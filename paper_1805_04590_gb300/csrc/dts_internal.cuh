@@ -115,7 +115,8 @@ struct PassArgs {
 struct BwdArgs {
     const float* x;         // the pass input recomputed from the checkpoint (pitch `pitch`)
     const void* d;          // distances along the pass direction
-    const float* gin;       // dL/d(pass output) (not read by the update variant)
+    const float* gin;       // dL/d(pass output)
+    const float* kout;      // the pass output (the next pass's input, or zbar for the last pass)
     float* gout;            // dL/d(pass input)
     float* dbar;            // += dL/d(distances)
     float* gz;              // dL/dz of the iterate (update variant: read then overwritten;
@@ -135,7 +136,7 @@ struct BwdArgs {
     int update;
     // columns taller than one cluster (vertical adjoint in chunks): chunk_mode 0 single chunk,
     // 1 write chunk totals, 2 apply with the totals of the other chunks; tot holds tot_chunks
-    // chunks of 14 planes of tot_pitch floats
+    // chunks of 9 planes of tot_pitch floats
     int chunk_mode, nchunks, tot_chunks;
     float* tot;
     long long tot_pitch;
