@@ -152,19 +152,24 @@ __global__ void __launch_bounds__(row_bwd_max_threads<ITEMS>()) row_bwd_kernel(B
     const float(&db)[ITEMS] = G;
 
     if (live) {
+        // every load before the first store (the stores could alias later loads); K is free again
+#pragma unroll
+        for (int q = 0; q < ITEMS / 4; ++q) load4_f(a.dbar, base + 4 * q, &K[4 * q]);
+        float gz[FINAL ? ITEMS : 1];
+        if constexpr (FINAL) {
+#pragma unroll
+            for (int q = 0; q < ITEMS / 4; ++q) load4_f(a.gz, base + 4 * q, &gz[4 * q]);
+        }
 #pragma unroll
         for (int q = 0; q < ITEMS / 4; ++q) {
             float acc[4];
-            load4_f(a.dbar, base + 4 * q, acc);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] += (e0 + 4 * q + i < a.W) ? db[4 * q + i] : 0.f;
+            for (int i = 0; i < 4; ++i) acc[i] = K[4 * q + i] + ((e0 + 4 * q + i < a.W) ? db[4 * q + i] : 0.f);
             store4_f(a.dbar, base + 4 * q, acc);
             if constexpr (FINAL) {
-                float gz[4];
-                load4_f(a.gz, base + 4 * q, gz);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) gz[i] += x[4 * q + i];
-                store4_f(a.gz, base + 4 * q, gz);
+                for (int i = 0; i < 4; ++i) gz[4 * q + i] += x[4 * q + i];
+                store4_f(a.gz, base + 4 * q, &gz[4 * q]);
             } else {
                 store4_f(a.gout, base + 4 * q, &x[4 * q]);
             }
@@ -290,12 +295,19 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_bloc
     const float gin = k_entering(suf, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
     segment_adjoint(x, w, wn, G, K, jin, hin, gin, a.lna);
 
+    // read every distance-gradient value before the first store (the stores could alias later
+    // loads, which would otherwise wait for them one by one); K is free again
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int r = row0 + j;
+        K[j] = (col_ok && r < a.H) ? a.dbar[(long long)r * P + col] : 0.f;
+    }
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int r = row0 + j;
         if (!(col_ok && r < a.H)) continue;
         const long long idx = (long long)r * P + col;
-        a.dbar[idx] += G[j];
+        a.dbar[idx] = K[j] + G[j];
         a.gout[idx] = x[j];
     }
     cluster_exit();
