@@ -353,38 +353,74 @@ __global__ void __launch_bounds__(256) guide_grad_kernel(GuideGradArgs a) {
 //   Jacobi  dzbar = lambda g / den,  dt += c g / den,  dc += lambda (t - zbar) g / den^2,  a.gz <- 0
 //           (den = lambda + c; where den = 0 the iterate was kept: a.gz <- g and nothing else)
 // dzbar goes to a.gout (the input gradient of the last pass's adjoint); a.x holds zbar (Jacobi).
+// Four consecutive pixels per thread; VEC: 16-byte accesses (W % 4 == 0, aligned planes), else
+// element by element.  Every operand is loaded before the first store.
+template <bool VEC>
 __global__ void __launch_bounds__(256) update_adjoint_kernel(BwdArgs a) {
     wait_predecessor();
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     const int y = blockIdx.y;
-    if (x >= a.W || y >= a.H) return;
-    const long long idx = (long long)y * a.pitch + x;
-    const long long di = (long long)y * a.W + x;
-    const float g = a.gz[idx];
-    const float cf = a.c[di];
-    const float t = load_any(a.t, di, a.t_dtype);
-    float dzb, dt, dc, dz;
-    if (a.update == DTS_UPDATE_JACOBI) {
-        const float den = a.lambda + cf;
-        if (den != 0.f) {
-            dzb = a.lambda / den * g;
-            dt = cf / den * g;
-            dc = a.lambda * (t - a.x[idx]) / (den * den) * g;
-            dz = 0.f;
-        } else {
-            dzb = dt = dc = 0.f;
-            dz = g;
-        }
+    if (x0 >= a.W || y >= a.H) return;
+    const long long idx = (long long)y * a.pitch + x0;
+    const long long di = (long long)y * a.W + x0;
+    const bool jac = a.update == DTS_UPDATE_JACOBI;
+    float g[4], cf[4], t[4], zz[4], gt[4] = {0.f, 0.f, 0.f, 0.f}, gc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (VEC) {
+        load4_f(a.gz, idx, g);
+        load4_f(a.c, di, cf);
+        load4_f(jac ? a.x : a.zk, idx, zz);
+        if (a.gt) load4_f(a.gt, di, gt);
+        if (a.gc) load4_f(a.gc, di, gc);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[k] = load_any(a.t, di + k, a.t_dtype);
     } else {
-        dzb = a.step * a.lambda * g;
-        dt = a.step * cf * g;
-        dc = a.step * (t - a.zk[idx]) * g;
-        dz = (1.f - a.step * a.lambda - a.step * cf) * g;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool ok = x0 + k < a.W;
+            g[k] = ok ? a.gz[idx + k] : 0.f;
+            cf[k] = ok ? a.c[di + k] : 0.f;
+            zz[k] = ok ? (jac ? a.x : a.zk)[idx + k] : 0.f;
+            t[k] = ok ? load_any(a.t, di + k, a.t_dtype) : 0.f;
+            if (a.gt && ok) gt[k] = a.gt[di + k];
+            if (a.gc && ok) gc[k] = a.gc[di + k];
+        }
     }
-    a.gout[idx] = dzb;
-    a.gz[idx] = dz;
-    if (a.gt) a.gt[di] += dt;
-    if (a.gc) a.gc[di] += dc;
+    float dzb[4], dz[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (jac) {
+            const float den = a.lambda + cf[k];
+            if (den != 0.f) {
+                dzb[k] = a.lambda / den * g[k];
+                gt[k] += cf[k] / den * g[k];
+                gc[k] += a.lambda * (t[k] - zz[k]) / (den * den) * g[k];
+                dz[k] = 0.f;
+            } else {
+                dzb[k] = 0.f;
+                dz[k] = g[k];
+            }
+        } else {
+            dzb[k] = a.step * a.lambda * g[k];
+            gt[k] += a.step * cf[k] * g[k];
+            gc[k] += a.step * (t[k] - zz[k]) * g[k];
+            dz[k] = (1.f - a.step * a.lambda - a.step * cf[k]) * g[k];
+        }
+    }
+    if (VEC) {
+        store4_f(a.gout, idx, dzb);
+        store4_f(a.gz, idx, dz);
+        if (a.gt) store4_f(a.gt, di, gt);
+        if (a.gc) store4_f(a.gc, di, gc);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (x0 + k >= a.W) continue;
+            a.gout[idx + k] = dzb[k];
+            a.gz[idx + k] = dz[k];
+            if (a.gt) a.gt[di + k] = gt[k];
+            if (a.gc) a.gc[di + k] = gc[k];
+        }
+    }
 }
 
 // dst[y][x] (pitch dp) += src[y][x] (pitch sp), or = when accumulate is 0
@@ -558,8 +594,12 @@ cudaError_t launch_guide_grad(const GuideGradArgs& a, cudaStream_t s) {
 
 cudaError_t launch_update_adjoint(const BwdArgs& a, cudaStream_t s) {
     const int h = prof_begin(KID_UPDATE_ADJ, (long long)a.H * a.W, a.t_dtype != DTS_F32 ? kFlagTarget16 : 0, s);
-    const dim3 grid((unsigned)((a.W + 255) / 256), (unsigned)a.H);
-    const cudaError_t e = launch_ex(update_adjoint_kernel, grid, dim3(256), 0, s, a);
+    const dim3 grid((unsigned)((a.W + 1023) / 1024), (unsigned)a.H);
+    auto al16 = [](const void* p) { return (uintptr_t)p % 16 == 0; };
+    const bool vec = a.W % 4 == 0 && a.pitch % 4 == 0 && al16(a.gz) && al16(a.c) && al16(a.x) && al16(a.zk) &&
+                     al16(a.gout) && (!a.gt || al16(a.gt)) && (!a.gc || al16(a.gc));
+    const cudaError_t e = vec ? launch_ex(update_adjoint_kernel<true>, grid, dim3(256), 0, s, a)
+                              : launch_ex(update_adjoint_kernel<false>, grid, dim3(256), 0, s, a);
     prof_end(h, s);
     return e;
 }

@@ -322,12 +322,15 @@ __device__ __forceinline__ void load4_t(const PassArgs& a, long long i, bool vec
     }
 }
 
-template <int ITEMS, bool DHALF, int KIND>
+// TWO: the normalised pass as two one-direction exchanges of affine maps (causal, then
+// anti-causal on its result) instead of one exchange of the coupled five numbers.
+template <int ITEMS, bool DHALF, int KIND, bool TWO = false>
 __global__ void __launch_bounds__(row_max_threads<ITEMS, KIND>()) row_pass_kernel(PassArgs a, int tpr) {
     static_assert(ITEMS % 4 == 0, "ITEMS must be a multiple of 4");
     using M = typename std::conditional<KIND == PASS_SUPPORT, SupportMode, CoupledMode>::type;
     __shared__ typename M::Pre s_pre[32];
     __shared__ typename M::Suf s_suf[32];
+    __shared__ Aff s_two[TWO ? 32 : 1];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
@@ -428,12 +431,47 @@ __global__ void __launch_bounds__(row_max_threads<ITEMS, KIND>()) row_pass_kerne
         wn = (row_ok && en < a.W) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)row * P + en)) : 0.f;
     }
 
-    typename M::Pre own_pre, pre;
-    typename M::Suf own_suf, suf;
-    M::local(x, w, wn, own_pre, own_suf);
-    row_exchange<M>(own_pre, own_suf, lane, warp, wrow, wbase, wpr, s_pre, s_suf, pre, suf);
-    release_successor();
-    M::apply(x, w, wn, own_pre, pre.B, suf);
+    if constexpr (TWO && KIND != PASS_SUPPORT) {
+        // causal sweep: segment map c -> A c + B, exclusive prefix, replay
+        float A = 1.f, B = 0.f;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            A *= w[j];
+            B = fmaf(w[j], B - x[j], x[j]);
+        }
+        const Aff pc = row_scan_aff<true>(Aff{A, B}, lane, warp, wrow, wbase, wpr, s_pre);
+        float v = pc.B;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            v = fmaf(w[j], v - x[j], x[j]);
+            x[j] = v;
+        }
+        // anti-causal sweep on the result, weights w' (the next position's)
+        A = 1.f;
+        B = 0.f;
+#pragma unroll
+        for (int j = ITEMS - 1; j >= 0; --j) {
+            const float wp = (j + 1 < ITEMS) ? w[j + 1] : wn;
+            A *= wp;
+            B = fmaf(wp, B - x[j], x[j]);
+        }
+        const Aff sk = row_scan_aff<false>(Aff{A, B}, lane, warp, wrow, wbase, wpr, s_two);
+        release_successor();
+        v = sk.B;
+#pragma unroll
+        for (int j = ITEMS - 1; j >= 0; --j) {
+            const float wp = (j + 1 < ITEMS) ? w[j + 1] : wn;
+            v = fmaf(wp, v - x[j], x[j]);
+            x[j] = v;
+        }
+    } else {
+        typename M::Pre own_pre, pre;
+        typename M::Suf own_suf, suf;
+        M::local(x, w, wn, own_pre, own_suf);
+        row_exchange<M>(own_pre, own_suf, lane, warp, wrow, wbase, wpr, s_pre, s_suf, pre, suf);
+        release_successor();
+        M::apply(x, w, wn, own_pre, pre.B, suf);
+    }
 
     if (live) {
 #pragma unroll
@@ -1092,9 +1130,14 @@ cudaError_t launch_row_k(const PassArgs& a, int kind, const RowPlan& p, cudaStre
     const dim3 grid((unsigned)((a.H + p.rpb - 1) / p.rpb));
     const dim3 block((unsigned)(p.tpr * p.rpb));
     if (kind == PASS_SUPPORT) return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_SUPPORT>, grid, block, 0, s, a, p.tpr);
+    // two one-direction exchanges (measured faster on the stereo and depth workloads);
+    // DTS_ROW_TWO=0 selects the single coupled exchange (tuning aid)
+    static const bool two = getenv("DTS_ROW_TWO") == nullptr || atoi(getenv("DTS_ROW_TWO")) != 0;
     if (kind == PASS_UPDATE_ROW)
-        return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_UPDATE_ROW>, grid, block, 0, s, a, p.tpr);
-    return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_PLAIN>, grid, block, 0, s, a, p.tpr);
+        return two ? launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_UPDATE_ROW, true>, grid, block, 0, s, a, p.tpr)
+                   : launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_UPDATE_ROW>, grid, block, 0, s, a, p.tpr);
+    return two ? launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_PLAIN, true>, grid, block, 0, s, a, p.tpr)
+               : launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_PLAIN>, grid, block, 0, s, a, p.tpr);
 }
 
 template <int ITEMS, bool DHALF>
@@ -1265,17 +1308,43 @@ cudaError_t launch_row_persist_t(const PassArgs& a, const RowPlan& p, cudaStream
 }
 
 // z_out[y][x] (pitch zout_pitch) = update(z_k, zbar = src, t, c) for every pixel
+// Four consecutive pixels per thread; VEC: 16-byte accesses (W % 4 == 0, aligned planes).
+template <bool VEC>
 __global__ void __launch_bounds__(256) update_kernel(PassArgs a) {
     wait_predecessor();
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     const int y = blockIdx.y;
-    if (x >= a.W || y >= a.H) return;
-    const long long idx = (long long)y * a.pitch + x;
-    const long long di = (long long)y * a.W + x;
-    const float c = a.c_pitched ? a.c[idx] : a.c[di];
-    a.zout[(long long)y * a.zout_pitch + x] =
-        dts_update_value(a.zk[idx], a.src[idx], load_any(a.t, di, a.t_dtype), c, a.lambda, a.step, a.update,
-                         a.clamp_step);
+    if (x0 >= a.W || y >= a.H) return;
+    const long long idx = (long long)y * a.pitch + x0;
+    const long long di = (long long)y * a.W + x0;
+    float zk[4], zb[4], t[4], c[4], z[4];
+    if (VEC) {
+        load4_f(a.zk, idx, zk);
+        load4_f(a.src, idx, zb);
+        load4_f(a.c, a.c_pitched ? idx : di, c);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[k] = load_any(a.t, di + k, a.t_dtype);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool ok = x0 + k < a.W;
+            zk[k] = ok ? a.zk[idx + k] : 0.f;
+            zb[k] = ok ? a.src[idx + k] : 0.f;
+            c[k] = ok ? (a.c_pitched ? a.c[idx + k] : a.c[di + k]) : 0.f;
+            t[k] = ok ? load_any(a.t, di + k, a.t_dtype) : 0.f;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        z[k] = dts_update_value(zk[k], zb[k], t[k], c[k], a.lambda, a.step, a.update, a.clamp_step);
+    const long long o = (long long)y * a.zout_pitch + x0;
+    if (VEC) {
+        store4_f(a.zout, o, z);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (x0 + k < a.W) a.zout[o + k] = z[k];
+    }
 }
 
 }  // namespace
@@ -1299,8 +1368,12 @@ bool plan_rows_update(int W, const RowPlan& plain, RowPlan* p) {
 
 cudaError_t launch_update(const PassArgs& a, cudaStream_t s) {
     const int h = prof_begin(KID_UPDATE, (long long)a.H * a.W, a.t_dtype != DTS_F32 ? kFlagTarget16 : 0, s);
-    const dim3 grid((unsigned)((a.W + 255) / 256), (unsigned)a.H);
-    const cudaError_t e = launch_ex(update_kernel, grid, dim3(256), 0, s, a);
+    const dim3 grid((unsigned)((a.W + 1023) / 1024), (unsigned)a.H);
+    auto al16 = [](const void* p) { return (uintptr_t)p % 16 == 0; };
+    const bool vec = a.W % 4 == 0 && a.pitch % 4 == 0 && a.zout_pitch % 4 == 0 && al16(a.zk) && al16(a.src) &&
+                     al16(a.c) && al16(a.zout);
+    const cudaError_t e = vec ? launch_ex(update_kernel<true>, grid, dim3(256), 0, s, a)
+                              : launch_ex(update_kernel<false>, grid, dim3(256), 0, s, a);
     prof_end(h, s);
     return e;
 }

@@ -193,6 +193,33 @@ __device__ __forceinline__ void row_exchange(const typename M::Pre& own_pre, con
     }
 }
 
+// One-direction exchange of affine maps along a row (same thread layout as row_exchange):
+// PREFIX: the map of everything left of this segment (maps compose left to right); else the map
+// of everything right of it (the rightmost applies first).  s_buf: 32 entries, not shared with
+// another exchange running before the same __syncthreads.  Contains __syncthreads when wpr > 1.
+template <bool PREFIX>
+__device__ __forceinline__ Aff row_scan_aff(Aff v, int lane, int warp, int wrow, int wbase, int wpr, Aff* s_buf) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const Aff o = PREFIX ? shfl_up_t(v, off) : shfl_down_t(v, off);
+        if (PREFIX ? lane >= off : lane + off < 32) v = aff_compose(o, v);
+    }
+    Aff ex = PREFIX ? shfl_up_t(v, 1) : shfl_down_t(v, 1);
+    if (PREFIX ? lane == 0 : lane == 31) ex = aff_identity();
+    if (wpr > 1) {
+        if (PREFIX ? lane == 31 : lane == 0) s_buf[warp] = v;
+        __syncthreads();
+        Aff w = aff_identity();
+        if (PREFIX) {
+            for (int q = 0; q < wrow; ++q) w = aff_compose(w, s_buf[wbase + q]);
+        } else {
+            for (int q = wpr - 1; q > wrow; --q) w = aff_compose(w, s_buf[wbase + q]);
+        }
+        ex = aff_compose(w, ex);
+    }
+    return ex;
+}
+
 // Shared state of a column exchange: NWMAX warps per CTA.
 template <class M, int NWMAX>
 struct ColShared {
