@@ -375,9 +375,10 @@ __global__ void __launch_bounds__(row_max_threads<ITEMS, KIND>()) row_pass_kerne
             // loads, which would otherwise wait for them); the update is computed in place in x.
             const long long di = (long long)row * a.W + e0;
             const bool full_seg = e0 + ITEMS <= a.W;
-            // operands in groups of HALF positions: 4 at 16 positions per thread (measured fastest:
-            // fewer live registers, more resident rows), 16 at 32 (rows over 8192)
-            constexpr int HALF = ITEMS <= 16 ? 4 : ITEMS / 2;
+            // operands in groups of HALF positions (a group's loads, its update, its stores): 8 at
+            // 16 positions per thread (measured: 37.0 us vs 37.5 with 4 and 40.7 with all 16 at
+            // once, which costs resident rows), 16 at 32 (rows over 8192)
+            constexpr int HALF = ITEMS <= 16 ? 8 : ITEMS / 2;
 #pragma unroll
             for (int h0 = 0; h0 < ITEMS; h0 += HALF) {
             float zk[HALF], tt[HALF], cc[HALF];

@@ -112,6 +112,17 @@ __device__ __forceinline__ T shfl_up_t(const T& v, int off) {
 }
 
 template <typename T>
+__device__ __forceinline__ T shfl_xor_t(const T& v, int mask) {
+    constexpr int n = sizeof(T) / 4;
+    T r;
+    const float* s = reinterpret_cast<const float*>(&v);
+    float* d = reinterpret_cast<float*>(&r);
+#pragma unroll
+    for (int i = 0; i < n; ++i) d[i] = __shfl_xor_sync(kFull, s[i], mask);
+    return r;
+}
+
+template <typename T>
 __device__ __forceinline__ T shfl_down_t(const T& v, int off) {
     constexpr int n = sizeof(T) / 4;
     T r;
