@@ -158,10 +158,15 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
+BACKWARD_KERNELS = ("row_bwd_kernel", "col_bwd_kernel", "update_adjoint_kernel", "guide_grad_kernel",
+                    "axpy_plane_kernel")
+
+
 def traffic_for(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, when that
-    summary was taken on the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_1805_04590_gb300", "csrc", "dts_forward.cu")
+    summary was taken on the current source of the file that holds the kernel (else None)."""
+    fn = "dts_backward.cu" if kernel.startswith(BACKWARD_KERNELS) else "dts_forward.cu"
+    src = os.path.join(ROOT, "paper_1805_04590_gb300", "csrc", fn)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
