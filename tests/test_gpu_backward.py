@@ -176,3 +176,74 @@ def test_backward_depth_sr_batch_full_size():
         close(gc.cpu().numpy(), ref["c"], f"image {i} grad conf")
         close(gg.cpu().numpy(), ref["guide"], f"image {i} grad guide")
         del ws
+
+
+def test_backward_depth_sr_reduced_finite_differences():
+    """The x16 depth-SR generator at 256 x 192 (K = 10, sigma_s = 320): GPU gradients against
+    central finite differences of the FP64 oracle's loss <g, z_K> at 64 random entries of each
+    of the target, the confidence and the guide."""
+    wl = workloads.workload_depth_sr(batch=1, H=192, W=256)
+    p, q = wl.problems[0], wl.params
+    kw = dict(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes)
+    prm = dts.Params(save_checkpoints=1, **{("lam" if k == "lam" else k): v for k, v in kw.items()})
+    rng = np.random.default_rng(192)
+    gz = rng.normal(size=p.target.shape)
+    g, tt, cc = T(p.guide), T(p.target), T(p.conf)
+    ws = dts.workspace(g, prm, with_backward=True)
+    dts.dts_solve(g, tt, cc, prm, ws=ws)
+    gt, gc, gg, _ = dts.dts_solve_backward(g, tt, cc, prm, ws, T(gz.astype(np.float32)))
+    gt, gc, gg = gt.cpu().numpy(), gc.cpu().numpy(), gg.cpu().numpy()
+    I0, t0, c0 = (x.astype(np.float64) for x in (p.guide, p.target, p.conf))
+
+    def loss(I, t, c):
+        return float(np.sum(gz * oracle.solve(I, t, c, **kw)))
+
+    H, W = t0.shape
+    for name, grad, h in (("target", gt, 1e-3), ("conf", gc, 1e-4)):
+        for _ in range(64):
+            y, x = int(rng.integers(H)), int(rng.integers(W))
+            a, b = t0.copy(), c0.copy()
+            arr = a if name == "target" else b
+            arr[y, x] += h
+            lp = loss(I0, a, b)
+            arr[y, x] -= 2 * h
+            lm = loss(I0, a, b)
+            fd = (lp - lm) / (2 * h)
+            assert abs(grad[y, x] - fd) <= GTOL * np.abs(grad).max(), (name, y, x, grad[y, x], fd)
+    # guide: entries whose neighbour differences (the L1 kinks) are all far from zero
+    h = 1e-6
+    checked = 0
+    while checked < 64:
+        k, y, x = int(rng.integers(I0.shape[0])), int(rng.integers(1, H - 1)), int(rng.integers(1, W - 1))
+        diffs = [I0[k, y, x] - I0[k, y, x - 1], I0[k, y, x + 1] - I0[k, y, x], I0[k, y, x] - I0[k, y - 1, x],
+                 I0[k, y + 1, x] - I0[k, y, x]]
+        if min(abs(d) for d in diffs) < 100 * h:
+            continue
+        Ip = I0.copy()
+        Ip[k, y, x] += h
+        lp = loss(Ip, t0, c0)
+        Ip[k, y, x] -= 2 * h
+        lm = loss(Ip, t0, c0)
+        fd = (lp - lm) / (2 * h)
+        assert abs(gg[k, y, x] - fd) <= GTOL * np.abs(gg).max(), ("guide", k, y, x, gg[k, y, x], fd)
+        checked += 1
+
+
+def test_backward_multispectral_reduced():
+    """The 16-band multispectral generator at 1200 x 1200 (K = 10): every gradient against the
+    oracle's reverse mode."""
+    wl = workloads.make(4, H=1200, W=1200)
+    p, q = wl.problems[0], wl.params
+    prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes,
+                     save_checkpoints=2)
+    gz = np.random.default_rng(1200).normal(size=p.target.shape).astype(np.float32)
+    g, tt, cc = T(p.guide), T(p.target), T(p.conf)
+    ws = dts.workspace(g, prm, with_backward=True)
+    dts.dts_solve(g, tt, cc, prm, ws=ws)
+    gt, gc, gg, _ = dts.dts_solve_backward(g, tt, cc, prm, ws, T(gz))
+    assert dts.dts_last_status() == 0
+    ref = oracle.solve_backward(p.guide, p.target, p.conf, gz, lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r,
+                                iterations=q.iterations, passes=q.passes)
+    close(gt.cpu().numpy(), ref["t"], "grad target")
+    close(gc.cpu().numpy(), ref["c"], "grad conf")
+    close(gg.cpu().numpy(), ref["guide"], "grad guide")

@@ -96,3 +96,46 @@ def test_autotuned_shapes_are_used_and_exact():
         ref = oracle.solve(p.guide, p.target, p.conf, lam=prm.lam, sigma_s=prm.sigma_s, sigma_r=prm.sigma_r,
                            iterations=prm.iterations)
         assert np.abs(outs[i].cpu().numpy() - ref).max() <= TOL * float(np.ptp(p.target))
+
+
+def test_batched_full_workload():
+    """The 64-image batch (H ~ U{240..1080}, W ~ U{320..1920}) at full size: every image against
+    the oracle."""
+    wl = workloads.make(3)
+    d = dev()
+    g = [torch.from_numpy(p.guide).to(d) for p in wl.problems]
+    t = [torch.from_numpy(p.target).to(d) for p in wl.problems]
+    c = [torch.from_numpy(p.conf).to(d) for p in wl.problems]
+    q = wl.params
+    prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes)
+    outs = dts.dts_solve_batched(g, t, c, prm)
+    torch.cuda.synchronize()
+    assert dts.dts_last_status() == 0
+    for i, p in enumerate(wl.problems):
+        ref = oracle.solve(p.guide, p.target, p.conf, lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r,
+                           iterations=q.iterations)
+        assert np.abs(outs[i].cpu().numpy() - ref).max() <= TOL * float(np.ptp(p.target)), (i, p.target.shape)
+
+
+# BF16 guide and target, FP32 arithmetic: against the oracle on the same rounded inputs the FP32
+# bound holds; against the oracle on the unrounded inputs the error is that of rounding the
+# inputs to BF16 (8 significant bits): the oracle on rounded vs unrounded inputs of this batch
+# differs by up to 5.5e-3 of the target range (2.8 x 2^-9), so the stated bound is 2^-7
+BF16_INPUT_TOL = 2.0 ** -7
+
+
+def test_batched_bf16_storage():
+    wl, g, t, c, prm = _batch(8, n=6)
+    gb = [x.to(torch.bfloat16) for x in g]
+    tb = [x.to(torch.bfloat16) for x in t]
+    outs = dts.dts_solve_batched(gb, tb, c, prm)
+    torch.cuda.synchronize()
+    assert dts.dts_last_status() == 0
+    for i, p in enumerate(wl.problems):
+        gr = gb[i].float().cpu().numpy().astype(np.float64)
+        tr = tb[i].float().cpu().numpy().astype(np.float64)
+        kw = dict(lam=prm.lam, sigma_s=prm.sigma_s, sigma_r=prm.sigma_r, iterations=prm.iterations)
+        z = outs[i].cpu().numpy()
+        rng = float(np.ptp(tr)) or 1.0
+        assert np.abs(z - oracle.solve(gr, tr, p.conf, **kw)).max() <= TOL * rng, i
+        assert np.abs(z - oracle.solve(p.guide, p.target, p.conf, **kw)).max() <= BF16_INPUT_TOL * rng, i

@@ -210,6 +210,31 @@ def test_solve_full_stereo_workload():
     assert_close(z.cpu().numpy(), ref, p.target, "stereo 2880x1988")
 
 
+def test_solve_multispectral_reduced():
+    """The 16-band multispectral generator at 2500 x 2500 (its full 10000 x 10000 size is timed
+    by the bench): the 10-iteration solve against the oracle."""
+    wl = workloads.make(4, H=2500, W=2500)
+    p, q = wl.problems[0], wl.params
+    prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes)
+    z = dts.dts_solve(to_dev(p.guide), to_dev(p.target), to_dev(p.conf), prm)
+    assert dts.dts_last_status() == 0
+    ref = oracle_solve(p.guide, p.target, p.conf, prm)
+    assert_close(z.cpu().numpy(), ref, p.target, "multispectral 2500x2500x16")
+
+
+def test_solve_multispectral_full_size_constant_target():
+    """The full 10000 x 10000 x 16 multispectral guide, in the launch configuration the bench
+    times, with a constant target: every iterate stays that constant (a property the solve keeps
+    at any size; the oracle cannot run this size)."""
+    wl = workloads.make(4)
+    p, q = wl.problems[0], wl.params
+    prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes)
+    t = torch.full(p.target.shape, 0.625, device=dev())
+    z = dts.dts_solve(to_dev(p.guide), t, to_dev(p.conf), prm)
+    assert dts.dts_last_status() == 0
+    assert float((z - 0.625).abs().max()) <= 1e-5
+
+
 def test_last_status_clean():
     dev()
     assert dts.dts_last_status() == 0
