@@ -367,6 +367,62 @@ def version() -> str:
     return load().dts_version().decode()
 
 
+class HostPipeline:
+    """Solves step after step on inputs held in pinned host memory, overlapping copies with
+    solves: the host-to-device copies of step i + 1 run on one copy stream and the
+    device-to-host copies of step i - 1 on another while step i solves on the current stream
+    (two device buffer sets, events between the streams).
+
+    ``solve_fn(inputs, outputs)`` enqueues the solve on the current stream, reading the device
+    tensors ``inputs`` (shaped like a step's host inputs) and writing ``outputs`` (shaped like a
+    step's host outputs)."""
+
+    def __init__(self, solve_fn, depth: int = 2, device=None):
+        self.solve_fn = solve_fn
+        self.depth = depth
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.h2d = torch.cuda.Stream(device=self.device)
+        self.d2h = torch.cuda.Stream(device=self.device)
+        self.copied = [torch.cuda.Event() for _ in range(depth)]
+        self.solved = [torch.cuda.Event() for _ in range(depth)]
+        self.read = [torch.cuda.Event() for _ in range(depth)]
+        self.bufs = [None] * depth
+
+    def _buffers(self, slot, hin, hout):
+        key = [(tuple(x.shape), x.dtype) for x in hin + hout]
+        if self.bufs[slot] is None or self.bufs[slot][0] != key:
+            din = [torch.empty(x.shape, dtype=x.dtype, device=self.device) for x in hin]
+            dout = [torch.empty(x.shape, dtype=x.dtype, device=self.device) for x in hout]
+            self.bufs[slot] = (key, din, dout)
+        return self.bufs[slot][1], self.bufs[slot][2]
+
+    def run(self, host_inputs, host_outputs, start_event=None):
+        """host_inputs / host_outputs: per step, lists of pinned CPU tensors.  Returns with every
+        copy enqueued and the current stream waiting for the last one."""
+        cur = torch.cuda.current_stream(self.device)
+        if start_event is not None:
+            self.h2d.wait_event(start_event)
+        for i, (hin, hout) in enumerate(zip(host_inputs, host_outputs)):
+            s = i % self.depth
+            din, dout = self._buffers(s, list(hin), list(hout))
+            self.h2d.wait_event(self.solved[s])  # the solve two steps back has read these inputs
+            with torch.cuda.stream(self.h2d):
+                for d, h in zip(din, hin):
+                    d.copy_(h, non_blocking=True)
+            self.copied[s].record(self.h2d)
+            cur.wait_event(self.copied[s])
+            cur.wait_event(self.read[s])  # the copy two steps back has read these outputs
+            self.solve_fn(din, dout)
+            self.solved[s].record(cur)
+            self.d2h.wait_event(self.solved[s])
+            with torch.cuda.stream(self.d2h):
+                for h, d in zip(hout, dout):
+                    h.copy_(d, non_blocking=True)
+            self.read[s].record(self.d2h)
+        cur.wait_stream(self.d2h)
+        cur.wait_stream(self.h2d)
+
+
 def backward_checkpoint_mode(guide: torch.Tensor, params: Params) -> int:
     """save_checkpoints for a solve that will be differentiated: 2 (keep every pass input,
     no recompute in the backward) when its workspace takes at most a quarter of the free

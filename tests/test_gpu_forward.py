@@ -235,6 +235,26 @@ def test_solve_multispectral_full_size_constant_target():
     assert float((z - 0.625).abs().max()) <= 1e-5
 
 
+def test_host_pipeline_matches_direct_solves():
+    """dts.HostPipeline (copies of neighbouring steps overlapping the solves, two device buffer
+    sets, shapes changing between steps) gives the same results, bit for bit, as direct solves."""
+    shapes = [(100, 130), (100, 130), (64, 80), (100, 130), (37, 51)]
+    probs = [workloads.random_problem(H, W, C=3, seed=40 + i) for i, (H, W) in enumerate(shapes)]
+    prm = dts.Params(lam=0.9, sigma_s=10.0, sigma_r=0.2, iterations=4)
+
+    def solve_fn(din, dout):
+        dts.dts_solve(din[0], din[1], din[2], prm, out=dout[0])
+
+    hin = [[torch.from_numpy(x).pin_memory() for x in (p.guide, p.target, p.conf)] for p in probs]
+    hout = [[torch.empty(p.target.shape, dtype=torch.float32).pin_memory()] for p in probs]
+    dev()
+    dts.HostPipeline(solve_fn).run(hin, hout)
+    torch.cuda.synchronize()
+    for p, (o,) in zip(probs, hout):
+        ref = dts.dts_solve(to_dev(p.guide), to_dev(p.target), to_dev(p.conf), prm).cpu()
+        assert torch.equal(o, ref)
+
+
 def test_last_status_clean():
     dev()
     assert dts.dts_last_status() == 0
