@@ -38,6 +38,7 @@ def _load():
         lib.orc_col_pass.argtypes = [i, i, p, p, d]
         lib.orc_filter.argtypes = [i, i, p, p, i, p, p, p]
         lib.orc_support.argtypes = [i, i, p, p, d, p, p]
+        lib.orc_confidence.argtypes = [i, i, p, p, i, p, p, d, p]
         lib.orc_solve.argtypes = [i, i, p, p, p, p, p, d, d, d, i, i, i, i, p, p]
         lib.orc_solve.restype = i
         lib.orc_filter_adjoint.argtypes = [i, i, p, p, i, p, p, p, p, p, p]
@@ -134,6 +135,23 @@ def filter(I, src, sigma_s, sigma_r, passes=3, norm=NORM_L1):
     dX, dY = distances(I, sigma_s, sigma_r, norm)
     _, a = schedule(sigma_s, passes)
     return filter_d(dX, dY, a, src)
+
+
+def confidence_d(dX, dY, a, t, sigma_c):
+    """c = exp(-V / (2 sigma_c^2)), V = DT(t^2) - DT(t)^2 (Eq. 7) for given distances."""
+    dX, dY, t = _f64(dX), _f64(dY), _f64(t)
+    a = _f64(a)
+    H, W = t.shape
+    c = np.empty((H, W))
+    _load().orc_confidence(H, W, _ptr(dX), _ptr(dY), a.size, _ptr(a), _ptr(t), float(sigma_c), _ptr(c))
+    return c
+
+
+def confidence(I, t, sigma_s, sigma_r, sigma_c, passes=3, norm=NORM_L1):
+    """Confidence from the edge-aware variance of t under guide I (Eq. 7)."""
+    dX, dY = distances(I, sigma_s, sigma_r, norm)
+    _, a = schedule(sigma_s, passes)
+    return confidence_d(dX, dY, a, t, sigma_c)
 
 
 def support(dX, dY, sigma_s):

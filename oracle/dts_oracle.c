@@ -25,6 +25,9 @@
  *   orc_filter          edge-aware mean z_bar = A z, Eq. 10 with the RF kernel
  *   orc_support         sum_j W_ij support used to weight the confidence (§3.1,
  *                       discussion after Eq. 6)
+ *   orc_confidence      confidence from the edge-aware variance of the target,
+ *                       Eq. 7 (§3.1): c = exp(-V / (2 sigma_c^2)),
+ *                       V = DT(t^2) - DT(t)^2 with DT the edge-aware mean
  *   orc_solve           gradient-descent iterations on Eq. 3 (step 0.99, §4)
  *                       or the fixed-point update of Eq. 4
  *   orc_solve_backward  hand-written reverse mode of orc_solve (the paper has
@@ -160,6 +163,29 @@ void orc_filter(int H, int W, const double* dX, const double* dY, int N, const d
         orc_row_pass(H, W, dst, dX, a[i]);
         orc_col_pass(H, W, dst, dY, a[i]);
     }
+}
+
+/* Confidence of Eq. 7 (§3.1): the edge-aware mean DT (Eq. 10, orc_filter) of the target and of
+ * its square give the local variance V = DT(t^2) - DT(t)^2, and c = exp(-V / (2 sigma_c^2)).
+ * V is never negative in exact arithmetic (DT is a non-negative, row-stochastic average); a
+ * negative value from rounding is taken as 0. */
+void orc_confidence(int H, int W, const double* dX, const double* dY, int N, const double* a,
+                    const double* t, double sigma_c, double* c) {
+    const size_t n = (size_t)H * W;
+    double* t2 = (double*)malloc(sizeof(double) * n);
+    double* m1 = (double*)malloc(sizeof(double) * n);
+    double* m2 = (double*)malloc(sizeof(double) * n);
+    for (size_t i = 0; i < n; ++i) t2[i] = t[i] * t[i];
+    orc_filter(H, W, dX, dY, N, a, t, m1);
+    orc_filter(H, W, dX, dY, N, a, t2, m2);
+    for (size_t i = 0; i < n; ++i) {
+        double v = m2[i] - m1[i] * m1[i];
+        if (v < 0.0) v = 0.0;
+        c[i] = exp(-v / (2.0 * sigma_c * sigma_c));
+    }
+    free(t2);
+    free(m1);
+    free(m2);
 }
 
 /* Support S_i = sum_j W_ij of the (unnormalised) separable recursive-filter

@@ -444,3 +444,41 @@ def test_workload_generators_are_seeded():
     np.testing.assert_array_equal(p.target, q.target)
     assert 0.2 <= p.conf.min() and p.conf.max() <= 1.0
     assert a.params.sigma_s == 8.0 and a.params.iterations == 10
+
+
+# ---------------------------------------------------------------- confidence (Eq. 7)
+def test_confidence_equals_dense_variance():
+    """c = exp(-V / (2 sigma_c^2)) with V_i = sum_j A_ij t_j^2 - (sum_j A_ij t_j)^2 computed from
+    the dense filter matrix (built from weight products, independent of the oracle's sweeps)."""
+    rng = np.random.default_rng(71)
+    H, W = 5, 6
+    I = rand_guide(rng, 3, H, W)
+    t = rng.normal(size=(H, W))
+    dX, dY = oracle.distances(I, 6.0, 0.4)
+    _, a = oracle.schedule(6.0, 3)
+    A = dense_filter_matrix(dX, dY, a)
+    tf = t.ravel()
+    V = A @ (tf * tf) - (A @ tf) ** 2
+    ref = np.exp(-np.maximum(V, 0.0) / (2 * 0.3 ** 2)).reshape(H, W)
+    got = oracle.confidence_d(dX, dY, a, t, 0.3)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+
+
+def test_confidence_properties():
+    rng = np.random.default_rng(72)
+    I = rand_guide(rng, 3, 12, 15)
+    # a constant target has zero variance: full confidence everywhere
+    c = oracle.confidence(I, np.full((12, 15), 0.7), 8.0, 0.2, sigma_c=0.1)
+    np.testing.assert_allclose(c, 1.0, rtol=0, atol=1e-12)
+    # the variance is non-negative (Jensen: A is non-negative and row-stochastic), so c <= 1,
+    # and a larger sigma_c never lowers the confidence
+    t = rng.normal(size=(12, 15))
+    c1 = oracle.confidence(I, t, 8.0, 0.2, sigma_c=0.2)
+    c2 = oracle.confidence(I, t, 8.0, 0.2, sigma_c=0.5)
+    assert (c1 <= 1.0).all() and (c1 > 0.0).all() and (c2 >= c1).all()
+    # two flat regions split by a strong guide edge: the variance stays near 0 away from it
+    G = np.zeros((1, 8, 16))
+    G[:, :, 8:] = 1.0
+    tt = np.where(np.arange(16) < 8, 0.0, 1.0)[None, :].repeat(8, 0)
+    c = oracle.confidence(G, tt, 8.0, 0.05, sigma_c=0.1)
+    assert c[:, :4].min() > 0.999 and c[:, 12:].min() > 0.999
