@@ -127,6 +127,17 @@ int dts_filter(const dts_guide* guide, const dts_params* params, const float* sr
 int dts_solve(const dts_guide* guide, const void* target, int target_dtype, const float* conf, const float* z_init,
               const dts_params* params, float* z_out, void* ws, size_t ws_bytes, dts_stream stream);
 
+/* Confidence from the edge-aware variance of the target (Eq. 7, §3.1):
+ *   V = DT(t^2) - DT(t)^2,   c = exp(-V / (2 sigma_c^2)),
+ * with DT the edge-aware mean of Eq. 10 (the filter of dts_filter: distances and passes from
+ * `params`).  The paper gives no value for sigma_c: the caller chooses it (sigma_c > 0, in the
+ * units of t).  V below 0 can only come from rounding and is taken as 0, so 0 < c <= 1.
+ * target: dense H x W of target_dtype (F32, BF16 or F16); conf_out: dense H x W FP32.
+ * Workspace as for dts_filter (dts_workspace_size with with_backward = 0).  Argument errors
+ * (including sigma_c <= 0) are DTS_ERR_INVALID_ARG, returned before any device work. */
+int dts_confidence(const dts_guide* guide, const void* target, int target_dtype, const dts_params* params,
+                   float sigma_c, float* conf_out, void* ws, size_t ws_bytes, dts_stream stream);
+
 /* Reverse mode of dts_solve (the paper has no backward; the adjoint of each
  * recurrence is the same recurrence run in the opposite direction).  Must follow
  * a dts_solve with the same arguments, save_checkpoints = 1 and this workspace

@@ -457,6 +457,54 @@ extern "C" int dts_filter(const dts_guide* guide, const dts_params* params, cons
     return DTS_OK;
 }
 
+extern "C" int dts_confidence(const dts_guide* guide, const void* target, int target_dtype,
+                              const dts_params* params, float sigma_c, float* conf_out, void* ws, size_t ws_bytes,
+                              dts_stream stream) {
+    int st = check_guide(guide);
+    if (!st) st = check_params(params);
+    if (st) return st;
+    if (!target || !conf_out || !valid_dtype(target_dtype) || !(sigma_c > 0.f) || !isfinite(sigma_c))
+        return DTS_ERR_INVALID_ARG;
+    Plans pl;
+    if ((st = make_plans(guide->H, guide->W, &pl))) return st;
+    dts_params p = *params;
+    p.conf_mode = DTS_CONF_PLAIN;
+    p.save_checkpoints = 0;
+    const Layout L = make_layout(guide->H, guide->W, &p, 0);
+    if (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.fwd_end) return DTS_ERR_WORKSPACE;
+    if ((st = ensure_prepared())) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = bind_workspace(ws, L, s))) return st;
+    const int H = guide->H, W = guide->W;
+    float* m1 = reinterpret_cast<float*>(ws_at(ws, L.u));  // DT(t), filtered in place
+    float* m2 = reinterpret_cast<float*>(ws_at(ws, L.z));  // DT(t^2), filtered in place
+    // distances, with t copied (as FP32) into the first working plane, then t^2 into the second
+    if ((st = run_distances(guide, &p, L, ws, target, target_dtype, m1, s))) return st;
+    if ((st = cuda_status(launch_square_plane(m1, m2, L.pitch, H, W, s)))) return st;
+    float k2[kMaxPasses];
+    pass_log2a(p.sigma_s, p.passes, k2);
+    const int dh = p.dist_dtype == DTS_F16;
+    for (int i = 0; i < p.passes; ++i) {
+        for (float* u : {m1, m2}) {  // the two planes back to back: the same distances stay in L2
+            PassArgs r = base_pass(guide, L);
+            r.src = u;
+            r.dst = u;
+            r.d = ws_at(ws, L.dX);
+            r.k2 = k2[i];
+            if ((st = cuda_status(launch_row_pass(r, dh, PASS_PLAIN, pl.rows, s)))) return st;
+        }
+        for (float* u : {m1, m2}) {
+            PassArgs c = base_pass(guide, L);
+            c.src = u;
+            c.dst = u;
+            c.d = ws_at(ws, L.dY);
+            c.k2 = k2[i];
+            if ((st = cuda_status(launch_col_pass(c, dh, PASS_PLAIN, pl.cols, s)))) return st;
+        }
+    }
+    return cuda_status(launch_confidence(m1, m2, L.pitch, H, W, sigma_c, conf_out, s));
+}
+
 extern "C" int dts_solve(const dts_guide* guide, const void* target, int target_dtype, const float* conf,
                          const float* z_init, const dts_params* params, float* z_out, void* ws, size_t ws_bytes,
                          dts_stream stream) {

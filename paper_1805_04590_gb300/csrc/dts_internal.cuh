@@ -189,6 +189,8 @@ enum KernelId {
     KID_UPDATE = 15,
     KID_UPDATE_ADJ = 16,
     KID_COL_STRIP = 17,
+    KID_SQUARE = 18,
+    KID_CONFIDENCE = 19,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
@@ -219,6 +221,9 @@ void set_tuned_row(int W, int items);
 void set_tuned_col(int H, const ColPlan& p);
 int col_candidates(int H, ColPlan* out, int max_out);
 cudaError_t launch_update(const PassArgs& a, cudaStream_t s);
+cudaError_t launch_square_plane(const float* src, float* dst, long long pitch, int H, int W, cudaStream_t s);
+cudaError_t launch_confidence(const float* m1, const float* m2, long long pitch, int H, int W, float sigma_c,
+                              float* c, cudaStream_t s);
 bool plan_cols(int H, ColPlan* p);
 bool plan_cols_cluster(int H, ColPlan* p);
 bool plan_cols_tma(int H, ColPlan* p);

@@ -110,6 +110,8 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_UPDATE: return "update_kernel";
         case KID_UPDATE_ADJ: return "update_adjoint_kernel";
         case KID_COL_STRIP: return "col_strip_kernel";
+        case KID_SQUARE: return "square_plane_kernel";
+        case KID_CONFIDENCE: return "confidence_kernel";
         default: return "unknown";
     }
 }

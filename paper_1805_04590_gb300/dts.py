@@ -70,7 +70,8 @@ _lib = None
 EXPORTS = ("dts_status_string", "dts_version", "dts_workspace_size", "dts_domain_transform", "dts_filter",
            "dts_solve", "dts_solve_backward", "dts_last_status", "dts_profile", "dts_profile_read",
            "dts_kernel_name", "dts_solve_noalloc", "dts_noalloc_max_workspace", "dts_batched_workspace_size",
-           "dts_solve_batched", "dts_debug_inject", "dts_autotune", "dts_autotune_export", "dts_autotune_import")
+           "dts_solve_batched", "dts_debug_inject", "dts_autotune", "dts_autotune_export", "dts_autotune_import",
+           "dts_confidence")
 
 
 def library_path() -> str:
@@ -99,6 +100,7 @@ def load(build_if_missing: bool = True):
     lib.dts_filter.argtypes = [P(CGuide), P(CParams), vp, vp, vp, sz, vp]
     lib.dts_solve.argtypes = [P(CGuide), vp, i, vp, vp, P(CParams), vp, vp, sz, vp]
     lib.dts_solve_backward.argtypes = [P(CGuide), vp, i, vp, vp, P(CParams), vp, sz, vp, vp, vp, vp, vp, vp]
+    lib.dts_confidence.argtypes = [P(CGuide), vp, i, P(CParams), ctypes.c_float, vp, vp, sz, vp]
     lib.dts_last_status.argtypes = [vp]
     lib.dts_solve_noalloc.argtypes = [P(CGuide), vp, i, vp, vp, P(CParams), vp, vp]
     lib.dts_batched_workspace_size.argtypes = [i, P(CGuide), P(CParams)]
@@ -114,6 +116,7 @@ def load(build_if_missing: bool = True):
     lib.dts_kernel_name.argtypes = [i]
     lib.dts_kernel_name.restype = ctypes.c_char_p
     for name in ("dts_domain_transform", "dts_filter", "dts_solve", "dts_solve_backward", "dts_last_status",
+                 "dts_confidence",
                  "dts_profile", "dts_profile_read", "dts_solve_noalloc", "dts_solve_batched", "dts_debug_inject",
                  "dts_autotune", "dts_autotune_export", "dts_autotune_import"):
         getattr(lib, name).restype = i
@@ -216,6 +219,23 @@ def dts_solve(guide: torch.Tensor, target: torch.Tensor, conf: torch.Tensor, par
     _check(load().dts_solve(ctypes.byref(g), target.data_ptr(), _TORCH_DTYPE[target.dtype], conf.data_ptr(),
                             _ptr(z_init), ctypes.byref(p), out.data_ptr(), ws.data_ptr(), ws.numel(),
                             _stream(stream)), "dts_solve")
+    return out
+
+
+def dts_confidence(guide: torch.Tensor, target: torch.Tensor, params: Params, sigma_c: float,
+                   out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Confidence exp(-V / (2 sigma_c^2)) from the edge-aware variance V = DT(t^2) - DT(t)^2 of the
+    target (Eq. 7): H x W float32."""
+    _need_cuda(guide, target)
+    _dense(target, "target", tuple(_TORCH_DTYPE))
+    g = guide_desc(guide)
+    out = torch.empty(target.shape, dtype=torch.float32, device=target.device) if out is None else out
+    p = dataclasses.replace(params, save_checkpoints=0)
+    ws = workspace(guide, p) if ws is None else ws
+    pc = p.c()
+    _check(load().dts_confidence(ctypes.byref(g), target.data_ptr(), _TORCH_DTYPE[target.dtype], ctypes.byref(pc),
+                                 float(sigma_c), out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)),
+           "dts_confidence")
     return out
 
 

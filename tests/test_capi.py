@@ -140,3 +140,14 @@ def test_autotune_table_roundtrip_without_gpu():
     dts.autotune_import("col 64 40 16 16\n")
     assert "col 64 " not in dts.autotune_export()
     assert lib.dts_autotune_import(b"bogus 1 2\n") == 1
+
+
+def test_confidence_rejects_bad_arguments():
+    lib = dts.load()
+    p = dts.Params().c()
+    g = _guide()
+    for sc in (0.0, -1.0, float("inf"), float("nan")):
+        assert lib.dts_confidence(ctypes.byref(g), 0x2000, 0, ctypes.byref(p), sc, 0x3000, 0x5000, 1 << 30, None) == 1
+    assert lib.dts_confidence(ctypes.byref(g), None, 0, ctypes.byref(p), 0.1, 0x3000, 0x5000, 1 << 30, None) == 1
+    assert lib.dts_confidence(ctypes.byref(g), 0x2000, 9, ctypes.byref(p), 0.1, 0x3000, 0x5000, 1 << 30, None) == 1
+    assert lib.dts_confidence(ctypes.byref(g), 0x2000, 0, ctypes.byref(p), 0.1, 0x3000, 0x5000, 16, None) == 3

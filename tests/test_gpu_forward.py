@@ -235,6 +235,30 @@ def test_solve_multispectral_full_size_constant_target():
     assert float((z - 0.625).abs().max()) <= 1e-5
 
 
+# ---------------------------------------------------------------- confidence (Eq. 7)
+@pytest.mark.parametrize("H,W,sdt", [(1, 1, torch.float32), (37, 53, torch.float32), (300, 517, torch.float32),
+                                     (1200, 90, torch.bfloat16), (2100, 40, torch.float32)])
+def test_confidence(H, W, sdt):
+    """exp(-V / (2 sigma_c^2)), V = DT(t^2) - DT(t)^2, against the oracle on the same (rounded)
+    target; c is in (0, 1], so the FP32 bound is absolute (1e-4, V computed from two FP32 means
+    of values of order 1)."""
+    prob = workloads.random_problem(H, W, C=3, seed=H + 5 * W)
+    prm = dts.Params(sigma_s=10.0, sigma_r=0.2, passes=3)
+    t = to_dev(prob.target, sdt)
+    c = dts.dts_confidence(to_dev(prob.guide), t, prm, sigma_c=0.15)
+    ref = oracle.confidence(prob.guide, rounded(t), 10.0, 0.2, sigma_c=0.15)
+    assert float(np.abs(c.cpu().numpy() - ref).max()) <= 1e-4
+
+
+def test_confidence_constant_target_is_one():
+    """A constant target has zero variance.  In FP32 the two means of t = 3.25 and t^2 = 10.5625
+    keep the constant to rounding through the segment exchanges, so V = DT(t^2) - DT(t)^2 is at
+    most about 1e-5 and c >= exp(-1e-5 / (2 * 0.1^2)) ~ 1 - 5e-4."""
+    prob = workloads.random_problem(120, 333, C=3, seed=9)
+    c = dts.dts_confidence(to_dev(prob.guide), torch.full((120, 333), 3.25, device=dev()), dts.Params(), 0.1)
+    assert float((c - 1.0).abs().max()) <= 1e-3
+
+
 def test_host_pipeline_matches_direct_solves():
     """dts.HostPipeline (copies of neighbouring steps overlapping the solves, two device buffer
     sets, shapes changing between steps) gives the same results, bit for bit, as direct solves."""
