@@ -39,6 +39,7 @@ def _load():
         lib.orc_filter.argtypes = [i, i, p, p, i, p, p, p]
         lib.orc_support.argtypes = [i, i, p, p, d, p, p]
         lib.orc_confidence.argtypes = [i, i, p, p, i, p, p, d, p]
+        lib.orc_box_filter.argtypes = [i, i, p, p, i, p, p, p]
         lib.orc_solve.argtypes = [i, i, p, p, p, p, p, d, d, d, i, i, i, i, p, p]
         lib.orc_solve.restype = i
         lib.orc_filter_adjoint.argtypes = [i, i, p, p, i, p, p, p, p, p, p]
@@ -135,6 +136,24 @@ def filter(I, src, sigma_s, sigma_r, passes=3, norm=NORM_L1):
     dX, dY = distances(I, sigma_s, sigma_r, norm)
     _, a = schedule(sigma_s, passes)
     return filter_d(dX, dY, a, src)
+
+
+def box_filter_d(dX, dY, sigma, src):
+    """Box-kernel edge-aware mean (Eq. 10's printed kernel) for given distances and per-pass
+    sigma_i (box radius sigma_i sqrt(3))."""
+    dX, dY, src = _f64(dX), _f64(dY), _f64(src)
+    sigma = _f64(sigma)
+    H, W = src.shape
+    dst = np.empty((H, W))
+    _load().orc_box_filter(H, W, _ptr(dX), _ptr(dY), sigma.size, _ptr(sigma), _ptr(src), _ptr(dst))
+    return dst
+
+
+def box_filter(I, src, sigma_s, sigma_r, passes=3, norm=NORM_L1):
+    """Box-kernel edge-aware mean of src under guide I."""
+    dX, dY = distances(I, sigma_s, sigma_r, norm)
+    sig, _ = schedule(sigma_s, passes)
+    return box_filter_d(dX, dY, sig, src)
 
 
 def confidence_d(dX, dY, a, t, sigma_c):

@@ -25,6 +25,9 @@
  *   orc_filter          edge-aware mean z_bar = A z, Eq. 10 with the RF kernel
  *   orc_support         sum_j W_ij support used to weight the confidence (§3.1,
  *                       discussion after Eq. 6)
+ *   orc_box_filter      the edge-aware mean with the box kernel Eq. 10 prints,
+ *                       W_ij = 1 if |DT_i - DT_j| <= r (normalized convolution in
+ *                       the transformed domain, G&O), r_i = sigma_i sqrt(3) per pass
  *   orc_confidence      confidence from the edge-aware variance of the target,
  *                       Eq. 7 (§3.1): c = exp(-V / (2 sigma_c^2)),
  *                       V = DT(t^2) - DT(t)^2 with DT the edge-aware mean
@@ -162,6 +165,51 @@ void orc_filter(int H, int W, const double* dX, const double* dY, int N, const d
     for (int i = 0; i < N; ++i) {
         orc_row_pass(H, W, dst, dX, a[i]);
         orc_col_pass(H, W, dst, dY, a[i]);
+    }
+}
+
+/* Box-kernel edge-aware mean along one line (Eq. 10 with the kernel it prints,
+ * W_ij = 1 if |DT_i - DT_j| <= r): the domain coordinate is ct[0] = 0, ct[n] = ct[n-1] + d[n]
+ * (d[n] the distance between n-1 and n), and out[n] is the plain average of x[m] over every m
+ * with |ct[m] - ct[n]| <= r.  Written from the definition: for each n, every m is tested.
+ * The distances are taken as given; coordinates are summed in double precision. */
+static void box_line(int n, double* x, long sx, const double* d, long sd, double r, double* ct, double* tmp) {
+    ct[0] = 0.0;
+    for (int j = 1; j < n; ++j) ct[j] = ct[j - 1] + d[j * sd];
+    for (int i = 0; i < n; ++i) {
+        double sum = 0.0;
+        int cnt = 0;
+        for (int m = 0; m < n; ++m) {
+            if (fabs(ct[m] - ct[i]) <= r) {
+                sum += x[m * sx];
+                ++cnt;
+            }
+        }
+        tmp[i] = sum / cnt;  /* m = i is always in the window */
+    }
+    for (int i = 0; i < n; ++i) x[i * sx] = tmp[i];
+}
+
+/* The box-kernel filter: N passes, each a horizontal then a vertical box average with radius
+ * r_i = sigma_i sqrt(3) (a box of half-width r has variance r^2 / 3, the sigma_i^2 of the
+ * recursive filter's pass i; schedule of orc_schedule), the first pass horizontal. */
+void orc_box_filter(int H, int W, const double* dX, const double* dY, int N, const double* sigma,
+                    const double* src, double* dst) {
+    memcpy(dst, src, sizeof(double) * (size_t)H * W);
+    const int n = H > W ? H : W;
+    for (int i = 0; i < N; ++i) {
+        const double r = sigma[i] * sqrt(3.0);
+#pragma omp parallel
+        {
+            double* ct = (double*)malloc(sizeof(double) * n);
+            double* tmp = (double*)malloc(sizeof(double) * n);
+#pragma omp for schedule(static)
+            for (int y = 0; y < H; ++y) box_line(W, dst + (long)y * W, 1, dX + (long)y * W, 1, r, ct, tmp);
+#pragma omp for schedule(static)
+            for (int x = 0; x < W; ++x) box_line(H, dst + x, W, dY + x, W, r, ct, tmp);
+            free(ct);
+            free(tmp);
+        }
     }
 }
 

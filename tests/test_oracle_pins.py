@@ -482,3 +482,62 @@ def test_confidence_properties():
     tt = np.where(np.arange(16) < 8, 0.0, 1.0)[None, :].repeat(8, 0)
     c = oracle.confidence(G, tt, 8.0, 0.05, sigma_c=0.1)
     assert c[:, :4].min() > 0.999 and c[:, 12:].min() > 0.999
+
+
+# ---------------------------------------------------------------- box-kernel filter (Eq. 10's printed kernel)
+def box_pass_dense(d_line, r):
+    """Row-normalised 0/1 matrix of one line: W_nm = 1 if |ct_n - ct_m| <= r, ct a cumulative sum
+    of the distances (numpy cumsum, independent of the oracle's loop)."""
+    ct = np.concatenate([[0.0], np.cumsum(d_line[1:])])
+    Wm = (np.abs(ct[:, None] - ct[None, :]) <= r).astype(float)
+    return Wm / Wm.sum(1, keepdims=True)
+
+
+@pytest.mark.parametrize("H,W,N", [(5, 7, 3), (1, 9, 2), (8, 1, 2), (6, 6, 1)])
+def test_box_filter_equals_dense_product(H, W, N):
+    rng = np.random.default_rng(300 + H * W + N)
+    I = rand_guide(rng, 3, H, W)
+    dX, dY = oracle.distances(I, 3.0, 0.5)
+    sig, _ = oracle.schedule(3.0, N)
+    src = rng.normal(size=(H, W))
+    x = src.ravel().copy()
+    n = H * W
+    for s in sig:
+        r = s * np.sqrt(3.0)
+        Hm = np.zeros((n, n))
+        for y in range(H):
+            idx = y * W + np.arange(W)
+            Hm[np.ix_(idx, idx)] = box_pass_dense(dX[y], r)
+        Vm = np.zeros((n, n))
+        for c in range(W):
+            idx = np.arange(H) * W + c
+            Vm[np.ix_(idx, idx)] = box_pass_dense(dY[:, c], r)
+        x = Vm @ (Hm @ x)
+    np.testing.assert_allclose(oracle.box_filter_d(dX, dY, sig, src).ravel(), x, rtol=0, atol=1e-13)
+
+
+def test_box_filter_uniform_guide_is_a_moving_average():
+    """Unit distances (flat guide): each pass averages the samples within floor(r) positions, a
+    plain moving average truncated at the borders."""
+    H, W = 1, 40
+    I = np.full((1, H, W), 0.5)
+    src = np.random.default_rng(5).normal(size=(H, W))
+    dX, dY = oracle.distances(I, 4.0, 0.2)
+    sig = np.array([2.1])  # r = 3.64: windows of 3 samples on each side
+    out = oracle.box_filter_d(dX, dY, sig, src)[0]
+    ref = np.array([src[0, max(0, i - 3):i + 4].mean() for i in range(W)])
+    np.testing.assert_allclose(out, ref, rtol=0, atol=1e-14)
+
+
+def test_box_filter_constants_and_edges():
+    rng = np.random.default_rng(6)
+    I = rand_guide(rng, 3, 10, 12)
+    out = oracle.box_filter(I, np.full((10, 12), -1.25), 6.0, 0.3)
+    np.testing.assert_allclose(out, -1.25, rtol=0, atol=1e-14)
+    # a strong guide edge (distance far above every radius) is never crossed
+    G = np.zeros((1, 6, 10))
+    G[:, :, 5:] = 1.0
+    src = np.where(np.arange(10) < 5, 2.0, -3.0)[None, :].repeat(6, 0) + 0.0
+    out = oracle.box_filter(G, src, 6.0, 0.001)
+    np.testing.assert_allclose(out[:, :5], 2.0, atol=1e-14)
+    np.testing.assert_allclose(out[:, 5:], -3.0, atol=1e-14)
