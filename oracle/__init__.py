@@ -19,6 +19,7 @@ from . import build as _build
 NORM_L1, NORM_L2 = 0, 1
 UPDATE_GD, UPDATE_JACOBI = 0, 1
 CONF_PLAIN, CONF_SUPPORT = 0, 1
+KERNEL_RF, KERNEL_BOX = 0, 1
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -40,6 +41,7 @@ def _load():
         lib.orc_support.argtypes = [i, i, p, p, d, p, p]
         lib.orc_confidence.argtypes = [i, i, p, p, i, p, p, d, p]
         lib.orc_box_filter.argtypes = [i, i, p, p, i, p, p, p]
+        lib.orc_solve_kernel.argtypes = [i, i, p, p, p, p, p, d, d, d, i, i, i, i, i, p, p]
         lib.orc_solve.argtypes = [i, i, p, p, p, p, p, d, d, d, i, i, i, i, p, p]
         lib.orc_solve.restype = i
         lib.orc_filter_adjoint.argtypes = [i, i, p, p, i, p, p, p, p, p, p]
@@ -184,26 +186,28 @@ def support(dX, dY, sigma_s):
 
 
 def solve_d(dX, dY, t, c, *, lam, sigma_s, step=0.99, iterations=10, passes=3, update=UPDATE_GD,
-            conf_mode=CONF_PLAIN, z_init=None, checkpoints=False):
-    """The solver on precomputed distances.  Returns z_K (and z_0..z_{K-1})."""
+            conf_mode=CONF_PLAIN, z_init=None, checkpoints=False, kernel=KERNEL_RF):
+    """The solver on precomputed distances.  Returns z_K (and z_0..z_{K-1}).  kernel: the
+    recursive filter (default) or the box kernel of Eq. 10."""
     dX, dY, t, c = _f64(dX), _f64(dY), _f64(t), _f64(c)
     z0 = None if z_init is None else _f64(z_init)
     H, W = t.shape
     z = np.empty((H, W))
     ck = np.empty((max(iterations, 1), H, W)) if checkpoints else None
-    _load().orc_solve(H, W, _ptr(dX), _ptr(dY), _ptr(t), _ptr(c), _ptr(z0), float(lam), float(sigma_s),
-                      float(step), int(iterations), int(passes), int(update), int(conf_mode), _ptr(z), _ptr(ck))
+    _load().orc_solve_kernel(H, W, _ptr(dX), _ptr(dY), _ptr(t), _ptr(c), _ptr(z0), float(lam), float(sigma_s),
+                             float(step), int(iterations), int(passes), int(update), int(conf_mode), int(kernel),
+                             _ptr(z), _ptr(ck))
     if checkpoints:
         return z, ck[:iterations]
     return z
 
 
 def solve(I, t, c, *, lam, sigma_s, sigma_r, step=0.99, iterations=10, passes=3, norm=NORM_L1,
-          update=UPDATE_GD, conf_mode=CONF_PLAIN, z_init=None, checkpoints=False):
+          update=UPDATE_GD, conf_mode=CONF_PLAIN, z_init=None, checkpoints=False, kernel=KERNEL_RF):
     """DTS solve on guide I (C, H, W) with target t and confidence c (H, W)."""
     dX, dY = distances(I, sigma_s, sigma_r, norm)
     return solve_d(dX, dY, t, c, lam=lam, sigma_s=sigma_s, step=step, iterations=iterations, passes=passes,
-                   update=update, conf_mode=conf_mode, z_init=z_init, checkpoints=checkpoints)
+                   update=update, conf_mode=conf_mode, z_init=z_init, checkpoints=checkpoints, kernel=kernel)
 
 
 def filter_adjoint(dX, dY, a, src, gdst):

@@ -316,9 +316,23 @@ static void update(long n, const double* zk, const double* zbar, const double* t
 /* The solver: K iterations of  z_bar = A z_k;  z_{k+1} = update(z_k, z_bar)
  * starting from z_0 = z0 (the target t when z0 is NULL).  When ckpt is not
  * NULL it receives z_0 .. z_{K-1} (K planes).  Returns 0. */
+/* The solve with either kernel of the edge-aware mean: kernel 0 the recursive filter
+ * (orc_filter), kernel 1 the box kernel Eq. 10 prints (orc_box_filter); the iterations and the
+ * update are the same. */
+int orc_solve_kernel(int H, int W, const double* dX, const double* dY, const double* t, const double* c,
+                     const double* z0, double lambda, double sigma_s, double eta, int K, int N, int update_mode,
+                     int conf_mode, int kernel, double* z_out, double* ckpt);
+
 int orc_solve(int H, int W, const double* dX, const double* dY, const double* t, const double* c, const double* z0,
               double lambda, double sigma_s, double eta, int K, int N, int update_mode, int conf_mode,
               double* z_out, double* ckpt) {
+    return orc_solve_kernel(H, W, dX, dY, t, c, z0, lambda, sigma_s, eta, K, N, update_mode, conf_mode, 0, z_out,
+                            ckpt);
+}
+
+int orc_solve_kernel(int H, int W, const double* dX, const double* dY, const double* t, const double* c,
+                     const double* z0, double lambda, double sigma_s, double eta, int K, int N, int update_mode,
+                     int conf_mode, int kernel, double* z_out, double* ckpt) {
     long n = (long)H * W;
     double* sig = (double*)malloc(sizeof(double) * (size_t)N);
     double* a = (double*)malloc(sizeof(double) * (size_t)N);
@@ -330,7 +344,8 @@ int orc_solve(int H, int W, const double* dX, const double* dY, const double* t,
     memcpy(z, z0 ? z0 : t, sizeof(double) * (size_t)n);
     for (int k = 0; k < K; ++k) {
         if (ckpt) memcpy(ckpt + (long)k * n, z, sizeof(double) * (size_t)n);
-        orc_filter(H, W, dX, dY, N, a, z, zbar);
+        if (kernel == 1) orc_box_filter(H, W, dX, dY, N, sig, z, zbar);
+        else orc_filter(H, W, dX, dY, N, a, z, zbar);
         update(n, z, zbar, t, chat, lambda, eta, update_mode, conf_mode == ORC_CONF_SUPPORT, z);
     }
     memcpy(z_out, z, sizeof(double) * (size_t)n);

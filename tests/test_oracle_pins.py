@@ -541,3 +541,37 @@ def test_box_filter_constants_and_edges():
     out = oracle.box_filter(G, src, 6.0, 0.001)
     np.testing.assert_allclose(out[:, :5], 2.0, atol=1e-14)
     np.testing.assert_allclose(out[:, 5:], -3.0, atol=1e-14)
+
+
+def test_box_solve_one_step_and_fixed_point():
+    """The solve with the box kernel: one GD step equals the dense update with the dense box
+    matrix, and many Jacobi steps reach the dense solution of (lambda (I - A) + C) z = C t."""
+    rng = np.random.default_rng(77)
+    H, W = 4, 5
+    I = rand_guide(rng, 3, H, W)
+    dX, dY = oracle.distances(I, 3.0, 0.5)
+    sig, _ = oracle.schedule(3.0, 2)
+    n = H * W
+    A = np.eye(n)
+    for s in sig:
+        r = s * np.sqrt(3.0)
+        Hm = np.zeros((n, n))
+        for y in range(H):
+            idx = y * W + np.arange(W)
+            Hm[np.ix_(idx, idx)] = box_pass_dense(dX[y], r)
+        Vm = np.zeros((n, n))
+        for cx in range(W):
+            idx = np.arange(H) * W + cx
+            Vm[np.ix_(idx, idx)] = box_pass_dense(dY[:, cx], r)
+        A = Vm @ Hm @ A
+    t = rng.normal(size=(H, W))
+    c = rng.uniform(0.2, 1.0, (H, W))
+    lam, eta = 0.8, 0.99
+    z1 = oracle.solve_d(dX, dY, t, c, lam=lam, sigma_s=3.0, passes=2, iterations=1, kernel=oracle.KERNEL_BOX)
+    tf, cf = t.ravel(), c.ravel()
+    ref = tf - eta * (lam * (tf - A @ tf) + cf * (tf - tf))
+    np.testing.assert_allclose(z1.ravel(), ref, rtol=0, atol=1e-13)
+    zK = oracle.solve_d(dX, dY, t, c, lam=lam, sigma_s=3.0, passes=2, iterations=3000, update=oracle.UPDATE_JACOBI,
+                        kernel=oracle.KERNEL_BOX)
+    zs = np.linalg.solve(lam * (np.eye(n) - A) + np.diag(cf), cf * tf)
+    np.testing.assert_allclose(zK.ravel(), zs, rtol=0, atol=1e-9)
