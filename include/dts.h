@@ -51,6 +51,7 @@ typedef enum dts_dtype { DTS_F32 = 0, DTS_BF16 = 1, DTS_F16 = 2 } dts_dtype;
 typedef enum dts_norm { DTS_NORM_L1 = 0, DTS_NORM_L2 = 1 } dts_norm;
 typedef enum dts_update { DTS_UPDATE_GD = 0, DTS_UPDATE_JACOBI = 1 } dts_update;
 typedef enum dts_conf_mode { DTS_CONF_PLAIN = 0, DTS_CONF_SUPPORT = 1 } dts_conf_mode;
+typedef enum dts_filter_kernel { DTS_KERNEL_RF = 0, DTS_KERNEL_BOX = 1 } dts_filter_kernel;
 
 /* Planar guide image I: channel k, row y, column x is element
  * k * ch_stride + y * row_stride + x of `data` (dtype F32, BF16 or F16).
@@ -77,6 +78,10 @@ typedef struct dts_guide {
  *  conf_mode   DTS_CONF_PLAIN (c as given) or DTS_CONF_SUPPORT (c weighted by
  *              S_flat / sum_j W_ij, §3.1 after Eq. 6)
  *  dist_dtype  storage of the distance planes: DTS_F32 or DTS_F16
+ *  filter_kernel  DTS_KERNEL_RF (default): the recursive-filter kernel; DTS_KERNEL_BOX: the
+ *              box kernel Eq. 10 prints, W_ij = 1 if |DT_i - DT_j| <= r with r = sigma_i sqrt(3)
+ *              per pass (normalized convolution in the transformed domain); FP32 distances,
+ *              DTS_CONF_PLAIN and no checkpoints only, lines up to 8192 positions, no backward
  *  save_checkpoints  0: nothing kept; 1: dts_solve keeps z_0 .. z_{K-1} in the
  *              workspace for dts_solve_backward (workspace sized with with_backward = 1),
  *              which recomputes each iteration's pass inputs from them; 2: it also keeps
@@ -89,6 +94,7 @@ typedef struct dts_params {
     int norm, update, conf_mode;
     int dist_dtype;
     int save_checkpoints;
+    int filter_kernel;
 } dts_params;
 
 /* Human-readable name of a status code (static string). */
@@ -134,7 +140,8 @@ int dts_solve(const dts_guide* guide, const void* target, int target_dtype, cons
  * units of t).  V below 0 can only come from rounding and is taken as 0, so 0 < c <= 1.
  * target: dense H x W of target_dtype (F32, BF16 or F16); conf_out: dense H x W FP32.
  * Workspace as for dts_filter (dts_workspace_size with with_backward = 0).  Argument errors
- * (including sigma_c <= 0) are DTS_ERR_INVALID_ARG, returned before any device work. */
+ * (including sigma_c <= 0) are DTS_ERR_INVALID_ARG, returned before any device work; the box
+ * kernel (filter_kernel = DTS_KERNEL_BOX) is DTS_ERR_UNSUPPORTED here. */
 int dts_confidence(const dts_guide* guide, const void* target, int target_dtype, const dts_params* params,
                    float sigma_c, float* conf_out, void* ws, size_t ws_bytes, dts_stream stream);
 

@@ -30,7 +30,9 @@ int ensure_prepared() {
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DTS_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_prep_mutex);
     if (!g_prepared[dev]) {
-        if (prepare_kernels() != cudaSuccess || prepare_backward_kernels() != cudaSuccess) return DTS_ERR_CUDA;
+        if (prepare_kernels() != cudaSuccess || prepare_backward_kernels() != cudaSuccess ||
+            prepare_box_kernels() != cudaSuccess)
+            return DTS_ERR_CUDA;
         g_prepared[dev] = true;
     }
     return DTS_OK;
@@ -88,6 +90,15 @@ int check_params(const dts_params* p) {
     if (p->conf_mode != DTS_CONF_PLAIN && p->conf_mode != DTS_CONF_SUPPORT) return DTS_ERR_INVALID_ARG;
     if (p->dist_dtype != DTS_F32 && p->dist_dtype != DTS_F16) return DTS_ERR_INVALID_ARG;
     if (p->save_checkpoints < 0 || p->save_checkpoints > 2) return DTS_ERR_INVALID_ARG;
+    if (p->filter_kernel != DTS_KERNEL_RF && p->filter_kernel != DTS_KERNEL_BOX) return DTS_ERR_INVALID_ARG;
+    return DTS_OK;
+}
+
+// what the box-kernel filter supports (DTS_ERR_UNSUPPORTED otherwise)
+int check_box(const dts_guide* g, const dts_params* p) {
+    if (p->filter_kernel != DTS_KERNEL_BOX) return DTS_OK;
+    if (p->dist_dtype != DTS_F32 || p->conf_mode != DTS_CONF_PLAIN || p->save_checkpoints) return DTS_ERR_UNSUPPORTED;
+    if (g->H > kBoxMaxLine || g->W > kBoxMaxLine) return DTS_ERR_UNSUPPORTED;
     return DTS_OK;
 }
 
@@ -102,6 +113,8 @@ struct Layout {
     int nstrips128;
     int z_planes;       // 1 (in place) or K checkpoints
     size_t passes;      // save_checkpoints = 2: K x 2N planes, (k, 0) = zbar_k, (k, q) = input of pass q
+    size_t dYt, ut;     // box kernel: transposed dY and working plane (W rows, pitch tpitch)
+    long long tpitch;
     size_t fwd_end;     // bytes used by the forward
     // backward scratch
     size_t xin;         // 2N pass-input planes
@@ -135,6 +148,14 @@ Layout make_layout(int H, int W, const dts_params* p, int with_backward) {
     const bool keep = p->save_checkpoints || with_backward;
     L.z_planes = keep ? (p->iterations > 0 ? p->iterations : 1) : 1;
     off += (size_t)L.z_planes * L.plane_f32;
+    if (p->filter_kernel == DTS_KERNEL_BOX) {  // transposed dY and working plane (W rows of pitch_for(H))
+        L.tpitch = pitch_for(H);
+        const size_t tplane = align_up((size_t)W * (size_t)L.tpitch * 4, kPlaneAlign);
+        L.dYt = off;
+        off += tplane;
+        L.ut = off;
+        off += tplane;
+    }
     L.passes = off;
     if (p->save_checkpoints == 2) off += (size_t)(p->iterations > 0 ? p->iterations : 1) * 2 * p->passes * L.plane_f32;
     L.fwd_end = off;
@@ -161,6 +182,12 @@ void pass_log2a(double sigma_s, int N, float* k2) {
         const double sig = sigma_s * sqrt(3.0) * ldexp(1.0, N - i) / sqrt(ldexp(1.0, 2 * N) - 1.0);
         k2[i - 1] = (float)(-sqrt(2.0) / (sig * log(2.0)));
     }
+}
+
+// Per-pass sigma_i of the same schedule (for the box kernel's radius r_i = sigma_i sqrt(3)).
+void pass_sigma(double sigma_s, int N, double* sig) {
+    for (int i = 1; i <= N; ++i)
+        sig[i - 1] = sigma_s * sqrt(3.0) * ldexp(1.0, N - i) / sqrt(ldexp(1.0, 2 * N) - 1.0);
 }
 
 int cuda_status(cudaError_t e) {
@@ -258,6 +285,75 @@ int run_support(const dts_guide* g, const dts_params* p, const Layout& L, void* 
     c.zout_pitch = L.pitch;
     c.s_flat = (float)(((1.0 + a) / (1.0 - a)) * ((1.0 + a) / (1.0 - a)));
     return cuda_status(launch_col_pass(c, dh, PASS_SUPPORT_CONF, pl.cols, s));
+}
+
+// The box-kernel filter of src (pitch L.pitch) into dst (pitch dst_pitch; may be src): per pass a
+// box average along the rows, then along the columns as rows of the transposed plane.  Needs the
+// distances, and dY transposed into L.dYt (prepare_box_distances).
+int run_box_filter(const dts_guide* g, const dts_params* p, const Layout& L, void* ws, const float* src, float* dst,
+                   long long dst_pitch, cudaStream_t s) {
+    const int H = g->H, W = g->W;
+    const long long P = L.pitch, TP = L.tpitch;
+    float* u = reinterpret_cast<float*>(ws_at(ws, L.u));
+    float* ut = reinterpret_cast<float*>(ws_at(ws, L.ut));
+    const float* dX = reinterpret_cast<const float*>(ws_at(ws, L.dX));
+    const float* dYt = reinterpret_cast<const float*>(ws_at(ws, L.dYt));
+    double sig[kMaxPasses];
+    pass_sigma(p->sigma_s, p->passes, sig);
+    int st;
+    for (int i = 0; i < p->passes; ++i) {
+        const double r = sig[i] * sqrt(3.0);
+        if ((st = cuda_status(launch_box_lines(i == 0 ? src : u, P, u, P, dX, P, W, H, r, s)))) return st;
+        if ((st = cuda_status(launch_transpose(u, P, ut, TP, H, W, s)))) return st;
+        if ((st = cuda_status(launch_box_lines(ut, TP, ut, TP, dYt, TP, H, W, r, s)))) return st;
+        const bool last = i + 1 == p->passes;
+        if ((st = cuda_status(launch_transpose(ut, TP, last ? dst : u, last ? dst_pitch : P, W, H, s)))) return st;
+    }
+    return DTS_OK;
+}
+
+int prepare_box_distances(const dts_guide* g, const Layout& L, void* ws, cudaStream_t s) {
+    return cuda_status(launch_transpose(reinterpret_cast<const float*>(ws_at(ws, L.dY)), L.pitch,
+                                        reinterpret_cast<float*>(ws_at(ws, L.dYt)), L.tpitch, g->H, g->W, s));
+}
+
+// The solve with the box kernel: z_0 = z_init or t; per iteration zbar = box filter of z_k, then
+// the update of Eq. 3 / Eq. 4 in place (elementwise kernel).
+int solve_box(const dts_guide* g, const void* target, int tdt, const float* conf, const float* z_init,
+              const dts_params* p, float* z_out, void* ws, const Layout& L, cudaStream_t s) {
+    const int K = p->iterations, H = g->H, W = g->W;
+    if (K == 0) {
+        if (z_init) return cuda_status(launch_copy_plane(z_init, DTS_F32, W, z_out, W, H, W, s));
+        return cuda_status(launch_copy_plane(target, tdt, W, z_out, W, H, W, s));
+    }
+    int st;
+    if ((st = bind_workspace(ws, L, s))) return st;
+    float* z = reinterpret_cast<float*>(ws_at(ws, L.z));
+    if (z_init) st = run_distances(g, p, L, ws, z_init, DTS_F32, z, s);
+    else st = run_distances(g, p, L, ws, target, tdt, z, s);
+    if (st || (st = prepare_box_distances(g, L, ws, s))) return st;
+    float* zbar = reinterpret_cast<float*>(ws_at(ws, L.u));
+    for (int k = 0; k < K; ++k) {
+        if ((st = run_box_filter(g, p, L, ws, z, zbar, L.pitch, s))) return st;
+        PassArgs a = base_pass(g, L);
+        a.src = zbar;
+        a.zk = z;
+        a.t = target;
+        a.t_dtype = tdt;
+        a.c = conf;
+        a.lambda = p->lambda;
+        a.step = p->step;
+        a.update = p->update;
+        if (k + 1 == K) {
+            a.zout = z_out;
+            a.zout_pitch = W;
+        } else {
+            a.zout = z;
+            a.zout_pitch = L.pitch;
+        }
+        if ((st = cuda_status(launch_update(a, s)))) return st;
+    }
+    return DTS_OK;
 }
 
 }  // namespace
@@ -425,6 +521,7 @@ extern "C" int dts_filter(const dts_guide* guide, const dts_params* params, cons
     dts_params p = *params;
     p.conf_mode = DTS_CONF_PLAIN;
     p.save_checkpoints = 0;
+    if ((st = check_box(guide, &p))) return st;
     const Layout L = make_layout(guide->H, guide->W, &p, 0);
     if (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.fwd_end) return DTS_ERR_WORKSPACE;
     if ((st = ensure_prepared())) return st;
@@ -432,6 +529,10 @@ extern "C" int dts_filter(const dts_guide* guide, const dts_params* params, cons
     if ((st = bind_workspace(ws, L, s))) return st;
     float* u = reinterpret_cast<float*>(ws_at(ws, L.u));
     if ((st = run_distances(guide, &p, L, ws, src, DTS_F32, u, s))) return st;
+    if (p.filter_kernel == DTS_KERNEL_BOX) {
+        if ((st = prepare_box_distances(guide, L, ws, s))) return st;
+        return run_box_filter(guide, &p, L, ws, u, dst, guide->W, s);
+    }
     float k2[kMaxPasses];
     pass_log2a(p.sigma_s, p.passes, k2);
     const int dh = p.dist_dtype == DTS_F16;
@@ -470,6 +571,7 @@ extern "C" int dts_confidence(const dts_guide* guide, const void* target, int ta
     dts_params p = *params;
     p.conf_mode = DTS_CONF_PLAIN;
     p.save_checkpoints = 0;
+    if (p.filter_kernel != DTS_KERNEL_RF) return DTS_ERR_UNSUPPORTED;  // the recursive-filter mean
     const Layout L = make_layout(guide->H, guide->W, &p, 0);
     if (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.fwd_end) return DTS_ERR_WORKSPACE;
     if ((st = ensure_prepared())) return st;
@@ -512,12 +614,15 @@ extern "C" int dts_solve(const dts_guide* guide, const void* target, int target_
     if (!st) st = check_params(params);
     if (st) return st;
     if (!target || !conf || !z_out || !valid_dtype(target_dtype)) return DTS_ERR_INVALID_ARG;
+    if ((st = check_box(guide, params))) return st;
     Plans pl;
     if ((st = make_plans(guide->H, guide->W, &pl))) return st;
     const Layout L = make_layout(guide->H, guide->W, params, 0);
     if (params->iterations > 0 && (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.fwd_end))
         return DTS_ERR_WORKSPACE;
     if ((st = ensure_prepared())) return st;
+    if (params->filter_kernel == DTS_KERNEL_BOX)
+        return solve_box(guide, target, target_dtype, conf, z_init, params, z_out, ws, L, (cudaStream_t)stream);
     return solve_forward(guide, target, target_dtype, conf, z_init, params, z_out, ws, L, pl, (cudaStream_t)stream);
 }
 
@@ -628,6 +733,7 @@ extern "C" int dts_solve_batched(int n, const dts_guide* guides, const void* con
                                  size_t ws_bytes, dts_stream stream) {
     if (n < 1 || !guides || !targets || !confs || !z_out || !valid_dtype(target_dtype)) return DTS_ERR_INVALID_ARG;
     int st = check_params(params);
+    if (!st && params->filter_kernel != DTS_KERNEL_RF) st = DTS_ERR_UNSUPPORTED;  // recursive-filter kernel only
     if (st) return st;
     if (params->save_checkpoints) return DTS_ERR_UNSUPPORTED;
     for (int i = 0; i < n; ++i) {
@@ -702,6 +808,7 @@ extern "C" int dts_autotune(const dts_guide* guide, const dts_params* params, vo
                             dts_stream stream) {
     int st = check_guide(guide);
     if (!st) st = check_params(params);
+    if (!st && params->filter_kernel != DTS_KERNEL_RF) st = DTS_ERR_UNSUPPORTED;  // recursive-filter kernel only
     if (st) return st;
     Plans pl;
     if ((st = make_plans(guide->H, guide->W, &pl))) return st;
@@ -848,6 +955,7 @@ extern "C" int dts_solve_noalloc(const dts_guide* guide, const void* target, int
                                  const float* z_init, const dts_params* params, float* z_out, dts_stream stream) {
     int st = check_guide(guide);
     if (!st) st = check_params(params);
+    if (!st && params->filter_kernel != DTS_KERNEL_RF) st = DTS_ERR_UNSUPPORTED;  // recursive-filter kernel only
     if (st) return st;
     if (!target || !conf || !z_out || !valid_dtype(target_dtype)) return DTS_ERR_INVALID_ARG;
     if (params->save_checkpoints) return DTS_ERR_UNSUPPORTED;  // checkpoints must outlive the call
@@ -867,6 +975,7 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
                                   float* grad_z_init, dts_stream stream) {
     int st = check_guide(guide);
     if (!st) st = check_params(params);
+    if (!st && params->filter_kernel != DTS_KERNEL_RF) st = DTS_ERR_UNSUPPORTED;  // recursive-filter kernel only
     if (st) return st;
     if (!target || !conf || !grad_z || !valid_dtype(target_dtype)) return DTS_ERR_INVALID_ARG;
     if (params->conf_mode != DTS_CONF_PLAIN) return DTS_ERR_UNSUPPORTED;

@@ -1,0 +1,156 @@
+// The edge-aware mean with the box kernel that Eq. 10 prints, W_ij = 1 if |DT_i - DT_j| <= r
+// (normalized convolution in the transformed domain; per pass radius r_i = sigma_i sqrt(3)).
+// Along a line the domain coordinate is ct[0] = 0, ct[n] = ct[n-1] + d[n]; out[n] averages the
+// x[m] with |ct[m] - ct[n]| <= r.  FP32 distances >= 1 are multiples of 2^-23, so ct is kept as
+// an exact integer count of 2^-23 units (64 bits: exact for coordinates below 2^40) and window
+// membership compares the exact difference ct[m] - ct[n] with R = floor(r 2^23), which is the
+// same decision as |ct[m] - ct[n]| <= r in exact arithmetic: which samples a window holds is
+// fixed by the inputs alone, whatever the order of the additions.  The sums of x are FP64
+// prefix sums (one addition and one subtraction per position: GB300's FP64 rate is low).
+// Rows run directly; columns run as rows of the transposed plane (transpose_kernel).
+#include "dts_scan.cuh"
+
+namespace dts {
+
+namespace {
+
+using namespace scan;
+
+constexpr int kBoxThreads = 512;
+constexpr double kBoxUnit = 8388608.0;  // 2^23: FP32 values >= 1 are whole multiples of 2^-23
+
+// One CTA per line of length L (L <= kBoxMaxLine): stage the line in shared memory, exact prefix
+// sums, then each thread averages the windows of its contiguous chunk of positions.
+__global__ void __launch_bounds__(kBoxThreads) box_line_kernel(const float* src, long long sp, float* dst,
+                                                               long long dstp, const float* d, long long dp, int L,
+                                                               int lines, long long R) {
+    extern __shared__ __align__(16) unsigned char box_smem[];
+    long long* ct = reinterpret_cast<long long*>(box_smem);  // L, in 2^-23 units
+    double* S = reinterpret_cast<double*>(ct + L);           // L + 1: S[m] = x[0] + ... + x[m-1]
+    float* xs = reinterpret_cast<float*>(S + L + 1);         // L
+    float* ds = xs + L;                                      // L
+    __shared__ long long w_d[kBoxThreads / 32];
+    __shared__ double w_x[kBoxThreads / 32];
+    const int line = blockIdx.x;
+    if (line >= lines) return;  // uniform over the CTA
+    wait_predecessor();
+    const float* xl = src + (long long)line * sp;
+    const float* dl = d + (long long)line * dp;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        xs[i] = xl[i];
+        ds[i] = i ? dl[i] : 0.f;  // ct[0] = 0: the first distance of a line is never used
+    }
+    __syncthreads();
+    const int per = (L + blockDim.x - 1) / blockDim.x;
+    const int b = min((int)threadIdx.x * per, L);
+    const int e = min(b + per, L);
+    long long sd = 0;
+    double sx = 0.0;
+    for (int i = b; i < e; ++i) {
+        sd += __double2ll_rn((double)ds[i] * kBoxUnit);
+        sx += (double)xs[i];
+    }
+    // exclusive scan of the chunk sums over the CTA (warp shuffles, then the warp totals)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long id = sd;
+    double ix = sx;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long od = __shfl_up_sync(kFull, id, off);
+        const double ox = __shfl_up_sync(kFull, ix, off);
+        if (lane >= off) {
+            id += od;
+            ix += ox;
+        }
+    }
+    if (lane == 31) {
+        w_d[warp] = id;
+        w_x[warp] = ix;
+    }
+    __syncthreads();
+    long long cd = id - sd;
+    double cx = ix - sx;
+    for (int q = 0; q < warp; ++q) {
+        cd += w_d[q];
+        cx += w_x[q];
+    }
+    for (int i = b; i < e; ++i) {
+        cd += __double2ll_rn((double)ds[i] * kBoxUnit);
+        ct[i] = cd;
+        S[i] = cx;
+        cx += (double)xs[i];
+    }
+    if (b < e && e == L) S[L] = cx;
+    __syncthreads();
+    release_successor();
+    if (b >= e) return;
+    // first window by binary search, then both ends move forward with the position
+    const long long cb = ct[b];
+    int lo = 0, hi = b;  // lo: first m with ct[b] - ct[m] <= R
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cb - ct[mid] <= R) hi = mid;
+        else lo = mid + 1;
+    }
+    int a = b, z = L - 1;  // up: last m with ct[m] - ct[b] <= R
+    while (a < z) {
+        const int mid = (a + z + 1) >> 1;
+        if (ct[mid] - cb <= R) a = mid;
+        else z = mid - 1;
+    }
+    int up = a;
+    float* out = dst + (long long)line * dstp;
+    for (int i = b; i < e; ++i) {
+        const long long ci = ct[i];
+        while (ci - ct[lo] > R) ++lo;
+        while (up + 1 < L && ct[up + 1] - ci <= R) ++up;
+        out[i] = (float)(S[up + 1] - S[lo]) / (float)(up - lo + 1);
+    }
+}
+
+// dst[x][y] = src[y][x] for an H x W plane (32 x 32 tiles through shared memory)
+__global__ void __launch_bounds__(256) transpose_kernel(const float* src, long long sp, float* dst, long long dp,
+                                                        int H, int W) {
+    __shared__ float tile[32][33];
+    wait_predecessor();
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int y = y0 + j, x = x0 + threadIdx.x;
+        if (y < H && x < W) tile[j][threadIdx.x] = src[(long long)y * sp + x];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int x = x0 + j, y = y0 + threadIdx.x;
+        if (x < W && y < H) dst[(long long)x * dp + y] = tile[threadIdx.x][j];
+    }
+}
+
+}  // namespace
+
+size_t box_line_smem(int L) { return (size_t)L * 8 + (size_t)(L + 1) * 8 + (size_t)L * 8; }  // ct, S, x and d
+
+cudaError_t prepare_box_kernels() {
+    return cudaFuncSetAttribute((const void*)box_line_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)box_line_smem(kBoxMaxLine));
+}
+
+cudaError_t launch_box_lines(const float* src, long long sp, float* dst, long long dstp, const float* d, long long dp,
+                             int L, int lines, double r, cudaStream_t s) {
+    if (L < 1 || L > kBoxMaxLine) return cudaErrorInvalidValue;
+    const long long R = (long long)floor(r * kBoxUnit);  // exact: r 2^23 scales by a power of two
+    const int h = prof_begin(KID_BOX, (long long)L * lines, 0, s);
+    const cudaError_t e = launch_ex_smem(box_line_kernel, dim3((unsigned)lines), dim3(kBoxThreads), 0, box_line_smem(L),
+                                         s, src, sp, dst, dstp, d, dp, L, lines, R);
+    prof_end(h, s);
+    return e;
+}
+
+cudaError_t launch_transpose(const float* src, long long sp, float* dst, long long dp, int H, int W, cudaStream_t s) {
+    const int h = prof_begin(KID_TRANSPOSE, (long long)H * W, 0, s);
+    const dim3 grid((unsigned)((W + 31) / 32), (unsigned)((H + 31) / 32));
+    const cudaError_t e = launch_ex(transpose_kernel, grid, dim3(32, 8), 0, s, src, sp, dst, dp, H, W);
+    prof_end(h, s);
+    return e;
+}
+
+}  // namespace dts

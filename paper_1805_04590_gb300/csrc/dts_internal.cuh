@@ -191,6 +191,8 @@ enum KernelId {
     KID_COL_STRIP = 17,
     KID_SQUARE = 18,
     KID_CONFIDENCE = 19,
+    KID_BOX = 20,
+    KID_TRANSPOSE = 21,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
@@ -221,6 +223,12 @@ void set_tuned_row(int W, int items);
 void set_tuned_col(int H, const ColPlan& p);
 int col_candidates(int H, ColPlan* out, int max_out);
 cudaError_t launch_update(const PassArgs& a, cudaStream_t s);
+// box-kernel filter (dts_box.cu): lines up to kBoxMaxLine positions (FP64 sums in shared memory)
+constexpr int kBoxMaxLine = 8192;
+cudaError_t prepare_box_kernels();
+cudaError_t launch_box_lines(const float* src, long long sp, float* dst, long long dstp, const float* d, long long dp,
+                             int L, int lines, double r, cudaStream_t s);
+cudaError_t launch_transpose(const float* src, long long sp, float* dst, long long dp, int H, int W, cudaStream_t s);
 cudaError_t launch_square_plane(const float* src, float* dst, long long pitch, int H, int W, cudaStream_t s);
 cudaError_t launch_confidence(const float* m1, const float* m2, long long pitch, int H, int W, float sigma_c,
                               float* c, cudaStream_t s);

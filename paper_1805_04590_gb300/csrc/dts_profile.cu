@@ -112,6 +112,8 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_COL_STRIP: return "col_strip_kernel";
         case KID_SQUARE: return "square_plane_kernel";
         case KID_CONFIDENCE: return "confidence_kernel";
+        case KID_BOX: return "box_line_kernel";
+        case KID_TRANSPOSE: return "transpose_kernel";
         default: return "unknown";
     }
 }

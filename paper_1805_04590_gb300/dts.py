@@ -21,6 +21,7 @@ F32, BF16, F16 = 0, 1, 2
 NORM_L1, NORM_L2 = 0, 1
 UPDATE_GD, UPDATE_JACOBI = 0, 1
 CONF_PLAIN, CONF_SUPPORT = 0, 1
+KERNEL_RF, KERNEL_BOX = 0, 1
 
 STATUS = {0: "DTS_OK", 1: "DTS_ERR_INVALID_ARG", 2: "DTS_ERR_UNSUPPORTED", 3: "DTS_ERR_WORKSPACE",
           4: "DTS_ERR_CUDA", 5: "DTS_ERR_TIMEOUT", 6: "DTS_ERR_NONFINITE"}
@@ -43,7 +44,7 @@ class CParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_float), ("sigma_s", ctypes.c_float), ("sigma_r", ctypes.c_float),
                 ("step", ctypes.c_float), ("iterations", ctypes.c_int), ("passes", ctypes.c_int),
                 ("norm", ctypes.c_int), ("update", ctypes.c_int), ("conf_mode", ctypes.c_int),
-                ("dist_dtype", ctypes.c_int), ("save_checkpoints", ctypes.c_int)]
+                ("dist_dtype", ctypes.c_int), ("save_checkpoints", ctypes.c_int), ("filter_kernel", ctypes.c_int)]
 
 
 @dataclasses.dataclass
@@ -60,10 +61,11 @@ class Params:
     conf_mode: int = CONF_PLAIN
     dist_dtype: int = F32
     save_checkpoints: int = 0
+    filter_kernel: int = KERNEL_RF
 
     def c(self) -> CParams:
         return CParams(self.lam, self.sigma_s, self.sigma_r, self.step, self.iterations, self.passes, self.norm,
-                       self.update, self.conf_mode, self.dist_dtype, self.save_checkpoints)
+                       self.update, self.conf_mode, self.dist_dtype, self.save_checkpoints, self.filter_kernel)
 
 
 _lib = None

@@ -259,6 +259,51 @@ def test_confidence_constant_target_is_one():
     assert float((c - 1.0).abs().max()) <= 1e-3
 
 
+# ---------------------------------------------------------------- box kernel (Eq. 10's printed kernel)
+def quantised_problem(H, W, seed, C=3):
+    """Guide values on a 1/64 grid: with sigma_s / sigma_r = 32 every distance is an exact binary
+    fraction on both sides, so the windows of the box kernel (a floating-point decision of which
+    samples to average) are the same for the kernel and the oracle."""
+    rng = np.random.default_rng(seed)
+    p = workloads.random_problem(H, W, C=C, seed=seed)
+    p.guide = (rng.integers(0, 65, (C, H, W)) / 64.0).astype(np.float32)
+    return p
+
+
+BOX = dict(sigma_s=8.0, sigma_r=0.25)
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 40), (29, 1), (7, 13), (33, 257), (300, 517), (1000, 77), (64, 2000),
+                                 (2100, 40)])
+def test_box_filter(H, W):
+    prob = quantised_problem(H, W, seed=H * 13 + W)
+    prm = dts.Params(passes=3, filter_kernel=dts.KERNEL_BOX, **BOX)
+    out = dts.dts_filter(to_dev(prob.guide), to_dev(prob.target), prm)
+    ref = oracle.box_filter(prob.guide, prob.target, passes=3, **BOX)
+    assert_close(out.cpu().numpy(), ref, prob.target, f"box filter {H}x{W}")
+
+
+@pytest.mark.parametrize("update", [dts.UPDATE_GD, dts.UPDATE_JACOBI])
+def test_box_solve(update):
+    prob = quantised_problem(150, 211, seed=31 + update)
+    prm = dts.Params(lam=0.9, iterations=6, update=update, filter_kernel=dts.KERNEL_BOX, **BOX)
+    z = dts.dts_solve(to_dev(prob.guide), to_dev(prob.target), to_dev(prob.conf), prm)
+    ref = oracle.solve(prob.guide, prob.target, prob.conf, lam=0.9, iterations=6, update=update,
+                       kernel=oracle.KERNEL_BOX, **BOX)
+    assert_close(z.cpu().numpy(), ref, prob.target, f"box solve update={update}")
+
+
+def test_box_kernel_limits():
+    dev()
+    g = torch.rand((3, 20, 30), device=dev())
+    t = torch.rand((20, 30), device=dev())
+    for kw in (dict(dist_dtype=dts.F16), dict(conf_mode=dts.CONF_SUPPORT)):
+        with pytest.raises(RuntimeError):
+            dts.dts_solve(g, t, t, dts.Params(filter_kernel=dts.KERNEL_BOX, **kw))
+    with pytest.raises(RuntimeError):
+        dts.dts_confidence(g, t, dts.Params(filter_kernel=dts.KERNEL_BOX), 0.1)
+
+
 def test_host_pipeline_matches_direct_solves():
     """dts.HostPipeline (copies of neighbouring steps overlapping the solves, two device buffer
     sets, shapes changing between steps) gives the same results, bit for bit, as direct solves."""
