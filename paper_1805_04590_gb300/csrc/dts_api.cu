@@ -108,6 +108,8 @@ struct Layout {
     size_t plane_f32;   // bytes of one FP32 plane
     size_t plane_d;     // bytes of one distance plane
     size_t dX, dY, u, chat, z;  // offsets
+    size_t dYs;         // dY tiled by 8-column strips (ys_rows rows per strip; 0: none)
+    long long ys_rows;
     size_t agg, carry, counters;  // split vertical pass scratch
     long long agg_pitch, agg_plane;
     int nstrips128;
@@ -135,6 +137,11 @@ Layout make_layout(int H, int W, const dts_params* p, int with_backward) {
     L.dX = off; off += L.plane_d;
     L.dY = off; off += L.plane_d;
     L.u = off; off += L.plane_f32;
+    // dY tiled by 8-column strips for the strip kernel (columns up to its height limit)
+    L.ys_rows = p->filter_kernel == DTS_KERNEL_RF ? strip_tile_rows(H) : 0;
+    L.dYs = off;
+    if (L.ys_rows)
+        off += align_up((size_t)((W + 7) / 8) * (size_t)L.ys_rows * 8 * (p->dist_dtype == DTS_F16 ? 2 : 4), kPlaneAlign);
     L.chat = off;
     if (p->conf_mode == DTS_CONF_SUPPORT) off += L.plane_f32;
     split_col_scratch(H, W, &L.agg_pitch, &L.agg_plane, &L.nstrips128);
@@ -229,6 +236,8 @@ int run_distances(const dts_guide* g, const dts_params* p, const Layout& L, void
     a.src = src;
     a.src_dtype = src_dtype;
     a.dst = dst;
+    a.ys_rows = L.ys_rows;
+    a.dYs = L.ys_rows ? ws_at(ws, L.dYs) : nullptr;
     return cuda_status(launch_distances(a, s));
 }
 
@@ -242,6 +251,10 @@ PassArgs base_pass(const dts_guide* g, const Layout& L) {
     a.pitch = L.pitch;
     a.dst_pitch = L.pitch;
     a.status = status_word();
+    if (t_ws && L.ys_rows) {  // read by the strip kernel in vertical passes (whose d is dY)
+        a.d_tiled = static_cast<char*>(t_ws) + L.dYs;
+        a.d_tiled_rows = L.ys_rows;
+    }
     if (t_ws) {
         a.agg = reinterpret_cast<float*>(static_cast<char*>(t_ws) + L.agg);
         a.carry = reinterpret_cast<float*>(static_cast<char*>(t_ws) + L.carry);

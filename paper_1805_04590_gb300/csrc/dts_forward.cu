@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(256) distance_kernel(DistArgs a) {
         const long long q = (long long)y * a.pitch + x;
         static_cast<DT*>(a.dX)[q] = from_f32<DT>(dx);
         static_cast<DT*>(a.dY)[q] = from_f32<DT>(dy);
+        if (a.dYs) static_cast<DT*>(a.dYs)[((long long)(x >> 3) * a.ys_rows + y) * 8 + (x & 7)] = from_f32<DT>(dy);
         if (a.dst) a.dst[q] = load_any(a.src, (long long)y * a.W + x, a.src_dtype);
     }
 }
@@ -273,6 +274,7 @@ __global__ void __launch_bounds__(256) distance4_kernel(DistArgs a) {
         const long long q = (long long)y * a.pitch + x0;
         store4_dist<DT>(static_cast<DT*>(a.dX) + q, dx);
         store4_dist<DT>(static_cast<DT*>(a.dY) + q, dy);
+        if (a.dYs) store4_dist<DT>(static_cast<DT*>(a.dYs) + ((long long)(x0 >> 3) * a.ys_rows + y) * 8 + (x0 & 7), dy);
         if (a.dst) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) a.dst[q + k] = load_any(a.src, (long long)y * a.W + x0 + k, a.src_dtype);
@@ -817,12 +819,20 @@ __global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const _
     }
     __syncwarp();
     wait_predecessor();
-    // full boxes count, the parts outside the plane included (they read as zero)
-    if (lane == 0 && (int)blockIdx.x < nstrips) {
+    // the slab's distances: one contiguous bulk copy from the strip-tiled plane when there is one,
+    // else a TMA box (full boxes count, the parts outside the plane included: they read as zero)
+    constexpr uint32_t kDBytes = (4 * ITEMS + 1) * kStripCols * (int)sizeof(DT);
+    const DT* dtile = static_cast<const DT*>(a.d_tiled);
+    auto load_slab = [&](int strip) {
         mbar_arrive_expect_tx(&bar[warp], kTx);
-        tma_load_2d(sx, &tm_x, blockIdx.x * kStripCols, slab_row, &bar[warp]);
-        tma_load_2d((void*)sd, &tm_d, blockIdx.x * kStripCols, slab_row, &bar[warp]);
-    }
+        tma_load_2d(sx, &tm_x, strip * kStripCols, slab_row, &bar[warp]);
+        if (dtile)
+            bulk_load_1d((void*)sd, dtile + ((long long)strip * a.d_tiled_rows + slab_row) * kStripCols, kDBytes,
+                         &bar[warp]);
+        else
+            tma_load_2d((void*)sd, &tm_d, strip * kStripCols, slab_row, &bar[warp]);
+    };
+    if (lane == 0 && (int)blockIdx.x < nstrips) load_slab(blockIdx.x);
     int it = 0;
     for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x, ++it) {
         const int next = strip + gridDim.x;
@@ -840,11 +850,7 @@ __global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const _
         // the reads above come before the next strip's TMA writes into the same region
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0 && next < nstrips) {
-            mbar_arrive_expect_tx(&bar[warp], kTx);
-            tma_load_2d(sx, &tm_x, next * kStripCols, slab_row, &bar[warp]);
-            tma_load_2d((void*)sd, &tm_d, next * kStripCols, slab_row, &bar[warp]);
-        }
+        if (lane == 0 && next < nstrips) load_slab(next);
         const float wn = (col_ok && row0 + ITEMS < a.H) ? ex2(a.k2 * dn) : 0.f;
         const bool full = col_ok && row0 + ITEMS <= a.H;
 #pragma unroll
@@ -1483,6 +1489,13 @@ void strip_shape(int H, int* items, int* warps) {
     const int segs = (H + it - 1) / it;
     *items = it;
     *warps = (segs + 3) / 4;
+}
+
+long long strip_tile_rows(int H) {
+    if (H > kStripMaxRows) return 0;
+    int items, warps;
+    strip_shape(H, &items, &warps);
+    return 4LL * warps * items + 1;  // every row a slab box reads, the extra row of the last included
 }
 
 // DTS_STRIP_LSU=1: the plain-load strip kernel instead of the TMA one (tuning aid)

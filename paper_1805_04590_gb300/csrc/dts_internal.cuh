@@ -76,10 +76,16 @@ struct DistArgs {
     const void* src;
     int src_dtype;
     float* dst;
+    // optional second copy of dY tiled by 8-column strips (the strip kernel's layout): element
+    // (y, x) at ((x / 8) * ys_rows + y) * 8 + x % 8
+    void* dYs;
+    long long ys_rows;
 };
 
 // One directional pass over lines of a plane held in the workspace.
 struct PassArgs {
+    const void* d_tiled;    // vertical passes: the distances tiled by 8-column strips (or null)
+    long long d_tiled_rows; // rows per strip of d_tiled
     const float* src;       // pass input (pitch `pitch`)
     float* dst;             // pass output (may equal src)
     long long dst_pitch;    // pitch of dst (vertical passes; horizontal passes use `pitch`)
@@ -234,6 +240,8 @@ cudaError_t launch_confidence(const float* m1, const float* m2, long long pitch,
                               float* c, cudaStream_t s);
 bool plan_cols(int H, ColPlan* p);
 bool plan_cols_cluster(int H, ColPlan* p);
+// rows per strip of the tiled distance plane the strip kernel reads (0: columns too tall for it)
+long long strip_tile_rows(int H);
 bool plan_cols_tma(int H, ColPlan* p);
 bool use_persistent();
 bool use_row_persistent();

@@ -53,11 +53,16 @@ def test_workspace_size_layout():
     # split vertical pass: 5 aggregate + 2 carry planes of (W rounded to 128) x ceil(H/32) floats,
     # and one ticket counter per 128 columns, each region 256-byte aligned
     split = 5 * 128 * 2 * 4 + 2 * 128 * 2 * 4 + 256
-    assert n0 == 4 * plane + split  # dX, dY, working buffer, iterate
+    # dY tiled by 8-column strips for the strip kernel: 7 strips of 4 * 2 warps * 9 rows + 1 rows
+    # of 8 values (segments of 9 rows, 2 warps for 40 rows), 256-byte aligned
+    tiled = (7 * 73 * 8 * 4 + 255) // 256 * 256
+    assert n0 == 4 * plane + split + tiled  # dX, dY, working buffer, iterate
     n1 = lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p), 1)
-    assert n1 == (3 + 5 + 2 * 3 + 5) * plane + split  # + K checkpoints, 2N pass inputs, adjoint buffers
+    assert n1 == (3 + 5 + 2 * 3 + 5) * plane + split + tiled  # + K checkpoints, 2N pass inputs, adjoint buffers
     p16 = dts.Params(iterations=5, dist_dtype=dts.F16).c()
-    assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p16), 0) == 2 * (40 * pitch * 2) + 2 * plane + split
+    tiled16 = (7 * 73 * 8 * 2 + 255) // 256 * 256
+    assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p16), 0) == \
+        2 * (40 * pitch * 2) + 2 * plane + split + tiled16
     bad = dts.Params(sigma_s=-1.0).c()
     assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(bad), 0) == 0
     # save_checkpoints = 2: K x 2N planes of kept pass inputs in the forward part, no recompute
