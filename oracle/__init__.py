@@ -42,6 +42,7 @@ def _load():
         lib.orc_confidence.argtypes = [i, i, p, p, i, p, p, d, p]
         lib.orc_box_filter.argtypes = [i, i, p, p, i, p, p, p]
         lib.orc_solve_kernel.argtypes = [i, i, p, p, p, p, p, d, d, d, i, i, i, i, i, p, p]
+        lib.orc_solve_cg.argtypes = [i, i, p, p, p, p, p, d, d, i, i, p]
         lib.orc_solve.argtypes = [i, i, p, p, p, p, p, d, d, d, i, i, i, i, p, p]
         lib.orc_solve.restype = i
         lib.orc_filter_adjoint.argtypes = [i, i, p, p, i, p, p, p, p, p, p]
@@ -208,6 +209,23 @@ def solve(I, t, c, *, lam, sigma_s, sigma_r, step=0.99, iterations=10, passes=3,
     dX, dY = distances(I, sigma_s, sigma_r, norm)
     return solve_d(dX, dY, t, c, lam=lam, sigma_s=sigma_s, step=step, iterations=iterations, passes=passes,
                    update=update, conf_mode=conf_mode, z_init=z_init, checkpoints=checkpoints, kernel=kernel)
+
+
+def solve_cg_d(dX, dY, t, c, *, lam, sigma_s, iterations=20, passes=3, z_init=None):
+    """Conjugate gradients on Eq. 2 (lambda/2 |z - A z|^2 + sum c (z - t)^2) for given distances."""
+    dX, dY, t, c = _f64(dX), _f64(dY), _f64(t), _f64(c)
+    z0 = None if z_init is None else _f64(z_init)
+    H, W = t.shape
+    z = np.empty((H, W))
+    _load().orc_solve_cg(H, W, _ptr(dX), _ptr(dY), _ptr(t), _ptr(c), _ptr(z0), float(lam), float(sigma_s),
+                         int(iterations), int(passes), _ptr(z))
+    return z
+
+
+def solve_cg(I, t, c, *, lam, sigma_s, sigma_r, iterations=20, passes=3, norm=NORM_L1, z_init=None):
+    """Conjugate gradients on Eq. 2 under guide I."""
+    dX, dY = distances(I, sigma_s, sigma_r, norm)
+    return solve_cg_d(dX, dY, t, c, lam=lam, sigma_s=sigma_s, iterations=iterations, passes=passes, z_init=z_init)
 
 
 def filter_adjoint(dX, dY, a, src, gdst):

@@ -28,6 +28,11 @@
  *   orc_box_filter      the edge-aware mean with the box kernel Eq. 10 prints,
  *                       W_ij = 1 if |DT_i - DT_j| <= r (normalized convolution in
  *                       the transformed domain, G&O), r_i = sigma_i sqrt(3) per pass
+ *   orc_solve_cg        conjugate gradients on the objective of Eq. 2 itself,
+ *                       F(z) = lambda/2 |z - A z|^2 + sum_i c_i (z_i - t_i)^2, whose
+ *                       minimiser solves (lambda (I-A)^T (I-A) + 2C) z = 2 C t
+ *                       (§3.1 notes that Eq. 3's update drops the factor 2 and
+ *                       treats z_bar as constant; this is the true gradient)
  *   orc_confidence      confidence from the edge-aware variance of the target,
  *                       Eq. 7 (§3.1): c = exp(-V / (2 sigma_c^2)),
  *                       V = DT(t^2) - DT(t)^2 with DT the edge-aware mean
@@ -461,6 +466,71 @@ void orc_filter_adjoint(int H, int W, const double* dX, const double* dY, int N,
     free(U);
     free(g);
     free(g2);
+}
+
+/* Conjugate gradients on F(z) = lambda/2 |z - A z|^2 + sum_i c_i (z_i - t_i)^2 (Eq. 2 with the
+ * recursive-filter mean): M = lambda (I - A)^T (I - A) + 2C is symmetric positive definite when
+ * some c_i > 0 (A keeps constants, so I - A vanishes only on them), and the minimiser solves
+ * M z = 2 C t.  K steps of textbook CG from z_0 (z_init, or t): r = b - M z, p = r; per step
+ * q = M p, alpha = r.r / p.q, z += alpha p, r -= alpha q, beta = r'.r' / r.r, p = r' + beta p.
+ * A^T comes from orc_filter_adjoint (its distance gradients are not needed here). */
+static void cg_apply_M(int H, int W, const double* dX, const double* dY, int N, const double* a, const double* c,
+                       double lambda, const double* p, double* q, double* t1, double* t2, double* junk) {
+    const long n = (long)H * W;
+    orc_filter(H, W, dX, dY, N, a, p, t1);
+    for (long i = 0; i < n; ++i) t1[i] = p[i] - t1[i];  /* (I - A) p */
+    memset(junk, 0, sizeof(double) * (size_t)(2 * n));
+    orc_filter_adjoint(H, W, dX, dY, N, a, t1, t1, t2, junk, junk + n);  /* A^T (I - A) p */
+    for (long i = 0; i < n; ++i) q[i] = lambda * (t1[i] - t2[i]) + 2.0 * c[i] * p[i];
+}
+
+int orc_solve_cg(int H, int W, const double* dX, const double* dY, const double* t, const double* c,
+                 const double* z0, double lambda, double sigma_s, int K, int N, double* z_out) {
+    const long n = (long)H * W;
+    double* sig = (double*)malloc(sizeof(double) * (size_t)N);
+    double* a = (double*)malloc(sizeof(double) * (size_t)N);
+    double* z = (double*)malloc(sizeof(double) * (size_t)n);
+    double* r = (double*)malloc(sizeof(double) * (size_t)n);
+    double* p = (double*)malloc(sizeof(double) * (size_t)n);
+    double* q = (double*)malloc(sizeof(double) * (size_t)n);
+    double* t1 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* t2 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* junk = (double*)malloc(sizeof(double) * (size_t)(2 * n));
+    orc_schedule(sigma_s, N, sig, a);
+    memcpy(z, z0 ? z0 : t, sizeof(double) * (size_t)n);
+    cg_apply_M(H, W, dX, dY, N, a, c, lambda, z, q, t1, t2, junk);
+    double rr = 0.0;
+    for (long i = 0; i < n; ++i) {
+        r[i] = 2.0 * c[i] * t[i] - q[i];
+        p[i] = r[i];
+        rr += r[i] * r[i];
+    }
+    for (int k = 0; k < K && rr > 0.0; ++k) {
+        cg_apply_M(H, W, dX, dY, N, a, c, lambda, p, q, t1, t2, junk);
+        double pq = 0.0;
+        for (long i = 0; i < n; ++i) pq += p[i] * q[i];
+        const double alpha = rr / pq;
+        double rr_new = 0.0;
+        for (long i = 0; i < n; ++i) {
+            z[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+            rr_new += r[i] * r[i];
+        }
+        const double beta = rr_new / rr;
+        for (long i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+        rr = rr_new;
+    }
+    memcpy(z_out, z, sizeof(double) * (size_t)n);
+    free(sig);
+    free(a);
+    free(z);
+    free(r);
+    free(p);
+    free(q);
+    free(t1);
+    free(t2);
+    free(junk);
+    return 0;
 }
 
 /* Gradient of the distances with respect to the guide (Eq. 8-9 forms above).

@@ -575,3 +575,45 @@ def test_box_solve_one_step_and_fixed_point():
                         kernel=oracle.KERNEL_BOX)
     zs = np.linalg.solve(lam * (np.eye(n) - A) + np.diag(cf), cf * tf)
     np.testing.assert_allclose(zK.ravel(), zs, rtol=0, atol=1e-9)
+
+
+# ---------------------------------------------------------------- conjugate gradients on Eq. 2
+def test_cg_reaches_the_minimiser_of_eq2():
+    """After n steps (exact arithmetic) CG on the SPD system reaches the dense solution of
+    (lambda (I - A)^T (I - A) + 2C) z = 2 C t; the gradient of Eq. 2 vanishes there."""
+    rng = np.random.default_rng(81)
+    H, W = 4, 6
+    I = rand_guide(rng, 3, H, W)
+    dX, dY = oracle.distances(I, 5.0, 0.4)
+    _, a = oracle.schedule(5.0, 3)
+    A = dense_filter_matrix(dX, dY, a)
+    t = rng.normal(size=(H, W))
+    c = rng.uniform(0.1, 1.0, (H, W))
+    lam = 1.3
+    n = H * W
+    B = np.eye(n) - A
+    M = lam * B.T @ B + 2 * np.diag(c.ravel())
+    zs = np.linalg.solve(M, 2 * c.ravel() * t.ravel())
+    z = oracle.solve_cg_d(dX, dY, t, c, lam=lam, sigma_s=5.0, iterations=3 * n)
+    np.testing.assert_allclose(z.ravel(), zs, rtol=0, atol=1e-10)
+    grad = M @ z.ravel() - 2 * c.ravel() * t.ravel()
+    assert np.abs(grad).max() <= 1e-9
+    # CG decreases the objective monotonically along its iterates (the energy norm of the error)
+    F = lambda v: 0.5 * lam * np.sum((B @ v) ** 2) + np.sum(c.ravel() * (v - t.ravel()) ** 2)
+    vals = [F(oracle.solve_cg_d(dX, dY, t, c, lam=lam, sigma_s=5.0, iterations=k).ravel()) for k in range(0, 8)]
+    assert all(vals[i + 1] <= vals[i] + 1e-12 for i in range(7))
+
+
+def test_cg_fixed_point_differs_from_eq4():
+    """The minimiser of Eq. 2 is not the fixed point of the paper's update (Eq. 4): the two agree
+    only when the target already is edge-aware smooth, e.g. a constant."""
+    rng = np.random.default_rng(82)
+    I = rand_guide(rng, 3, 5, 5)
+    t = rng.normal(size=(5, 5))
+    c = rng.uniform(0.2, 1.0, (5, 5))
+    zcg = oracle.solve_cg(I, t, c, lam=1.0, sigma_s=4.0, sigma_r=0.3, iterations=200)
+    zj = oracle.solve(I, t, c, lam=1.0, sigma_s=4.0, sigma_r=0.3, iterations=3000, update=oracle.UPDATE_JACOBI)
+    assert np.abs(zcg - zj).max() > 1e-3
+    tc = np.full((5, 5), 0.4)
+    np.testing.assert_allclose(oracle.solve_cg(I, tc, c, lam=1.0, sigma_s=4.0, sigma_r=0.3, iterations=30), tc,
+                               atol=1e-12)
