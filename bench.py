@@ -42,6 +42,23 @@ UNIT = "MP/s"
 TOL = 1e-4
 PROFILE_EVERY = 10
 
+UPDATES = {"gd": 0, "jacobi": 1, "cg": 2}
+
+
+def update_desc(update, step):
+    return {"gd": f"GD step {step:g} (Eq. 3)", "jacobi": "fixed-point update (Eq. 4)",
+            "cg": "conjugate gradients on Eq. 2"}[update]
+
+
+def oracle_solve(update, I, t, c, kw):
+    """The oracle's solve for this update rule (kw: lam, sigma_s, sigma_r, step, iterations, passes)."""
+    import oracle
+    if update == "cg":
+        k = {n: v for n, v in kw.items() if n != "step"}
+        return oracle.solve_cg(I, t, c, **k)
+    return oracle.solve(I, t, c, update=UPDATES[update], **kw)
+
+
 # algorithmic bytes per pixel of each kernel (s_d distance storage, s_t target storage, C guide
 # channels of s_g bytes): every input element read once, every output element written once
 def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4):
@@ -64,6 +81,11 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4):
         "guide_grad_kernel": C * s_g + 2 * s_d + 8 + 4 * C,
         "axpy_plane_kernel": 12,
         "update_adjoint_kernel": 36 + s_t,
+        "row_pass_kernel<transpose>": 8 + s_d,
+        "col_pass_kernel<transpose>": 8 + s_d,
+        "cg_apply_kernel": 20,
+        "cg_step_kernel": 24,
+        "cg_direction_kernel": 12,
     }.get(name)
 
 
@@ -80,6 +102,8 @@ def parse_args():
                     default="stereo")
     ap.add_argument("--storage", choices=["f32", "bf16"], default="f32", help="guide and target storage")
     ap.add_argument("--direction", choices=["fwd", "fwdbwd"], default="fwd")
+    ap.add_argument("--update", choices=["gd", "jacobi", "cg"], default="gd",
+                    help="Eq. 3 gradient step, Eq. 4 fixed point, or conjugate gradients on Eq. 2")
     return ap.parse_args()
 
 
@@ -205,6 +229,8 @@ class Case:
         self.bwd = args.direction == "fwdbwd"
         if self.name == "batched" and self.bwd:
             raise SystemExit("the batched entry point is forward only")
+        if args.update == "cg" and self.bwd:
+            raise SystemExit("conjugate gradients have no backward")
         self.wl = workloads.make(WORKLOAD_INDEX[self.name])
         q = self.wl.params
         self.s_d = 2 if args.dist_dtype == "f16" else 4
@@ -212,7 +238,7 @@ class Case:
         self.s_io = 2 if args.storage == "bf16" else 4
         self.prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, step=q.step, iterations=q.iterations,
                               passes=q.passes, dist_dtype=dts.F16 if self.s_d == 2 else dts.F32,
-                              save_checkpoints=0)
+                              save_checkpoints=0, update=UPDATES[args.update])
         probs = self.wl.problems
         self.mp = sum(p.target.size for p in probs) / 1e6
         self.g = [torch.from_numpy(p.guide).to(dev).to(self.sdt) for p in probs]
@@ -271,11 +297,11 @@ class Case:
                 "depth_sr": "depth SR x16, batch 8 x 2048x1536 RGB", "batched": "64 uneven RGB images",
                 "multispectral": "multispectral 10000x10000 x 16 bands"}[self.name]
         return {"workload": f"{desc}, {q.iterations} iterations, sigma_s={q.sigma_s:g}, sigma_r={q.sigma_r:g}, "
-                            f"lambda={q.lam:g}, N={q.passes} passes, GD step {q.step:g}",
+                            f"lambda={q.lam:g}, N={q.passes} passes, {update_desc(self.args.update, q.step)}",
                 "images": len(self.wl.problems), "channels": int(p.guide.shape[0]),
                 "shape_hw": list(shapes[0]) if len(shapes) == 1 else "uneven",
                 "iterations": q.iterations, "passes": q.passes, "megapixels_per_step": round(self.mp, 6),
-                "direction": self.args.direction, "storage": self.args.storage,
+                "direction": self.args.direction, "storage": self.args.storage, "update": self.args.update,
                 "distance_storage": self.args.dist_dtype, "l2": "flushed between steps (512 MiB write)",
                 "backward_checkpoints": ({1: "iterates (pass inputs recomputed)", 2: "every pass input"}
                                          .get(self.prm.save_checkpoints) if self.bwd else None),
@@ -300,7 +326,7 @@ class Case:
                 I, t, cc = I[:, :2500, :2500], t[:2500, :2500], p.conf[:2500, :2500]
             else:
                 cc = p.conf
-            z = oracle.solve(I, t, cc, **kw)
+            z = oracle_solve(self.args.update, I, t, cc, kw)
             mp += t.size / 1e6
             if self.name != "multispectral":
                 zg = self.out[i].float().cpu().numpy()
@@ -487,6 +513,8 @@ def run_reference(args):
     """The FP64 oracle timed on the host cores, each step a bounded sample of the workload."""
     import oracle
     from paper_1805_04590_gb300 import workloads
+    if args.update == "cg" and args.direction == "fwdbwd":
+        raise SystemExit("conjugate gradients have no backward")
     wl = workloads.make(WORKLOAD_INDEX[args.workload])
     q = wl.params
     p = wl.problems[0]
@@ -518,7 +546,7 @@ def run_reference(args):
         if args.direction == "fwdbwd":
             oracle.solve_backward(gi, ti, ci, gz, **kw)  # recomputes the forward inside
         else:
-            oracle.solve(gi, ti, ci, **kw)
+            oracle_solve(args.update, gi, ti, ci, kw)
 
     for _ in range(args.warmup):
         step()
@@ -533,7 +561,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": WORKLOAD_DATA[args.workload],
             "config": {"workload": args.workload, "sample": sample, "iterations": q.iterations,
-                       "direction": args.direction, "storage": args.storage, "parallelism": "host cores"},
+                       "direction": args.direction, "update": args.update, "storage": args.storage, "parallelism": "host cores"},
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

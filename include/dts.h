@@ -49,7 +49,7 @@ typedef enum dts_status {
 
 typedef enum dts_dtype { DTS_F32 = 0, DTS_BF16 = 1, DTS_F16 = 2 } dts_dtype;
 typedef enum dts_norm { DTS_NORM_L1 = 0, DTS_NORM_L2 = 1 } dts_norm;
-typedef enum dts_update { DTS_UPDATE_GD = 0, DTS_UPDATE_JACOBI = 1 } dts_update;
+typedef enum dts_update { DTS_UPDATE_GD = 0, DTS_UPDATE_JACOBI = 1, DTS_UPDATE_CG = 2 } dts_update;
 typedef enum dts_conf_mode { DTS_CONF_PLAIN = 0, DTS_CONF_SUPPORT = 1 } dts_conf_mode;
 typedef enum dts_filter_kernel { DTS_KERNEL_RF = 0, DTS_KERNEL_BOX = 1 } dts_filter_kernel;
 
@@ -74,7 +74,13 @@ typedef struct dts_guide {
  *  passes      recursive-filter passes N per edge-aware mean, 1..16 (3 by default)
  *  norm        distance norm: DTS_NORM_L1 (1 + sigma_s/sigma_r sum_k |dI_k|) or
  *              DTS_NORM_L2 (sqrt(1 + (sigma_s/sigma_r)^2 sum_k dI_k^2), §3.2)
- *  update      DTS_UPDATE_GD (Eq. 3) or DTS_UPDATE_JACOBI (Eq. 4)
+ *  update      DTS_UPDATE_GD (Eq. 3), DTS_UPDATE_JACOBI (Eq. 4), or DTS_UPDATE_CG:
+ *              conjugate gradients (named in §5 as the way to faster convergence) on the
+ *              objective of Eq. 2 itself, lambda/2 |z - A z|^2 + sum_i c_i (z_i - t_i)^2,
+ *              i.e. on (lambda (I - A)^T (I - A) + 2 C) z = 2 C t from z_0 (target or z_init);
+ *              `iterations` CG steps, `step` unused; DTS_KERNEL_RF, DTS_CONF_PLAIN and no
+ *              checkpoints only (else DTS_ERR_UNSUPPORTED), no backward.  Each step applies
+ *              A and A^T (4N passes) plus three elementwise kernels with FP64 dot products
  *  conf_mode   DTS_CONF_PLAIN (c as given) or DTS_CONF_SUPPORT (c weighted by
  *              S_flat / sum_j W_ij, §3.1 after Eq. 6)
  *  dist_dtype  storage of the distance planes: DTS_F32 or DTS_F16

@@ -86,7 +86,8 @@ int check_params(const dts_params* p) {
     if (!(p->step > 0.f) || !isfinite(p->step)) return DTS_ERR_INVALID_ARG;
     if (p->iterations < 0 || p->passes < 1 || p->passes > kMaxPasses) return DTS_ERR_INVALID_ARG;
     if (p->norm != DTS_NORM_L1 && p->norm != DTS_NORM_L2) return DTS_ERR_INVALID_ARG;
-    if (p->update != DTS_UPDATE_GD && p->update != DTS_UPDATE_JACOBI) return DTS_ERR_INVALID_ARG;
+    if (p->update != DTS_UPDATE_GD && p->update != DTS_UPDATE_JACOBI && p->update != DTS_UPDATE_CG)
+        return DTS_ERR_INVALID_ARG;
     if (p->conf_mode != DTS_CONF_PLAIN && p->conf_mode != DTS_CONF_SUPPORT) return DTS_ERR_INVALID_ARG;
     if (p->dist_dtype != DTS_F32 && p->dist_dtype != DTS_F16) return DTS_ERR_INVALID_ARG;
     if (p->save_checkpoints < 0 || p->save_checkpoints > 2) return DTS_ERR_INVALID_ARG;
@@ -94,13 +95,19 @@ int check_params(const dts_params* p) {
     return DTS_OK;
 }
 
-// what the box-kernel filter supports (DTS_ERR_UNSUPPORTED otherwise)
+// what conjugate gradients and the box-kernel filter support (DTS_ERR_UNSUPPORTED otherwise)
 int check_box(const dts_guide* g, const dts_params* p) {
+    if (p->update == DTS_UPDATE_CG &&
+        (p->filter_kernel != DTS_KERNEL_RF || p->conf_mode != DTS_CONF_PLAIN || p->save_checkpoints))
+        return DTS_ERR_UNSUPPORTED;
     if (p->filter_kernel != DTS_KERNEL_BOX) return DTS_OK;
     if (p->dist_dtype != DTS_F32 || p->conf_mode != DTS_CONF_PLAIN || p->save_checkpoints) return DTS_ERR_UNSUPPORTED;
     if (g->H > kBoxMaxLine || g->W > kBoxMaxLine) return DTS_ERR_UNSUPPORTED;
     return DTS_OK;
 }
+
+// bytes before the partial sums in the conjugate-gradient block: 8 FP64 scalars, the ticket
+constexpr size_t kCgScalarBytes = 128;
 
 // Workspace layout (byte offsets from the workspace base).
 struct Layout {
@@ -116,6 +123,7 @@ struct Layout {
     int z_planes;       // 1 (in place) or K checkpoints
     size_t passes;      // save_checkpoints = 2: K x 2N planes, (k, 0) = zbar_k, (k, q) = input of pass q
     size_t dYt, ut;     // box kernel: transposed dY and working plane (W rows, pitch tpitch)
+    size_t cg;          // conjugate gradients: planes r, p, q, then FP64 scalars, ticket, partials
     long long tpitch;
     size_t fwd_end;     // bytes used by the forward
     // backward scratch
@@ -163,6 +171,8 @@ Layout make_layout(int H, int W, const dts_params* p, int with_backward) {
         L.ut = off;
         off += tplane;
     }
+    L.cg = off;
+    if (p->update == DTS_UPDATE_CG) off += 3 * L.plane_f32 + align_up(kCgScalarBytes + kCgMaxBlocks * sizeof(double), kPlaneAlign);
     L.passes = off;
     if (p->save_checkpoints == 2) off += (size_t)(p->iterations > 0 ? p->iterations : 1) * 2 * p->passes * L.plane_f32;
     L.fwd_end = off;
@@ -374,6 +384,102 @@ int solve_box(const dts_guide* g, const void* target, int tdt, const float* conf
 
 namespace dts {
 namespace {
+// Conjugate gradients on the objective of Eq. 2 (the method the paper names for faster
+// convergence, §5): M z = b with M = lambda (I - A)^T (I - A) + 2 C and b = 2 C t, from z_0 =
+// z_init or t, K iterations (K >= 1).  A product M x is the 2N passes of A on x into u, then the
+// 2N transposed passes in reverse order (column before row) on x - u into q, the first of which
+// forms x - u as it loads, then cg_apply_kernel.
+int solve_cg(const dts_guide* g, const void* target, int tdt, const float* conf, const float* z_init,
+             const dts_params* p, float* z_out, void* ws, const Layout& L, const Plans& pl, cudaStream_t s) {
+    const int K = p->iterations, N = p->passes, W = g->W;
+    int st;
+    if ((st = bind_workspace(ws, L, s))) return st;
+    float* z = reinterpret_cast<float*>(ws_at(ws, L.z));
+    if (z_init) st = run_distances(g, p, L, ws, z_init, DTS_F32, z, s);
+    else st = run_distances(g, p, L, ws, target, tdt, z, s);
+    if (st) return st;
+    float* u = reinterpret_cast<float*>(ws_at(ws, L.u));
+    float* r = reinterpret_cast<float*>(ws_at(ws, L.cg));
+    float* pd = reinterpret_cast<float*>(ws_at(ws, L.cg + L.plane_f32));
+    float* q = reinterpret_cast<float*>(ws_at(ws, L.cg + 2 * L.plane_f32));
+    char* sc = ws_at(ws, L.cg + 3 * L.plane_f32);
+    if (cudaMemsetAsync(sc, 0, kCgScalarBytes, s) != cudaSuccess) return DTS_ERR_CUDA;
+    float k2[kMaxPasses];
+    pass_log2a(p->sigma_s, N, k2);
+    const int dh = p->dist_dtype == DTS_F16;
+    auto filter_pair = [&](const float* x) -> int {  // u = A x, q = A^T (x - A x)
+        int e;
+        for (int i = 0; i < N; ++i) {
+            PassArgs a = base_pass(g, L);
+            a.src = i == 0 ? x : u;
+            a.dst = u;
+            a.d = ws_at(ws, L.dX);
+            a.k2 = k2[i];
+            if ((e = cuda_status(launch_row_pass(a, dh, PASS_PLAIN, pl.rows, s)))) return e;
+            PassArgs c = base_pass(g, L);
+            c.src = u;
+            c.dst = u;
+            c.d = ws_at(ws, L.dY);
+            c.k2 = k2[i];
+            if ((e = cuda_status(launch_col_pass(c, dh, PASS_PLAIN, pl.cols, s)))) return e;
+        }
+        for (int i = N - 1; i >= 0; --i) {
+            PassArgs c = base_pass(g, L);
+            c.src = i == N - 1 ? u : q;
+            c.zk = i == N - 1 ? x : nullptr;
+            c.dst = q;
+            c.d = ws_at(ws, L.dY);
+            c.k2 = k2[i];
+            if ((e = cuda_status(launch_col_pass(c, dh, PASS_TRANSPOSE, pl.cols, s)))) return e;
+            PassArgs a = base_pass(g, L);
+            a.src = q;
+            a.dst = q;
+            a.d = ws_at(ws, L.dX);
+            a.k2 = k2[i];
+            if ((e = cuda_status(launch_row_pass(a, dh, PASS_TRANSPOSE, pl.rows, s)))) return e;
+        }
+        return DTS_OK;
+    };
+    CgArgs a = {};
+    a.H = g->H;
+    a.W = W;
+    a.pitch = L.pitch;
+    a.z = z;
+    a.r = r;
+    a.p = pd;
+    a.q = q;
+    a.u = u;
+    a.s = q;
+    a.c = conf;
+    a.t = target;
+    a.t_dtype = tdt;
+    a.dvec = W % 4 == 0 && (uintptr_t)conf % 16 == 0;
+    a.lambda = p->lambda;
+    a.scal = reinterpret_cast<double*>(sc);
+    a.ticket = reinterpret_cast<unsigned*>(sc + 64);
+    a.partials = reinterpret_cast<double*>(sc + kCgScalarBytes);
+    a.zout = z;
+    a.zout_pitch = L.pitch;
+    a.zout_vec = true;
+    // r_0 = b - M z_0, p_0 = r_0
+    if ((st = filter_pair(z))) return st;
+    a.slot_rr = 0;
+    if ((st = cuda_status(launch_cg_apply(a, true, s)))) return st;
+    for (int k = 0; k < K; ++k) {
+        if ((st = filter_pair(pd))) return st;
+        a.slot_rr = k & 1;
+        if ((st = cuda_status(launch_cg_apply(a, false, s)))) return st;
+        if (k == K - 1) {
+            a.zout = z_out;
+            a.zout_pitch = W;
+            a.zout_vec = W % 4 == 0 && (uintptr_t)z_out % 16 == 0;
+        }
+        if ((st = cuda_status(launch_cg_step(a, s)))) return st;
+        if (k + 1 < K && (st = cuda_status(launch_cg_direction(a, s)))) return st;
+    }
+    return DTS_OK;
+}
+
 int solve_forward(const dts_guide* g, const void* target, int tdt, const float* conf, const float* z_init,
                        const dts_params* p, float* z_out, void* ws, const Layout& L, const Plans& pl,
                        cudaStream_t s) {
@@ -384,6 +490,7 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
         if (z_init) return cuda_status(launch_copy_plane(z_init, DTS_F32, W, z_out, W, g->H, W, s));
         return cuda_status(launch_copy_plane(target, tdt, W, z_out, W, g->H, W, s));
     }
+    if (p->update == DTS_UPDATE_CG) return solve_cg(g, target, tdt, conf, z_init, p, z_out, ws, L, pl, s);
     if ((st = bind_workspace(ws, L, s))) return st;
     const bool keep = L.z_planes > 1 || p->save_checkpoints;
     auto zslot = [&](int k) -> float* {
@@ -749,6 +856,7 @@ extern "C" int dts_solve_batched(int n, const dts_guide* guides, const void* con
     if (!st && params->filter_kernel != DTS_KERNEL_RF) st = DTS_ERR_UNSUPPORTED;  // recursive-filter kernel only
     if (st) return st;
     if (params->save_checkpoints) return DTS_ERR_UNSUPPORTED;
+    if (params->update == DTS_UPDATE_CG && params->conf_mode != DTS_CONF_PLAIN) return DTS_ERR_UNSUPPORTED;
     for (int i = 0; i < n; ++i) {
         if ((st = check_guide(&guides[i]))) return st;
         if (!targets[i] || !confs[i] || !z_out[i]) return DTS_ERR_INVALID_ARG;
@@ -972,6 +1080,7 @@ extern "C" int dts_solve_noalloc(const dts_guide* guide, const void* target, int
     if (st) return st;
     if (!target || !conf || !z_out || !valid_dtype(target_dtype)) return DTS_ERR_INVALID_ARG;
     if (params->save_checkpoints) return DTS_ERR_UNSUPPORTED;  // checkpoints must outlive the call
+    if ((st = check_box(guide, params))) return st;
     Plans pl;
     if ((st = make_plans(guide->H, guide->W, &pl))) return st;
     const Layout L = make_layout(guide->H, guide->W, params, 0);
@@ -991,7 +1100,7 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
     if (!st && params->filter_kernel != DTS_KERNEL_RF) st = DTS_ERR_UNSUPPORTED;  // recursive-filter kernel only
     if (st) return st;
     if (!target || !conf || !grad_z || !valid_dtype(target_dtype)) return DTS_ERR_INVALID_ARG;
-    if (params->conf_mode != DTS_CONF_PLAIN) return DTS_ERR_UNSUPPORTED;
+    if (params->conf_mode != DTS_CONF_PLAIN || params->update == DTS_UPDATE_CG) return DTS_ERR_UNSUPPORTED;
     if (params->save_checkpoints == 0) return DTS_ERR_INVALID_ARG;  // the forward kept no iterates
     Plans pl;
     if ((st = make_plans(guide->H, guide->W, &pl))) return st;

@@ -75,6 +75,44 @@ struct CoupledMode {
     }
 };
 
+// Transpose of a normalised pass.  The pass is (anti-causal) o (causal) with causal = L^-1 D,
+// D = diag(1 - w_n), L unit lower bidiagonal with -w_n below the diagonal, and anti-causal
+// = U^-1 D' with D' = diag(1 - w_{n+1}), U unit upper bidiagonal with -w_{n+1} above it.  Its
+// transpose D L^-T D' U^-T is: the unnormalised causal sweep h[n] = g[n] + w_n h[n-1], then the
+// normalised anti-causal sweep on h, then a factor (1 - w_n) per position.  The first two have
+// the coupled five-number form with an unnormalised left-to-right recurrence.
+struct TransposeMode {
+    using Pre = Aff;
+    using Suf = Coupled;
+    static __device__ __forceinline__ Pre pre_identity() { return aff_identity(); }
+    static __device__ __forceinline__ Pre pre_compose(const Pre& f, const Pre& s) { return aff_compose(f, s); }
+    static __device__ __forceinline__ Suf suf_identity() { return coupled_identity(); }
+    static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) { return coupled_compose(f, s); }
+    template <int N>
+    static __device__ __forceinline__ void local(const float (&x)[N], const float (&w)[N], float wn, Pre& pre,
+                                                 Suf& suf) {
+        suf = coupled_local<false>(x, w, wn);
+        pre = Aff{suf.A, suf.B};
+    }
+    template <int N>
+    static __device__ __forceinline__ void apply(float (&x)[N], const float (&w)[N], float wn, const Pre& own,
+                                                 float c, const Suf& after) {
+        float h = c;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            h = fmaf(w[j], h, x[j]);
+            x[j] = h;
+        }
+        float K = k_entering(after, fmaf(own.A, c, own.B));
+#pragma unroll
+        for (int j = N - 1; j >= 0; --j) {
+            const float wp = (j + 1 < N) ? w[j + 1] : wn;
+            K = fmaf(wp, K - x[j], x[j]);
+            x[j] = fmaf(-w[j], K, K);
+        }
+    }
+};
+
 // Support of the unnormalised kernel (confidence weighting): causal P[n] = x[n] + w_n P[n-1] and
 // anti-causal Q[n] = x[n] + w'_n Q[n+1], both on x; the result is P + Q - x.  The two sweeps are
 // independent: Suf carries (al, de) with Q_start = al Q_in + de.
@@ -329,7 +367,9 @@ __device__ __forceinline__ void load4_t(const PassArgs& a, long long i, bool vec
 template <int ITEMS, bool DHALF, int KIND, bool TWO = false>
 __global__ void __launch_bounds__(row_max_threads<ITEMS, KIND>()) row_pass_kernel(PassArgs a, int tpr) {
     static_assert(ITEMS % 4 == 0, "ITEMS must be a multiple of 4");
-    using M = typename std::conditional<KIND == PASS_SUPPORT, SupportMode, CoupledMode>::type;
+    using M = typename std::conditional<KIND == PASS_SUPPORT, SupportMode,
+                                        typename std::conditional<KIND == PASS_TRANSPOSE, TransposeMode,
+                                                                  CoupledMode>::type>::type;
     __shared__ typename M::Pre s_pre[32];
     __shared__ typename M::Suf s_suf[32];
     __shared__ Aff s_two[TWO ? 32 : 1];
@@ -503,7 +543,9 @@ constexpr int col_min_blocks() {
 
 template <int ITEMS, bool DHALF, int KIND>
 __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS, KIND>()) col_pass_kernel(PassArgs a) {
-    using M = typename std::conditional<KIND == PASS_SUPPORT_CONF, SupportMode, CoupledMode>::type;
+    using M = typename std::conditional<KIND == PASS_SUPPORT_CONF, SupportMode,
+                                        typename std::conditional<KIND == PASS_TRANSPOSE, TransposeMode,
+                                                                  CoupledMode>::type>::type;
     __shared__ ColShared<M, 32> sh;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -555,6 +597,16 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
             }
         }
     }
+    if constexpr (KIND == PASS_TRANSPOSE) {
+        if (a.zk) {  // the pass filters zk - src (the residual p - A p of conjugate gradients)
+            const float* pz = a.zk + (long long)row0 * P + col;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if (col_ok && row0 + j < a.H) x[j] = *pz - x[j];
+                pz += P;
+            }
+        }
+    }
     float wn;
     {
         const int rn = row0 + ITEMS;
@@ -577,7 +629,7 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
     M::apply(x, w, wn, own_pre, pre.B, suf);
 
     // ---- epilogue
-    if constexpr (KIND == PASS_PLAIN) {
+    if constexpr (KIND == PASS_PLAIN || KIND == PASS_TRANSPOSE) {
         float* pdst = a.dst + (long long)row0 * a.dst_pitch + col;
         if (full) {
 #pragma unroll
@@ -1128,6 +1180,7 @@ cudaError_t launch_col_k(const PassArgs& a, int kind, const ColPlan& p, cudaStre
         case PASS_PLAIN: return launch_col_t<ITEMS, DHALF, PASS_PLAIN>(a, p, s);
         case PASS_UPDATE: return launch_col_t<ITEMS, DHALF, PASS_UPDATE>(a, p, s);
         case PASS_SUPPORT_CONF: return launch_col_t<ITEMS, DHALF, PASS_SUPPORT_CONF>(a, p, s);
+        case PASS_TRANSPOSE: return launch_col_t<ITEMS, DHALF, PASS_TRANSPOSE>(a, p, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1137,6 +1190,7 @@ cudaError_t launch_row_k(const PassArgs& a, int kind, const RowPlan& p, cudaStre
     const dim3 grid((unsigned)((a.H + p.rpb - 1) / p.rpb));
     const dim3 block((unsigned)(p.tpr * p.rpb));
     if (kind == PASS_SUPPORT) return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_SUPPORT>, grid, block, 0, s, a, p.tpr);
+    if (kind == PASS_TRANSPOSE) return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_TRANSPOSE>, grid, block, 0, s, a, p.tpr);
     // two one-direction exchanges (measured faster on the stereo and depth workloads);
     // DTS_ROW_TWO=0 selects the single coupled exchange (tuning aid)
     static const bool two = getenv("DTS_ROW_TWO") == nullptr || atoi(getenv("DTS_ROW_TWO")) != 0;
@@ -1150,9 +1204,10 @@ cudaError_t launch_row_k(const PassArgs& a, int kind, const RowPlan& p, cudaStre
 template <int ITEMS, bool DHALF>
 cudaError_t allow_clusters() {
     cudaError_t e = cudaSuccess;
-    const void* fs[3] = {(const void*)col_pass_kernel<ITEMS, DHALF, PASS_PLAIN>,
+    const void* fs[4] = {(const void*)col_pass_kernel<ITEMS, DHALF, PASS_PLAIN>,
                          (const void*)col_pass_kernel<ITEMS, DHALF, PASS_UPDATE>,
-                         (const void*)col_pass_kernel<ITEMS, DHALF, PASS_SUPPORT_CONF>};
+                         (const void*)col_pass_kernel<ITEMS, DHALF, PASS_SUPPORT_CONF>,
+                         (const void*)col_pass_kernel<ITEMS, DHALF, PASS_TRANSPOSE>};
     for (const void* f : fs) {
         const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (r != cudaSuccess) e = r;
@@ -1434,11 +1489,12 @@ cudaError_t launch_copy_plane(const void* src, int src_dtype, long long src_pitc
 }
 
 cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const RowPlan& p, cudaStream_t s) {
-    const int h = prof_begin(kind == PASS_SUPPORT ? KID_ROW_SUPPORT : kind == PASS_UPDATE_ROW ? KID_ROW_UPDATE : KID_ROW_PLAIN,
+    const int h = prof_begin(kind == PASS_SUPPORT ? KID_ROW_SUPPORT : kind == PASS_UPDATE_ROW ? KID_ROW_UPDATE
+                             : kind == PASS_TRANSPOSE ? KID_ROW_TRANSPOSE : KID_ROW_PLAIN,
                              (long long)a.H * a.W,
                              (dist_half ? kFlagDistHalf : 0) | (kind == PASS_UPDATE_ROW && a.t_dtype != DTS_F32 ? kFlagTarget16 : 0), s);
     cudaError_t e = cudaErrorInvalidValue;
-    if (kind != PASS_UPDATE_ROW && use_row_persistent() && (!row_prefetch() || p.tpr * p.rpb <= (p.items <= 8 ? 1024 : 512))) {
+    if (kind != PASS_UPDATE_ROW && kind != PASS_TRANSPOSE && use_row_persistent() && (!row_prefetch() || p.tpr * p.rpb <= (p.items <= 8 ? 1024 : 512))) {
         const bool sup = kind == PASS_SUPPORT;
         if (p.items == 8)
             e = dist_half ? (sup ? launch_row_persist_t<8, true, PASS_SUPPORT>(a, p, s) : launch_row_persist_t<8, true, PASS_PLAIN>(a, p, s))
@@ -1464,15 +1520,18 @@ cudaError_t launch_col_strip(const PassArgs& a, int dist_half, const ColPlan& p,
 
 cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
     ColPlan tp_probe;
-    const bool inject = injected_tma_skip_pending() && kind != PASS_SUPPORT_CONF && plan_cols_tma(a.H, &tp_probe);
-    if (!inject && use_col_split() && kind != PASS_SUPPORT_CONF && a.agg && a.carry && a.counters)
+    // the transposed pass runs on the cluster kernel only
+    const bool tr = kind == PASS_TRANSPOSE;
+    const bool inject = !tr && injected_tma_skip_pending() && kind != PASS_SUPPORT_CONF && plan_cols_tma(a.H, &tp_probe);
+    if (!tr && !inject && use_col_split() && kind != PASS_SUPPORT_CONF && a.agg && a.carry && a.counters)
         return launch_col_split(a, dist_half, kind, s);
     // the strip kernel runs plain passes only; other kinds (and fault injection) take the cluster shape
     ColPlan q = p;
     if (q.cluster == 0 && (kind != PASS_PLAIN || inject) && !plan_cols_cluster(a.H, &q)) return cudaErrorInvalidValue;
     const bool strip = q.cluster == 0;
     const int kid = strip ? KID_COL_STRIP
-                  : kind == PASS_UPDATE ? KID_COL_UPDATE : kind == PASS_SUPPORT_CONF ? KID_COL_SUPPORT : KID_COL_PLAIN;
+                  : kind == PASS_UPDATE ? KID_COL_UPDATE : kind == PASS_SUPPORT_CONF ? KID_COL_SUPPORT
+                  : tr ? KID_COL_TRANSPOSE : KID_COL_PLAIN;
     const int flags = (dist_half ? kFlagDistHalf : 0) | (kind == PASS_UPDATE && a.t_dtype != DTS_F32 ? kFlagTarget16 : 0);
     const int h = prof_begin(kid, (long long)a.H * a.W, flags, s);
     const cudaError_t e = strip ? launch_col_strip(a, dist_half, q, s) : launch_col_dispatch(a, dist_half, kind, q, s);
@@ -1536,11 +1595,12 @@ cudaError_t launch_col_strip(const PassArgs& a, int dist_half, const ColPlan& p,
 
 cudaError_t launch_col_dispatch(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
     // a pending fault injection exercises the bounded waits of the TMA kernel
-    const bool inject = injected_tma_skip_pending();
-    if (!inject && use_col_split() && kind != PASS_SUPPORT_CONF && a.agg && a.carry && a.counters)
+    const bool tr = kind == PASS_TRANSPOSE;
+    const bool inject = !tr && injected_tma_skip_pending();
+    if (!tr && !inject && use_col_split() && kind != PASS_SUPPORT_CONF && a.agg && a.carry && a.counters)
         return launch_col_split(a, dist_half, kind, s);
     ColPlan tp;
-    if ((inject || use_col_tma()) && kind != PASS_SUPPORT_CONF && plan_cols_tma(a.H, &tp)) {
+    if (!tr && (inject || use_col_tma()) && kind != PASS_SUPPORT_CONF && plan_cols_tma(a.H, &tp)) {
         const bool up = kind == PASS_UPDATE;
         if (tp.items == 8)
             return dist_half ? (up ? launch_col_tma_t<8, true, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<8, true, PASS_PLAIN>(a, tp, s))

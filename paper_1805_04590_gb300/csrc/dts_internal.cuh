@@ -94,7 +94,8 @@ struct PassArgs {
     long long pitch;
     float k2;               // log2(a_i): w = exp2(k2 * d)
     // update epilogue (last vertical pass of an iteration only)
-    const float* zk;        // z_k (pitch `pitch`)
+    const float* zk;        // z_k (pitch `pitch`); vertical PASS_TRANSPOSE: optional minuend
+                            // (the pass then filters zk - src)
     const void* t;          // target (dense, pitch W, dtype t_dtype)
     int t_dtype;
     const float* c;         // confidence (dense pitch W) -- or chat (pitch `pitch`) when c_pitched
@@ -173,7 +174,15 @@ struct RowPlan {
     int rpb;     // rows per CTA
 };
 
-enum PassKind { PASS_PLAIN = 0, PASS_UPDATE = 1, PASS_SUPPORT = 2, PASS_SUPPORT_CONF = 3, PASS_UPDATE_ROW = 4 };
+// PASS_TRANSPOSE: the transpose of a normalised pass (conjugate gradients on Eq. 2)
+enum PassKind {
+    PASS_PLAIN = 0,
+    PASS_UPDATE = 1,
+    PASS_SUPPORT = 2,
+    PASS_SUPPORT_CONF = 3,
+    PASS_UPDATE_ROW = 4,
+    PASS_TRANSPOSE = 5
+};
 
 // Kernel ids reported by the per-launch timer (dts_profile / dts_kernel_name).
 enum KernelId {
@@ -199,6 +208,11 @@ enum KernelId {
     KID_CONFIDENCE = 19,
     KID_BOX = 20,
     KID_TRANSPOSE = 21,
+    KID_ROW_TRANSPOSE = 22,
+    KID_COL_TRANSPOSE = 23,
+    KID_CG_APPLY = 24,
+    KID_CG_STEP = 25,
+    KID_CG_DIRECTION = 26,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
@@ -238,6 +252,41 @@ cudaError_t launch_transpose(const float* src, long long sp, float* dst, long lo
 cudaError_t launch_square_plane(const float* src, float* dst, long long pitch, int H, int W, cudaStream_t s);
 cudaError_t launch_confidence(const float* m1, const float* m2, long long pitch, int H, int W, float sigma_c,
                               float* c, cudaStream_t s);
+
+// conjugate gradients on Eq. 2 (dts_cg.cu).  Pitched planes (row pitch `pitch`, a multiple of 4):
+// z, r, p, q, u = A p, s = A^T (p - A p); c and t dense (row pitch W).  scal holds the FP64 dot
+// products: slots 0 / 1 the residual norms r.r of consecutive iterations (slot_rr the current
+// one), kCgSlotPq the product p.q.  partials (kCgMaxBlocks) and the ticket are the reduction's
+// scratch; the ticket starts at 0 and every reduction leaves it at 0.
+constexpr int kCgMaxBlocks = 2048;
+constexpr int kCgSlotPq = 2;
+struct CgArgs {
+    int H, W;
+    long long pitch;
+    float* z;
+    float* r;
+    float* p;
+    float* q;
+    const float* u;
+    const float* s;
+    const float* c;
+    const void* t;
+    int t_dtype;
+    bool dvec;          // c (and t) readable as aligned 16-byte vectors (W % 4 == 0)
+    float lambda;
+    double* scal;
+    double* partials;
+    unsigned* ticket;
+    int slot_rr;
+    float* zout;        // where the step writes z (z itself, or the caller's dense output)
+    long long zout_pitch;
+    bool zout_vec;      // zout rows 16-byte aligned with a pitch that is a multiple of 4
+};
+int cg_blocks(int H, long long pitch);
+cudaError_t launch_cg_apply(const CgArgs& a, bool init, cudaStream_t s);
+cudaError_t launch_cg_step(const CgArgs& a, cudaStream_t s);
+cudaError_t launch_cg_direction(const CgArgs& a, cudaStream_t s);
+
 bool plan_cols(int H, ColPlan* p);
 bool plan_cols_cluster(int H, ColPlan* p);
 // rows per strip of the tiled distance plane the strip kernel reads (0: columns too tall for it)

@@ -114,6 +114,11 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_CONFIDENCE: return "confidence_kernel";
         case KID_BOX: return "box_line_kernel";
         case KID_TRANSPOSE: return "transpose_kernel";
+        case KID_ROW_TRANSPOSE: return "row_pass_kernel<transpose>";
+        case KID_COL_TRANSPOSE: return "col_pass_kernel<transpose>";
+        case KID_CG_APPLY: return "cg_apply_kernel";
+        case KID_CG_STEP: return "cg_step_kernel";
+        case KID_CG_DIRECTION: return "cg_direction_kernel";
         default: return "unknown";
     }
 }

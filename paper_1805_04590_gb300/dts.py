@@ -19,7 +19,7 @@ from . import build as _build
 
 F32, BF16, F16 = 0, 1, 2
 NORM_L1, NORM_L2 = 0, 1
-UPDATE_GD, UPDATE_JACOBI = 0, 1
+UPDATE_GD, UPDATE_JACOBI, UPDATE_CG = 0, 1, 2
 CONF_PLAIN, CONF_SUPPORT = 0, 1
 KERNEL_RF, KERNEL_BOX = 0, 1
 

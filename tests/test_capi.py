@@ -76,7 +76,7 @@ def test_workspace_size_layout():
 
 @pytest.mark.parametrize("field,value", [("sigma_s", 0.0), ("sigma_r", -1.0), ("lam", -0.5), ("step", 0.0),
                                          ("iterations", -1), ("passes", 0), ("passes", 17), ("norm", 2),
-                                         ("update", 3), ("conf_mode", 2), ("dist_dtype", 1)])
+                                         ("update", 3), ("update", -1), ("conf_mode", 2), ("dist_dtype", 1)])
 def test_invalid_params_rejected_synchronously(field, value):
     lib = dts.load()
     prm = dts.Params()
@@ -156,3 +156,22 @@ def test_confidence_rejects_bad_arguments():
     assert lib.dts_confidence(ctypes.byref(g), None, 0, ctypes.byref(p), 0.1, 0x3000, 0x5000, 1 << 30, None) == 1
     assert lib.dts_confidence(ctypes.byref(g), 0x2000, 9, ctypes.byref(p), 0.1, 0x3000, 0x5000, 1 << 30, None) == 1
     assert lib.dts_confidence(ctypes.byref(g), 0x2000, 0, ctypes.byref(p), 0.1, 0x3000, 0x5000, 16, None) == 3
+
+
+def test_conjugate_gradient_workspace_and_limits():
+    lib = dts.load()
+    g = _guide(H=40, W=50)
+    base = dts.Params(iterations=5).c()
+    cg = dts.Params(iterations=5, update=dts.UPDATE_CG).c()
+    n0 = lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(base), 0)
+    plane = 40 * 64 * 4
+    # planes r, p, q and the FP64 block: 8 scalars and the ticket (128 bytes), 2048 partial sums
+    assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(cg), 0) == \
+        n0 + 3 * plane + (128 + 2048 * 8 + 255) // 256 * 256
+    # the objective's weights are c as given; no checkpoints (no backward), no box kernel
+    for field, value in (("conf_mode", dts.CONF_SUPPORT), ("save_checkpoints", 1), ("filter_kernel", dts.KERNEL_BOX)):
+        prm = dts.Params(iterations=5, update=dts.UPDATE_CG)
+        setattr(prm, field, value)
+        p = prm.c()
+        assert lib.dts_solve(ctypes.byref(g), 0x2000, 0, 0x3000, None, ctypes.byref(p), 0x4000, 0x5000, 1 << 30,
+                             None) == 2, field
