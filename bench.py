@@ -83,6 +83,7 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4):
         "update_adjoint_kernel": 36 + s_t,
         "row_pass_kernel<transpose>": 8 + s_d,
         "col_pass_kernel<transpose>": 8 + s_d,
+        "col_strip_kernel<transpose>": 8 + s_d,
         "cg_apply_kernel": 20,
         "cg_step_kernel": 24,
         "cg_direction_kernel": 12,

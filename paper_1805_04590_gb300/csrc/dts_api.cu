@@ -392,6 +392,8 @@ namespace {
 int solve_cg(const dts_guide* g, const void* target, int tdt, const float* conf, const float* z_init,
              const dts_params* p, float* z_out, void* ws, const Layout& L, const Plans& pl, cudaStream_t s) {
     const int K = p->iterations, N = p->passes, W = g->W;
+    ColPlan cluster_shape;  // the transposed vertical pass needs the strip or the cluster kernel
+    if (!plan_cols_cluster(g->H, &cluster_shape)) return DTS_ERR_UNSUPPORTED;
     int st;
     if ((st = bind_workspace(ws, L, s))) return st;
     float* z = reinterpret_cast<float*>(ws_at(ws, L.z));

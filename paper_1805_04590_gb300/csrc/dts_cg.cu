@@ -11,10 +11,12 @@
 //   cg_direction_kernel  beta = r.r(new) / r.r(old);  p = r + beta p
 //
 // A thread takes four consecutive pixels of a row (one 16-byte vector of each pitched plane) in
-// a grid-stride loop.  Dot products accumulate in FP64: every block writes its partial sum, and
-// the block that finishes last adds the partials in index order, so the scalars do not depend
-// on the order the blocks ran in.  The scalars stay on the device (no host round trip between
-// the kernels of an iteration).
+// a grid-stride loop.  A thread adds its few products in FP32 (GB300's FP64 rate is a small
+// fraction of its FP32 rate, and an FP64 operation per pixel costs more time than the memory
+// traffic); the thread sums are added in FP64 across the block, every block writes its partial
+// sum, and the block that finishes last adds the partials in index order, so the scalars do not
+// depend on the order the blocks ran in.  The scalars stay on the device (no host round trip
+// between the kernels of an iteration).
 #include "dts_scan.cuh"
 
 namespace dts {
@@ -74,13 +76,12 @@ __device__ __forceinline__ void grid_sum(double v, double* partials, unsigned* t
 template <bool INIT>
 __global__ void __launch_bounds__(kCgThreads) cg_apply_kernel(CgArgs a) {
     wait_predecessor();
-    const long long Qp = a.pitch >> 2;
-    const long long units = (long long)a.H * Qp;
-    double acc = 0.0;
-    for (long long u = (long long)blockIdx.x * kCgThreads + threadIdx.x; u < units;
-         u += (long long)gridDim.x * kCgThreads) {
+    const unsigned Qp = (unsigned)(a.pitch >> 2);
+    const unsigned units = (unsigned)a.H * Qp;
+    float acc = 0.f;
+    for (unsigned u = blockIdx.x * kCgThreads + threadIdx.x; u < units; u += gridDim.x * kCgThreads) {
         const int y = (int)(u / Qp);
-        const int x0 = (int)(u - (long long)y * Qp) * 4;
+        const int x0 = (int)(u - (unsigned)y * Qp) * 4;
         if (x0 >= a.W) continue;
         const long long i = (long long)y * a.pitch + x0;
         const long long di = (long long)y * a.W + x0;
@@ -100,10 +101,10 @@ __global__ void __launch_bounds__(kCgThreads) cg_apply_kernel(CgArgs a) {
             const float mp = fmaf(a.lambda, (p[k] - Ap[k]) - s[k], 2.f * c[k] * p[k]);
             if constexpr (INIT) {
                 o[k] = ok ? fmaf(2.f * c[k], t[k], -mp) : 0.f;
-                acc += (double)o[k] * (double)o[k];
+                acc = fmaf(o[k], o[k], acc);
             } else {
                 o[k] = ok ? mp : 0.f;
-                acc += (double)p[k] * (double)o[k];
+                acc = fmaf(ok ? p[k] : 0.f, o[k], acc);
             }
         }
         if constexpr (INIT) {
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kCgThreads) cg_apply_kernel(CgArgs a) {
         }
     }
     release_successor();
-    grid_sum(acc, a.partials, a.ticket, a.scal + (INIT ? a.slot_rr : kCgSlotPq));
+    grid_sum((double)acc, a.partials, a.ticket, a.scal + (INIT ? a.slot_rr : kCgSlotPq));
 }
 
 // alpha = rr / pq (0 once the residual or the direction vanishes: the iteration has stopped)
@@ -123,13 +124,12 @@ __global__ void __launch_bounds__(kCgThreads) cg_step_kernel(CgArgs a) {
     const double rr = a.scal[a.slot_rr];
     const double pq = a.scal[kCgSlotPq];
     const float alpha = (rr > 0.0 && pq > 0.0) ? (float)(rr / pq) : 0.f;
-    const long long Qp = a.pitch >> 2;
-    const long long units = (long long)a.H * Qp;
-    double acc = 0.0;
-    for (long long u = (long long)blockIdx.x * kCgThreads + threadIdx.x; u < units;
-         u += (long long)gridDim.x * kCgThreads) {
+    const unsigned Qp = (unsigned)(a.pitch >> 2);
+    const unsigned units = (unsigned)a.H * Qp;
+    float acc = 0.f;
+    for (unsigned u = blockIdx.x * kCgThreads + threadIdx.x; u < units; u += gridDim.x * kCgThreads) {
         const int y = (int)(u / Qp);
-        const int x0 = (int)(u - (long long)y * Qp) * 4;
+        const int x0 = (int)(u - (unsigned)y * Qp) * 4;
         if (x0 >= a.W) continue;
         const long long i = (long long)y * a.pitch + x0;
         float z[4], p[4], r[4], q[4];
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kCgThreads) cg_step_kernel(CgArgs a) {
         for (int k = 0; k < 4; ++k) {
             z[k] = fmaf(alpha, p[k], z[k]);
             r[k] = fmaf(-alpha, q[k], r[k]);
-            if (x0 + k < a.W) acc += (double)r[k] * (double)r[k];
+            if (x0 + k < a.W) acc = fmaf(r[k], r[k], acc);
         }
         store4_f(a.r, i, r);
         if (a.zout_vec) {
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kCgThreads) cg_step_kernel(CgArgs a) {
         }
     }
     release_successor();
-    grid_sum(acc, a.partials, a.ticket, a.scal + (a.slot_rr ^ 1));
+    grid_sum((double)acc, a.partials, a.ticket, a.scal + (a.slot_rr ^ 1));
 }
 
 __global__ void __launch_bounds__(kCgThreads) cg_direction_kernel(CgArgs a) {
@@ -161,12 +161,11 @@ __global__ void __launch_bounds__(kCgThreads) cg_direction_kernel(CgArgs a) {
     const double rr_old = a.scal[a.slot_rr];
     const double rr_new = a.scal[a.slot_rr ^ 1];
     const float beta = rr_old > 0.0 ? (float)(rr_new / rr_old) : 0.f;
-    const long long Qp = a.pitch >> 2;
-    const long long units = (long long)a.H * Qp;
-    for (long long u = (long long)blockIdx.x * kCgThreads + threadIdx.x; u < units;
-         u += (long long)gridDim.x * kCgThreads) {
+    const unsigned Qp = (unsigned)(a.pitch >> 2);
+    const unsigned units = (unsigned)a.H * Qp;
+    for (unsigned u = blockIdx.x * kCgThreads + threadIdx.x; u < units; u += gridDim.x * kCgThreads) {
         const int y = (int)(u / Qp);
-        const int x0 = (int)(u - (long long)y * Qp) * 4;
+        const int x0 = (int)(u - (unsigned)y * Qp) * 4;
         if (x0 >= a.W) continue;
         const long long i = (long long)y * a.pitch + x0;
         float p[4], r[4];

@@ -840,14 +840,15 @@ __host__ __device__ constexpr int strip_slab_bytes() {
     return 2 * strip_x_bytes<ITEMS, DHALF>() + strip_d_bytes<ITEMS, DHALF>();
 }
 
-template <int ITEMS, bool DHALF>
+// TR: the transposed pass (TransposeMode), with the optional minuend a.zk (zk - src is filtered)
+template <int ITEMS, bool DHALF, bool TR = false>
 __global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const __grid_constant__ CUtensorMap tm_x,
                                                                           const __grid_constant__ CUtensorMap tm_d,
                                                                           const __grid_constant__ CUtensorMap tm_o,
                                                                           PassArgs a, int nstrips, long long timeout) {
     static_assert(ITEMS % 2 == 1, "odd segment length (bank-conflict-free column accesses)");
     static_assert(strip_x_bytes<ITEMS, DHALF>() % 128 == 0, "slab alignment");
-    using M = CoupledMode;
+    using M = typename std::conditional<TR, TransposeMode, CoupledMode>::type;
     using DT = typename std::conditional<DHALF, __half, float>::type;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ StripShared<M> sh;
@@ -899,6 +900,13 @@ __global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const _
             w[j] = to_f32<DT>(sd[(sw * ITEMS + j) * kStripCols + cl]);
         }
         const float dn = to_f32<DT>(sd[((sw + 1) * ITEMS) * kStripCols + cl]);
+        if constexpr (TR) {
+            if (a.zk && col_ok) {
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j)
+                    if (row0 + j < a.H) x[j] = a.zk[(long long)(row0 + j) * a.pitch + col] - x[j];
+            }
+        }
         // the reads above come before the next strip's TMA writes into the same region
         fence_proxy_async_smem();
         __syncwarp();
@@ -1516,7 +1524,7 @@ cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const Ro
     return e;
 }
 
-cudaError_t launch_col_strip(const PassArgs& a, int dist_half, const ColPlan& p, cudaStream_t s);
+cudaError_t launch_col_strip(const PassArgs& a, int dist_half, const ColPlan& p, bool tr, cudaStream_t s);
 
 cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
     ColPlan tp_probe;
@@ -1525,16 +1533,18 @@ cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const Co
     const bool inject = !tr && injected_tma_skip_pending() && kind != PASS_SUPPORT_CONF && plan_cols_tma(a.H, &tp_probe);
     if (!tr && !inject && use_col_split() && kind != PASS_SUPPORT_CONF && a.agg && a.carry && a.counters)
         return launch_col_split(a, dist_half, kind, s);
-    // the strip kernel runs plain passes only; other kinds (and fault injection) take the cluster shape
+    // the strip kernel runs plain and transposed passes; other kinds (and fault injection) take the
+    // cluster shape
     ColPlan q = p;
-    if (q.cluster == 0 && (kind != PASS_PLAIN || inject) && !plan_cols_cluster(a.H, &q)) return cudaErrorInvalidValue;
+    if (q.cluster == 0 && ((kind != PASS_PLAIN && !tr) || inject) && !plan_cols_cluster(a.H, &q))
+        return cudaErrorInvalidValue;
     const bool strip = q.cluster == 0;
-    const int kid = strip ? KID_COL_STRIP
+    const int kid = strip ? (tr ? KID_COL_STRIP_TRANSPOSE : KID_COL_STRIP)
                   : kind == PASS_UPDATE ? KID_COL_UPDATE : kind == PASS_SUPPORT_CONF ? KID_COL_SUPPORT
                   : tr ? KID_COL_TRANSPOSE : KID_COL_PLAIN;
     const int flags = (dist_half ? kFlagDistHalf : 0) | (kind == PASS_UPDATE && a.t_dtype != DTS_F32 ? kFlagTarget16 : 0);
     const int h = prof_begin(kid, (long long)a.H * a.W, flags, s);
-    const cudaError_t e = strip ? launch_col_strip(a, dist_half, q, s) : launch_col_dispatch(a, dist_half, kind, q, s);
+    const cudaError_t e = strip ? launch_col_strip(a, dist_half, q, tr, s) : launch_col_dispatch(a, dist_half, kind, q, s);
     prof_end(h, s);
     return e;
 }
@@ -1564,14 +1574,15 @@ bool strip_lsu() {
 }
 
 template <int ITEMS, bool DHALF>
-cudaError_t launch_col_strip_t(const PassArgs& a, int nw, cudaStream_t s) {
+cudaError_t launch_col_strip_t(const PassArgs& a, int nw, bool tr, cudaStream_t s) {
     const dim3 grid((unsigned)((a.W + kStripCols - 1) / kStripCols));
     const dim3 block((unsigned)(32 * nw));
     CUtensorMap tx, td, to;
     if (!strip_lsu() && make_box_map(&tx, a.src, false, a.W, a.H, a.pitch, kStripCols, 4 * ITEMS) &&
         make_box_map(&td, a.d, DHALF, a.W, a.H, a.pitch, kStripCols, 4 * ITEMS + 1) &&
         make_box_map(&to, a.dst, false, a.W, a.H, a.dst_pitch, kStripCols, 4 * ITEMS)) {
-        auto kernel = col_strip_tma_kernel<ITEMS, DHALF>;  // shared-memory limit raised in prepare_kernels
+        // shared-memory limits raised in prepare_kernels
+        auto kernel = tr ? col_strip_tma_kernel<ITEMS, DHALF, true> : col_strip_tma_kernel<ITEMS, DHALF, false>;
         const size_t smem = (size_t)nw * strip_slab_bytes<ITEMS, DHALF>();
         // persistent: as many CTAs as fit at once (each loops over strips), at most one per strip
         const int nstrips = (int)grid.x;
@@ -1581,15 +1592,22 @@ cudaError_t launch_col_strip_t(const PassArgs& a, int nw, cudaStream_t s) {
         return launch_ex_smem(kernel, dim3((unsigned)g), block, 0, smem, s, tx, td, to, a, nstrips,
                               default_timeout_cycles());
     }
-    // planes that tensor maps cannot describe (e.g. a caller's unaligned output): plain loads
+    // planes that tensor maps cannot describe (e.g. a caller's unaligned output): plain loads, or
+    // the cluster kernel for the transposed pass
+    if (tr) {
+        ColPlan q;
+        if (!plan_cols_cluster(a.H, &q)) return cudaErrorInvalidValue;
+        return launch_col_dispatch(a, DHALF, PASS_TRANSPOSE, q, s);
+    }
     return launch_ex(col_strip_kernel<ITEMS, DHALF>, grid, block, 0, s, a);
 }
 
-cudaError_t launch_col_strip(const PassArgs& a, int dist_half, const ColPlan& p, cudaStream_t s) {
+cudaError_t launch_col_strip(const PassArgs& a, int dist_half, const ColPlan& p, bool tr, cudaStream_t s) {
     if (p.warps < 1 || p.warps > kStripWarps || (long long)4 * p.warps * p.items < a.H) return cudaErrorInvalidValue;
-    if (p.items == 9) return dist_half ? launch_col_strip_t<9, true>(a, p.warps, s) : launch_col_strip_t<9, false>(a, p.warps, s);
+    if (p.items == 9)
+        return dist_half ? launch_col_strip_t<9, true>(a, p.warps, tr, s) : launch_col_strip_t<9, false>(a, p.warps, tr, s);
     if (p.items == 17)
-        return dist_half ? launch_col_strip_t<17, true>(a, p.warps, s) : launch_col_strip_t<17, false>(a, p.warps, s);
+        return dist_half ? launch_col_strip_t<17, true>(a, p.warps, tr, s) : launch_col_strip_t<17, false>(a, p.warps, tr, s);
     return cudaErrorInvalidValue;
 }
 
@@ -1826,7 +1844,11 @@ bool plan_cols_tma(int H, ColPlan* p) {
 // dynamic shared memory of the TMA strip kernel: up to 32 slabs (208 KB at 17 rows, FP32)
 template <int ITEMS, bool DHALF>
 cudaError_t allow_strip_smem() {
-    return cudaFuncSetAttribute((const void*)col_strip_tma_kernel<ITEMS, DHALF>,
+    const cudaError_t e = cudaFuncSetAttribute((const void*)col_strip_tma_kernel<ITEMS, DHALF, false>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               kStripWarps * strip_slab_bytes<ITEMS, DHALF>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)col_strip_tma_kernel<ITEMS, DHALF, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kStripWarps * strip_slab_bytes<ITEMS, DHALF>());
 }

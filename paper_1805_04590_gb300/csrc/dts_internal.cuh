@@ -213,6 +213,7 @@ enum KernelId {
     KID_CG_APPLY = 24,
     KID_CG_STEP = 25,
     KID_CG_DIRECTION = 26,
+    KID_COL_STRIP_TRANSPOSE = 27,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16

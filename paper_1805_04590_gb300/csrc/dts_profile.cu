@@ -119,6 +119,7 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_CG_APPLY: return "cg_apply_kernel";
         case KID_CG_STEP: return "cg_step_kernel";
         case KID_CG_DIRECTION: return "cg_direction_kernel";
+        case KID_COL_STRIP_TRANSPOSE: return "col_strip_kernel<transpose>";
         default: return "unknown";
     }
 }
