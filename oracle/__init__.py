@@ -41,13 +41,13 @@ def _load():
         lib.orc_support.argtypes = [i, i, p, p, d, p, p]
         lib.orc_confidence.argtypes = [i, i, p, p, i, p, p, d, p]
         lib.orc_box_filter.argtypes = [i, i, p, p, i, p, p, p]
-        lib.orc_solve_kernel.argtypes = [i, i, p, p, p, p, p, d, d, d, i, i, i, i, i, p, p]
+        lib.orc_solve_kernel.argtypes = [i, i, p, p, p, p, p, d, d, d, i, i, i, d, i, i, p, p]
         lib.orc_solve_cg.argtypes = [i, i, p, p, p, p, p, d, d, i, i, p]
         lib.orc_solve.argtypes = [i, i, p, p, p, p, p, d, d, d, i, i, i, i, p, p]
         lib.orc_solve.restype = i
         lib.orc_filter_adjoint.argtypes = [i, i, p, p, i, p, p, p, p, p, p]
         lib.orc_distances_adjoint.argtypes = [i, i, i, p, d, d, i, p, p, p, p, p]
-        lib.orc_solve_backward.argtypes = [i, i, i, p, d, d, i, p, p, p, d, d, i, i, i, i, p, p, p, p, p]
+        lib.orc_solve_backward.argtypes = [i, i, i, p, d, d, i, p, p, p, d, d, i, i, i, d, i, p, p, p, p, p]
         lib.orc_solve_backward.restype = i
         lib.orc_num_threads.restype = i
         lib.orc_set_num_threads.argtypes = [i]
@@ -187,28 +187,31 @@ def support(dX, dY, sigma_s):
 
 
 def solve_d(dX, dY, t, c, *, lam, sigma_s, step=0.99, iterations=10, passes=3, update=UPDATE_GD,
-            conf_mode=CONF_PLAIN, z_init=None, checkpoints=False, kernel=KERNEL_RF):
+            conf_mode=CONF_PLAIN, z_init=None, checkpoints=False, kernel=KERNEL_RF, charbonnier_eps=0.0):
     """The solver on precomputed distances.  Returns z_K (and z_0..z_{K-1}).  kernel: the
-    recursive filter (default) or the box kernel of Eq. 10."""
+    recursive filter (default) or the box kernel of Eq. 10.  charbonnier_eps > 0: the gradient
+    step takes the Charbonnier loss sqrt(r^2 + eps^2) on the target term (§4)."""
     dX, dY, t, c = _f64(dX), _f64(dY), _f64(t), _f64(c)
     z0 = None if z_init is None else _f64(z_init)
     H, W = t.shape
     z = np.empty((H, W))
     ck = np.empty((max(iterations, 1), H, W)) if checkpoints else None
     _load().orc_solve_kernel(H, W, _ptr(dX), _ptr(dY), _ptr(t), _ptr(c), _ptr(z0), float(lam), float(sigma_s),
-                             float(step), int(iterations), int(passes), int(update), int(conf_mode), int(kernel),
-                             _ptr(z), _ptr(ck))
+                             float(step), int(iterations), int(passes), int(update), float(charbonnier_eps),
+                             int(conf_mode), int(kernel), _ptr(z), _ptr(ck))
     if checkpoints:
         return z, ck[:iterations]
     return z
 
 
 def solve(I, t, c, *, lam, sigma_s, sigma_r, step=0.99, iterations=10, passes=3, norm=NORM_L1,
-          update=UPDATE_GD, conf_mode=CONF_PLAIN, z_init=None, checkpoints=False, kernel=KERNEL_RF):
+          update=UPDATE_GD, conf_mode=CONF_PLAIN, z_init=None, checkpoints=False, kernel=KERNEL_RF,
+          charbonnier_eps=0.0):
     """DTS solve on guide I (C, H, W) with target t and confidence c (H, W)."""
     dX, dY = distances(I, sigma_s, sigma_r, norm)
     return solve_d(dX, dY, t, c, lam=lam, sigma_s=sigma_s, step=step, iterations=iterations, passes=passes,
-                   update=update, conf_mode=conf_mode, z_init=z_init, checkpoints=checkpoints, kernel=kernel)
+                   update=update, conf_mode=conf_mode, z_init=z_init, checkpoints=checkpoints, kernel=kernel,
+                   charbonnier_eps=charbonnier_eps)
 
 
 def solve_cg_d(dX, dY, t, c, *, lam, sigma_s, iterations=20, passes=3, z_init=None):
@@ -251,7 +254,7 @@ def distances_adjoint(I, sigma_s, sigma_r, dXbar, dYbar, norm=NORM_L1):
 
 
 def solve_backward(I, t, c, grad_z, *, lam, sigma_s, sigma_r, step=0.99, iterations=10, passes=3, norm=NORM_L1,
-                   update=UPDATE_GD, conf_mode=CONF_PLAIN, z_init=None):
+                   update=UPDATE_GD, conf_mode=CONF_PLAIN, z_init=None, charbonnier_eps=0.0):
     """Gradients of <grad_z, z_K> with respect to t, c, the guide and z_init.
 
     Returns a dict with keys ``t``, ``c``, ``guide`` and (when z_init is given)
@@ -265,7 +268,8 @@ def solve_backward(I, t, c, grad_z, *, lam, sigma_s, sigma_r, step=0.99, iterati
     gz0 = np.empty((H, W)) if z0 is not None else None
     rc = _load().orc_solve_backward(C, H, W, _ptr(I), float(sigma_s), float(sigma_r), int(norm), _ptr(t), _ptr(c),
                                     _ptr(z0), float(lam), float(step), int(iterations), int(passes), int(update),
-                                    int(conf_mode), _ptr(gz), _ptr(gt), _ptr(gc), _ptr(gI), _ptr(gz0))
+                                    float(charbonnier_eps), int(conf_mode), _ptr(gz), _ptr(gt), _ptr(gc), _ptr(gI),
+                                    _ptr(gz0))
     if rc != 0:
         raise ValueError("oracle backward supports the PLAIN confidence mode only")
     out = {"t": gt, "c": gc, "guide": gI}

@@ -37,7 +37,10 @@
  *                       Eq. 7 (§3.1): c = exp(-V / (2 sigma_c^2)),
  *                       V = DT(t^2) - DT(t)^2 with DT the edge-aware mean
  *   orc_solve           gradient-descent iterations on Eq. 3 (step 0.99, §4)
- *                       or the fixed-point update of Eq. 4
+ *                       or the fixed-point update of Eq. 4; with eps > 0 the
+ *                       gradient step uses the Charbonnier loss
+ *                       rho(r) = sqrt(r^2 + eps^2) on the target term instead of
+ *                       the square (§4, the stereo loss of Eq. 11: eps = 0.001)
  *   orc_solve_backward  hand-written reverse mode of orc_solve (the paper has
  *                       no backward; derived from the forward steps above)
  */
@@ -297,15 +300,21 @@ static void effective_confidence(int H, int W, const double* dX, const double* d
     }
 }
 
+/* Derivative of the target term's loss per unit confidence at r = z - t: the square's r
+ * (Eq. 3 writes c (z - t), without the factor 2 of Eq. 2), or for eps > 0 the Charbonnier
+ * loss rho(r) = sqrt(r^2 + eps^2) of §4, rho'(r) = r / sqrt(r^2 + eps^2). */
+static double target_slope(double r, double eps) { return eps > 0.0 ? r / sqrt(r * r + eps * eps) : r; }
+
 /* One data-term update given z_k, z_bar = A z_k and the effective confidence.
  *   GD (Eq. 3, step eta; §4 uses eta = 0.99):
- *       z_{k+1} = z_k - eta * (lambda (z_k - z_bar) + c (z_k - t))
+ *       z_{k+1} = z_k - eta * (lambda (z_k - z_bar) + c rho'(z_k - t))
+ *     with rho'(r) = r for the square, r / sqrt(r^2 + eps^2) for the Charbonnier loss
  *     In SUPPORT mode the step is limited to eta_i = min(eta, 1 / (lambda + c_i))
  *     so that the iteration stays stable where c_i is large.
  *   Jacobi (the fixed point of Eq. 4):
  *       z_{k+1} = (lambda z_bar + c t) / (lambda + c);  z_k is kept where lambda + c = 0. */
 static void update(long n, const double* zk, const double* zbar, const double* t, const double* chat, double lambda,
-                   double eta, int update_mode, int clamp_step, double* out) {
+                   double eta, int update_mode, double eps, int clamp_step, double* out) {
     for (long p = 0; p < n; ++p) {
         if (update_mode == ORC_UPDATE_JACOBI) {
             double den = lambda + chat[p];
@@ -313,7 +322,7 @@ static void update(long n, const double* zk, const double* zbar, const double* t
         } else {
             double e = eta;
             if (clamp_step && lambda + chat[p] > 0.0 && 1.0 / (lambda + chat[p]) < e) e = 1.0 / (lambda + chat[p]);
-            out[p] = zk[p] - e * (lambda * (zk[p] - zbar[p]) + chat[p] * (zk[p] - t[p]));
+            out[p] = zk[p] - e * (lambda * (zk[p] - zbar[p]) + chat[p] * target_slope(zk[p] - t[p], eps));
         }
     }
 }
@@ -326,18 +335,18 @@ static void update(long n, const double* zk, const double* zbar, const double* t
  * update are the same. */
 int orc_solve_kernel(int H, int W, const double* dX, const double* dY, const double* t, const double* c,
                      const double* z0, double lambda, double sigma_s, double eta, int K, int N, int update_mode,
-                     int conf_mode, int kernel, double* z_out, double* ckpt);
+                     double eps, int conf_mode, int kernel, double* z_out, double* ckpt);
 
 int orc_solve(int H, int W, const double* dX, const double* dY, const double* t, const double* c, const double* z0,
               double lambda, double sigma_s, double eta, int K, int N, int update_mode, int conf_mode,
               double* z_out, double* ckpt) {
-    return orc_solve_kernel(H, W, dX, dY, t, c, z0, lambda, sigma_s, eta, K, N, update_mode, conf_mode, 0, z_out,
-                            ckpt);
+    return orc_solve_kernel(H, W, dX, dY, t, c, z0, lambda, sigma_s, eta, K, N, update_mode, 0.0, conf_mode, 0,
+                            z_out, ckpt);
 }
 
 int orc_solve_kernel(int H, int W, const double* dX, const double* dY, const double* t, const double* c,
                      const double* z0, double lambda, double sigma_s, double eta, int K, int N, int update_mode,
-                     int conf_mode, int kernel, double* z_out, double* ckpt) {
+                     double eps, int conf_mode, int kernel, double* z_out, double* ckpt) {
     long n = (long)H * W;
     double* sig = (double*)malloc(sizeof(double) * (size_t)N);
     double* a = (double*)malloc(sizeof(double) * (size_t)N);
@@ -351,7 +360,7 @@ int orc_solve_kernel(int H, int W, const double* dX, const double* dY, const dou
         if (ckpt) memcpy(ckpt + (long)k * n, z, sizeof(double) * (size_t)n);
         if (kernel == 1) orc_box_filter(H, W, dX, dY, N, sig, z, zbar);
         else orc_filter(H, W, dX, dY, N, a, z, zbar);
-        update(n, z, zbar, t, chat, lambda, eta, update_mode, conf_mode == ORC_CONF_SUPPORT, z);
+        update(n, z, zbar, t, chat, lambda, eta, update_mode, eps, conf_mode == ORC_CONF_SUPPORT, z);
     }
     memcpy(z_out, z, sizeof(double) * (size_t)n);
     free(sig);
@@ -573,8 +582,8 @@ void orc_distances_adjoint(int C, int H, int W, const double* I, double sigma_s,
  * given).  The iterates are recomputed by a forward solve. */
 int orc_solve_backward(int C, int H, int W, const double* I, double sigma_s, double sigma_r, int norm,
                        const double* t, const double* c, const double* z0, double lambda, double eta, int K, int N,
-                       int update_mode, int conf_mode, const double* gz, double* gt, double* gc, double* gI,
-                       double* gz0) {
+                       int update_mode, double eps, int conf_mode, const double* gz, double* gt, double* gc,
+                       double* gI, double* gz0) {
     if (conf_mode != ORC_CONF_PLAIN) return -1;
     long n = (long)H * W;
     double* dX = (double*)malloc(sizeof(double) * (size_t)n);
@@ -594,7 +603,7 @@ int orc_solve_backward(int C, int H, int W, const double* I, double sigma_s, dou
 
     orc_distances(C, H, W, I, sigma_s, sigma_r, norm, dX, dY);
     orc_schedule(sigma_s, N, sig, a);
-    orc_solve(H, W, dX, dY, t, c, z0, lambda, sigma_s, eta, K, N, update_mode, conf_mode, zlast, Z);
+    orc_solve_kernel(H, W, dX, dY, t, c, z0, lambda, sigma_s, eta, K, N, update_mode, eps, conf_mode, 0, zlast, Z);
     memcpy(g, gz, sizeof(double) * (size_t)n);
 
     for (int k = K - 1; k >= 0; --k) {
@@ -613,10 +622,16 @@ int orc_solve_backward(int C, int H, int W, const double* I, double sigma_s, dou
                     gprev[p] = g[p];
                 }
             } else {
-                tb[p] += eta * c[p] * g[p];
-                cb[p] += eta * (t[p] - zk[p]) * g[p];
+                /* rho'(r) and rho''(r) at r = z_k - t: r and 1 for the square, r / s and
+                 * eps^2 / s^3 (s = sqrt(r^2 + eps^2)) for the Charbonnier loss */
+                const double r = zk[p] - t[p];
+                const double s = sqrt(r * r + eps * eps);
+                const double d1 = target_slope(r, eps);
+                const double d2 = eps > 0.0 ? eps * eps / (s * s * s) : 1.0;
+                tb[p] += eta * c[p] * d2 * g[p];
+                cb[p] -= eta * d1 * g[p];
                 gbar[p] = eta * lambda * g[p];
-                gprev[p] = (1.0 - eta * lambda - eta * c[p]) * g[p];
+                gprev[p] = (1.0 - eta * lambda - eta * c[p] * d2) * g[p];
             }
         }
         /* g <- A^T gbar, accumulate distance gradients */

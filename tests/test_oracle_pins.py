@@ -375,16 +375,20 @@ def _objective(I, t, c, gz, z0=None, **kw):
     return float((oracle.solve(I, t, c, z_init=z0, **kw) * gz).sum())
 
 
-@pytest.mark.parametrize("update,norm", [(oracle.UPDATE_GD, oracle.NORM_L1), (oracle.UPDATE_JACOBI, oracle.NORM_L1),
-                                         (oracle.UPDATE_GD, oracle.NORM_L2)])
-def test_backward_matches_central_differences(update, norm):
+# the last case: the gradient step with the Charbonnier target loss (eps where the loss is smooth
+# on the scale of the difference step)
+@pytest.mark.parametrize("update,norm,eps", [(oracle.UPDATE_GD, oracle.NORM_L1, 0.0),
+                                             (oracle.UPDATE_JACOBI, oracle.NORM_L1, 0.0),
+                                             (oracle.UPDATE_GD, oracle.NORM_L2, 0.0),
+                                             (oracle.UPDATE_GD, oracle.NORM_L1, 0.3)])
+def test_backward_matches_central_differences(update, norm, eps):
     rng = np.random.default_rng(23 + update + 2 * norm)
     C, H, W = 2, 5, 6
     I = rand_guide(rng, C, H, W)
     t = rng.normal(size=(H, W))
     c = rng.uniform(0.2, 1.0, (H, W))
     gz = rng.normal(size=(H, W))
-    kw = dict(lam=0.9, sigma_s=4.0, sigma_r=0.5, iterations=3, update=update, norm=norm)
+    kw = dict(lam=0.9, sigma_s=4.0, sigma_r=0.5, iterations=3, update=update, norm=norm, charbonnier_eps=eps)
     g = oracle.solve_backward(I, t, c, gz, **kw)
     h = 1e-6
     for name, arr in (("t", t), ("c", c), ("guide", I)):
@@ -617,3 +621,36 @@ def test_cg_fixed_point_differs_from_eq4():
     tc = np.full((5, 5), 0.4)
     np.testing.assert_allclose(oracle.solve_cg(I, tc, c, lam=1.0, sigma_s=4.0, sigma_r=0.3, iterations=30), tc,
                                atol=1e-12)
+
+
+# ---------------------------------------------------------------- Charbonnier target term (§4)
+def test_charbonnier_step_is_the_gradient_of_the_loss():
+    """One gradient step with the Charbonnier loss c sqrt((z - t)^2 + eps^2) on the target term:
+    its data part is the derivative of that loss, taken here by central differences of the loss
+    itself (it is separable, so elementwise), and its smoothness part that of Eq. 3."""
+    I, t, c = _small()
+    rng = np.random.default_rng(5)
+    z0 = t + rng.normal(0, 0.01, t.shape)  # residuals on both sides of eps = 0.001 and 0.05
+    for eps in (1e-3, 0.05):
+        z1 = oracle.solve(I, t, c, lam=0.9, sigma_s=8.0, sigma_r=0.2, step=0.7, iterations=1, z_init=z0,
+                          charbonnier_eps=eps)
+        zbar = oracle.filter(I, z0, 8.0, 0.2)
+        h = 1e-4 * eps
+        loss = lambda z: c * np.sqrt((z - t) ** 2 + eps ** 2)
+        g = (loss(z0 + h) - loss(z0 - h)) / (2 * h)
+        np.testing.assert_allclose(z1, z0 - 0.7 * (0.9 * (z0 - zbar) + g), rtol=0, atol=1e-8)
+
+
+def test_charbonnier_limits():
+    """eps >> |z - t|: c eps rho'(r) = c r (1 + O(r^2 / eps^2)), so the solve with confidence c eps
+    is the solve of Eq. 3 with c.  eps << |z - t|: rho'(r) = sign(r), the L1 (sub)gradient step."""
+    I, t, c = _small()
+    kw = dict(lam=0.9, sigma_s=8.0, sigma_r=0.2, step=0.99)
+    eps = 1e6
+    np.testing.assert_allclose(oracle.solve(I, t, c * eps, iterations=5, charbonnier_eps=eps, **kw),
+                               oracle.solve(I, t, c, iterations=5, **kw), rtol=0, atol=1e-9)
+    rng = np.random.default_rng(6)
+    z0 = t + rng.choice([-0.5, 0.5], t.shape)
+    z1 = oracle.solve(I, t, c, iterations=1, z_init=z0, charbonnier_eps=1e-9, **kw)
+    zbar = oracle.filter(I, z0, 8.0, 0.2)
+    np.testing.assert_allclose(z1, z0 - 0.99 * (0.9 * (z0 - zbar) + c * np.sign(z0 - t)), rtol=0, atol=1e-12)
