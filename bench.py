@@ -54,7 +54,7 @@ def oracle_solve(update, I, t, c, kw):
     """The oracle's solve for this update rule (kw: lam, sigma_s, sigma_r, step, iterations, passes)."""
     import oracle
     if update == "cg":
-        k = {n: v for n, v in kw.items() if n != "step"}
+        k = {n: v for n, v in kw.items() if n not in ("step", "charbonnier_eps")}
         return oracle.solve_cg(I, t, c, **k)
     return oracle.solve(I, t, c, update=UPDATES[update], **kw)
 
@@ -105,6 +105,8 @@ def parse_args():
     ap.add_argument("--direction", choices=["fwd", "fwdbwd"], default="fwd")
     ap.add_argument("--update", choices=["gd", "jacobi", "cg"], default="gd",
                     help="Eq. 3 gradient step, Eq. 4 fixed point, or conjugate gradients on Eq. 2")
+    ap.add_argument("--charbonnier-eps", type=float, default=0.0,
+                    help="> 0: Charbonnier loss on the target term (the paper's stereo loss uses 0.001)")
     return ap.parse_args()
 
 
@@ -239,7 +241,8 @@ class Case:
         self.s_io = 2 if args.storage == "bf16" else 4
         self.prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, step=q.step, iterations=q.iterations,
                               passes=q.passes, dist_dtype=dts.F16 if self.s_d == 2 else dts.F32,
-                              save_checkpoints=0, update=UPDATES[args.update])
+                              save_checkpoints=0, update=UPDATES[args.update],
+                              charbonnier_eps=args.charbonnier_eps)
         probs = self.wl.problems
         self.mp = sum(p.target.size for p in probs) / 1e6
         self.g = [torch.from_numpy(p.guide).to(dev).to(self.sdt) for p in probs]
@@ -303,6 +306,8 @@ class Case:
                 "shape_hw": list(shapes[0]) if len(shapes) == 1 else "uneven",
                 "iterations": q.iterations, "passes": q.passes, "megapixels_per_step": round(self.mp, 6),
                 "direction": self.args.direction, "storage": self.args.storage, "update": self.args.update,
+                "target_loss": (f"charbonnier eps={self.args.charbonnier_eps:g}" if self.args.charbonnier_eps > 0
+                                else "square"),
                 "distance_storage": self.args.dist_dtype, "l2": "flushed between steps (512 MiB write)",
                 "backward_checkpoints": ({1: "iterates (pass inputs recomputed)", 2: "every pass input"}
                                          .get(self.prm.save_checkpoints) if self.bwd else None),
@@ -315,7 +320,7 @@ class Case:
         probs = self.wl.problems
         idx = list(range(min(len(probs), 8 if self.name == "batched" else 1)))
         kw = dict(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, step=q.step, iterations=q.iterations,
-                  passes=q.passes)
+                  passes=q.passes, charbonnier_eps=self.args.charbonnier_eps)
         mp = 0.0
         errs, rels = [], []
         t0 = time.perf_counter()
@@ -539,7 +544,7 @@ def run_reference(args):
         ti = torch.from_numpy(ti).to(torch.bfloat16).float().numpy()
     mp = ti.size / 1e6
     kw = dict(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, step=q.step, iterations=q.iterations,
-              passes=q.passes)
+              passes=q.passes, charbonnier_eps=args.charbonnier_eps)
     rng = np.random.default_rng(77)
     gz = rng.standard_normal(ti.shape)
 

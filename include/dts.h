@@ -88,6 +88,10 @@ typedef struct dts_guide {
  *              box kernel Eq. 10 prints, W_ij = 1 if |DT_i - DT_j| <= r with r = sigma_i sqrt(3)
  *              per pass (normalized convolution in the transformed domain); FP32 distances,
  *              DTS_CONF_PLAIN and no checkpoints only, lines up to 8192 positions, no backward
+ *  charbonnier_eps  0 (default): the square (z - t)^2 on the target term.  > 0, with
+ *              DTS_UPDATE_GD only: the Charbonnier loss sqrt((z - t)^2 + eps^2) that §4
+ *              uses for stereo (eps = 0.001), so the gradient step of Eq. 3 takes
+ *              c (z - t) / sqrt((z - t)^2 + eps^2) for the data term; forward and backward
  *  save_checkpoints  0: nothing kept; 1: dts_solve keeps z_0 .. z_{K-1} in the
  *              workspace for dts_solve_backward (workspace sized with with_backward = 1),
  *              which recomputes each iteration's pass inputs from them; 2: it also keeps
@@ -101,6 +105,7 @@ typedef struct dts_params {
     int dist_dtype;
     int save_checkpoints;
     int filter_kernel;
+    float charbonnier_eps;
 } dts_params;
 
 /* Human-readable name of a status code (static string). */

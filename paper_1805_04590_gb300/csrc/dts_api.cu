@@ -92,11 +92,13 @@ int check_params(const dts_params* p) {
     if (p->dist_dtype != DTS_F32 && p->dist_dtype != DTS_F16) return DTS_ERR_INVALID_ARG;
     if (p->save_checkpoints < 0 || p->save_checkpoints > 2) return DTS_ERR_INVALID_ARG;
     if (p->filter_kernel != DTS_KERNEL_RF && p->filter_kernel != DTS_KERNEL_BOX) return DTS_ERR_INVALID_ARG;
+    if (!(p->charbonnier_eps >= 0.f) || !isfinite(p->charbonnier_eps)) return DTS_ERR_INVALID_ARG;
     return DTS_OK;
 }
 
 // what conjugate gradients and the box-kernel filter support (DTS_ERR_UNSUPPORTED otherwise)
 int check_box(const dts_guide* g, const dts_params* p) {
+    if (p->charbonnier_eps > 0.f && p->update != DTS_UPDATE_GD) return DTS_ERR_UNSUPPORTED;
     if (p->update == DTS_UPDATE_CG &&
         (p->filter_kernel != DTS_KERNEL_RF || p->conf_mode != DTS_CONF_PLAIN || p->save_checkpoints))
         return DTS_ERR_UNSUPPORTED;
@@ -367,6 +369,7 @@ int solve_box(const dts_guide* g, const void* target, int tdt, const float* conf
         a.lambda = p->lambda;
         a.step = p->step;
         a.update = p->update;
+        a.eps = p->charbonnier_eps;
         if (k + 1 == K) {
             a.zout = z_out;
             a.zout_pitch = W;
@@ -527,6 +530,7 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
         a.lambda = p->lambda;
         a.step = p->step;
         a.update = p->update;
+        a.eps = p->charbonnier_eps;
         const int tsz = tdt == DTS_F32 ? 4 : 2;
         a.tc_vec = (W % 4 == 0) && ((uintptr_t)target % (4 * tsz) == 0) && ((uintptr_t)conf % 16 == 0);
     };
@@ -1173,6 +1177,7 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
             b.lambda = params->lambda;
             b.step = params->step;
             b.update = params->update;
+            b.eps = params->charbonnier_eps;
             if ((st = cuda_status(launch_update_adjoint(b, s)))) return st;
         }
         // adjoint passes in reverse order

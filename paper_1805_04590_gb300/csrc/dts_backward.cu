@@ -349,7 +349,9 @@ __global__ void __launch_bounds__(256) guide_grad_kernel(GuideGradArgs a) {
 }
 
 // Adjoint of the data-term update at every pixel, given g = dL/dz_{k+1} in a.gz:
-//   GD      dzbar = eta lambda g,  dt += eta c g,  dc += eta (t - z_k) g,  a.gz <- (1 - eta lambda - eta c) g
+//   GD      dzbar = eta lambda g,  dt += eta c rho'' g,  dc -= eta rho' g,
+//           a.gz <- (1 - eta lambda - eta c rho'') g,  with rho' and rho'' at r = z_k - t: r and 1
+//           for the square, r / s and eps^2 / s^3 (s = sqrt(r^2 + eps^2)) for the Charbonnier loss
 //   Jacobi  dzbar = lambda g / den,  dt += c g / den,  dc += lambda (t - zbar) g / den^2,  a.gz <- 0
 //           (den = lambda + c; where den = 0 the iterate was kept: a.gz <- g and nothing else)
 // dzbar goes to a.gout (the input gradient of the last pass's adjoint); a.x holds zbar (Jacobi).
@@ -400,10 +402,17 @@ __global__ void __launch_bounds__(256) update_adjoint_kernel(BwdArgs a) {
                 dz[k] = g[k];
             }
         } else {
+            const float r = zz[k] - t[k];
+            float d1 = r, d2 = 1.f;
+            if (a.eps > 0.f) {
+                const float is = rsqrtf(fmaf(r, r, a.eps * a.eps));
+                d1 = r * is;
+                d2 = a.eps * a.eps * is * is * is;
+            }
             dzb[k] = a.step * a.lambda * g[k];
-            gt[k] += a.step * cf[k] * g[k];
-            gc[k] += a.step * (t[k] - zz[k]) * g[k];
-            dz[k] = (1.f - a.step * a.lambda - a.step * cf[k]) * g[k];
+            gt[k] += a.step * cf[k] * d2 * g[k];
+            gc[k] -= a.step * d1 * g[k];
+            dz[k] = (1.f - a.step * a.lambda - a.step * cf[k] * d2) * g[k];
         }
     }
     if (VEC) {

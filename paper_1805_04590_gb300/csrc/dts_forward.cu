@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(row_max_threads<ITEMS, KIND>()) row_pass_kerne
 #pragma unroll
             for (int j = 0; j < HALF; ++j) {
                 const float zn = dts_update_value(zk[j], x[h0 + j], tt[j], cc[j], a.lambda, a.step, a.update,
-                                                  a.clamp_step);
+                                                  a.clamp_step, a.eps);
                 x[h0 + j] = (e0 + h0 + j < a.W) ? zn : 0.f;
             }
 #pragma unroll
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
             } else {
                 float eta = a.step;
                 if (a.clamp_step && a.lambda + cf > 0.f) eta = fminf(eta, 1.f / (a.lambda + cf));
-                zn = z - eta * (a.lambda * (z - zb) + cf * (z - t));
+                zn = z - eta * (a.lambda * (z - zb) + cf * target_slope(z - t, a.eps));
             }
             a.zout[(long long)r * a.zout_pitch + col] = zn;
         } else {
@@ -1167,7 +1167,7 @@ __global__ void __launch_bounds__(32 * kTmaColMaxWarps, tma_col_min_blocks<ITEMS
                 } else {
                     float eta = a.step;
                     if (a.clamp_step && a.lambda + cf > 0.f) eta = fminf(eta, 1.f / (a.lambda + cf));
-                    zn = z - eta * (a.lambda * (z - zb) + cf * (z - t));
+                    zn = z - eta * (a.lambda * (z - zb) + cf * target_slope(z - t, a.eps));
                 }
                 a.zout[(long long)r * a.zout_pitch + col] = zn;
             }
@@ -1406,7 +1406,7 @@ __global__ void __launch_bounds__(256) update_kernel(PassArgs a) {
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        z[k] = dts_update_value(zk[k], zb[k], t[k], c[k], a.lambda, a.step, a.update, a.clamp_step);
+        z[k] = dts_update_value(zk[k], zb[k], t[k], c[k], a.lambda, a.step, a.update, a.clamp_step, a.eps);
     const long long o = (long long)y * a.zout_pitch + x0;
     if (VEC) {
         store4_f(a.zout, o, z);

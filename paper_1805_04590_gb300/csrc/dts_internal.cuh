@@ -46,20 +46,26 @@ __device__ __forceinline__ float load_any(const void* p, long long i, int dtype)
     return static_cast<const float*>(p)[i];
 }
 
+// Slope of the target term's loss per unit confidence at r = z - t: r for the square of Eq. 3,
+// r / sqrt(r^2 + eps^2) for the Charbonnier loss sqrt(r^2 + eps^2) of §4 (eps > 0).
+__device__ __forceinline__ float target_slope(float r, float eps) {
+    return eps > 0.f ? r / sqrtf(fmaf(r, r, eps * eps)) : r;
+}
+
 // One data-term update of the solver at a pixel: z = z_k, zb = zbar = A z_k, t, c (confidence,
 // or the support-weighted confidence).
-//   GD (Eq. 3):      z - step (lambda (z - zb) + c (z - t)), with the step limited to
-//                    1 / (lambda + c) when clamp is set
+//   GD (Eq. 3):      z - step (lambda (z - zb) + c rho'(z - t)), with the step limited to
+//                    1 / (lambda + c) when clamp is set; rho'(r) = target_slope(r, eps)
 //   Jacobi (Eq. 4):  (lambda zb + c t) / (lambda + c); z is kept where lambda + c = 0
 __device__ __forceinline__ float dts_update_value(float z, float zb, float t, float c, float lambda, float step,
-                                                  int update, int clamp) {
+                                                  int update, int clamp, float eps) {
     if (update == DTS_UPDATE_JACOBI) {
         const float den = lambda + c;
         return den != 0.f ? (lambda * zb + c * t) / den : z;
     }
     float eta = step;
     if (clamp && lambda + c > 0.f) eta = fminf(eta, 1.f / (lambda + c));
-    return z - eta * (lambda * (z - zb) + c * (z - t));
+    return z - eta * (lambda * (z - zb) + c * target_slope(z - t, eps));
 }
 
 // ---------------------------------------------------------------- kernel arguments
@@ -105,6 +111,7 @@ struct PassArgs {
     float lambda, step;
     int update;             // DTS_UPDATE_GD / DTS_UPDATE_JACOBI
     int clamp_step;         // SUPPORT mode: step_i = min(step, 1 / (lambda + c_i))
+    float eps;              // GD: Charbonnier loss on the target term when > 0 (else the square)
     int tc_vec;             // t and c rows may be read with 16-byte vectors (W % 4 == 0, aligned)
     // support mode: S -> chat = c * s_flat / S (written to zout)
     float s_flat;
@@ -141,6 +148,7 @@ struct BwdArgs {
     float* gc;              // += dL/dc (dense, may be null)
     float lambda, step;
     int update;
+    float eps;              // Charbonnier loss on the target term when > 0
     // columns taller than one cluster (vertical adjoint in chunks): chunk_mode 0 single chunk,
     // 1 write chunk totals, 2 apply with the totals of the other chunks; tot holds tot_chunks
     // chunks of 9 planes of tot_pitch floats

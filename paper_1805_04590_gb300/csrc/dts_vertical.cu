@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(32 * kApplyWarps, 5) col_apply_kernel(PassArgs
             } else {
                 float eta = a.step;
                 if (a.clamp_step && a.lambda + cf > 0.f) eta = fminf(eta, 1.f / (a.lambda + cf));
-                zn = z - eta * (a.lambda * (z - zb) + cf * (z - t));
+                zn = z - eta * (a.lambda * (z - zb) + cf * target_slope(z - t, a.eps));
             }
             a.zout[(long long)row * a.zout_pitch + col] = zn;
         }

@@ -44,7 +44,8 @@ class CParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_float), ("sigma_s", ctypes.c_float), ("sigma_r", ctypes.c_float),
                 ("step", ctypes.c_float), ("iterations", ctypes.c_int), ("passes", ctypes.c_int),
                 ("norm", ctypes.c_int), ("update", ctypes.c_int), ("conf_mode", ctypes.c_int),
-                ("dist_dtype", ctypes.c_int), ("save_checkpoints", ctypes.c_int), ("filter_kernel", ctypes.c_int)]
+                ("dist_dtype", ctypes.c_int), ("save_checkpoints", ctypes.c_int), ("filter_kernel", ctypes.c_int),
+                ("charbonnier_eps", ctypes.c_float)]
 
 
 @dataclasses.dataclass
@@ -62,10 +63,12 @@ class Params:
     dist_dtype: int = F32
     save_checkpoints: int = 0
     filter_kernel: int = KERNEL_RF
+    charbonnier_eps: float = 0.0
 
     def c(self) -> CParams:
         return CParams(self.lam, self.sigma_s, self.sigma_r, self.step, self.iterations, self.passes, self.norm,
-                       self.update, self.conf_mode, self.dist_dtype, self.save_checkpoints, self.filter_kernel)
+                       self.update, self.conf_mode, self.dist_dtype, self.save_checkpoints, self.filter_kernel,
+                       self.charbonnier_eps)
 
 
 _lib = None

@@ -76,7 +76,8 @@ def test_workspace_size_layout():
 
 @pytest.mark.parametrize("field,value", [("sigma_s", 0.0), ("sigma_r", -1.0), ("lam", -0.5), ("step", 0.0),
                                          ("iterations", -1), ("passes", 0), ("passes", 17), ("norm", 2),
-                                         ("update", 3), ("update", -1), ("conf_mode", 2), ("dist_dtype", 1)])
+                                         ("update", 3), ("update", -1), ("conf_mode", 2),
+                                         ("charbonnier_eps", -1.0), ("charbonnier_eps", float("nan")), ("dist_dtype", 1)])
 def test_invalid_params_rejected_synchronously(field, value):
     lib = dts.load()
     prm = dts.Params()
@@ -169,9 +170,19 @@ def test_conjugate_gradient_workspace_and_limits():
     assert lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(cg), 0) == \
         n0 + 3 * plane + (128 + 2048 * 8 + 255) // 256 * 256
     # the objective's weights are c as given; no checkpoints (no backward), no box kernel
-    for field, value in (("conf_mode", dts.CONF_SUPPORT), ("save_checkpoints", 1), ("filter_kernel", dts.KERNEL_BOX)):
+    for field, value in (("conf_mode", dts.CONF_SUPPORT), ("save_checkpoints", 1), ("filter_kernel", dts.KERNEL_BOX),
+                         ("charbonnier_eps", 1e-3)):
         prm = dts.Params(iterations=5, update=dts.UPDATE_CG)
         setattr(prm, field, value)
         p = prm.c()
         assert lib.dts_solve(ctypes.byref(g), 0x2000, 0, 0x3000, None, ctypes.byref(p), 0x4000, 0x5000, 1 << 30,
                              None) == 2, field
+
+
+def test_charbonnier_needs_the_gradient_step():
+    lib = dts.load()
+    g = _guide()
+    for upd in (dts.UPDATE_JACOBI, dts.UPDATE_CG):
+        p = dts.Params(update=upd, charbonnier_eps=1e-3).c()
+        assert lib.dts_solve(ctypes.byref(g), 0x2000, 0, 0x3000, None, ctypes.byref(p), 0x4000, 0x5000, 1 << 30,
+                             None) == 2

@@ -36,7 +36,7 @@ def close(gpu, ref, what):
 
 
 def run_case(H, W, C=3, K=4, update=dts.UPDATE_GD, norm=dts.NORM_L1, zinit=False, seed=0, passes=3,
-             sigma_s=8.0, sigma_r=0.3, dist=dts.F32, keep=1):
+             sigma_s=8.0, sigma_r=0.3, dist=dts.F32, keep=1, eps=0.0):
     rng = np.random.default_rng(seed)
     I = guide_noisy(H, W, C, seed)
     t = rng.normal(size=(H, W)).astype(np.float32)
@@ -44,14 +44,15 @@ def run_case(H, W, C=3, K=4, update=dts.UPDATE_GD, norm=dts.NORM_L1, zinit=False
     gz = rng.normal(size=(H, W)).astype(np.float32)
     z0 = rng.normal(size=(H, W)).astype(np.float32) if zinit else None
     prm = dts.Params(lam=0.9, sigma_s=sigma_s, sigma_r=sigma_r, iterations=K, passes=passes, update=update,
-                     norm=norm, dist_dtype=dist, save_checkpoints=keep)
+                     norm=norm, dist_dtype=dist, save_checkpoints=keep, charbonnier_eps=eps)
     g, tt, cc = T(I), T(t), T(c)
     zi = T(z0) if zinit else None
     ws = dts.workspace(g, prm, with_backward=True)
     z = dts.dts_solve(g, tt, cc, prm, z_init=zi, ws=ws)
     gt, gc, gg, gz0 = dts.dts_solve_backward(g, tt, cc, prm, ws, T(gz), z_init=zi)
     assert dts.dts_last_status() == 0
-    kw = dict(lam=0.9, sigma_s=sigma_s, sigma_r=sigma_r, iterations=K, passes=passes, update=update, norm=norm)
+    kw = dict(lam=0.9, sigma_s=sigma_s, sigma_r=sigma_r, iterations=K, passes=passes, update=update, norm=norm,
+              charbonnier_eps=eps)
     if dist == dts.F16:
         return z, gt, gc, gg, gz0, None
     ref = oracle.solve_backward(I, t, c, gz, z_init=z0, **kw)
@@ -68,6 +69,15 @@ def run_case(H, W, C=3, K=4, update=dts.UPDATE_GD, norm=dts.NORM_L1, zinit=False
 @pytest.mark.parametrize("H,W", [(1, 1), (1, 23), (29, 1), (17, 31), (64, 80), (130, 70), (45, 300), (300, 45)])
 def test_backward_shapes(H, W):
     run_case(H, W, seed=H * 31 + W)
+
+
+@pytest.mark.parametrize("H,W", [(64, 80), (300, 45)])
+def test_backward_charbonnier(H, W):
+    """The reverse mode of the gradient step with the Charbonnier target loss (§4): eps = 1, the
+    step's curvature in the stable range (see the forward tests), and with a starting point away
+    from the target."""
+    run_case(H, W, K=4, seed=H + W + 5, eps=1.0)
+    run_case(H, W, K=3, seed=H + W + 6, eps=1.0, zinit=True)
 
 
 @pytest.mark.parametrize("update", [dts.UPDATE_GD, dts.UPDATE_JACOBI])

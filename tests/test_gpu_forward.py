@@ -210,6 +210,42 @@ def test_solve_full_stereo_workload():
     assert_close(z.cpu().numpy(), ref, p.target, "stereo 2880x1988")
 
 
+# ---------------------------------------------------------------- Charbonnier target loss (§4)
+# The gradient step's curvature on the target term is c rho''(r) <= c / eps.  eps = 1 keeps it
+# below c (the stable range of the quadratic solve); the paper's eps = 0.001 with confidences
+# below 1e-3 keeps eta c / eps < 1.  Outside that range the step overshoots where |z - t| < eps
+# and amplifies rounding by up to eta c / eps per iteration, so no elementwise bound holds there.
+@pytest.mark.parametrize("H,W", [(37, 53), (300, 257), (1100, 96)])
+@pytest.mark.parametrize("eps,cscale", [(1.0, 1.0), (1e-3, 1e-3)])
+def test_solve_charbonnier(H, W, eps, cscale):
+    prob = workloads.random_problem(H, W, C=3, seed=H + 7 * W)
+    c = (prob.conf * cscale).astype(np.float32)
+    prm = dts.Params(lam=0.99, sigma_s=8.0, sigma_r=0.2, iterations=10, charbonnier_eps=eps)
+    z = dts.dts_solve(to_dev(prob.guide), to_dev(prob.target), to_dev(c), prm)
+    assert dts.dts_last_status() == 0
+    ref = oracle_solve(prob.guide, prob.target, c, prm, charbonnier_eps=eps)
+    assert_close(z.cpu().numpy(), ref, prob.target, f"charbonnier eps={eps} {H}x{W}")
+
+
+def test_solve_charbonnier_box_kernel_and_full_stereo_workload():
+    """The Charbonnier step with the box kernel, and on the full 2880 x 1988 stereo workload
+    (disparities in pixels, eps = 1 pixel)."""
+    prob = workloads.random_problem(70, 90, C=3, seed=4)
+    prm = dts.Params(lam=0.99, sigma_s=8.0, sigma_r=0.2, iterations=6, charbonnier_eps=1.0,
+                     filter_kernel=dts.KERNEL_BOX)
+    z = dts.dts_solve(to_dev(prob.guide), to_dev(prob.target), to_dev(prob.conf), prm)
+    ref = oracle_solve(prob.guide, prob.target, prob.conf, prm, charbonnier_eps=1.0, kernel=oracle.KERNEL_BOX)
+    assert_close(z.cpu().numpy(), ref, prob.target, "charbonnier, box kernel")
+    wl = workloads.make(1)
+    p, q = wl.problems[0], wl.params
+    prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes,
+                     charbonnier_eps=1.0)
+    z = dts.dts_solve(to_dev(p.guide), to_dev(p.target), to_dev(p.conf), prm)
+    assert dts.dts_last_status() == 0
+    ref = oracle_solve(p.guide, p.target, p.conf, prm, charbonnier_eps=1.0)
+    assert_close(z.cpu().numpy(), ref, p.target, "charbonnier stereo 2880x1988")
+
+
 def test_solve_multispectral_reduced():
     """The 16-band multispectral generator at 2500 x 2500 (its full 10000 x 10000 size is timed
     by the bench): the 10-iteration solve against the oracle."""
