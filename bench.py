@@ -61,7 +61,7 @@ def oracle_solve(update, I, t, c, kw):
 
 # algorithmic bytes per pixel of each kernel (s_d distance storage, s_t target storage, C guide
 # channels of s_g bytes): every input element read once, every output element written once
-def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4):
+def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3):
     return {
         "distance_kernel": C * s_g + 2 * s_d + s_t + 4,
         "copy_plane_kernel": s_t + 4,
@@ -82,8 +82,9 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4):
         "axpy_plane_kernel": 12,
         "update_adjoint_kernel": 36 + s_t,
         "row_pass_kernel<transpose>": 8 + s_d,
-        "col_pass_kernel<transpose>": 8 + s_d,
-        "col_strip_kernel<transpose>": 8 + s_d,
+        # the first transposed vertical pass of a product also reads the minuend plane
+        "col_pass_kernel<transpose>": 8 + s_d + 4.0 / N,
+        "col_strip_kernel<transpose>": 8 + s_d + 4.0 / N,
         "cg_apply_kernel": 20,
         "cg_step_kernel": 24,
         "cg_direction_kernel": 12,
@@ -192,7 +193,8 @@ BACKWARD_KERNELS = ("row_bwd_kernel", "col_bwd_kernel", "update_adjoint_kernel",
 def traffic_for(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, when that
     summary was taken on the current source of the file that holds the kernel (else None)."""
-    fn = "dts_backward.cu" if kernel.startswith(BACKWARD_KERNELS) else "dts_forward.cu"
+    fn = ("dts_backward.cu" if kernel.startswith(BACKWARD_KERNELS) else "dts_cg.cu" if kernel.startswith("cg_")
+          else "dts_forward.cu")
     src = os.path.join(ROOT, "paper_1805_04590_gb300", "csrc", fn)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     pdir = os.path.join(ROOT, "profiles")
@@ -425,14 +427,14 @@ def run_ours(args, rank, world, local_rank):
     if kern:
         dom = max(kern, key=lambda n: kern[n]["ms"])
         kd = kern[dom]
-        bpp = bytes_per_pixel(dom, case.s_d, case.s_io, C=C, s_g=s_g)
+        bpp = bytes_per_pixel(dom, case.s_d, case.s_io, C=C, s_g=s_g, N=case.prm.passes)
         alg_bytes = bpp * kd["pixels"] / kd["launches"]
         avg_s = kd["ms"] / kd["launches"] / 1e3
         peak, peak_kind = measured_peak()
         achieved = alg_bytes / avg_s / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs (copy)",
-                "algorithmic_bytes_per_launch": int(alg_bytes), "bytes_per_pixel": bpp,
+                "algorithmic_bytes_per_launch": int(alg_bytes), "bytes_per_pixel": round(bpp, 3),
                 "avg_launch_us": round(avg_s * 1e6, 2), "traffic": traffic_for(dom),
                 "share_of_step": round(kd["ms"] / sum(v["ms"] for v in kern.values()), 4)}
         kernels = {n: {"launches": v["launches"], "avg_us": round(v["ms"] / v["launches"] * 1e3, 2),
