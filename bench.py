@@ -106,6 +106,9 @@ def parse_args():
     ap.add_argument("--direction", choices=["fwd", "fwdbwd"], default="fwd")
     ap.add_argument("--update", choices=["gd", "jacobi", "cg"], default="gd",
                     help="Eq. 3 gradient step, Eq. 4 fixed point, or conjugate gradients on Eq. 2")
+    ap.add_argument("--sweep", choices=["iterations", "sigma", "size"], default=None,
+                    help="one JSON line per point instead of the bench line: accuracy and time against "
+                         "iterations (GD, Jacobi, CG), time against sigma_s / sigma_r, time against megapixels")
     ap.add_argument("--charbonnier-eps", type=float, default=0.0,
                     help="> 0: Charbonnier loss on the target term (the paper's stereo loss uses 0.001)")
     return ap.parse_args()
@@ -575,8 +578,90 @@ def run_reference(args):
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------- sweeps
+def _time_solve(torch, dts, g, t, c, prm, out, ws, flush, reps=3):
+    """Median device time (ms) of one solve, L2 flushed before each."""
+    dts.dts_solve(g, t, c, prm, out=out, ws=ws)
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dts.dts_solve(g, t, c, prm, out=out, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    if dts.dts_last_status() != 0:
+        raise RuntimeError("device status not clean")
+    return sorted(times)[len(times) // 2]
+
+
+def run_sweep(args):
+    """The paper's scaling experiments on the stereo-shaped workload (synthetic): accuracy (MAE and
+    RMSE against the generator's true disparity, and the objective of Eq. 2) and time against the
+    number of iterations for the three update rules; time against sigma_s and sigma_r; time against
+    the image size."""
+    import torch
+    from paper_1805_04590_gb300 import dts, workloads
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    lines = []
+
+    def load(wl):
+        p = wl.problems[0]
+        return (p, torch.from_numpy(p.guide).to(dev), torch.from_numpy(p.target).to(dev),
+                torch.from_numpy(p.conf).to(dev))
+
+    if args.sweep == "iterations":
+        wl = workloads.make(1)
+        q = wl.params
+        p, g, t, c = load(wl)
+        truth = torch.from_numpy(p.truth).to(dev).double()
+        out = torch.empty_like(t)
+        for upd in ("gd", "jacobi", "cg"):
+            for K in (1, 2, 5, 10, 20, 50, 100, 200):
+                prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, step=q.step, iterations=K,
+                                 passes=q.passes, update=UPDATES[upd])
+                ws = dts.workspace(g, prm)
+                ms = _time_solve(torch, dts, g, t, c, prm, out, ws, flush)
+                z = out.double()
+                Az = dts.dts_filter(g, out, prm).double()
+                F = float(0.5 * q.lam * ((z - Az) ** 2).sum() + (c.double() * (z - t.double()) ** 2).sum())
+                err = z - truth
+                lines.append({"sweep": "iterations", "update": upd, "iterations": K, "ms_per_solve": round(ms, 4),
+                              "mae_px": round(float(err.abs().mean()), 5),
+                              "rmse_px": round(float((err ** 2).mean().sqrt()), 5), "objective_eq2": F})
+    elif args.sweep == "sigma":
+        wl = workloads.make(1)
+        q = wl.params
+        _, g, t, c = load(wl)
+        out = torch.empty_like(t)
+        for ss, sr in [(s_, 0.1) for s_ in (16.0, 32.0, 128.0, 256.0)] + [(16.0, r_) for r_ in (0.3, 0.5, 0.7, 0.9)]:
+            prm = dts.Params(lam=q.lam, sigma_s=ss, sigma_r=sr, iterations=q.iterations, passes=q.passes)
+            ms = _time_solve(torch, dts, g, t, c, prm, out, dts.workspace(g, prm), flush)
+            lines.append({"sweep": "sigma", "sigma_s": ss, "sigma_r": sr, "iterations": q.iterations,
+                          "ms_per_solve": round(ms, 4)})
+    else:
+        for f in (0.25, 0.5, 0.75, 1.0, 1.5):
+            H, W = int(round(1988 * f)), int(round(2880 * f))
+            wl = workloads.workload_stereo(H=H, W=W)
+            q = wl.params
+            _, g, t, c = load(wl)
+            out = torch.empty_like(t)
+            prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes)
+            ms = _time_solve(torch, dts, g, t, c, prm, out, dts.workspace(g, prm), flush)
+            lines.append({"sweep": "size", "H": H, "W": W, "megapixels": round(H * W / 1e6, 4),
+                          "iterations": q.iterations, "ms_per_solve": round(ms, 4),
+                          "mp_per_s": round(H * W / 1e6 / (ms / 1e3), 1)})
+    return lines
+
+
 def main():
     args = parse_args()
+    if args.sweep:
+        for line in run_sweep(args):
+            print(json.dumps(line), flush=True)
+        return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
