@@ -440,6 +440,13 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic_bytes_per_launch": int(alg_bytes), "bytes_per_pixel": round(bpp, 3),
                 "avg_launch_us": round(avg_s * 1e6, 2), "traffic": traffic_for(dom),
                 "share_of_step": round(kd["ms"] / sum(v["ms"] for v in kern.values()), 4)}
+        # the whole step against the same peak: every kernel's algorithmic bytes over the step time
+        bpps = {n: bytes_per_pixel(n, case.s_d, case.s_io, C=C, s_g=s_g, N=case.prm.passes) for n in kern}
+        step_bytes = sum(bpps[n] * v["pixels"] for n, v in kern.items() if bpps[n] is not None) / profiled_steps
+        step_s = total_ms / args.steps / 1e3
+        roof["step"] = {"algorithmic_bytes": int(step_bytes), "achieved": round(step_bytes / step_s / 1e9, 1),
+                        "frac": round(step_bytes / step_s / 1e9 / peak, 4),
+                        "kernels_without_bytes": sorted(n for n in kern if bpps[n] is None)}
         kernels = {n: {"launches": v["launches"], "avg_us": round(v["ms"] / v["launches"] * 1e3, 2),
                        "share": round(v["ms"] / sum(x["ms"] for x in kern.values()), 4)} for n, v in kern.items()}
 
@@ -642,7 +649,7 @@ def run_sweep(args):
             lines.append({"sweep": "sigma", "sigma_s": ss, "sigma_r": sr, "iterations": q.iterations,
                           "ms_per_solve": round(ms, 4)})
     else:
-        for f in (0.25, 0.5, 0.75, 1.0, 1.5):
+        for f in (0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.18):
             H, W = int(round(1988 * f)), int(round(2880 * f))
             wl = workloads.workload_stereo(H=H, W=W)
             q = wl.params
