@@ -263,6 +263,30 @@ __global__ void __launch_bounds__(256) distance4_kernel(DistArgs a) {
     const int y0 = (blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kDistRows;
     const bool xok = x0 < a.W;  // W % 4 == 0: the thread's four columns are all inside or all outside
     const GT* I = static_cast<const GT*>(a.guide);
+    if (a.dst && xok) {
+        // the fused copy first, all rows' loads in flight at once (16-byte vectors for an FP32
+        // source on 16-byte boundaries); its stores retire while the guide is read
+        const bool vsrc = a.src_dtype == DTS_F32 && ((uintptr_t)a.src & 15) == 0;
+        float tv[kDistRows][4];
+#pragma unroll
+        for (int r = 0; r < kDistRows; ++r) {
+            const int y = y0 + r;
+            if (y >= a.H) break;
+            const long long di = (long long)y * a.W + x0;
+            if (vsrc) {
+                load4_f(static_cast<const float*>(a.src), di, tv[r]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) tv[r][k] = load_any(a.src, di + k, a.src_dtype);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kDistRows; ++r) {
+            const int y = y0 + r;
+            if (y >= a.H) break;
+            store4_f(a.dst, (long long)y * a.pitch + x0, tv[r]);
+        }
+    }
     float sx[kDistRows][4], sy[kDistRows][4];
 #pragma unroll
     for (int r = 0; r < kDistRows; ++r)
@@ -313,10 +337,6 @@ __global__ void __launch_bounds__(256) distance4_kernel(DistArgs a) {
         store4_dist<DT>(static_cast<DT*>(a.dX) + q, dx);
         store4_dist<DT>(static_cast<DT*>(a.dY) + q, dy);
         if (a.dYs) store4_dist<DT>(static_cast<DT*>(a.dYs) + ((long long)(x0 >> 3) * a.ys_rows + y) * 8 + (x0 & 7), dy);
-        if (a.dst) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) a.dst[q + k] = load_any(a.src, (long long)y * a.W + x0 + k, a.src_dtype);
-        }
     }
 }
 

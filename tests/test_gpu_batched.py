@@ -139,3 +139,16 @@ def test_batched_bf16_storage():
         rng = float(np.ptp(tr)) or 1.0
         assert np.abs(z - oracle.solve(gr, tr, p.conf, **kw)).max() <= TOL * rng, i
         assert np.abs(z - oracle.solve(p.guide, p.target, p.conf, **kw)).max() <= BF16_INPUT_TOL * rng, i
+
+
+def test_batched_charbonnier():
+    """The Charbonnier target loss (§4) in the batched graph, eps = 1 (contractive step)."""
+    wl, g, t, c, prm = _batch(9, n=5)
+    prm.charbonnier_eps = 1.0
+    outs = dts.dts_solve_batched(g, t, c, prm)
+    torch.cuda.synchronize()
+    assert dts.dts_last_status() == 0
+    for i, p in enumerate(wl.problems):
+        ref = oracle.solve(p.guide, p.target, p.conf, lam=prm.lam, sigma_s=prm.sigma_s, sigma_r=prm.sigma_r,
+                           iterations=prm.iterations, charbonnier_eps=1.0)
+        assert np.abs(outs[i].cpu().numpy() - ref).max() <= TOL * float(np.ptp(p.target)), i

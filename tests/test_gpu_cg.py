@@ -57,6 +57,17 @@ def test_cg_matches_oracle(H, W, K):
     assert_close(z.cpu().numpy(), ref, prob.target, f"{H}x{W} K={K}")
 
 
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 23), (29, 1), (2, 2), (3, 700)])
+def test_cg_degenerate_shapes(H, W):
+    """Lines of one position (the passes are the identity there) and very short lines."""
+    prob = workloads.random_problem(H, W, seed=3 * H + W)
+    z = dts.dts_solve(to_dev(prob.guide), to_dev(prob.target), to_dev(prob.conf), params(4))
+    torch.cuda.synchronize()
+    assert dts.dts_last_status() == 0
+    ref = oracle.solve_cg(prob.guide, prob.target, prob.conf, lam=LAM, sigma_s=SIG_S, sigma_r=SIG_R, iterations=4)
+    assert_close(z.cpu().numpy(), ref, prob.target, f"{H}x{W}")
+
+
 def test_cg_first_step_uses_the_transposed_filter():
     """One step from z_0 = t: r_0 = 2 C t - M t involves A^T.  The same step with A in place of
     A^T (a plausible slip) is far from the GPU result, so the check can tell them apart."""
