@@ -405,12 +405,8 @@ def run_ours(args, rank, world, local_rank):
     if rejected(clk):
         ms, wall, clk, recs = timed_loop()
         clk["remeasured"] = True
-    total_ms = float(np.sum(ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * args.steps * case.mp / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(np.sum(ms)), world, dev)
+    value = job_value(world, args.steps, case.mp, total_ms)
     if dts.dts_last_status() != 0:
         raise RuntimeError("device status not clean after the timed region")
 
@@ -583,6 +579,22 @@ def run_reference(args):
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------- replicas across ranks
+def max_over_ranks(x, world, device=None):
+    """The largest x over the ranks of the process group (the slowest replica's time)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, mp_per_step, total_ms):
+    """Whole-job throughput: every rank's megapixels over the slowest rank's time (MP/s)."""
+    return world * steps * mp_per_step / (total_ms / 1e3)
 
 
 # ---------------------------------------------------------------- sweeps

@@ -1,0 +1,59 @@
+"""The multi-rank bench logic on the CPU (world size 2, gloo): replicas time their own solves,
+the job's time is the slowest rank's and its throughput counts every rank's pixels; the
+reference arm runs on rank 0 only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, times, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        total = bench.max_over_ranks(times[rank], world)
+        out[rank] = (total, bench.job_value(world, 10, 5.0, total))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replicas_take_the_slowest_rank_and_count_every_rank():
+    world = 2
+    times = [120.0, 150.0]  # ms of each rank's timed region
+    out = mp.Manager().dict()
+    mp.spawn(_rank_main, args=(world, _free_port(), times, out), nprocs=world, join=True)
+    for r in range(world):
+        total, value = out[r]
+        assert total == 150.0
+        assert value == pytest.approx(world * 10 * 5.0 / 0.150)
+
+
+def test_single_rank_is_its_own_maximum():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(42.0, 1) == 42.0
+    assert bench.job_value(1, 4, 2.0, 1000.0) == pytest.approx(8.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
