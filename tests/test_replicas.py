@@ -36,7 +36,7 @@ def _rank_main(rank, world, port, times, out):
 def test_replicas_take_the_slowest_rank_and_count_every_rank():
     world = 2
     times = [120.0, 150.0]  # ms of each rank's timed region
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_rank_main, args=(world, _free_port(), times, out), nprocs=world, join=True)
     for r in range(world):
         total, value = out[r]
