@@ -41,9 +41,9 @@ def assert_close(z, ref, t, what=""):
     assert err <= TOL * rng, f"{what}: max|gpu-oracle| = {err:.3e} > {TOL * rng:.3e}"
 
 
-# one-CTA columns, cluster columns, columns above the strip kernel's height, long rows, ragged
-# widths (the transposed vertical pass always takes the cluster kernel)
-SHAPES = [(37, 53), (130, 300), (300, 257), (1100, 96), (2300, 70), (70, 5000)]
+# one-CTA columns, columns of strip CTAs with 9- and 17-row segments, columns above the strip
+# kernel's height (cluster kernel), long rows (up to 9000: 576-thread row CTAs), ragged widths
+SHAPES = [(37, 53), (130, 300), (300, 257), (1100, 96), (2300, 70), (70, 5000), (20, 9000)]
 
 
 @pytest.mark.parametrize("H,W", SHAPES)
