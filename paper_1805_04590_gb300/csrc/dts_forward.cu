@@ -167,7 +167,7 @@ struct SupportMode {
 // Thread = one column x and kDistRows consecutive rows; a warp covers 32 consecutive columns,
 // so every guide row segment is one coalesced access and the left neighbour comes from the
 // adjacent lane.
-constexpr int kDistRows = 8;
+constexpr int kDistRows = 4;
 
 template <typename GT, typename DT>
 __global__ void __launch_bounds__(256) distance_kernel(DistArgs a) {
