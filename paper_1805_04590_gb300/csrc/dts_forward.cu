@@ -382,10 +382,17 @@ __device__ __forceinline__ void load4_t(const PassArgs& a, long long i, bool vec
     }
 }
 
+// the update pass at up to 16 positions per thread is capped at 64 registers (two CTAs of 512
+// threads per SM at most); 32 positions would spill
+template <int ITEMS, int KIND>
+constexpr int row_min_blocks() {
+    return (KIND == PASS_UPDATE_ROW && ITEMS <= 16) ? 2 : 1;
+}
+
 // TWO: the normalised pass as two one-direction exchanges of affine maps (causal, then
 // anti-causal on its result) instead of one exchange of the coupled five numbers.
 template <int ITEMS, bool DHALF, int KIND, bool TWO = false>
-__global__ void __launch_bounds__(row_max_threads<ITEMS, KIND>()) row_pass_kernel(PassArgs a, int tpr) {
+__global__ void __launch_bounds__(row_max_threads<ITEMS, KIND>(), row_min_blocks<ITEMS, KIND>()) row_pass_kernel(PassArgs a, int tpr) {
     static_assert(ITEMS % 4 == 0, "ITEMS must be a multiple of 4");
     using M = typename std::conditional<KIND == PASS_SUPPORT, SupportMode,
                                         typename std::conditional<KIND == PASS_TRANSPOSE, TransposeMode,
