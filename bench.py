@@ -85,6 +85,8 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3):
         # the first transposed vertical pass of a product also reads the minuend plane
         "col_pass_kernel<transpose>": 8 + s_d + 4.0 / N,
         "col_strip_kernel<transpose>": 8 + s_d + 4.0 / N,
+        "box_line_kernel": 12,
+        "transpose_kernel": 8,
         "cg_apply_kernel": 20,
         "cg_step_kernel": 24,
         "cg_direction_kernel": 12,
@@ -109,6 +111,8 @@ def parse_args():
     ap.add_argument("--sweep", choices=["iterations", "sigma", "size"], default=None,
                     help="one JSON line per point instead of the bench line: accuracy and time against "
                          "iterations (GD, Jacobi, CG), time against sigma_s / sigma_r, time against megapixels")
+    ap.add_argument("--filter-kernel", choices=["rf", "box"], default="rf",
+                    help="recursive-filter kernel, or the box kernel Eq. 10 prints")
     ap.add_argument("--charbonnier-eps", type=float, default=0.0,
                     help="> 0: Charbonnier loss on the target term (the paper's stereo loss uses 0.001)")
     return ap.parse_args()
@@ -247,7 +251,8 @@ class Case:
         self.prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, step=q.step, iterations=q.iterations,
                               passes=q.passes, dist_dtype=dts.F16 if self.s_d == 2 else dts.F32,
                               save_checkpoints=0, update=UPDATES[args.update],
-                              charbonnier_eps=args.charbonnier_eps)
+                              charbonnier_eps=args.charbonnier_eps,
+                              filter_kernel=dts.KERNEL_BOX if args.filter_kernel == "box" else dts.KERNEL_RF)
         probs = self.wl.problems
         self.mp = sum(p.target.size for p in probs) / 1e6
         self.g = [torch.from_numpy(p.guide).to(dev).to(self.sdt) for p in probs]
@@ -313,6 +318,7 @@ class Case:
                 "direction": self.args.direction, "storage": self.args.storage, "update": self.args.update,
                 "target_loss": (f"charbonnier eps={self.args.charbonnier_eps:g}" if self.args.charbonnier_eps > 0
                                 else "square"),
+                "filter_kernel": {"rf": "recursive filter", "box": "box (Eq. 10 as printed)"}[self.args.filter_kernel],
                 "distance_storage": self.args.dist_dtype, "l2": "flushed between steps (512 MiB write)",
                 "backward_checkpoints": ({1: "iterates (pass inputs recomputed)", 2: "every pass input"}
                                          .get(self.prm.save_checkpoints) if self.bwd else None),
@@ -520,7 +526,9 @@ def run_ours(args, rank, world, local_rank):
     if case.name == "batched":
         line["gpu_launches_note"] = "one CUDA graph launch per step; its kernels are not bracketed by events"
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    # the oracle's box filter tests every sample of a line for every position (quadratic in the
+    # line length): no bounded sample of a full-size image, so no CPU baseline for that kernel
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.filter_kernel == "rf":
         import oracle
         mp, dt, desc, error = case.cpu_sample()
         line["cpu_baseline"] = {"value": round(mp / dt, 4), "unit": UNIT, "cores": oracle.num_threads(),
@@ -537,6 +545,9 @@ def run_reference(args):
     from paper_1805_04590_gb300 import workloads
     if args.update == "cg" and args.direction == "fwdbwd":
         raise SystemExit("conjugate gradients have no backward")
+    if args.filter_kernel == "box":
+        raise SystemExit("the reference arm times the recursive-filter solve (the oracle's box filter is quadratic "
+                         "in the line length)")
     wl = workloads.make(WORKLOAD_INDEX[args.workload])
     q = wl.params
     p = wl.problems[0]

@@ -5,9 +5,12 @@
 // an exact integer count of 2^-23 units (64 bits: exact for coordinates below 2^40) and window
 // membership compares the exact difference ct[m] - ct[n] with R = floor(r 2^23), which is the
 // same decision as |ct[m] - ct[n]| <= r in exact arithmetic: which samples a window holds is
-// fixed by the inputs alone, whatever the order of the additions.  The sums of x are FP64
-// prefix sums (one addition and one subtraction per position: GB300's FP64 rate is low).
-// Rows run directly; columns run as rows of the transposed plane (transpose_kernel).
+// fixed by the inputs alone, whatever the order of the additions.  The integer comes from the
+// distance's bits (for d >= 1, d 2^23 is its significand shifted by its exponent) and the sums of
+// x are prefix sums held as pairs of FP32 numbers (error-free addition, Knuth's two-sum: about 48
+// significant bits), so the kernel uses no FP64 arithmetic, whose rate on GB300 is a small
+// fraction of FP32's.  Rows run directly; columns run as rows of the transposed plane
+// (transpose_kernel).
 #include "dts_scan.cuh"
 
 namespace dts {
@@ -19,6 +22,37 @@ using namespace scan;
 constexpr int kBoxThreads = 512;
 constexpr double kBoxUnit = 8388608.0;  // 2^23: FP32 values >= 1 are whole multiples of 2^-23
 
+// d 2^23 as an exact integer for an FP32 distance d >= 1; 0 for the unused first entry of a line
+__device__ __forceinline__ long long dist_units(float d) {
+    if (!(d >= 1.f)) return 0;
+    const unsigned b = __float_as_uint(d);
+    const int e = (int)((b >> 23) & 0xffu) - 127;
+    return (long long)((b & 0x7fffffu) | 0x800000u) << e;
+}
+
+// a value as an unevaluated sum h + l of two FP32 numbers
+struct Pair {
+    float h, l;
+};
+// a + b with the rounding error of the leading part kept (two-sum), then renormalised
+__device__ __forceinline__ Pair pair_add(Pair a, Pair b) {
+    const float s = a.h + b.h;
+    const float bv = s - a.h;
+    const float err = ((a.h - (s - bv)) + (b.h - bv)) + (a.l + b.l);
+    const float h = s + err;
+    return Pair{h, err - (h - s)};
+}
+// a - b rounded to FP32
+__device__ __forceinline__ float pair_diff(Pair a, Pair b) {
+    const float s = a.h - b.h;
+    const float bv = s - a.h;
+    const float err = (a.h - (s - bv)) + (-b.h - bv);
+    return s + (err + (a.l - b.l));
+}
+__device__ __forceinline__ Pair pair_shfl_up(Pair v, int off) {
+    return Pair{__shfl_up_sync(kFull, v.h, off), __shfl_up_sync(kFull, v.l, off)};
+}
+
 // One CTA per line of length L (L <= kBoxMaxLine): stage the line in shared memory, exact prefix
 // sums, then each thread averages the windows of its contiguous chunk of positions.
 __global__ void __launch_bounds__(kBoxThreads) box_line_kernel(const float* src, long long sp, float* dst,
@@ -26,11 +60,12 @@ __global__ void __launch_bounds__(kBoxThreads) box_line_kernel(const float* src,
                                                                int lines, long long R) {
     extern __shared__ __align__(16) unsigned char box_smem[];
     long long* ct = reinterpret_cast<long long*>(box_smem);  // L, in 2^-23 units
-    double* S = reinterpret_cast<double*>(ct + L);           // L + 1: S[m] = x[0] + ... + x[m-1]
-    float* xs = reinterpret_cast<float*>(S + L + 1);         // L
+    float* Sh = reinterpret_cast<float*>(ct + L);            // L + 1: S[m] = x[0] + ... + x[m-1]
+    float* Sl = Sh + (L + 1);                                //        as the pair (Sh, Sl)
+    float* xs = Sl + (L + 1);                                // L
     float* ds = xs + L;                                      // L
     __shared__ long long w_d[kBoxThreads / 32];
-    __shared__ double w_x[kBoxThreads / 32];
+    __shared__ Pair w_x[kBoxThreads / 32];
     const int line = blockIdx.x;
     if (line >= lines) return;  // uniform over the CTA
     wait_predecessor();
@@ -45,42 +80,50 @@ __global__ void __launch_bounds__(kBoxThreads) box_line_kernel(const float* src,
     const int b = min((int)threadIdx.x * per, L);
     const int e = min(b + per, L);
     long long sd = 0;
-    double sx = 0.0;
+    Pair sx = {0.f, 0.f};
     for (int i = b; i < e; ++i) {
-        sd += __double2ll_rn((double)ds[i] * kBoxUnit);
-        sx += (double)xs[i];
+        sd += dist_units(ds[i]);
+        sx = pair_add(sx, Pair{xs[i], 0.f});
     }
     // exclusive scan of the chunk sums over the CTA (warp shuffles, then the warp totals)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long id = sd;
-    double ix = sx;
+    Pair ix = sx;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const long long od = __shfl_up_sync(kFull, id, off);
-        const double ox = __shfl_up_sync(kFull, ix, off);
+        const Pair ox = pair_shfl_up(ix, off);
         if (lane >= off) {
             id += od;
-            ix += ox;
+            ix = pair_add(ox, ix);
         }
     }
     if (lane == 31) {
         w_d[warp] = id;
         w_x[warp] = ix;
     }
+    long long cd = __shfl_up_sync(kFull, id, 1);
+    Pair cx = pair_shfl_up(ix, 1);
+    if (lane == 0) {
+        cd = 0;
+        cx = Pair{0.f, 0.f};
+    }
     __syncthreads();
-    long long cd = id - sd;
-    double cx = ix - sx;
-    for (int q = 0; q < warp; ++q) {
+    for (int q = warp - 1; q >= 0; --q) {
         cd += w_d[q];
-        cx += w_x[q];
+        cx = pair_add(w_x[q], cx);
     }
     for (int i = b; i < e; ++i) {
-        cd += __double2ll_rn((double)ds[i] * kBoxUnit);
+        cd += dist_units(ds[i]);
         ct[i] = cd;
-        S[i] = cx;
-        cx += (double)xs[i];
+        Sh[i] = cx.h;
+        Sl[i] = cx.l;
+        cx = pair_add(cx, Pair{xs[i], 0.f});
     }
-    if (b < e && e == L) S[L] = cx;
+    if (b < e && e == L) {
+        Sh[L] = cx.h;
+        Sl[L] = cx.l;
+    }
     __syncthreads();
     release_successor();
     if (b >= e) return;
@@ -104,7 +147,7 @@ __global__ void __launch_bounds__(kBoxThreads) box_line_kernel(const float* src,
         const long long ci = ct[i];
         while (ci - ct[lo] > R) ++lo;
         while (up + 1 < L && ct[up + 1] - ci <= R) ++up;
-        out[i] = (float)(S[up + 1] - S[lo]) / (float)(up - lo + 1);
+        out[i] = pair_diff(Pair{Sh[up + 1], Sl[up + 1]}, Pair{Sh[lo], Sl[lo]}) / (float)(up - lo + 1);
     }
 }
 
@@ -127,7 +170,7 @@ __global__ void __launch_bounds__(256) transpose_kernel(const float* src, long l
 
 }  // namespace
 
-size_t box_line_smem(int L) { return (size_t)L * 8 + (size_t)(L + 1) * 8 + (size_t)L * 8; }  // ct, S, x and d
+size_t box_line_smem(int L) { return (size_t)L * 8 + (size_t)(L + 1) * 8 + (size_t)L * 8; }  // ct, S pairs, x, d
 
 cudaError_t prepare_box_kernels() {
     return cudaFuncSetAttribute((const void*)box_line_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
