@@ -201,7 +201,7 @@ def traffic_for(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, when that
     summary was taken on the current source of the file that holds the kernel (else None)."""
     fn = ("dts_backward.cu" if kernel.startswith(BACKWARD_KERNELS) else "dts_cg.cu" if kernel.startswith("cg_")
-          else "dts_forward.cu")
+          else "dts_box.cu" if kernel.startswith(("box_", "transpose_")) else "dts_forward.cu")
     src = os.path.join(ROOT, "paper_1805_04590_gb300", "csrc", fn)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     pdir = os.path.join(ROOT, "profiles")

@@ -11,6 +11,8 @@
 // significant bits), so the kernel uses no FP64 arithmetic, whose rate on GB300 is a small
 // fraction of FP32's.  Rows run directly; columns run as rows of the transposed plane
 // (transpose_kernel).
+#include <algorithm>
+
 #include "dts_scan.cuh"
 
 namespace dts {
@@ -54,15 +56,19 @@ __device__ __forceinline__ Pair pair_shfl_up(Pair v, int off) {
 }
 
 // One CTA per line of length L (L <= kBoxMaxLine): stage the line in shared memory, exact prefix
-// sums, then each thread averages the windows of its contiguous chunk of positions.
+// sums, then each thread averages the windows of its contiguous chunk of `per` positions.  `per`
+// is odd, so the 32 threads of a warp, per positions apart, touch 32 different shared-memory
+// banks in the chunk loops.  Every distance is at least 1 (2^23 units), so positions more than
+// rmax = floor(r) apart never share a window: a window's ends are searched within rmax positions.
+// Results go back through shared memory for coalesced stores.
 __global__ void __launch_bounds__(kBoxThreads) box_line_kernel(const float* src, long long sp, float* dst,
                                                                long long dstp, const float* d, long long dp, int L,
-                                                               int lines, long long R) {
+                                                               int lines, long long R, int per, int rmax, int top) {
     extern __shared__ __align__(16) unsigned char box_smem[];
     long long* ct = reinterpret_cast<long long*>(box_smem);  // L, in 2^-23 units
     float* Sh = reinterpret_cast<float*>(ct + L);            // L + 1: S[m] = x[0] + ... + x[m-1]
     float* Sl = Sh + (L + 1);                                //        as the pair (Sh, Sl)
-    float* xs = Sl + (L + 1);                                // L
+    float* xs = Sl + (L + 1);                                // L: the line, later the results
     float* ds = xs + L;                                      // L
     __shared__ long long w_d[kBoxThreads / 32];
     __shared__ Pair w_x[kBoxThreads / 32];
@@ -76,7 +82,6 @@ __global__ void __launch_bounds__(kBoxThreads) box_line_kernel(const float* src,
         ds[i] = i ? dl[i] : 0.f;  // ct[0] = 0: the first distance of a line is never used
     }
     __syncthreads();
-    const int per = (L + blockDim.x - 1) / blockDim.x;
     const int b = min((int)threadIdx.x * per, L);
     const int e = min(b + per, L);
     long long sd = 0;
@@ -85,7 +90,7 @@ __global__ void __launch_bounds__(kBoxThreads) box_line_kernel(const float* src,
         sd += dist_units(ds[i]);
         sx = pair_add(sx, Pair{xs[i], 0.f});
     }
-    // exclusive scan of the chunk sums over the CTA (warp shuffles, then the warp totals)
+    // exclusive scan of the chunk sums over the CTA: warp shuffles, then warp 0 scans the warp totals
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long id = sd;
     Pair ix = sx;
@@ -109,10 +114,33 @@ __global__ void __launch_bounds__(kBoxThreads) box_line_kernel(const float* src,
         cx = Pair{0.f, 0.f};
     }
     __syncthreads();
-    for (int q = warp - 1; q >= 0; --q) {
-        cd += w_d[q];
-        cx = pair_add(w_x[q], cx);
+    if (warp == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        long long vd = lane < nw ? w_d[lane] : 0;
+        Pair vx = lane < nw ? w_x[lane] : Pair{0.f, 0.f};
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long od = __shfl_up_sync(kFull, vd, off);
+            const Pair ox = pair_shfl_up(vx, off);
+            if (lane >= off) {
+                vd += od;
+                vx = pair_add(ox, vx);
+            }
+        }
+        long long ed = __shfl_up_sync(kFull, vd, 1);
+        Pair ex = pair_shfl_up(vx, 1);
+        if (lane == 0) {
+            ed = 0;
+            ex = Pair{0.f, 0.f};
+        }
+        if (lane < nw) {
+            w_d[lane] = ed;
+            w_x[lane] = ex;
+        }
     }
+    __syncthreads();
+    cd += w_d[warp];
+    cx = pair_add(w_x[warp], cx);
     for (int i = b; i < e; ++i) {
         cd += dist_units(ds[i]);
         ct[i] = cd;
@@ -126,43 +154,43 @@ __global__ void __launch_bounds__(kBoxThreads) box_line_kernel(const float* src,
     }
     __syncthreads();
     release_successor();
-    if (b >= e) return;
-    // first window by binary search, then both ends move forward with the position
-    const long long cb = ct[b];
-    int lo = 0, hi = b;  // lo: first m with ct[b] - ct[m] <= R
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (cb - ct[mid] <= R) hi = mid;
-        else lo = mid + 1;
-    }
-    int a = b, z = L - 1;  // up: last m with ct[m] - ct[b] <= R
-    while (a < z) {
-        const int mid = (a + z + 1) >> 1;
-        if (ct[mid] - cb <= R) a = mid;
-        else z = mid - 1;
-    }
-    int up = a;
-    float* out = dst + (long long)line * dstp;
+    // each window's ends by binary lifting with the same number of steps in every thread (top: the
+    // largest power of two <= rmax), so the warps do not diverge where a window jumps an edge.
+    // xs[b..e) was last read by this thread above: the results replace it.
     for (int i = b; i < e; ++i) {
         const long long ci = ct[i];
-        while (ci - ct[lo] > R) ++lo;
-        while (up + 1 < L && ct[up + 1] - ci <= R) ++up;
-        out[i] = pair_diff(Pair{Sh[up + 1], Sl[up + 1]}, Pair{Sh[lo], Sl[lo]}) / (float)(up - lo + 1);
+        int lo = max(0, i - rmax);  // first m with ci - ct[m] <= R (m = i qualifies)
+        int up = i;                 // last m <= min(L - 1, i + rmax) with ct[m] - ci <= R
+        const int hb = min(L - 1, i + rmax);
+        for (int st = top; st > 0; st >>= 1) {
+            const int ml = min(lo + st - 1, i);
+            if (ci - ct[ml] > R) lo = ml + 1;
+            const int mu = min(up + st, hb);
+            if (ct[mu] - ci <= R) up = mu;
+        }
+        xs[i] = __fdividef(pair_diff(Pair{Sh[up + 1], Sl[up + 1]}, Pair{Sh[lo], Sl[lo]}), (float)(up - lo + 1));
     }
+    __syncthreads();
+    float* out = dst + (long long)line * dstp;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) out[i] = xs[i];
 }
 
-// dst[x][y] = src[y][x] for an H x W plane (32 x 32 tiles through shared memory)
-__global__ void __launch_bounds__(256) transpose_kernel(const float* src, long long sp, float* dst, long long dp,
-                                                        int H, int W) {
+// dst[x][y] = src[y][x] for an H x W plane (32 x 32 tiles through shared memory; 32 x kTransposeRows
+// threads, each moving 32 / kTransposeRows elements with all its loads in flight)
+constexpr int kTransposeRows = 8;
+__global__ void __launch_bounds__(32 * kTransposeRows) transpose_kernel(const float* src, long long sp, float* dst,
+                                                                        long long dp, int H, int W) {
     __shared__ float tile[32][33];
     wait_predecessor();
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+#pragma unroll
+    for (int j = threadIdx.y; j < 32; j += kTransposeRows) {
         const int y = y0 + j, x = x0 + threadIdx.x;
         if (y < H && x < W) tile[j][threadIdx.x] = src[(long long)y * sp + x];
     }
     __syncthreads();
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+#pragma unroll
+    for (int j = threadIdx.y; j < 32; j += kTransposeRows) {
         const int x = x0 + j, y = y0 + threadIdx.x;
         if (x < W && y < H) dst[(long long)x * dp + y] = tile[threadIdx.x][j];
     }
@@ -179,11 +207,18 @@ cudaError_t prepare_box_kernels() {
 
 cudaError_t launch_box_lines(const float* src, long long sp, float* dst, long long dstp, const float* d, long long dp,
                              int L, int lines, double r, cudaStream_t s) {
-    if (L < 1 || L > kBoxMaxLine) return cudaErrorInvalidValue;
+    if (L < 1 || L > kBoxMaxLine || !(r >= 0.0)) return cudaErrorInvalidValue;
     const long long R = (long long)floor(r * kBoxUnit);  // exact: r 2^23 scales by a power of two
+    const int rmax = (int)std::min(floor(r), (double)L);
+    int top = rmax > 0 ? 1 : 0;  // the largest power of two <= rmax
+    while (top > 0 && 2 * top <= rmax) top *= 2;
+    // the fewest odd positions per thread with at most kBoxThreads threads, whole warps
+    int per = (L + kBoxThreads - 1) / kBoxThreads;
+    if (per % 2 == 0) ++per;
+    const int threads = ((L + per - 1) / per + 31) / 32 * 32;
     const int h = prof_begin(KID_BOX, (long long)L * lines, 0, s);
-    const cudaError_t e = launch_ex_smem(box_line_kernel, dim3((unsigned)lines), dim3(kBoxThreads), 0, box_line_smem(L),
-                                         s, src, sp, dst, dstp, d, dp, L, lines, R);
+    const cudaError_t e = launch_ex_smem(box_line_kernel, dim3((unsigned)lines), dim3((unsigned)threads), 0,
+                                         box_line_smem(L), s, src, sp, dst, dstp, d, dp, L, lines, R, per, rmax, top);
     prof_end(h, s);
     return e;
 }
@@ -191,7 +226,7 @@ cudaError_t launch_box_lines(const float* src, long long sp, float* dst, long lo
 cudaError_t launch_transpose(const float* src, long long sp, float* dst, long long dp, int H, int W, cudaStream_t s) {
     const int h = prof_begin(KID_TRANSPOSE, (long long)H * W, 0, s);
     const dim3 grid((unsigned)((W + 31) / 32), (unsigned)((H + 31) / 32));
-    const cudaError_t e = launch_ex(transpose_kernel, grid, dim3(32, 8), 0, s, src, sp, dst, dp, H, W);
+    const cudaError_t e = launch_ex(transpose_kernel, grid, dim3(32, kTransposeRows), 0, s, src, sp, dst, dp, H, W);
     prof_end(h, s);
     return e;
 }

@@ -319,6 +319,20 @@ def test_box_filter(H, W):
     assert_close(out.cpu().numpy(), ref, prob.target, f"box filter {H}x{W}")
 
 
+@pytest.mark.parametrize("H,W,sigma_s", [(3, 8192, 8.0), (8192, 2, 8.0), (40, 300, 200.0), (300, 40, 200.0),
+                                         (5, 700, 4000.0)])
+def test_box_filter_long_lines_and_wide_windows(H, W, sigma_s):
+    """Lines of the longest supported length, and windows wider than the line (sigma_s / sigma_r
+    stays 32, so the windows are exact on both sides): the window ends are searched within
+    floor(r) positions with a step count set by r."""
+    prob = quantised_problem(H, W, seed=H * 7 + W)
+    kw = dict(sigma_s=sigma_s, sigma_r=sigma_s / 32.0)
+    prm = dts.Params(passes=3, filter_kernel=dts.KERNEL_BOX, **kw)
+    out = dts.dts_filter(to_dev(prob.guide), to_dev(prob.target), prm)
+    ref = oracle.box_filter(prob.guide, prob.target, passes=3, **kw)
+    assert_close(out.cpu().numpy(), ref, prob.target, f"box filter {H}x{W} sigma_s={sigma_s}")
+
+
 @pytest.mark.parametrize("update", [dts.UPDATE_GD, dts.UPDATE_JACOBI])
 def test_box_solve(update):
     prob = quantised_problem(150, 211, seed=31 + update)
