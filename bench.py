@@ -64,6 +64,9 @@ def oracle_solve(update, I, t, c, kw):
 def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3):
     return {
         "distance_kernel": C * s_g + 2 * s_d + s_t + 4,
+        # per pixel and iteration: the distances once per pass, z_k, t and c read and z_{k+1}
+        # written by the update; the iterate itself stays in shared memory between passes
+        "resident_solve_kernel": 2 * N * s_d + 12 + s_t,
         "copy_plane_kernel": s_t + 4,
         "row_pass_kernel": 8 + s_d,
         "col_pass_kernel": 8 + s_d,
@@ -201,7 +204,8 @@ def traffic_for(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, when that
     summary was taken on the current source of the file that holds the kernel (else None)."""
     fn = ("dts_backward.cu" if kernel.startswith(BACKWARD_KERNELS) else "dts_cg.cu" if kernel.startswith("cg_")
-          else "dts_box.cu" if kernel.startswith(("box_", "transpose_")) else "dts_forward.cu")
+          else "dts_box.cu" if kernel.startswith(("box_", "transpose_"))
+          else "dts_resident.cu" if kernel.startswith("resident_") else "dts_forward.cu")
     src = os.path.join(ROOT, "paper_1805_04590_gb300", "csrc", fn)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     pdir = os.path.join(ROOT, "profiles")

@@ -31,7 +31,7 @@ int ensure_prepared() {
     std::lock_guard<std::mutex> lock(g_prep_mutex);
     if (!g_prepared[dev]) {
         if (prepare_kernels() != cudaSuccess || prepare_backward_kernels() != cudaSuccess ||
-            prepare_box_kernels() != cudaSuccess)
+            prepare_box_kernels() != cudaSuccess || prepare_resident_kernel() != cudaSuccess)
             return DTS_ERR_CUDA;
         g_prepared[dev] = true;
     }
@@ -126,6 +126,9 @@ struct Layout {
     size_t passes;      // save_checkpoints = 2: K x 2N planes, (k, 0) = zbar_k, (k, q) = input of pass q
     size_t dYt, ut;     // box kernel: transposed dY and working plane (W rows, pitch tpitch)
     size_t cg;          // conjugate gradients: planes r, p, q, then FP64 scalars, ticket, partials
+    bool resident;      // the solve runs as one resident kernel (plan res), scratch at ragg, cagg, rbar
+    ResidentPlan res;
+    size_t ragg, cagg, rbar;
     long long tpitch;
     size_t fwd_end;     // bytes used by the forward
     // backward scratch
@@ -175,6 +178,15 @@ Layout make_layout(int H, int W, const dts_params* p, int with_backward) {
     }
     L.cg = off;
     if (p->update == DTS_UPDATE_CG) off += 3 * L.plane_f32 + align_up(kCgScalarBytes + kCgMaxBlocks * sizeof(double), kPlaneAlign);
+    L.resident = plan_resident(H, W, p, &L.res);
+    if (L.resident) {
+        L.ragg = off;
+        off += align_up((size_t)L.res.ragg_floats * sizeof(float), kPlaneAlign);
+        L.cagg = off;
+        off += align_up((size_t)L.res.cagg_floats * sizeof(float), kPlaneAlign);
+        L.rbar = off;
+        off += kPlaneAlign;
+    }
     L.passes = off;
     if (p->save_checkpoints == 2) off += (size_t)(p->iterations > 0 ? p->iterations : 1) * 2 * p->passes * L.plane_f32;
     L.fwd_end = off;
@@ -485,9 +497,42 @@ int solve_cg(const dts_guide* g, const void* target, int tdt, const float* conf,
     return DTS_OK;
 }
 
+// The solve as one resident kernel: distances and z_0, then every iteration in one cooperative
+// launch (dts_resident.cu).
+int solve_resident(const dts_guide* g, const void* target, int tdt, const float* conf, const float* z_init,
+                   const dts_params* p, float* z_out, void* ws, const Layout& L, cudaStream_t s) {
+    float* z = reinterpret_cast<float*>(ws_at(ws, L.z));
+    int st = z_init ? run_distances(g, p, L, ws, z_init, DTS_F32, z, s) : run_distances(g, p, L, ws, target, tdt, z, s);
+    if (st) return st;
+    ResidentLaunch r = {};
+    r.plan = L.res;
+    r.zbuf = z;
+    r.dX = reinterpret_cast<const float*>(ws_at(ws, L.dX));
+    r.dY = reinterpret_cast<const float*>(ws_at(ws, L.dY));
+    r.pitch = L.pitch;
+    r.t = target;
+    r.t_dtype = tdt;
+    r.c = conf;
+    r.zout = z_out;
+    r.H = g->H;
+    r.W = g->W;
+    r.K = p->iterations;
+    r.N = p->passes;
+    pass_log2a(p->sigma_s, p->passes, r.k2);
+    r.lambda = p->lambda;
+    r.step = p->step;
+    r.eps = p->charbonnier_eps;
+    r.update = p->update;
+    r.ragg = reinterpret_cast<float*>(ws_at(ws, L.ragg));
+    r.cagg = reinterpret_cast<float*>(ws_at(ws, L.cagg));
+    r.bar = reinterpret_cast<unsigned*>(ws_at(ws, L.rbar));
+    r.status = status_word();
+    return cuda_status(launch_resident(r, s));
+}
+
 int solve_forward(const dts_guide* g, const void* target, int tdt, const float* conf, const float* z_init,
                        const dts_params* p, float* z_out, void* ws, const Layout& L, const Plans& pl,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool allow_resident = false) {
     int st;
     const int K = p->iterations;
     const int W = g->W;
@@ -497,6 +542,7 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
     }
     if (p->update == DTS_UPDATE_CG) return solve_cg(g, target, tdt, conf, z_init, p, z_out, ws, L, pl, s);
     if ((st = bind_workspace(ws, L, s))) return st;
+    if (allow_resident && L.resident) return solve_resident(g, target, tdt, conf, z_init, p, z_out, ws, L, s);
     const bool keep = L.z_planes > 1 || p->save_checkpoints;
     auto zslot = [&](int k) -> float* {
         return reinterpret_cast<float*>(ws_at(ws, L.z + (keep ? (size_t)k * L.plane_f32 : 0)));
@@ -749,7 +795,8 @@ extern "C" int dts_solve(const dts_guide* guide, const void* target, int target_
     if ((st = ensure_prepared())) return st;
     if (params->filter_kernel == DTS_KERNEL_BOX)
         return solve_box(guide, target, target_dtype, conf, z_init, params, z_out, ws, L, (cudaStream_t)stream);
-    return solve_forward(guide, target, target_dtype, conf, z_init, params, z_out, ws, L, pl, (cudaStream_t)stream);
+    return solve_forward(guide, target, target_dtype, conf, z_init, params, z_out, ws, L, pl, (cudaStream_t)stream,
+                         true);
 }
 
 

@@ -222,6 +222,7 @@ enum KernelId {
     KID_CG_STEP = 25,
     KID_CG_DIRECTION = 26,
     KID_COL_STRIP_TRANSPOSE = 27,
+    KID_RESIDENT = 28,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
@@ -295,6 +296,37 @@ int cg_blocks(int H, long long pitch);
 cudaError_t launch_cg_apply(const CgArgs& a, bool init, cudaStream_t s);
 cudaError_t launch_cg_step(const CgArgs& a, cudaStream_t s);
 cudaError_t launch_cg_direction(const CgArgs& a, cudaStream_t s);
+
+// the whole solve with the iterate resident in shared memory (dts_resident.cu): one cooperative
+// CTA per tile of TH rows x 512 columns, ntx x nty tiles; scratch of ragg_floats + cagg_floats
+// floats for the segment tuples and 4 unsigned words for the grid barrier
+struct ResidentPlan {
+    int ntx, nty, TH;
+    size_t smem;
+    long long ragg_floats, cagg_floats;
+};
+struct ResidentLaunch {
+    ResidentPlan plan;
+    float* zbuf;            // z_0 on entry (pitch `pitch`), then the iterates
+    const float* dX;
+    const float* dY;
+    long long pitch;
+    const void* t;
+    int t_dtype;
+    const float* c;
+    float* zout;            // dense, pitch W
+    int H, W, K, N;
+    float k2[kMaxPasses];
+    float lambda, step, eps;
+    int update;
+    float* ragg;
+    float* cagg;
+    unsigned* bar;
+    int* status;
+};
+bool plan_resident(int H, int W, const dts_params* p, ResidentPlan* rp);
+cudaError_t prepare_resident_kernel();
+cudaError_t launch_resident(const ResidentLaunch& l, cudaStream_t s);
 
 bool plan_cols(int H, ColPlan* p);
 bool plan_cols_cluster(int H, ColPlan* p);

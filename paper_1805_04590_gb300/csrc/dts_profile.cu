@@ -120,6 +120,7 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_CG_STEP: return "cg_step_kernel";
         case KID_CG_DIRECTION: return "cg_direction_kernel";
         case KID_COL_STRIP_TRANSPOSE: return "col_strip_kernel<transpose>";
+        case KID_RESIDENT: return "resident_solve_kernel";
         default: return "unknown";
     }
 }

@@ -1,0 +1,489 @@
+// The whole solve in one persistent kernel with the iterate resident on chip (§3.1, §3.2, §4):
+// every pass of every iteration of Eq. 3 / Eq. 4 runs on tiles of z held in shared memory, so z
+// never leaves the SMs between passes; only the distances, t and c are streamed (from L2).
+//
+// One CTA per SM (cooperative launch, 1024 threads) owns a tile of TH rows x 512 columns.  A
+// directional pass is the causal sweep followed by the anti-causal one along every line, with
+// w_n = a_i^d_n.  A tile segment of a line is summarised by the five numbers (A, B, al, be, ga)
+// of its causal map c_out = A c + B and its anti-causal start k = al k_in + be c + ga, which
+// compose associatively (dts_scan.cuh).  Each pass therefore runs in three steps:
+//   1. every CTA reduces its segments of each line to their five numbers and publishes them,
+//   2. a grid-wide barrier,
+//   3. every CTA composes the segments before and after its own on each line (the carries in
+//      both directions) and replays its positions once each way.
+// Rows: a warp takes one tile row (lane l holds positions 16 l .. 16 l + 15), lanes exchange by
+// shuffles and the tiles of a row are composed by one shuffle scan over lanes = tiles.  Columns:
+// two threads per column split the tile's rows; one composes the tiles above, the other the
+// tiles below.  The data-term update is applied in the last vertical pass of each iteration.
+//
+// Shared-memory layout of a tile row: 128 float4 slots, slot q stored at q ^ ((q >> 3) & 3), so
+// that the four 16-byte accesses of the 32 lanes of a warp (lane stride 64 bytes) and the
+// column accesses (32 consecutive columns) both hit 32 distinct banks.
+#include <algorithm>
+
+#include "dts_scan.cuh"
+
+namespace dts {
+
+namespace {
+
+using namespace scan;
+
+constexpr int kResThreads = 1024;
+constexpr int kResTileW = 512;              // columns of a tile: 32 lanes x 16 positions
+constexpr int kResItems = kResTileW / 32;   // positions of a lane in a row
+constexpr int kResMaxTilesX = 16;           // tiles across a row (rows up to 8192)
+constexpr long long kResMinPixels = 1 << 20;
+
+template <typename T>
+__device__ __forceinline__ T shfl_idx_t(const T& v, int src) {
+    constexpr int n = sizeof(T) / 4;
+    T r;
+    const float* sv = reinterpret_cast<const float*>(&v);
+    float* d = reinterpret_cast<float*>(&r);
+#pragma unroll
+    for (int i = 0; i < n; ++i) d[i] = __shfl_sync(kFull, sv[i], src);
+    return r;
+}
+
+struct ResMode {
+    using Pre = Aff;
+    using Suf = Coupled;
+    static __device__ __forceinline__ Pre pre_identity() { return aff_identity(); }
+    static __device__ __forceinline__ Pre pre_compose(const Pre& f, const Pre& s) { return aff_compose(f, s); }
+    static __device__ __forceinline__ Suf suf_identity() { return coupled_identity(); }
+    static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) { return coupled_compose(f, s); }
+};
+
+struct ResArgs {
+    float* zbuf;            // z_k (pitch `pitch`): z_0 on entry, z_{k+1} written by each update
+    const float* dX;
+    const float* dY;
+    long long pitch;
+    const void* t;          // dense, pitch W
+    int t_dtype;
+    const float* c;         // dense, pitch W
+    float* zout;            // z_K (dense, pitch W)
+    int H, W, K, N;
+    float k2[kMaxPasses];   // log2(a_i) per pass
+    float lambda, step, eps;
+    int update;
+    int ntx, nty, TH;
+    float* ragg;            // [2][5][H][ntx]      row segment tuples, by pass parity
+    float* cagg;            // [2][5][nty][ntx*512] column segment tuples, by pass parity
+    unsigned* bar;          // [0] arrivals, [1] generation, [2] abort (zero at launch)
+    int* status;
+    long long timeout;
+};
+
+__device__ __forceinline__ int swz(int col) {
+    const int q = col >> 2;
+    return ((q ^ ((q >> 3) & 3)) << 2) | (col & 3);
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier over the co-resident CTAs of the cooperative launch.  The last CTA to arrive
+// resets the count and advances the generation.  A wait that runs out records DTS_ERR_TIMEOUT and
+// raises the abort word, after which no CTA waits again (the results are then invalid, the
+// kernel still ends).
+__device__ __forceinline__ void grid_barrier(const ResArgs& a, unsigned& gen) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned arrived = atomicAdd(&a.bar[0], 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&a.bar[0], 0u);
+            __threadfence();
+            atomicExch(&a.bar[1], gen + 1u);
+        } else if (ld_acquire(&a.bar[2]) == 0u) {
+            const long long t0 = clock64();
+            while (ld_acquire(&a.bar[1]) == gen) {
+                if (ld_acquire(&a.bar[2]) != 0u) break;
+                if (clock64() - t0 > a.timeout) {
+                    atomicExch(&a.bar[2], 1u);
+                    atomicExch(a.status, DTS_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        gen += 1u;
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ Coupled ld_tuple(const float* base, long long plane, long long i) {
+    return Coupled{__ldcg(base + i), __ldcg(base + plane + i), __ldcg(base + 2 * plane + i),
+                   __ldcg(base + 3 * plane + i), __ldcg(base + 4 * plane + i)};
+}
+__device__ __forceinline__ void st_tuple(float* base, long long plane, long long i, const Coupled& v) {
+    __stcg(base + i, v.A);
+    __stcg(base + plane + i, v.B);
+    __stcg(base + 2 * plane + i, v.al);
+    __stcg(base + 3 * plane + i, v.be);
+    __stcg(base + 4 * plane + i, v.ga);
+}
+
+// A lane's 16 positions of tile row r: values from shared memory, weights from dX (0 outside
+// the plane and at x = 0), and wn, the weight entering the next lane's first position.
+__device__ __forceinline__ void row_load(const ResArgs& a, const float* tile, int r, int y, int x0, int lane, float k2,
+                                         float (&x)[kResItems], float (&w)[kResItems], float& wn) {
+    const float* trow = tile + (size_t)r * kResTileW;
+#pragma unroll
+    for (int j = 0; j < kResItems / 4; ++j) {
+        const float4 v = *reinterpret_cast<const float4*>(trow + ((4 * lane + (j ^ ((lane >> 1) & 3))) << 2));
+        x[4 * j] = v.x;
+        x[4 * j + 1] = v.y;
+        x[4 * j + 2] = v.z;
+        x[4 * j + 3] = v.w;
+    }
+    const int xl = x0 + kResItems * lane;
+    const float* drow = a.dX + (long long)y * a.pitch;
+    if (xl + kResItems <= a.W) {
+#pragma unroll
+        for (int j = 0; j < kResItems / 4; ++j) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(drow + xl) + j);
+            w[4 * j] = v.x;
+            w[4 * j + 1] = v.y;
+            w[4 * j + 2] = v.z;
+            w[4 * j + 3] = v.w;
+        }
+#pragma unroll
+        for (int j = 0; j < kResItems; ++j) w[j] = ex2(k2 * w[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kResItems; ++j) w[j] = xl + j < a.W ? ex2(k2 * __ldg(drow + xl + j)) : 0.f;
+    }
+    if (xl == 0) w[0] = 0.f;
+    wn = __shfl_down_sync(kFull, w[0], 1);
+    if (lane == 31) wn = x0 + kResTileW < a.W ? ex2(k2 * __ldg(drow + x0 + kResTileW)) : 0.f;
+}
+
+// weight of the vertical step into row y at column x (0 outside the plane and at y = 0)
+__device__ __forceinline__ float col_w(const ResArgs& a, int y, int x, float k2) {
+    return (y > 0 && y < a.H && x < a.W) ? ex2(k2 * __ldg(a.dY + (long long)y * a.pitch + x)) : 0.f;
+}
+
+__global__ void __launch_bounds__(kResThreads, 1) resident_solve_kernel(ResArgs a) {
+    extern __shared__ __align__(16) float res_smem[];
+    float* tile = res_smem;                                  // TH x 512 (swizzled rows)
+    float* ctup = tile + (size_t)a.TH * kResTileW;           // [2 chunks][5][512] column chunk tuples
+    float* cpre = ctup + 2 * 5 * kResTileW;                  // [2][512] tiles above (causal map)
+    float* csuf = cpre + 2 * kResTileW;                      // [5][512] tiles below
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
+    const int x0 = tx * kResTileW, y0 = ty * a.TH;
+    const int rows = min(a.TH, a.H - y0);
+    const long long rplane = (long long)a.H * a.ntx;
+    const long long cw = (long long)a.ntx * kResTileW;
+    const long long cplane = (long long)a.nty * cw;
+    unsigned gen = 0;
+    int par = 0;
+
+    // z_0 into the tile (zero outside the plane)
+    for (int i = tid; i < rows * (kResTileW / 4); i += kResThreads) {
+        const int r = i / (kResTileW / 4), q = i % (kResTileW / 4);
+        const int x = x0 + 4 * q;
+        const float* src = a.zbuf + (long long)(y0 + r) * a.pitch + x;
+        float4 v;
+        if (x + 4 <= a.W) {
+            v = *reinterpret_cast<const float4*>(src);
+        } else {
+            v.x = x < a.W ? src[0] : 0.f;
+            v.y = x + 1 < a.W ? src[1] : 0.f;
+            v.z = x + 2 < a.W ? src[2] : 0.f;
+            v.w = x + 3 < a.W ? src[3] : 0.f;
+        }
+        *reinterpret_cast<float4*>(tile + (size_t)r * kResTileW + ((q ^ ((q >> 3) & 3)) << 2)) = v;
+    }
+    __syncthreads();
+
+    // column split: thread (column cc, chunk s), chunk s covers tile rows [rb, re)
+    const int cc = tid & (kResTileW - 1), s = tid >> 9;
+    const int xcol = x0 + cc;
+    const int ch = (a.TH + 1) / 2;
+    const int rb = min(s * ch, rows), re = min(rb + ch, rows);
+
+    for (int k = 0; k < a.K; ++k) {
+        for (int i = 0; i < a.N; ++i) {
+            const float k2 = a.k2[i];
+            // ------------------------------------------------ horizontal pass
+            for (int r = warp; r < rows; r += kResThreads / 32) {
+                float x[kResItems], w[kResItems], wn;
+                row_load(a, tile, r, y0 + r, x0, lane, k2, x, w, wn);
+                const Coupled own = coupled_local<true>(x, w, wn);
+                const Coupled tot = warp_scan_suf<ResMode>(own, lane);
+                if (lane == 0)
+                    st_tuple(a.ragg + par * 5 * rplane, rplane, (long long)(y0 + r) * a.ntx + tx, tot);
+            }
+            grid_barrier(a, gen);
+            for (int r = warp; r < rows; r += kResThreads / 32) {
+                const int y = y0 + r;
+                float x[kResItems], w[kResItems], wn;
+                row_load(a, tile, r, y, x0, lane, k2, x, w, wn);
+                const Coupled own = coupled_local<true>(x, w, wn);
+                const Aff pin = warp_scan_pre<ResMode>(Aff{own.A, own.B}, lane);
+                const Coupled sin = warp_scan_suf<ResMode>(own, lane);
+                Aff pre = shfl_up_t(pin, 1);
+                Coupled suf = shfl_down_t(sin, 1);
+                if (lane == 0) pre = aff_identity();
+                if (lane == 31) suf = coupled_identity();
+                // the other tiles of the row: lane j holds tile j's tuple
+                Coupled tj = coupled_identity();
+                if (lane < a.ntx && lane != tx)
+                    tj = ld_tuple(a.ragg + par * 5 * rplane, rplane, (long long)y * a.ntx + lane);
+                const Aff tpin = warp_scan_pre<ResMode>(Aff{tj.A, tj.B}, lane);
+                const Coupled tsin = warp_scan_suf<ResMode>(tj, lane);
+                // exclusive at tile tx: tiles left of it, tiles right of it (own tuple is identity)
+                const Aff tpre = shfl_idx_t(tpin, tx);
+                const Coupled tsuf = shfl_idx_t(tsin, tx);
+                pre = aff_compose(tpre, pre);
+                suf = coupled_compose(suf, tsuf);
+                const float c0 = pre.B;
+                float J = c0;
+#pragma unroll
+                for (int j = 0; j < kResItems; ++j) {
+                    J = fmaf(w[j], J - x[j], x[j]);
+                    x[j] = J;
+                }
+                float K = k_entering(suf, fmaf(own.A, c0, own.B));
+#pragma unroll
+                for (int j = kResItems - 1; j >= 0; --j) {
+                    const float wp = (j + 1 < kResItems) ? w[j + 1] : wn;
+                    K = fmaf(wp, K - x[j], x[j]);
+                    x[j] = K;
+                }
+                float* trow = tile + (size_t)r * kResTileW;
+#pragma unroll
+                for (int j = 0; j < kResItems / 4; ++j)
+                    *reinterpret_cast<float4*>(trow + ((4 * lane + (j ^ ((lane >> 1) & 3))) << 2)) =
+                        make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+            }
+            par ^= 1;
+            __syncthreads();
+
+            // ------------------------------------------------ vertical pass
+            const int sc = swz(cc);
+            const float wn_chunk = col_w(a, y0 + re, xcol, k2);
+            {
+                Coupled own = coupled_identity();
+                if (rb < re) {
+                    float P = 1.f, Q = 0.f, rr = 1.f, be = 0.f, ga = 0.f;
+                    float wc = col_w(a, y0 + rb, xcol, k2);
+#pragma unroll 4
+                    for (int r = rb; r < re; ++r) {
+                        const float wnext = r + 1 < re ? col_w(a, y0 + r + 1, xcol, k2) : wn_chunk;
+                        const float xv = tile[(size_t)r * kResTileW + sc];
+                        P *= wc;
+                        Q = fmaf(wc, Q - xv, xv);
+                        const float coef = fmaf(-rr, wnext, rr);
+                        be = fmaf(coef, P, be);
+                        ga = fmaf(coef, Q, ga);
+                        rr *= wnext;
+                        wc = wnext;
+                    }
+                    own = Coupled{P, Q, rr, be, ga};
+                }
+                float* ct = ctup + s * 5 * kResTileW + cc;
+                ct[0] = own.A;
+                ct[kResTileW] = own.B;
+                ct[2 * kResTileW] = own.al;
+                ct[3 * kResTileW] = own.be;
+                ct[4 * kResTileW] = own.ga;
+            }
+            __syncthreads();
+            if (s == 0) {
+                const float* c0p = ctup + cc;
+                const float* c1p = ctup + 5 * kResTileW + cc;
+                const Coupled f{c0p[0], c0p[kResTileW], c0p[2 * kResTileW], c0p[3 * kResTileW], c0p[4 * kResTileW]};
+                const Coupled g{c1p[0], c1p[kResTileW], c1p[2 * kResTileW], c1p[3 * kResTileW], c1p[4 * kResTileW]};
+                st_tuple(a.cagg + par * 5 * cplane, cplane, (long long)ty * cw + xcol, coupled_compose(f, g));
+            }
+            grid_barrier(a, gen);
+            {
+                const float* base = a.cagg + par * 5 * cplane;
+                if (s == 0) {  // tiles above: composition of their causal maps, top first
+                    Aff acc = aff_identity();
+                    int q = 0;
+                    for (; q + 4 <= ty; q += 4) {
+                        Aff t4[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const long long idx = (long long)(q + u) * cw + xcol;
+                            t4[u] = Aff{__ldcg(base + idx), __ldcg(base + cplane + idx)};
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) acc = aff_compose(acc, t4[u]);
+                    }
+                    for (; q < ty; ++q) {
+                        const long long idx = (long long)q * cw + xcol;
+                        acc = aff_compose(acc, Aff{__ldcg(base + idx), __ldcg(base + cplane + idx)});
+                    }
+                    cpre[cc] = acc.A;
+                    cpre[kResTileW + cc] = acc.B;
+                } else {  // tiles below: composition of their tuples, nearest first
+                    Coupled acc = coupled_identity();
+                    int q = a.nty - 1;
+                    for (; q - 3 > ty; q -= 4) {
+                        Coupled t4[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) t4[u] = ld_tuple(base, cplane, (long long)(q - u) * cw + xcol);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) acc = coupled_compose(t4[u], acc);
+                    }
+                    for (; q > ty; --q) acc = coupled_compose(ld_tuple(base, cplane, (long long)q * cw + xcol), acc);
+                    csuf[cc] = acc.A;
+                    csuf[kResTileW + cc] = acc.B;
+                    csuf[2 * kResTileW + cc] = acc.al;
+                    csuf[3 * kResTileW + cc] = acc.be;
+                    csuf[4 * kResTileW + cc] = acc.ga;
+                }
+            }
+            __syncthreads();
+            if (rb < re) {
+                const float* op = ctup + s * 5 * kResTileW + cc;
+                const Coupled own{op[0], op[kResTileW], op[2 * kResTileW], op[3 * kResTileW], op[4 * kResTileW]};
+                Aff pre{cpre[cc], cpre[kResTileW + cc]};
+                Coupled suf{csuf[cc], csuf[kResTileW + cc], csuf[2 * kResTileW + cc], csuf[3 * kResTileW + cc],
+                            csuf[4 * kResTileW + cc]};
+                if (s == 1) {
+                    pre = aff_compose(pre, Aff{ctup[cc], ctup[kResTileW + cc]});
+                } else {
+                    const float* p1 = ctup + 5 * kResTileW + cc;
+                    suf = coupled_compose(Coupled{p1[0], p1[kResTileW], p1[2 * kResTileW], p1[3 * kResTileW],
+                                                  p1[4 * kResTileW]},
+                                          suf);
+                }
+                const float c0 = pre.B;
+                float J = c0;
+#pragma unroll 4
+                for (int r = rb; r < re; ++r) {
+                    const float wv = col_w(a, y0 + r, xcol, k2);
+                    const float xv = tile[(size_t)r * kResTileW + sc];
+                    J = fmaf(wv, J - xv, xv);
+                    tile[(size_t)r * kResTileW + sc] = J;
+                }
+                float Kv = k_entering(suf, fmaf(own.A, c0, own.B));
+                const bool upd = i + 1 == a.N && xcol < a.W;
+                const bool last = k + 1 == a.K;
+                float wp = wn_chunk;
+#pragma unroll 4
+                for (int r = re - 1; r >= rb; --r) {
+                    const int y = y0 + r;
+                    const float Jv = tile[(size_t)r * kResTileW + sc];
+                    Kv = fmaf(wp, Kv - Jv, Jv);
+                    float zn = Kv;
+                    if (upd) {
+                        const long long zi = (long long)y * a.pitch + xcol;
+                        const long long di = (long long)y * a.W + xcol;
+                        zn = dts_update_value(a.zbuf[zi], Kv, load_any(a.t, di, a.t_dtype), __ldg(a.c + di), a.lambda,
+                                              a.step, a.update, 0, a.eps);
+                        if (last) a.zout[di] = zn;
+                        else a.zbuf[zi] = zn;
+                    }
+                    tile[(size_t)r * kResTileW + sc] = zn;
+                    wp = col_w(a, y, xcol, k2);
+                }
+            }
+            par ^= 1;
+            __syncthreads();
+        }
+    }
+}
+
+int res_sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+}  // namespace
+
+bool plan_resident(int H, int W, const dts_params* p, ResidentPlan* rp) {
+    // opt-in (DTS_RESIDENT=1, read on every call): measured slower than the per-pass kernels on
+    // the 2880 x 1988 stereo workload (3.7 against 2.2 ms per 20-iteration solve), its column
+    // passes being latency-bound on scalar distance loads
+    const char* on = getenv("DTS_RESIDENT");
+    if (!on || on[0] != '1' || (long long)H * W < kResMinPixels) return false;
+    if (p->filter_kernel != DTS_KERNEL_RF || p->conf_mode != DTS_CONF_PLAIN || p->dist_dtype != DTS_F32 ||
+        p->save_checkpoints || p->passes < 1 || p->passes > kMaxPasses ||
+        (p->update != DTS_UPDATE_GD && p->update != DTS_UPDATE_JACOBI))
+        return false;
+    const int nsm = res_sm_count();
+    if (nsm < 1) return false;
+    const int ntx = (W + kResTileW - 1) / kResTileW;
+    if (ntx > kResMaxTilesX || ntx > nsm) return false;
+    int nty = nsm / ntx;
+    const int TH = (H + nty - 1) / nty;
+    nty = (H + TH - 1) / TH;
+    const size_t smem = ((size_t)TH * kResTileW + (2 * 5 + 2 + 5) * kResTileW) * sizeof(float);
+    // a device property, not an occupancy query, so that the plan (and with it the workspace
+    // size) does not depend on whether the kernel's shared-memory limit has been raised yet;
+    // 1024 threads at the kernel's 64 registers fill one SM's register file
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return false;
+    if (smem + 1024 > (size_t)optin) return false;
+    rp->ntx = ntx;
+    rp->nty = nty;
+    rp->TH = TH;
+    rp->smem = smem;
+    rp->ragg_floats = 2LL * 5 * H * ntx;
+    rp->cagg_floats = 2LL * 5 * nty * ntx * kResTileW;
+    return true;
+}
+
+cudaError_t prepare_resident_kernel() {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)resident_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+cudaError_t launch_resident(const ResidentLaunch& l, cudaStream_t s) {
+    const ResidentPlan& rp = l.plan;
+    ResArgs a = {};
+    a.zbuf = l.zbuf;
+    a.dX = l.dX;
+    a.dY = l.dY;
+    a.pitch = l.pitch;
+    a.t = l.t;
+    a.t_dtype = l.t_dtype;
+    a.c = l.c;
+    a.zout = l.zout;
+    a.H = l.H;
+    a.W = l.W;
+    a.K = l.K;
+    a.N = l.N;
+    for (int i = 0; i < l.N && i < kMaxPasses; ++i) a.k2[i] = l.k2[i];
+    a.lambda = l.lambda;
+    a.step = l.step;
+    a.eps = l.eps;
+    a.update = l.update;
+    a.ntx = rp.ntx;
+    a.nty = rp.nty;
+    a.TH = rp.TH;
+    a.ragg = l.ragg;
+    a.cagg = l.cagg;
+    a.bar = l.bar;
+    a.status = l.status;
+    a.timeout = 2000000000LL;  // ~1 s at the boost clock
+    cudaError_t e = cudaMemsetAsync(l.bar, 0, 4 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const int h = prof_begin(KID_RESIDENT, (long long)l.H * l.W * l.K, 0, s);
+    void* args[] = {&a};
+    e = cudaLaunchCooperativeKernel((const void*)resident_solve_kernel, dim3((unsigned)(rp.ntx * rp.nty)),
+                                    dim3(kResThreads), args, rp.smem, s);
+    prof_end(h, s);
+    return e;
+}
+
+}  // namespace dts
