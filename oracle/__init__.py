@@ -28,7 +28,9 @@ _dp = ctypes.POINTER(ctypes.c_double)
 def _load():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # DTS_ORACLE_SO: a separately compiled copy of this oracle (the mutation test builds copies
+        # with planted mistakes and runs the pins against them)
+        path = os.environ.get("DTS_ORACLE_SO") or _build.build()
         lib = ctypes.CDLL(path)
         i, d, p = ctypes.c_int, ctypes.c_double, _dp
         lib.orc_schedule.argtypes = [d, i, p, p]
