@@ -88,6 +88,8 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3):
         # the first transposed vertical pass of a product also reads the minuend plane
         "col_pass_kernel<transpose>": 8 + s_d + 4.0 / N,
         "col_strip_kernel<transpose>": 8 + s_d + 4.0 / N,
+        "square_plane_kernel": 8,
+        "confidence_kernel": 12,
         "box_line_kernel": 12,
         "transpose_kernel": 8,
         "cg_apply_kernel": 20,
@@ -200,13 +202,20 @@ BACKWARD_KERNELS = ("row_bwd_kernel", "col_bwd_kernel", "update_adjoint_kernel",
                     "axpy_plane_kernel")
 
 
+def kernel_source(kernel):
+    """Path of the library source file that holds `kernel` (a name the per-launch timer reports)."""
+    fn = ("dts_backward.cu" if kernel.startswith(BACKWARD_KERNELS) else "dts_cg.cu" if kernel.startswith("cg_")
+          else "dts_box.cu" if kernel.startswith(("box_", "transpose_"))
+          else "dts_resident.cu" if kernel.startswith("resident_")
+          else "dts_confidence.cu" if kernel.startswith(("square_plane_", "confidence_"))
+          else "dts_vertical.cu" if kernel.startswith("col_agg_") else "dts_forward.cu")
+    return os.path.join(ROOT, "paper_1805_04590_gb300", "csrc", fn)
+
+
 def traffic_for(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, when that
     summary was taken on the current source of the file that holds the kernel (else None)."""
-    fn = ("dts_backward.cu" if kernel.startswith(BACKWARD_KERNELS) else "dts_cg.cu" if kernel.startswith("cg_")
-          else "dts_box.cu" if kernel.startswith(("box_", "transpose_"))
-          else "dts_resident.cu" if kernel.startswith("resident_") else "dts_forward.cu")
-    src = os.path.join(ROOT, "paper_1805_04590_gb300", "csrc", fn)
+    src = kernel_source(kernel)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):

@@ -28,3 +28,30 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_every_timed_kernel_has_algorithmic_bytes():
+    """Every kernel name the library's per-launch timer reports has algorithmic bytes per pixel in
+    the bench (else that kernel would drop out of the bench line's roofline), and the library
+    source file the traffic lookup maps it to exists."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+    from paper_1805_04590_gb300 import dts
+
+    lib = dts.load()
+    names = []
+    for k in range(256):
+        n = lib.dts_kernel_name(k).decode()
+        if n == "unknown":
+            break
+        names.append(n)
+    assert len(names) > 20
+    for n in names:
+        for s_d, s_t in ((4, 4), (2, 2)):
+            b = bench.bytes_per_pixel(n, s_d, s_t)
+            assert b is not None and b > 0, n
+        src = bench.kernel_source(n)
+        assert os.path.exists(src), n
+        stem = n.split("<")[0]
+        assert stem in open(src).read(), f"{n} not defined in {os.path.basename(src)}"
