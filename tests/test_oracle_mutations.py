@@ -1,6 +1,6 @@
 """The pins catch plausible mistakes in the oracle (CPU).
 
-Each case below plants one mistake in a copy of oracle/dts_oracle.c — a dropped term, a wrong
+Each of the 50 cases below plants one mistake in a copy of oracle/dts_oracle.c — a dropped term, a wrong
 sign, index or operand, passes in the wrong order — compiles the copy with the oracle's own
 flags, and runs the pin suite (tests/test_oracle_pins.py) against it in a fresh process
 (DTS_ORACLE_SO points the oracle package at the copy).  Every mutant must fail at least one pin;
@@ -70,6 +70,28 @@ MUTANTS = [
      "tb[p] += eta * d2 * g[p];"),
     ("backward: the z_0 = t path dropped", "for (long p = 0; p < n; ++p) tb[p] += g[p];", ";"),
     ("CG: initial residual without the factor 2", "r[i] = 2.0 * c[i] * t[i] - q[i];", "r[i] = c[i] * t[i] - q[i];"),
+    ("causal sweep: first step skipped", "for (int j = 1; j < n; ++j) {\n        double w = pow(a, d[j * sd]);",
+     "for (int j = 2; j < n; ++j) {\n        double w = pow(a, d[j * sd]);"),
+    ("anti-causal sweep: last step skipped",
+     "for (int j = n - 2; j >= 0; --j) {\n        double w = pow(a, d[(j + 1) * sd]);",
+     "for (int j = n - 3; j >= 0; --j) {\n        double w = pow(a, d[(j + 1) * sd]);"),
+    ("support weighting: step limit inverted", "1.0 / (lambda + chat[p]) < e) e =", "1.0 / (lambda + chat[p]) > e) e ="),
+    ("box kernel: average over one sample too many", "tmp[i] = sum / cnt;", "tmp[i] = sum / (cnt + 1);"),
+    ("distances: dY without the absolute value",
+     "double diff = I[c * plane + p] - I[c * plane + p - W];\n                    s += (norm == ORC_NORM_L2) ? diff * diff : fabs(diff);",
+     "double diff = I[c * plane + p] - I[c * plane + p - W];\n                    s += (norm == ORC_NORM_L2) ? diff * diff : diff;"),
+    ("box kernel: columns on dX", "box_line(H, dst + x, W, dY + x, W, r, ct, tmp);",
+     "box_line(H, dst + x, W, dX + x, W, r, ct, tmp);"),
+    ("adjoint: first input gradient dropped", "gin[0] = gJ[0];", "gin[0] = 0.0;"),
+    ("backward, fixed point: lambda for c in the target gradient", "tb[p] += c[p] / den * g[p];",
+     "tb[p] += lambda / den * g[p];"),
+    ("backward, Charbonnier: curvature", "eps * eps / (s * s * s)", "eps / (s * s)"),
+    ("CG: alpha inverted", "const double alpha = rr / pq;", "const double alpha = pq / rr;"),
+    ("CG: residual updated with p", "r[i] -= alpha * q[i];", "r[i] -= alpha * p[i];"),
+    ("support: distance ignored", "P[j] = x[j * sx] + pow(a, d[j * sd]) * P[j - 1];", "P[j] = x[j * sx] + a * P[j - 1];"),
+    ("guide gradient, dY: wrong neighbour", "Gc[p - W] -= g;", "Gc[p - 1] -= g;"),
+    ("schedule: the -1 of 4^N - 1 dropped", "sqrt(pow(4.0, (double)N) - 1.0)", "sqrt(pow(4.0, (double)N))"),
+    ("adjoint: carried gradient weighted by w_j", "gJ[j] = h[j] + w[j + 1] * gJ[j + 1];", "gJ[j] = h[j] + w[j] * gJ[j + 1];"),
 ]
 
 

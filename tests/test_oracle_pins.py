@@ -355,6 +355,28 @@ def test_support_mode_equals_plain_on_scaled_confidence():
     np.testing.assert_allclose(z_s, z_p, atol=1e-14)
 
 
+def test_support_gradient_step_is_limited_per_pixel():
+    """Reading of the support weighting for the gradient step: where the weighted confidence chat
+    is large the step at pixel i is min(eta, 1 / (lambda + chat_i)).  One step from z0 against
+    that update written out, on a case where the limit holds at some pixels and not at others."""
+    rng = np.random.default_rng(23)
+    H, W, sigma_s, sigma_r = 9, 11, 6.0, 0.3
+    I = rand_guide(rng, 3, H, W)
+    t, z0 = rng.random((H, W)), rng.random((H, W))
+    c = 10.0 ** rng.uniform(-3.0, 0.3, (H, W))
+    lam, eta = 0.5, 0.99
+    dX, dY = oracle.distances(I, sigma_s, sigma_r)
+    S, sf = oracle.support(dX, dY, sigma_s)
+    chat = c * sf / S
+    _, a = oracle.schedule(sigma_s, 3)
+    e = np.minimum(eta, 1.0 / (lam + chat))
+    assert (e < eta).any() and (e == eta).any()
+    want = z0 - e * (lam * (z0 - oracle.filter_d(dX, dY, a, z0)) + chat * (z0 - t))
+    got = oracle.solve(I, t, c, lam=lam, sigma_s=sigma_s, sigma_r=sigma_r, step=eta, iterations=1,
+                       update=oracle.UPDATE_GD, conf_mode=oracle.CONF_SUPPORT, z_init=z0)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+
+
 # ---------------------------------------------------------------- reverse mode
 def test_filter_adjoint_dot_product_and_dense_transpose():
     rng = np.random.default_rng(17)
