@@ -1,6 +1,6 @@
 """The pins catch plausible mistakes in the oracle (CPU).
 
-Each of the 50 cases below plants one mistake in a copy of oracle/dts_oracle.c — a dropped term, a wrong
+Each of the 65 cases below plants one mistake in a copy of oracle/dts_oracle.c — a dropped term, a wrong
 sign, index or operand, passes in the wrong order — compiles the copy with the oracle's own
 flags, and runs the pin suite (tests/test_oracle_pins.py) against it in a fresh process
 (DTS_ORACLE_SO points the oracle package at the copy).  Every mutant must fail at least one pin;
@@ -92,6 +92,30 @@ MUTANTS = [
     ("guide gradient, dY: wrong neighbour", "Gc[p - W] -= g;", "Gc[p - 1] -= g;"),
     ("schedule: the -1 of 4^N - 1 dropped", "sqrt(pow(4.0, (double)N) - 1.0)", "sqrt(pow(4.0, (double)N))"),
     ("adjoint: carried gradient weighted by w_j", "gJ[j] = h[j] + w[j + 1] * gJ[j + 1];", "gJ[j] = h[j] + w[j] * gJ[j + 1];"),
+    ("adjoint: anti-causal gradient carried with w_{j-1}", "h[j] = gout[j * sg] + w[j] * h[j - 1];",
+     "h[j] = gout[j * sg] + w[j - 1] * h[j - 1];"),
+    ("fixed point: lambda + c = 0 gives 0", "/ den : zk[p];", "/ den : 0.0;"),
+    ("backward, fixed point: lambda + c = 0 stops the gradient", "gprev[p] = g[p];", "gprev[p] = 0.0;"),
+    ("gradient step: step size ignored", "double e = eta;", "double e = 1.0;"),
+    ("distances: sigma_r / sigma_s",
+     "double k = sigma_s / sigma_r;\n    long plane = (long)H * W;\n#pragma omp parallel for",
+     "double k = sigma_r / sigma_s;\n    long plane = (long)H * W;\n#pragma omp parallel for"),
+    ("distances: L2 without the square root", "dX[p] = (norm == ORC_NORM_L2) ? sqrt(1.0 + k * k * s)",
+     "dX[p] = (norm == ORC_NORM_L2) ? (1.0 + k * k * s)"),
+    ("checkpoints in reverse order", "if (ckpt) memcpy(ckpt + (long)k * n, z,", "if (ckpt) memcpy(ckpt + (long)(K - 1 - k) * n, z,"),
+    ("CG: one step fewer", "for (int k = 0; k < K && rr > 0.0; ++k)", "for (int k = 1; k < K && rr > 0.0; ++k)"),
+    ("CG: z_init ignored", "memcpy(z, z0 ? z0 : t, sizeof(double) * (size_t)n);\n    cg_apply_M",
+     "memcpy(z, t, sizeof(double) * (size_t)n);\n    cg_apply_M"),
+    ("filter adjoint: pass inputs recomputed in the wrong direction",
+     "if (p % 2 == 0)\n            orc_row_pass(H, W, U + (long)(p + 1) * n, dX, a[p / 2]);",
+     "if (p % 2 == 1)\n            orc_row_pass(H, W, U + (long)(p + 1) * n, dX, a[p / 2]);"),
+    ("gradient step: z_bar halved", "lambda * (zk[p] - zbar[p]) + chat[p]", "lambda * (zk[p] - zbar[p] * 0.5) + chat[p]"),
+    ("backward, gradient step: lambda dropped from the smoothness gradient", "gbar[p] = eta * lambda * g[p];",
+     "gbar[p] = eta * g[p];"),
+    ("backward: z_bar not recomputed", "orc_filter(H, W, dX, dY, N, a, zk, zbar);\n        for (long p = 0; p < n; ++p) {",
+     "memcpy(zbar, zk, sizeof(double) * (size_t)n);\n        for (long p = 0; p < n; ++p) {"),
+    ("guide gradient, L1: k dropped", ": dXbar[p] * k * ((diff > 0) - (diff < 0));", ": dXbar[p] * ((diff > 0) - (diff < 0));"),
+    ("Eq. 7: variance squared", "c[i] = exp(-v / (2.0 * sigma_c * sigma_c));", "c[i] = exp(-v * v / (2.0 * sigma_c * sigma_c));"),
 ]
 
 

@@ -630,6 +630,57 @@ def test_cg_reaches_the_minimiser_of_eq2():
     assert all(vals[i + 1] <= vals[i] + 1e-12 for i in range(7))
 
 
+def test_cg_iterates_minimise_over_the_krylov_space():
+    """K steps of CG from z_init give the minimiser of 1/2 z^T M z - b^T z over z_init plus the Krylov
+    space span{r0, M r0, ..., M^(K-1) r0}, r0 = b - M z_init (M = lambda (I - A)^T (I - A) + 2C, dense
+    from unit vectors; b = 2Ct): pins the number of steps and the starting point, which
+    convergence alone does not."""
+    rng = np.random.default_rng(83)
+    H, W = 4, 5
+    I = rand_guide(rng, 3, H, W)
+    dX, dY = oracle.distances(I, 5.0, 0.4)
+    _, a = oracle.schedule(5.0, 3)
+    A = dense_filter_matrix(dX, dY, a)
+    t, z0 = rng.normal(size=(H, W)), rng.normal(size=(H, W))
+    c = rng.uniform(0.1, 1.0, (H, W))
+    lam = 0.8
+    n = H * W
+    B = np.eye(n) - A
+    M = lam * B.T @ B + 2 * np.diag(c.ravel())
+    b = 2 * c.ravel() * t.ravel()
+    r0 = b - M @ z0.ravel()
+    for K in (0, 1, 2, 4):
+        want = z0.ravel().copy()
+        if K:
+            V, _ = np.linalg.qr(np.stack([np.linalg.matrix_power(M, j) @ r0 for j in range(K)], axis=1))
+            want = want + V @ np.linalg.solve(V.T @ M @ V, V.T @ r0)
+        got = oracle.solve_cg_d(dX, dY, t, c, lam=lam, sigma_s=5.0, iterations=K, z_init=z0).ravel()
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-9 * max(1.0, np.abs(want).max()))
+        if K:
+            assert np.abs(got - z0.ravel()).max() > 1e-3  # each case moves away from z_init
+
+
+def test_fixed_point_keeps_pixels_without_data_or_smoothness():
+    """Reading of Eq. 4 where lambda + c = 0: the fixed-point update leaves such a pixel at z_k.  With
+    lambda = 0 every pixel with c > 0 takes t and every pixel with c = 0 keeps z_init, after any
+    number of iterations; in reverse mode the gradient of a c = 0 pixel passes straight to z_init
+    and that of a c > 0 pixel to t."""
+    rng = np.random.default_rng(24)
+    H, W = 6, 7
+    I = rand_guide(rng, 3, H, W)
+    t, z0 = rng.random((H, W)), rng.random((H, W))
+    c = rng.uniform(0.2, 1.0, (H, W))
+    c[rng.random((H, W)) < 0.4] = 0.0
+    assert (c == 0).any() and (c > 0).any()
+    kw = dict(lam=0.0, sigma_s=6.0, sigma_r=0.3, iterations=3, update=oracle.UPDATE_JACOBI)
+    z = oracle.solve(I, t, c, z_init=z0, **kw)
+    np.testing.assert_allclose(z, np.where(c > 0, t, z0), rtol=0, atol=1e-15)
+    gz = rng.normal(size=(H, W))
+    g = oracle.solve_backward(I, t, c, gz, z_init=z0, **kw)
+    np.testing.assert_allclose(g["z_init"], np.where(c == 0, gz, 0.0), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(g["t"], np.where(c > 0, gz, 0.0), rtol=0, atol=1e-14)
+
+
 def test_cg_fixed_point_differs_from_eq4():
     """The minimiser of Eq. 2 is not the fixed point of the paper's update (Eq. 4): the two agree
     only when the target already is edge-aware smooth, e.g. a constant."""
