@@ -1,6 +1,6 @@
 """The pins catch plausible mistakes in the oracle (CPU).
 
-Each of the 65 cases below plants one mistake in a copy of oracle/dts_oracle.c — a dropped term, a wrong
+Each of the 79 cases below plants one mistake in a copy of oracle/dts_oracle.c — a dropped term, a wrong
 sign, index or operand, passes in the wrong order — compiles the copy with the oracle's own
 flags, and runs the pin suite (tests/test_oracle_pins.py) against it in a fresh process
 (DTS_ORACLE_SO points the oracle package at the copy).  Every mutant must fail at least one pin;
@@ -116,6 +116,27 @@ MUTANTS = [
      "memcpy(zbar, zk, sizeof(double) * (size_t)n);\n        for (long p = 0; p < n; ++p) {"),
     ("guide gradient, L1: k dropped", ": dXbar[p] * k * ((diff > 0) - (diff < 0));", ": dXbar[p] * ((diff > 0) - (diff < 0));"),
     ("Eq. 7: variance squared", "c[i] = exp(-v / (2.0 * sigma_c * sigma_c));", "c[i] = exp(-v * v / (2.0 * sigma_c * sigma_c));"),
+    ("Eq. 7: the mean of t for the mean of t^2", "orc_filter(H, W, dX, dY, N, a, t2, m2);",
+     "orc_filter(H, W, dX, dY, N, a, t, m2);"),
+    ("Eq. 7: small variances dropped", "if (v < 0.0) v = 0.0;", "if (v < 1e-3) v = 0.0;"),
+    ("support: columns on dX", "support_line(H, s + x, W, S + x, W, dY + x, W, a, P, Q);",
+     "support_line(H, s + x, W, S + x, W, dX + x, W, a, P, Q);"),
+    ("support: anti-causal sum starts at 0", "Q[n - 1] = x[(n - 1) * sx];", "Q[n - 1] = 0.0;"),
+    ("support: causal sum starts at 0", "P[0] = x[0];", "P[0] = 0.0;"),
+    ("box kernel: window without the absolute value", "if (fabs(ct[m] - ct[i]) <= r) {", "if ((ct[m] - ct[i]) <= r) {"),
+    ("Charbonnier: taken for eps = 0 too", "return eps > 0.0 ? r / sqrt(r * r + eps * eps) : r;",
+     "return eps >= 0.0 ? r / sqrt(r * r + eps * eps) : r;"),
+    ("guide gradient, L2, dY: distance not divided out", "? dYbar[p] * k * k * diff / dY[p]", "? dYbar[p] * k * k * diff"),
+    ("backward, Charbonnier: r for rho'(r) in the confidence gradient", "cb[p] -= eta * d1 * g[p];",
+     "cb[p] -= eta * r * g[p];"),
+    ("filter adjoint: first pass skipped", "for (int p = 2 * N - 1; p >= 0; --p) {", "for (int p = 2 * N - 1; p >= 1; --p) {"),
+    ("guide gradient, dY: own pixel sign", "Gc[p] += g;\n                    Gc[p - W] -= g;",
+     "Gc[p] -= g;\n                    Gc[p - W] -= g;"),
+    ("CG: (I - A) p with the wrong sign", "t1[i] = p[i] - t1[i];", "t1[i] = t1[i] - p[i];"),
+    ("backward, gradient step: target gradient sign", "tb[p] += eta * c[p] * d2 * g[p];", "tb[p] -= eta * c[p] * d2 * g[p];"),
+    ("backward, gradient step: smoothness sign in the carry",
+     "gprev[p] = (1.0 - eta * lambda - eta * c[p] * d2) * g[p];",
+     "gprev[p] = (1.0 + eta * lambda - eta * c[p] * d2) * g[p];"),
 ]
 
 
