@@ -1,0 +1,110 @@
+"""The five-number segment algebra under random segmentations and association orders (CPU).
+
+Every pass kernel splits a line into segments, reduces each segment to five numbers (A, B, al,
+be, ga) — its causal map c_out = A c + B and its anti-causal start k = al k_in + be c + ga — and
+composes them: the prefix of a segment from the causal maps of the segments before it, the
+suffix from the five numbers of the segments after it.  The kernels compose in different orders
+(warp shuffles, shared memory, clusters, tiles), so the composition must not depend on the
+order.  This test cuts random lines at random points, composes the prefixes and suffixes along
+random binary trees, replays every segment from its carries, and compares with the oracle's
+sweeps: the normalised pass (causal then anti-causal) and the transposed pass that conjugate
+gradients use (unnormalised causal sweep, normalised anti-causal sweep, then a factor 1 - w per
+position), the latter against the oracle's adjoint of one horizontal pass.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+ID5 = (1.0, 0.0, 1.0, 0.0, 0.0)
+ID2 = (1.0, 0.0)
+
+
+def aff(f, s):
+    return (f[0] * s[0], s[0] * f[1] + s[1])
+
+
+def coupled(f, s):
+    return (f[0] * s[0], s[0] * f[1] + s[1], f[2] * s[2], f[2] * s[3] * f[0] + f[3],
+            f[2] * (s[3] * f[1] + s[4]) + f[4])
+
+
+def fold(items, compose, identity, rng):
+    """Composition of items in order, bracketed along a random binary tree."""
+    if not items:
+        return identity
+    if len(items) == 1:
+        return items[0]
+    k = int(rng.integers(1, len(items)))
+    return compose(fold(items[:k], compose, identity, rng), fold(items[k:], compose, identity, rng))
+
+
+def reduce_segment(x, w, w_next, normalised):
+    P, Q, r, be, ga = 1.0, 0.0, 1.0, 0.0, 0.0
+    for j in range(len(x)):
+        P *= w[j]
+        Q = w[j] * (Q - x[j]) + x[j] if normalised else w[j] * Q + x[j]
+        wp = w[j + 1] if j + 1 < len(x) else w_next
+        coef = r * (1.0 - wp)
+        be += coef * P
+        ga += coef * Q
+        r *= wp
+    return (P, Q, r, be, ga)
+
+
+def replay(x, w, w_next, own, c_in, after, normalised):
+    out = list(x)
+    J = c_in
+    for j in range(len(out)):
+        J = w[j] * (J - out[j]) + out[j] if normalised else w[j] * J + out[j]
+        out[j] = J
+    K = after[3] * (own[0] * c_in + own[1]) + after[4]
+    for j in range(len(out) - 1, -1, -1):
+        wp = w[j + 1] if j + 1 < len(out) else w_next
+        K = wp * (K - out[j]) + out[j]
+        out[j] = K if normalised else (1.0 - w[j]) * K
+    return out
+
+
+def segmented_pass(x, d, a, rng, normalised):
+    n = len(x)
+    w = [a ** d[j] if j > 0 else 0.0 for j in range(n)]
+    cuts = sorted(set(int(v) for v in rng.integers(1, n, size=int(rng.integers(0, min(n, 12))))) if n > 1 else [])
+    bounds = [0] + cuts + [n]
+    segs = []
+    for b, e in zip(bounds[:-1], bounds[1:]):
+        w_next = w[e] if e < n else 0.0
+        segs.append((b, e, w_next, reduce_segment(x[b:e], w[b:e], w_next, normalised)))
+    out = np.empty(n)
+    for s, (b, e, w_next, own) in enumerate(segs):
+        pre = fold([g[3][:2] for g in segs[:s]], aff, ID2, rng)
+        suf = fold([g[3] for g in segs[s + 1:]], coupled, ID5, rng)
+        out[b:e] = replay(x[b:e], w[b:e], w_next, own, pre[1], suf, normalised)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_normalised_pass_is_independent_of_segmentation_and_order(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 160))
+    x = rng.normal(size=n)
+    d = 1.0 + rng.exponential(3.0, n) * (rng.random(n) < 0.5)
+    a = float(rng.uniform(0.3, 0.995))
+    ref = oracle.anticausal(oracle.causal(x, d, a), d, a)
+    for _ in range(4):
+        got = segmented_pass(x, d, a, rng, normalised=True)
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * max(1.0, np.abs(ref).max()))
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_transposed_pass_is_independent_of_segmentation_and_order(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(1, 120))
+    g = rng.normal(size=n)
+    d = 1.0 + rng.exponential(3.0, n) * (rng.random(n) < 0.5)
+    a = float(rng.uniform(0.3, 0.995))
+    dX = d[None, :].copy()
+    ref, _, _ = oracle.filter_adjoint(dX, np.ones((1, n)), np.array([a]), rng.normal(size=(1, n)), g[None, :])
+    for _ in range(4):
+        got = segmented_pass(g, d, a, rng, normalised=False)
+        np.testing.assert_allclose(got, ref[0], rtol=0, atol=1e-13 * max(1.0, np.abs(ref).max()))
