@@ -9,7 +9,9 @@ order.  This test cuts random lines at random points, composes the prefixes and 
 random binary trees, replays every segment from its carries, and compares with the oracle's
 sweeps: the normalised pass (causal then anti-causal) and the transposed pass that conjugate
 gradients use (unnormalised causal sweep, normalised anti-causal sweep, then a factor 1 - w per
-position), the latter against the oracle's adjoint of one horizontal pass.
+position), the latter against the oracle's adjoint of one horizontal pass; and the reverse mode
+of a pass as the backward kernels form it (two causal maps and one five-number transform per
+segment), for the input gradient and the distance gradient.
 """
 import numpy as np
 import pytest
@@ -108,3 +110,64 @@ def test_transposed_pass_is_independent_of_segmentation_and_order(seed):
     for _ in range(4):
         got = segmented_pass(g, d, a, rng, normalised=False)
         np.testing.assert_allclose(got, ref[0], rtol=0, atol=1e-13 * max(1.0, np.abs(ref).max()))
+
+
+def adjoint_segmented(x, G, K, d, a, rng):
+    """Reverse mode of one pass by segments: each segment reduces the causal map of J on the pass
+    input x and the coupled transform of (h, gJ) on G = dL/dK; prefixes (both causal maps) and
+    suffixes (the coupled transforms) are composed along random trees; each segment then replays
+    with its carries and yields dL/dx and ln(a) w dL/dw, the gradient of its distances."""
+    n = len(x)
+    w = [a ** d[j] if j > 0 else 0.0 for j in range(n)]
+    lna = np.log(a)
+    cuts = sorted(set(int(v) for v in rng.integers(1, n, size=int(rng.integers(0, min(n, 12))))) if n > 1 else [])
+    bounds = [0] + cuts + [n]
+    segs = []
+    for b, e in zip(bounds[:-1], bounds[1:]):
+        w_next = w[e] if e < n else 0.0
+        suf = reduce_segment(G[b:e], w[b:e], w_next, normalised=False)
+        q = 0.0
+        for j in range(b, e):
+            q = w[j] * (q - x[j]) + x[j]
+        segs.append((b, e, w_next, (suf[0], q), (suf[0], suf[1]), suf))
+    gx, dd = np.empty(n), np.empty(n)
+    for s, (b, e, w_next, own_jk, own_hg, own) in enumerate(segs):
+        pre_jk = fold([g[3] for g in segs[:s]], aff, ID2, rng)
+        pre_hg = fold([g[4] for g in segs[:s]], aff, ID2, rng)
+        after = fold([g[5] for g in segs[s + 1:]], coupled, ID5, rng)
+        jin, hin = pre_jk[1], pre_hg[1]
+        gin = after[3] * (own_hg[0] * hin + own_hg[1]) + after[4]
+        xs, Gs, Ks = list(x[b:e]), list(G[b:e]), list(K[b:e])
+        Jp, hp = jin, hin
+        for j in range(e - b):  # left to right: J, h and the parts of dL/dw that need J[n-1], h[n-1]
+            J = w[b + j] * (Jp - xs[j]) + xs[j]
+            Ks[j] = hp * (Ks[j] - Jp)
+            xs[j] = Jp - xs[j]
+            hp = w[b + j] * hp + Gs[j]
+            Gs[j] = hp
+            Jp = J
+        g = gin
+        for j in range(e - b - 1, -1, -1):  # right to left: gJ, then both gradients
+            wp = w[b + j + 1] if j + 1 < e - b else w_next
+            g = wp * (g - Gs[j]) + Gs[j]
+            dd[b + j] = lna * w[b + j] * (g * xs[j] + Ks[j])
+            gx[b + j] = (1.0 - w[b + j]) * g
+    return gx, dd
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_pass_adjoint_is_independent_of_segmentation_and_order(seed):
+    """The reverse mode of one horizontal pass (the backward kernels' form: J recomputed from the
+    pass input by its causal map, the pass output K read back) against the oracle's adjoint of a
+    one-row image with one pass, for both the input gradient and the distance gradient."""
+    rng = np.random.default_rng(200 + seed)
+    n = int(rng.integers(2, 120))
+    x, G = rng.normal(size=n), rng.normal(size=n)
+    d = 1.0 + rng.exponential(3.0, n) * (rng.random(n) < 0.5)
+    a = float(rng.uniform(0.3, 0.995))
+    K = oracle.row_pass(x[None, :], d[None, :], a)[0]
+    gsrc, dXb, _ = oracle.filter_adjoint(d[None, :], np.ones((1, n)), np.array([a]), x[None, :], G[None, :])
+    for _ in range(4):
+        gx, dd = adjoint_segmented(x, G, K, d, a, rng)
+        np.testing.assert_allclose(gx, gsrc[0], rtol=0, atol=1e-12 * max(1.0, np.abs(gsrc).max()))
+        np.testing.assert_allclose(dd[1:], dXb[0, 1:], rtol=0, atol=1e-12 * max(1.0, np.abs(dXb).max()))
