@@ -140,7 +140,12 @@ int dts_filter(const dts_guide* guide, const dts_params* params, const float* sr
  *                  or (lambda zbar + c t) / (lambda + c)                           (Jacobi, Eq. 4)
  * target: dense H x W of target_dtype (F32, BF16 or F16); conf: dense H x W FP32
  * (c >= 0); z_out: dense H x W FP32 (may alias z_init, not target/conf).
- * With save_checkpoints = 1 the iterates z_0 .. z_{K-1} stay in the workspace. */
+ * With save_checkpoints = 1 the iterates z_0 .. z_{K-1} stay in the workspace.
+ * With DTS_RESIDENT=1 in the environment (read on every call), a solve of at least 2^20 pixels
+ * with the recursive filter, GD or Jacobi, plain confidence, FP32 distances and no checkpoints
+ * runs its iterations as one cooperative kernel launch holding the iterate in shared memory (one
+ * CTA per SM, so it waits for the whole GPU); dts_workspace_size must then be called with the
+ * same setting.  Off by default. */
 int dts_solve(const dts_guide* guide, const void* target, int target_dtype, const float* conf, const float* z_init,
               const dts_params* params, float* z_out, void* ws, size_t ws_bytes, dts_stream stream);
 
