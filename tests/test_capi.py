@@ -4,6 +4,7 @@ device work (no GPU needed)."""
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -186,3 +187,36 @@ def test_charbonnier_needs_the_gradient_step():
         p = dts.Params(update=upd, charbonnier_eps=1e-3).c()
         assert lib.dts_solve(ctypes.byref(g), 0x2000, 0, 0x3000, None, ctypes.byref(p), 0x4000, 0x5000, 1 << 30,
                              None) == 2
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    """The ctypes mirrors of dts_guide and dts_params in the binding have the C compiler's field
+    offsets and sizes (a mismatch would pass every parameter to the library shifted)."""
+    from paper_1805_04590_gb300 import dts
+
+    fields = {"dts_guide": (dts.CGuide, ["C", "H", "W", "dtype", "data", "ch_stride", "row_stride"]),
+              "dts_params": (dts.CParams, ["lambda", "sigma_s", "sigma_r", "step", "iterations", "passes", "norm",
+                                           "update", "conf_mode", "dist_dtype", "save_checkpoints", "filter_kernel",
+                                           "charbonnier_eps"])}
+    lines = ['#include <stdio.h>', '#include "dts.h"', "int main(void) {"]
+    for st, (_, names) in fields.items():
+        lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
+        for n in names:
+            lines.append(f'printf("{st} {n} %zu %zu\\n", offsetof({st}, {n}), sizeof((({st}*)0)->{n}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    c_layout = {}
+    for line in filter(None, out):
+        parts = line.split()
+        c_layout[(parts[0], parts[1])] = tuple(int(v) for v in parts[2:])
+    for st, (cls, names) in fields.items():
+        assert ctypes.sizeof(cls) == c_layout[(st, "size")][0], st
+        py_names = [f[0] for f in cls._fields_]
+        assert len(py_names) == len(names), st
+        for py, n in zip(py_names, names):
+            f = getattr(cls, py)
+            assert (f.offset, f.size) == c_layout[(st, n)], (st, n)
