@@ -11,7 +11,8 @@ sweeps: the normalised pass (causal then anti-causal) and the transposed pass th
 gradients use (unnormalised causal sweep, normalised anti-causal sweep, then a factor 1 - w per
 position), the latter against the oracle's adjoint of one horizontal pass; and the reverse mode
 of a pass as the backward kernels form it (two causal maps and one five-number transform per
-segment), for the input gradient and the distance gradient.
+segment), for the input gradient and the distance gradient; and the unnormalised support sweeps
+of the support weighting (a causal map and a two-number suffix per segment).
 """
 import numpy as np
 import pytest
@@ -171,3 +172,51 @@ def test_pass_adjoint_is_independent_of_segmentation_and_order(seed):
         gx, dd = adjoint_segmented(x, G, K, d, a, rng)
         np.testing.assert_allclose(gx, gsrc[0], rtol=0, atol=1e-12 * max(1.0, np.abs(gsrc).max()))
         np.testing.assert_allclose(dd[1:], dXb[0, 1:], rtol=0, atol=1e-12 * max(1.0, np.abs(dXb).max()))
+
+
+def support_segmented(x, d, a, rng):
+    """Support sweeps by segments, as the support pass kernels run them: P[n] = x[n] + w_n P[n-1]
+    composes as causal maps (A, B), Q[n] = x[n] + w_{n+1} Q[n+1] as pairs (al, de) with
+    Q_start = al Q_in + de; each segment replays P + Q - x from its two carries."""
+    n = len(x)
+    w = [a ** d[j] if j > 0 else 0.0 for j in range(n)]
+    cuts = sorted(set(int(v) for v in rng.integers(1, n, size=int(rng.integers(0, min(n, 12))))) if n > 1 else [])
+    bounds = [0] + cuts + [n]
+    segs = []
+    for b, e in zip(bounds[:-1], bounds[1:]):
+        A, B, r, de = 1.0, 0.0, 1.0, 0.0
+        for j in range(b, e):
+            A *= w[j]
+            B = w[j] * B + x[j]
+            de += r * x[j]
+            r *= w[j + 1] if j + 1 < n else 0.0
+        segs.append((b, e, (A, B), (r, de)))
+    out = np.empty(n)
+    for s, (b, e, _, _) in enumerate(segs):
+        pre = fold([g[2] for g in segs[:s]], aff, ID2, rng)
+        suf = fold([g[3] for g in segs[s + 1:]], lambda f, g: (f[0] * g[0], f[0] * g[1] + f[1]), (1.0, 0.0), rng)
+        P, Pv = pre[1], []
+        for j in range(b, e):
+            P = w[j] * P + x[j]
+            Pv.append(P)
+        Q = suf[1]
+        for j in range(e - 1, b - 1, -1):
+            Q = (w[j + 1] if j + 1 < n else 0.0) * Q + x[j]
+            out[j] = Pv[j - b] + Q - x[j]
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_support_sweeps_are_independent_of_segmentation_and_order(seed):
+    """The support S = sum_j W_ij of the unnormalised kernel (rows on ones, columns on the row
+    result) by segments in random orders, against the oracle's support."""
+    rng = np.random.default_rng(300 + seed)
+    H, W = int(rng.integers(2, 30)), int(rng.integers(2, 40))
+    dX = 1.0 + rng.exponential(3.0, (H, W)) * (rng.random((H, W)) < 0.5)
+    dY = 1.0 + rng.exponential(3.0, (H, W)) * (rng.random((H, W)) < 0.5)
+    sigma_s = float(rng.uniform(2.0, 20.0))
+    a = float(np.exp(-np.sqrt(2.0) / sigma_s))
+    ref, _ = oracle.support(dX, dY, sigma_s)
+    rows = np.stack([support_segmented(np.ones(W), dX[y], a, rng) for y in range(H)])
+    got = np.stack([support_segmented(rows[:, x], dY[:, x], a, rng) for x in range(W)], axis=1)
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=0)
