@@ -30,17 +30,21 @@ _TORCH_DTYPE = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 
 
 class DTSError(RuntimeError):
+    """A libdts call returned a non-zero status (``status``; names in ``STATUS``)."""
+
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {STATUS.get(status, status)}")
         self.status = status
 
 
 class CGuide(ctypes.Structure):
+    """ctypes mirror of ``dts_guide`` (planar C x H x W guide: dtype, device pointer, strides)."""
     _fields_ = [("C", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int), ("dtype", ctypes.c_int),
                 ("data", ctypes.c_void_p), ("ch_stride", ctypes.c_longlong), ("row_stride", ctypes.c_longlong)]
 
 
 class CParams(ctypes.Structure):
+    """ctypes mirror of ``dts_params`` (field order and types as in include/dts.h)."""
     _fields_ = [("lambda_", ctypes.c_float), ("sigma_s", ctypes.c_float), ("sigma_r", ctypes.c_float),
                 ("step", ctypes.c_float), ("iterations", ctypes.c_int), ("passes", ctypes.c_int),
                 ("norm", ctypes.c_int), ("update", ctypes.c_int), ("conf_mode", ctypes.c_int),
@@ -66,6 +70,7 @@ class Params:
     charbonnier_eps: float = 0.0
 
     def c(self) -> CParams:
+        """The ``dts_params`` struct these values describe."""
         return CParams(self.lam, self.sigma_s, self.sigma_r, self.step, self.iterations, self.passes, self.norm,
                        self.update, self.conf_mode, self.dist_dtype, self.save_checkpoints, self.filter_kernel,
                        self.charbonnier_eps)
@@ -80,6 +85,7 @@ EXPORTS = ("dts_status_string", "dts_version", "dts_workspace_size", "dts_domain
 
 
 def library_path() -> str:
+    """Path of the in-tree libdts.so."""
     return _build.LIB
 
 
@@ -167,6 +173,7 @@ def _dense(t: torch.Tensor, name: str, dtypes=(torch.float32,)):
 
 
 def workspace_size(guide: torch.Tensor, params: Params, with_backward: bool = False) -> int:
+    """Bytes of workspace a solve (and, with_backward, its reverse mode) needs (dts_workspace_size)."""
     g = guide_desc(guide)
     p = params.c()
     return load().dts_workspace_size(ctypes.byref(g), ctypes.byref(p), int(with_backward))
@@ -264,6 +271,7 @@ def dts_autotune(guide: torch.Tensor, params: Params, ws: Optional[torch.Tensor]
 
 
 def autotune_export() -> str:
+    """The tile shapes recorded by dts_autotune, as text ("row W items" / "col H items warps cluster")."""
     lib = load()
     n = lib.dts_autotune_export(None, 0)
     buf = ctypes.create_string_buffer(n)
@@ -272,6 +280,7 @@ def autotune_export() -> str:
 
 
 def autotune_import(text: str) -> None:
+    """Record tile shapes from text in the format of autotune_export."""
     _check(load().dts_autotune_import(text.encode()), "dts_autotune_import")
 
 
@@ -389,6 +398,7 @@ def dts_profile_read(max_records: int = 1 << 16):
 
 
 def version() -> str:
+    """The library's version string."""
     return load().dts_version().decode()
 
 
