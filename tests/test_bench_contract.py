@@ -55,3 +55,34 @@ def test_every_timed_kernel_has_algorithmic_bytes():
         assert os.path.exists(src), n
         stem = n.split("<")[0]
         assert stem in open(src).read(), f"{n} not defined in {os.path.basename(src)}"
+
+
+def test_clock_records_decide_which_runs_are_rejected():
+    """A timed run whose clock samples show a hardware or thermal slowdown, or SM clocks stuck
+    well below their maximum with no reason given (a leftover clock lock), is rejected; a power cap
+    alone is kept and reported."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+
+    def summary(rows):
+        s = bench.ClockSampler(0)
+        s.rows = [[x.strip() for x in r.split(",")] for r in rows]
+        return s.summary()
+
+    ok = "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    capped = "0, 1470, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active"
+    hw = "0, 2070, 2070, 900.0, 0x8, Active, Not Active, Not Active, Not Active"
+    thermal = "0, 1800, 2070, 900.0, 0x20, Not Active, Not Active, Active, Not Active"
+    locked = "0, 900, 2070, 500.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+
+    s = summary([ok] * 5)
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 5}
+    assert not bench.rejected(s)
+    s = summary([ok, capped, capped])
+    assert s["reasons"] == ["sw_power_cap"] and not bench.rejected(s)
+    assert bench.rejected(summary([ok, hw, ok]))
+    assert summary([ok, hw])["reasons"] == ["hw_slowdown"]
+    assert bench.rejected(summary([ok, thermal, ok]))
+    assert bench.rejected(summary([locked] * 4))
+    assert not bench.rejected(summary([]))  # no samples: nothing to judge
