@@ -2,17 +2,23 @@
 """Benchmark of the GB300 Domain Transform Solver.
 
 One step = one complete DTS solve (distances + K iterations of N horizontal and
-N vertical recursive-filter passes + the data-term update) of the stereo-shaped
-workload: a 2880 x 1988 RGB guide, 20 iterations, sigma_s = 16, sigma_r = 0.1,
-lambda = 0.99, FP32 (seeded synthetic data shaped like the paper's Middlebury
-stereo refinement; the dataset itself is not available).
+N vertical recursive-filter passes + the data-term update) of the default
+workload: the 10000 x 10000 multispectral image with 16 bands, 10 iterations,
+sigma_s = 32, sigma_r = 0.1, lambda = 0.99, FP32 (seeded synthetic data shaped
+like satellite imagery; the largest configuration that fits one GPU).  The
+line's value is the forward solve; ``fwdbwd`` holds the same measurement for
+the forward solve followed by its reverse mode (dts_solve_backward, gradients
+for target, confidence and guide).  ``--workload`` picks the stereo-shaped,
+depth-SR, batched or 256 x 256 workload instead.
 
 Prints ONE JSON line (rank 0).  ``value`` is megapixels solved per second over
 all ranks with inputs resident in HBM; ``e2e`` is the same metric through the
 Python binding with host-resident (pinned) inputs copied in and the result
 copied out every step; ``roofline`` is the dominant kernel's algorithmic bytes
 per launch over its event-timed duration, against the measured HBM copy
-bandwidth; ``cpu_baseline`` is the FP64 oracle timed on the host cores.
+bandwidth, with the whole step's on the method's byte count; ``cpu_baseline`` is
+the FP64 oracle timed on the host cores on a bounded sample, and ``error`` the
+GPU's distance from it on that sample.
 
 ``--impl reference`` times the oracle itself (the CPU program the GPU path is
 checked against) on the same workload and metric.
@@ -71,16 +77,15 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3):
         "row_pass_kernel": 8 + s_d,
         "col_pass_kernel": 8 + s_d,
         "col_strip_kernel": 8 + s_d,
-        "col_pass_kernel<update>": 16 + s_d + s_t,
+        "col_chain_kernel": 8 + s_d,
+        "col_bwd_chain_kernel": 24 + s_d,
         "row_pass_kernel<support>": s_d + 4,
         "col_pass_kernel<support>": 12 + s_d,
         "row_pass_kernel<update>": 20 + s_t + s_d,
         "update_kernel": 16 + s_t,
-        "col_agg_kernel": 4 + s_d,
         "row_bwd_kernel": 24 + s_d,
         "row_bwd_kernel<final>": 28 + s_d,
         "col_bwd_kernel": 24 + s_d,
-        "col_bwd_kernel<update>": 48 + s_d + s_t,
         "guide_grad_kernel": C * s_g + 2 * s_d + 8 + 4 * C,
         "axpy_plane_kernel": 12,
         "update_adjoint_kernel": 36 + s_t,
@@ -88,6 +93,7 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3):
         # the first transposed vertical pass of a product also reads the minuend plane
         "col_pass_kernel<transpose>": 8 + s_d + 4.0 / N,
         "col_strip_kernel<transpose>": 8 + s_d + 4.0 / N,
+        "col_chain_kernel<transpose>": 8 + s_d + 4.0 / N,
         "square_plane_kernel": 8,
         "confidence_kernel": 12,
         "box_line_kernel": 12,
@@ -108,9 +114,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--workload", choices=["stereo", "plain", "depth_sr", "batched", "multispectral"],
-                    default="stereo")
+                    default="multispectral")
     ap.add_argument("--storage", choices=["f32", "bf16"], default="f32", help="guide and target storage")
-    ap.add_argument("--direction", choices=["fwd", "fwdbwd"], default="fwd")
+    ap.add_argument("--direction", choices=["fwd", "fwdbwd", "both"], default="both",
+                    help="both: forward as the line's value, forward + backward under 'fwdbwd'")
     ap.add_argument("--update", choices=["gd", "jacobi", "cg"], default="gd",
                     help="Eq. 3 gradient step, Eq. 4 fixed point, or conjugate gradients on Eq. 2")
     ap.add_argument("--sweep", choices=["iterations", "sigma", "size"], default=None,
@@ -198,8 +205,8 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
-BACKWARD_KERNELS = ("row_bwd_kernel", "col_bwd_kernel", "update_adjoint_kernel", "guide_grad_kernel",
-                    "axpy_plane_kernel")
+BACKWARD_KERNELS = ("row_bwd_kernel", "col_bwd_kernel", "col_bwd_chain_kernel", "update_adjoint_kernel",
+                    "guide_grad_kernel", "axpy_plane_kernel")
 
 
 def kernel_source(kernel):
@@ -208,15 +215,34 @@ def kernel_source(kernel):
           else "dts_box.cu" if kernel.startswith(("box_", "transpose_"))
           else "dts_resident.cu" if kernel.startswith("resident_")
           else "dts_confidence.cu" if kernel.startswith(("square_plane_", "confidence_"))
-          else "dts_vertical.cu" if kernel.startswith("col_agg_") else "dts_forward.cu")
+          else "dts_forward.cu")
     return os.path.join(ROOT, "paper_1805_04590_gb300", "csrc", fn)
 
 
+def source_hash(path):
+    """SHA-256 (first 16 hex digits) of a library source file together with every local header it
+    includes, recursively (a change to any of them changes the kernel)."""
+    seen, h = set(), hashlib.sha256()
+
+    def add(fn):
+        fn = os.path.normpath(fn)
+        if fn in seen or not os.path.exists(fn):
+            return
+        seen.add(fn)
+        text = open(fn, "rb").read()
+        h.update(text)
+        for inc in re.findall(rb'#include\s+"([^"]+)"', text):
+            add(os.path.join(os.path.dirname(fn), inc.decode()))
+
+    add(path)
+    return h.hexdigest()[:16]
+
+
 def traffic_for(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, when that
-    summary was taken on the current source of the file that holds the kernel (else None)."""
-    src = kernel_source(kernel)
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, when that summary was
+    taken on the current source of the kernel's translation unit (its .cu file and the headers it
+    includes), else None."""
+    sha = source_hash(kernel_source(kernel))
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None
@@ -242,37 +268,49 @@ WORKLOAD_DATA = {
 }
 
 
-class Case:
-    """One step of a workload on the GPU: inputs resident, outputs and gradients preallocated."""
+class Inputs:
+    """A workload's inputs resident on the device (guides and targets in the storage dtype)."""
 
     def __init__(self, args, dev):
         import torch
-        from paper_1805_04590_gb300 import dts, workloads
-        self.torch, self.dts = torch, dts
-        self.args, self.dev = args, dev
+        from paper_1805_04590_gb300 import workloads
         self.name = args.workload
-        self.bwd = args.direction == "fwdbwd"
-        if self.name == "batched" and self.bwd:
-            raise SystemExit("the batched entry point is forward only")
-        if args.update == "cg" and self.bwd:
-            raise SystemExit("conjugate gradients have no backward")
         self.wl = workloads.make(WORKLOAD_INDEX[self.name])
-        q = self.wl.params
-        self.s_d = 2 if args.dist_dtype == "f16" else 4
         self.sdt = torch.bfloat16 if args.storage == "bf16" else torch.float32
         self.s_io = 2 if args.storage == "bf16" else 4
+        probs = self.wl.problems
+        self.mp = sum(p.target.size for p in probs) / 1e6
+        self.g = [torch.from_numpy(p.guide).to(dev).to(self.sdt) for p in probs]
+        self.t = [torch.from_numpy(p.target).to(dev).to(self.sdt) for p in probs]
+        self.c = [torch.from_numpy(p.conf).to(dev) for p in probs]
+
+
+class Case:
+    """One step of a workload in one direction on the GPU: inputs resident, outputs, gradients and
+    the workspace preallocated."""
+
+    def __init__(self, args, dev, inputs, direction):
+        import torch
+        from paper_1805_04590_gb300 import dts
+        self.torch, self.dts = torch, dts
+        self.args, self.dev, self.inp = args, dev, inputs
+        self.name = inputs.name
+        self.wl = inputs.wl
+        self.mp = inputs.mp
+        self.g, self.t, self.c = inputs.g, inputs.t, inputs.c
+        self.s_io = inputs.s_io
+        self.direction = direction
+        self.bwd = direction == "fwdbwd"
+        q = self.wl.params
+        self.s_d = 2 if args.dist_dtype == "f16" else 4
         self.prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, step=q.step, iterations=q.iterations,
                               passes=q.passes, dist_dtype=dts.F16 if self.s_d == 2 else dts.F32,
                               save_checkpoints=0, update=UPDATES[args.update],
                               charbonnier_eps=args.charbonnier_eps,
                               filter_kernel=dts.KERNEL_BOX if args.filter_kernel == "box" else dts.KERNEL_RF)
         probs = self.wl.problems
-        self.mp = sum(p.target.size for p in probs) / 1e6
-        self.g = [torch.from_numpy(p.guide).to(dev).to(self.sdt) for p in probs]
-        self.t = [torch.from_numpy(p.target).to(dev).to(self.sdt) for p in probs]
-        self.c = [torch.from_numpy(p.conf).to(dev) for p in probs]
+        big = max(range(len(probs)), key=lambda i: probs[i].target.size)
         if self.bwd:  # what the autograd path picks: every pass input kept when memory allows
-            big = max(range(len(probs)), key=lambda i: probs[i].target.size)
             self.prm.save_checkpoints = dts.backward_checkpoint_mode(self.g[big], self.prm)
         self.out = [torch.empty(p.target.shape, dtype=torch.float32, device=dev) for p in probs]
         rng = np.random.default_rng(77)
@@ -281,7 +319,6 @@ class Case:
         if self.name == "batched":
             self.ws = [dts.batched_workspace(self.g, self.prm)]
         else:
-            big = max(range(len(probs)), key=lambda i: probs[i].target.size)
             self.ws = [dts.workspace(self.g[big], self.prm, with_backward=self.bwd)]
         self.grads = None
 
@@ -328,60 +365,67 @@ class Case:
                 "images": len(self.wl.problems), "channels": int(p.guide.shape[0]),
                 "shape_hw": list(shapes[0]) if len(shapes) == 1 else "uneven",
                 "iterations": q.iterations, "passes": q.passes, "megapixels_per_step": round(self.mp, 6),
-                "direction": self.args.direction, "storage": self.args.storage, "update": self.args.update,
+                "direction": self.direction, "storage": self.args.storage, "update": self.args.update,
                 "target_loss": (f"charbonnier eps={self.args.charbonnier_eps:g}" if self.args.charbonnier_eps > 0
                                 else "square"),
                 "filter_kernel": {"rf": "recursive filter", "box": "box (Eq. 10 as printed)"}[self.args.filter_kernel],
-                "distance_storage": self.args.dist_dtype, "l2": "flushed between steps (512 MiB write)",
+                "distance_storage": self.args.dist_dtype,
+                "l2": "flushed between steps (512 MiB write), in the device-timed and the end-to-end loops",
                 "backward_checkpoints": ({1: "iterates (pass inputs recomputed)", 2: "every pass input"}
                                          .get(self.prm.save_checkpoints) if self.bwd else None),
                 "parallelism": f"replicas x{world}"}
 
-    def cpu_sample(self):
-        """The oracle on a bounded sample of this workload: (megapixels, seconds, description, error)."""
-        import oracle
-        q = self.wl.params
-        probs = self.wl.problems
-        idx = list(range(min(len(probs), 8 if self.name == "batched" else 1)))
-        kw = dict(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, step=q.step, iterations=q.iterations,
-                  passes=q.passes, charbonnier_eps=self.args.charbonnier_eps)
-        mp = 0.0
-        errs, rels = [], []
-        t0 = time.perf_counter()
-        for i in idx:
-            p = probs[i]
-            I = self.g[i].float().cpu().numpy()  # the values the GPU saw (rounded when stored in bf16)
-            t = self.t[i].float().cpu().numpy()
-            if self.name == "multispectral":  # a 2500 x 2500 crop
-                I, t, cc = I[:, :2500, :2500], t[:2500, :2500], p.conf[:2500, :2500]
-            else:
-                cc = p.conf
-            z = oracle_solve(self.args.update, I, t, cc, kw)
-            mp += t.size / 1e6
-            if self.name != "multispectral":
-                zg = self.out[i].float().cpu().numpy()
-                err = float(np.abs(zg - z).max())
-                errs.append(err)
-                rels.append(err / max(float(np.ptp(t)), 1e-30))
-        dt = time.perf_counter() - t0
-        what = (f"{len(idx)} of {len(probs)} images" if len(probs) > 1 else "the full image") \
-            if self.name != "multispectral" else "a 2500x2500 crop (16 bands)"
-        desc = f"FP64 oracle, {what}, all {q.iterations} iterations forward, {dt:.2f} s"
-        error = None
-        if errs:
-            error = {"max_abs_vs_oracle": max(errs), "rel_to_target_range": max(rels), "tolerance": TOL,
-                     "within": max(rels) <= TOL, "inputs": "as stored on the GPU"}
-        return mp, dt, desc, error
 
-
-def run_ours(args, rank, world, local_rank):
+def cpu_sample(args, inp, case):
+    """The oracle on a bounded sample of the workload: (megapixels, seconds, description, error).
+    The error compares the GPU's solve of the same sample (for the multispectral image: a solve of
+    its 2500 x 2500 crop) with the oracle's on the inputs as stored on the GPU, and for 16-bit
+    storage also with the oracle's on the unrounded inputs."""
+    import oracle
     import torch
-    from paper_1805_04590_gb300 import dts
+    q = inp.wl.params
+    probs = inp.wl.problems
+    idx = list(range(min(len(probs), 8 if inp.name == "batched" else 1)))
+    kw = dict(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, step=q.step, iterations=q.iterations,
+              passes=q.passes, charbonnier_eps=args.charbonnier_eps)
+    crop = inp.name == "multispectral"
+    sl = (slice(0, 2500), slice(0, 2500)) if crop else (slice(None), slice(None))
+    mp, dt, rels, rels0 = 0.0, 0.0, [], []
+    for i in idx:
+        p = probs[i]
+        gd = inp.g[i][:, sl[0], sl[1]].contiguous()
+        td = inp.t[i][sl].contiguous()
+        cd = inp.c[i][sl].contiguous()
+        I = gd.float().cpu().numpy()  # the values the GPU saw (rounded when stored in bf16)
+        t = td.float().cpu().numpy()
+        cc = cd.cpu().numpy()
+        t0 = time.perf_counter()
+        z = oracle_solve(args.update, I, t, cc, kw)
+        dt += time.perf_counter() - t0
+        mp += t.size / 1e6
+        zg = (case.dts.dts_solve(gd, td, cd, case.prm) if crop else case.out[i]).float().cpu().numpy()
+        rng = max(float(np.ptp(t)), 1e-30)
+        rels.append(float(np.abs(zg - z).max()) / rng)
+        if args.storage != "f32":
+            z0 = oracle_solve(args.update, np.ascontiguousarray(p.guide[:, sl[0], sl[1]]),
+                              np.ascontiguousarray(p.target[sl]), cc, kw)
+            rels0.append(float(np.abs(zg - z0).max()) / rng)
+    what = ("a 2500x2500 crop (16 bands)" if crop else
+            f"{len(idx)} of {len(probs)} images" if len(probs) > 1 else "the full image")
+    desc = f"FP64 oracle, {what}, all {q.iterations} iterations forward, {dt:.2f} s"
+    error = {"rel_to_target_range": max(rels), "tolerance": TOL, "within": max(rels) <= TOL,
+             "inputs": "as stored on the GPU", "sample": what}
+    if rels0:
+        error["rel_to_target_range_unrounded_inputs"] = max(rels0)
+    return mp, dt, desc, error
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    case = Case(args, dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+def measure(args, case, world, local_rank, flush):
+    """Warm-up, the timed region (max over ranks), the dominant kernel's roofline and the whole
+    step's, and the end-to-end leg through the binding with host buffers, for one Case."""
+    import torch
+    dts = case.dts
+    dev = case.dev
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -428,113 +472,184 @@ def run_ours(args, rank, world, local_rank):
     value = job_value(world, args.steps, case.mp, total_ms)
     if dts.dts_last_status() != 0:
         raise RuntimeError("device status not clean after the timed region")
+    res = {"value": round(value, 2), "ms_per_step": round(total_ms / args.steps, 4), "clocks": clk,
+           "wall_s_timed_region": round(wall, 4)}
+    res.update(roofline_of(args, case, recs, total_ms))
+    res["e2e"] = e2e_of(args, case, world, flush)
+    return res
 
-    # per-kernel durations inside the timed region (sampled steps; kernels inside a CUDA graph are
-    # not bracketed, so the batched workload reports none)
+
+def roofline_of(args, case, recs, total_ms):
+    """The dominant kernel's algorithmic bytes per launch over its mean event-timed duration, and
+    the whole step's algorithmic bytes (the method's, by the per-pixel count of each pass, not the
+    implementation's) over the step time, against the measured HBM copy bandwidth."""
     profiled_steps = len(range(0, args.steps, PROFILE_EVERY))
     launches_per_step = len(recs) // profiled_steps if recs else None
     kern = {}
     C = int(case.g[0].shape[0])
-    s_g = 2 if args.storage == "bf16" else 4
+    s_g = case.s_io
     for name, _, px, fl, t_ms in recs:
         k = kern.setdefault(name, {"launches": 0, "ms": 0.0, "pixels": 0})
         k["launches"] += 1
         k["ms"] += t_ms
         k["pixels"] += px
-    roof, kernels = None, None
-    if kern:
-        dom = max(kern, key=lambda n: kern[n]["ms"])
-        kd = kern[dom]
-        bpp = bytes_per_pixel(dom, case.s_d, case.s_io, C=C, s_g=s_g, N=case.prm.passes)
-        alg_bytes = bpp * kd["pixels"] / kd["launches"]
-        avg_s = kd["ms"] / kd["launches"] / 1e3
-        peak, peak_kind = measured_peak()
-        achieved = alg_bytes / avg_s / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs (copy)",
-                "algorithmic_bytes_per_launch": int(alg_bytes), "bytes_per_pixel": round(bpp, 3),
-                "avg_launch_us": round(avg_s * 1e6, 2), "traffic": traffic_for(dom),
-                "share_of_step": round(kd["ms"] / sum(v["ms"] for v in kern.values()), 4)}
-        # the whole step against the same peak: every kernel's algorithmic bytes over the step time
-        bpps = {n: bytes_per_pixel(n, case.s_d, case.s_io, C=C, s_g=s_g, N=case.prm.passes) for n in kern}
-        step_bytes = sum(bpps[n] * v["pixels"] for n, v in kern.items() if bpps[n] is not None) / profiled_steps
-        step_s = total_ms / args.steps / 1e3
-        roof["step"] = {"algorithmic_bytes": int(step_bytes), "achieved": round(step_bytes / step_s / 1e9, 1),
-                        "frac": round(step_bytes / step_s / 1e9 / peak, 4),
-                        "kernels_without_bytes": sorted(n for n in kern if bpps[n] is None)}
-        kernels = {n: {"launches": v["launches"], "avg_us": round(v["ms"] / v["launches"] * 1e3, 2),
-                       "share": round(v["ms"] / sum(x["ms"] for x in kern.values()), 4)} for n, v in kern.items()}
+    out = {"roofline": None, "kernels": None,
+           "gpu_launches": launches_per_step * args.steps if launches_per_step else None}
+    if not kern:
+        return out
+    N = case.prm.passes
+    dom = max(kern, key=lambda n: kern[n]["ms"])
+    kd = kern[dom]
+    bpp = bytes_per_pixel(dom, case.s_d, case.s_io, C=C, s_g=s_g, N=N)
+    alg_bytes = bpp * kd["pixels"] / kd["launches"]
+    avg_s = kd["ms"] / kd["launches"] / 1e3
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / avg_s / 1e9
+    tot_ms = sum(v["ms"] for v in kern.values())
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs (copy)",
+            "algorithmic_bytes_per_launch": int(alg_bytes), "bytes_per_pixel": round(bpp, 3),
+            "avg_launch_us": round(avg_s * 1e6, 2), "traffic": traffic_for(dom),
+            "share_of_step": round(kd["ms"] / tot_ms, 4)}
+    step_bytes = step_algorithmic_bytes(case, C, s_g)
+    step_s = total_ms / args.steps / 1e3
+    profiled = len(range(0, args.steps, PROFILE_EVERY))
+    bpps = {n: bytes_per_pixel(n, case.s_d, case.s_io, C=C, s_g=s_g, N=N) for n in kern}
+    moved = sum(bpps[n] * v["pixels"] for n, v in kern.items() if bpps[n] is not None) / profiled
+    roof["step"] = {"algorithmic_bytes": int(step_bytes), "achieved": round(step_bytes / step_s / 1e9, 1),
+                    "frac": round(step_bytes / step_s / 1e9 / peak, 4),
+                    "bytes_per_pixel": round(step_bytes / (case.mp * 1e6), 2),
+                    "count": "the method's bytes per pixel: distances C s_g + 2 s_d once, then per iteration "
+                             "2N (8 + s_d) for the passes and 8 + s_t for the update (z_k, t, c read)"
+                             + ("; backward per iteration the forward recompute, 8N for saving the pass "
+                                "inputs, 2N (20 + s_d) for the adjoint passes and 24 for the update "
+                                "adjoint, then 8 + C s_g + 4C for the guide gradient" if case.bwd else ""),
+                    "kernel_bytes": int(moved),
+                    "kernel_frac": round(moved / step_s / 1e9 / peak, 4),
+                    "kernels_without_bytes": sorted(n for n in kern if bpps[n] is None)}
+    out["roofline"] = roof
+    out["kernels"] = {n: {"launches": v["launches"], "avg_us": round(v["ms"] / v["launches"] * 1e3, 2),
+                          "share": round(v["ms"] / tot_ms, 4)} for n, v in kern.items()}
+    return out
 
-    # end to end through the binding with host-resident inputs and outputs
+
+def step_algorithmic_bytes(case, C, s_g):
+    """The method's algorithmic bytes of one step (the per-pixel count of the path's design, not
+    of this implementation's kernels): the distances once (C s_g in, 2 s_d out); per iteration
+    2N passes of 8 + s_d (iterate read and written, distances read) and the update reading z_k, t
+    and c (8 + s_t); conjugate gradients run 4N passes and three vector kernels (20, 24 and 12 bytes)
+    per step; the backward adds per iteration the forward's bytes again (the pass inputs
+    recomputed), 8N for keeping them, 2N adjoint passes of 20 + s_d (adjoint and pass input read,
+    input adjoint written, distance adjoint updated) and 24 for the update adjoint, and once
+    8 + C s_g + 4C for the guide gradient."""
+    q = case.wl.params
+    N, K, s_d, s_t = case.prm.passes, q.iterations, case.s_d, case.s_io
+    if case.args.update == "cg":
+        per_iter = 4 * N * (8 + s_d) + 20 + 24 + 12
+    else:
+        per_iter = 2 * N * (8 + s_d) + 8 + s_t
+    bpp = C * s_g + 2 * s_d + K * per_iter
+    if case.bwd:
+        bpp += K * (per_iter + 8 * N + 2 * N * (20 + s_d) + 24) + 8 + C * s_g + 4 * C
+    return bpp * case.mp * 1e6
+
+
+def e2e_of(args, case, world, flush):
+    """The same metric through the binding with pinned host inputs copied in and the result (and
+    the gradients) copied out every step, L2 flushed before every solve as in the timed region."""
+    import torch
+    dts = case.dts
+    stream = torch.cuda.current_stream()
     gh = [x.cpu().pin_memory() for x in case.g]
     th = [x.cpu().pin_memory() for x in case.t]
     ch = [x.cpu().pin_memory() for x in case.c]
     zh = [torch.empty(x.shape, dtype=torch.float32).pin_memory() for x in case.out]
-    gd = [torch.empty_like(x) for x in case.g]
-    td = [torch.empty_like(x) for x in case.t]
-    cd = [torch.empty_like(x) for x in case.c]
-    gradh = None
-
-    # backward: the incoming gradient comes from pinned host memory too, and the gradients go
-    # back into pinned host buffers, all asynchronous on the stream
     gzh = [x.cpu().pin_memory() for x in case.gz] if case.bwd else []
+    n_e2e = max(1, min(args.e2e_steps, args.steps))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if case.bwd:
+        gd = [torch.empty_like(x) for x in case.g]
+        td = [torch.empty_like(x) for x in case.t]
+        cd = [torch.empty_like(x) for x in case.c]
+        gradh = None
 
-    def e2e_step():
-        nonlocal gradh
-        for dst, src in zip(gd + td + cd + (case.gz or []), gh + th + ch + gzh):
-            dst.copy_(src, non_blocking=True)
-        case.step(gd, td, cd)
-        for dst, src in zip(zh, case.out):
-            dst.copy_(src, non_blocking=True)
-        if case.bwd:
+        def e2e_step():
+            nonlocal gradh
+            for dst, src in zip(gd + td + cd + case.gz, gh + th + ch + gzh):
+                dst.copy_(src, non_blocking=True)
+            flush.zero_()
+            case.step(gd, td, cd)
+            for dst, src in zip(zh, case.out):
+                dst.copy_(src, non_blocking=True)
             grads = [x for gr in case.grads for x in gr if x is not None]
             if gradh is None:
                 gradh = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in grads]
             for dst, src in zip(gradh, grads):
                 dst.copy_(src, non_blocking=True)
 
-    n_e2e = max(1, min(args.e2e_steps, args.steps))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if case.bwd:
         for _ in range(2):
             e2e_step()
         torch.cuda.synchronize()
-        barrier()
         e0.record(stream)
         for _ in range(n_e2e):
             e2e_step()
         e1.record(stream)
+        copies = "serial with the solve, asynchronous on its stream (pinned host buffers)"
     else:
-        # forward: the binding's host pipeline overlaps each step's copies with the neighbouring
-        # steps' solves (every step still copies its inputs in and its result out)
-        pipe = dts.HostPipeline(case.solve_into)
+        # the binding's host pipeline overlaps each step's copies with the neighbouring steps'
+        # solves (every step still copies its inputs in and its result out)
+        def solve_flushed(din, dout):
+            flush.zero_()
+            case.solve_into(din, dout)
+
+        pipe = dts.HostPipeline(solve_flushed)
         hin, hout = gh + th + ch, zh
         pipe.run([hin] * 2, [hout] * 2)
         torch.cuda.synchronize()
-        barrier()
         e0.record(stream)
         pipe.run([hin] * n_e2e, [hout] * n_e2e, start_event=e0)
         e1.record(stream)
+        copies = ("dts.HostPipeline: step i+1's host-to-device and step i-1's device-to-host copies overlap "
+                  "step i's solve")
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
+        tt = torch.tensor([e2e_ms], device=case.dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(tt.item())
     h2d, d2h = case.io_bytes()
-    e2e = {"value": round(world * n_e2e * case.mp / (e2e_ms / 1e3), 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "steps": n_e2e,
-           "copies": ("serial with the solve, asynchronous on its stream (pinned host buffers)" if case.bwd else
-                      "dts.HostPipeline: step i+1's host-to-device and step i-1's device-to-host copies overlap "
-                      "step i's solve")}
+    return {"value": round(world * n_e2e * case.mp / (e2e_ms / 1e3), 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": n_e2e, "copies": copies,
+            "l2": "flushed before every solve (512 MiB write), as in the device-timed loop"}
 
-    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": WORKLOAD_DATA[case.name], "config": case.config(world),
-            "roofline": roof, "kernels": kernels, "e2e": e2e,
-            "gpu_launches": launches_per_step * args.steps if launches_per_step else None,
-            "clocks": clk, "wall_s_timed_region": round(wall, 4),
+
+def directions_for(args):
+    """The directions a run measures: forward, and forward plus backward when the solve has a
+    backward (not the batched entry point, conjugate gradients or the box kernel)."""
+    has_bwd = args.workload != "batched" and args.update != "cg" and args.filter_kernel == "rf"
+    if args.direction == "both":
+        return ["fwd", "fwdbwd"] if has_bwd else ["fwd"]
+    if args.direction == "fwdbwd" and not has_bwd:
+        raise SystemExit("this solve has no backward (batched entry point, conjugate gradients or box kernel)")
+    return [args.direction]
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    inp = Inputs(args, dev)
+    dirs = directions_for(args)
+    case = Case(args, dev, inp, dirs[0])
+    main = measure(args, case, world, local_rank, flush)
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": WORKLOAD_DATA[case.name],
+            "config": case.config(world), "roofline": main["roofline"], "kernels": main["kernels"],
+            "e2e": main["e2e"], "gpu_launches": main["gpu_launches"], "clocks": main["clocks"],
+            "wall_s_timed_region": main["wall_s_timed_region"],
             "kernel_timing": f"CUDA events around each kernel on every {PROFILE_EVERY}th timed step"}
     if case.name == "batched":
         line["gpu_launches_note"] = "one CUDA graph launch per step; its kernels are not bracketed by events"
@@ -543,11 +658,22 @@ def run_ours(args, rank, world, local_rank):
     # line length): no bounded sample of a full-size image, so no CPU baseline for that kernel
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.filter_kernel == "rf":
         import oracle
-        mp, dt, desc, error = case.cpu_sample()
+        mp, dt, desc, error = cpu_sample(args, inp, case)
         line["cpu_baseline"] = {"value": round(mp / dt, 4), "unit": UNIT, "cores": oracle.num_threads(),
                                 "kind": "oracle", "sample": desc}
-        if error:
-            line["error"] = error
+        line["error"] = error
+    if len(dirs) > 1:
+        del case
+        torch.cuda.empty_cache()
+        case_b = Case(args, dev, inp, dirs[1])
+        sub = measure(args, case_b, world, local_rank, flush)
+        line["fwdbwd"] = {"value": sub["value"], "unit": UNIT, "ms_per_step": sub["ms_per_step"],
+                          "direction": "forward solve and dts_solve_backward (gradients for target, "
+                                       "confidence and guide)",
+                          "backward_checkpoints": case_b.config(world)["backward_checkpoints"],
+                          "roofline": sub["roofline"], "kernels": sub["kernels"], "e2e": sub["e2e"],
+                          "gpu_launches": sub["gpu_launches"], "clocks": sub["clocks"],
+                          "wall_s_timed_region": sub["wall_s_timed_region"]}
     return line
 
 

@@ -88,10 +88,14 @@ typedef struct dts_guide {
  *              box kernel Eq. 10 prints, W_ij = 1 if |DT_i - DT_j| <= r with r = sigma_i sqrt(3)
  *              per pass (normalized convolution in the transformed domain); FP32 distances,
  *              DTS_CONF_PLAIN and no checkpoints only, lines up to 8192 positions, no backward
- *  charbonnier_eps  0 (default): the square (z - t)^2 on the target term.  > 0, with
- *              DTS_UPDATE_GD only: the Charbonnier loss sqrt((z - t)^2 + eps^2) that §4
- *              uses for stereo (eps = 0.001), so the gradient step of Eq. 3 takes
- *              c (z - t) / sqrt((z - t)^2 + eps^2) for the data term; forward and backward
+ *  charbonnier_eps  0 (default): the square (z - t)^2 on the target term.  > 0: the
+ *              Charbonnier loss sqrt((z - t)^2 + eps^2) that §4 uses for stereo (eps = 0.001);
+ *              DTS_UPDATE_GD: the gradient step of Eq. 3 takes c (z - t) / sqrt((z - t)^2 + eps^2)
+ *              for the data term (its curvature c / eps makes the step unstable where c > eps);
+ *              DTS_UPDATE_JACOBI: the fixed point of Eq. 4 with the loss's weight at the
+ *              current iterate, c~ = c / sqrt((z_k - t)^2 + eps^2) in place of c (stable at any
+ *              eps; its fixed points solve lambda (z - A z) + c rho'(z - t) = 0 like the gradient
+ *              step's); not with DTS_UPDATE_CG.  Forward and backward
  *  save_checkpoints  0: nothing kept; 1: dts_solve keeps z_0 .. z_{K-1} in the
  *              workspace for dts_solve_backward (workspace sized with with_backward = 1),
  *              which recomputes each iteration's pass inputs from them; 2: it also keeps
@@ -179,17 +183,19 @@ int dts_solve_backward(const dts_guide* guide, const void* target, int target_dt
  * for callers that cannot allocate device memory (code inside a host framework that owns every
  * device allocation, or a latency-critical loop where an allocation could block, fail or break
  * a fixed memory budget) and so cannot pass a workspace.  Arguments and results are those of
- * dts_solve; inputs and outputs are still the caller's.  The scratch is a 16 MiB device array
- * inside the library (dts_noalloc_max_workspace() bytes), held by every GPU that loads the
- * library until the process exits; problems whose dts_workspace_size(with_backward = 0)
- * exceeds it return DTS_ERR_WORKSPACE (16 bytes per padded pixel with FP32 distances: about
- * one megapixel), and
- * save_checkpoints = 1 returns DTS_ERR_UNSUPPORTED.  It allocates nothing: no cudaMalloc, no
- * cudaFree, no allocating library call.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the one array and it keeps the last call's contents
- * (every plane a solve reads is written by that solve first): calls that overlap on the GPU,
- * on any streams, race and give wrong results. */
+ * dts_solve with the recursive-filter kernel (filter_kernel = DTS_KERNEL_BOX returns
+ * DTS_ERR_UNSUPPORTED here); inputs and outputs are still the caller's.  The scratch is a
+ * 16 MiB device array inside the library (dts_noalloc_max_workspace() bytes), reserved on a
+ * device when the library's module is loaded there -- with CUDA's lazy module loading, at the
+ * first libdts call on that device, so make that first call (this one or any other) outside a
+ * latency-critical loop -- and held until the process exits; problems whose
+ * dts_workspace_size(with_backward = 0) exceeds it return DTS_ERR_WORKSPACE (16 bytes per padded
+ * pixel with FP32 distances: about one megapixel), and save_checkpoints = 1 returns
+ * DTS_ERR_UNSUPPORTED.  It allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ * call.  The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  All calls share the
+ * one array and it keeps the last call's contents (every plane a solve reads is written by that
+ * solve first): calls that overlap on the GPU, on any streams, race and give wrong results. */
 int dts_solve_noalloc(const dts_guide* guide, const void* target, int target_dtype, const float* conf,
                       const float* z_init, const dts_params* params, float* z_out, dts_stream stream);
 
@@ -234,13 +240,21 @@ int dts_autotune_import(const char* text);
 int dts_last_status(dts_stream stream);
 
 /* ---- fault injection for tests (host-requested, one-shot; nothing faults or traps) ----
- * DTS_INJECT_TMA_SKIP: the next vertical pass runs on the kernel that stages its tiles with
- * TMA (the one path with device-side waits) and, when it covers its columns in a single round,
- * skips the first tile load of its first CTA; that CTA's bounded wait (about a millisecond under
- * injection) gives up, computes on unfilled shared memory and records DTS_ERR_TIMEOUT, which
- * dts_last_status() then returns.  kind 0 cancels.
- * DTS_ERR_INVALID_ARG for unknown kinds. */
+ * Each kind makes one bounded device-side wait of the next matching launch run out (about a
+ * millisecond under injection instead of about a second): the kernel records DTS_ERR_TIMEOUT,
+ * which dts_last_status() then returns, issues no further copies into the memory the failed wait
+ * guarded, finishes (its results are invalid) and leaves the context usable.
+ * DTS_INJECT_TMA_SKIP: the next vertical pass on the strip kernel (columns up to 2176 rows), when
+ *   its grid covers every strip in one round, leaves out the first slab load of warp 0 of CTA 0.
+ * DTS_INJECT_CHAIN_SKIP: the next chained vertical pass (taller columns) does not count the
+ *   arrival of its first chunk, so the CTAs of the first strip wait for a composition that
+ *   never comes.
+ * DTS_INJECT_BARRIER_SKIP: the next resident solve (DTS_RESIDENT=1) leaves out CTA 0's arrival
+ *   at its first grid-wide barrier.
+ * kind 0 cancels; DTS_ERR_INVALID_ARG for unknown kinds. */
 #define DTS_INJECT_TMA_SKIP 1
+#define DTS_INJECT_CHAIN_SKIP 2
+#define DTS_INJECT_BARRIER_SKIP 3
 int dts_debug_inject(int kind);
 
 /* ---- per-launch kernel timing (a tracing aid; not part of the paper's method) ----

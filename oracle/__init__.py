@@ -191,8 +191,9 @@ def support(dX, dY, sigma_s):
 def solve_d(dX, dY, t, c, *, lam, sigma_s, step=0.99, iterations=10, passes=3, update=UPDATE_GD,
             conf_mode=CONF_PLAIN, z_init=None, checkpoints=False, kernel=KERNEL_RF, charbonnier_eps=0.0):
     """The solver on precomputed distances.  Returns z_K (and z_0..z_{K-1}).  kernel: the
-    recursive filter (default) or the box kernel of Eq. 10.  charbonnier_eps > 0: the gradient
-    step takes the Charbonnier loss sqrt(r^2 + eps^2) on the target term (§4)."""
+    recursive filter (default) or the box kernel of Eq. 10.  charbonnier_eps > 0: the
+    Charbonnier loss sqrt(r^2 + eps^2) on the target term (§4): the gradient step takes its
+    slope, the fixed point of Eq. 4 its weight 1 / sqrt(r^2 + eps^2) at the current iterate."""
     dX, dY, t, c = _f64(dX), _f64(dY), _f64(t), _f64(c)
     z0 = None if z_init is None else _f64(z_init)
     H, W = t.shape

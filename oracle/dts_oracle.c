@@ -38,9 +38,10 @@
  *                       V = DT(t^2) - DT(t)^2 with DT the edge-aware mean
  *   orc_solve           gradient-descent iterations on Eq. 3 (step 0.99, §4)
  *                       or the fixed-point update of Eq. 4; with eps > 0 the
- *                       gradient step uses the Charbonnier loss
- *                       rho(r) = sqrt(r^2 + eps^2) on the target term instead of
- *                       the square (§4, the stereo loss of Eq. 11: eps = 0.001)
+ *                       Charbonnier loss rho(r) = sqrt(r^2 + eps^2) on the target
+ *                       term instead of the square (§4, the stereo loss of Eq. 11:
+ *                       eps = 0.001): the gradient step takes c rho'(z - t), the
+ *                       fixed point the loss's weight at the current iterate
  *   orc_solve_backward  hand-written reverse mode of orc_solve (the paper has
  *                       no backward; derived from the forward steps above)
  */
@@ -312,13 +313,22 @@ static double target_slope(double r, double eps) { return eps > 0.0 ? r / sqrt(r
  *     In SUPPORT mode the step is limited to eta_i = min(eta, 1 / (lambda + c_i))
  *     so that the iteration stays stable where c_i is large.
  *   Jacobi (the fixed point of Eq. 4):
- *       z_{k+1} = (lambda z_bar + c t) / (lambda + c);  z_k is kept where lambda + c = 0. */
+ *       z_{k+1} = (lambda z_bar + c t) / (lambda + c);  z_k is kept where lambda + c = 0.
+ *     With the Charbonnier loss (eps > 0) Eq. 4 is taken with the loss's weight at the current
+ *     iterate, c~ = c / sqrt((z_k - t)^2 + eps^2) in place of c (the loss written as
+ *     c~ (z - t)^2 / 2 plus a constant around z_k): a fixed point of the iteration satisfies
+ *     lambda (z - z_bar) + c rho'(z - t) = 0, the stationarity the gradient step aims at. */
 static void update(long n, const double* zk, const double* zbar, const double* t, const double* chat, double lambda,
                    double eta, int update_mode, double eps, int clamp_step, double* out) {
     for (long p = 0; p < n; ++p) {
         if (update_mode == ORC_UPDATE_JACOBI) {
-            double den = lambda + chat[p];
-            out[p] = (den != 0.0) ? (lambda * zbar[p] + chat[p] * t[p]) / den : zk[p];
+            double cw = chat[p];
+            if (eps > 0.0) {
+                const double r = zk[p] - t[p];
+                cw = chat[p] / sqrt(r * r + eps * eps);
+            }
+            double den = lambda + cw;
+            out[p] = (den != 0.0) ? (lambda * zbar[p] + cw * t[p]) / den : zk[p];
         } else {
             double e = eta;
             if (clamp_step && lambda + chat[p] > 0.0 && 1.0 / (lambda + chat[p]) < e) e = 1.0 / (lambda + chat[p]);
@@ -611,12 +621,20 @@ int orc_solve_backward(int C, int H, int W, const double* I, double sigma_s, dou
         orc_filter(H, W, dX, dY, N, a, zk, zbar);
         for (long p = 0; p < n; ++p) {
             if (update_mode == ORC_UPDATE_JACOBI) {
-                double den = lambda + c[p];
+                /* the weight of the Charbonnier loss at z_k: w = 1 / sqrt(r^2 + eps^2), r = z_k - t
+                 * (w = 1 for the square); c~ = c w enters like c, and reaches z_k and t through r,
+                 * dc~/dr = -c r w^3 */
+                const double r = zk[p] - t[p];
+                const double w = eps > 0.0 ? 1.0 / sqrt(r * r + eps * eps) : 1.0;
+                const double cw = c[p] * w;
+                double den = lambda + cw;
                 if (den != 0.0) {
-                    tb[p] += c[p] / den * g[p];
-                    cb[p] += lambda * (t[p] - zbar[p]) / (den * den) * g[p];
+                    const double gcw = lambda * (t[p] - zbar[p]) / (den * den) * g[p];
+                    const double gr = eps > 0.0 ? -c[p] * r * w * w * w * gcw : 0.0;
+                    tb[p] += cw / den * g[p] - gr;
+                    cb[p] += w * gcw;
                     gbar[p] = lambda / den * g[p];
-                    gprev[p] = 0.0;
+                    gprev[p] = gr;
                 } else {
                     gbar[p] = 0.0;
                     gprev[p] = g[p];

@@ -6,7 +6,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -20,11 +23,14 @@ __device__ int g_status = 0;
 namespace {
 
 constexpr int kMaxDevices = 64;
-int* g_status_ptr[kMaxDevices] = {};
-bool g_inject_tma_skip = false;
+std::atomic<int*> g_status_ptr[kMaxDevices] = {};
+int g_inject = 0;  // pending fault injection (dts_debug_inject), one-shot
 std::mutex g_prep_mutex;
 bool g_prepared[kMaxDevices] = {};
 
+// Once per device, with that device current: kernel attributes, and the device address of the
+// status word (the bounded waits of the kernels write DTS_ERR_TIMEOUT there).  Every entry point
+// calls this before its first launch, so a launch never gets a null status word.
 int ensure_prepared() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DTS_ERR_CUDA;
@@ -33,6 +39,9 @@ int ensure_prepared() {
         if (prepare_kernels() != cudaSuccess || prepare_backward_kernels() != cudaSuccess ||
             prepare_box_kernels() != cudaSuccess || prepare_resident_kernel() != cudaSuccess)
             return DTS_ERR_CUDA;
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess || p == nullptr) return DTS_ERR_CUDA;
+        g_status_ptr[dev].store(static_cast<int*>(p));
         g_prepared[dev] = true;
     }
     return DTS_OK;
@@ -40,27 +49,44 @@ int ensure_prepared() {
 
 }  // namespace
 
+// SMs of the current device (cached per process: one kind of GPU).
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// resident CTAs per SM of a kernel (cached per kernel, block size and dynamic shared memory)
+int blocks_per_sm(const void* kernel, int block, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, size_t>, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(kernel, block, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess) n = 0;
+    cache[key] = n;
+    return n;
+}
+
+// The status word of the current device, as looked up by ensure_prepared (null before).
 int* status_word() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-    if (!g_status_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
-        g_status_ptr[dev] = static_cast<int*>(p);
-    }
-    return g_status_ptr[dev];
+    return g_status_ptr[dev].load();
 }
 
-bool injected_tma_skip_pending() {
+bool take_injected(int kind) {
     std::lock_guard<std::mutex> lock(g_prep_mutex);
-    return g_inject_tma_skip;
-}
-
-bool take_injected_tma_skip() {
-    std::lock_guard<std::mutex> lock(g_prep_mutex);
-    const bool v = g_inject_tma_skip;
-    g_inject_tma_skip = false;
-    return v;
+    if (g_inject != kind) return false;
+    g_inject = 0;
+    return true;
 }
 
 namespace {
@@ -98,7 +124,7 @@ int check_params(const dts_params* p) {
 
 // what conjugate gradients and the box-kernel filter support (DTS_ERR_UNSUPPORTED otherwise)
 int check_box(const dts_guide* g, const dts_params* p) {
-    if (p->charbonnier_eps > 0.f && p->update != DTS_UPDATE_GD) return DTS_ERR_UNSUPPORTED;
+    if (p->charbonnier_eps > 0.f && p->update == DTS_UPDATE_CG) return DTS_ERR_UNSUPPORTED;
     if (p->update == DTS_UPDATE_CG &&
         (p->filter_kernel != DTS_KERNEL_RF || p->conf_mode != DTS_CONF_PLAIN || p->save_checkpoints))
         return DTS_ERR_UNSUPPORTED;
@@ -119,9 +145,7 @@ struct Layout {
     size_t dX, dY, u, chat, z;  // offsets
     size_t dYs;         // dY tiled by 8-column strips (ys_rows rows per strip; 0: none)
     long long ys_rows;
-    size_t agg, carry, counters;  // split vertical pass scratch
-    long long agg_pitch, agg_plane;
-    int nstrips128;
+    size_t chain_ctl, chain_agg;  // chained vertical passes: control words, chunk tuples
     int z_planes;       // 1 (in place) or K checkpoints
     size_t passes;      // save_checkpoints = 2: K x 2N planes, (k, 0) = zbar_k, (k, q) = input of pass q
     size_t dYt, ut;     // box kernel: transposed dY and working plane (W rows, pitch tpitch)
@@ -136,8 +160,6 @@ struct Layout {
     size_t g0, g1;      // adjoint ping-pong planes
     size_t gz;          // adjoint of the iterate
     size_t dXb, dYb;    // distance gradients
-    size_t tot;         // chunk totals of the vertical adjoint (columns taller than one cluster)
-    int tot_chunks;
     size_t total;
 };
 
@@ -157,13 +179,10 @@ Layout make_layout(int H, int W, const dts_params* p, int with_backward) {
         off += align_up((size_t)((W + 7) / 8) * (size_t)L.ys_rows * 8 * (p->dist_dtype == DTS_F16 ? 2 : 4), kPlaneAlign);
     L.chat = off;
     if (p->conf_mode == DTS_CONF_SUPPORT) off += L.plane_f32;
-    split_col_scratch(H, W, &L.agg_pitch, &L.agg_plane, &L.nstrips128);
-    L.agg = off;
-    off += align_up((size_t)L.agg_plane * 5 * sizeof(float), kPlaneAlign);
-    L.carry = off;
-    off += align_up((size_t)L.agg_plane * 2 * sizeof(float), kPlaneAlign);
-    L.counters = off;
-    off += align_up((size_t)L.nstrips128 * sizeof(unsigned), kPlaneAlign);
+    L.chain_ctl = off;
+    off += align_up(chain_ctl_bytes(W), kPlaneAlign);
+    L.chain_agg = off;
+    off += align_up(chain_agg_bytes(H, W), kPlaneAlign);
     L.z = off;
     const bool keep = p->save_checkpoints || with_backward;
     L.z_planes = keep ? (p->iterations > 0 ? p->iterations : 1) : 1;
@@ -198,9 +217,6 @@ Layout make_layout(int H, int W, const dts_params* p, int with_backward) {
         L.gz = off; off += L.plane_f32;
         L.dXb = off; off += L.plane_f32;
         L.dYb = off; off += L.plane_f32;
-        L.tot_chunks = bwd_col_chunks(H);
-        L.tot = off;
-        off += align_up((size_t)L.tot_chunks * 9 * (size_t)L.pitch * sizeof(float), kPlaneAlign);
     }
     L.total = off;
     return L;
@@ -280,21 +296,18 @@ PassArgs base_pass(const dts_guide* g, const Layout& L) {
         a.d_tiled_rows = L.ys_rows;
     }
     if (t_ws) {
-        a.agg = reinterpret_cast<float*>(static_cast<char*>(t_ws) + L.agg);
-        a.carry = reinterpret_cast<float*>(static_cast<char*>(t_ws) + L.carry);
-        a.counters = reinterpret_cast<unsigned*>(static_cast<char*>(t_ws) + L.counters);
-        a.agg_pitch = L.agg_pitch;
-        a.agg_plane = L.agg_plane;
+        a.chain_ctl = reinterpret_cast<unsigned*>(static_cast<char*>(t_ws) + L.chain_ctl);
+        a.chain_agg = reinterpret_cast<float*>(static_cast<char*>(t_ws) + L.chain_agg);
     }
     return a;
 }
 
-// Binds the workspace for base_pass and zeroes the split pass's ticket counters (each strip's
-// last CTA resets its own counter, so one clear per call suffices).
-int bind_workspace(void* ws, const Layout& L, cudaStream_t s) {
+// Binds the workspace for base_pass and zeroes the chained passes' control words (every chained
+// launch leaves them at zero again, so one clear per call suffices; it also clears an abort
+// left by a wait that ran out in an earlier call).
+int bind_workspace(void* ws, const Layout& L, int W, cudaStream_t s) {
     t_ws = ws;
-    if (cudaMemsetAsync(static_cast<char*>(ws) + L.counters, 0, (size_t)L.nstrips128 * sizeof(unsigned), s) !=
-        cudaSuccess)
+    if (cudaMemsetAsync(static_cast<char*>(ws) + L.chain_ctl, 0, chain_ctl_bytes(W), s) != cudaSuccess)
         return DTS_ERR_CUDA;
     return DTS_OK;
 }
@@ -364,7 +377,7 @@ int solve_box(const dts_guide* g, const void* target, int tdt, const float* conf
         return cuda_status(launch_copy_plane(target, tdt, W, z_out, W, H, W, s));
     }
     int st;
-    if ((st = bind_workspace(ws, L, s))) return st;
+    if ((st = bind_workspace(ws, L, g->W, s))) return st;
     float* z = reinterpret_cast<float*>(ws_at(ws, L.z));
     if (z_init) st = run_distances(g, p, L, ws, z_init, DTS_F32, z, s);
     else st = run_distances(g, p, L, ws, target, tdt, z, s);
@@ -407,10 +420,10 @@ namespace {
 int solve_cg(const dts_guide* g, const void* target, int tdt, const float* conf, const float* z_init,
              const dts_params* p, float* z_out, void* ws, const Layout& L, const Plans& pl, cudaStream_t s) {
     const int K = p->iterations, N = p->passes, W = g->W;
-    ColPlan cluster_shape;  // the transposed vertical pass needs the strip or the cluster kernel
-    if (!plan_cols_cluster(g->H, &cluster_shape)) return DTS_ERR_UNSUPPORTED;
+    ColPlan multi_shape;  // the transposed vertical pass needs the strip, chain or cluster kernel
+    if (!plan_cols_multi(g->H, &multi_shape)) return DTS_ERR_UNSUPPORTED;
     int st;
-    if ((st = bind_workspace(ws, L, s))) return st;
+    if ((st = bind_workspace(ws, L, g->W, s))) return st;
     float* z = reinterpret_cast<float*>(ws_at(ws, L.z));
     if (z_init) st = run_distances(g, p, L, ws, z_init, DTS_F32, z, s);
     else st = run_distances(g, p, L, ws, target, tdt, z, s);
@@ -541,7 +554,7 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
         return cuda_status(launch_copy_plane(target, tdt, W, z_out, W, g->H, W, s));
     }
     if (p->update == DTS_UPDATE_CG) return solve_cg(g, target, tdt, conf, z_init, p, z_out, ws, L, pl, s);
-    if ((st = bind_workspace(ws, L, s))) return st;
+    if ((st = bind_workspace(ws, L, g->W, s))) return st;
     if (allow_resident && L.resident) return solve_resident(g, target, tdt, conf, z_init, p, z_out, ws, L, s);
     const bool keep = L.z_planes > 1 || p->save_checkpoints;
     auto zslot = [&](int k) -> float* {
@@ -582,10 +595,9 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
     };
     // The data-term update of iteration k is applied by the first horizontal pass of iteration
     // k + 1 (reading z_k, zbar, t and c as vectors along rows and writing z_{k+1}); after the
-    // last iteration a standalone kernel applies it.  Rows too long for that kernel (over 16384)
-    // keep the update in the last vertical pass.
+    // last iteration a standalone kernel applies it.  Every row the horizontal passes take fits.
     RowPlan urows;
-    const bool row_update = plan_rows_update(W, pl.rows, &urows);
+    if (!plan_rows_update(W, pl.rows, &urows)) return DTS_ERR_UNSUPPORTED;
     for (int k = 0; k < K; ++k) {
         float* zin = zslot(k);
         for (int i = 0; i < p->passes; ++i) {
@@ -595,7 +607,7 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
             r.d = ws_at(ws, L.dX);
             r.k2 = k2[i];
             int rkind = PASS_PLAIN;
-            if (row_update && i == 0 && k > 0) {
+            if (i == 0 && k > 0) {
                 rkind = PASS_UPDATE_ROW;
                 r.src = pslot(k - 1, 0);  // zbar of iteration k - 1
                 set_update(r, zslot(k - 1));
@@ -608,22 +620,10 @@ int solve_forward(const dts_guide* g, const void* target, int tdt, const float* 
             c.dst = pslot(k, (2 * i + 2) % NP);
             c.d = ws_at(ws, L.dY);
             c.k2 = k2[i];
-            int kind = PASS_PLAIN;
-            if (!row_update && i == p->passes - 1) {
-                kind = PASS_UPDATE;
-                set_update(c, zin);
-                if (k == K - 1) {
-                    c.zout = z_out;
-                    c.zout_pitch = W;
-                } else {
-                    c.zout = zslot(k + 1);
-                    c.zout_pitch = L.pitch;
-                }
-            }
-            if ((st = cuda_status(launch_col_pass(c, dh, kind, pl.cols, s)))) return st;
+            if ((st = cuda_status(launch_col_pass(c, dh, PASS_PLAIN, pl.cols, s)))) return st;
         }
     }
-    if (row_update) {
+    {
         PassArgs a = base_pass(g, L);
         a.src = pslot(K - 1, 0);
         set_update(a, zslot(K - 1));
@@ -698,7 +698,7 @@ extern "C" int dts_filter(const dts_guide* guide, const dts_params* params, cons
     if (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.fwd_end) return DTS_ERR_WORKSPACE;
     if ((st = ensure_prepared())) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = bind_workspace(ws, L, s))) return st;
+    if ((st = bind_workspace(ws, L, guide->W, s))) return st;
     float* u = reinterpret_cast<float*>(ws_at(ws, L.u));
     if ((st = run_distances(guide, &p, L, ws, src, DTS_F32, u, s))) return st;
     if (p.filter_kernel == DTS_KERNEL_BOX) {
@@ -748,7 +748,7 @@ extern "C" int dts_confidence(const dts_guide* guide, const void* target, int ta
     if (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.fwd_end) return DTS_ERR_WORKSPACE;
     if ((st = ensure_prepared())) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = bind_workspace(ws, L, s))) return st;
+    if ((st = bind_workspace(ws, L, guide->W, s))) return st;
     const int H = guide->H, W = guide->W;
     float* m1 = reinterpret_cast<float*>(ws_at(ws, L.u));  // DT(t), filtered in place
     float* m2 = reinterpret_cast<float*>(ws_at(ws, L.z));  // DT(t^2), filtered in place
@@ -874,8 +874,9 @@ int issue_batch(int n, const dts_guide* guides, const void* const* targets, int 
         int st = make_plans(guides[i].H, guides[i].W, &pl);
         if (st) return st;
         // solves that run side by side keep the cluster shapes for the vertical passes: their
-        // smaller CTAs pack several images onto an SM (measured on the 64-image batch)
-        if (pl.cols.cluster == 0 && !plan_cols_cluster(guides[i].H, &pl.cols)) return DTS_ERR_UNSUPPORTED;
+        // smaller CTAs pack several images onto an SM (measured on the 64-image batch), and no
+        // CTA of one image waits for CTAs of another to be scheduled (as a chain's might)
+        if (pl.cols.cluster <= 0 && !plan_cols_cluster(guides[i].H, &pl.cols)) return DTS_ERR_UNSUPPORTED;
         const Layout L = make_layout(guides[i].H, guides[i].W, p, 0);
         st = solve_forward(&guides[i], targets[i], tdt, confs[i], nullptr, p, z_out[i], ws_at(ws, offset[i]), L, pl,
                            r.side[j]);
@@ -915,6 +916,7 @@ extern "C" int dts_solve_batched(int n, const dts_guide* guides, const void* con
         if (!targets[i] || !confs[i] || !z_out[i]) return DTS_ERR_INVALID_ARG;
         Plans pl;
         if ((st = make_plans(guides[i].H, guides[i].W, &pl))) return st;
+        if (!plan_cols_cluster(guides[i].H, &pl.cols)) return DTS_ERR_UNSUPPORTED;  // see issue_batch
     }
     const size_t need = dts_batched_workspace_size(n, guides, params);
     if (params->iterations > 0 && (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < need))
@@ -993,7 +995,7 @@ extern "C" int dts_autotune(const dts_guide* guide, const dts_params* params, vo
     if (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.fwd_end) return DTS_ERR_WORKSPACE;
     if ((st = ensure_prepared())) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = bind_workspace(ws, L, s))) return st;
+    if ((st = bind_workspace(ws, L, guide->W, s))) return st;
     // real distances of this guide; the pass input is the iterate plane (any finite values)
     float* u = reinterpret_cast<float*>(ws_at(ws, L.u));
     if (cudaMemsetAsync(u, 0, L.plane_f32, s) != cudaSuccess) return DTS_ERR_CUDA;
@@ -1027,7 +1029,6 @@ extern "C" int dts_autotune(const dts_guide* guide, const dts_params* params, vo
         c.dst = u;
         c.d = ws_at(ws, L.dY);
         c.k2 = k2[0];
-        c.agg = nullptr;  // not the split kernel: the shape being chosen
         const float t = time_it([&] { return launch_col_pass(c, dh, PASS_PLAIN, cand[i], s); });
         cudaGetLastError();
         if (t > 0.f && t < best) {
@@ -1164,7 +1165,7 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
     if (!ws || ((uintptr_t)ws % kPlaneAlign) != 0 || ws_bytes < L.total) return DTS_ERR_WORKSPACE;
     if ((st = ensure_prepared())) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = bind_workspace(ws, L, s))) return st;
+    if ((st = bind_workspace(ws, L, guide->W, s))) return st;
     const int H = guide->H, W = guide->W, K = params->iterations, N = params->passes;
     const long long P = L.pitch;
     const int dh = params->dist_dtype == DTS_F16;
@@ -1244,9 +1245,9 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
             if (p % 2 == 1) {
                 b.d = ws_at(ws, L.dY);
                 b.dbar = dYb;
-                b.tot = plane(L.tot);
-                b.tot_chunks = L.tot_chunks;
-                b.tot_pitch = P;
+                b.chain_ctl = reinterpret_cast<unsigned*>(ws_at(ws, L.chain_ctl));
+                b.chain_agg = reinterpret_cast<float*>(ws_at(ws, L.chain_agg));
+                b.status = status_word();
                 if ((st = cuda_status(launch_col_bwd(b, dh, cb, s)))) return st;
             } else {
                 b.d = ws_at(ws, L.dX);
@@ -1286,9 +1287,10 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
 }
 
 extern "C" int dts_debug_inject(int kind) {
-    if (kind != 0 && kind != DTS_INJECT_TMA_SKIP) return DTS_ERR_INVALID_ARG;
+    if (kind != 0 && kind != DTS_INJECT_TMA_SKIP && kind != DTS_INJECT_CHAIN_SKIP && kind != DTS_INJECT_BARRIER_SKIP)
+        return DTS_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_prep_mutex);
-    g_inject_tma_skip = kind == DTS_INJECT_TMA_SKIP;
+    g_inject = kind;
     return DTS_OK;
 }
 

@@ -16,6 +16,8 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <algorithm>
+
 #include "dts_scan.cuh"
 
 namespace dts {
@@ -178,75 +180,24 @@ __global__ void __launch_bounds__(row_bwd_max_threads<ITEMS>()) row_bwd_kernel(B
 }
 
 // ---------------------------------------------------------------- vertical pass adjoint
-// Same layout as the forward vertical pass (lane = column, one cluster per 32-column strip).
-// Columns taller than one cluster are cut into chunks of CS x NW x ITEMS rows, one cluster each
-// (grid.y = CS x chunks).  Then the pass runs twice: chunk mode 1 writes each chunk's total
-// transforms (prefix and suffix direction) to a.tot; chunk mode 2 composes the totals of the
-// chunks above and below into every segment's carries and replays.  Mode 0: a single chunk.
+// Same layout as the forward vertical pass (lane = column): one cluster per 32-column strip
+// (col_bwd_kernel), or a chain of CTAs per strip linked through global memory for taller
+// columns (col_bwd_chain_kernel, chain_exchange).
+
+// the distance gradient is read-modified-written at the end: lane j brings row j of the warp's
+// rows into L2 now (one 128-byte line per row of the strip)
 template <int ITEMS>
-constexpr int bwd_col_max_threads() {
-    return 512;
-}
-inline int bwd_col_max_threads_host(int) { return 512; }
-
-// two resident CTAs of the 8-row shape (64 registers)
-template <int ITEMS>
-constexpr int bwd_col_min_blocks() {
-    return ITEMS <= 8 ? 2 : 1;
+__device__ __forceinline__ void col_bwd_prefetch(const BwdArgs& a, int row0, int c0, int lane) {
+    if (lane < ITEMS && row0 + lane < a.H && c0 < a.W) prefetch_l2(a.dbar + (long long)(row0 + lane) * a.pitch + c0);
 }
 
-// chunk totals in a.tot: plane f of chunk c at (c * kTotFields + f) * tot_pitch
-constexpr int kTotFields = 9;  // prefix: 2 x (A, B); suffix: (A, B, al, be, ga)
-
-__device__ __forceinline__ void store_tot_pre(const BwdArgs& a, int chunk, int col, const Pre2& p) {
-    float* t = a.tot + (long long)chunk * kTotFields * a.tot_pitch + col;
-    const long long q = a.tot_pitch;
-    t[0] = p.jk.A;
-    t[q] = p.jk.B;
-    t[2 * q] = p.hg.A;
-    t[3 * q] = p.hg.B;
-}
-__device__ __forceinline__ void store_tot_suf(const BwdArgs& a, int chunk, int col, const Coupled& f) {
-    float* t = a.tot + (long long)chunk * kTotFields * a.tot_pitch + col + 4 * a.tot_pitch;
-    const long long q = a.tot_pitch;
-    t[0] = f.A;
-    t[q] = f.B;
-    t[2 * q] = f.al;
-    t[3 * q] = f.be;
-    t[4 * q] = f.ga;
-}
-__device__ __forceinline__ Pre2 load_tot_pre(const BwdArgs& a, int chunk, int col) {
-    const float* t = a.tot + (long long)chunk * kTotFields * a.tot_pitch + col;
-    return Pre2{Aff{t[0], t[a.tot_pitch]}, Aff{t[2 * a.tot_pitch], t[3 * a.tot_pitch]}};
-}
-__device__ __forceinline__ Coupled load_tot_suf(const BwdArgs& a, int chunk, int col) {
-    const float* t = a.tot + (long long)chunk * kTotFields * a.tot_pitch + col + 4 * a.tot_pitch;
-    const long long q = a.tot_pitch;
-    return Coupled{t[0], t[q], t[2 * q], t[3 * q], t[4 * q]};
-}
-
-template <int ITEMS, bool DHALF, bool FOLD = false, bool CHUNKED = false>
-__global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_blocks<ITEMS>()) col_bwd_kernel(BwdArgs a) {
-    using M = BackwardMode;
-    __shared__ ColShared<M, 16> sh;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int NW = blockDim.x >> 5;
-    const int rank = (int)cluster.block_rank();
-    const int CS = (int)cluster.num_blocks();
-    const int chunk = CHUNKED ? (int)blockIdx.y / CS : 0;
-    const int col = blockIdx.x * 32 + lane;
-    const bool col_ok = col < a.W;
-    const int row0 = ((chunk * CS + rank) * NW + warp) * ITEMS;
+// A thread's positions of column `col` from row0: pass input x, weights w, incoming adjoint G
+// and pass output K (zero outside the plane), and wn, the weight entering the next segment.
+template <int ITEMS, bool DHALF>
+__device__ __forceinline__ void col_bwd_load(const BwdArgs& a, int row0, int col, float (&x)[ITEMS], float (&w)[ITEMS],
+                                             float (&G)[ITEMS], float (&K)[ITEMS], float& wn) {
     const long long P = a.pitch;
-
-    wait_predecessor();
-    // the distance gradient is read-modified-written at the end: lane j brings row j of the
-    // warp's rows into L2 now (one 128-byte line per row of the strip)
-    if (lane < ITEMS && row0 + lane < a.H && blockIdx.x * 32 < a.W)
-        prefetch_l2(a.dbar + (long long)(row0 + lane) * P + blockIdx.x * 32);
-    float x[ITEMS], w[ITEMS], G[ITEMS], K[ITEMS];
+    const bool col_ok = col < a.W;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int r = row0 + j;
@@ -257,44 +208,27 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_bloc
         G[j] = ok ? a.gin[idx] : 0.f;
         K[j] = ok ? a.kout[idx] : 0.f;
     }
-    float wn;
-    {
-        const int rn = row0 + ITEMS;
-        wn = (col_ok && rn < a.H) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)rn * P + col)) : 0.f;
-    }
+    const int rn = row0 + ITEMS;
+    wn = (col_ok && rn < a.H) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)rn * P + col)) : 0.f;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int r = row0 + j;
         w[j] = (col_ok && r > 0 && r < a.H) ? ex2(a.k2 * w[j]) : 0.f;
     }
+}
 
-    M::Pre own_pre, pre;
-    M::Suf own_suf, suf;
-    adjoint_local(x, w, wn, G, own_pre, own_suf);
-    if constexpr (FOLD) col_exchange<M, 16>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
-    else col_exchange_scan<M, 16>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
-    release_successor();
-    if (CHUNKED && a.chunk_mode == 1) {
-        // this chunk's totals: the inclusive prefix at its last segment, the inclusive suffix at
-        // its first
-        if (col_ok && rank == CS - 1 && warp == NW - 1) store_tot_pre(a, chunk, col, M::pre_compose(pre, own_pre));
-        if (col_ok && rank == 0 && warp == 0) store_tot_suf(a, chunk, col, M::suf_compose(own_suf, suf));
-        cluster_exit();
-        return;
-    }
-    if (CHUNKED && a.chunk_mode == 2 && col_ok) {
-        M::Pre ep = M::pre_identity();
-        for (int c = 0; c < chunk; ++c) ep = M::pre_compose(ep, load_tot_pre(a, c, col));
-        M::Suf es = M::suf_identity();
-        for (int c = a.nchunks - 1; c > chunk; --c) es = M::suf_compose(load_tot_suf(a, c, col), es);
-        pre = M::pre_compose(ep, pre);
-        suf = M::suf_compose(suf, es);
-    }
+// Given the carries (pre: everything above, suf: everything below), the segment's adjoint:
+// dL/dx into gout, ln(a) w dL/dw added into dbar.
+template <int ITEMS>
+__device__ __forceinline__ void col_bwd_finish(const BwdArgs& a, int row0, int col, float (&x)[ITEMS],
+                                               const float (&w)[ITEMS], float wn, float (&G)[ITEMS], float (&K)[ITEMS],
+                                               const Pre2& own_pre, const Pre2& pre, const Coupled& suf) {
+    const long long P = a.pitch;
+    const bool col_ok = col < a.W;
     const float jin = pre.jk.B;
     const float hin = pre.hg.B;
     const float gin = k_entering(suf, fmaf(own_pre.hg.A, hin, own_pre.hg.B));
     segment_adjoint(x, w, wn, G, K, jin, hin, gin, a.lna);
-
     // read every distance-gradient value before the first store (the stores could alias later
     // loads, which would otherwise wait for them one by one); K is free again
 #pragma unroll
@@ -310,7 +244,67 @@ __global__ void __launch_bounds__(bwd_col_max_threads<ITEMS>(), bwd_col_min_bloc
         a.dbar[idx] = K[j] + G[j];
         a.gout[idx] = x[j];
     }
+}
+
+// one cluster per strip: warp q of CTA r owns rows [(r NW + q) ITEMS, + ITEMS)
+template <int ITEMS>
+constexpr int bwd_col_min_blocks() {
+    return ITEMS <= 8 ? 2 : 1;  // two resident CTAs of the 8-row shape (64 registers)
+}
+
+template <int ITEMS, bool DHALF>
+__global__ void __launch_bounds__(512, bwd_col_min_blocks<ITEMS>()) col_bwd_kernel(BwdArgs a) {
+    using M = BackwardMode;
+    __shared__ ColShared<M, 16> sh;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int NW = blockDim.x >> 5;
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int col = blockIdx.x * 32 + lane;
+    const int row0 = (rank * NW + warp) * ITEMS;
+
+    wait_predecessor();
+    col_bwd_prefetch<ITEMS>(a, row0, blockIdx.x * 32, lane);
+    float x[ITEMS], w[ITEMS], G[ITEMS], K[ITEMS], wn;
+    col_bwd_load<ITEMS, DHALF>(a, row0, col, x, w, G, K, wn);
+    M::Pre own_pre, pre;
+    M::Suf own_suf, suf;
+    adjoint_local(x, w, wn, G, own_pre, own_suf);
+    col_exchange_scan<M, 16>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
+    release_successor();
+    col_bwd_finish<ITEMS>(a, row0, col, x, w, wn, G, K, own_pre, pre, suf);
     cluster_exit();
+}
+
+// chained: one CTA of NW warps per chunk of NW x ITEMS rows of a strip (strip and chunk from the
+// CTA's ticket)
+template <int ITEMS, int NW>
+constexpr int bwd_chain_min_blocks() {
+    return ITEMS * NW <= 64 ? 4 : 2;
+}
+
+template <int ITEMS, int NW, bool DHALF>
+__global__ void __launch_bounds__(32 * NW, bwd_chain_min_blocks<ITEMS, NW>()) col_bwd_chain_kernel(BwdArgs a, ChainArgs c) {
+    using M = BackwardMode;
+    __shared__ ChainShared<M, NW> sh;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+
+    wait_predecessor();
+    const int ticket = chain_ticket(c);
+    const int strip = ticket / c.J;
+    const int chunk = ticket - strip * c.J;
+    const int col = strip * 32 + lane;
+    const int row0 = (chunk * NW + warp) * ITEMS;
+    col_bwd_prefetch<ITEMS>(a, row0, strip * 32, lane);
+    float x[ITEMS], w[ITEMS], G[ITEMS], K[ITEMS], wn;
+    col_bwd_load<ITEMS, DHALF>(a, row0, col, x, w, G, K, wn);
+    M::Pre own_pre, pre;
+    M::Suf own_suf, suf;
+    adjoint_local(x, w, wn, G, own_pre, own_suf);
+    chain_exchange<M, NW>(own_pre, own_suf, lane, warp, NW, sh, c, ticket, pre, suf);
+    release_successor();
+    col_bwd_finish<ITEMS>(a, row0, col, x, w, wn, G, K, own_pre, pre, suf);
 }
 
 // ---------------------------------------------------------------- guide gradient
@@ -366,11 +360,15 @@ __global__ void __launch_bounds__(256) update_adjoint_kernel(BwdArgs a) {
     const long long idx = (long long)y * a.pitch + x0;
     const long long di = (long long)y * a.W + x0;
     const bool jac = a.update == DTS_UPDATE_JACOBI;
-    float g[4], cf[4], t[4], zz[4], gt[4] = {0.f, 0.f, 0.f, 0.f}, gc[4] = {0.f, 0.f, 0.f, 0.f};
+    // zz: zbar (Jacobi) or z_k (GD); zk: z_k where the Jacobi update's weight needs it
+    const bool need_zk = jac && a.eps > 0.f;
+    float g[4], cf[4], t[4], zz[4], zk[4] = {0.f, 0.f, 0.f, 0.f}, gt[4] = {0.f, 0.f, 0.f, 0.f},
+          gc[4] = {0.f, 0.f, 0.f, 0.f};
     if (VEC) {
         load4_f(a.gz, idx, g);
         load4_f(a.c, di, cf);
         load4_f(jac ? a.x : a.zk, idx, zz);
+        if (need_zk) load4_f(a.zk, idx, zk);
         if (a.gt) load4_f(a.gt, di, gt);
         if (a.gc) load4_f(a.gc, di, gc);
 #pragma unroll
@@ -382,6 +380,7 @@ __global__ void __launch_bounds__(256) update_adjoint_kernel(BwdArgs a) {
             g[k] = ok ? a.gz[idx + k] : 0.f;
             cf[k] = ok ? a.c[di + k] : 0.f;
             zz[k] = ok ? (jac ? a.x : a.zk)[idx + k] : 0.f;
+            if (need_zk && ok) zk[k] = a.zk[idx + k];
             t[k] = ok ? load_any(a.t, di + k, a.t_dtype) : 0.f;
             if (a.gt && ok) gt[k] = a.gt[di + k];
             if (a.gc && ok) gc[k] = a.gc[di + k];
@@ -391,12 +390,22 @@ __global__ void __launch_bounds__(256) update_adjoint_kernel(BwdArgs a) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         if (jac) {
-            const float den = a.lambda + cf[k];
+            // c~ = c w, w = 1 / sqrt(r^2 + eps^2) at r = z_k - t for the Charbonnier loss (w = 1 for
+            // the square); c~ reaches z_k and t through r: dc~/dr = -c r w^3
+            float w = 1.f, r = 0.f;
+            if (a.eps > 0.f) {
+                r = zk[k] - t[k];
+                w = rsqrtf(fmaf(r, r, a.eps * a.eps));
+            }
+            const float cw = cf[k] * w;
+            const float den = a.lambda + cw;
             if (den != 0.f) {
+                const float gcw = a.lambda * (t[k] - zz[k]) / (den * den) * g[k];
+                const float gr = a.eps > 0.f ? -cf[k] * r * w * w * w * gcw : 0.f;
                 dzb[k] = a.lambda / den * g[k];
-                gt[k] += cf[k] / den * g[k];
-                gc[k] += a.lambda * (t[k] - zz[k]) / (den * den) * g[k];
-                dz[k] = 0.f;
+                gt[k] += cw / den * g[k] - gr;
+                gc[k] += w * gcw;
+                dz[k] = gr;
             } else {
                 dzb[k] = 0.f;
                 dz[k] = g[k];
@@ -454,38 +463,44 @@ cudaError_t launch_row_bwd_t(const BwdArgs& a, bool final_pass, const RowPlan& p
 
 template <int ITEMS, bool DHALF>
 cudaError_t launch_col_bwd_t(const BwdArgs& a, const ColPlan& p, cudaStream_t s) {
-    const int rows = ITEMS * p.warps * p.cluster;  // one chunk
-    const int nch = (a.H + rows - 1) / rows;
-    const dim3 grid((unsigned)((a.W + 31) / 32), (unsigned)(p.cluster * nch), 1);
-    const dim3 block((unsigned)(32 * p.warps));
-    static const bool fold = getenv("DTS_BWD_FOLD") != nullptr;  // tuning aid
-    if (nch == 1) {
-        auto kernel = fold ? col_bwd_kernel<ITEMS, DHALF, true> : col_bwd_kernel<ITEMS, DHALF, false>;
-        BwdArgs b = a;
-        b.chunk_mode = 0;
-        return launch_ex(kernel, grid, block, p.cluster, s, b);
-    }
-    if (!a.tot || a.tot_chunks < nch) return cudaErrorInvalidValue;
-    auto kernel = col_bwd_kernel<ITEMS, DHALF, false, true>;
-    BwdArgs b = a;
-    b.nchunks = nch;
-    b.chunk_mode = 1;
-    cudaError_t e = launch_ex(kernel, grid, block, p.cluster, s, b);
-    if (e != cudaSuccess) return e;
-    b.chunk_mode = 2;
-    return launch_ex(kernel, grid, block, p.cluster, s, b);
+    if (p.cluster < 1 || (long long)ITEMS * p.warps * p.cluster < a.H) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((a.W + 31) / 32), (unsigned)p.cluster, 1);
+    return launch_ex(col_bwd_kernel<ITEMS, DHALF>, grid, dim3((unsigned)(32 * p.warps)), p.cluster, s, a);
+}
+
+// chunks per staging block of the strip composition (two resident CTAs per SM)
+constexpr int kBwdChainStage = 64;
+
+template <int ITEMS, int NW, bool DHALF>
+cudaError_t allow_bwd_chain_smem() {
+    return cudaFuncSetAttribute((const void*)col_bwd_chain_kernel<ITEMS, NW, DHALF>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)chain_stage_bytes<BackwardMode>(kBwdChainStage));
+}
+
+// refused (invalid configuration) when fewer than 2 J CTAs of the kernel fit on the GPU at once
+template <int ITEMS, int NW, bool DHALF>
+cudaError_t launch_col_bwd_chain_t(const BwdArgs& a, cudaStream_t s) {
+    auto kernel = col_bwd_chain_kernel<ITEMS, NW, DHALF>;
+    ChainArgs c = {};
+    c.ctl = a.chain_ctl;
+    c.agg = a.chain_agg;
+    c.J = (a.H + ITEMS * NW - 1) / (ITEMS * NW);
+    c.S = (a.W + 31) / 32;
+    c.status = a.status;
+    if (!c.ctl || !c.agg || c.J > kChainMaxChunks) return cudaErrorInvalidValue;
+    c.stage = std::min(c.J, kBwdChainStage);
+    const size_t smem = chain_stage_bytes<BackwardMode>(c.stage);
+    if (blocks_per_sm((const void*)kernel, 32 * NW, smem) * sm_count() < 2 * c.J) return cudaErrorInvalidConfiguration;
+    const bool skip = take_injected(DTS_INJECT_CHAIN_SKIP);
+    c.timeout = skip ? kInjectedTimeout : default_timeout_cycles();
+    c.skip_ticket = skip && c.J > 1 ? 0 : -1;
+    return launch_ex_smem(kernel, dim3((unsigned)(c.S * c.J)), dim3(32 * NW), 0, smem, s, a, c);
 }
 
 template <int ITEMS, bool DHALF>
 cudaError_t allow_bwd_clusters() {
-    cudaError_t e = cudaSuccess;
-    const void* fs[3] = {(const void*)col_bwd_kernel<ITEMS, DHALF, false>, (const void*)col_bwd_kernel<ITEMS, DHALF, true>,
-                         (const void*)col_bwd_kernel<ITEMS, DHALF, false, true>};
-    for (const void* f : fs) {
-        const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (r != cudaSuccess) e = r;
-    }
-    return e;
+    return cudaFuncSetAttribute((const void*)col_bwd_kernel<ITEMS, DHALF>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 }  // namespace
@@ -505,25 +520,13 @@ bool plan_rows_bwd(int W, RowPlan* p) {
     return true;
 }
 
-// Backward vertical plan (CTA at most bwd_col_max_threads): one cluster for columns up to 4096
-// rows, chunks of 2048 rows above (bwd_col_chunks).
+// chain shapes of the vertical adjoint (rows per thread, warps per CTA), the default first
+constexpr int kBwdChainShapes[][2] = {{8, 16}, {8, 8}, {16, 8}};
+
+// Backward vertical plan: one cluster for columns up to 4096 rows (measured on the 2880 x 1988
+// stereo workload: 16 rows x 16 warps in clusters of 8 is fastest), a chain above.
 bool plan_cols_bwd(int H, ColPlan* p) {
-    // DTS_BWD_COL_PLAN="items,warps" overrides the shape (tuning aid)
-    static const char* env = getenv("DTS_BWD_COL_PLAN");
-    if (env) {
-        int it = 0, nw = 0;
-        if (sscanf(env, "%d,%d", &it, &nw) == 2 && (it == 8 || it == 16) && nw >= 1 && (nw & (nw - 1)) == 0 &&
-            nw * 32 <= bwd_col_max_threads_host(it)) {
-            const int cs = (H + it * nw - 1) / (it * nw);
-            if (cs <= 16) {
-                p->items = it;
-                p->warps = nw;
-                p->cluster = cs;
-                return true;
-            }
-        }
-    }
-    // measured on the 2880 x 1988 stereo workload: 16 rows x 16 warps (clusters of 8) is fastest
+    if (H > kMaxColRows) return false;
     static const int cand[][2] = {{16, 16}, {8, 16}, {16, 8}, {8, 8}};
     if (H <= 128) {
         int nw = 1;
@@ -545,14 +548,10 @@ bool plan_cols_bwd(int H, ColPlan* p) {
             }
         }
     }
-    // taller columns: chunks of 2048 rows (16 x 16 x 8), two launches per pass
-    if (H <= kBwdMaxRows) {
-        p->items = 16;
-        p->warps = 16;
-        p->cluster = 8;
-        return true;
-    }
-    return false;
+    p->items = kBwdChainShapes[0][0];
+    p->warps = kBwdChainShapes[0][1];
+    p->cluster = -1;
+    return (H + p->items * p->warps - 1) / (p->items * p->warps) <= kChainMaxChunks;
 }
 
 cudaError_t launch_row_bwd(const BwdArgs& a, int dist_half, bool final_pass, const RowPlan& p, cudaStream_t s) {
@@ -566,19 +565,21 @@ cudaError_t launch_row_bwd(const BwdArgs& a, int dist_half, bool final_pass, con
     return e;
 }
 
-int bwd_col_chunks(int H) {
-    ColPlan p;
-    if (!plan_cols_bwd(H, &p)) return 0;
-    const int rows = p.items * p.warps * p.cluster;
-    const int n = (H + rows - 1) / rows;
-    return n > 1 ? n : 0;
-}
-
 cudaError_t launch_col_bwd(const BwdArgs& a, int dist_half, const ColPlan& p, cudaStream_t s) {
-    const int h = prof_begin(KID_COL_BWD, (long long)a.H * a.W, dist_half ? kFlagDistHalf : 0, s);
+    const int h = prof_begin(p.cluster < 0 ? KID_COL_BWD_CHAIN : KID_COL_BWD, (long long)a.H * a.W,
+                             dist_half ? kFlagDistHalf : 0, s);
     cudaError_t e = cudaErrorInvalidValue;
-    if (p.items == 8) e = dist_half ? launch_col_bwd_t<8, true>(a, p, s) : launch_col_bwd_t<8, false>(a, p, s);
-    if (p.items == 16) e = dist_half ? launch_col_bwd_t<16, true>(a, p, s) : launch_col_bwd_t<16, false>(a, p, s);
+    if (p.cluster < 0) {
+        if (p.items == 8 && p.warps == 16)
+            e = dist_half ? launch_col_bwd_chain_t<8, 16, true>(a, s) : launch_col_bwd_chain_t<8, 16, false>(a, s);
+        if (p.items == 8 && p.warps == 8)
+            e = dist_half ? launch_col_bwd_chain_t<8, 8, true>(a, s) : launch_col_bwd_chain_t<8, 8, false>(a, s);
+        if (p.items == 16 && p.warps == 8)
+            e = dist_half ? launch_col_bwd_chain_t<16, 8, true>(a, s) : launch_col_bwd_chain_t<16, 8, false>(a, s);
+    } else {
+        if (p.items == 8) e = dist_half ? launch_col_bwd_t<8, true>(a, p, s) : launch_col_bwd_t<8, false>(a, p, s);
+        if (p.items == 16) e = dist_half ? launch_col_bwd_t<16, true>(a, p, s) : launch_col_bwd_t<16, false>(a, p, s);
+    }
     prof_end(h, s);
     return e;
 }
@@ -629,6 +630,12 @@ cudaError_t prepare_backward_kernels() {
     if ((r = allow_bwd_clusters<8, true>()) != cudaSuccess) e = r;
     if ((r = allow_bwd_clusters<16, false>()) != cudaSuccess) e = r;
     if ((r = allow_bwd_clusters<16, true>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_chain_smem<8, 16, false>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_chain_smem<8, 16, true>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_chain_smem<8, 8, false>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_chain_smem<8, 8, true>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_chain_smem<16, 8, false>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_chain_smem<16, 8, true>()) != cudaSuccess) e = r;
     return e;
 }
 

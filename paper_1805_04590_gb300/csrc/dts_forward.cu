@@ -27,6 +27,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <algorithm>
 #include <map>
 #include <string>
 #include <mutex>
@@ -550,57 +551,28 @@ __global__ void __launch_bounds__(row_max_threads<ITEMS, KIND>(), row_min_blocks
 }
 
 // ---------------------------------------------------------------- vertical pass
-// Grid (ceil(W/32), cluster) with cluster dims (1, cluster, 1): one cluster per strip of 32
-// columns covering all H rows.  Lane = column (128-byte coalesced row segments); warp q of CTA
-// r owns rows [(r*NW + q)*ITEMS, +ITEMS).  The segments of a column are the warps of all CTAs of
-// the cluster: one shared-memory round inside a CTA, one distributed-shared-memory round
-// across CTAs.
-// KIND: PASS_PLAIN (CoupledMode, store), PASS_UPDATE (CoupledMode, then z_{k+1} from z_k, t, c
-// and zbar) or PASS_SUPPORT_CONF (SupportMode on the row support s, then chat = c s_flat / S).
-template <int ITEMS>
-constexpr int col_max_threads() {
-    return ITEMS <= 8 ? 1024 : 512;
-}
-// resident CTAs of the largest shape the register budget must allow (the update epilogue keeps
-// its operand loads in flight and gets the larger budget)
-template <int ITEMS, int KIND>
-constexpr int col_min_blocks() {
-    return ITEMS == 16 ? 2 : 1;
-}
+// Lane = column (128-byte coalesced row segments); a warp owns ITEMS consecutive rows of 32
+// columns.  The segments of a column are the warps of the CTAs that hold it: one shared-memory
+// round inside a CTA, then one round across CTAs -- in distributed shared memory between the
+// CTAs of a cluster (col_pass_kernel), or through global memory along a chain of CTAs
+// (col_chain_kernel, chain_exchange).
+// KIND: PASS_PLAIN (CoupledMode, store), PASS_SUPPORT_CONF (SupportMode on the row support s,
+// then chat = c s_flat / S) or PASS_TRANSPOSE (TransposeMode, on zk - src when a.zk is set).  The
+// data-term update is applied by the horizontal passes.
+template <int KIND>
+using ColMode = typename std::conditional<KIND == PASS_SUPPORT_CONF, SupportMode,
+                                          typename std::conditional<KIND == PASS_TRANSPOSE, TransposeMode,
+                                                                    CoupledMode>::type>::type;
 
+// A thread's ITEMS positions of column `col` from row0 (zero outside the plane) and their
+// weights w = a^d (0 outside the plane and at the column start), and wn, the weight entering
+// the next segment.  The transposed pass with a minuend filters zk - src.
 template <int ITEMS, bool DHALF, int KIND>
-__global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS, KIND>()) col_pass_kernel(PassArgs a) {
-    using M = typename std::conditional<KIND == PASS_SUPPORT_CONF, SupportMode,
-                                        typename std::conditional<KIND == PASS_TRANSPOSE, TransposeMode,
-                                                                  CoupledMode>::type>::type;
-    __shared__ ColShared<M, 32> sh;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int NW = blockDim.x >> 5;
-    const int rank = (int)cg::this_cluster().block_rank();
-    const int col = blockIdx.x * 32 + lane;
-    const bool col_ok = col < a.W;
-    const int row0 = (rank * NW + warp) * ITEMS;
-    const long long P = a.pitch;
-
-    wait_predecessor();
-    if constexpr (KIND == PASS_UPDATE) {
-        // the update operands are read only at the end: start bringing them into L2 now, lane j
-        // taking row j of the warp's rows (each prefetch covers the warp's 128-byte row segment)
-        const int c0 = blockIdx.x * 32;
-        const int tsz = a.t_dtype == DTS_F32 ? 4 : 2;
-        for (int j = lane; j < ITEMS; j += 32) {
-            const int r = row0 + j;
-            if (r < a.H) {
-                prefetch_l2(a.zk + (long long)r * P + c0);
-                prefetch_l2(static_cast<const char*>(a.t) + ((long long)r * a.W + c0) * tsz);
-                prefetch_l2(a.c + (a.c_pitched ? (long long)r * P : (long long)r * a.W) + c0);
-            }
-        }
-    }
-
+__device__ __forceinline__ void col_load(const PassArgs& a, int row0, int col, float (&x)[ITEMS], float (&w)[ITEMS],
+                                         float& wn) {
     using DT = typename std::conditional<DHALF, __half, float>::type;
-    float x[ITEMS], w[ITEMS];
+    const long long P = a.pitch;
+    const bool col_ok = col < a.W;
     const bool full = col_ok && row0 + ITEMS <= a.H;
     {
         const float* ps = a.src + (long long)row0 * P + col;
@@ -634,7 +606,6 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
             }
         }
     }
-    float wn;
     {
         const int rn = row0 + ITEMS;
         wn = (col_ok && rn < a.H) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)rn * P + col)) : 0.f;
@@ -647,18 +618,16 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
             if (!(col_ok && row0 + j < a.H)) w[j] = 0.f;
     }
     if (row0 == 0) w[0] = 0.f;  // the column starts here
+}
 
-    typename M::Pre own_pre, pre;
-    typename M::Suf own_suf, suf;
-    M::local(x, w, wn, own_pre, own_suf);
-    col_exchange<M, 32>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
-    release_successor();
-    M::apply(x, w, wn, own_pre, pre.B, suf);
-
-    // ---- epilogue
+// The pass result x of a thread's positions: stored (plain, transposed), or the support-weighted
+// confidence into zout.
+template <int ITEMS, int KIND>
+__device__ __forceinline__ void col_store(const PassArgs& a, int row0, int col, const float (&x)[ITEMS]) {
+    const bool col_ok = col < a.W;
     if constexpr (KIND == PASS_PLAIN || KIND == PASS_TRANSPOSE) {
         float* pdst = a.dst + (long long)row0 * a.dst_pitch + col;
-        if (full) {
+        if (col_ok && row0 + ITEMS <= a.H) {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) {
                 *pdst = x[j];
@@ -671,39 +640,83 @@ __global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS
                 pdst += a.dst_pitch;
             }
         }
-        cluster_exit();
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const int r = row0 + j;
-        if (!(col_ok && r < a.H)) continue;
-        const long long idx = (long long)r * P + col;
-        if constexpr (KIND == PASS_PLAIN) {
-            a.dst[(long long)r * a.dst_pitch + col] = x[j];
-        } else if constexpr (KIND == PASS_UPDATE) {
-            const long long di = (long long)r * a.W + col;
-            const float zb = x[j];
-            const float z = a.zk[idx];
-            const float t = load_any(a.t, di, a.t_dtype);
-            const float cf = a.c_pitched ? a.c[idx] : a.c[di];
-            float zn;
-            if (a.update == DTS_UPDATE_JACOBI) {
-                const float den = a.lambda + cf;
-                zn = den != 0.f ? (a.lambda * zb + cf * t) / den : z;
-            } else {
-                float eta = a.step;
-                if (a.clamp_step && a.lambda + cf > 0.f) eta = fminf(eta, 1.f / (a.lambda + cf));
-                zn = z - eta * (a.lambda * (z - zb) + cf * target_slope(z - t, a.eps));
-            }
-            a.zout[(long long)r * a.zout_pitch + col] = zn;
-        } else {
-            a.zout[idx] = a.c[(long long)r * a.W + col] * a.s_flat / x[j];
+        for (int j = 0; j < ITEMS; ++j) {
+            const int r = row0 + j;
+            if (!(col_ok && r < a.H)) continue;
+            a.zout[(long long)r * a.pitch + col] = a.c[(long long)r * a.W + col] * a.s_flat / x[j];
         }
     }
+}
+
+// Grid (ceil(W/32), cluster) with cluster dims (1, cluster, 1): one cluster per strip of 32
+// columns covering all H rows; warp q of CTA r owns rows [(r*NW + q)*ITEMS, +ITEMS).
+template <int ITEMS>
+constexpr int col_max_threads() {
+    return ITEMS <= 8 ? 1024 : 512;
+}
+// resident CTAs of the largest shape the register budget must allow
+template <int ITEMS, int KIND>
+constexpr int col_min_blocks() {
+    return ITEMS == 16 ? 2 : 1;
+}
+
+template <int ITEMS, bool DHALF, int KIND>
+__global__ void __launch_bounds__(col_max_threads<ITEMS>(), col_min_blocks<ITEMS, KIND>()) col_pass_kernel(PassArgs a) {
+    using M = ColMode<KIND>;
+    __shared__ ColShared<M, 32> sh;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int NW = blockDim.x >> 5;
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int col = blockIdx.x * 32 + lane;
+    const int row0 = (rank * NW + warp) * ITEMS;
+
+    wait_predecessor();
+    float x[ITEMS], w[ITEMS], wn;
+    col_load<ITEMS, DHALF, KIND>(a, row0, col, x, w, wn);
+    typename M::Pre own_pre, pre;
+    typename M::Suf own_suf, suf;
+    M::local(x, w, wn, own_pre, own_suf);
+    col_exchange<M, 32>(own_pre, own_suf, lane, warp, NW, sh, pre, suf);
+    release_successor();
+    M::apply(x, w, wn, own_pre, pre.B, suf);
+    col_store<ITEMS, KIND>(a, row0, col, x);
     cluster_exit();
 }
 
+// Chained vertical pass (columns of any height up to the chain's limit): one CTA of NW warps per
+// chunk of NW x ITEMS rows of a 32-column strip, the chunks of a strip linked through global
+// memory (chain_exchange); the CTA's strip and chunk come from its ticket.
+template <int ITEMS, int NW>
+constexpr int chain_min_blocks() {
+    return ITEMS * NW <= 128 ? 4 : 2;
+}
+
+template <int ITEMS, int NW, bool DHALF, int KIND>
+__global__ void __launch_bounds__(32 * NW, chain_min_blocks<ITEMS, NW>()) col_chain_kernel(PassArgs a, ChainArgs c) {
+    using M = ColMode<KIND>;
+    __shared__ ChainShared<M, NW> sh;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+
+    wait_predecessor();
+    const int ticket = chain_ticket(c);
+    const int strip = ticket / c.J;
+    const int chunk = ticket - strip * c.J;
+    const int col = strip * 32 + lane;
+    const int row0 = (chunk * NW + warp) * ITEMS;
+    float x[ITEMS], w[ITEMS], wn;
+    col_load<ITEMS, DHALF, KIND>(a, row0, col, x, w, wn);
+    typename M::Pre own_pre, pre;
+    typename M::Suf own_suf, suf;
+    M::local(x, w, wn, own_pre, own_suf);
+    chain_exchange<M, NW>(own_pre, own_suf, lane, warp, NW, sh, c, ticket, pre, suf);
+    release_successor();
+    M::apply(x, w, wn, own_pre, pre.B, suf);
+    col_store<ITEMS, KIND>(a, row0, col, x);
+}
 
 // ---------------------------------------------------------------- strip vertical pass (no cluster)
 // CTA = NW <= 32 warps over a strip of 8 columns and the whole column height.  Lane l of warp q
@@ -719,7 +732,8 @@ struct StripShared {
     typename M::Suf suf[kStripWarps][kStripCols + 1];
 };
 
-// pre / suf: the transforms of everything above / below this thread's segment in its column
+// pre / suf: the transforms of everything above / below this thread's segment in its column.
+// Shared-memory writes made before the call are visible to every thread after it.
 template <class M>
 __device__ __forceinline__ void strip_exchange(const typename M::Pre& own_pre, const typename M::Suf& own_suf,
                                                int lane, int warp, int NW, int cl, int sw, StripShared<M>& sh,
@@ -867,12 +881,18 @@ __host__ __device__ constexpr int strip_slab_bytes() {
     return 2 * strip_x_bytes<ITEMS, DHALF>() + strip_d_bytes<ITEMS, DHALF>();
 }
 
-// TR: the transposed pass (TransposeMode), with the optional minuend a.zk (zk - src is filtered)
+// TR: the transposed pass (TransposeMode), with the optional minuend a.zk (zk - src is filtered).
+// Waits on a warp's slab barrier are bounded (timeout cycles).  A wait that gives up records
+// DTS_ERR_TIMEOUT; that warp issues no further loads into its region (the late copy may still
+// land there), the CTA finishes the strip at hand with what it holds (the results are invalid,
+// the status says so) and leaves the strip loop, after one more bounded wait for every load of
+// its own still in flight.  skip (fault injection): warp 0 of CTA 0 leaves out its first load.
 template <int ITEMS, bool DHALF, bool TR = false>
 __global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const __grid_constant__ CUtensorMap tm_x,
                                                                           const __grid_constant__ CUtensorMap tm_d,
                                                                           const __grid_constant__ CUtensorMap tm_o,
-                                                                          PassArgs a, int nstrips, long long timeout) {
+                                                                          PassArgs a, int nstrips, long long timeout,
+                                                                          int skip) {
     static_assert(ITEMS % 2 == 1, "odd segment length (bank-conflict-free column accesses)");
     static_assert(strip_x_bytes<ITEMS, DHALF>() % 128 == 0, "slab alignment");
     using M = typename std::conditional<TR, TransposeMode, CoupledMode>::type;
@@ -880,6 +900,11 @@ __global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const _
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ StripShared<M> sh;
     __shared__ __align__(8) uint64_t bar[kStripWarps];
+    __shared__ int s_failed[kStripWarps];  // a wait of this warp gave up
+    // a wait of the CTA gave up in an iteration of this parity: the CTA leaves the strip loop (a
+    // slot per parity, so that a failure in the next iteration cannot change what a slower warp
+    // reads for this one)
+    __shared__ int s_abort[2];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int NW = blockDim.x >> 5;
@@ -896,8 +921,10 @@ __global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const _
     if (lane == 0) {
         mbar_init(&bar[warp], 1);
         mbar_init_fence();
+        s_failed[warp] = 0;
     }
-    __syncwarp();
+    if (threadIdx.x < 2) s_abort[threadIdx.x] = 0;
+    __syncthreads();
     wait_predecessor();
     // the slab's distances: one contiguous bulk copy from the strip-tiled plane when there is one,
     // else a TMA box (full boxes count, the parts outside the plane included: they read as zero)
@@ -912,14 +939,18 @@ __global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const _
         else
             tma_load_2d((void*)sd, &tm_d, strip * kStripCols, slab_row, &bar[warp]);
     };
-    if (lane == 0 && (int)blockIdx.x < nstrips) load_slab(blockIdx.x);
+    if (lane == 0 && (int)blockIdx.x < nstrips && !(skip && blockIdx.x == 0 && warp == 0)) load_slab(blockIdx.x);
     int it = 0;
     for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x, ++it) {
         const int next = strip + gridDim.x;
         const int col = strip * kStripCols + cl;
         const bool col_ok = col < a.W;
-        if (!mbar_wait_bounded(&bar[warp], (uint32_t)(it & 1), timeout) && lane == 0)
-            atomicExch(a.status, DTS_ERR_TIMEOUT);
+        const int failed = !mbar_wait_bounded(&bar[warp], (uint32_t)(it & 1), timeout);
+        if (failed) {
+            record_status(a.status, DTS_ERR_TIMEOUT);
+            s_failed[warp] = 1;
+            s_abort[it & 1] = 1;
+        }
         float x[ITEMS], w[ITEMS];
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
@@ -937,7 +968,7 @@ __global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const _
         // the reads above come before the next strip's TMA writes into the same region
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0 && next < nstrips) load_slab(next);
+        if (lane == 0 && next < nstrips && !s_failed[warp]) load_slab(next);
         const float wn = (col_ok && row0 + ITEMS < a.H) ? ex2(a.k2 * dn) : 0.f;
         const bool full = col_ok && row0 + ITEMS <= a.H;
 #pragma unroll
@@ -953,6 +984,7 @@ __global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const _
         typename M::Suf own_suf, suf;
         M::local(x, w, wn, own_pre, own_suf);
         strip_exchange<M>(own_pre, own_suf, lane, warp, NW, cl, sw, sh, pre, suf);
+        const bool abort = s_abort[it & 1] != 0;  // CTA-uniform (set before the exchange's barriers)
         if (next >= nstrips) release_successor();
         M::apply(x, w, wn, own_pre, pre.B, suf);
 
@@ -967,240 +999,17 @@ __global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const _
             tma_store_2d(&tm_o, strip * kStripCols, slab_row, so);
             bulk_commit();
         }
+        if (abort) {
+            // a load still in flight (the one a wait gave up on, or the next strip's) must land
+            // before the CTA's shared memory goes to another CTA
+            if (lane == 0) {
+                if (s_failed[warp]) mbar_wait_bounded(&bar[warp], (uint32_t)(it & 1), timeout);
+                else if (next < nstrips) mbar_wait_bounded(&bar[warp], (uint32_t)((it + 1) & 1), timeout);
+            }
+            break;
+        }
     }
     if (lane == 0) bulk_wait_read();
-}
-
-// ---------------------------------------------------------------- persistent horizontal pass
-// Persistent CTAs loop over groups of rpb rows; the next group's positions and distances are
-// loaded into a second register set while the current group is exchanged and replayed, so the
-// memory pipe stays busy through the compute.  Same thread layout as row_pass_kernel.
-// largest CTA of the persistent horizontal pass (the prefetch registers double the data)
-template <int ITEMS>
-constexpr int row_persist_max_threads() {
-    return ITEMS <= 8 ? 1024 : 512;
-}
-
-template <int ITEMS, bool DHALF, int KIND, bool PREFETCH>
-__global__ void __launch_bounds__(PREFETCH ? row_persist_max_threads<ITEMS>() : 1024) row_persist_kernel(PassArgs a, int tpr, int ngroups) {
-    static_assert(ITEMS % 4 == 0, "ITEMS must be a multiple of 4");
-    using M = typename std::conditional<KIND == PASS_SUPPORT, SupportMode, CoupledMode>::type;
-    __shared__ typename M::Pre s_pre[2][32];
-    __shared__ typename M::Suf s_suf[2][32];
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int warp = tid >> 5;
-    const int rloc = tid / tpr;
-    const int t = tid - rloc * tpr;
-    const int wpr = tpr >> 5;
-    const int wrow = t >> 5;
-    const int wbase = warp - wrow;
-    const int rpb = blockDim.x / tpr;
-    const int e0 = t * ITEMS;
-    const long long P = a.pitch;
-
-    float xn[ITEMS], dn[ITEMS];
-    auto load = [&](int grp) {
-        const int row = grp * rpb + rloc;
-        if (row < a.H && e0 < P) {
-            const long long base = (long long)row * P + e0;
-#pragma unroll
-            for (int q = 0; q < ITEMS / 4; ++q) {
-                if constexpr (KIND != PASS_SUPPORT) load4_f(a.src, base + 4 * q, &xn[4 * q]);
-                load4_d<DHALF>(a.d, base + 4 * q, &dn[4 * q]);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) xn[j] = dn[j] = 0.f;
-        }
-    };
-
-    wait_predecessor();
-    int g = blockIdx.x;
-    if (PREFETCH && g < ngroups) load(g);
-    for (int it = 0; g < ngroups; g += gridDim.x, ++it) {
-        if (!PREFETCH) load(g);
-        float x[ITEMS], w[ITEMS];
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            x[j] = KIND == PASS_SUPPORT ? 1.f : xn[j];
-            w[j] = dn[j];
-        }
-        const int gnext = g + gridDim.x;
-        if (PREFETCH && gnext < ngroups) load(gnext);
-        if (gnext >= ngroups) release_successor();
-
-        const int row = g * rpb + rloc;
-        const bool row_ok = row < a.H;
-        const long long base = (long long)row * P + e0;
-        const bool live = row_ok && e0 < P;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) w[j] = ex2(a.k2 * w[j]);
-        if (!live || e0 + ITEMS > a.W) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j)
-                if (!live || e0 + j >= a.W) x[j] = w[j] = 0.f;
-        }
-        if (e0 == 0) w[0] = 0.f;
-        float wn = __shfl_down_sync(kFull, w[0], 1);
-        if (lane == 31) {
-            const int en = e0 + ITEMS;
-            wn = (row_ok && en < a.W) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)row * P + en)) : 0.f;
-        }
-        typename M::Pre own_pre, pre;
-        typename M::Suf own_suf, suf;
-        M::local(x, w, wn, own_pre, own_suf);
-        row_exchange<M>(own_pre, own_suf, lane, warp, wrow, wbase, wpr, s_pre[it & 1], s_suf[it & 1], pre, suf);
-        M::apply(x, w, wn, own_pre, pre.B, suf);
-        if (live) {
-#pragma unroll
-            for (int q = 0; q < ITEMS / 4; ++q) store4_f(a.dst, base + 4 * q, &x[4 * q]);
-        }
-    }
-}
-
-// ---------------------------------------------------------------- persistent TMA vertical pass
-// One cluster of CS CTAs per strip of 32 columns, looping over strips (persistent grid).  CTA r
-// owns rows [r R, r R + R) of the strip, R = NW * ITEMS; its tile of the pass input and of the
-// distances arrives by 2-D TMA into one of two shared-memory stages, the next strip's tile
-// streaming in while the current one is exchanged and replayed.  Lane = column, warp q holds rows
-// [q ITEMS, q ITEMS + ITEMS) of the tile: every shared-memory row read is 128 contiguous bytes.
-// Waits on the stage barriers are bounded (a.timeout cycles); a wait that gives up records
-// DTS_ERR_TIMEOUT in the status word and the CTA carries on (every barrier is still executed).
-// KIND: PASS_PLAIN or PASS_UPDATE (as in col_pass_kernel).
-constexpr int kTmaColMaxWarps = 8;
-
-template <int ITEMS, bool DHALF>
-constexpr size_t tma_stage_bytes(int NW) {
-    return (size_t)NW * ITEMS * 32 * (4 + (DHALF ? 2 : 4));
-}
-
-// register budget: three resident CTAs of 8 warps up to 16 rows per thread, two beyond
-template <int ITEMS>
-constexpr int tma_col_min_blocks() {
-    return ITEMS <= 16 ? 3 : 2;
-}
-
-template <int ITEMS, bool DHALF, int KIND>
-__global__ void __launch_bounds__(32 * kTmaColMaxWarps, tma_col_min_blocks<ITEMS>()) col_tma_kernel(const __grid_constant__ CUtensorMap tm_x,
-                                                                      const __grid_constant__ CUtensorMap tm_d,
-                                                                      PassArgs a, int nstrips, long long timeout,
-                                                                      int skip_first) {
-    using M = CoupledMode;
-    using DT = typename std::conditional<DHALF, __half, float>::type;
-    extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ ColShared<M, kTmaColMaxWarps> sh;
-    __shared__ __align__(8) uint64_t bar[2];
-
-    cg::cluster_group cluster = cg::this_cluster();
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int NW = blockDim.x >> 5;
-    const int R = NW * ITEMS;
-    const int rank = (int)cluster.block_rank();
-    const int CS = (int)cluster.num_blocks();
-    const int tile_row = rank * R;
-    const int row0 = tile_row + warp * ITEMS;
-    const long long P = a.pitch;
-    const size_t xbytes = (size_t)R * 32 * 4;
-    const size_t stage_bytes = (size_t)R * 32 * (4 + sizeof(DT));
-    const uint32_t tx = (uint32_t)stage_bytes;
-
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    wait_predecessor();
-    auto issue = [&](int stage, int strip) {
-        unsigned char* st = dsm + (size_t)stage * stage_bytes;
-        mbar_arrive_expect_tx(&bar[stage], tx);
-        tma_load_2d(st, &tm_x, strip * 32, tile_row, &bar[stage]);
-        tma_load_2d(st + xbytes, &tm_d, strip * 32, tile_row, &bar[stage]);
-    };
-    if (threadIdx.x == 0 && (int)blockIdx.x < nstrips) {
-        // fault injection for tests (single-strip grids only): leave the first stage unfilled
-        if (!(skip_first && blockIdx.x == 0 && rank == 0 && nstrips <= (int)gridDim.x)) issue(0, blockIdx.x);
-    }
-    int it = 0;
-    for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x, ++it) {
-        const int stage = it & 1;
-        const uint32_t parity = (it >> 1) & 1;
-        const int next = strip + gridDim.x;
-        if (threadIdx.x == 0 && next < nstrips) issue(stage ^ 1, next);
-        const int col = strip * 32 + lane;
-        const bool col_ok = col < a.W;
-        if constexpr (KIND == PASS_UPDATE) {
-            if ((lane == 0 || lane == 31) && col_ok) {
-                const int tsz = a.t_dtype == DTS_F32 ? 4 : 2;
-#pragma unroll 1
-                for (int j = 0; j < ITEMS; ++j) {
-                    const int r = row0 + j;
-                    if (r < a.H) {
-                        prefetch_l2(a.zk + (long long)r * P + col);
-                        prefetch_l2(static_cast<const char*>(a.t) + ((long long)r * a.W + col) * tsz);
-                        prefetch_l2(a.c + (a.c_pitched ? (long long)r * P : (long long)r * a.W) + col);
-                    }
-                }
-            }
-        }
-        if (!mbar_wait_bounded(&bar[stage], parity, timeout)) atomicExch(a.status, DTS_ERR_TIMEOUT);
-        const float* sx = reinterpret_cast<const float*>(dsm + (size_t)stage * stage_bytes);
-        const DT* sd = reinterpret_cast<const DT*>(dsm + (size_t)stage * stage_bytes + xbytes);
-        float x[ITEMS], w[ITEMS];
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            x[j] = sx[(warp * ITEMS + j) * 32 + lane];
-            w[j] = to_f32<DT>(sd[(warp * ITEMS + j) * 32 + lane]);
-        }
-        float dnext = 0.f;
-        if (warp + 1 < NW) dnext = to_f32<DT>(sd[((warp + 1) * ITEMS) * 32 + lane]);
-        __syncthreads();  // this stage is free again: the next-but-one tile may land in it
-        {
-            const int rn = row0 + ITEMS;
-            if (warp + 1 == NW && col_ok && rn < a.H) dnext = load1_d<DHALF>(a.d, (long long)rn * P + col);
-        }
-        const float wn = (col_ok && row0 + ITEMS < a.H) ? ex2(a.k2 * dnext) : 0.f;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int r = row0 + j;
-            w[j] = (col_ok && r > 0 && r < a.H) ? ex2(a.k2 * w[j]) : 0.f;
-            if (!(col_ok && r < a.H)) x[j] = 0.f;
-        }
-        typename M::Pre own_pre, pre;
-        typename M::Suf own_suf, suf;
-        M::local(x, w, wn, own_pre, own_suf);
-        col_exchange_iter<M, kTmaColMaxWarps>(own_pre, own_suf, lane, warp, NW, sh, it == 0, pre, suf);
-        if (next >= nstrips) release_successor();
-        M::apply(x, w, wn, own_pre, pre.B, suf);
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int r = row0 + j;
-            if (!(col_ok && r < a.H)) continue;
-            if constexpr (KIND == PASS_PLAIN) {
-                a.dst[(long long)r * a.dst_pitch + col] = x[j];
-            } else {
-                const long long idx = (long long)r * P + col;
-                const long long di = (long long)r * a.W + col;
-                const float zb = x[j];
-                const float z = a.zk[idx];
-                const float t = load_any(a.t, di, a.t_dtype);
-                const float cf = a.c_pitched ? a.c[idx] : a.c[di];
-                float zn;
-                if (a.update == DTS_UPDATE_JACOBI) {
-                    const float den = a.lambda + cf;
-                    zn = den != 0.f ? (a.lambda * zb + cf * t) / den : z;
-                } else {
-                    float eta = a.step;
-                    if (a.clamp_step && a.lambda + cf > 0.f) eta = fminf(eta, 1.f / (a.lambda + cf));
-                    zn = z - eta * (a.lambda * (z - zb) + cf * target_slope(z - t, a.eps));
-                }
-                a.zout[(long long)r * a.zout_pitch + col] = zn;
-            }
-        }
-    }
-    if (CS > 1 && it > 0) cluster_exit();
 }
 
 template <int ITEMS, bool DHALF, int KIND>
@@ -1213,7 +1022,6 @@ template <int ITEMS, bool DHALF>
 cudaError_t launch_col_k(const PassArgs& a, int kind, const ColPlan& p, cudaStream_t s) {
     switch (kind) {
         case PASS_PLAIN: return launch_col_t<ITEMS, DHALF, PASS_PLAIN>(a, p, s);
-        case PASS_UPDATE: return launch_col_t<ITEMS, DHALF, PASS_UPDATE>(a, p, s);
         case PASS_SUPPORT_CONF: return launch_col_t<ITEMS, DHALF, PASS_SUPPORT_CONF>(a, p, s);
         case PASS_TRANSPOSE: return launch_col_t<ITEMS, DHALF, PASS_TRANSPOSE>(a, p, s);
         default: return cudaErrorInvalidValue;
@@ -1226,21 +1034,17 @@ cudaError_t launch_row_k(const PassArgs& a, int kind, const RowPlan& p, cudaStre
     const dim3 block((unsigned)(p.tpr * p.rpb));
     if (kind == PASS_SUPPORT) return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_SUPPORT>, grid, block, 0, s, a, p.tpr);
     if (kind == PASS_TRANSPOSE) return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_TRANSPOSE>, grid, block, 0, s, a, p.tpr);
-    // two one-direction exchanges (measured faster on the stereo and depth workloads);
-    // DTS_ROW_TWO=0 selects the single coupled exchange (tuning aid)
-    static const bool two = getenv("DTS_ROW_TWO") == nullptr || atoi(getenv("DTS_ROW_TWO")) != 0;
+    // plain and update passes: two one-direction exchanges (measured faster on the stereo and
+    // depth workloads than one exchange of the coupled five numbers)
     if (kind == PASS_UPDATE_ROW)
-        return two ? launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_UPDATE_ROW, true>, grid, block, 0, s, a, p.tpr)
-                   : launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_UPDATE_ROW>, grid, block, 0, s, a, p.tpr);
-    return two ? launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_PLAIN, true>, grid, block, 0, s, a, p.tpr)
-               : launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_PLAIN>, grid, block, 0, s, a, p.tpr);
+        return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_UPDATE_ROW, true>, grid, block, 0, s, a, p.tpr);
+    return launch_ex(row_pass_kernel<ITEMS, DHALF, PASS_PLAIN, true>, grid, block, 0, s, a, p.tpr);
 }
 
 template <int ITEMS, bool DHALF>
 cudaError_t allow_clusters() {
     cudaError_t e = cudaSuccess;
-    const void* fs[4] = {(const void*)col_pass_kernel<ITEMS, DHALF, PASS_PLAIN>,
-                         (const void*)col_pass_kernel<ITEMS, DHALF, PASS_UPDATE>,
+    const void* fs[3] = {(const void*)col_pass_kernel<ITEMS, DHALF, PASS_PLAIN>,
                          (const void*)col_pass_kernel<ITEMS, DHALF, PASS_SUPPORT_CONF>,
                          (const void*)col_pass_kernel<ITEMS, DHALF, PASS_TRANSPOSE>};
     for (const void* f : fs) {
@@ -1300,31 +1104,6 @@ bool make_tile_map(CUtensorMap* m, const void* base, bool half, int W, int H, lo
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
-
-// resident CTAs per SM of a kernel (cached per kernel and block size)
-int blocks_per_sm(const void* kernel, int block, size_t smem) {
-    static std::mutex mu;
-    static std::map<std::tuple<const void*, int, size_t>, int> cache;
-    std::lock_guard<std::mutex> lock(mu);
-    auto key = std::make_tuple(kernel, block, smem);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess) n = 0;
-    cache[key] = n;
-    return n;
-}
-
 // clusters of `cs` CTAs that fit at once (cached)
 int max_clusters(const void* kernel, int block, int cs, size_t smem) {
     static std::mutex mu;
@@ -1357,52 +1136,6 @@ int balanced_grid(int units, int slots) {
     return (units + rounds - 1) / rounds;
 }
 
-long long default_timeout_cycles() { return 2000000000LL; }  // ~1 s at the boost clock
-
-template <int ITEMS, bool DHALF, int KIND>
-cudaError_t launch_col_tma_t(const PassArgs& a, const ColPlan& p, cudaStream_t s) {
-    auto kernel = col_tma_kernel<ITEMS, DHALF, KIND>;
-    const int NW = p.warps;
-    const int R = NW * ITEMS;
-    // DTS_TMA_GRID=full: one cluster per strip, no persistence and a single stage (tuning aid)
-    static const bool full_grid = getenv("DTS_TMA_GRID") && getenv("DTS_TMA_GRID")[0] == 'f';
-    const size_t smem = (full_grid ? 1 : 2) * tma_stage_bytes<ITEMS, DHALF>(NW);
-    if (cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return cudaErrorInvalidConfiguration;
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        configured = true;
-    }
-    CUtensorMap tx, td;
-    if (!make_tile_map(&tx, a.src, false, a.W, a.H, a.pitch, R)) return cudaErrorInvalidValue;
-    if (!make_tile_map(&td, a.d, DHALF, a.W, a.H, a.pitch, R)) return cudaErrorInvalidValue;
-    const int nstrips = (a.W + 31) / 32;
-    const int mc = max_clusters((const void*)kernel, 32 * NW, p.cluster, smem);
-    if (mc < 1) return cudaErrorInvalidConfiguration;
-    const int gx = full_grid ? nstrips : balanced_grid(nstrips, mc);
-    const int skip = take_injected_tma_skip() ? 1 : 0;
-    const long long timeout = skip ? 2000000LL : default_timeout_cycles();
-    return launch_ex_smem(kernel, dim3((unsigned)gx, (unsigned)p.cluster, 1), dim3((unsigned)(32 * NW)), p.cluster,
-                          smem, s, tx, td, a, nstrips, timeout, skip);
-}
-
-// DTS_ROW_PREFETCH=1: the register-prefetch variant (tuning aid)
-bool row_prefetch() {
-    static const bool on = getenv("DTS_ROW_PREFETCH") != nullptr;
-    return on;
-}
-
-template <int ITEMS, bool DHALF, int KIND>
-cudaError_t launch_row_persist_t(const PassArgs& a, const RowPlan& p, cudaStream_t s) {
-    auto kernel = row_prefetch() ? row_persist_kernel<ITEMS, DHALF, KIND, true> : row_persist_kernel<ITEMS, DHALF, KIND, false>;
-    const int block = p.tpr * p.rpb;
-    const int ngroups = (a.H + p.rpb - 1) / p.rpb;
-    const int per_sm = blocks_per_sm((const void*)kernel, block, 0);
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int grid = balanced_grid(ngroups, per_sm * sm_count());
-    return launch_ex(kernel, dim3((unsigned)grid), dim3((unsigned)block), 0, s, a, p.tpr, ngroups);
-}
 
 // z_out[y][x] (pitch zout_pitch) = update(z_k, zbar = src, t, c) for every pixel
 // Four consecutive pixels per thread; VEC: 16-byte accesses (W % 4 == 0, aligned planes).
@@ -1529,49 +1262,38 @@ cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const Ro
                              (long long)a.H * a.W,
                              (dist_half ? kFlagDistHalf : 0) | (kind == PASS_UPDATE_ROW && a.t_dtype != DTS_F32 ? kFlagTarget16 : 0), s);
     cudaError_t e = cudaErrorInvalidValue;
-    if (kind != PASS_UPDATE_ROW && kind != PASS_TRANSPOSE && use_row_persistent() && (!row_prefetch() || p.tpr * p.rpb <= (p.items <= 8 ? 1024 : 512))) {
-        const bool sup = kind == PASS_SUPPORT;
-        if (p.items == 8)
-            e = dist_half ? (sup ? launch_row_persist_t<8, true, PASS_SUPPORT>(a, p, s) : launch_row_persist_t<8, true, PASS_PLAIN>(a, p, s))
-                          : (sup ? launch_row_persist_t<8, false, PASS_SUPPORT>(a, p, s) : launch_row_persist_t<8, false, PASS_PLAIN>(a, p, s));
-        if (p.items == 16)
-            e = dist_half ? (sup ? launch_row_persist_t<16, true, PASS_SUPPORT>(a, p, s) : launch_row_persist_t<16, true, PASS_PLAIN>(a, p, s))
-                          : (sup ? launch_row_persist_t<16, false, PASS_SUPPORT>(a, p, s) : launch_row_persist_t<16, false, PASS_PLAIN>(a, p, s));
-    } else {
-        if (p.items == 8) e = dist_half ? launch_row_k<8, true>(a, kind, p, s) : launch_row_k<8, false>(a, kind, p, s);
-        if (p.items == 16) e = dist_half ? launch_row_k<16, true>(a, kind, p, s) : launch_row_k<16, false>(a, kind, p, s);
-        if (p.items == 32 && kind == PASS_UPDATE_ROW) {  // long rows (plan_rows_update)
-            const dim3 grid((unsigned)((a.H + p.rpb - 1) / p.rpb));
-            const dim3 block((unsigned)(p.tpr * p.rpb));
-            e = dist_half ? launch_ex(row_pass_kernel<32, true, PASS_UPDATE_ROW>, grid, block, 0, s, a, p.tpr)
-                          : launch_ex(row_pass_kernel<32, false, PASS_UPDATE_ROW>, grid, block, 0, s, a, p.tpr);
-        }
+    if (p.items == 8) e = dist_half ? launch_row_k<8, true>(a, kind, p, s) : launch_row_k<8, false>(a, kind, p, s);
+    if (p.items == 16) e = dist_half ? launch_row_k<16, true>(a, kind, p, s) : launch_row_k<16, false>(a, kind, p, s);
+    if (p.items == 32 && kind == PASS_UPDATE_ROW) {  // long rows (plan_rows_update)
+        const dim3 grid((unsigned)((a.H + p.rpb - 1) / p.rpb));
+        const dim3 block((unsigned)(p.tpr * p.rpb));
+        e = dist_half ? launch_ex(row_pass_kernel<32, true, PASS_UPDATE_ROW>, grid, block, 0, s, a, p.tpr)
+                      : launch_ex(row_pass_kernel<32, false, PASS_UPDATE_ROW>, grid, block, 0, s, a, p.tpr);
     }
     prof_end(h, s);
     return e;
 }
 
 cudaError_t launch_col_strip(const PassArgs& a, int dist_half, const ColPlan& p, bool tr, cudaStream_t s);
+cudaError_t launch_col_chain(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s);
 
 cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
-    ColPlan tp_probe;
-    // the transposed pass runs on the cluster kernel only
     const bool tr = kind == PASS_TRANSPOSE;
-    const bool inject = !tr && injected_tma_skip_pending() && kind != PASS_SUPPORT_CONF && plan_cols_tma(a.H, &tp_probe);
-    if (!tr && !inject && use_col_split() && kind != PASS_SUPPORT_CONF && a.agg && a.carry && a.counters)
-        return launch_col_split(a, dist_half, kind, s);
-    // the strip kernel runs plain and transposed passes; other kinds (and fault injection) take the
-    // cluster shape
+    // the strip kernel runs plain and transposed passes; the other kinds take the chain (or the
+    // cluster) shape of the same height
     ColPlan q = p;
-    if (q.cluster == 0 && ((kind != PASS_PLAIN && !tr) || inject) && !plan_cols_cluster(a.H, &q))
-        return cudaErrorInvalidValue;
+    if (q.cluster == 0 && kind != PASS_PLAIN && !tr && !plan_cols_multi(a.H, &q)) return cudaErrorInvalidValue;
     const bool strip = q.cluster == 0;
+    const bool chain = q.cluster < 0;
     const int kid = strip ? (tr ? KID_COL_STRIP_TRANSPOSE : KID_COL_STRIP)
-                  : kind == PASS_UPDATE ? KID_COL_UPDATE : kind == PASS_SUPPORT_CONF ? KID_COL_SUPPORT
-                  : tr ? KID_COL_TRANSPOSE : KID_COL_PLAIN;
-    const int flags = (dist_half ? kFlagDistHalf : 0) | (kind == PASS_UPDATE && a.t_dtype != DTS_F32 ? kFlagTarget16 : 0);
+                  : kind == PASS_SUPPORT_CONF ? KID_COL_SUPPORT
+                  : tr ? (chain ? KID_COL_CHAIN_TRANSPOSE : KID_COL_TRANSPOSE)
+                  : chain ? KID_COL_CHAIN : KID_COL_PLAIN;
+    const int flags = dist_half ? kFlagDistHalf : 0;
     const int h = prof_begin(kid, (long long)a.H * a.W, flags, s);
-    const cudaError_t e = strip ? launch_col_strip(a, dist_half, q, tr, s) : launch_col_dispatch(a, dist_half, kind, q, s);
+    const cudaError_t e = strip ? launch_col_strip(a, dist_half, q, tr, s)
+                        : chain ? launch_col_chain(a, dist_half, kind, q, s)
+                                : launch_col_dispatch(a, dist_half, kind, q, s);
     prof_end(h, s);
     return e;
 }
@@ -1594,18 +1316,12 @@ long long strip_tile_rows(int H) {
     return 4LL * warps * items + 1;  // every row a slab box reads, the extra row of the last included
 }
 
-// DTS_STRIP_LSU=1: the plain-load strip kernel instead of the TMA one (tuning aid)
-bool strip_lsu() {
-    static const bool on = getenv("DTS_STRIP_LSU") != nullptr;
-    return on;
-}
-
 template <int ITEMS, bool DHALF>
 cudaError_t launch_col_strip_t(const PassArgs& a, int nw, bool tr, cudaStream_t s) {
     const dim3 grid((unsigned)((a.W + kStripCols - 1) / kStripCols));
     const dim3 block((unsigned)(32 * nw));
     CUtensorMap tx, td, to;
-    if (!strip_lsu() && make_box_map(&tx, a.src, false, a.W, a.H, a.pitch, kStripCols, 4 * ITEMS) &&
+    if (make_box_map(&tx, a.src, false, a.W, a.H, a.pitch, kStripCols, 4 * ITEMS) &&
         make_box_map(&td, a.d, DHALF, a.W, a.H, a.pitch, kStripCols, 4 * ITEMS + 1) &&
         make_box_map(&to, a.dst, false, a.W, a.H, a.dst_pitch, kStripCols, 4 * ITEMS)) {
         // shared-memory limits raised in prepare_kernels
@@ -1616,15 +1332,19 @@ cudaError_t launch_col_strip_t(const PassArgs& a, int nw, bool tr, cudaStream_t 
         const int per_sm = blocks_per_sm((const void*)kernel, 32 * nw, smem);
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         const int g = std::min(nstrips, per_sm * sm_count());
+        // fault injection (tests): on a single-round grid, the first slab load of warp 0 of CTA 0
+        // is left out, so that warp's bounded wait runs out (about a millisecond)
+        const bool skip = g == nstrips && take_injected(DTS_INJECT_TMA_SKIP);
         return launch_ex_smem(kernel, dim3((unsigned)g), block, 0, smem, s, tx, td, to, a, nstrips,
-                              default_timeout_cycles());
+                              skip ? kInjectedTimeout : default_timeout_cycles(), skip ? 1 : 0);
     }
     // planes that tensor maps cannot describe (e.g. a caller's unaligned output): plain loads, or
     // the cluster kernel for the transposed pass
     if (tr) {
         ColPlan q;
-        if (!plan_cols_cluster(a.H, &q)) return cudaErrorInvalidValue;
-        return launch_col_dispatch(a, DHALF, PASS_TRANSPOSE, q, s);
+        if (!plan_cols_multi(a.H, &q)) return cudaErrorInvalidValue;
+        return q.cluster < 0 ? launch_col_chain(a, DHALF, PASS_TRANSPOSE, q, s)
+                             : launch_col_dispatch(a, DHALF, PASS_TRANSPOSE, q, s);
     }
     return launch_ex(col_strip_kernel<ITEMS, DHALF>, grid, block, 0, s, a);
 }
@@ -1639,24 +1359,7 @@ cudaError_t launch_col_strip(const PassArgs& a, int dist_half, const ColPlan& p,
 }
 
 cudaError_t launch_col_dispatch(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
-    // a pending fault injection exercises the bounded waits of the TMA kernel
-    const bool tr = kind == PASS_TRANSPOSE;
-    const bool inject = !tr && injected_tma_skip_pending();
-    if (!tr && !inject && use_col_split() && kind != PASS_SUPPORT_CONF && a.agg && a.carry && a.counters)
-        return launch_col_split(a, dist_half, kind, s);
-    ColPlan tp;
-    if (!tr && (inject || use_col_tma()) && kind != PASS_SUPPORT_CONF && plan_cols_tma(a.H, &tp)) {
-        const bool up = kind == PASS_UPDATE;
-        if (tp.items == 8)
-            return dist_half ? (up ? launch_col_tma_t<8, true, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<8, true, PASS_PLAIN>(a, tp, s))
-                             : (up ? launch_col_tma_t<8, false, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<8, false, PASS_PLAIN>(a, tp, s));
-        if (tp.items == 16)
-            return dist_half ? (up ? launch_col_tma_t<16, true, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<16, true, PASS_PLAIN>(a, tp, s))
-                             : (up ? launch_col_tma_t<16, false, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<16, false, PASS_PLAIN>(a, tp, s));
-        if (tp.items == 32)
-            return dist_half ? (up ? launch_col_tma_t<32, true, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<32, true, PASS_PLAIN>(a, tp, s))
-                             : (up ? launch_col_tma_t<32, false, PASS_UPDATE>(a, tp, s) : launch_col_tma_t<32, false, PASS_PLAIN>(a, tp, s));
-    }
+    if (p.cluster < 1) return cudaErrorInvalidValue;
     if (p.items == 8) return dist_half ? launch_col_k<8, true>(a, kind, p, s) : launch_col_k<8, false>(a, kind, p, s);
     if (p.items == 16) return dist_half ? launch_col_k<16, true>(a, kind, p, s) : launch_col_k<16, false>(a, kind, p, s);
     if (p.items == 32) return dist_half ? launch_col_k<32, true>(a, kind, p, s) : launch_col_k<32, false>(a, kind, p, s);
@@ -1664,7 +1367,70 @@ cudaError_t launch_col_dispatch(const PassArgs& a, int dist_half, int kind, cons
     return cudaErrorInvalidValue;
 }
 
-// Horizontal plan: ITEMS elements per thread, one row per tpr threads (<= 1024).
+// chained vertical pass: one CTA per chunk of a strip, S x J CTAs; refused (invalid
+// configuration) when fewer than 2 J CTAs of the kernel fit on the GPU at once
+// chunks per staging block of the strip composition: the shared memory of four resident CTAs of
+// 128 rows, or two of 256 rows
+template <int ITEMS, int NW>
+constexpr int chain_stage_cap() {
+    return ITEMS * NW <= 128 ? 40 : 80;
+}
+
+template <int ITEMS, int NW, bool DHALF, int KIND>
+cudaError_t allow_chain_smem() {
+    return cudaFuncSetAttribute((const void*)col_chain_kernel<ITEMS, NW, DHALF, KIND>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)chain_stage_bytes<ColMode<KIND>>(chain_stage_cap<ITEMS, NW>()));
+}
+
+template <int ITEMS, int NW, bool DHALF>
+cudaError_t allow_chain_smem_all() {
+    cudaError_t e = cudaSuccess, r;
+    if ((r = allow_chain_smem<ITEMS, NW, DHALF, PASS_PLAIN>()) != cudaSuccess) e = r;
+    if ((r = allow_chain_smem<ITEMS, NW, DHALF, PASS_SUPPORT_CONF>()) != cudaSuccess) e = r;
+    if ((r = allow_chain_smem<ITEMS, NW, DHALF, PASS_TRANSPOSE>()) != cudaSuccess) e = r;
+    return e;
+}
+
+template <int ITEMS, int NW, bool DHALF, int KIND>
+cudaError_t launch_chain_t(const PassArgs& a, cudaStream_t s) {
+    auto kernel = col_chain_kernel<ITEMS, NW, DHALF, KIND>;
+    ChainArgs c = {};
+    c.ctl = a.chain_ctl;
+    c.agg = a.chain_agg;
+    c.J = (a.H + ITEMS * NW - 1) / (ITEMS * NW);
+    c.S = (a.W + 31) / 32;
+    c.status = a.status;
+    if (!c.ctl || !c.agg || c.J > kChainMaxChunks) return cudaErrorInvalidValue;
+    c.stage = std::min(c.J, chain_stage_cap<ITEMS, NW>());
+    const size_t smem = chain_stage_bytes<ColMode<KIND>>(c.stage);
+    if (blocks_per_sm((const void*)kernel, 32 * NW, smem) * sm_count() < 2 * c.J) return cudaErrorInvalidConfiguration;
+    const bool skip = KIND != PASS_SUPPORT_CONF && take_injected(DTS_INJECT_CHAIN_SKIP);
+    c.timeout = skip ? kInjectedTimeout : default_timeout_cycles();
+    c.skip_ticket = skip && c.J > 1 ? 0 : -1;
+    return launch_ex_smem(kernel, dim3((unsigned)(c.S * c.J)), dim3(32 * NW), 0, smem, s, a, c);
+}
+
+template <int ITEMS, int NW, bool DHALF>
+cudaError_t launch_chain_k(const PassArgs& a, int kind, cudaStream_t s) {
+    switch (kind) {
+        case PASS_PLAIN: return launch_chain_t<ITEMS, NW, DHALF, PASS_PLAIN>(a, s);
+        case PASS_SUPPORT_CONF: return launch_chain_t<ITEMS, NW, DHALF, PASS_SUPPORT_CONF>(a, s);
+        case PASS_TRANSPOSE: return launch_chain_t<ITEMS, NW, DHALF, PASS_TRANSPOSE>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_col_chain(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
+    if (p.items == 16 && p.warps == 8)
+        return dist_half ? launch_chain_k<16, 8, true>(a, kind, s) : launch_chain_k<16, 8, false>(a, kind, s);
+    if (p.items == 16 && p.warps == 16)
+        return dist_half ? launch_chain_k<16, 16, true>(a, kind, s) : launch_chain_k<16, 16, false>(a, kind, s);
+    if (p.items == 32 && p.warps == 8)
+        return dist_half ? launch_chain_k<32, 8, true>(a, kind, s) : launch_chain_k<32, 8, false>(a, kind, s);
+    return cudaErrorInvalidValue;
+}
+
 // ---------------------------------------------------------------- tuned shapes
 // Shapes chosen by dts_autotune (measured per line length), consulted before the defaults.
 std::mutex g_tuned_mutex;
@@ -1708,8 +1474,23 @@ std::string tuned_export() {
     return out;
 }
 
-// vertical shapes the tuner tries: the strip kernel (columns up to 2048 rows), then rows per
-// thread x warps per CTA in clusters of at most 16
+size_t chain_ctl_bytes(int W) { return (size_t)chain_ctl_words((W + 31) / 32) * sizeof(unsigned); }
+size_t chain_agg_bytes(int H, int W) {
+    // chunks of at least 64 rows; Pre and Suf of up to 9 floats together (the adjoint's)
+    const size_t S = (size_t)(W + 31) / 32, J = (size_t)(H + 63) / 64;
+    return S * J * 32 * 9 * sizeof(float);
+}
+
+// chain shapes (rows per thread, warps per CTA), the default first
+constexpr int kChainShapes[][2] = {{16, 8}, {16, 16}, {32, 8}};
+
+bool chain_shape_fits(int H, int items, int warps) {
+    const int J = (H + items * warps - 1) / (items * warps);
+    return H <= kMaxColRows && J <= kChainMaxChunks;
+}
+
+// vertical shapes the tuner tries: the strip kernel (columns up to kStripMaxRows rows), the
+// chain shapes, then rows per thread x warps per CTA in clusters of at most 16
 int col_candidates(int H, ColPlan* out, int max_out) {
     static const int cand[][2] = {{8, 8}, {8, 16}, {8, 32}, {16, 8}, {16, 16}, {32, 8}, {32, 16}, {40, 16}};
     int n = 0;
@@ -1717,6 +1498,8 @@ int col_candidates(int H, ColPlan* out, int max_out) {
         strip_shape(H, &out[n].items, &out[n].warps);
         out[n++].cluster = 0;
     }
+    for (const auto& c : kChainShapes)
+        if (H > 1 && chain_shape_fits(H, c[0], c[1]) && n < max_out) out[n++] = ColPlan{c[0], c[1], -1};
     for (const auto& c : cand) {
         const int rows = c[0] * c[1];
         const int cs = (H + rows - 1) / rows;
@@ -1733,8 +1516,6 @@ bool plan_rows(int W, RowPlan* p) {
     else return false;
     const int tuned = tuned_row(W);
     if ((tuned == 8 || tuned == 16) && (W + tuned - 1) / tuned <= 1024) items = tuned;
-    static const char* env = getenv("DTS_ROW_ITEMS");  // tuning aid: force 8 or 16
-    if (env && (atoi(env) == 8 || atoi(env) == 16) && (W + atoi(env) - 1) / atoi(env) <= 1024) items = atoi(env);
     int tpr = (W + items - 1) / items;
     tpr = (tpr + 31) / 32 * 32;
     int rpb = 256 / tpr;
@@ -1745,42 +1526,38 @@ bool plan_rows(int W, RowPlan* p) {
     return true;
 }
 
-bool use_col_tma();
-bool use_col_split();
-
-// Vertical plan: the strip kernel for columns up to 2048 rows (measured faster than clusters on
-// the stereo, depth and 256 x 256 workloads; DTS_NO_STRIP=1 keeps clusters, a tuning aid), else
-// the cluster plan.  A tuned shape comes first.
+// Vertical plan: a tuned shape first; else the strip kernel for columns up to kStripMaxRows rows
+// (measured faster than clusters on the stereo, depth and 256 x 256 workloads), else the chain.
 bool plan_cols(int H, ColPlan* p) {
+    if (H > kMaxColRows) return false;
     if (tuned_col(H, p)) return true;
-    static const bool strip = getenv("DTS_NO_STRIP") == nullptr && getenv("DTS_COL_PLAN") == nullptr;
-    if (strip && !use_col_tma() && !use_col_split() && H <= kStripMaxRows) {
+    if (H <= kStripMaxRows) {
         strip_shape(H, &p->items, &p->warps);
         p->cluster = 0;
         return true;
     }
+    return plan_cols_multi(H, p);
+}
+
+// Plan for the pass kinds the strip kernel does not run: a tuned chain or cluster shape, else
+// the chain for columns taller than one CTA of the cluster kernel's single-CTA shape, else that.
+bool plan_cols_multi(int H, ColPlan* p) {
+    if (H > kMaxColRows) return false;
+    if (tuned_col(H, p) && p->cluster != 0) return true;
+    if (H > 256) {
+        p->items = kChainShapes[0][0];
+        p->warps = kChainShapes[0][1];
+        p->cluster = -1;
+        return chain_shape_fits(H, p->items, p->warps);
+    }
     return plan_cols_cluster(H, p);
 }
 
-// Cluster plan: columns up to 256 rows in one CTA; else the first (items, warps) shape whose
-// cluster holds the whole column with at most 8 CTAs, else at most 16 (non-portable size).
+// Cluster plan (solves that run side by side, whose CTAs must not wait on one another across
+// streams): columns up to 256 rows in one CTA; else the first (items, warps) shape whose cluster
+// holds the whole column with at most 8 CTAs, else at most 16 (non-portable size).
 bool plan_cols_cluster(int H, ColPlan* p) {
     if (tuned_col(H, p) && p->cluster > 0) return true;
-    // DTS_COL_PLAN="items,warps" overrides the shape (tuning aid)
-    static const char* env = getenv("DTS_COL_PLAN");
-    if (env) {
-        int it = 0, nw = 0;
-        if (sscanf(env, "%d,%d", &it, &nw) == 2 && (it == 8 || it == 16 || it == 32 || it == 40) && nw >= 1 &&
-            (nw & (nw - 1)) == 0 && nw * 32 <= (it <= 8 ? 1024 : 512)) {
-            const int cs = (H + it * nw - 1) / (it * nw);
-            if (cs <= 16) {
-                p->items = it;
-                p->warps = nw;
-                p->cluster = cs;
-                return true;
-            }
-        }
-    }
     if (H <= 256) {
         int nw = 1;
         while (nw * 8 < H) nw <<= 1;  // a power of two (the CTA scan works in lane groups)
@@ -1805,67 +1582,6 @@ bool plan_cols_cluster(int H, ColPlan* p) {
         }
     }
     return false;
-}
-
-// Alternative kernels kept for tuning (measured slower on the stereo workload, off by default):
-// DTS_ROW_PERSIST=1 persistent horizontal pass, DTS_COL_TMA=1 persistent TMA vertical pass.
-bool use_persistent() {
-    static const bool on = getenv("DTS_NO_PERSIST") == nullptr;
-    return on;
-}
-bool use_row_persistent() {
-    static const bool on = getenv("DTS_ROW_PERSIST") != nullptr;
-    return on;
-}
-bool use_col_tma() {
-    static const bool on = getenv("DTS_COL_TMA") != nullptr;
-    return on;
-}
-// split (two-kernel, cluster-free) vertical pass, measured slower than the cluster kernel on the
-// stereo workload; DTS_COL_SPLIT=1 selects it (tuning aid)
-bool use_col_split() {
-    static const bool on = getenv("DTS_COL_SPLIT") != nullptr;
-    return on;
-}
-
-// TMA vertical plan: tiles of R = items x warps rows (R <= 256, one TMA box), clusters of at most
-// 16 CTAs: columns up to 4096 rows.  DTS_TMA_COL_PLAN="items,warps" overrides (tuning aid).
-bool plan_cols_tma(int H, ColPlan* p) {
-    static const char* env = getenv("DTS_TMA_COL_PLAN");
-    int it = 16, nw = 8;
-    if (env) {
-        int a = 0, b = 0;
-        if (sscanf(env, "%d,%d", &a, &b) == 2 && (a == 8 || a == 16 || a == 32) && b >= 1 &&
-            b <= kTmaColMaxWarps) {
-            it = a;
-            nw = b;
-        }
-    } else if (H <= 64) {
-        it = 8;
-        nw = (H + 7) / 8;
-    } else if (H <= 128) {
-        it = 16;
-        nw = (H + 15) / 16;
-    }
-    if (nw > kTmaColMaxWarps) return false;
-    const int R = it * nw;
-    const int cs = (H + R - 1) / R;
-    if (cs > 16) {
-        if (env) return false;
-        // taller columns: the largest tile
-        it = 32;
-        nw = 8;
-        const int cs2 = (H + 255) / 256;
-        if (cs2 > 16) return false;
-        p->items = it;
-        p->warps = nw;
-        p->cluster = cs2;
-        return true;
-    }
-    p->items = it;
-    p->warps = nw;
-    p->cluster = cs;
-    return true;
 }
 
 // dynamic shared memory of the TMA strip kernel: up to 32 slabs (208 KB at 17 rows, FP32)
@@ -1894,6 +1610,12 @@ cudaError_t prepare_kernels() {
     if ((r = allow_strip_smem<9, true>()) != cudaSuccess) e = r;
     if ((r = allow_strip_smem<17, false>()) != cudaSuccess) e = r;
     if ((r = allow_strip_smem<17, true>()) != cudaSuccess) e = r;
+    if ((r = allow_chain_smem_all<16, 8, false>()) != cudaSuccess) e = r;
+    if ((r = allow_chain_smem_all<16, 8, true>()) != cudaSuccess) e = r;
+    if ((r = allow_chain_smem_all<16, 16, false>()) != cudaSuccess) e = r;
+    if ((r = allow_chain_smem_all<16, 16, true>()) != cudaSuccess) e = r;
+    if ((r = allow_chain_smem_all<32, 8, false>()) != cudaSuccess) e = r;
+    if ((r = allow_chain_smem_all<32, 8, true>()) != cudaSuccess) e = r;
     return e;
 }
 

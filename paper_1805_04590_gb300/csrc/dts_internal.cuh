@@ -21,11 +21,8 @@ constexpr int kPitchAlign = 64;     // elements
 constexpr size_t kPlaneAlign = 256; // bytes
 constexpr int kMaxPasses = 16;
 
-// Programmatic dependent launch between consecutive kernels (off when DTS_NO_PDL is set).
-inline bool pdl_enabled() {
-    static const bool on = getenv("DTS_NO_PDL") == nullptr;
-    return on;
-}
+// Programmatic dependent launch between consecutive kernels: every launch allows it.
+inline bool pdl_enabled() { return true; }
 
 inline long long pitch_for(int W) { return ((long long)W + kPitchAlign - 1) / kPitchAlign * kPitchAlign; }
 
@@ -56,12 +53,19 @@ __device__ __forceinline__ float target_slope(float r, float eps) {
 // or the support-weighted confidence).
 //   GD (Eq. 3):      z - step (lambda (z - zb) + c rho'(z - t)), with the step limited to
 //                    1 / (lambda + c) when clamp is set; rho'(r) = target_slope(r, eps)
-//   Jacobi (Eq. 4):  (lambda zb + c t) / (lambda + c); z is kept where lambda + c = 0
+//   Jacobi (Eq. 4):  (lambda zb + c~ t) / (lambda + c~); z is kept where lambda + c~ = 0; c~ = c
+//                    for the square, c / sqrt((z - t)^2 + eps^2) for the Charbonnier loss (its
+//                    weight at the current iterate)
 __device__ __forceinline__ float dts_update_value(float z, float zb, float t, float c, float lambda, float step,
                                                   int update, int clamp, float eps) {
     if (update == DTS_UPDATE_JACOBI) {
-        const float den = lambda + c;
-        return den != 0.f ? (lambda * zb + c * t) / den : z;
+        float cw = c;
+        if (eps > 0.f) {
+            const float r = z - t;
+            cw = c * rsqrtf(fmaf(r, r, eps * eps));
+        }
+        const float den = lambda + cw;
+        return den != 0.f ? (lambda * zb + cw * t) / den : z;
     }
     float eta = step;
     if (clamp && lambda + c > 0.f) eta = fminf(eta, 1.f / (lambda + c));
@@ -117,12 +121,9 @@ struct PassArgs {
     float s_flat;
     // device status word (bounded waits that give up write DTS_ERR_TIMEOUT here)
     int* status;
-    // scratch of the split vertical pass (dts_vertical.cu): five aggregate planes and two carry
-    // planes of agg_plane floats each (row pitch agg_pitch), one ticket counter per 128 columns
-    float* agg;
-    float* carry;
-    unsigned* counters;
-    long long agg_pitch, agg_plane;
+    // scratch of the chained vertical pass (col_chain_kernel): control words and chunk tuples
+    unsigned* chain_ctl;
+    float* chain_agg;
 };
 
 // One directional pass adjoint (see dts_backward.cu).
@@ -149,12 +150,11 @@ struct BwdArgs {
     float lambda, step;
     int update;
     float eps;              // Charbonnier loss on the target term when > 0
-    // columns taller than one cluster (vertical adjoint in chunks): chunk_mode 0 single chunk,
-    // 1 write chunk totals, 2 apply with the totals of the other chunks; tot holds tot_chunks
-    // chunks of 9 planes of tot_pitch floats
-    int chunk_mode, nchunks, tot_chunks;
-    float* tot;
-    long long tot_pitch;
+    // chained vertical adjoint (columns taller than one cluster): control words, chunk tuples,
+    // and the status word its bounded waits write
+    unsigned* chain_ctl;
+    float* chain_agg;
+    int* status;
 };
 
 struct GuideGradArgs {
@@ -199,15 +199,15 @@ enum KernelId {
     KID_ROW_PLAIN = 2,
     KID_ROW_SUPPORT = 3,
     KID_COL_PLAIN = 4,
-    KID_COL_UPDATE = 5,
+    // 5: no longer used
     KID_COL_SUPPORT = 6,
     KID_ROW_BWD = 7,
     KID_ROW_BWD_FINAL = 8,
     KID_COL_BWD = 9,
-    KID_COL_BWD_UPDATE = 10,
+    // 10: no longer used
     KID_GUIDE_GRAD = 11,
     KID_AXPY = 12,
-    KID_COL_AGG = 13,
+    // 13: no longer used
     KID_ROW_UPDATE = 14,
     KID_UPDATE = 15,
     KID_UPDATE_ADJ = 16,
@@ -223,6 +223,10 @@ enum KernelId {
     KID_CG_DIRECTION = 26,
     KID_COL_STRIP_TRANSPOSE = 27,
     KID_RESIDENT = 28,
+    KID_COL_CHAIN = 29,
+    // 30: no longer used
+    KID_COL_CHAIN_TRANSPOSE = 31,
+    KID_COL_BWD_CHAIN = 32,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
@@ -232,12 +236,30 @@ constexpr int kFlagTarget16 = 2;   // target stored in 16 bits
 int prof_begin(int kernel, long long pixels, int flags, cudaStream_t s);
 void prof_end(int handle, cudaStream_t s);
 
-// device status word of the current device (dts_api.cu)
+// device status word of the current device (dts_api.cu; set up by the entry points before
+// their first launch)
 int* status_word();
-// one-shot fault injection for tests: the next TMA vertical pass skips its first tile load in
-// its first CTA, so that CTA's bounded wait gives up (dts_api.cu)
-bool take_injected_tma_skip();
-bool injected_tma_skip_pending();
+// SMs of the device, and resident CTAs per SM of a kernel at this block size (dts_api.cu)
+int sm_count();
+int blocks_per_sm(const void* kernel, int block, size_t smem);
+// one-shot fault injection for tests (dts_debug_inject): true when `kind` is pending, which it
+// then no longer is (dts_api.cu)
+bool take_injected(int kind);
+
+// Bounded device-side waits: about a second at the boost clock, about a millisecond when a test
+// has requested a fault injection.
+constexpr long long kWaitTimeout = 2000000000LL;
+constexpr long long kInjectedTimeout = 2000000LL;
+inline long long default_timeout_cycles() { return kWaitTimeout; }
+
+// Tallest column of a vertical pass, and the most chunks a chained vertical pass cuts one into
+// (its CTAs of a strip must be resident together; the launch checks that twice as many fit).
+constexpr int kMaxColRows = 16384;
+constexpr int kChainMaxChunks = 256;
+// scratch of the chained passes for an H x W plane (control words; chunk tuples of up to 9
+// floats per column for both directions together, at the shortest chunk of 64 rows)
+size_t chain_ctl_bytes(int W);
+size_t chain_agg_bytes(int H, int W);
 
 // launchers (dts_forward.cu); return cudaGetLastError() after the launch
 cudaError_t launch_distances(const DistArgs& a, cudaStream_t s);
@@ -328,30 +350,21 @@ bool plan_resident(int H, int W, const dts_params* p, ResidentPlan* rp);
 cudaError_t prepare_resident_kernel();
 cudaError_t launch_resident(const ResidentLaunch& l, cudaStream_t s);
 
+// Vertical plans: the strip kernel (cluster 0), the cluster kernel (cluster > 0 CTAs) or the
+// chained kernel (cluster -1).  plan_cols: any pass; plan_cols_multi: the kinds the strip kernel
+// does not run; plan_cols_cluster: the cluster kernel (solves that run side by side).
 bool plan_cols(int H, ColPlan* p);
+bool plan_cols_multi(int H, ColPlan* p);
 bool plan_cols_cluster(int H, ColPlan* p);
 // rows per strip of the tiled distance plane the strip kernel reads (0: columns too tall for it)
 long long strip_tile_rows(int H);
-bool plan_cols_tma(int H, ColPlan* p);
-bool use_persistent();
-bool use_row_persistent();
-bool use_col_tma();
 cudaError_t prepare_kernels();
-
-// split vertical pass (dts_vertical.cu)
-void split_col_scratch(int H, int W, long long* agg_pitch, long long* agg_plane, int* nstrips128);
-cudaError_t launch_col_split(const PassArgs& a, int dist_half, int kind, cudaStream_t s);
-bool use_col_split();
 
 // backward launchers (dts_backward.cu)
 bool plan_rows_bwd(int W, RowPlan* p);
 bool plan_cols_bwd(int H, ColPlan* p);
 cudaError_t launch_row_bwd(const BwdArgs& a, int dist_half, bool final_pass, const RowPlan& p, cudaStream_t s);
 cudaError_t launch_col_bwd(const BwdArgs& a, int dist_half, const ColPlan& p, cudaStream_t s);
-// tallest column of the backward (the forward's limit) and the chunks a column of H rows takes
-// in the vertical adjoint (0: one cluster holds it)
-constexpr int kBwdMaxRows = 10240;
-int bwd_col_chunks(int H);
 cudaError_t launch_guide_grad(const GuideGradArgs& a, cudaStream_t s);
 cudaError_t launch_update_adjoint(const BwdArgs& a, cudaStream_t s);
 cudaError_t launch_axpy_plane(const float* src, long long sp, float* dst, long long dp, int H, int W, int accumulate,

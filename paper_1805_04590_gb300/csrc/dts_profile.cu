@@ -97,15 +97,12 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_ROW_PLAIN: return "row_pass_kernel";
         case KID_ROW_SUPPORT: return "row_pass_kernel<support>";
         case KID_COL_PLAIN: return "col_pass_kernel";
-        case KID_COL_UPDATE: return "col_pass_kernel<update>";
         case KID_COL_SUPPORT: return "col_pass_kernel<support>";
         case KID_ROW_BWD: return "row_bwd_kernel";
         case KID_ROW_BWD_FINAL: return "row_bwd_kernel<final>";
         case KID_COL_BWD: return "col_bwd_kernel";
-        case KID_COL_BWD_UPDATE: return "col_bwd_kernel<update>";
         case KID_GUIDE_GRAD: return "guide_grad_kernel";
         case KID_AXPY: return "axpy_plane_kernel";
-        case KID_COL_AGG: return "col_agg_kernel";
         case KID_ROW_UPDATE: return "row_pass_kernel<update>";
         case KID_UPDATE: return "update_kernel";
         case KID_UPDATE_ADJ: return "update_adjoint_kernel";
@@ -121,6 +118,9 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_CG_DIRECTION: return "cg_direction_kernel";
         case KID_COL_STRIP_TRANSPOSE: return "col_strip_kernel<transpose>";
         case KID_RESIDENT: return "resident_solve_kernel";
+        case KID_COL_CHAIN: return "col_chain_kernel";
+        case KID_COL_CHAIN_TRANSPOSE: return "col_chain_kernel<transpose>";
+        case KID_COL_BWD_CHAIN: return "col_bwd_chain_kernel";
         default: return "unknown";
     }
 }

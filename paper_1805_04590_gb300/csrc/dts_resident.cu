@@ -74,6 +74,7 @@ struct ResArgs {
     unsigned* bar;          // [0] arrivals, [1] generation, [2] abort (zero at launch)
     int* status;
     long long timeout;
+    int skip_cta;           // fault injection: this CTA leaves out its first barrier arrival (-1: none)
 };
 
 __device__ __forceinline__ int swz(int col) {
@@ -95,7 +96,8 @@ __device__ __forceinline__ void grid_barrier(const ResArgs& a, unsigned& gen) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned arrived = atomicAdd(&a.bar[0], 1u) + 1u;
+        const bool arrive = !(gen == 0u && (int)blockIdx.x == a.skip_cta);
+        const unsigned arrived = arrive ? atomicAdd(&a.bar[0], 1u) + 1u : 0u;
         if (arrived == gridDim.x) {
             atomicExch(&a.bar[0], 0u);
             __threadfence();
@@ -106,7 +108,7 @@ __device__ __forceinline__ void grid_barrier(const ResArgs& a, unsigned& gen) {
                 if (ld_acquire(&a.bar[2]) != 0u) break;
                 if (clock64() - t0 > a.timeout) {
                     atomicExch(&a.bar[2], 1u);
-                    atomicExch(a.status, DTS_ERR_TIMEOUT);
+                    record_status(a.status, DTS_ERR_TIMEOUT);
                     break;
                 }
             }
@@ -475,7 +477,11 @@ cudaError_t launch_resident(const ResidentLaunch& l, cudaStream_t s) {
     a.cagg = l.cagg;
     a.bar = l.bar;
     a.status = l.status;
-    a.timeout = 2000000000LL;  // ~1 s at the boost clock
+    // fault injection (tests): CTA 0 leaves out its first arrival, so every wait at that barrier
+    // runs out (about a millisecond)
+    const bool skip = take_injected(DTS_INJECT_BARRIER_SKIP);
+    a.timeout = skip ? kInjectedTimeout : kWaitTimeout;
+    a.skip_cta = skip ? 0 : -1;
     cudaError_t e = cudaMemsetAsync(l.bar, 0, 4 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     const int h = prof_begin(KID_RESIDENT, (long long)l.H * l.W * l.K, 0, s);

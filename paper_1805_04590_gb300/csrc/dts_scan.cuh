@@ -394,6 +394,205 @@ __device__ __forceinline__ void col_exchange_iter(const typename M::Pre& own_pre
     suf = wsuf;
 }
 
+// ---------------------------------------------------------------- chained column exchange
+// Columns too tall for one CTA run as a chain of chunks of R rows, one CTA per chunk and no
+// cluster.  A CTA draws a ticket t from an atomic counter (so tickets go out in the order CTAs
+// start) and takes chunk t % J of 32-column strip t / J.  After the exchange inside the CTA it
+// publishes its chunk totals (the composition of its segments in both directions, per column) to
+// global memory and counts its arrival at the strip.  The CTA whose arrival completes the strip
+// turns every chunk's totals, in place, into the chunk's exclusive carries (everything above it,
+// everything below it), then raises the strip's flag; the other CTAs wait for the flag, read
+// their carries and compose them with their own.  A pass thus reads and writes every pixel once,
+// as with a cluster, but without gang scheduling: small CTAs of many strips share each SM.
+//
+// No deadlock when J CTAs can be resident at once: the chunks of a strip hold consecutive
+// tickets and every CTA publishes before it waits, so every strip older than the newest one
+// completes, and the newest one's at most J - 1 waiting CTAs leave a slot for the rest of it.
+// Waits are bounded: one that runs out records DTS_ERR_TIMEOUT and raises the abort word, after
+// which no CTA of the solve waits again (its results are then invalid; the kernel still ends).
+//
+// Control words (zeroed once per solve; every launch leaves them at zero again):
+//   ctl[0] ticket counter, ctl[1] abort, ctl[32 + s] arrivals at strip s,
+//   ctl[32 + S + s] flag of strip s, ctl[32 + 2 S + s] CTAs of strip s that have read their carries.
+struct ChainArgs {
+    unsigned* ctl;
+    float* agg;       // S x J x 32 Pre tuples, then S x J x 32 Suf tuples
+    int J;            // chunks per strip
+    int S;            // strips
+    long long timeout;
+    int* status;
+    int skip_ticket;  // fault injection: this ticket does not count its arrival (-1: none)
+    int stage;        // chunks per block of the composition's shared-memory staging (>= 1)
+};
+// dynamic shared memory of a chained exchange staging `stage` chunks of mode M's tuples
+template <class M>
+__host__ __device__ constexpr size_t chain_stage_bytes(int stage) {
+    return (size_t)stage * 32 * (sizeof(typename M::Pre) + sizeof(typename M::Suf));
+}
+constexpr int kChainCtlHead = 32;
+__host__ __device__ constexpr long long chain_ctl_words(int S) { return kChainCtlHead + 3LL * S; }
+
+template <typename T>
+__device__ __forceinline__ void st_cg(T* p, const T& v) {
+    constexpr int n = sizeof(T) / 4;
+    const float* s = reinterpret_cast<const float*>(&v);
+    float* d = reinterpret_cast<float*>(p);
+#pragma unroll
+    for (int i = 0; i < n; ++i) __stcg(d + i, s[i]);
+}
+template <typename T>
+__device__ __forceinline__ T ld_cg(const T* p) {
+    constexpr int n = sizeof(T) / 4;
+    T v;
+    const float* s = reinterpret_cast<const float*>(p);
+    float* d = reinterpret_cast<float*>(&v);
+#pragma unroll
+    for (int i = 0; i < n; ++i) d[i] = __ldcg(s + i);
+    return v;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// records a device-side error in the status word (when there is one)
+__device__ __forceinline__ void record_status(int* status, int code) {
+    if (status) atomicExch(status, code);
+}
+
+// This CTA's ticket (call after wait_predecessor: the previous launch has reset the counter).
+__device__ __forceinline__ int chain_ticket(const ChainArgs& c) {
+    __shared__ int s_ticket;
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(&c.ctl[0], 1u);
+        if (t == (unsigned)(c.S * c.J) - 1u) atomicExch(&c.ctl[0], 0u);  // every ticket is out
+        s_ticket = (int)t;
+    }
+    __syncthreads();
+    return s_ticket;
+}
+
+// Shared state of a chained exchange: NWMAX warps per CTA (rows padded to 33 entries).
+template <class M, int NWMAX>
+struct ChainShared {
+    typename M::Pre pre[NWMAX][33];
+    typename M::Suf suf[NWMAX][33];
+};
+
+// pre / suf: the transforms of everything above / below this warp's segment in its column
+// (warp q of chunk r is segment r NW + q of the column; lane = column).  NW >= 2.
+template <class M, int NWMAX>
+__device__ __forceinline__ void chain_exchange(const typename M::Pre& own_pre, const typename M::Suf& own_suf,
+                                               int lane, int warp, int NW, ChainShared<M, NWMAX>& sh,
+                                               const ChainArgs& c, int ticket, typename M::Pre& pre,
+                                               typename M::Suf& suf) {
+    using Pre = typename M::Pre;
+    using Suf = typename M::Suf;
+    __shared__ int s_combine;
+    const int strip = ticket / c.J;
+    const int chunk = ticket - strip * c.J;
+    sh.pre[warp][lane] = own_pre;
+    sh.suf[warp][lane] = own_suf;
+    __syncthreads();
+    Pre wpre = M::pre_identity();
+    for (int q = 0; q < warp; ++q) wpre = M::pre_compose(wpre, sh.pre[q][lane]);
+    Suf wsuf = M::suf_identity();
+    for (int q = warp + 1; q < NW; ++q) wsuf = M::suf_compose(wsuf, sh.suf[q][lane]);
+    if (c.J > 1) {
+        Pre* gpre = reinterpret_cast<Pre*>(c.agg);
+        Suf* gsuf = reinterpret_cast<Suf*>(c.agg + (size_t)c.S * c.J * 32 * (sizeof(Pre) / 4));
+        const size_t mine = ((size_t)strip * c.J + chunk) * 32 + lane;
+        // this chunk's totals: the last warp holds the full prefix, the first the full suffix
+        if (warp == NW - 1) st_cg(gpre + mine, M::pre_compose(wpre, own_pre));
+        if (warp == 0) st_cg(gsuf + mine, M::suf_compose(own_suf, wsuf));
+        __threadfence();
+        __syncthreads();
+        unsigned* arrive = c.ctl + kChainCtlHead + strip;
+        unsigned* flag = c.ctl + kChainCtlHead + c.S + strip;
+        unsigned* reads = c.ctl + kChainCtlHead + 2 * c.S + strip;
+        if (threadIdx.x == 0) {
+            s_combine = 0;
+            if (ticket != c.skip_ticket) s_combine = atomicAdd(arrive, 1u) == (unsigned)c.J - 1u;
+        }
+        __syncthreads();
+        if (s_combine) {
+            // every chunk of the strip has published: exclusive carries in place, top down (prefix
+            // direction, warp 0) and bottom up (suffix direction, warp 1).  The tuples come into
+            // shared memory in blocks of c.stage chunks, loaded by the whole CTA at once: one L2
+            // round trip per block, not one per chunk
+            __threadfence();
+            extern __shared__ __align__(16) float chain_stage[];
+            constexpr int NP = sizeof(Pre) / 4, NS = sizeof(Suf) / 4;
+            float* stp = chain_stage;                                  // c.stage x 32 Pre
+            float* sts = chain_stage + (size_t)c.stage * 32 * NP;      // c.stage x 32 Suf
+            Pre pacc = M::pre_identity();
+            Suf sacc = M::suf_identity();
+            const size_t sbase = (size_t)strip * c.J;
+            for (int b0 = 0; b0 < c.J; b0 += c.stage) {
+                const int nb = min(c.stage, c.J - b0);
+                const int s0 = c.J - b0 - nb;  // the suffix block: chunks [s0, s0 + nb), from the bottom
+                const float4* gp = reinterpret_cast<const float4*>(gpre + (sbase + b0) * 32);
+                const float4* gs = reinterpret_cast<const float4*>(gsuf + (sbase + s0) * 32);
+                float4* sp4 = reinterpret_cast<float4*>(stp);
+                float4* ss4 = reinterpret_cast<float4*>(sts);
+                for (int i = threadIdx.x; i < nb * 8 * NP; i += blockDim.x) sp4[i] = __ldcg(gp + i);
+                for (int i = threadIdx.x; i < nb * 8 * NS; i += blockDim.x) ss4[i] = __ldcg(gs + i);
+                __syncthreads();
+                if (warp == 0) {
+                    const Pre* sp = reinterpret_cast<const Pre*>(stp);
+                    for (int j = 0; j < nb; ++j) {
+                        const Pre v = sp[j * 32 + lane];
+                        st_cg(gpre + (sbase + b0 + j) * 32 + lane, pacc);
+                        pacc = M::pre_compose(pacc, v);
+                    }
+                } else if (warp == 1) {
+                    const Suf* ss = reinterpret_cast<const Suf*>(sts);
+                    for (int j = nb - 1; j >= 0; --j) {
+                        const Suf v = ss[j * 32 + lane];
+                        st_cg(gsuf + (sbase + s0 + j) * 32 + lane, sacc);
+                        sacc = M::suf_compose(v, sacc);
+                    }
+                }
+                __syncthreads();
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                atomicExch(arrive, 0u);
+                st_release_u32(flag, 1u);
+            }
+        } else if (threadIdx.x == 0) {
+            if (ld_acquire_u32(flag) == 0u && ld_acquire_u32(c.ctl + 1) == 0u) {
+                const long long t0 = clock64();
+                while (ld_acquire_u32(flag) == 0u) {
+                    if (ld_acquire_u32(c.ctl + 1) != 0u) break;
+                    if (clock64() - t0 > c.timeout) {
+                        atomicExch(c.ctl + 1, 1u);
+                        record_status(c.status, DTS_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(64);  // leave the L2 to the composing CTA
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        wpre = M::pre_compose(ld_cg(gpre + mine), wpre);
+        wsuf = M::suf_compose(wsuf, ld_cg(gsuf + mine));
+        __syncthreads();  // every lane has read its carries
+        if (threadIdx.x == 0 && atomicAdd(reads, 1u) == (unsigned)c.J - 1u) {
+            // the strip's last reader: its flag and count go back to zero for the next launch
+            atomicExch(reads, 0u);
+            atomicExch(flag, 0u);
+        }
+    }
+    pre = wpre;
+    suf = wsuf;
+}
+
 // ---------------------------------------------------------------- TMA and mbarriers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 

@@ -479,24 +479,27 @@ class DTSSolve(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, guide, target, conf, z_init, params: Params):
+        # what dts_solve_backward differentiates; refused here, before the workspace is allocated
+        if params.update == UPDATE_CG or params.conf_mode != CONF_PLAIN or params.filter_kernel != KERNEL_RF:
+            raise ValueError("DTSSolve: the backward supports the recursive-filter kernel, plain confidence and "
+                             "the GD or Jacobi update only")
         p = dataclasses.replace(params, save_checkpoints=backward_checkpoint_mode(guide, params))
         ws = workspace(guide, p, with_backward=True)
         z = dts_solve(guide, target, conf, p, z_init=z_init, ws=ws)
         zi = z_init if z_init is not None else torch.empty(0, device=target.device)
-        ctx.save_for_backward(guide, target, conf, zi)
-        ctx.ws = ws
+        # the workspace holds the checkpoints: a saved tensor, kept while the graph is retained
+        ctx.save_for_backward(guide, target, conf, zi, ws)
         ctx.params = p
         ctx.has_zinit = z_init is not None
         return z
 
     @staticmethod
     def backward(ctx, grad_z):
-        guide, target, conf, zi = ctx.saved_tensors
-        gt, gc, gg, gz0 = dts_solve_backward(guide, target, conf, ctx.params, ctx.ws,
+        guide, target, conf, zi, ws = ctx.saved_tensors
+        gt, gc, gg, gz0 = dts_solve_backward(guide, target, conf, ctx.params, ws,
                                              grad_z.contiguous().float(),
                                              z_init=zi if ctx.has_zinit else None,
                                              need_guide=ctx.needs_input_grad[0])
-        ctx.ws = None
         return (gg.to(guide.dtype).reshape(guide.shape) if ctx.needs_input_grad[0] else None,
                 gt.to(target.dtype) if ctx.needs_input_grad[1] else None,
                 gc if ctx.needs_input_grad[2] else None,

@@ -40,12 +40,7 @@ def test_every_timed_kernel_has_algorithmic_bytes():
     from paper_1805_04590_gb300 import dts
 
     lib = dts.load()
-    names = []
-    for k in range(256):
-        n = lib.dts_kernel_name(k).decode()
-        if n == "unknown":
-            break
-        names.append(n)
+    names = [n for n in (lib.dts_kernel_name(k).decode() for k in range(256)) if n != "unknown"]
     assert len(names) > 20
     for n in names:
         for s_d, s_t in ((4, 4), (2, 2)):

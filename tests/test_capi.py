@@ -51,9 +51,9 @@ def test_workspace_size_layout():
     n0 = lib.dts_workspace_size(ctypes.byref(g), ctypes.byref(p), 0)
     pitch = 64
     plane = 40 * pitch * 4
-    # split vertical pass: 5 aggregate + 2 carry planes of (W rounded to 128) x ceil(H/32) floats,
-    # and one ticket counter per 128 columns, each region 256-byte aligned
-    split = 5 * 128 * 2 * 4 + 2 * 128 * 2 * 4 + 256
+    # chained vertical passes: 32 + 3 S control words (S = 2 strips of 32 columns), then per strip
+    # and 64-row chunk 32 columns of up to 9 floats of tuples, each region 256-byte aligned
+    split = 256 + 2 * 1 * 32 * 9 * 4
     # dY tiled by 8-column strips for the strip kernel: 7 strips of 4 * 2 warps * 9 rows + 1 rows
     # of 8 values (segments of 9 rows, 2 warps for 40 rows), 256-byte aligned
     tiled = (7 * 73 * 8 * 4 + 255) // 256 * 256
@@ -180,13 +180,14 @@ def test_conjugate_gradient_workspace_and_limits():
                              None) == 2, field
 
 
-def test_charbonnier_needs_the_gradient_step():
+def test_charbonnier_is_not_taken_with_conjugate_gradients():
+    """The Charbonnier loss goes with the gradient step and the fixed point of Eq. 4; conjugate
+    gradients keep the square (DTS_ERR_UNSUPPORTED before any device work)."""
     lib = dts.load()
     g = _guide()
-    for upd in (dts.UPDATE_JACOBI, dts.UPDATE_CG):
-        p = dts.Params(update=upd, charbonnier_eps=1e-3).c()
-        assert lib.dts_solve(ctypes.byref(g), 0x2000, 0, 0x3000, None, ctypes.byref(p), 0x4000, 0x5000, 1 << 30,
-                             None) == 2
+    p = dts.Params(update=dts.UPDATE_CG, charbonnier_eps=1e-3).c()
+    assert lib.dts_solve(ctypes.byref(g), 0x2000, 0, 0x3000, None, ctypes.byref(p), 0x4000, 0x5000, 1 << 30,
+                         None) == 2
 
 
 def test_binding_structs_match_the_c_layout(tmp_path):

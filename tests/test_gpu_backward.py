@@ -80,6 +80,14 @@ def test_backward_charbonnier(H, W):
     run_case(H, W, K=3, seed=H + W + 6, eps=1.0, zinit=True)
 
 
+@pytest.mark.parametrize("eps", [0.3, 0.01])
+def test_backward_charbonnier_fixed_point(eps):
+    """The reverse mode of the fixed point of Eq. 4 with the Charbonnier loss's weight at the
+    current iterate (the weight reaches z_k and t through the residual)."""
+    run_case(64, 80, K=4, update=dts.UPDATE_JACOBI, seed=71, eps=eps)
+    run_case(300, 45, K=3, update=dts.UPDATE_JACOBI, seed=72, eps=eps, zinit=True)
+
+
 @pytest.mark.parametrize("update", [dts.UPDATE_GD, dts.UPDATE_JACOBI])
 def test_backward_kept_pass_inputs(update):
     """save_checkpoints = 2 (every pass input kept, no recompute) gives the same forward and
@@ -101,8 +109,9 @@ def test_backward_needs_kept_iterates():
         dts.dts_solve_backward(g, t, t, prm, ws, t)
 
 
-# columns over 4096 rows: the vertical adjoint runs in chunks of 2048 rows (two launches, chunk
-# totals composed across chunks); rows over 8192: 16 positions per thread in the row adjoint
+# columns over 4096 rows: the vertical adjoint runs on chains of CTAs of 128 rows (one launch,
+# chunk totals composed through global memory); rows over 8192: 16 positions per thread in the
+# row adjoint
 @pytest.mark.parametrize("H,W,update", [(4500, 40, dts.UPDATE_GD), (9000, 9, dts.UPDATE_JACOBI),
                                         (5, 9000, dts.UPDATE_GD), (3, 10240, dts.UPDATE_JACOBI)])
 def test_backward_tall_and_wide(H, W, update):
@@ -156,6 +165,29 @@ def test_autograd_function_matches_oracle():
     close(tt.grad.cpu().numpy(), ref["t"], "autograd t")
     close(cc.grad.cpu().numpy(), ref["c"], "autograd c")
     close(g.grad.cpu().numpy(), ref["guide"], "autograd guide")
+
+
+def test_autograd_retain_graph_and_unsupported_modes():
+    """A second backward through a retained graph gives the same gradients (the workspace holding
+    the checkpoints is a saved tensor); modes without a backward are refused in the forward."""
+    H, W = 33, 41
+    rng = np.random.default_rng(33)
+    I = guide_noisy(H, W, 3, 33)
+    t = rng.normal(size=(H, W)).astype(np.float32)
+    c = rng.uniform(0.1, 1.0, (H, W)).astype(np.float32)
+    prm = dts.Params(lam=0.9, sigma_s=8.0, sigma_r=0.3, iterations=3)
+    tt = T(t).requires_grad_(True)
+    z = dts.solve(T(I), tt, T(c), prm)
+    loss = (z * z).sum()
+    loss.backward(retain_graph=True)
+    first = tt.grad.clone()
+    tt.grad = None
+    loss.backward()
+    assert torch.equal(first, tt.grad)
+    for bad in (dict(update=dts.UPDATE_CG), dict(conf_mode=dts.CONF_SUPPORT), dict(filter_kernel=dts.KERNEL_BOX)):
+        q = dts.Params(lam=0.9, sigma_s=8.0, sigma_r=0.3, iterations=3, **bad)
+        with pytest.raises(ValueError):
+            dts.solve(T(I), T(t).requires_grad_(True), T(c), q)
 
 
 def test_backward_fp16_distances_runs_and_agrees_roughly():
@@ -247,6 +279,29 @@ def test_backward_multispectral_reduced():
     prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes,
                      save_checkpoints=2)
     gz = np.random.default_rng(1200).normal(size=p.target.shape).astype(np.float32)
+    g, tt, cc = T(p.guide), T(p.target), T(p.conf)
+    ws = dts.workspace(g, prm, with_backward=True)
+    dts.dts_solve(g, tt, cc, prm, ws=ws)
+    gt, gc, gg, _ = dts.dts_solve_backward(g, tt, cc, prm, ws, T(gz))
+    assert dts.dts_last_status() == 0
+    ref = oracle.solve_backward(p.guide, p.target, p.conf, gz, lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r,
+                                iterations=q.iterations, passes=q.passes)
+    close(gt.cpu().numpy(), ref["t"], "grad target")
+    close(gc.cpu().numpy(), ref["c"], "grad conf")
+    close(gg.cpu().numpy(), ref["guide"], "grad guide")
+
+
+@pytest.mark.parametrize("H,W", [(10000, 64), (64, 10000)])
+def test_backward_multispectral_full_size_slices(H, W):
+    """The multispectral generator on slices that run the full 10000 x 10000 image's backward
+    plans (the 10000-row chained vertical adjoint; 10000-column rows), K = 10 with every pass input
+    kept, as the bench runs it: every gradient against the oracle's reverse mode."""
+    rng = np.random.Generator(np.random.PCG64(1004))
+    p = workloads.multispectral_image(H, W, rng, bands=16, gy=max(1, H // 100), gx=max(1, W // 100))
+    q = workloads.make(4, H=8, W=8).params
+    prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes,
+                     save_checkpoints=2)
+    gz = np.random.default_rng(H + W).normal(size=p.target.shape).astype(np.float32)
     g, tt, cc = T(p.guide), T(p.target), T(p.conf)
     ws = dts.workspace(g, prm, with_backward=True)
     dts.dts_solve(g, tt, cc, prm, ws=ws)

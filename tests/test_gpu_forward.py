@@ -246,6 +246,33 @@ def test_solve_charbonnier_box_kernel_and_full_stereo_workload():
     assert_close(z.cpu().numpy(), ref, p.target, "charbonnier stereo 2880x1988")
 
 
+@pytest.mark.parametrize("H,W", [(37, 53), (300, 257), (2300, 96)])
+def test_solve_charbonnier_fixed_point_paper_eps(H, W):
+    """The Charbonnier loss at the paper's eps = 0.001 with confidences in [0.1, 1], through the
+    fixed point of Eq. 4 with the loss's weight at the current iterate (its steps are majorize-
+    minimize steps, so FP32 and FP64 iterates do not part): the FP32 bound."""
+    prob = workloads.random_problem(H, W, C=3, seed=H + 11 * W)
+    prm = dts.Params(lam=0.99, sigma_s=8.0, sigma_r=0.2, iterations=10, update=dts.UPDATE_JACOBI,
+                     charbonnier_eps=1e-3)
+    z = dts.dts_solve(to_dev(prob.guide), to_dev(prob.target), to_dev(prob.conf), prm)
+    assert dts.dts_last_status() == 0
+    ref = oracle_solve(prob.guide, prob.target, prob.conf, prm, charbonnier_eps=1e-3)
+    assert_close(z.cpu().numpy(), ref, prob.target, f"charbonnier fixed point {H}x{W}")
+
+
+def test_solve_charbonnier_fixed_point_full_stereo_workload():
+    """The stereo workload at full size (2880 x 1988, 20 iterations, confidences from the residual
+    in [0.05, 1]) with the paper's stereo loss, eps = 0.001 pixel, through the fixed point of Eq. 4."""
+    wl = workloads.make(1)
+    p, q = wl.problems[0], wl.params
+    prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes,
+                     update=dts.UPDATE_JACOBI, charbonnier_eps=1e-3)
+    z = dts.dts_solve(to_dev(p.guide), to_dev(p.target), to_dev(p.conf), prm)
+    assert dts.dts_last_status() == 0
+    ref = oracle_solve(p.guide, p.target, p.conf, prm, charbonnier_eps=1e-3)
+    assert_close(z.cpu().numpy(), ref, p.target, "charbonnier fixed point stereo 2880x1988")
+
+
 def test_solve_multispectral_reduced():
     """The 16-band multispectral generator at 2500 x 2500 (its full 10000 x 10000 size is timed
     by the bench): the 10-iteration solve against the oracle."""
@@ -269,6 +296,79 @@ def test_solve_multispectral_full_size_constant_target():
     z = dts.dts_solve(to_dev(p.guide), t, to_dev(p.conf), prm)
     assert dts.dts_last_status() == 0
     assert float((z - 0.625).abs().max()) <= 1e-5
+
+
+def multispectral_slice(H, W, seed=1004):
+    """A slice of the 16-band multispectral generator at its full-size cell density (cells of about
+    100 x 100 pixels): 10000 x 64 runs every vertical pass with the 10000-row plan of the full
+    image, 64 x 10000 every horizontal pass with its 10000-column plan."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return workloads.multispectral_image(H, W, rng, bands=16, gy=max(1, H // 100), gx=max(1, W // 100))
+
+
+@pytest.mark.parametrize("H,W", [(10000, 64), (64, 10000)])
+@pytest.mark.parametrize("sdt", [torch.float32, torch.bfloat16])
+def test_solve_multispectral_full_size_slices(H, W, sdt):
+    """The multispectral solve (sigma_s 32, sigma_r 0.1, lambda 0.99, K = 10) on slices that run the
+    full 10000 x 10000 image's launch plans, against the oracle element by element.  BF16 guide and
+    target storage: within the FP32 bound of the oracle run on the same rounded inputs; from the
+    oracle run on the unrounded inputs, no further than the rounding itself moves the oracle's
+    solution plus that bound (with sigma_s / sigma_r = 320 the rounding of 16 guide bands moves the
+    distances, and the solution, by a few percent of the target range)."""
+    p = multispectral_slice(H, W)
+    q = workloads.make(4, H=8, W=8).params
+    prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes)
+    g, t = to_dev(p.guide, sdt), to_dev(p.target, sdt)
+    z = dts.dts_solve(g, t, to_dev(p.conf), prm).cpu().numpy()
+    assert dts.dts_last_status() == 0
+    ref = oracle_solve(rounded(g), rounded(t), p.conf, prm)
+    assert_close(z, ref, rounded(t), f"multispectral slice {H}x{W} on the stored inputs")
+    if sdt != torch.float32:
+        ref0 = oracle_solve(p.guide, p.target, p.conf, prm)
+        rng0 = float(np.ptp(p.target))
+        err = float(np.abs(z - ref0).max()) / rng0
+        moved = float(np.abs(ref - ref0).max()) / rng0  # what the input rounding alone does
+        assert err <= moved + TOL, f"bf16 storage: {err:.3e} of the range from the unrounded solve " \
+                                   f"(rounding alone: {moved:.3e})"
+
+
+# ---------------------------------------------------------------- chained and cluster vertical passes
+# Columns over 2176 rows run on chains of CTAs (col_chain_kernel): 128-row chunks (16 rows x 8
+# warps) by default, 256-row chunks (16 x 16, 32 x 8) as tuned shapes; the cluster kernel keeps
+# tall columns for batched solves and as a tuned shape ((40, 16) in clusters of 7 here).  Each
+# shape is set through a tuned plan for a height no other test uses (tuned plans last for the
+# process).  16384 rows is the tallest column.
+@pytest.mark.parametrize("H,shape", [(2305, (16, 8, -1)), (2306, (16, 16, -1)), (2307, (32, 8, -1)),
+                                     (4101, (40, 16, 7)), (16384, None)])
+def test_filter_chain_and_cluster_shapes(H, shape):
+    W = 70 if H < 16384 else 5
+    if shape is not None:
+        dts.autotune_import("col %d %d %d %d\n" % ((H,) + shape))
+        assert ("col %d %d %d %d" % ((H,) + shape)) in dts.autotune_export()
+    prob = workloads.random_problem(H, W, C=3, seed=H + W)
+    prm = dts.Params(sigma_s=40.0, sigma_r=0.3, passes=3)
+    out = dts.dts_filter(to_dev(prob.guide), to_dev(prob.target), prm)
+    assert dts.dts_last_status() == 0
+    ref = oracle.filter(prob.guide, prob.target, 40.0, 0.3, passes=3)
+    assert_close(out.cpu().numpy(), ref, prob.target, f"filter {H}x{W} shape {shape}")
+
+
+@pytest.mark.parametrize("update", [dts.UPDATE_GD, dts.UPDATE_JACOBI])
+def test_solve_chained_columns_support_and_zinit(update):
+    """Chained vertical passes inside the solve: the support-weighted confidence (its column sweep
+    runs on the chain for any column over 256 rows) and a caller's z_init."""
+    prob = workloads.random_problem(2600, 45, C=3, seed=26 + update)
+    prm = dts.Params(lam=1.0, sigma_s=8.0, sigma_r=0.2, iterations=4, update=update)
+    z0 = np.random.default_rng(5).normal(size=prob.target.shape).astype(np.float32)
+    z = dts.dts_solve(to_dev(prob.guide), to_dev(prob.target), to_dev(prob.conf), prm, z_init=to_dev(z0))
+    ref = oracle_solve(prob.guide, prob.target, prob.conf, prm, z_init=z0)
+    assert_close(z.cpu().numpy(), ref, prob.target, "chain z_init")
+    prm.conf_mode = dts.CONF_SUPPORT
+    prm.update = dts.UPDATE_JACOBI
+    z = dts.dts_solve(to_dev(prob.guide), to_dev(prob.target), to_dev(prob.conf), prm)
+    ref = oracle_solve(prob.guide, prob.target, prob.conf, prm)
+    assert_close(z.cpu().numpy(), ref, prob.target, "chain support")
+    assert dts.dts_last_status() == 0
 
 
 # ---------------------------------------------------------------- confidence (Eq. 7)

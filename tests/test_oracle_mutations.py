@@ -1,6 +1,6 @@
 """The pins catch plausible mistakes in the oracle (CPU).
 
-Each of the 79 cases below plants one mistake in a copy of oracle/dts_oracle.c — a dropped term, a wrong
+Each of the 85 cases below plants one mistake in a copy of oracle/dts_oracle.c — a dropped term, a wrong
 sign, index or operand, passes in the wrong order — compiles the copy with the oracle's own
 flags, and runs the pin suite (tests/test_oracle_pins.py) against it in a fresh process
 (DTS_ORACLE_SO points the oracle package at the copy).  Every mutant must fail at least one pin;
@@ -35,7 +35,7 @@ MUTANTS = [
      "orc_col_pass(H, W, dst, dY, a[N - 1 - i]);"),
     ("gradient step: smoothness term sign", "out[p] = zk[p] - e * (lambda * (zk[p] - zbar[p])",
      "out[p] = zk[p] - e * (lambda * (zbar[p] - zk[p])"),
-    ("fixed point: z_k for z_bar", "(lambda * zbar[p] + chat[p] * t[p]) / den", "(lambda * zk[p] + chat[p] * t[p]) / den"),
+    ("fixed point: z_k for z_bar", "(lambda * zbar[p] + cw * t[p]) / den", "(lambda * zk[p] + cw * t[p]) / den"),
     ("Charbonnier: eps not squared", "r / sqrt(r * r + eps * eps) : r;", "r / sqrt(r * r + eps) : r;"),
     ("support: own weight counted twice", "out[j * so] = P[j] + Q[j] - x[j * sx];", "out[j * so] = P[j] + Q[j];"),
     ("Eq. 7: variance without the square", "double v = m2[i] - m1[i] * m1[i];", "double v = m2[i] - m1[i];"),
@@ -43,8 +43,19 @@ MUTANTS = [
     ("adjoint: sign of ln a", "double la = log(a);", "double la = -log(a);"),
     ("adjoint: causal weight gradient sign", "wbar[j] += gJ[j] * (J[j - 1] - x[j * sx]);",
      "wbar[j] += gJ[j] * (x[j * sx] - J[j - 1]);"),
-    ("backward, fixed point: confidence gradient sign", "cb[p] += lambda * (t[p] - zbar[p]) / (den * den) * g[p];",
-     "cb[p] += lambda * (zbar[p] - t[p]) / (den * den) * g[p];"),
+    ("backward, fixed point: confidence gradient sign",
+     "const double gcw = lambda * (t[p] - zbar[p]) / (den * den) * g[p];",
+     "const double gcw = lambda * (zbar[p] - t[p]) / (den * den) * g[p];"),
+    ("fixed point, Charbonnier: loss weight left out", "cw = chat[p] / sqrt(r * r + eps * eps);", "cw = chat[p];"),
+    ("fixed point, Charbonnier: weight squared", "cw = chat[p] / sqrt(r * r + eps * eps);",
+     "cw = chat[p] / (r * r + eps * eps);"),
+    ("backward, fixed point Charbonnier: iterate path dropped", "gprev[p] = gr;", "gprev[p] = 0.0;"),
+    ("backward, fixed point Charbonnier: target path sign", "tb[p] += cw / den * g[p] - gr;",
+     "tb[p] += cw / den * g[p] + gr;"),
+    ("backward, fixed point Charbonnier: weight derivative power", "-c[p] * r * w * w * w * gcw",
+     "-c[p] * r * w * w * gcw"),
+    ("backward, fixed point Charbonnier: confidence gradient without the weight", "cb[p] += w * gcw;",
+     "cb[p] += gcw;"),
     ("backward, gradient step: data term dropped from the carry",
      "gprev[p] = (1.0 - eta * lambda - eta * c[p] * d2) * g[p];", "gprev[p] = (1.0 - eta * lambda) * g[p];"),
     ("CG: factor 2 of the data term dropped", "q[i] = lambda * (t1[i] - t2[i]) + 2.0 * c[i] * p[i];",
@@ -83,8 +94,8 @@ MUTANTS = [
     ("box kernel: columns on dX", "box_line(H, dst + x, W, dY + x, W, r, ct, tmp);",
      "box_line(H, dst + x, W, dX + x, W, r, ct, tmp);"),
     ("adjoint: first input gradient dropped", "gin[0] = gJ[0];", "gin[0] = 0.0;"),
-    ("backward, fixed point: lambda for c in the target gradient", "tb[p] += c[p] / den * g[p];",
-     "tb[p] += lambda / den * g[p];"),
+    ("backward, fixed point: lambda for c in the target gradient", "tb[p] += cw / den * g[p] - gr;",
+     "tb[p] += lambda / den * g[p] - gr;"),
     ("backward, Charbonnier: curvature", "eps * eps / (s * s * s)", "eps / (s * s)"),
     ("CG: alpha inverted", "const double alpha = rr / pq;", "const double alpha = pq / rr;"),
     ("CG: residual updated with p", "r[i] -= alpha * q[i];", "r[i] -= alpha * p[i];"),

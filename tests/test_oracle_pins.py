@@ -402,7 +402,9 @@ def _objective(I, t, c, gz, z0=None, **kw):
 @pytest.mark.parametrize("update,norm,eps", [(oracle.UPDATE_GD, oracle.NORM_L1, 0.0),
                                              (oracle.UPDATE_JACOBI, oracle.NORM_L1, 0.0),
                                              (oracle.UPDATE_GD, oracle.NORM_L2, 0.0),
-                                             (oracle.UPDATE_GD, oracle.NORM_L1, 0.3)])
+                                             (oracle.UPDATE_GD, oracle.NORM_L1, 0.3),
+                                             (oracle.UPDATE_JACOBI, oracle.NORM_L1, 0.3),
+                                             (oracle.UPDATE_JACOBI, oracle.NORM_L2, 0.05)])
 def test_backward_matches_central_differences(update, norm, eps):
     rng = np.random.default_rng(23 + update + 2 * norm)
     C, H, W = 2, 5, 6
@@ -727,3 +729,54 @@ def test_charbonnier_limits():
     z1 = oracle.solve(I, t, c, iterations=1, z_init=z0, charbonnier_eps=1e-9, **kw)
     zbar = oracle.filter(I, z0, 8.0, 0.2)
     np.testing.assert_allclose(z1, z0 - 0.99 * (0.9 * (z0 - zbar) + c * np.sign(z0 - t)), rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Charbonnier loss, fixed point of Eq. 4
+def test_charbonnier_fixed_point_step_descends_its_pixel_objective():
+    """One fixed-point step with the Charbonnier loss is a majorize-minimize step: with z_bar = A z_k
+    held, every pixel's h(z) = lambda/2 (z - z_bar)^2 + c sqrt((z - t)^2 + eps^2) does not increase
+    from z_k to z_{k+1} (at the paper's eps = 0.001 and at 0.05, residuals on both sides of eps)."""
+    I, t, c = _small(H=9, W=11, seed=41)
+    rng = np.random.default_rng(41)
+    for eps in (1e-3, 0.05):
+        for spread in (1e-3, 0.3):
+            z0 = t + rng.normal(0, spread, t.shape)
+            z1 = oracle.solve(I, t, c, lam=0.9, sigma_s=8.0, sigma_r=0.2, iterations=1, z_init=z0,
+                              update=oracle.UPDATE_JACOBI, charbonnier_eps=eps)
+            zbar = oracle.filter(I, z0, 8.0, 0.2)
+            h = lambda z: 0.45 * (z - zbar) ** 2 + c * np.sqrt((z - t) ** 2 + eps ** 2)
+            assert np.all(h(z1) <= h(z0) + 1e-12), (eps, spread, float((h(z1) - h(z0)).max()))
+            # and it is a strict descent wherever z_k is not already the minimiser of h
+            assert float((h(z0) - h(z1)).max()) > 0.0
+
+
+@pytest.mark.parametrize("eps", [1e-3, 0.05])
+def test_charbonnier_fixed_point_is_stationary_for_the_loss(eps):
+    """Iterated to convergence, the fixed point satisfies the Charbonnier stationarity
+    lambda (z - A z) + c rho'(z - t) = 0, rho'(r) = r / sqrt(r^2 + eps^2) -- the derivative of the loss,
+    here by central differences of the loss itself -- on a dense 8 x 10 problem."""
+    I, t, c = _small(H=8, W=10, seed=43)
+    z = oracle.solve(I, t, c, lam=0.9, sigma_s=8.0, sigma_r=0.2, iterations=4000, update=oracle.UPDATE_JACOBI,
+                     charbonnier_eps=eps)
+    hh = 1e-4 * eps
+    loss = lambda zz: c * np.sqrt((zz - t) ** 2 + eps ** 2)
+    slope = (loss(z + hh) - loss(z - hh)) / (2 * hh)
+    res = 0.9 * (z - oracle.filter(I, z, 8.0, 0.2)) + slope
+    assert float(np.abs(res).max()) <= 1e-8
+
+
+def test_charbonnier_fixed_point_matches_the_gradient_step_and_the_quadratic_limit():
+    """Where the gradient step of the Charbonnier loss is stable (eps = 0.3, step 0.5) both readings
+    converge to the same point; for eps >> |z - t| the fixed point with confidence c eps is that of
+    Eq. 4 with c."""
+    I, t, c = _small(H=7, W=9, seed=47)
+    kw = dict(lam=0.9, sigma_s=8.0, sigma_r=0.2, iterations=3000, charbonnier_eps=0.3)
+    zj = oracle.solve(I, t, c, update=oracle.UPDATE_JACOBI, **kw)
+    zg = oracle.solve(I, t, c, update=oracle.UPDATE_GD, step=0.5, **kw)
+    np.testing.assert_allclose(zj, zg, rtol=0, atol=1e-9)
+    eps = 1e6
+    np.testing.assert_allclose(
+        oracle.solve(I, t, c * eps, lam=0.9, sigma_s=8.0, sigma_r=0.2, iterations=5, update=oracle.UPDATE_JACOBI,
+                     charbonnier_eps=eps),
+        oracle.solve(I, t, c, lam=0.9, sigma_s=8.0, sigma_r=0.2, iterations=5, update=oracle.UPDATE_JACOBI),
+        rtol=0, atol=1e-9)

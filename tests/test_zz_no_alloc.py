@@ -54,6 +54,40 @@ def test_noalloc_matches_workspace_solve_on_consecutive_calls():
             assert err <= TOL * rng, err
 
 
+# modes whose working planes differ: conjugate gradients (three more planes and FP64 scalars), the
+# support-weighted confidence (its own plane), FP16 distances (and their strip-tiled copy), and a
+# column tall enough for the chained vertical pass (its control words and chunk tuples)
+CONFIGS = {
+    "cg": ((173, 250), dict(update=dts.UPDATE_CG)),
+    "support": ((173, 250), dict(conf_mode=dts.CONF_SUPPORT, update=dts.UPDATE_JACOBI)),
+    "f16": ((173, 250), dict(dist_dtype=dts.F16)),
+    "chain": ((2300, 40), dict()),
+}
+
+
+@pytest.mark.parametrize("name", list(CONFIGS))
+def test_noalloc_after_a_call_of_another_mode_and_size(name):
+    """Every plane a solve reads is written by that solve first: a mode run right after a call of
+    another mode and size on the shared array matches the workspace solve, twice in a row."""
+    lib = dts.load()
+    other = "chain" if name != "chain" else "cg"
+    (H0, W0), kw0 = CONFIGS[other]
+    g0, t0, c0, _ = _problem(H0 + 11, W0 + 7, 80)
+    p0 = dts.Params(lam=0.99, sigma_s=16.0, sigma_r=0.1, iterations=4, **kw0)
+    assert _call(lib, g0, t0, c0, p0, torch.empty_like(t0)) == 0
+    (H, W), kw = CONFIGS[name]
+    g, t, c, rng = _problem(H, W, 81)
+    prm = dts.Params(lam=0.99, sigma_s=16.0, sigma_r=0.1, iterations=5, **kw)
+    ref = dts.dts_solve(g, t, c, prm)
+    for _ in range(2):
+        out = torch.full_like(t, float("nan"))
+        assert _call(lib, g, t, c, prm, out) == 0
+        torch.cuda.synchronize()
+        assert dts.dts_last_status() == 0
+        err = float((out - ref).abs().max())
+        assert err <= TOL * rng, (name, err)
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch():
     lib = dts.load()
     cap = lib.dts_noalloc_max_workspace()
