@@ -78,6 +78,7 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3):
         "col_pass_kernel": 8 + s_d,
         "col_strip_kernel": 8 + s_d,
         "col_chain_kernel": 8 + s_d,
+        "col_tall_kernel": 8 + s_d,
         "col_bwd_chain_kernel": 24 + s_d,
         "row_pass_kernel<support>": s_d + 4,
         "col_pass_kernel<support>": 12 + s_d,
@@ -94,6 +95,7 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3):
         "col_pass_kernel<transpose>": 8 + s_d + 4.0 / N,
         "col_strip_kernel<transpose>": 8 + s_d + 4.0 / N,
         "col_chain_kernel<transpose>": 8 + s_d + 4.0 / N,
+        "col_tall_kernel<transpose>": 8 + s_d + 4.0 / N,
         "square_plane_kernel": 8,
         "confidence_kernel": 12,
         "box_line_kernel": 12,

@@ -224,10 +224,13 @@ int dts_solve_batched(int n, const dts_guide* guides, const void* const* targets
  * them.  Synchronises `stream`.  The results live in the process (see dts_autotune_export). */
 int dts_autotune(const dts_guide* guide, const dts_params* params, void* ws, size_t ws_bytes, dts_stream stream);
 
-/* Text of the recorded shapes ("row W items" and "col H items warps cluster" lines; cluster 0:
- * the strip kernel).  Batched solves take the cluster shapes for their vertical passes.  With
- * buf == NULL returns the bytes needed (including the terminating 0); else copies and returns
- * that count, or minus DTS_ERR_INVALID_ARG when len is too small. */
+/* Text of the recorded shapes: "row W items" lines (positions per thread of the horizontal
+ * passes), "col H items warps cluster" lines (the vertical passes: cluster > 0 CTAs of `warps`
+ * warps of `items` rows per thread; 0 the strip kernel; -1 the chained CTAs; -2 the persistent
+ * TMA-fed clusters for tall columns) and "bcol H items warps cluster" lines (the vertical passes
+ * of dts_solve_backward: cluster > 0, or -1 chained).  Batched solves take the cluster shapes for
+ * their vertical passes.  With buf == NULL returns the bytes needed (including the terminating
+ * 0); else copies and returns that count, or minus DTS_ERR_INVALID_ARG when len is too small. */
 int dts_autotune_export(char* buf, size_t len);
 
 /* Records shapes from text in the format of dts_autotune_export (shapes that are not valid

@@ -75,6 +75,15 @@ int blocks_per_sm(const void* kernel, int block, size_t smem) {
     return n;
 }
 
+// Flag value of the next chained vertical pass: distinct for every launch of the process (a
+// 32-bit counter that skips 0, the value a solve's cleared flags hold).
+unsigned next_chain_epoch() {
+    static std::atomic<unsigned> counter{0};
+    unsigned e = counter.fetch_add(1u) + 1u;
+    while (e == 0u) e = counter.fetch_add(1u) + 1u;
+    return e;
+}
+
 // The status word of the current device, as looked up by ensure_prepared (null before).
 int* status_word() {
     int dev = 0;
@@ -978,6 +987,7 @@ extern "C" int dts_solve_batched(int n, const dts_guide* guides, const void* con
 // ---------------------------------------------------------------- autotuner
 namespace dts {
 std::string tuned_export();
+std::string tuned_bwd_export();
 }
 
 extern "C" int dts_autotune(const dts_guide* guide, const dts_params* params, void* ws, size_t ws_bytes,
@@ -1040,11 +1050,11 @@ extern "C" int dts_autotune(const dts_guide* guide, const dts_params* params, vo
     // horizontal items per thread
     int best_items = pl.rows.items;
     best = 1e30f;
-    for (int items : {8, 16}) {
+    for (int items : {8, 16, 32}) {
         RowPlan rp;
         rp.items = items;
         rp.tpr = ((guide->W + items - 1) / items + 31) / 32 * 32;
-        if (rp.tpr > 1024) continue;
+        if (rp.tpr > (items >= 32 ? 320 : 1024)) continue;
         rp.rpb = rp.tpr < 256 ? 256 / rp.tpr : 1;
         PassArgs r = base_pass(guide, L);
         r.src = u;
@@ -1065,7 +1075,7 @@ extern "C" int dts_autotune(const dts_guide* guide, const dts_params* params, vo
 }
 
 extern "C" int dts_autotune_export(char* buf, size_t len) {
-    const std::string t = tuned_export();
+    const std::string t = tuned_export() + tuned_bwd_export();
     if (!buf) return (int)t.size() + 1;
     if (len < t.size() + 1) return -DTS_ERR_INVALID_ARG;
     memcpy(buf, t.c_str(), t.size() + 1);
@@ -1078,7 +1088,9 @@ extern "C" int dts_autotune_import(const char* text) {
     while (*p) {
         int a = 0, b = 0, c = 0, d = 0, used = 0;
         if (sscanf(p, "row %d %d %n", &a, &b, &used) == 2 && used > 0) {
-            if (a >= 1 && (b == 8 || b == 16)) set_tuned_row(a, b);
+            if (a >= 1 && (b == 8 || b == 16 || b == 32)) set_tuned_row(a, b);
+        } else if (sscanf(p, "bcol %d %d %d %d %n", &a, &b, &c, &d, &used) == 4 && used > 0) {
+            set_tuned_bwd_col(a, ColPlan{b, c, d});
         } else if (sscanf(p, "col %d %d %d %d %n", &a, &b, &c, &d, &used) == 4 && used > 0) {
             ColPlan cp{b, c, d};
             ColPlan cand[16];

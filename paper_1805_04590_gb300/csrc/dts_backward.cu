@@ -17,6 +17,9 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "dts_scan.cuh"
 
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(512, bwd_col_min_blocks<ITEMS>()) col_bwd_kern
 // CTA's ticket)
 template <int ITEMS, int NW>
 constexpr int bwd_chain_min_blocks() {
-    return ITEMS * NW <= 64 ? 4 : 2;
+    return (NW >= 32 || ITEMS >= 16) ? 1 : ITEMS * NW <= 64 ? 4 : 2;
 }
 
 template <int ITEMS, int NW, bool DHALF>
@@ -490,6 +493,7 @@ cudaError_t launch_col_bwd_chain_t(const BwdArgs& a, cudaStream_t s) {
     c.status = a.status;
     if (!c.ctl || !c.agg || c.J > kChainMaxChunks) return cudaErrorInvalidValue;
     c.stage = std::min(c.J, kBwdChainStage);
+    c.epoch = next_chain_epoch();
     const size_t smem = chain_stage_bytes<BackwardMode>(c.stage);
     if (blocks_per_sm((const void*)kernel, 32 * NW, smem) * sm_count() < 2 * c.J) return cudaErrorInvalidConfiguration;
     const bool skip = take_injected(DTS_INJECT_CHAIN_SKIP);
@@ -521,12 +525,37 @@ bool plan_rows_bwd(int W, RowPlan* p) {
 }
 
 // chain shapes of the vertical adjoint (rows per thread, warps per CTA), the default first
-constexpr int kBwdChainShapes[][2] = {{8, 16}, {8, 8}, {16, 8}};
+// (measured on 10000 x 1024: 16 x 16 170 us per pass, 8 x 32 200 us, 8 x 16 229 us; the shorter
+// chain of 256-row chunks waits less for the last chunk of its strip)
+constexpr int kBwdChainShapes[][2] = {{16, 16}, {8, 16}, {8, 8}, {16, 8}, {8, 32}};
 
-// Backward vertical plan: one cluster for columns up to 4096 rows (measured on the 2880 x 1988
-// stereo workload: 16 rows x 16 warps in clusters of 8 is fastest), a chain above.
+std::mutex g_tuned_bwd_mutex;
+std::map<int, ColPlan> g_tuned_bwd_cols;  // H -> vertical adjoint shape
+
+bool valid_bwd_shape(int H, const ColPlan& p) {
+    if (p.cluster == kColChain) {
+        for (const auto& c : kBwdChainShapes)
+            if (c[0] == p.items && c[1] == p.warps)
+                return (H + p.items * p.warps - 1) / (p.items * p.warps) <= kChainMaxChunks;
+        return false;
+    }
+    return (p.items == 8 || p.items == 16) && (p.warps == 8 || p.warps == 16) && p.cluster >= 1 &&
+           p.cluster <= 16 && (long long)p.items * p.warps * p.cluster >= H;
+}
+
+// Backward vertical plan: a tuned shape first (set_tuned_bwd_col); else one cluster for columns
+// up to 4096 rows (measured on the 2880 x 1988 stereo workload: 16 rows x 16 warps in clusters of
+// 8 is fastest), a chain above.
 bool plan_cols_bwd(int H, ColPlan* p) {
     if (H > kMaxColRows) return false;
+    {
+        std::lock_guard<std::mutex> lock(g_tuned_bwd_mutex);
+        auto it = g_tuned_bwd_cols.find(H);
+        if (it != g_tuned_bwd_cols.end()) {
+            *p = it->second;
+            return true;
+        }
+    }
     static const int cand[][2] = {{16, 16}, {8, 16}, {16, 8}, {8, 8}};
     if (H <= 128) {
         int nw = 1;
@@ -554,6 +583,26 @@ bool plan_cols_bwd(int H, ColPlan* p) {
     return (H + p->items * p->warps - 1) / (p->items * p->warps) <= kChainMaxChunks;
 }
 
+// records a vertical adjoint shape for columns of H rows (from dts_autotune_import); false when
+// it is not a valid shape for that height
+bool set_tuned_bwd_col(int H, const ColPlan& p) {
+    if (H < 1 || !valid_bwd_shape(H, p)) return false;
+    std::lock_guard<std::mutex> lock(g_tuned_bwd_mutex);
+    g_tuned_bwd_cols[H] = p;
+    return true;
+}
+
+std::string tuned_bwd_export() {
+    std::lock_guard<std::mutex> lock(g_tuned_bwd_mutex);
+    std::string out;
+    char line[96];
+    for (auto& kv : g_tuned_bwd_cols) {
+        snprintf(line, sizeof(line), "bcol %d %d %d %d\n", kv.first, kv.second.items, kv.second.warps, kv.second.cluster);
+        out += line;
+    }
+    return out;
+}
+
 cudaError_t launch_row_bwd(const BwdArgs& a, int dist_half, bool final_pass, const RowPlan& p, cudaStream_t s) {
     const int h = prof_begin(final_pass ? KID_ROW_BWD_FINAL : KID_ROW_BWD, (long long)a.H * a.W,
                              dist_half ? kFlagDistHalf : 0, s);
@@ -576,6 +625,10 @@ cudaError_t launch_col_bwd(const BwdArgs& a, int dist_half, const ColPlan& p, cu
             e = dist_half ? launch_col_bwd_chain_t<8, 8, true>(a, s) : launch_col_bwd_chain_t<8, 8, false>(a, s);
         if (p.items == 16 && p.warps == 8)
             e = dist_half ? launch_col_bwd_chain_t<16, 8, true>(a, s) : launch_col_bwd_chain_t<16, 8, false>(a, s);
+        if (p.items == 8 && p.warps == 32)
+            e = dist_half ? launch_col_bwd_chain_t<8, 32, true>(a, s) : launch_col_bwd_chain_t<8, 32, false>(a, s);
+        if (p.items == 16 && p.warps == 16)
+            e = dist_half ? launch_col_bwd_chain_t<16, 16, true>(a, s) : launch_col_bwd_chain_t<16, 16, false>(a, s);
     } else {
         if (p.items == 8) e = dist_half ? launch_col_bwd_t<8, true>(a, p, s) : launch_col_bwd_t<8, false>(a, p, s);
         if (p.items == 16) e = dist_half ? launch_col_bwd_t<16, true>(a, p, s) : launch_col_bwd_t<16, false>(a, p, s);
@@ -636,6 +689,10 @@ cudaError_t prepare_backward_kernels() {
     if ((r = allow_bwd_chain_smem<8, 8, true>()) != cudaSuccess) e = r;
     if ((r = allow_bwd_chain_smem<16, 8, false>()) != cudaSuccess) e = r;
     if ((r = allow_bwd_chain_smem<16, 8, true>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_chain_smem<8, 32, false>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_chain_smem<8, 32, true>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_chain_smem<16, 16, false>()) != cudaSuccess) e = r;
+    if ((r = allow_bwd_chain_smem<16, 16, true>()) != cudaSuccess) e = r;
     return e;
 }
 

@@ -33,136 +33,13 @@
 #include <mutex>
 #include <tuple>
 
-#include "dts_scan.cuh"
+#include "dts_modes.cuh"
 
 namespace dts {
 
 namespace {
 
 using namespace scan;
-
-// ---------------------------------------------------------------- modes
-// Normalised pass: causal sweep, then the anti-causal sweep on its result.
-struct CoupledMode {
-    using Pre = Aff;
-    using Suf = Coupled;
-    static __device__ __forceinline__ Pre pre_identity() { return aff_identity(); }
-    static __device__ __forceinline__ Pre pre_compose(const Pre& f, const Pre& s) { return aff_compose(f, s); }
-    static __device__ __forceinline__ Suf suf_identity() { return coupled_identity(); }
-    static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) { return coupled_compose(f, s); }
-    template <int N>
-    static __device__ __forceinline__ void local(const float (&x)[N], const float (&w)[N], float wn, Pre& pre,
-                                                 Suf& suf) {
-        suf = coupled_local<true>(x, w, wn);
-        pre = Aff{suf.A, suf.B};
-    }
-    // c: causal value entering on the left; after: composition of every segment to the right
-    template <int N>
-    static __device__ __forceinline__ void apply(float (&x)[N], const float (&w)[N], float wn, const Pre& own,
-                                                 float c, const Suf& after) {
-        float J = c;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            J = fmaf(w[j], J - x[j], x[j]);
-            x[j] = J;
-        }
-        float K = k_entering(after, fmaf(own.A, c, own.B));
-#pragma unroll
-        for (int j = N - 1; j >= 0; --j) {
-            const float wp = (j + 1 < N) ? w[j + 1] : wn;
-            K = fmaf(wp, K - x[j], x[j]);
-            x[j] = K;
-        }
-    }
-};
-
-// Transpose of a normalised pass.  The pass is (anti-causal) o (causal) with causal = L^-1 D,
-// D = diag(1 - w_n), L unit lower bidiagonal with -w_n below the diagonal, and anti-causal
-// = U^-1 D' with D' = diag(1 - w_{n+1}), U unit upper bidiagonal with -w_{n+1} above it.  Its
-// transpose D L^-T D' U^-T is: the unnormalised causal sweep h[n] = g[n] + w_n h[n-1], then the
-// normalised anti-causal sweep on h, then a factor (1 - w_n) per position.  The first two have
-// the coupled five-number form with an unnormalised left-to-right recurrence.
-struct TransposeMode {
-    using Pre = Aff;
-    using Suf = Coupled;
-    static __device__ __forceinline__ Pre pre_identity() { return aff_identity(); }
-    static __device__ __forceinline__ Pre pre_compose(const Pre& f, const Pre& s) { return aff_compose(f, s); }
-    static __device__ __forceinline__ Suf suf_identity() { return coupled_identity(); }
-    static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) { return coupled_compose(f, s); }
-    template <int N>
-    static __device__ __forceinline__ void local(const float (&x)[N], const float (&w)[N], float wn, Pre& pre,
-                                                 Suf& suf) {
-        suf = coupled_local<false>(x, w, wn);
-        pre = Aff{suf.A, suf.B};
-    }
-    template <int N>
-    static __device__ __forceinline__ void apply(float (&x)[N], const float (&w)[N], float wn, const Pre& own,
-                                                 float c, const Suf& after) {
-        float h = c;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            h = fmaf(w[j], h, x[j]);
-            x[j] = h;
-        }
-        float K = k_entering(after, fmaf(own.A, c, own.B));
-#pragma unroll
-        for (int j = N - 1; j >= 0; --j) {
-            const float wp = (j + 1 < N) ? w[j + 1] : wn;
-            K = fmaf(wp, K - x[j], x[j]);
-            x[j] = fmaf(-w[j], K, K);
-        }
-    }
-};
-
-// Support of the unnormalised kernel (confidence weighting): causal P[n] = x[n] + w_n P[n-1] and
-// anti-causal Q[n] = x[n] + w'_n Q[n+1], both on x; the result is P + Q - x.  The two sweeps are
-// independent: Suf carries (al, de) with Q_start = al Q_in + de.
-struct SupSuf {
-    float al, de;
-};
-struct SupportMode {
-    using Pre = Aff;
-    using Suf = SupSuf;
-    static __device__ __forceinline__ Pre pre_identity() { return aff_identity(); }
-    static __device__ __forceinline__ Pre pre_compose(const Pre& f, const Pre& s) { return aff_compose(f, s); }
-    static __device__ __forceinline__ Suf suf_identity() { return Suf{1.f, 0.f}; }
-    static __device__ __forceinline__ Suf suf_compose(const Suf& f, const Suf& s) {
-        return Suf{f.al * s.al, fmaf(f.al, s.de, f.de)};
-    }
-    template <int N>
-    static __device__ __forceinline__ void local(const float (&x)[N], const float (&w)[N], float wn, Pre& pre,
-                                                 Suf& suf) {
-        float A = 1.f, B = 0.f, r = 1.f, de = 0.f;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            A *= w[j];
-            B = fmaf(w[j], B, x[j]);
-            de = fmaf(r, x[j], de);
-            r *= (j + 1 < N) ? w[j + 1] : wn;
-        }
-        pre = Aff{A, B};
-        suf = Suf{r, de};
-    }
-    template <int N>
-    static __device__ __forceinline__ void apply(float (&x)[N], const float (&w)[N], float wn, const Pre& own,
-                                                 float c, const Suf& after) {
-        (void)own;
-        float Pv[N];
-        float Pc = c;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            Pc = fmaf(w[j], Pc, x[j]);
-            Pv[j] = Pc;
-        }
-        float Qc = after.de;
-#pragma unroll
-        for (int j = N - 1; j >= 0; --j) {
-            const float wp = (j + 1 < N) ? w[j + 1] : wn;
-            Qc = fmaf(wp, Qc, x[j]);
-            x[j] = Pv[j] + Qc - x[j];
-        }
-    }
-};
 
 // ---------------------------------------------------------------- distances
 // Thread = one column x and kDistRows consecutive rows; a warp covers 32 consecutive columns,
@@ -358,196 +235,24 @@ __global__ void __launch_bounds__(256) copy_plane_kernel(const void* src, int sr
 // KIND PASS_UPDATE_ROW: the first pass of an iteration also applies the previous iteration's
 // data-term update: it reads zbar (a.src), z_k (a.zk), t and c, writes z_{k+1} to a.zout and
 // filters z_{k+1}.
+// 32 positions per thread: the update pass in CTAs of up to 512 threads (rows up to 16384), the
+// other passes in CTAs of up to 320 threads (rows up to 10240), two of them per SM
 template <int ITEMS, int KIND>
 constexpr int row_max_threads() {
-    return KIND == PASS_UPDATE_ROW ? 512 : 1024;
-}
-
-// four consecutive target / confidence values at dense index i (16-byte vectors when allowed)
-__device__ __forceinline__ void load4_t(const PassArgs& a, long long i, bool vec, float* out) {
-    if (vec) {
-        if (a.t_dtype == DTS_F32) {
-            load4_f(static_cast<const float*>(a.t), i, out);
-        } else {
-            const uint2 v = *reinterpret_cast<const uint2*>(static_cast<const unsigned short*>(a.t) + i);
-            const unsigned short h[4] = {(unsigned short)(v.x & 0xffff), (unsigned short)(v.x >> 16),
-                                         (unsigned short)(v.y & 0xffff), (unsigned short)(v.y >> 16)};
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                out[k] = a.t_dtype == DTS_BF16 ? __bfloat162float(__ushort_as_bfloat16(h[k]))
-                                               : __half2float(__ushort_as_half(h[k]));
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) out[k] = load_any(a.t, i + k, a.t_dtype);
-    }
+    return KIND == PASS_UPDATE_ROW ? 512 : ITEMS >= 32 ? 320 : 1024;
 }
 
 // the update pass at up to 16 positions per thread is capped at 64 registers (two CTAs of 512
 // threads per SM at most); 32 positions would spill
 template <int ITEMS, int KIND>
 constexpr int row_min_blocks() {
-    return (KIND == PASS_UPDATE_ROW && ITEMS <= 16) ? 2 : 1;
+    return (KIND == PASS_UPDATE_ROW && ITEMS <= 16) || (KIND != PASS_UPDATE_ROW && ITEMS >= 32) ? 2 : 1;
 }
 
-// TWO: the normalised pass as two one-direction exchanges of affine maps (causal, then
-// anti-causal on its result) instead of one exchange of the coupled five numbers.
 template <int ITEMS, bool DHALF, int KIND, bool TWO = false>
 __global__ void __launch_bounds__(row_max_threads<ITEMS, KIND>(), row_min_blocks<ITEMS, KIND>()) row_pass_kernel(PassArgs a, int tpr) {
-    static_assert(ITEMS % 4 == 0, "ITEMS must be a multiple of 4");
-    using M = typename std::conditional<KIND == PASS_SUPPORT, SupportMode,
-                                        typename std::conditional<KIND == PASS_TRANSPOSE, TransposeMode,
-                                                                  CoupledMode>::type>::type;
-    __shared__ typename M::Pre s_pre[32];
-    __shared__ typename M::Suf s_suf[32];
-    __shared__ Aff s_two[TWO ? 32 : 1];
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int warp = tid >> 5;
-    const int rloc = tid / tpr;
-    const int t = tid - rloc * tpr;
-    const int wpr = tpr >> 5;       // warps per row
-    const int wrow = t >> 5;        // warp index within the row
-    const int wbase = warp - wrow;  // first warp of this row
-    const int rpb = blockDim.x / tpr;
-    const int row = blockIdx.x * rpb + rloc;
-    const bool row_ok = row < a.H;
-    const int e0 = t * ITEMS;
-    const long long P = a.pitch;
-    const long long base = (long long)row * P + e0;
-    const bool live = row_ok && e0 < P;
-
     wait_predecessor();
-    if constexpr (KIND == PASS_UPDATE_ROW) {
-        // the update operands are read group by group between stores of z_{k+1}: start bringing
-        // this thread's lines into L2 now
-        if (row_ok && e0 < a.W) {  // addresses inside the dense planes only
-            const long long di = (long long)row * a.W + e0;
-            prefetch_l2(a.zk + base);
-            prefetch_l2(static_cast<const char*>(a.t) + di * (a.t_dtype == DTS_F32 ? 4 : 2));
-            prefetch_l2(a.c + (a.c_pitched ? base : di));
-        }
-    }
-    float x[ITEMS], w[ITEMS];
-    if (live) {
-#pragma unroll
-        for (int q = 0; q < ITEMS / 4; ++q) {
-            if constexpr (KIND == PASS_SUPPORT) {
-                x[4 * q] = x[4 * q + 1] = x[4 * q + 2] = x[4 * q + 3] = 1.f;
-            } else {
-                load4_f(a.src, base + 4 * q, &x[4 * q]);
-            }
-            load4_d<DHALF>(a.d, base + 4 * q, &w[4 * q]);
-        }
-        if constexpr (KIND == PASS_UPDATE_ROW) {
-            // z_{k+1} from z_k, zbar (already in x), t and c; padding positions stay 0.  Every
-            // operand is loaded before the first store of z_{k+1} (the stores could alias later
-            // loads, which would otherwise wait for them); the update is computed in place in x.
-            const long long di = (long long)row * a.W + e0;
-            const bool full_seg = e0 + ITEMS <= a.W;
-            // operands in groups of HALF positions (a group's loads, its update, its stores): 8 at
-            // 16 positions per thread (measured: 37.0 us vs 37.5 with 4 and 40.7 with all 16 at
-            // once, which costs resident rows), 16 at 32 (rows over 8192)
-            constexpr int HALF = ITEMS <= 16 ? 8 : ITEMS / 2;
-#pragma unroll
-            for (int h0 = 0; h0 < ITEMS; h0 += HALF) {
-            float zk[HALF], tt[HALF], cc[HALF];
-#pragma unroll
-            for (int q = h0 / 4; q < (h0 + HALF) / 4; ++q) {
-                const int l = 4 * q - h0;
-                load4_f(a.zk, base + 4 * q, &zk[l]);
-                if (full_seg) {
-                    load4_t(a, di + 4 * q, a.tc_vec, &tt[l]);
-                    if (a.c_pitched) load4_f(a.c, base + 4 * q, &cc[l]);
-                    else if (a.tc_vec) load4_f(a.c, di + 4 * q, &cc[l]);
-                    else {
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) cc[l + k] = a.c[di + 4 * q + k];
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const bool ok = e0 + 4 * q + k < a.W;
-                        tt[l + k] = ok ? load_any(a.t, di + 4 * q + k, a.t_dtype) : 0.f;
-                        cc[l + k] = ok ? (a.c_pitched ? a.c[base + 4 * q + k] : a.c[di + 4 * q + k]) : 0.f;
-                    }
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < HALF; ++j) {
-                const float zn = dts_update_value(zk[j], x[h0 + j], tt[j], cc[j], a.lambda, a.step, a.update,
-                                                  a.clamp_step, a.eps);
-                x[h0 + j] = (e0 + h0 + j < a.W) ? zn : 0.f;
-            }
-#pragma unroll
-            for (int q = h0 / 4; q < (h0 + HALF) / 4; ++q) store4_f(a.zout, base + 4 * q, &x[4 * q]);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) w[j] = ex2(a.k2 * w[j]);
-        if (e0 + ITEMS > a.W) {  // the segment holding the row end: clear the padding
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j)
-                if (e0 + j >= a.W) x[j] = w[j] = 0.f;
-        }
-        if (e0 == 0) w[0] = 0.f;  // the row starts here
-    } else {
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) x[j] = w[j] = 0.f;
-    }
-    // weight between this segment's last position and the next segment's first
-    float wn = __shfl_down_sync(kFull, w[0], 1);
-    if (lane == 31) {
-        const int en = e0 + ITEMS;
-        wn = (row_ok && en < a.W) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)row * P + en)) : 0.f;
-    }
-
-    if constexpr (TWO && KIND != PASS_SUPPORT) {
-        // causal sweep: segment map c -> A c + B, exclusive prefix, replay
-        float A = 1.f, B = 0.f;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            A *= w[j];
-            B = fmaf(w[j], B - x[j], x[j]);
-        }
-        const Aff pc = row_scan_aff<true>(Aff{A, B}, lane, warp, wrow, wbase, wpr, s_pre);
-        float v = pc.B;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            v = fmaf(w[j], v - x[j], x[j]);
-            x[j] = v;
-        }
-        // anti-causal sweep on the result, weights w' (the next position's)
-        A = 1.f;
-        B = 0.f;
-#pragma unroll
-        for (int j = ITEMS - 1; j >= 0; --j) {
-            const float wp = (j + 1 < ITEMS) ? w[j + 1] : wn;
-            A *= wp;
-            B = fmaf(wp, B - x[j], x[j]);
-        }
-        const Aff sk = row_scan_aff<false>(Aff{A, B}, lane, warp, wrow, wbase, wpr, s_two);
-        release_successor();
-        v = sk.B;
-#pragma unroll
-        for (int j = ITEMS - 1; j >= 0; --j) {
-            const float wp = (j + 1 < ITEMS) ? w[j + 1] : wn;
-            v = fmaf(wp, v - x[j], x[j]);
-            x[j] = v;
-        }
-    } else {
-        typename M::Pre own_pre, pre;
-        typename M::Suf own_suf, suf;
-        M::local(x, w, wn, own_pre, own_suf);
-        row_exchange<M>(own_pre, own_suf, lane, warp, wrow, wbase, wpr, s_pre, s_suf, pre, suf);
-        release_successor();
-        M::apply(x, w, wn, own_pre, pre.B, suf);
-    }
-
-    if (live) {
-#pragma unroll
-        for (int q = 0; q < ITEMS / 4; ++q) store4_f(a.dst, base + 4 * q, &x[4 * q]);
-    }
+    row_pass_body<ITEMS, DHALF, KIND, TWO, false>(a, tpr, blockDim.x / tpr, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- vertical pass
@@ -718,144 +423,127 @@ __global__ void __launch_bounds__(32 * NW, chain_min_blocks<ITEMS, NW>()) col_ch
     col_store<ITEMS, KIND>(a, row0, col, x);
 }
 
-// ---------------------------------------------------------------- strip vertical pass (no cluster)
-// CTA = NW <= 32 warps over a strip of 8 columns and the whole column height.  Lane l of warp q
-// takes column l % 8 and segment 4q + l / 8 (ITEMS rows each): 4 NW segments per column.
-// Exchange: the 4 segments of a column inside a warp scan with shuffles at stride 8; the NW warp
-// totals of a column scan in one warp (lane = warp); two __syncthreads, no cluster barrier.
-constexpr int kStripCols = 8;
-constexpr int kStripWarps = 32;
+// ---------------------------------------------------------------- tall columns: persistent clusters fed by TMA
+// Columns over the strip kernel's height.  One cluster of CS CTAs holds a 32-column strip, CTA r
+// the rows [r R, r R + R), R = kTallWarps x ITEMS (lane = column, warp q rows [q ITEMS, + ITEMS)
+// of the CTA's tile); the grid is persistent (as many clusters as fit at once, each looping over
+// strips s, s + gridDim.x, ...).  A CTA's tile of the pass input and of the distances arrives by
+// 2-D TMA (boxes of 32 columns x kTallBox rows) into one shared-memory stage; as soon as the CTA
+// holds the tile in registers it starts the next strip's loads into the stage, so they stream in
+// while the strip is exchanged (shared memory in the CTA, distributed shared memory across the
+// cluster), replayed and stored (128-byte rows straight from registers).  Waits on the stage's
+// barrier are bounded: one that gives up records DTS_ERR_TIMEOUT, after which the CTA issues no
+// more loads and waits no more (its results are invalid, the status says so; every cluster
+// barrier is still passed), and before it exits it waits, bounded, for the load it gave up on.
+// skip (fault injection): CTA 0 of cluster 0 leaves out its first tile load.
+constexpr int kTallBox = 128;
+constexpr int kTallWarps = 16;
 
-template <class M>
-struct StripShared {
-    typename M::Pre pre[kStripWarps][kStripCols + 1];
-    typename M::Suf suf[kStripWarps][kStripCols + 1];
-};
-
-// pre / suf: the transforms of everything above / below this thread's segment in its column.
-// Shared-memory writes made before the call are visible to every thread after it.
-template <class M>
-__device__ __forceinline__ void strip_exchange(const typename M::Pre& own_pre, const typename M::Suf& own_suf,
-                                               int lane, int warp, int NW, int cl, int sw, StripShared<M>& sh,
-                                               typename M::Pre& pre, typename M::Suf& suf) {
-    using Pre = typename M::Pre;
-    using Suf = typename M::Suf;
-    constexpr int SEGS = 32 / kStripCols;
-    // inside the warp: the column's segments are lanes cl, cl + 8, cl + 16, cl + 24
-    Pre ip = own_pre;
-    Suf is = own_suf;
-#pragma unroll
-    for (int off = 1; off < SEGS; off <<= 1) {
-        const Pre op = shfl_up_t(ip, off * kStripCols);
-        const Suf os = shfl_down_t(is, off * kStripCols);
-        if (sw >= off) ip = M::pre_compose(op, ip);
-        if (sw + off < SEGS) is = M::suf_compose(is, os);
-    }
-    Pre xp = shfl_up_t(ip, kStripCols);
-    Suf xs = shfl_down_t(is, kStripCols);
-    if (sw == 0) xp = M::pre_identity();
-    if (sw == SEGS - 1) xs = M::suf_identity();
-    if (sw == SEGS - 1) sh.pre[warp][cl] = ip;  // warp total, prefix direction
-    if (sw == 0) sh.suf[warp][cl] = is;         // warp total, suffix direction
-    __syncthreads();
-    // across the warps: warp c < 8 (or every warp of a smaller CTA, in turn) scans column c over
-    // the NW warp totals (lane = warp)
-    for (int c = warp; c < kStripCols; c += NW) {
-        const bool in = lane < NW;
-        const Pre p = in ? sh.pre[lane][c] : M::pre_identity();
-        const Suf f = in ? sh.suf[lane][c] : M::suf_identity();
-        const Pre ip2 = warp_scan_pre<M>(p, lane);
-        const Suf is2 = warp_scan_suf<M>(f, lane);
-        Pre pe = shfl_up_t(ip2, 1);
-        Suf fe = shfl_down_t(is2, 1);
-        if (lane == 0) pe = M::pre_identity();
-        if (lane == 31) fe = M::suf_identity();
-        if (in) {
-            sh.pre[lane][c] = pe;
-            sh.suf[lane][c] = fe;
-        }
-    }
-    __syncthreads();
-    pre = M::pre_compose(sh.pre[warp][cl], xp);
-    suf = M::suf_compose(xs, sh.suf[warp][cl]);
+template <int ITEMS, bool DHALF>
+__host__ __device__ constexpr size_t tall_stage_bytes() {
+    return (size_t)kTallWarps * ITEMS * 32 * (4 + (DHALF ? 2 : 4));
+}
+template <int ITEMS>
+constexpr int tall_min_blocks() {
+    return ITEMS <= 16 ? 2 : 1;
 }
 
-// Strip kernel with plain loads: each warp load covers four 32-byte row pieces.
-template <int ITEMS, bool DHALF>
-__global__ void __launch_bounds__(32 * kStripWarps) col_strip_kernel(PassArgs a) {
-    using M = CoupledMode;
+template <int ITEMS, bool DHALF, int KIND>
+__global__ void __launch_bounds__(32 * kTallWarps, tall_min_blocks<ITEMS>())
+    col_tall_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_d, PassArgs a,
+                    int nstrips, long long timeout, int skip) {
+    using M = ColMode<KIND>;
     using DT = typename std::conditional<DHALF, __half, float>::type;
-    __shared__ StripShared<M> sh;
+    constexpr int R = kTallWarps * ITEMS;
+    constexpr int kBoxes = R / kTallBox;
+    static_assert(R % kTallBox == 0, "whole boxes per tile");
+    constexpr uint32_t kTx = (uint32_t)tall_stage_bytes<ITEMS, DHALF>();
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ ColShared<M, kTallWarps> sh;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_failed;  // 0, or 1 + the parity of the phase a wait gave up on
+    cg::cluster_group cluster = cg::this_cluster();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int NW = blockDim.x >> 5;
-    const int cl = lane & (kStripCols - 1);  // column within the strip
-    const int sw = lane / kStripCols;        // segment within the warp (0..3)
-    const int col = blockIdx.x * kStripCols + cl;
-    const bool col_ok = col < a.W;
-    const int row0 = (warp * (32 / kStripCols) + sw) * ITEMS;
+    const int rank = (int)cluster.block_rank();
+    const int CS = (int)cluster.num_blocks();
+    const int tile_row = rank * R;
+    const int row0 = tile_row + warp * ITEMS;
     const long long P = a.pitch;
+    float* sx = reinterpret_cast<float*>(dsm);
+    const DT* sd = reinterpret_cast<const DT*>(dsm + (size_t)R * 32 * 4);
 
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        s_failed = 0;
+    }
+    __syncthreads();
     wait_predecessor();
-    float x[ITEMS], w[ITEMS];
-    const bool full = col_ok && row0 + ITEMS <= a.H;
-    {
-        const float* ps = a.src + (long long)row0 * P + col;
-        const DT* pd = static_cast<const DT*>(a.d) + (long long)row0 * P + col;
-        if (full) {
+    auto issue = [&](int strip) {
+        mbar_arrive_expect_tx(&bar, kTx);
 #pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                x[j] = *ps;
-                w[j] = to_f32<DT>(*pd);
-                ps += P;
-                pd += P;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                const bool ok = col_ok && row0 + j < a.H;
-                x[j] = ok ? *ps : 0.f;
-                w[j] = ok ? to_f32<DT>(*pd) : 0.f;
-                ps += P;
-                pd += P;
-            }
+        for (int b = 0; b < kBoxes; ++b) {
+            tma_load_2d(sx + (size_t)b * kTallBox * 32, &tm_x, strip * 32, tile_row + b * kTallBox, &bar);
+            tma_load_2d((void*)(sd + (size_t)b * kTallBox * 32), &tm_d, strip * 32, tile_row + b * kTallBox, &bar);
         }
-    }
-    float wn;
-    {
+    };
+    if (threadIdx.x == 0 && (int)blockIdx.x < nstrips && !(skip && blockIdx.x == 0 && rank == 0)) issue(blockIdx.x);
+    int it = 0;
+    for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x, ++it) {
+        const int next = strip + gridDim.x;
+        const int col = strip * 32 + lane;
+        const bool col_ok = col < a.W;
+        if (!s_failed && !mbar_wait_bounded(&bar, (uint32_t)(it & 1), timeout)) {
+            record_status(a.status, DTS_ERR_TIMEOUT);
+            s_failed = 1 + (it & 1);
+        }
+        float x[ITEMS], w[ITEMS];
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            x[j] = sx[(warp * ITEMS + j) * 32 + lane];
+            w[j] = to_f32<DT>(sd[(warp * ITEMS + j) * 32 + lane]);
+        }
+        float dnext = warp + 1 < kTallWarps ? to_f32<DT>(sd[((warp + 1) * ITEMS) * 32 + lane]) : 0.f;
+        // the reads above come before the next strip's TMA writes into the stage
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0 && next < nstrips && !s_failed) issue(next);
         const int rn = row0 + ITEMS;
-        wn = (col_ok && rn < a.H) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)rn * P + col)) : 0.f;
-    }
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) w[j] = ex2(a.k2 * w[j]);
-    if (!full) {
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j)
-            if (!(col_ok && row0 + j < a.H)) w[j] = 0.f;
-    }
-    if (row0 == 0) w[0] = 0.f;
-
-    typename M::Pre own_pre, pre;
-    typename M::Suf own_suf, suf;
-    M::local(x, w, wn, own_pre, own_suf);
-    strip_exchange<M>(own_pre, own_suf, lane, warp, NW, cl, sw, sh, pre, suf);
-    release_successor();
-    M::apply(x, w, wn, own_pre, pre.B, suf);
-
-    float* pdst = a.dst + (long long)row0 * a.dst_pitch + col;
-    if (full) {
+        if (warp + 1 == kTallWarps && col_ok && rn < a.H) dnext = load1_d<DHALF>(a.d, (long long)rn * P + col);
+        const float wn = (col_ok && rn < a.H) ? ex2(a.k2 * dnext) : 0.f;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
-            *pdst = x[j];
-            pdst += a.dst_pitch;
+            const int r = row0 + j;
+            const bool ok = col_ok && r < a.H;
+            w[j] = (ok && r > 0) ? ex2(a.k2 * w[j]) : 0.f;
+            if (!ok) x[j] = 0.f;
         }
-    } else {
+        if constexpr (KIND == PASS_TRANSPOSE) {
+            if (a.zk && col_ok) {  // the pass filters zk - src
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if (col_ok && row0 + j < a.H) *pdst = x[j];
-            pdst += a.dst_pitch;
+                for (int j = 0; j < ITEMS; ++j)
+                    if (row0 + j < a.H) x[j] = a.zk[(long long)(row0 + j) * P + col] - x[j];
+            }
         }
+        typename M::Pre own_pre, pre;
+        typename M::Suf own_suf, suf;
+        M::local(x, w, wn, own_pre, own_suf);
+        col_exchange_iter<M, kTallWarps>(own_pre, own_suf, lane, warp, kTallWarps, sh, it == 0, pre, suf);
+        if (next >= nstrips) release_successor();
+        M::apply(x, w, wn, own_pre, pre.B, suf);
+        col_store<ITEMS, KIND>(a, row0, col, x);
     }
+    if (CS > 1 && it > 0) cluster_exit();
+    // the load a wait gave up on lands before the CTA's shared memory goes to another CTA
+    if (threadIdx.x == 0 && s_failed) mbar_wait_bounded(&bar, (uint32_t)(s_failed - 1), timeout);
+}
+
+// Strip kernel with plain loads (planes that tensor maps cannot describe): one CTA per strip.
+template <int ITEMS, bool DHALF>
+__global__ void __launch_bounds__(32 * kStripWarps) col_strip_kernel(PassArgs a) {
+    wait_predecessor();
+    strip_pass_body<ITEMS, DHALF, false>(a, blockIdx.x);
 }
 
 // Strip kernel fed by TMA, persistent over strips.  Warp q owns the slab of rows
@@ -1264,36 +952,39 @@ cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const Ro
     cudaError_t e = cudaErrorInvalidValue;
     if (p.items == 8) e = dist_half ? launch_row_k<8, true>(a, kind, p, s) : launch_row_k<8, false>(a, kind, p, s);
     if (p.items == 16) e = dist_half ? launch_row_k<16, true>(a, kind, p, s) : launch_row_k<16, false>(a, kind, p, s);
-    if (p.items == 32 && kind == PASS_UPDATE_ROW) {  // long rows (plan_rows_update)
-        const dim3 grid((unsigned)((a.H + p.rpb - 1) / p.rpb));
-        const dim3 block((unsigned)(p.tpr * p.rpb));
-        e = dist_half ? launch_ex(row_pass_kernel<32, true, PASS_UPDATE_ROW>, grid, block, 0, s, a, p.tpr)
-                      : launch_ex(row_pass_kernel<32, false, PASS_UPDATE_ROW>, grid, block, 0, s, a, p.tpr);
-    }
+    if (p.items == 32 && p.tpr * p.rpb <= (kind == PASS_UPDATE_ROW ? 512 : 320))
+        e = dist_half ? launch_row_k<32, true>(a, kind, p, s) : launch_row_k<32, false>(a, kind, p, s);
     prof_end(h, s);
     return e;
 }
 
 cudaError_t launch_col_strip(const PassArgs& a, int dist_half, const ColPlan& p, bool tr, cudaStream_t s);
 cudaError_t launch_col_chain(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s);
+cudaError_t launch_col_tall(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s);
+
+// the vertical kernel a plan names: the strip kernel (cluster 0), the cluster kernel (cluster > 0
+// CTAs), the chain (-1) or the persistent TMA clusters for tall columns (-2)
+cudaError_t launch_col_planned(const PassArgs& a, int dist_half, int kind, const ColPlan& q, cudaStream_t s) {
+    if (q.cluster == kColStrip) return launch_col_strip(a, dist_half, q, kind == PASS_TRANSPOSE, s);
+    if (q.cluster == kColChain) return launch_col_chain(a, dist_half, kind, q, s);
+    if (q.cluster == kColTall) return launch_col_tall(a, dist_half, kind, q, s);
+    return launch_col_dispatch(a, dist_half, kind, q, s);
+}
 
 cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
     const bool tr = kind == PASS_TRANSPOSE;
-    // the strip kernel runs plain and transposed passes; the other kinds take the chain (or the
-    // cluster) shape of the same height
+    // the strip kernel runs plain and transposed passes; the other kinds take the plan of the
+    // same height that the other kernels give
     ColPlan q = p;
-    if (q.cluster == 0 && kind != PASS_PLAIN && !tr && !plan_cols_multi(a.H, &q)) return cudaErrorInvalidValue;
-    const bool strip = q.cluster == 0;
-    const bool chain = q.cluster < 0;
-    const int kid = strip ? (tr ? KID_COL_STRIP_TRANSPOSE : KID_COL_STRIP)
+    if (q.cluster == kColStrip && kind != PASS_PLAIN && !tr && !plan_cols_multi(a.H, &q)) return cudaErrorInvalidValue;
+    const int kid = q.cluster == kColStrip ? (tr ? KID_COL_STRIP_TRANSPOSE : KID_COL_STRIP)
                   : kind == PASS_SUPPORT_CONF ? KID_COL_SUPPORT
-                  : tr ? (chain ? KID_COL_CHAIN_TRANSPOSE : KID_COL_TRANSPOSE)
-                  : chain ? KID_COL_CHAIN : KID_COL_PLAIN;
+                  : q.cluster == kColChain ? (tr ? KID_COL_CHAIN_TRANSPOSE : KID_COL_CHAIN)
+                  : q.cluster == kColTall ? (tr ? KID_COL_TALL_TRANSPOSE : KID_COL_TALL)
+                  : tr ? KID_COL_TRANSPOSE : KID_COL_PLAIN;
     const int flags = dist_half ? kFlagDistHalf : 0;
     const int h = prof_begin(kid, (long long)a.H * a.W, flags, s);
-    const cudaError_t e = strip ? launch_col_strip(a, dist_half, q, tr, s)
-                        : chain ? launch_col_chain(a, dist_half, kind, q, s)
-                                : launch_col_dispatch(a, dist_half, kind, q, s);
+    const cudaError_t e = launch_col_planned(a, dist_half, kind, q, s);
     prof_end(h, s);
     return e;
 }
@@ -1342,9 +1033,11 @@ cudaError_t launch_col_strip_t(const PassArgs& a, int nw, bool tr, cudaStream_t 
     // the cluster kernel for the transposed pass
     if (tr) {
         ColPlan q;
-        if (!plan_cols_multi(a.H, &q)) return cudaErrorInvalidValue;
-        return q.cluster < 0 ? launch_col_chain(a, DHALF, PASS_TRANSPOSE, q, s)
-                             : launch_col_dispatch(a, DHALF, PASS_TRANSPOSE, q, s);
+        if (!plan_cols_multi(a.H, &q) || q.cluster == kColTall) {
+            // the tall kernel loads through tensor maps too: the cluster kernel, or the chain
+            if (!plan_cols_cluster(a.H, &q) && !chain_plan(a.H, &q)) return cudaErrorInvalidValue;
+        }
+        return launch_col_planned(a, DHALF, PASS_TRANSPOSE, q, s);
     }
     return launch_ex(col_strip_kernel<ITEMS, DHALF>, grid, block, 0, s, a);
 }
@@ -1403,6 +1096,7 @@ cudaError_t launch_chain_t(const PassArgs& a, cudaStream_t s) {
     c.status = a.status;
     if (!c.ctl || !c.agg || c.J > kChainMaxChunks) return cudaErrorInvalidValue;
     c.stage = std::min(c.J, chain_stage_cap<ITEMS, NW>());
+    c.epoch = next_chain_epoch();
     const size_t smem = chain_stage_bytes<ColMode<KIND>>(c.stage);
     if (blocks_per_sm((const void*)kernel, 32 * NW, smem) * sm_count() < 2 * c.J) return cudaErrorInvalidConfiguration;
     const bool skip = KIND != PASS_SUPPORT_CONF && take_injected(DTS_INJECT_CHAIN_SKIP);
@@ -1429,6 +1123,63 @@ cudaError_t launch_col_chain(const PassArgs& a, int dist_half, int kind, const C
     if (p.items == 32 && p.warps == 8)
         return dist_half ? launch_chain_k<32, 8, true>(a, kind, s) : launch_chain_k<32, 8, false>(a, kind, s);
     return cudaErrorInvalidValue;
+}
+
+// persistent TMA clusters for tall columns: ceil(H / R) CTAs per cluster (at most 16), as many
+// clusters as fit at once
+template <int ITEMS, bool DHALF, int KIND>
+cudaError_t launch_tall_t(const PassArgs& a, cudaStream_t s) {
+    auto kernel = col_tall_kernel<ITEMS, DHALF, KIND>;
+    constexpr int R = kTallWarps * ITEMS;
+    const int cs = (a.H + R - 1) / R;
+    if (cs > 16) return cudaErrorInvalidValue;
+    const size_t smem = tall_stage_bytes<ITEMS, DHALF>();
+    CUtensorMap tx, td;
+    if (!make_box_map(&tx, a.src, false, a.W, a.H, a.pitch, 32, kTallBox) ||
+        !make_box_map(&td, a.d, DHALF, a.W, a.H, a.pitch, 32, kTallBox))
+        return cudaErrorInvalidValue;
+    const int nstrips = (a.W + 31) / 32;
+    const int mc = max_clusters((const void*)kernel, 32 * kTallWarps, cs, smem);
+    if (mc < 1) return cudaErrorInvalidConfiguration;
+    const int gx = balanced_grid(nstrips, mc);
+    // fault injection (tests): on a single-round grid, CTA 0 of cluster 0 leaves out its first load
+    const bool skip = gx == nstrips && take_injected(DTS_INJECT_TMA_SKIP);
+    return launch_ex_smem(kernel, dim3((unsigned)gx, (unsigned)cs, 1), dim3(32 * kTallWarps), cs, smem, s, tx, td, a,
+                          nstrips, skip ? kInjectedTimeout : default_timeout_cycles(), skip ? 1 : 0);
+}
+
+template <int ITEMS, bool DHALF>
+cudaError_t launch_tall_k(const PassArgs& a, int kind, cudaStream_t s) {
+    switch (kind) {
+        case PASS_PLAIN: return launch_tall_t<ITEMS, DHALF, PASS_PLAIN>(a, s);
+        case PASS_SUPPORT_CONF: return launch_tall_t<ITEMS, DHALF, PASS_SUPPORT_CONF>(a, s);
+        case PASS_TRANSPOSE: return launch_tall_t<ITEMS, DHALF, PASS_TRANSPOSE>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_col_tall(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
+    if (p.items == 16) return dist_half ? launch_tall_k<16, true>(a, kind, s) : launch_tall_k<16, false>(a, kind, s);
+    if (p.items == 32) return dist_half ? launch_tall_k<32, true>(a, kind, s) : launch_tall_k<32, false>(a, kind, s);
+    if (p.items == 40) return dist_half ? launch_tall_k<40, true>(a, kind, s) : launch_tall_k<40, false>(a, kind, s);
+    return cudaErrorInvalidValue;
+}
+
+template <int ITEMS, bool DHALF, int KIND>
+cudaError_t allow_tall_t() {
+    const void* f = (const void*)col_tall_kernel<ITEMS, DHALF, KIND>;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tall_stage_bytes<ITEMS, DHALF>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+template <int ITEMS, bool DHALF>
+cudaError_t allow_tall() {
+    cudaError_t e = cudaSuccess, r;
+    if ((r = allow_tall_t<ITEMS, DHALF, PASS_PLAIN>()) != cudaSuccess) e = r;
+    if ((r = allow_tall_t<ITEMS, DHALF, PASS_SUPPORT_CONF>()) != cudaSuccess) e = r;
+    if ((r = allow_tall_t<ITEMS, DHALF, PASS_TRANSPOSE>()) != cudaSuccess) e = r;
+    return e;
 }
 
 // ---------------------------------------------------------------- tuned shapes
@@ -1489,17 +1240,42 @@ bool chain_shape_fits(int H, int items, int warps) {
     return H <= kMaxColRows && J <= kChainMaxChunks;
 }
 
-// vertical shapes the tuner tries: the strip kernel (columns up to kStripMaxRows rows), the
-// chain shapes, then rows per thread x warps per CTA in clusters of at most 16
+// the default chain plan for columns of H rows
+bool chain_plan(int H, ColPlan* p) {
+    p->items = kChainShapes[0][0];
+    p->warps = kChainShapes[0][1];
+    p->cluster = kColChain;
+    return chain_shape_fits(H, p->items, p->warps);
+}
+
+// rows per thread of the tall kernel: the fewest whose clusters of at most 16 CTAs of 16 warps
+// hold the column (columns up to 10240 rows)
+bool tall_plan(int H, ColPlan* p) {
+    for (int items : {16, 32, 40}) {
+        if ((H + kTallWarps * items - 1) / (kTallWarps * items) <= 16) {
+            p->items = items;
+            p->warps = kTallWarps;
+            p->cluster = kColTall;
+            return true;
+        }
+    }
+    return false;
+}
+
+// vertical shapes the tuner tries: the strip kernel (columns up to kStripMaxRows rows), the tall
+// kernel's shapes, the chain shapes, then rows per thread x warps per CTA in clusters of at most 16
 int col_candidates(int H, ColPlan* out, int max_out) {
     static const int cand[][2] = {{8, 8}, {8, 16}, {8, 32}, {16, 8}, {16, 16}, {32, 8}, {32, 16}, {40, 16}};
     int n = 0;
     if (H <= kStripMaxRows && n < max_out) {
         strip_shape(H, &out[n].items, &out[n].warps);
-        out[n++].cluster = 0;
+        out[n++].cluster = kColStrip;
     }
+    for (int items : {16, 32, 40})
+        if (H > 1 && (H + kTallWarps * items - 1) / (kTallWarps * items) <= 16 && n < max_out)
+            out[n++] = ColPlan{items, kTallWarps, kColTall};
     for (const auto& c : kChainShapes)
-        if (H > 1 && chain_shape_fits(H, c[0], c[1]) && n < max_out) out[n++] = ColPlan{c[0], c[1], -1};
+        if (H > 1 && chain_shape_fits(H, c[0], c[1]) && n < max_out) out[n++] = ColPlan{c[0], c[1], kColChain};
     for (const auto& c : cand) {
         const int rows = c[0] * c[1];
         const int cs = (H + rows - 1) / rows;
@@ -1509,13 +1285,18 @@ int col_candidates(int H, ColPlan* out, int max_out) {
     return n;
 }
 
+// Horizontal plan: ITEMS positions per thread, one row per tpr threads (a multiple of 32): 8 up
+// to 256 columns, 16 up to 8192 and above 10240, 32 in between (CTAs of at most 320 threads, two
+// per SM, where 16 positions in CTAs of over 512 threads leave one CTA per SM), or a tuned count.
 bool plan_rows(int W, RowPlan* p) {
     int items;
     if (W <= 256) items = 8;
-    else if (W <= 16 * 1024) items = 16;
-    else return false;
+    else if (W <= 8192 || W > 10240) items = 16;
+    else items = 32;
+    if (W > 16 * 1024) return false;
     const int tuned = tuned_row(W);
-    if ((tuned == 8 || tuned == 16) && (W + tuned - 1) / tuned <= 1024) items = tuned;
+    if ((tuned == 8 || tuned == 16 || tuned == 32) && ((W + tuned - 1) / tuned + 31) / 32 * 32 <= (tuned >= 32 ? 320 : 1024))
+        items = tuned;
     int tpr = (W + items - 1) / items;
     tpr = (tpr + 31) / 32 * 32;
     int rpb = 256 / tpr;
@@ -1527,30 +1308,28 @@ bool plan_rows(int W, RowPlan* p) {
 }
 
 // Vertical plan: a tuned shape first; else the strip kernel for columns up to kStripMaxRows rows
-// (measured faster than clusters on the stereo, depth and 256 x 256 workloads), else the chain.
+// (measured faster than clusters on the stereo, depth and 256 x 256 workloads), else the plan of
+// the other kernels.
 bool plan_cols(int H, ColPlan* p) {
     if (H > kMaxColRows) return false;
     if (tuned_col(H, p)) return true;
     if (H <= kStripMaxRows) {
         strip_shape(H, &p->items, &p->warps);
-        p->cluster = 0;
+        p->cluster = kColStrip;
         return true;
     }
     return plan_cols_multi(H, p);
 }
 
-// Plan for the pass kinds the strip kernel does not run: a tuned chain or cluster shape, else
-// the chain for columns taller than one CTA of the cluster kernel's single-CTA shape, else that.
+// Plan for the pass kinds the strip kernel does not run (and columns taller than it): a tuned
+// shape of another kernel first; else the cluster kernel up to 256 rows (one CTA), the
+// persistent TMA clusters up to 10240 rows, the chain above.
 bool plan_cols_multi(int H, ColPlan* p) {
     if (H > kMaxColRows) return false;
-    if (tuned_col(H, p) && p->cluster != 0) return true;
-    if (H > 256) {
-        p->items = kChainShapes[0][0];
-        p->warps = kChainShapes[0][1];
-        p->cluster = -1;
-        return chain_shape_fits(H, p->items, p->warps);
-    }
-    return plan_cols_cluster(H, p);
+    if (tuned_col(H, p) && p->cluster != kColStrip) return true;
+    if (H <= 256) return plan_cols_cluster(H, p);
+    if (tall_plan(H, p)) return true;
+    return chain_plan(H, p);
 }
 
 // Cluster plan (solves that run side by side, whose CTAs must not wait on one another across
@@ -1616,6 +1395,12 @@ cudaError_t prepare_kernels() {
     if ((r = allow_chain_smem_all<16, 16, true>()) != cudaSuccess) e = r;
     if ((r = allow_chain_smem_all<32, 8, false>()) != cudaSuccess) e = r;
     if ((r = allow_chain_smem_all<32, 8, true>()) != cudaSuccess) e = r;
+    if ((r = allow_tall<16, false>()) != cudaSuccess) e = r;
+    if ((r = allow_tall<16, true>()) != cudaSuccess) e = r;
+    if ((r = allow_tall<32, false>()) != cudaSuccess) e = r;
+    if ((r = allow_tall<32, true>()) != cudaSuccess) e = r;
+    if ((r = allow_tall<40, false>()) != cudaSuccess) e = r;
+    if ((r = allow_tall<40, true>()) != cudaSuccess) e = r;
     return e;
 }
 

@@ -173,8 +173,11 @@ struct GuideGradArgs {
 struct ColPlan {
     int items;   // rows per thread
     int warps;   // warps per CTA
-    int cluster; // CTAs per cluster along the column; 0: one CTA per 8-column strip (no cluster)
+    int cluster; // CTAs per cluster along the column, or one of the kernels below
 };
+constexpr int kColStrip = 0;   // one CTA per 8-column strip (col_strip_tma_kernel)
+constexpr int kColChain = -1;  // chained CTAs (col_chain_kernel)
+constexpr int kColTall = -2;   // persistent clusters fed by TMA (col_tall_kernel), ceil(H / rows) CTAs
 
 struct RowPlan {
     int items;   // elements per thread
@@ -227,6 +230,8 @@ enum KernelId {
     // 30: no longer used
     KID_COL_CHAIN_TRANSPOSE = 31,
     KID_COL_BWD_CHAIN = 32,
+    KID_COL_TALL = 33,
+    KID_COL_TALL_TRANSPOSE = 34,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
@@ -239,6 +244,8 @@ void prof_end(int handle, cudaStream_t s);
 // device status word of the current device (dts_api.cu; set up by the entry points before
 // their first launch)
 int* status_word();
+// flag value of the next chained vertical pass (never 0; dts_api.cu)
+unsigned next_chain_epoch();
 // SMs of the device, and resident CTAs per SM of a kernel at this block size (dts_api.cu)
 int sm_count();
 int blocks_per_sm(const void* kernel, int block, size_t smem);
@@ -356,6 +363,7 @@ cudaError_t launch_resident(const ResidentLaunch& l, cudaStream_t s);
 bool plan_cols(int H, ColPlan* p);
 bool plan_cols_multi(int H, ColPlan* p);
 bool plan_cols_cluster(int H, ColPlan* p);
+bool chain_plan(int H, ColPlan* p);
 // rows per strip of the tiled distance plane the strip kernel reads (0: columns too tall for it)
 long long strip_tile_rows(int H);
 cudaError_t prepare_kernels();
@@ -363,6 +371,7 @@ cudaError_t prepare_kernels();
 // backward launchers (dts_backward.cu)
 bool plan_rows_bwd(int W, RowPlan* p);
 bool plan_cols_bwd(int H, ColPlan* p);
+bool set_tuned_bwd_col(int H, const ColPlan& p);
 cudaError_t launch_row_bwd(const BwdArgs& a, int dist_half, bool final_pass, const RowPlan& p, cudaStream_t s);
 cudaError_t launch_col_bwd(const BwdArgs& a, int dist_half, const ColPlan& p, cudaStream_t s);
 cudaError_t launch_guide_grad(const GuideGradArgs& a, cudaStream_t s);

@@ -121,6 +121,8 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_COL_CHAIN: return "col_chain_kernel";
         case KID_COL_CHAIN_TRANSPOSE: return "col_chain_kernel<transpose>";
         case KID_COL_BWD_CHAIN: return "col_bwd_chain_kernel";
+        case KID_COL_TALL: return "col_tall_kernel";
+        case KID_COL_TALL_TRANSPOSE: return "col_tall_kernel<transpose>";
         default: return "unknown";
     }
 }

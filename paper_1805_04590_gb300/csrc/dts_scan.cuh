@@ -411,9 +411,9 @@ __device__ __forceinline__ void col_exchange_iter(const typename M::Pre& own_pre
 // Waits are bounded: one that runs out records DTS_ERR_TIMEOUT and raises the abort word, after
 // which no CTA of the solve waits again (its results are then invalid; the kernel still ends).
 //
-// Control words (zeroed once per solve; every launch leaves them at zero again):
-//   ctl[0] ticket counter, ctl[1] abort, ctl[32 + s] arrivals at strip s,
-//   ctl[32 + S + s] flag of strip s, ctl[32 + 2 S + s] CTAs of strip s that have read their carries.
+// Control words (zeroed once per solve): ctl[0] ticket counter and ctl[32 + s] arrivals at strip
+// s (every launch leaves both at zero again), ctl[1] abort, ctl[32 + S + s] flag of strip s: the
+// launch's epoch (a number the host gives every launch, never 0) once its carries are in place.
 struct ChainArgs {
     unsigned* ctl;
     float* agg;       // S x J x 32 Pre tuples, then S x J x 32 Suf tuples
@@ -423,6 +423,7 @@ struct ChainArgs {
     int* status;
     int skip_ticket;  // fault injection: this ticket does not count its arrival (-1: none)
     int stage;        // chunks per block of the composition's shared-memory staging (>= 1)
+    unsigned epoch;   // this launch's flag value (not 0, not that of an earlier launch of the solve)
 };
 // dynamic shared memory of a chained exchange staging `stage` chunks of mode M's tuples
 template <class M>
@@ -430,7 +431,7 @@ __host__ __device__ constexpr size_t chain_stage_bytes(int stage) {
     return (size_t)stage * 32 * (sizeof(typename M::Pre) + sizeof(typename M::Suf));
 }
 constexpr int kChainCtlHead = 32;
-__host__ __device__ constexpr long long chain_ctl_words(int S) { return kChainCtlHead + 3LL * S; }
+__host__ __device__ constexpr long long chain_ctl_words(int S) { return kChainCtlHead + 2LL * S; }
 
 template <typename T>
 __device__ __forceinline__ void st_cg(T* p, const T& v) {
@@ -457,6 +458,12 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 }
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// atomic add with acquire-release semantics at GPU scope; returns the old value
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
 }
 // records a device-side error in the status word (when there is one)
 __device__ __forceinline__ void record_status(int* status, int code) {
@@ -508,14 +515,15 @@ __device__ __forceinline__ void chain_exchange(const typename M::Pre& own_pre, c
         // this chunk's totals: the last warp holds the full prefix, the first the full suffix
         if (warp == NW - 1) st_cg(gpre + mine, M::pre_compose(wpre, own_pre));
         if (warp == 0) st_cg(gsuf + mine, M::suf_compose(own_suf, wsuf));
-        __threadfence();
         __syncthreads();
         unsigned* arrive = c.ctl + kChainCtlHead + strip;
         unsigned* flag = c.ctl + kChainCtlHead + c.S + strip;
-        unsigned* reads = c.ctl + kChainCtlHead + 2 * c.S + strip;
         if (threadIdx.x == 0) {
+            // the fence publishes the CTA's tuples (ordered before it by the barrier); the
+            // arrival's acquire side makes the other chunks' tuples visible to the composing CTA
+            __threadfence();
             s_combine = 0;
-            if (ticket != c.skip_ticket) s_combine = atomicAdd(arrive, 1u) == (unsigned)c.J - 1u;
+            if (ticket != c.skip_ticket) s_combine = atom_add_acq_rel_u32(arrive, 1u) == (unsigned)c.J - 1u;
         }
         __syncthreads();
         if (s_combine) {
@@ -523,7 +531,6 @@ __device__ __forceinline__ void chain_exchange(const typename M::Pre& own_pre, c
             // direction, warp 0) and bottom up (suffix direction, warp 1).  The tuples come into
             // shared memory in blocks of c.stage chunks, loaded by the whole CTA at once: one L2
             // round trip per block, not one per chunk
-            __threadfence();
             extern __shared__ __align__(16) float chain_stage[];
             constexpr int NP = sizeof(Pre) / 4, NS = sizeof(Suf) / 4;
             float* stp = chain_stage;                                  // c.stage x 32 Pre
@@ -558,36 +565,29 @@ __device__ __forceinline__ void chain_exchange(const typename M::Pre& own_pre, c
                 }
                 __syncthreads();
             }
-            __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) {
                 atomicExch(arrive, 0u);
-                st_release_u32(flag, 1u);
+                __threadfence();
+                st_release_u32(flag, c.epoch);
             }
         } else if (threadIdx.x == 0) {
-            if (ld_acquire_u32(flag) == 0u && ld_acquire_u32(c.ctl + 1) == 0u) {
+            if (ld_acquire_u32(flag) != c.epoch && ld_acquire_u32(c.ctl + 1) == 0u) {
                 const long long t0 = clock64();
-                while (ld_acquire_u32(flag) == 0u) {
+                while (ld_acquire_u32(flag) != c.epoch) {
                     if (ld_acquire_u32(c.ctl + 1) != 0u) break;
                     if (clock64() - t0 > c.timeout) {
                         atomicExch(c.ctl + 1, 1u);
                         record_status(c.status, DTS_ERR_TIMEOUT);
                         break;
                     }
-                    __nanosleep(64);  // leave the L2 to the composing CTA
+                    __nanosleep(32);  // leave the L2 to the composing CTA
                 }
             }
-            __threadfence();
         }
         __syncthreads();
         wpre = M::pre_compose(ld_cg(gpre + mine), wpre);
         wsuf = M::suf_compose(wsuf, ld_cg(gsuf + mine));
-        __syncthreads();  // every lane has read its carries
-        if (threadIdx.x == 0 && atomicAdd(reads, 1u) == (unsigned)c.J - 1u) {
-            // the strip's last reader: its flag and count go back to zero for the next launch
-            atomicExch(reads, 0u);
-            atomicExch(flag, 0u);
-        }
     }
     pre = wpre;
     suf = wsuf;
@@ -682,6 +682,21 @@ __device__ __forceinline__ float load1_d(const void* base, long long idx) {
 __device__ __forceinline__ void load4_f(const float* base, long long idx, float* out) {
     const float4 v = *reinterpret_cast<const float4*>(base + idx);
     out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+
+// four consecutive floats of a plane; CG: through L2 only (the plane is rewritten within the
+// launch by other SMs, whose writes an SM's L1 would not see)
+template <bool CG>
+__device__ __forceinline__ void load4_p(const float* base, long long idx, float* out) {
+    float4 v;
+    if constexpr (CG) v = __ldcg(reinterpret_cast<const float4*>(base + idx));
+    else v = *reinterpret_cast<const float4*>(base + idx);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+template <bool CG>
+__device__ __forceinline__ float load1_p(const float* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
 }
 
 __device__ __forceinline__ void store4_f(float* base, long long idx, const float* v) {

@@ -312,3 +312,13 @@ def test_backward_multispectral_full_size_slices(H, W):
     close(gt.cpu().numpy(), ref["t"], "grad target")
     close(gc.cpu().numpy(), ref["c"], "grad conf")
     close(gg.cpu().numpy(), ref["guide"], "grad guide")
+
+
+# the vertical adjoint's chain shapes (rows per thread, warps per CTA), each through a tuned plan
+# ("bcol H items warps -1") for a height no other test uses
+@pytest.mark.parametrize("H,items,warps", [(4501, 8, 16), (4502, 8, 8), (4503, 16, 8), (4504, 8, 32),
+                                           (4505, 16, 16)])
+def test_backward_chain_shapes(H, items, warps):
+    dts.autotune_import("bcol %d %d %d -1\n" % (H, items, warps))
+    assert ("bcol %d %d %d -1" % (H, items, warps)) in dts.autotune_export()
+    run_case(H, 40, K=2, update=dts.UPDATE_GD, seed=H, keep=2)

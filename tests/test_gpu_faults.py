@@ -40,9 +40,11 @@ def check_filter(prob, out, prm):
     assert float(np.abs(out.cpu().numpy() - ref).max()) <= 1e-4 * float(np.ptp(prob.target))
 
 
-# 100 x 200: the strip kernel covers the 25 strips in one round; 3000 x 70: chains of 24 chunks
+# 100 x 200: the strip kernel covers the 25 strips in one round; 3000 x 70: the tall-column
+# clusters cover the 3 strips in one round; 12000 x 70: chains of 94 chunks
 @pytest.mark.parametrize("H,W,kind,kernel", [(100, 200, INJECT_TMA_SKIP, "col_strip_kernel"),
-                                             (3000, 70, INJECT_CHAIN_SKIP, "col_chain_kernel")])
+                                             (3000, 70, INJECT_TMA_SKIP, "col_tall_kernel"),
+                                             (12000, 70, INJECT_CHAIN_SKIP, "col_chain_kernel")])
 def test_vertical_pass_wait_reports_timeout_and_recovers(H, W, kind, kernel):
     d = dev()
     lib = dts.load()

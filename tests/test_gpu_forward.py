@@ -332,16 +332,19 @@ def test_solve_multispectral_full_size_slices(H, W, sdt):
                                    f"(rounding alone: {moved:.3e})"
 
 
-# ---------------------------------------------------------------- chained and cluster vertical passes
-# Columns over 2176 rows run on chains of CTAs (col_chain_kernel): 128-row chunks (16 rows x 8
-# warps) by default, 256-row chunks (16 x 16, 32 x 8) as tuned shapes; the cluster kernel keeps
-# tall columns for batched solves and as a tuned shape ((40, 16) in clusters of 7 here).  Each
-# shape is set through a tuned plan for a height no other test uses (tuned plans last for the
-# process).  16384 rows is the tallest column.
+# ---------------------------------------------------------------- tall-column vertical passes
+# Columns over 2176 rows run on persistent TMA-fed clusters (col_tall_kernel: 16 warps of 16, 32 or
+# 40 rows per CTA, clusters of up to 16 CTAs: up to 10240 rows), taller ones on chains of CTAs
+# (col_chain_kernel: 128-row chunks, 16 rows x 8 warps, by default; 256-row chunks, 16 x 16 and
+# 32 x 8, as tuned shapes); the cluster kernel keeps tall columns for batched solves and as a
+# tuned shape ((40, 16) in clusters of 7 here).  Each non-default shape is set through a tuned plan
+# for a height no other test uses (tuned plans last for the process).  16384 rows is the tallest
+# column.
 @pytest.mark.parametrize("H,shape", [(2305, (16, 8, -1)), (2306, (16, 16, -1)), (2307, (32, 8, -1)),
-                                     (4101, (40, 16, 7)), (16384, None)])
+                                     (2308, (16, 16, -2)), (2309, (32, 16, -2)), (2310, (40, 16, -2)),
+                                     (4101, (40, 16, 7)), (10240, None), (12000, None), (16384, None)])
 def test_filter_chain_and_cluster_shapes(H, shape):
-    W = 70 if H < 16384 else 5
+    W = 70 if H < 10000 else 7
     if shape is not None:
         dts.autotune_import("col %d %d %d %d\n" % ((H,) + shape))
         assert ("col %d %d %d %d" % ((H,) + shape)) in dts.autotune_export()
