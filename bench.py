@@ -67,8 +67,12 @@ def oracle_solve(update, I, t, c, kw):
 
 # algorithmic bytes per pixel of each kernel (s_d distance storage, s_t target storage, C guide
 # channels of s_g bytes): every input element read once, every output element written once
-def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3):
+def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3, K=10):
     return {
+        # the persistent batched kernel runs a whole solve per launch: the distances, per iteration
+        # 2N passes, the update fused into K - 1 of the horizontal ones, and the last update
+        "batched_solve_kernel": (C * s_g + 2 * s_d + s_t + 4 + K * 2 * N * (8 + s_d) + (K - 1) * (12 + s_t)
+                                 + 16 + s_t),
         "distance_kernel": C * s_g + 2 * s_d + s_t + 4,
         # per pixel and iteration: the distances once per pass, z_k, t and c read and z_{k+1}
         # written by the update; the iterate itself stays in shared memory between passes
@@ -127,6 +131,8 @@ def parse_args():
                          "iterations (GD, Jacobi, CG), time against sigma_s / sigma_r, time against megapixels")
     ap.add_argument("--filter-kernel", choices=["rf", "box"], default="rf",
                     help="recursive-filter kernel, or the box kernel Eq. 10 prints")
+    ap.add_argument("--batch-policy", choices=["persistent", "graph"], default="persistent",
+                    help="batched workload: the persistent kernel, or the graph of per-image launch sequences")
     ap.add_argument("--charbonnier-eps", type=float, default=0.0,
                     help="> 0: Charbonnier loss on the target term (the paper's stereo loss uses 0.001)")
     return ap.parse_args()
@@ -216,6 +222,7 @@ def kernel_source(kernel):
     fn = ("dts_backward.cu" if kernel.startswith(BACKWARD_KERNELS) else "dts_cg.cu" if kernel.startswith("cg_")
           else "dts_box.cu" if kernel.startswith(("box_", "transpose_"))
           else "dts_resident.cu" if kernel.startswith("resident_")
+          else "dts_batched.cu" if kernel.startswith("batched_")
           else "dts_confidence.cu" if kernel.startswith(("square_plane_", "confidence_"))
           else "dts_forward.cu")
     return os.path.join(ROOT, "paper_1805_04590_gb300", "csrc", fn)
@@ -499,10 +506,10 @@ def roofline_of(args, case, recs, total_ms):
            "gpu_launches": launches_per_step * args.steps if launches_per_step else None}
     if not kern:
         return out
-    N = case.prm.passes
+    N, K = case.prm.passes, case.prm.iterations
     dom = max(kern, key=lambda n: kern[n]["ms"])
     kd = kern[dom]
-    bpp = bytes_per_pixel(dom, case.s_d, case.s_io, C=C, s_g=s_g, N=N)
+    bpp = bytes_per_pixel(dom, case.s_d, case.s_io, C=C, s_g=s_g, N=N, K=K)
     alg_bytes = bpp * kd["pixels"] / kd["launches"]
     avg_s = kd["ms"] / kd["launches"] / 1e3
     peak, peak_kind = measured_peak()
@@ -516,7 +523,7 @@ def roofline_of(args, case, recs, total_ms):
     step_bytes = step_algorithmic_bytes(case, C, s_g)
     step_s = total_ms / args.steps / 1e3
     profiled = len(range(0, args.steps, PROFILE_EVERY))
-    bpps = {n: bytes_per_pixel(n, case.s_d, case.s_io, C=C, s_g=s_g, N=N) for n in kern}
+    bpps = {n: bytes_per_pixel(n, case.s_d, case.s_io, C=C, s_g=s_g, N=N, K=K) for n in kern}
     moved = sum(bpps[n] * v["pixels"] for n, v in kern.items() if bpps[n] is not None) / profiled
     roof["step"] = {"algorithmic_bytes": int(step_bytes), "achieved": round(step_bytes / step_s / 1e9, 1),
                     "frac": round(step_bytes / step_s / 1e9 / peak, 4),
@@ -644,6 +651,8 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     inp = Inputs(args, dev)
     dirs = directions_for(args)
+    from paper_1805_04590_gb300 import dts as _dts
+    _dts.autotune_import("batch %d\n" % (1 if args.batch_policy == "graph" else 0))
     case = Case(args, dev, inp, dirs[0])
     main = measure(args, case, world, local_rank, flush)
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,

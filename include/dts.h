@@ -205,16 +205,33 @@ size_t dts_noalloc_max_workspace(void);
 /* Workspace bytes for dts_solve_batched over these n guides (0 on invalid arguments). */
 size_t dts_batched_workspace_size(int n, const dts_guide* guides, const dts_params* params);
 
-/* n independent solves of uneven sizes (the same parameters) as ONE CUDA graph launch on `stream`:
- * each image's launch sequence is captured on a few internal streams forked from one origin, so
- * small images run side by side; the instantiated graph is cached per argument set (pointers,
- * shapes, parameters) and later calls with the same arguments replay it.  If `stream` is being
- * captured by the caller, the launches join the caller's graph instead.  guides, targets, confs
- * and z_out are HOST arrays of n entries (device pointers, as in dts_solve; target_dtype shared);
- * z_init is the target; save_checkpoints must be 0.  The workspace holds one slice per image. */
+/* n independent solves of uneven sizes (the same parameters) as ONE CUDA graph launch on `stream`,
+ * the graph cached per argument set (pointers, shapes, parameters) and replayed by later calls
+ * with the same arguments.  When the batch allows it -- the recursive filter, GD or Jacobi (with
+ * or without the Charbonnier loss), plain confidence, iterations >= 1, at most 96 images of at
+ * most 1088 x 8192 with one guide dtype -- the graph holds one persistent kernel (after a reset of
+ * its control words): every image's solve is cut into stages (distances; per iteration N
+ * horizontal and N vertical passes, the update fused into the first horizontal pass; the last
+ * update) and the stages into jobs (groups of rows, 8-column strips), which the kernel's CTAs take
+ * from one queue in stage order, each job waiting (bounded) for its image's previous stage.
+ * Otherwise (or under the "batch 1" policy, see dts_autotune_batched) each image's launch sequence
+ * is captured on a few internal streams forked from one origin, so small images run side by side.
+ * If `stream` is being captured by the caller, the launches join the caller's graph instead.
+ * guides, targets, confs and z_out are HOST arrays of n entries (device pointers, as in dts_solve;
+ * target_dtype shared); z_init is the target; save_checkpoints must be 0.  The workspace holds the
+ * kernel's control words, then one slice per image. */
 int dts_solve_batched(int n, const dts_guide* guides, const void* const* targets, int target_dtype,
                       const float* const* confs, const dts_params* params, float* const* z_out, void* ws,
                       size_t ws_bytes, dts_stream stream);
+
+/* Autotuner for a batch (not part of the paper's method): times dts_solve_batched on these
+ * arguments with the persistent kernel and with the graph of per-image launches (2 warm-up and 3
+ * timed runs each on `stream`) and keeps the faster for later batched solves ("batch 0" or
+ * "batch 1" in dts_autotune_export).  A batch the persistent kernel does not take is solved once
+ * and leaves the choice as it is.  Synchronises `stream`.  Arguments as for dts_solve_batched. */
+int dts_autotune_batched(int n, const dts_guide* guides, const void* const* targets, int target_dtype,
+                         const float* const* confs, const dts_params* params, float* const* z_out, void* ws,
+                         size_t ws_bytes, dts_stream stream);
 
 /* Autotuner (not part of the paper's method): for this guide's height and width, times each
  * candidate vertical tile shape (rows per thread x warps per CTA x cluster size, where cluster
@@ -228,8 +245,9 @@ int dts_autotune(const dts_guide* guide, const dts_params* params, void* ws, siz
  * passes), "col H items warps cluster" lines (the vertical passes: cluster > 0 CTAs of `warps`
  * warps of `items` rows per thread; 0 the strip kernel; -1 the chained CTAs; -2 the persistent
  * TMA-fed clusters for tall columns) and "bcol H items warps cluster" lines (the vertical passes
- * of dts_solve_backward: cluster > 0, or -1 chained).  Batched solves take the cluster shapes for
- * their vertical passes.  With buf == NULL returns the bytes needed (including the terminating
+ * of dts_solve_backward: cluster > 0, or -1 chained), and a "batch P" line (P = 0: batched solves
+ * run the persistent kernel where the batch allows it; 1: the graph of per-image launches).
+ * Batched solves on the graph of launches take the cluster shapes for their vertical passes.  With buf == NULL returns the bytes needed (including the terminating
  * 0); else copies and returns that count, or minus DTS_ERR_INVALID_ARG when len is too small. */
 int dts_autotune_export(char* buf, size_t len);
 
@@ -254,17 +272,21 @@ int dts_last_status(dts_stream stream);
  *   never comes.
  * DTS_INJECT_BARRIER_SKIP: the next resident solve (DTS_RESIDENT=1) leaves out CTA 0's arrival
  *   at its first grid-wide barrier.
+ * DTS_INJECT_QUEUE_SKIP: the next persistent batched solve does not count its first job done, so
+ *   the jobs of that image's next stage wait for it.
  * kind 0 cancels; DTS_ERR_INVALID_ARG for unknown kinds. */
 #define DTS_INJECT_TMA_SKIP 1
 #define DTS_INJECT_CHAIN_SKIP 2
 #define DTS_INJECT_BARRIER_SKIP 3
+#define DTS_INJECT_QUEUE_SKIP 4
 int dts_debug_inject(int kind);
 
 /* ---- per-launch kernel timing (a tracing aid; not part of the paper's method) ----
  * mode 1: clear the record and start bracketing every kernel the library launches with two
  * CUDA events on that launch's stream; mode 2: resume without clearing; mode 0: stop.
  * Host-side only; it does not change what the kernels compute (events between kernels do
- * prevent the programmatic early launch of the next kernel).  DTS_ERR_INVALID_ARG for other modes. */
+ * prevent the programmatic early launch of the next kernel; batched solves issue their launches
+ * directly instead of replaying their cached graph).  DTS_ERR_INVALID_ARG for other modes. */
 int dts_profile(int mode);
 
 /* Copies up to max_records records of the launches made since dts_profile(1), in launch

@@ -91,6 +91,11 @@ int* status_word() {
     return g_status_ptr[dev].load();
 }
 
+bool injection_pending() {
+    std::lock_guard<std::mutex> lock(g_prep_mutex);
+    return g_inject != 0;
+}
+
 bool take_injected(int kind) {
     std::lock_guard<std::mutex> lock(g_prep_mutex);
     if (g_inject != kind) return false;
@@ -855,6 +860,50 @@ size_t batch_slice(const dts_guide& g, const dts_params* p) {
     return align_up(make_layout(g.H, g.W, p, 0).fwd_end, kPlaneAlign);
 }
 
+// How batches run: 0, the persistent kernel where the batch allows it (else the graph of
+// per-image launches); 1, the graph of per-image launches.  Set by the batched autotuner or by
+// the tuner text's "batch" line.
+std::atomic<int> g_batch_policy{0};
+
+// the batch runs as the persistent kernel: recursive filter, GD or Jacobi, plain confidence, at
+// least one iteration, at most kBatchMax images of one guide dtype within its size limits
+bool batch_is_persistent(int n, const dts_guide* guides, const dts_params* p) {
+    if (g_batch_policy.load() != 0 || n > kBatchMax || p->iterations < 1 || p->filter_kernel != DTS_KERNEL_RF ||
+        p->conf_mode != DTS_CONF_PLAIN || (p->update != DTS_UPDATE_GD && p->update != DTS_UPDATE_JACOBI))
+        return false;
+    for (int i = 0; i < n; ++i)
+        if (guides[i].dtype != guides[0].dtype || !batch_persistent_fits(guides[i].H, guides[i].W)) return false;
+    return true;
+}
+
+// The batch as one persistent kernel launch (with the reset of its control words) on `origin`.
+int issue_batch_persistent(int n, const dts_guide* guides, const void* const* targets, int tdt,
+                           const float* const* confs, const dts_params* p, float* const* z_out, void* ws,
+                           cudaStream_t origin) {
+    std::vector<BatchPlanes> planes(n);
+    size_t off = batch_ctl_bytes(n, p);
+    for (int i = 0; i < n; ++i) {
+        const Layout L = make_layout(guides[i].H, guides[i].W, p, 0);
+        char* base = ws_at(ws, off);
+        planes[i] = BatchPlanes{base + L.dX, base + L.dY, reinterpret_cast<float*>(base + L.u),
+                                reinterpret_cast<float*>(base + L.z), L.pitch};
+        off += batch_slice(guides[i], p);
+    }
+    BatchLaunch l = {};
+    l.n = n;
+    l.guides = guides;
+    l.targets = targets;
+    l.tdtype = tdt;
+    l.confs = confs;
+    l.p = p;
+    l.z_out = z_out;
+    l.planes = planes.data();
+    pass_log2a(p->sigma_s, p->passes, l.k2);
+    l.ctl = static_cast<unsigned*>(ws);
+    l.status = status_word();
+    return cuda_status(launch_batched(l, origin));
+}
+
 // Issues every image's solve on the side streams, forked from and joined back into `origin`.
 int issue_batch(int n, const dts_guide* guides, const void* const* targets, int tdt, const float* const* confs,
                 const dts_params* p, float* const* z_out, void* ws, BatchResources& r, cudaStream_t origin) {
@@ -868,7 +917,7 @@ int issue_batch(int n, const dts_guide* guides, const void* const* targets, int 
         return (long long)guides[a].H * guides[a].W > (long long)guides[b].H * guides[b].W;
     });
     std::vector<size_t> offset(n);
-    size_t off = 0;
+    size_t off = batch_ctl_bytes(n, p);
     for (int i = 0; i < n; ++i) {
         offset[i] = off;
         off += batch_slice(guides[i], p);
@@ -903,7 +952,7 @@ int issue_batch(int n, const dts_guide* guides, const void* const* targets, int 
 
 extern "C" size_t dts_batched_workspace_size(int n, const dts_guide* guides, const dts_params* params) {
     if (n < 1 || !guides || check_params(params)) return 0;
-    size_t total = 0;
+    size_t total = batch_ctl_bytes(n, params);
     for (int i = 0; i < n; ++i) {
         if (check_guide(&guides[i])) return 0;
         total += batch_slice(guides[i], params);
@@ -937,13 +986,21 @@ extern "C" int dts_solve_batched(int n, const dts_guide* guides, const void* con
     std::lock_guard<std::mutex> lock(g_batch_mutex);
     BatchResources* r = nullptr;
     if ((st = batch_resources(dev, &r))) return st;
+    const bool persistent = batch_is_persistent(n, guides, params);
+    auto issue = [&](cudaStream_t origin) {
+        return persistent ? issue_batch_persistent(n, guides, targets, target_dtype, confs, params, z_out, ws, origin)
+                          : issue_batch(n, guides, targets, target_dtype, confs, params, z_out, ws, *r, origin);
+    };
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return DTS_ERR_CUDA;
-    if (cap != cudaStreamCaptureStatusNone)  // the caller is capturing: become part of its graph
-        return issue_batch(n, guides, targets, target_dtype, confs, params, z_out, ws, *r, s);
+    // the caller is capturing: become part of its graph; the per-launch timer is on, or a fault
+    // injection is pending: launch directly (a replayed graph's kernels are not bracketed by
+    // events, and an injection captured into the cached graph would recur on every replay)
+    if (cap != cudaStreamCaptureStatusNone || prof_active() || injection_pending()) return issue(s);
     // key: every pointer, shape and parameter that the captured launches bake in
     std::vector<unsigned long long> key;
     key.push_back((unsigned long long)n);
+    key.push_back((unsigned long long)persistent);
     key.push_back((unsigned long long)(uintptr_t)ws);
     key.push_back((unsigned long long)target_dtype);
     {
@@ -963,7 +1020,7 @@ extern "C" int dts_solve_batched(int n, const dts_guide* guides, const void* con
     for (auto& bg : cache)
         if (bg.key == key) return cudaGraphLaunch(bg.exec, s) == cudaSuccess ? DTS_OK : DTS_ERR_CUDA;
     if (cudaStreamBeginCapture(r->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DTS_ERR_CUDA;
-    st = issue_batch(n, guides, targets, target_dtype, confs, params, z_out, ws, *r, r->capture);
+    st = issue(r->capture);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(r->capture, &graph);
     if (st) {
@@ -983,6 +1040,51 @@ extern "C" int dts_solve_batched(int n, const dts_guide* guides, const void* con
     return cudaGraphLaunch(exec, s) == cudaSuccess ? DTS_OK : DTS_ERR_CUDA;
 }
 
+
+// Times this batch both ways -- the persistent kernel and the graph of per-image launches, each
+// replayed from its cached graph, 2 warm-up and 3 timed runs on `stream` -- and keeps the faster
+// as the policy of later batched solves.  Batches the persistent kernel does not take leave the
+// policy as it is.
+extern "C" int dts_autotune_batched(int n, const dts_guide* guides, const void* const* targets, int target_dtype,
+                                    const float* const* confs, const dts_params* params, float* const* z_out,
+                                    void* ws, size_t ws_bytes, dts_stream stream) {
+    if (n < 1 || !guides || !params) return DTS_ERR_INVALID_ARG;
+    const int saved = g_batch_policy.load();
+    g_batch_policy.store(0);
+    const bool eligible = batch_is_persistent(n, guides, params);
+    g_batch_policy.store(saved);
+    int st;
+    if (!eligible)  // validates the arguments all the same
+        return dts_solve_batched(n, guides, targets, target_dtype, confs, params, z_out, ws, ws_bytes, stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return DTS_ERR_CUDA;
+    float ms[2] = {0.f, 0.f};
+    for (int policy = 0; policy < 2; ++policy) {
+        g_batch_policy.store(policy);
+        for (int r = 0; r < 5; ++r) {
+            st = r == 2 && cudaEventRecord(e0, s) != cudaSuccess ? (int)DTS_ERR_CUDA : (int)DTS_OK;
+            if (st || (st = dts_solve_batched(n, guides, targets, target_dtype, confs, params, z_out, ws, ws_bytes,
+                                              stream))) {
+                g_batch_policy.store(saved);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return st;
+            }
+        }
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms[policy], e0, e1) != cudaSuccess) {
+            g_batch_policy.store(saved);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return DTS_ERR_CUDA;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_batch_policy.store(ms[1] < ms[0] ? 1 : 0);
+    return DTS_OK;
+}
 
 // ---------------------------------------------------------------- autotuner
 namespace dts {
@@ -1075,7 +1177,7 @@ extern "C" int dts_autotune(const dts_guide* guide, const dts_params* params, vo
 }
 
 extern "C" int dts_autotune_export(char* buf, size_t len) {
-    const std::string t = tuned_export() + tuned_bwd_export();
+    const std::string t = tuned_export() + tuned_bwd_export() + "batch " + std::to_string(g_batch_policy.load()) + "\n";
     if (!buf) return (int)t.size() + 1;
     if (len < t.size() + 1) return -DTS_ERR_INVALID_ARG;
     memcpy(buf, t.c_str(), t.size() + 1);
@@ -1089,6 +1191,8 @@ extern "C" int dts_autotune_import(const char* text) {
         int a = 0, b = 0, c = 0, d = 0, used = 0;
         if (sscanf(p, "row %d %d %n", &a, &b, &used) == 2 && used > 0) {
             if (a >= 1 && (b == 8 || b == 16 || b == 32)) set_tuned_row(a, b);
+        } else if (sscanf(p, "batch %d %n", &a, &used) == 1 && used > 0) {
+            if (a == 0 || a == 1) g_batch_policy.store(a);
         } else if (sscanf(p, "bcol %d %d %d %d %n", &a, &b, &c, &d, &used) == 4 && used > 0) {
             set_tuned_bwd_col(a, ColPlan{b, c, d});
         } else if (sscanf(p, "col %d %d %d %d %n", &a, &b, &c, &d, &used) == 4 && used > 0) {
@@ -1299,8 +1403,7 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
 }
 
 extern "C" int dts_debug_inject(int kind) {
-    if (kind != 0 && kind != DTS_INJECT_TMA_SKIP && kind != DTS_INJECT_CHAIN_SKIP && kind != DTS_INJECT_BARRIER_SKIP)
-        return DTS_ERR_INVALID_ARG;
+    if (kind < 0 || kind > DTS_INJECT_QUEUE_SKIP) return DTS_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_prep_mutex);
     g_inject = kind;
     return DTS_OK;

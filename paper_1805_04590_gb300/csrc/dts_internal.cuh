@@ -232,14 +232,17 @@ enum KernelId {
     KID_COL_BWD_CHAIN = 32,
     KID_COL_TALL = 33,
     KID_COL_TALL_TRANSPOSE = 34,
+    KID_BATCHED = 35,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
 constexpr int kFlagTarget16 = 2;   // target stored in 16 bits
 
-// per-launch timer (dts_profile.cu): returns a handle for prof_end, or -1 when off
+// per-launch timer (dts_profile.cu): returns a handle for prof_end, or -1 when off (launches
+// captured into a graph are not timed); prof_active: the timer is on
 int prof_begin(int kernel, long long pixels, int flags, cudaStream_t s);
 void prof_end(int handle, cudaStream_t s);
+bool prof_active();
 
 // device status word of the current device (dts_api.cu; set up by the entry points before
 // their first launch)
@@ -252,6 +255,7 @@ int blocks_per_sm(const void* kernel, int block, size_t smem);
 // one-shot fault injection for tests (dts_debug_inject): true when `kind` is pending, which it
 // then no longer is (dts_api.cu)
 bool take_injected(int kind);
+bool injection_pending();
 
 // Bounded device-side waits: about a second at the boost clock, about a millisecond when a test
 // has requested a fault injection.
@@ -325,6 +329,38 @@ int cg_blocks(int H, long long pitch);
 cudaError_t launch_cg_apply(const CgArgs& a, bool init, cudaStream_t s);
 cudaError_t launch_cg_step(const CgArgs& a, cudaStream_t s);
 cudaError_t launch_cg_direction(const CgArgs& a, cudaStream_t s);
+
+// the batched solve as one persistent kernel over a queue of jobs (dts_batched.cu): up to
+// kBatchMax images of at most kBatchMaxRows x kBatchMaxCols, recursive filter, GD or Jacobi,
+// plain confidence, no checkpoints, iterations >= 1.  Control words: kBatchCtlHead words, then
+// one finished-job counter per image and stage, batch_ctl_bytes in all (at the workspace start).
+constexpr int kBatchMax = 96;
+constexpr int kBatchCtlHead = 32;
+constexpr int kBatchMaxRows = 4 * 16 * 17;  // a vertical job: 16 warps x 4 segments x 17 rows
+constexpr int kBatchMaxCols = 16 * 512;     // a horizontal job: 512 threads x 16 positions
+struct BatchPlanes {
+    void* dX;
+    void* dY;
+    float* u;
+    float* z;
+    long long pitch;
+};
+struct BatchLaunch {
+    int n;
+    const dts_guide* guides;
+    const void* const* targets;
+    int tdtype;
+    const float* const* confs;
+    const dts_params* p;
+    float* const* z_out;
+    const BatchPlanes* planes;
+    float k2[kMaxPasses];
+    unsigned* ctl;
+    int* status;
+};
+size_t batch_ctl_bytes(int n, const dts_params* p);
+bool batch_persistent_fits(int H, int W);
+cudaError_t launch_batched(const BatchLaunch& l, cudaStream_t s);
 
 // the whole solve with the iterate resident in shared memory (dts_resident.cu): one cooperative
 // CTA per tile of TH rows x 512 columns, ntx x nty tiles; scratch of ragg_floats + cagg_floats

@@ -56,6 +56,11 @@ int prof_begin(int kernel, long long pixels, int flags, cudaStream_t s) {
     return (int)g_records.size() - 1;
 }
 
+bool prof_active() {
+    std::lock_guard<std::mutex> lock(g_mu);
+    return g_enabled;
+}
+
 void prof_end(int handle, cudaStream_t s) {
     if (handle < 0) return;
     std::lock_guard<std::mutex> lock(g_mu);
@@ -123,6 +128,7 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_COL_BWD_CHAIN: return "col_bwd_chain_kernel";
         case KID_COL_TALL: return "col_tall_kernel";
         case KID_COL_TALL_TRANSPOSE: return "col_tall_kernel<transpose>";
+        case KID_BATCHED: return "batched_solve_kernel";
         default: return "unknown";
     }
 }

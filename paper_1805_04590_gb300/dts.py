@@ -81,6 +81,7 @@ EXPORTS = ("dts_status_string", "dts_version", "dts_workspace_size", "dts_domain
            "dts_solve", "dts_solve_backward", "dts_last_status", "dts_profile", "dts_profile_read",
            "dts_kernel_name", "dts_solve_noalloc", "dts_noalloc_max_workspace", "dts_batched_workspace_size",
            "dts_solve_batched", "dts_debug_inject", "dts_autotune", "dts_autotune_export", "dts_autotune_import",
+           "dts_autotune_batched",
            "dts_confidence")
 
 
@@ -117,6 +118,7 @@ def load(build_if_missing: bool = True):
     lib.dts_batched_workspace_size.argtypes = [i, P(CGuide), P(CParams)]
     lib.dts_batched_workspace_size.restype = sz
     lib.dts_solve_batched.argtypes = [i, P(CGuide), P(vp), i, P(vp), P(CParams), P(vp), vp, sz, vp]
+    lib.dts_autotune_batched.argtypes = [i, P(CGuide), P(vp), i, P(vp), P(CParams), P(vp), vp, sz, vp]
     lib.dts_debug_inject.argtypes = [i]
     lib.dts_autotune.argtypes = [P(CGuide), P(CParams), vp, sz, vp]
     lib.dts_autotune_export.argtypes = [ctypes.c_char_p, sz]
@@ -128,7 +130,8 @@ def load(build_if_missing: bool = True):
     lib.dts_kernel_name.restype = ctypes.c_char_p
     for name in ("dts_domain_transform", "dts_filter", "dts_solve", "dts_solve_backward", "dts_last_status",
                  "dts_confidence",
-                 "dts_profile", "dts_profile_read", "dts_solve_noalloc", "dts_solve_batched", "dts_debug_inject",
+                 "dts_profile", "dts_profile_read", "dts_solve_noalloc", "dts_solve_batched", "dts_autotune_batched",
+                 "dts_debug_inject",
                  "dts_autotune", "dts_autotune_export", "dts_autotune_import"):
         getattr(lib, name).restype = i
     _lib = lib
@@ -304,17 +307,8 @@ def autotune_load(path: str) -> bool:
     return True
 
 
-def dts_solve_batched(guides, targets, confs, params: Params, outs=None, ws: Optional[torch.Tensor] = None,
-                      stream=None, autotune: bool = False):
-    """Solves of uneven sizes (lists of CUDA tensors, same parameters) as one CUDA graph launch.
-    With autotune=True the tile shapes of every distinct size are measured first."""
+def _batch_args(guides, targets, confs, params: Params, outs, ws):
     n = len(guides)
-    if autotune:
-        tuned = set()
-        for g in guides:
-            if tuple(g.shape) not in tuned:
-                dts_autotune(g, params, stream=stream)
-                tuned.add(tuple(g.shape))
     if not (len(targets) == len(confs) == n) or n == 0:
         raise ValueError("guides, targets and confs must be non-empty lists of equal length")
     dt = targets[0].dtype
@@ -328,9 +322,28 @@ def dts_solve_batched(guides, targets, confs, params: Params, outs=None, ws: Opt
     carr = (ctypes.c_void_p * n)(*[c.data_ptr() for c in confs])
     oarr = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
     ws = batched_workspace(guides, params) if ws is None else ws
+    return n, garr, tarr, _TORCH_DTYPE[dt], carr, outs, oarr, ws
+
+
+def dts_solve_batched(guides, targets, confs, params: Params, outs=None, ws: Optional[torch.Tensor] = None,
+                      stream=None, autotune: bool = False):
+    """Solves of uneven sizes (lists of CUDA tensors, same parameters) as one CUDA graph launch
+    (one persistent kernel when the batch allows it).  With autotune=True the tile shapes of every
+    distinct size are measured first, then the batch's two ways of running (dts_autotune_batched)."""
+    if autotune:
+        tuned = set()
+        for g in guides:
+            if tuple(g.shape) not in tuned:
+                dts_autotune(g, params, stream=stream)
+                tuned.add(tuple(g.shape))
+    n, garr, tarr, tdt, carr, outs, oarr, ws = _batch_args(guides, targets, confs, params, outs, ws)
     p = params.c()
-    _check(load().dts_solve_batched(n, garr, tarr, _TORCH_DTYPE[dt], carr, ctypes.byref(p), oarr, ws.data_ptr(),
-                                    ws.numel(), _stream(stream)), "dts_solve_batched")
+    lib = load()
+    if autotune:
+        _check(lib.dts_autotune_batched(n, garr, tarr, tdt, carr, ctypes.byref(p), oarr, ws.data_ptr(), ws.numel(),
+                                        _stream(stream)), "dts_autotune_batched")
+    _check(lib.dts_solve_batched(n, garr, tarr, tdt, carr, ctypes.byref(p), oarr, ws.data_ptr(), ws.numel(),
+                                 _stream(stream)), "dts_solve_batched")
     return outs
 
 

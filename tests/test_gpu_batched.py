@@ -1,6 +1,7 @@
-"""The batched entry point: images of uneven sizes solved as one CUDA graph launch,
-checked image by image against the FP64 oracle and against dts_solve, on repeated
-calls (graph replay) and after the arguments change (new capture)."""
+"""The batched entry point: images of uneven sizes solved as one CUDA graph launch -- one
+persistent kernel over a queue of jobs where the batch allows it, else the per-image launch
+sequences on side streams -- checked image by image against the FP64 oracle and against
+dts_solve, on repeated calls (graph replay) and after the arguments change (new capture)."""
 import numpy as np
 import pytest
 import torch
@@ -152,3 +153,92 @@ def test_batched_charbonnier():
         ref = oracle.solve(p.guide, p.target, p.conf, lam=prm.lam, sigma_s=prm.sigma_s, sigma_r=prm.sigma_r,
                            iterations=prm.iterations, charbonnier_eps=1.0)
         assert np.abs(outs[i].cpu().numpy() - ref).max() <= TOL * float(np.ptp(p.target)), i
+
+
+
+def launched(fn):
+    """Runs fn with the library's launch timer on; returns the names of the kernels it launched."""
+    dts.dts_profile(1)
+    try:
+        out = fn()
+        torch.cuda.synchronize()
+        return out, {r[0] for r in dts.dts_profile_read()}
+    finally:
+        dts.dts_profile(0)
+
+
+def _oracle_check(wl, outs, prm, guides=None, targets=None, **kw):
+    for i, p in enumerate(wl.problems):
+        gi = p.guide if guides is None else guides[i].float().cpu().numpy().astype(np.float64)
+        ti = p.target if targets is None else targets[i].float().cpu().numpy().astype(np.float64)
+        ref = oracle.solve(gi, ti, p.conf, lam=prm.lam, sigma_s=prm.sigma_s, sigma_r=prm.sigma_r,
+                           iterations=prm.iterations, passes=prm.passes, update=prm.update, **kw)
+        z = outs[i].cpu().numpy()
+        assert np.abs(z - ref).max() <= TOL * (float(np.ptp(ti)) or 1.0), (i, p.target.shape)
+
+
+# The persistent kernel (the default for batches it takes): variants of the update and the
+# storage, FP16 distances, and the edge sizes of its jobs -- one pixel, a row of 8192 (one row group
+# of 512 threads x 16 positions), a column of 1088 (16 warps x 4 segments x 17 rows), the switch
+# from 9 to 17 rows per thread above 576 rows.
+@pytest.mark.parametrize("variant", ["gd", "jacobi_charbonnier", "f16_distances", "bf16", "edges"])
+def test_persistent_batched_kernel(variant):
+    dts.autotune_import("batch 0\n")
+    if variant == "edges":
+        d = dev()
+        sizes = [(1, 1), (1, 8192), (1088, 3), (577, 40), (576, 21), (9, 1000)]
+        probs = [workloads.random_problem(H, W, C=3, seed=H + W) for H, W in sizes]
+
+        class WL:
+            problems = probs
+        wl = WL()
+        g = [torch.from_numpy(p.guide).to(d) for p in probs]
+        t = [torch.from_numpy(p.target).to(d) for p in probs]
+        c = [torch.from_numpy(p.conf).to(d) for p in probs]
+        prm = dts.Params(lam=0.99, sigma_s=16.0, sigma_r=0.1, iterations=4, passes=3)
+    else:
+        wl, g, t, c, prm = _batch(10, n=6)
+    kw = {}
+    if variant == "jacobi_charbonnier":
+        prm.update = dts.UPDATE_JACOBI
+        prm.charbonnier_eps = 1e-3
+        kw["charbonnier_eps"] = 1e-3
+    if variant == "f16_distances":
+        prm.dist_dtype = dts.F16
+    if variant == "bf16":
+        g = [x.to(torch.bfloat16) for x in g]
+        t = [x.to(torch.bfloat16) for x in t]
+    outs, names = launched(lambda: dts.dts_solve_batched(g, t, c, prm))
+    assert "batched_solve_kernel" in names, names
+    assert dts.dts_last_status() == 0
+    if variant == "f16_distances":  # against the workspace solve with the same FP16 distances
+        for i in range(len(g)):
+            single = dts.dts_solve(g[i], t[i], c[i], prm).cpu().numpy()
+            assert np.abs(outs[i].cpu().numpy() - single).max() <= TOL * float(np.ptp(wl.problems[i].target)), i
+    else:
+        _oracle_check(wl, outs, prm, guides=g if variant == "bf16" else None,
+                      targets=t if variant == "bf16" else None, **kw)
+    # the replayed graph (no timer) gives the same result
+    again = dts.dts_solve_batched(g, t, c, prm)
+    torch.cuda.synchronize()
+    for a, b in zip(outs, again):
+        assert torch.equal(a, b)
+
+
+def test_batch_policy_and_its_tuner():
+    """The graph of per-image launches ("batch 1") and the persistent kernel ("batch 0") agree with
+    the oracle; the batched tuner times both, keeps one, and the solve it then runs is exact."""
+    wl, g, t, c, prm = _batch(11, n=5)
+    dts.autotune_import("batch 1\n")
+    outs, names = launched(lambda: dts.dts_solve_batched(g, t, c, prm))
+    assert "batched_solve_kernel" not in names and "row_pass_kernel" in names, names
+    _oracle_check(wl, outs, prm)
+    dts.autotune_import("batch 0\n")
+    outs, names = launched(lambda: dts.dts_solve_batched(g, t, c, prm))
+    assert "batched_solve_kernel" in names, names
+    _oracle_check(wl, outs, prm)
+    outs = dts.dts_solve_batched(g, t, c, prm, autotune=True)
+    torch.cuda.synchronize()
+    assert ("batch 0" in dts.autotune_export()) or ("batch 1" in dts.autotune_export())
+    _oracle_check(wl, outs, prm)
+    dts.autotune_import("batch 0\n")

@@ -1,8 +1,9 @@
 """Failure detection without a GPU fault.  A host-requested, one-shot injection makes one bounded
 device-side wait of the hot path run out (about a millisecond under injection): the strip kernel's
 wait for a slab load that was left out, the chained vertical pass's wait for a strip composition
-that never comes (one chunk does not count its arrival), and the resident solve's grid barrier
-(one CTA leaves out its arrival).  Each time the kernel records DTS_ERR_TIMEOUT in the device
+that never comes (one chunk does not count its arrival), the resident solve's grid barrier
+(one CTA leaves out its arrival), and the persistent batched solve's wait for an image's previous
+stage (one job does not count itself done).  Each time the kernel records DTS_ERR_TIMEOUT in the device
 status word and still completes; the status reads back once and is then clear, and the next call
 on the same workspace matches the oracle again."""
 import numpy as np
@@ -14,7 +15,7 @@ from paper_1805_04590_gb300 import dts, workloads
 
 pytestmark = pytest.mark.gpu
 
-INJECT_TMA_SKIP, INJECT_CHAIN_SKIP, INJECT_BARRIER_SKIP = 1, 2, 3
+INJECT_TMA_SKIP, INJECT_CHAIN_SKIP, INJECT_BARRIER_SKIP, INJECT_QUEUE_SKIP = 1, 2, 3, 4
 TIMEOUT = 5
 
 
@@ -111,3 +112,23 @@ def test_resident_grid_barrier_reports_timeout_and_recovers(monkeypatch):
     assert dts.dts_last_status() == 0
     ref = oracle.solve(prob.guide, prob.target, prob.conf, lam=1.0, sigma_s=8.0, sigma_r=0.2, iterations=3)
     assert float(np.abs(z.cpu().numpy() - ref).max()) <= 1e-4 * float(np.ptp(prob.target))
+
+
+def test_batched_queue_wait_reports_timeout_and_recovers():
+    d = dev()
+    lib = dts.load()
+    wl = workloads.workload_batched(seed=12, n=4, hmin=20, hmax=120, wmin=20, wmax=160)
+    g = [torch.from_numpy(p.guide).to(d) for p in wl.problems]
+    t = [torch.from_numpy(p.target).to(d) for p in wl.problems]
+    c = [torch.from_numpy(p.conf).to(d) for p in wl.problems]
+    prm = dts.Params(lam=1.0, sigma_s=8.0, sigma_r=0.2, iterations=2)
+    dts.autotune_import("batch 0\n")
+    assert lib.dts_debug_inject(INJECT_QUEUE_SKIP) == 0
+    assert "batched_solve_kernel" in launched(lambda: dts.dts_solve_batched(g, t, c, prm))
+    assert dts.dts_last_status() == TIMEOUT
+    assert dts.dts_last_status() == 0
+    outs = dts.dts_solve_batched(g, t, c, prm)
+    assert dts.dts_last_status() == 0
+    for i, p in enumerate(wl.problems):
+        ref = oracle.solve(p.guide, p.target, p.conf, lam=1.0, sigma_s=8.0, sigma_r=0.2, iterations=2)
+        assert float(np.abs(outs[i].cpu().numpy() - ref).max()) <= 1e-4 * float(np.ptp(p.target)), i
