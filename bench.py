@@ -87,6 +87,8 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3, K=10):
         "row_pass_kernel<support>": s_d + 4,
         "col_pass_kernel<support>": 12 + s_d,
         "row_pass_kernel<update>": 20 + s_t + s_d,
+        "row_stream_kernel": 8 + s_d,
+        "row_stream_kernel<update>": 20 + s_t + s_d,
         "update_kernel": 16 + s_t,
         "row_bwd_kernel": 24 + s_d,
         "row_bwd_kernel<final>": 28 + s_d,
@@ -223,6 +225,7 @@ def kernel_source(kernel):
           else "dts_box.cu" if kernel.startswith(("box_", "transpose_"))
           else "dts_resident.cu" if kernel.startswith("resident_")
           else "dts_batched.cu" if kernel.startswith("batched_")
+          else "dts_rows.cu" if kernel.startswith("row_stream_")
           else "dts_confidence.cu" if kernel.startswith(("square_plane_", "confidence_"))
           else "dts_forward.cu")
     return os.path.join(ROOT, "paper_1805_04590_gb300", "csrc", fn)

@@ -274,11 +274,14 @@ int dts_last_status(dts_stream stream);
  *   at its first grid-wide barrier.
  * DTS_INJECT_QUEUE_SKIP: the next persistent batched solve does not count its first job done, so
  *   the jobs of that image's next stage wait for it.
+ * DTS_INJECT_STAGE_SKIP: the next horizontal pass on the streaming row kernel (rows over 8192
+ *   columns by default) leaves out CTA 0's copies of its first row.
  * kind 0 cancels; DTS_ERR_INVALID_ARG for unknown kinds. */
 #define DTS_INJECT_TMA_SKIP 1
 #define DTS_INJECT_CHAIN_SKIP 2
 #define DTS_INJECT_BARRIER_SKIP 3
 #define DTS_INJECT_QUEUE_SKIP 4
+#define DTS_INJECT_STAGE_SKIP 5
 int dts_debug_inject(int kind);
 
 /* ---- per-launch kernel timing (a tracing aid; not part of the paper's method) ----

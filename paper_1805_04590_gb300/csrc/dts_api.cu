@@ -37,7 +37,8 @@ int ensure_prepared() {
     std::lock_guard<std::mutex> lock(g_prep_mutex);
     if (!g_prepared[dev]) {
         if (prepare_kernels() != cudaSuccess || prepare_backward_kernels() != cudaSuccess ||
-            prepare_box_kernels() != cudaSuccess || prepare_resident_kernel() != cudaSuccess)
+            prepare_box_kernels() != cudaSuccess || prepare_resident_kernel() != cudaSuccess ||
+            prepare_row_stream_kernels() != cudaSuccess)
             return DTS_ERR_CUDA;
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess || p == nullptr) return DTS_ERR_CUDA;
@@ -1152,12 +1153,12 @@ extern "C" int dts_autotune(const dts_guide* guide, const dts_params* params, vo
     // horizontal items per thread
     int best_items = pl.rows.items;
     best = 1e30f;
-    for (int items : {8, 16, 32}) {
+    for (int items : {8, 16, 32, 17, 33}) {
         RowPlan rp;
         rp.items = items;
         rp.tpr = ((guide->W + items - 1) / items + 31) / 32 * 32;
-        if (rp.tpr > (items >= 32 ? 320 : 1024)) continue;
-        rp.rpb = rp.tpr < 256 ? 256 / rp.tpr : 1;
+        if (items % 2 ? !row_stream_fits(guide->W, items, dh) : rp.tpr > (items >= 32 ? 320 : 1024)) continue;
+        rp.rpb = items % 2 || rp.tpr >= 256 ? 1 : 256 / rp.tpr;
         PassArgs r = base_pass(guide, L);
         r.src = u;
         r.dst = u;
@@ -1190,7 +1191,7 @@ extern "C" int dts_autotune_import(const char* text) {
     while (*p) {
         int a = 0, b = 0, c = 0, d = 0, used = 0;
         if (sscanf(p, "row %d %d %n", &a, &b, &used) == 2 && used > 0) {
-            if (a >= 1 && (b == 8 || b == 16 || b == 32)) set_tuned_row(a, b);
+            if (a >= 1 && (b == 8 || b == 16 || b == 32 || b == 17 || b == 33)) set_tuned_row(a, b);
         } else if (sscanf(p, "batch %d %n", &a, &used) == 1 && used > 0) {
             if (a == 0 || a == 1) g_batch_policy.store(a);
         } else if (sscanf(p, "bcol %d %d %d %d %n", &a, &b, &c, &d, &used) == 4 && used > 0) {
@@ -1403,7 +1404,7 @@ extern "C" int dts_solve_backward(const dts_guide* guide, const void* target, in
 }
 
 extern "C" int dts_debug_inject(int kind) {
-    if (kind < 0 || kind > DTS_INJECT_QUEUE_SKIP) return DTS_ERR_INVALID_ARG;
+    if (kind < 0 || kind > DTS_INJECT_STAGE_SKIP) return DTS_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_prep_mutex);
     g_inject = kind;
     return DTS_OK;

@@ -945,15 +945,32 @@ cudaError_t launch_copy_plane(const void* src, int src_dtype, long long src_pitc
 }
 
 cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const RowPlan& p, cudaStream_t s) {
+    const int flags = (dist_half ? kFlagDistHalf : 0) | (kind == PASS_UPDATE_ROW && a.t_dtype != DTS_F32 ? kFlagTarget16 : 0);
+    RowPlan q = p;
+    if (p.items % 2) {
+        // a streaming plan: the plain and update passes on planes the bulk copies can address,
+        // else the regular kernel's plan for the row length
+        const bool upd = kind == PASS_UPDATE_ROW;
+        if ((kind == PASS_PLAIN || upd) && row_stream_fits(a.W, p.items, dist_half) &&
+            row_stream_addressable(a, dist_half, upd)) {
+            const int h = prof_begin(upd ? KID_ROW_STREAM_UPDATE : KID_ROW_STREAM, (long long)a.H * a.W, flags, s);
+            const cudaError_t e = launch_row_stream(a, dist_half, p.items, upd, s);
+            prof_end(h, s);
+            return e;
+        }
+        RowPlan plain;
+        if (!plan_rows_regular(a.W, &plain)) return cudaErrorInvalidValue;
+        if (!upd) q = plain;
+        else if (!plan_rows_update(a.W, plain, &q)) return cudaErrorInvalidValue;
+    }
     const int h = prof_begin(kind == PASS_SUPPORT ? KID_ROW_SUPPORT : kind == PASS_UPDATE_ROW ? KID_ROW_UPDATE
                              : kind == PASS_TRANSPOSE ? KID_ROW_TRANSPOSE : KID_ROW_PLAIN,
-                             (long long)a.H * a.W,
-                             (dist_half ? kFlagDistHalf : 0) | (kind == PASS_UPDATE_ROW && a.t_dtype != DTS_F32 ? kFlagTarget16 : 0), s);
+                             (long long)a.H * a.W, flags, s);
     cudaError_t e = cudaErrorInvalidValue;
-    if (p.items == 8) e = dist_half ? launch_row_k<8, true>(a, kind, p, s) : launch_row_k<8, false>(a, kind, p, s);
-    if (p.items == 16) e = dist_half ? launch_row_k<16, true>(a, kind, p, s) : launch_row_k<16, false>(a, kind, p, s);
-    if (p.items == 32 && p.tpr * p.rpb <= (kind == PASS_UPDATE_ROW ? 512 : 320))
-        e = dist_half ? launch_row_k<32, true>(a, kind, p, s) : launch_row_k<32, false>(a, kind, p, s);
+    if (q.items == 8) e = dist_half ? launch_row_k<8, true>(a, kind, q, s) : launch_row_k<8, false>(a, kind, q, s);
+    if (q.items == 16) e = dist_half ? launch_row_k<16, true>(a, kind, q, s) : launch_row_k<16, false>(a, kind, q, s);
+    if (q.items == 32 && q.tpr * q.rpb <= (kind == PASS_UPDATE_ROW ? 512 : 320))
+        e = dist_half ? launch_row_k<32, true>(a, kind, q, s) : launch_row_k<32, false>(a, kind, q, s);
     prof_end(h, s);
     return e;
 }
@@ -1285,25 +1302,45 @@ int col_candidates(int H, ColPlan* out, int max_out) {
     return n;
 }
 
-// Horizontal plan: ITEMS positions per thread, one row per tpr threads (a multiple of 32): 8 up
-// to 256 columns, 16 up to 8192 and above 10240, 32 in between (CTAs of at most 320 threads, two
-// per SM, where 16 positions in CTAs of over 512 threads leave one CTA per SM), or a tuned count.
-bool plan_rows(int W, RowPlan* p) {
-    int items;
-    if (W <= 256) items = 8;
-    else if (W <= 8192 || W > 10240) items = 16;
-    else items = 32;
-    if (W > 16 * 1024) return false;
-    const int tuned = tuned_row(W);
-    if ((tuned == 8 || tuned == 16 || tuned == 32) && ((W + tuned - 1) / tuned + 31) / 32 * 32 <= (tuned >= 32 ? 320 : 1024))
-        items = tuned;
+namespace {
+void row_plan_of(int W, int items, RowPlan* p) {
     int tpr = (W + items - 1) / items;
     tpr = (tpr + 31) / 32 * 32;
-    int rpb = 256 / tpr;
+    int rpb = items % 2 ? 1 : 256 / tpr;  // the streaming kernel takes one row per CTA
     if (rpb < 1) rpb = 1;
     p->items = items;
     p->tpr = tpr;
     p->rpb = rpb;
+}
+}  // namespace
+
+// The regular horizontal kernel's plan: ITEMS positions per thread, one row per tpr threads (a
+// multiple of 32): 8 up to 256 columns, 16 up to 8192 and above 10240, 32 in between (CTAs of
+// at most 320 threads, two per SM, where 16 positions in CTAs of over 512 threads leave one CTA
+// per SM).
+bool plan_rows_regular(int W, RowPlan* p) {
+    if (W > 16 * 1024) return false;
+    row_plan_of(W, W <= 256 ? 8 : (W <= 8192 || W > 10240) ? 16 : 32, p);
+    return true;
+}
+
+// Horizontal plan: a tuned segment length first (8, 16, 32: the regular kernel; 17, 33: the
+// streaming kernel); else, for rows of at least 1024 columns, the streaming kernel at 17
+// positions per thread where it takes the row (up to 8704 columns), else at 33 (up to 12672);
+// else the regular plan.  Measured on GB300 (plain pass, then the pass with the update): 2048
+// columns 12.4 -> 11.3 us and 25.4 -> 18.6 us (1536 rows); 2880 columns 17.7 -> 16.0 and 38.6 ->
+// 35.7 us (1988 rows); 10000 columns 316 -> 222 us and 854 -> 623 us (10000 rows).
+bool plan_rows(int W, RowPlan* p) {
+    if (!plan_rows_regular(W, p)) return false;
+    const int tuned = tuned_row(W);
+    if ((tuned == 8 || tuned == 16 || tuned == 32) && ((W + tuned - 1) / tuned + 31) / 32 * 32 <= (tuned >= 32 ? 320 : 1024))
+        row_plan_of(W, tuned, p);
+    else if ((tuned == 17 || tuned == 33) && row_stream_fits(W, tuned, 0))
+        row_plan_of(W, tuned, p);
+    else if (W >= 1024 && row_stream_fits(W, 17, 0))
+        row_plan_of(W, 17, p);
+    else if (W >= 1024 && row_stream_fits(W, 33, 0))
+        row_plan_of(W, 33, p);
     return true;
 }
 

@@ -233,6 +233,8 @@ enum KernelId {
     KID_COL_TALL = 33,
     KID_COL_TALL_TRANSPOSE = 34,
     KID_BATCHED = 35,
+    KID_ROW_STREAM = 36,
+    KID_ROW_STREAM_UPDATE = 37,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16
@@ -279,6 +281,12 @@ cudaError_t launch_copy_plane(const void* src, int src_dtype, long long src_pitc
 cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const RowPlan& p, cudaStream_t s);
 cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s);
 bool plan_rows(int W, RowPlan* p);
+bool plan_rows_regular(int W, RowPlan* p);
+// the streaming horizontal pass (dts_rows.cu): plans with an odd segment length (17 or 33)
+bool row_stream_fits(int W, int items, int dist_half);
+bool row_stream_addressable(const PassArgs& a, int dist_half, bool upd);
+cudaError_t launch_row_stream(const PassArgs& a, int dist_half, int items, bool upd, cudaStream_t s);
+cudaError_t prepare_row_stream_kernels();
 bool row_update_fits(const RowPlan& p);
 bool plan_rows_update(int W, const RowPlan& plain, RowPlan* p);
 // autotuner tables (dts_forward.cu)

@@ -129,6 +129,8 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_COL_TALL: return "col_tall_kernel";
         case KID_COL_TALL_TRANSPOSE: return "col_tall_kernel<transpose>";
         case KID_BATCHED: return "batched_solve_kernel";
+        case KID_ROW_STREAM: return "row_stream_kernel";
+        case KID_ROW_STREAM_UPDATE: return "row_stream_kernel<update>";
         default: return "unknown";
     }
 }

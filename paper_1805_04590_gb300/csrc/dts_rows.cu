@@ -1,0 +1,269 @@
+// Horizontal pass (§2, §3.2: causal then anti-causal recursive filter along each row) for wide
+// rows, persistent and fed by bulk copies.  One CTA of NW warps takes one row at a time (rows
+// blockIdx.x, blockIdx.x + gridDim.x, ...); thread t owns positions [t ITEMS, (t + 1) ITEMS).
+// The row's pass input and distances arrive in shared memory by two 1-D bulk copies (one stage
+// of two, completing on the stage's mbarrier), issued two rows ahead, so the copies of the next
+// rows stream in while a row is scanned.  ITEMS is odd, so the threads' column-wise reads of the
+// stage are free of bank conflicts.  The results go back into the stage (the same conflict-free
+// pattern) and leave it as 16-byte coalesced stores of each warp's span.
+// UPD: the first pass of an iteration also applies the previous iteration's data-term update
+// (Eq. 3 or Eq. 4): the staged row is zbar; each warp reads z_k, t and c of its span with
+// coalesced vector loads, writes z_{k+1} to a.zout and into the stage, and filters z_{k+1}.
+#include "dts_internal.cuh"
+#include "dts_modes.cuh"
+
+namespace dts {
+using namespace scan;
+
+namespace {
+
+// shared memory of a stage: the position row and the distance row of a CTA of nw warps
+__host__ __device__ constexpr size_t stream_x_bytes(int nw, int items) {
+    return ((size_t)nw * 32 * items * 4 + 127) / 128 * 128;
+}
+__host__ __device__ constexpr size_t stream_d_bytes(int nw, int items, int dsize) {
+    return ((size_t)nw * 32 * items * dsize + 127) / 128 * 128;
+}
+__host__ __device__ constexpr size_t stream_stage_bytes(int nw, int items, int dsize) {
+    return stream_x_bytes(nw, items) + stream_d_bytes(nw, items, dsize);
+}
+
+// largest CTA per segment length: two stages within 227 KB of shared memory
+template <int ITEMS>
+constexpr int stream_max_threads() {
+    return ITEMS >= 33 ? 384 : 512;
+}
+
+// Waits on a stage are bounded (timeout cycles).  A wait that gives up records DTS_ERR_TIMEOUT;
+// the CTA finishes the row at hand with what it holds (the results are invalid, the status says
+// so), issues no further copies and leaves the row loop after one more bounded wait for each
+// copy of its own still in flight.  skip (fault injection): CTA 0 leaves out its first row's copies.
+template <int ITEMS, bool DHALF, bool UPD>
+__global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel(PassArgs a, long long timeout,
+                                                                                  int skip) {
+    static_assert(ITEMS % 2 == 1, "odd segment length (bank-conflict-free shared-memory reads)");
+    using DT = typename std::conditional<DHALF, __half, float>::type;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ Aff s_pre[32];
+    __shared__ Aff s_suf[32];
+    __shared__ __align__(8) uint64_t bar[2];
+    // a wait gave up in an iteration of this parity (a slot per parity, so that a failure in the
+    // next iteration cannot change what a slower thread reads for this one)
+    __shared__ int s_abort[2];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int NW = blockDim.x >> 5;
+    const int W = a.W;
+    const long long P = a.pitch;
+    const size_t xb = stream_x_bytes(NW, ITEMS);
+    const size_t stage = xb + stream_d_bytes(NW, ITEMS, (int)sizeof(DT));
+    const uint32_t kx = (uint32_t)W * 4u, kd = (uint32_t)W * (uint32_t)sizeof(DT);
+    const int e0 = tid * ITEMS;
+    const int span0 = warp * 32 * ITEMS;  // this warp's span of the row
+    const int span1 = min(span0 + 32 * ITEMS, W);
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    if (tid < 2) s_abort[tid] = 0;
+    __syncthreads();
+    wait_predecessor();
+    auto issue = [&](int row, int st) {
+        unsigned char* base = dsm + (size_t)st * stage;
+        mbar_arrive_expect_tx(&bar[st], kx + kd);
+        bulk_load_1d(base, a.src + (long long)row * P, kx, &bar[st]);
+        bulk_load_1d(base + xb, static_cast<const DT*>(a.d) + (long long)row * P, kd, &bar[st]);
+    };
+    if (tid == 0) {
+        if ((int)blockIdx.x < a.H && !(skip && blockIdx.x == 0)) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < a.H) issue(blockIdx.x + gridDim.x, 1);
+    }
+    int it = 0;
+    for (int row = blockIdx.x; row < a.H; row += gridDim.x, ++it) {
+        const int st = it & 1;
+        float* sx = reinterpret_cast<float*>(dsm + (size_t)st * stage);
+        const DT* sd = reinterpret_cast<const DT*>(dsm + (size_t)st * stage + xb);
+        if (!mbar_wait_bounded(&bar[st], (uint32_t)((it >> 1) & 1), timeout)) {
+            record_status(a.status, DTS_ERR_TIMEOUT);
+            s_abort[it & 1] = 1;
+        }
+        const long long rb = (long long)row * P;
+        if constexpr (UPD) {
+            // z_{k+1} from z_k, zbar (the stage), t and c, four positions per lane and step;
+            // every operand of a group is loaded before the group's stores (z_{k+1} may alias z_k)
+            const long long tb = (long long)row * W;
+            constexpr int G = 5;  // float4 groups per lane and round
+            for (int e1 = span0 + 4 * lane; e1 < span1; e1 += 4 * 32 * G) {
+                float zk[G][4], tt[G][4], cc[G][4];
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int e = e1 + 128 * g;
+                    if (e < span1) {
+                        load4_f(a.zk, rb + e, zk[g]);
+                        load4_t(a, tb + e, a.tc_vec, tt[g]);
+                        if (a.c_pitched) load4_f(a.c, rb + e, cc[g]);
+                        else if (a.tc_vec) load4_f(a.c, tb + e, cc[g]);
+                        else {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) cc[g][k] = a.c[tb + e + k];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int e = e1 + 128 * g;
+                    if (e < span1) {
+                        const float4 zb = *reinterpret_cast<const float4*>(sx + e);
+                        const float zbv[4] = {zb.x, zb.y, zb.z, zb.w};
+                        float z[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            z[k] = dts_update_value(zk[g][k], zbv[k], tt[g][k], cc[g][k], a.lambda, a.step, a.update,
+                                                    a.clamp_step, a.eps);
+                        store4_f(a.zout, rb + e, z);
+                        *reinterpret_cast<float4*>(sx + e) = make_float4(z[0], z[1], z[2], z[3]);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        float x[ITEMS], w[ITEMS];
+        if (e0 + ITEMS <= W) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                x[j] = sx[e0 + j];
+                w[j] = ex2(a.k2 * to_f32<DT>(sd[e0 + j]));
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const bool ok = e0 + j < W;  // positions past the row end read as 0
+                x[j] = ok ? sx[e0 + j] : 0.f;
+                w[j] = ok ? ex2(a.k2 * to_f32<DT>(sd[e0 + j])) : 0.f;
+            }
+        }
+        if (e0 == 0) w[0] = 0.f;  // the row starts here
+        const float wn = e0 + ITEMS < W ? ex2(a.k2 * to_f32<DT>(sd[e0 + ITEMS])) : 0.f;
+
+        // causal sweep: segment map c -> A c + B, exclusive prefix over the row, replay
+        float A = 1.f, B = 0.f;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            A *= w[j];
+            B = fmaf(w[j], B - x[j], x[j]);
+        }
+        const Aff pc = row_scan_aff<true>(Aff{A, B}, lane, warp, warp, 0, NW, s_pre);
+        float v = pc.B;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            v = fmaf(w[j], v - x[j], x[j]);
+            x[j] = v;
+        }
+        // anti-causal sweep on the result, weights w' (the next position's)
+        A = 1.f;
+        B = 0.f;
+#pragma unroll
+        for (int j = ITEMS - 1; j >= 0; --j) {
+            const float wp = (j + 1 < ITEMS) ? w[j + 1] : wn;
+            A *= wp;
+            B = fmaf(wp, B - x[j], x[j]);
+        }
+        const Aff sk = row_scan_aff<false>(Aff{A, B}, lane, warp, warp, 0, NW, s_suf);
+        if (row + (int)gridDim.x >= a.H) release_successor();
+        v = sk.B;
+#pragma unroll
+        for (int j = ITEMS - 1; j >= 0; --j) {
+            const float wp = (j + 1 < ITEMS) ? w[j + 1] : wn;
+            v = fmaf(wp, v - x[j], x[j]);
+            x[j] = v;
+        }
+        // results into the stage, then out as the warp's coalesced span
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j)
+            if (e0 + j < W) sx[e0 + j] = x[j];
+        __syncwarp();
+        for (int e = span0 + 4 * lane; e < span1; e += 128) {
+            const float4 o = *reinterpret_cast<const float4*>(sx + e);
+            *reinterpret_cast<float4*>(a.dst + rb + e) = o;
+        }
+        // every thread's reads and writes of the stage come before the next copy into it
+        fence_proxy_async_smem();
+        __syncthreads();
+        const bool abort = s_abort[it & 1] != 0;  // CTA-uniform (written before the barrier)
+        const int ahead = row + 2 * (int)gridDim.x;
+        if (tid == 0 && !abort && ahead < a.H) issue(ahead, st);
+        if (abort) {
+            // copies still in flight (the one a wait gave up on, the next row's) must land before
+            // the CTA's shared memory goes to another CTA
+            if (tid == 0) {
+                mbar_wait_bounded(&bar[st], (uint32_t)((it >> 1) & 1), timeout);
+                if (row + (int)gridDim.x < a.H) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1), timeout);
+            }
+            break;
+        }
+    }
+}
+
+template <int ITEMS, bool DHALF, bool UPD>
+cudaError_t allow_stream_t() {
+    return cudaFuncSetAttribute((const void*)row_stream_kernel<ITEMS, DHALF, UPD>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * stream_stage_bytes(stream_max_threads<ITEMS>() / 32, ITEMS, DHALF ? 2 : 4)));
+}
+
+template <int ITEMS, bool DHALF>
+cudaError_t launch_stream_t(const PassArgs& a, bool upd, cudaStream_t s) {
+    const int nw = ((a.W + ITEMS - 1) / ITEMS + 31) / 32;
+    const size_t smem = 2 * stream_stage_bytes(nw, ITEMS, DHALF ? 2 : 4);
+    auto kernel = upd ? row_stream_kernel<ITEMS, DHALF, true> : row_stream_kernel<ITEMS, DHALF, false>;
+    const int per_sm = blocks_per_sm((const void*)kernel, 32 * nw, smem);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int g = std::min(a.H, per_sm * sm_count());
+    // fault injection (tests): CTA 0 leaves out its first row's copies, so its wait runs out
+    const bool skip = take_injected(DTS_INJECT_STAGE_SKIP);
+    return launch_ex_smem(kernel, dim3((unsigned)g), dim3((unsigned)(32 * nw)), 0, smem, s, a,
+                          skip ? kInjectedTimeout : default_timeout_cycles(), skip ? 1 : 0);
+}
+
+}  // namespace
+
+// Whether the streaming kernel takes this pass with ITEMS positions per thread: rows of at
+// least two warps' spans within its largest CTA, and planes the bulk copies and vector stores
+// can address (16-byte aligned rows, row lengths in whole 16-byte units).
+bool row_stream_fits(int W, int items, int dist_half) {
+    if (items != 17 && items != 33) return false;
+    const int nw = ((W + items - 1) / items + 31) / 32;
+    const int max_nw = (items >= 33 ? 384 : 512) / 32;
+    return nw >= 2 && nw <= max_nw && W % (dist_half ? 8 : 4) == 0;
+}
+
+bool row_stream_addressable(const PassArgs& a, int dist_half, bool upd) {
+    auto al16 = [](const void* p) { return (uintptr_t)p % 16 == 0; };
+    if (!al16(a.src) || !al16(a.d) || !al16(a.dst) || a.pitch % (dist_half ? 8 : 4) != 0) return false;
+    if (upd && (!al16(a.zk) || !al16(a.zout))) return false;
+    return true;
+}
+
+cudaError_t launch_row_stream(const PassArgs& a, int dist_half, int items, bool upd, cudaStream_t s) {
+    if (items == 33) return dist_half ? launch_stream_t<33, true>(a, upd, s) : launch_stream_t<33, false>(a, upd, s);
+    if (items == 17) return dist_half ? launch_stream_t<17, true>(a, upd, s) : launch_stream_t<17, false>(a, upd, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t prepare_row_stream_kernels() {
+    cudaError_t e = cudaSuccess, r;
+    if ((r = allow_stream_t<17, false, false>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<17, false, true>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<17, true, false>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<17, true, true>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<33, false, false>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<33, false, true>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<33, true, false>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<33, true, true>()) != cudaSuccess) e = r;
+    return e;
+}
+
+}  // namespace dts

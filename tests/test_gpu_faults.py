@@ -1,6 +1,6 @@
 """Failure detection without a GPU fault.  A host-requested, one-shot injection makes one bounded
 device-side wait of the hot path run out (about a millisecond under injection): the strip kernel's
-wait for a slab load that was left out, the chained vertical pass's wait for a strip composition
+wait for a slab load that was left out, the streaming row kernel's wait for a row copy that was left out, the chained vertical pass's wait for a strip composition
 that never comes (one chunk does not count its arrival), the resident solve's grid barrier
 (one CTA leaves out its arrival), and the persistent batched solve's wait for an image's previous
 stage (one job does not count itself done).  Each time the kernel records DTS_ERR_TIMEOUT in the device
@@ -15,7 +15,7 @@ from paper_1805_04590_gb300 import dts, workloads
 
 pytestmark = pytest.mark.gpu
 
-INJECT_TMA_SKIP, INJECT_CHAIN_SKIP, INJECT_BARRIER_SKIP, INJECT_QUEUE_SKIP = 1, 2, 3, 4
+INJECT_TMA_SKIP, INJECT_CHAIN_SKIP, INJECT_BARRIER_SKIP, INJECT_QUEUE_SKIP, INJECT_STAGE_SKIP = 1, 2, 3, 4, 5
 TIMEOUT = 5
 
 
@@ -42,11 +42,13 @@ def check_filter(prob, out, prm):
 
 
 # 100 x 200: the strip kernel covers the 25 strips in one round; 3000 x 70: the tall-column
-# clusters cover the 3 strips in one round; 12000 x 70: chains of 94 chunks
+# clusters cover the 3 strips in one round; 12000 x 70: chains of 94 chunks; 20 x 9000: the
+# streaming row kernel (CTA 0's first row)
 @pytest.mark.parametrize("H,W,kind,kernel", [(100, 200, INJECT_TMA_SKIP, "col_strip_kernel"),
                                              (3000, 70, INJECT_TMA_SKIP, "col_tall_kernel"),
-                                             (12000, 70, INJECT_CHAIN_SKIP, "col_chain_kernel")])
-def test_vertical_pass_wait_reports_timeout_and_recovers(H, W, kind, kernel):
+                                             (12000, 70, INJECT_CHAIN_SKIP, "col_chain_kernel"),
+                                             (20, 9000, INJECT_STAGE_SKIP, "row_stream_kernel")])
+def test_pass_wait_reports_timeout_and_recovers(H, W, kind, kernel):
     d = dev()
     lib = dts.load()
     prob = workloads.random_problem(H, W, C=3, seed=3)

@@ -332,6 +332,101 @@ def test_solve_multispectral_full_size_slices(H, W, sdt):
                                    f"(rounding alone: {moved:.3e})"
 
 
+# ---------------------------------------------------------------- streaming horizontal passes
+# Rows of 1024 columns or more run on the streaming row kernel (row_stream_kernel: persistent CTAs,
+# one row at a time, each row's input and distances copied into shared memory two rows ahead) when
+# it takes them: a row length in whole 16-byte units (8 positions with FP16 distances) and two to
+# sixteen warps' spans at 17 positions per thread (up to 8704 columns), else two to twelve at 33
+# (up to 12672); other segment lengths and narrower rows as tuned plans, set here for row lengths
+# no other test uses.  700 x 10000: four or five rows per CTA (both stages reused, both barrier
+# parities); 12672: the widest row at 33; 12676 and 1101: not taken (the regular kernel runs);
+# 1092 at 33: two warps, a ragged last segment; 8200 at 17: 16 warps; 1100 at 17: three warps.
+STREAM_SHAPES = [(700, 10000, None), (3, 9000, None), (2, 12672, None), (2, 12676, None), (1500, 1100, 17),
+                 (9, 1092, 33), (40, 2884, 33), (6, 1101, 33), (3, 8200, 17)]
+
+
+def stream_fits(W, items, dist_half=False):
+    nw = -(-(-(-W // items)) // 32)
+    return W % (8 if dist_half else 4) == 0 and 2 <= nw <= (12 if items == 33 else 16)
+
+
+def stream_taken(W, items=None):
+    """Whether the plan for W (a tuned segment length, or the default) runs the streaming kernel
+    with FP32 distances."""
+    if items is not None and stream_fits(W, items):
+        return True
+    return W >= 1024 and (stream_fits(W, 17) or stream_fits(W, 33))
+
+
+def kernels_of(fn):
+    dts.dts_profile(1)
+    try:
+        fn()
+        torch.cuda.synchronize()
+        return {r[0] for r in dts.dts_profile_read()}
+    finally:
+        dts.dts_profile(0)
+
+
+@pytest.mark.parametrize("H,W,items", STREAM_SHAPES)
+def test_filter_streaming_rows(H, W, items):
+    if items is not None:
+        dts.autotune_import("row %d %d\n" % (W, items))
+    prob = workloads.random_problem(H, W, C=3, seed=H + 5 * W)
+    prm = dts.Params(sigma_s=40.0, sigma_r=0.3, passes=3)
+    g, src = to_dev(prob.guide), to_dev(prob.target)
+    out = {}
+    names = kernels_of(lambda: out.setdefault("z", dts.dts_filter(g, src, prm)))
+    assert dts.dts_last_status() == 0
+    assert ("row_stream_kernel" in names) == stream_taken(W, items), names
+    ref = oracle.filter(prob.guide, prob.target, 40.0, 0.3, passes=3)
+    assert_close(out["z"].cpu().numpy(), ref, prob.target, f"filter {H}x{W} items {items}")
+
+
+# the data-term update in the streaming pass: Eq. 3, Eq. 4, the Charbonnier loss (both readings),
+# BF16 target storage, the support-weighted confidence (its chat plane), a caller's z_init; FP16
+# distances at 8200 (taken) and 8196 (a row of 16-byte units of FP32 but not of FP16: the regular
+# kernel runs)
+@pytest.mark.parametrize("variant", ["gd", "jacobi", "charbonnier_gd", "charbonnier_jacobi", "bf16", "support",
+                                     "zinit", "f16_8200", "f16_8196"])
+def test_solve_streaming_rows(variant):
+    H, W = (24, 8196) if variant == "f16_8196" else (24, 8200)
+    prob = workloads.random_problem(H, W, C=3, seed=31 + len(variant))
+    prm = dts.Params(lam=0.99, sigma_s=24.0, sigma_r=0.2, iterations=4)
+    sdt, kw, z_init = torch.float32, {}, None
+    if variant == "jacobi":
+        prm.update = dts.UPDATE_JACOBI
+    elif variant == "charbonnier_gd":
+        prm.charbonnier_eps = 1.0
+    elif variant == "charbonnier_jacobi":
+        prm.update, prm.charbonnier_eps = dts.UPDATE_JACOBI, 1e-3
+    elif variant == "bf16":
+        sdt = torch.bfloat16
+    elif variant == "support":
+        prm.conf_mode = dts.CONF_SUPPORT
+    elif variant == "zinit":
+        z_init = np.random.default_rng(5).random(prob.target.shape).astype(np.float32)
+        kw["z_init"] = z_init.astype(np.float64)
+    elif variant.startswith("f16"):
+        prm.dist_dtype = dts.F16
+    g, t = to_dev(prob.guide, sdt), to_dev(prob.target, sdt)
+    out = {}
+    names = kernels_of(lambda: out.setdefault("z", dts.dts_solve(
+        g, t, to_dev(prob.conf), prm, z_init=None if z_init is None else to_dev(z_init))))
+    assert dts.dts_last_status() == 0
+    assert ("row_stream_kernel<update>" in names) == (variant != "f16_8196"), names
+    z = out["z"].cpu().numpy()
+    if variant.startswith("f16"):
+        dX, dY = oracle.distances(prob.guide, 24.0, 0.2)
+        ref = oracle.solve_d(dX.astype(np.float16).astype(np.float64), dY.astype(np.float16).astype(np.float64),
+                             prob.target, prob.conf, lam=0.99, sigma_s=24.0, iterations=4)
+    elif variant.startswith("charbonnier"):
+        ref = oracle_solve(prob.guide, prob.target, prob.conf, prm, charbonnier_eps=prm.charbonnier_eps)
+    else:
+        ref = oracle_solve(rounded(g), rounded(t), prob.conf, prm, **kw)
+    assert_close(z, ref, rounded(t), f"streaming rows, {variant}")
+
+
 # ---------------------------------------------------------------- tall-column vertical passes
 # Columns over 2176 rows run on persistent TMA-fed clusters (col_tall_kernel: 16 warps of 16, 32 or
 # 40 rows per CTA, clusters of up to 16 CTAs: up to 10240 rows), taller ones on chains of CTAs
