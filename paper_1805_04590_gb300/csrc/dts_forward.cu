@@ -479,21 +479,40 @@ __global__ void __launch_bounds__(32 * kTallWarps, tall_min_blocks<ITEMS>())
         s_failed = 0;
     }
     __syncthreads();
-    wait_predecessor();
+    auto issue_d = [&](int strip) {
+#pragma unroll
+        for (int b = 0; b < kBoxes; ++b)
+            tma_load_2d((void*)(sd + (size_t)b * kTallBox * 32), &tm_d, strip * 32, tile_row + b * kTallBox, &bar);
+    };
+    auto issue_x = [&](int strip) {
+#pragma unroll
+        for (int b = 0; b < kBoxes; ++b)
+            tma_load_2d(sx + (size_t)b * kTallBox * 32, &tm_x, strip * 32, tile_row + b * kTallBox, &bar);
+    };
     auto issue = [&](int strip) {
         mbar_arrive_expect_tx(&bar, kTx);
-#pragma unroll
-        for (int b = 0; b < kBoxes; ++b) {
-            tma_load_2d(sx + (size_t)b * kTallBox * 32, &tm_x, strip * 32, tile_row + b * kTallBox, &bar);
-            tma_load_2d((void*)(sd + (size_t)b * kTallBox * 32), &tm_d, strip * 32, tile_row + b * kTallBox, &bar);
-        }
+        issue_x(strip);
+        issue_d(strip);
     };
-    if (threadIdx.x == 0 && (int)blockIdx.x < nstrips && !(skip && blockIdx.x == 0 && rank == 0)) issue(blockIdx.x);
+    // the first tile's distances before the wait for the previous kernel (they were written at
+    // the start of the solve, before the horizontal pass that precedes every vertical pass), its
+    // positions after it
+    const bool first = threadIdx.x == 0 && (int)blockIdx.x < nstrips && !(skip && blockIdx.x == 0 && rank == 0);
+    if (first) {
+        mbar_arrive_expect_tx(&bar, kTx);
+        issue_d(blockIdx.x);
+    }
+    wait_predecessor();
+    if (first) issue_x(blockIdx.x);
     int it = 0;
     for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x, ++it) {
         const int next = strip + gridDim.x;
         const int col = strip * 32 + lane;
         const bool col_ok = col < a.W;
+        // the distance entering the next tile: a plain load, in flight while the stage lands
+        const int rn = row0 + ITEMS;
+        float dnext = 0.f;
+        if (warp + 1 == kTallWarps && col_ok && rn < a.H) dnext = load1_d<DHALF>(a.d, (long long)rn * P + col);
         if (!s_failed && !mbar_wait_bounded(&bar, (uint32_t)(it & 1), timeout)) {
             record_status(a.status, DTS_ERR_TIMEOUT);
             s_failed = 1 + (it & 1);
@@ -504,13 +523,11 @@ __global__ void __launch_bounds__(32 * kTallWarps, tall_min_blocks<ITEMS>())
             x[j] = sx[(warp * ITEMS + j) * 32 + lane];
             w[j] = to_f32<DT>(sd[(warp * ITEMS + j) * 32 + lane]);
         }
-        float dnext = warp + 1 < kTallWarps ? to_f32<DT>(sd[((warp + 1) * ITEMS) * 32 + lane]) : 0.f;
+        if (warp + 1 < kTallWarps) dnext = to_f32<DT>(sd[((warp + 1) * ITEMS) * 32 + lane]);
         // the reads above come before the next strip's TMA writes into the stage
         fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0 && next < nstrips && !s_failed) issue(next);
-        const int rn = row0 + ITEMS;
-        if (warp + 1 == kTallWarps && col_ok && rn < a.H) dnext = load1_d<DHALF>(a.d, (long long)rn * P + col);
         const float wn = (col_ok && rn < a.H) ? ex2(a.k2 * dnext) : 0.f;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
@@ -613,21 +630,33 @@ __global__ void __launch_bounds__(32 * kStripWarps) col_strip_tma_kernel(const _
     }
     if (threadIdx.x < 2) s_abort[threadIdx.x] = 0;
     __syncthreads();
-    wait_predecessor();
     // the slab's distances: one contiguous bulk copy from the strip-tiled plane when there is one,
     // else a TMA box (full boxes count, the parts outside the plane included: they read as zero)
     constexpr uint32_t kDBytes = (4 * ITEMS + 1) * kStripCols * (int)sizeof(DT);
     const DT* dtile = static_cast<const DT*>(a.d_tiled);
-    auto load_slab = [&](int strip) {
-        mbar_arrive_expect_tx(&bar[warp], kTx);
-        tma_load_2d(sx, &tm_x, strip * kStripCols, slab_row, &bar[warp]);
+    auto load_d = [&](int strip) {
         if (dtile)
             bulk_load_1d((void*)sd, dtile + ((long long)strip * a.d_tiled_rows + slab_row) * kStripCols, kDBytes,
                          &bar[warp]);
         else
             tma_load_2d((void*)sd, &tm_d, strip * kStripCols, slab_row, &bar[warp]);
     };
-    if (lane == 0 && (int)blockIdx.x < nstrips && !(skip && blockIdx.x == 0 && warp == 0)) load_slab(blockIdx.x);
+    auto load_slab = [&](int strip) {
+        mbar_arrive_expect_tx(&bar[warp], kTx);
+        tma_load_2d(sx, &tm_x, strip * kStripCols, slab_row, &bar[warp]);
+        load_d(strip);
+    };
+    // The distances were written at the start of the solve, before the horizontal pass that
+    // precedes every vertical pass (that pass waited for them before it let this launch start):
+    // the first slab's distances are copied before the wait for the previous kernel, its
+    // positions after it.
+    const bool first = lane == 0 && (int)blockIdx.x < nstrips && !(skip && blockIdx.x == 0 && warp == 0);
+    if (first) {
+        mbar_arrive_expect_tx(&bar[warp], kTx);
+        load_d(blockIdx.x);
+    }
+    wait_predecessor();
+    if (first) tma_load_2d(sx, &tm_x, blockIdx.x * kStripCols, slab_row, &bar[warp]);
     int it = 0;
     for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x, ++it) {
         const int next = strip + gridDim.x;
