@@ -133,8 +133,9 @@ def parse_args():
                          "iterations (GD, Jacobi, CG), time against sigma_s / sigma_r, time against megapixels")
     ap.add_argument("--filter-kernel", choices=["rf", "box"], default="rf",
                     help="recursive-filter kernel, or the box kernel Eq. 10 prints")
-    ap.add_argument("--batch-policy", choices=["persistent", "graph"], default="persistent",
-                    help="batched workload: the persistent kernel, or the graph of per-image launch sequences")
+    ap.add_argument("--batch-policy", choices=["auto", "persistent", "graph"], default="auto",
+                    help="batched workload: the persistent kernel, the graph of per-image launch sequences, "
+                         "or (auto) whichever dts_autotune_batched measures faster before the warm-up")
     ap.add_argument("--charbonnier-eps", type=float, default=0.0,
                     help="> 0: Charbonnier loss on the target term (the paper's stereo loss uses 0.001)")
     return ap.parse_args()
@@ -657,6 +658,9 @@ def run_ours(args, rank, world, local_rank):
     from paper_1805_04590_gb300 import dts as _dts
     _dts.autotune_import("batch %d\n" % (1 if args.batch_policy == "graph" else 0))
     case = Case(args, dev, inp, dirs[0])
+    batch_policy = args.batch_policy
+    if case.name == "batched" and batch_policy == "auto":
+        batch_policy = _dts.dts_autotune_batched(case.g, case.t, case.c, case.prm, outs=case.out, ws=case.ws[0])
     main = measure(args, case, world, local_rank, flush)
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
@@ -666,6 +670,8 @@ def run_ours(args, rank, world, local_rank):
             "wall_s_timed_region": main["wall_s_timed_region"],
             "kernel_timing": f"CUDA events around each kernel on every {PROFILE_EVERY}th timed step"}
     if case.name == "batched":
+        line["config"]["batch_policy"] = (batch_policy + " (measured faster by dts_autotune_batched)"
+                                          if args.batch_policy == "auto" else batch_policy)
         line["gpu_launches_note"] = "one CUDA graph launch per step; its kernels are not bracketed by events"
 
     # the oracle's box filter tests every sample of a line for every position (quadratic in the

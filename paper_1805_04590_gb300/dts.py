@@ -347,6 +347,18 @@ def dts_solve_batched(guides, targets, confs, params: Params, outs=None, ws: Opt
     return outs
 
 
+def dts_autotune_batched(guides, targets, confs, params: Params, outs=None, ws: Optional[torch.Tensor] = None,
+                         stream=None) -> str:
+    """Times the batch's two ways of running (the persistent kernel, the graph of per-image launch
+    sequences) and keeps the faster for batches of this composition; returns "persistent" or
+    "graph"."""
+    n, garr, tarr, tdt, carr, outs, oarr, ws = _batch_args(guides, targets, confs, params, outs, ws)
+    p = params.c()
+    _check(load().dts_autotune_batched(n, garr, tarr, tdt, carr, ctypes.byref(p), oarr, ws.data_ptr(), ws.numel(),
+                                       _stream(stream)), "dts_autotune_batched")
+    return "graph" if "batch 1" in autotune_export() else "persistent"
+
+
 def dts_solve_noalloc(guide: torch.Tensor, target: torch.Tensor, conf: torch.Tensor, params: Params,
                       z_init: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
                       stream=None) -> torch.Tensor:
