@@ -28,17 +28,44 @@ __host__ __device__ constexpr size_t stream_stage_bytes(int nw, int items, int d
     return stream_x_bytes(nw, items) + stream_d_bytes(nw, items, dsize);
 }
 
+// Four consecutive target values from element i (i a multiple of 4, rows of 16-byte or 8-byte
+// aligned vectors), storage TT fixed at compile time so that a group's loads issue together and
+// their widening waits for the update: one 16-byte load for FP32, one 8-byte load for 16-bit
+// storage (a BF16 value is the upper half of the FP32 one).
+template <int TT>
+__device__ __forceinline__ void load4_target(const void* t, long long i, float (&out)[4]) {
+    if constexpr (TT == DTS_F32) {
+        load4_f(static_cast<const float*>(t), i, out);
+    } else {
+        const uint2 v = *reinterpret_cast<const uint2*>(static_cast<const unsigned short*>(t) + i);
+        if constexpr (TT == DTS_BF16) {
+            out[0] = __uint_as_float(v.x << 16);
+            out[1] = __uint_as_float(v.x & 0xffff0000u);
+            out[2] = __uint_as_float(v.y << 16);
+            out[3] = __uint_as_float(v.y & 0xffff0000u);
+        } else {
+            const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+            const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+            out[0] = f0.x;
+            out[1] = f0.y;
+            out[2] = f1.x;
+            out[3] = f1.y;
+        }
+    }
+}
+
 // largest CTA per segment length: two stages within 227 KB of shared memory
 template <int ITEMS>
 constexpr int stream_max_threads() {
     return ITEMS >= 33 ? 384 : 512;
 }
 
-// Waits on a stage are bounded (timeout cycles).  A wait that gives up records DTS_ERR_TIMEOUT;
+// UPD > 0: the pass with the update, for a target stored as dtype UPD - 1 (DTS_F32, DTS_BF16,
+// DTS_F16).  Waits on a stage are bounded (timeout cycles).  A wait that gives up records DTS_ERR_TIMEOUT;
 // the CTA finishes the row at hand with what it holds (the results are invalid, the status says
 // so), issues no further copies and leaves the row loop after one more bounded wait for each
 // copy of its own still in flight.  skip (fault injection): CTA 0 leaves out its first row's copies.
-template <int ITEMS, bool DHALF, bool UPD>
+template <int ITEMS, bool DHALF, int UPD>
 __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel(PassArgs a, long long timeout,
                                                                                   int skip) {
     static_assert(ITEMS % 2 == 1, "odd segment length (bank-conflict-free shared-memory reads)");
@@ -91,7 +118,7 @@ __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel
             s_abort[it & 1] = 1;
         }
         const long long rb = (long long)row * P;
-        if constexpr (UPD) {
+        if constexpr (UPD > 0) {
             // z_{k+1} from z_k, zbar (the stage), t and c, four positions per lane and step;
             // every operand of a group is loaded before the group's stores (z_{k+1} may alias z_k)
             const long long tb = (long long)row * W;
@@ -103,7 +130,11 @@ __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel
                     const int e = e1 + 128 * g;
                     if (e < span1) {
                         load4_f(a.zk, rb + e, zk[g]);
-                        load4_t(a, tb + e, a.tc_vec, tt[g]);
+                        if (a.tc_vec) load4_target<UPD - 1>(a.t, tb + e, tt[g]);
+                        else {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) tt[g][k] = load_any(a.t, tb + e + k, a.t_dtype);
+                        }
                         if (a.c_pitched) load4_f(a.c, rb + e, cc[g]);
                         else if (a.tc_vec) load4_f(a.c, tb + e, cc[g]);
                         else {
@@ -207,7 +238,7 @@ __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel
     }
 }
 
-template <int ITEMS, bool DHALF, bool UPD>
+template <int ITEMS, bool DHALF, int UPD>
 cudaError_t allow_stream_t() {
     return cudaFuncSetAttribute((const void*)row_stream_kernel<ITEMS, DHALF, UPD>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -215,10 +246,23 @@ cudaError_t allow_stream_t() {
 }
 
 template <int ITEMS, bool DHALF>
+cudaError_t allow_stream_k() {
+    cudaError_t e = cudaSuccess, r;
+    if ((r = allow_stream_t<ITEMS, DHALF, 0>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<ITEMS, DHALF, 1 + DTS_F32>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<ITEMS, DHALF, 1 + DTS_BF16>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<ITEMS, DHALF, 1 + DTS_F16>()) != cudaSuccess) e = r;
+    return e;
+}
+
+template <int ITEMS, bool DHALF>
 cudaError_t launch_stream_t(const PassArgs& a, bool upd, cudaStream_t s) {
     const int nw = ((a.W + ITEMS - 1) / ITEMS + 31) / 32;
     const size_t smem = 2 * stream_stage_bytes(nw, ITEMS, DHALF ? 2 : 4);
-    auto kernel = upd ? row_stream_kernel<ITEMS, DHALF, true> : row_stream_kernel<ITEMS, DHALF, false>;
+    auto kernel = !upd ? row_stream_kernel<ITEMS, DHALF, 0>
+                  : a.t_dtype == DTS_BF16 ? row_stream_kernel<ITEMS, DHALF, 1 + DTS_BF16>
+                  : a.t_dtype == DTS_F16 ? row_stream_kernel<ITEMS, DHALF, 1 + DTS_F16>
+                                          : row_stream_kernel<ITEMS, DHALF, 1 + DTS_F32>;
     const int per_sm = blocks_per_sm((const void*)kernel, 32 * nw, smem);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int g = std::min(a.H, per_sm * sm_count());
@@ -255,14 +299,10 @@ cudaError_t launch_row_stream(const PassArgs& a, int dist_half, int items, bool 
 
 cudaError_t prepare_row_stream_kernels() {
     cudaError_t e = cudaSuccess, r;
-    if ((r = allow_stream_t<17, false, false>()) != cudaSuccess) e = r;
-    if ((r = allow_stream_t<17, false, true>()) != cudaSuccess) e = r;
-    if ((r = allow_stream_t<17, true, false>()) != cudaSuccess) e = r;
-    if ((r = allow_stream_t<17, true, true>()) != cudaSuccess) e = r;
-    if ((r = allow_stream_t<33, false, false>()) != cudaSuccess) e = r;
-    if ((r = allow_stream_t<33, false, true>()) != cudaSuccess) e = r;
-    if ((r = allow_stream_t<33, true, false>()) != cudaSuccess) e = r;
-    if ((r = allow_stream_t<33, true, true>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_k<17, false>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_k<17, true>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_k<33, false>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_k<33, true>()) != cudaSuccess) e = r;
     return e;
 }
 
