@@ -136,6 +136,9 @@ def parse_args():
     ap.add_argument("--batch-policy", choices=["auto", "persistent", "graph"], default="auto",
                     help="batched workload: the persistent kernel, the graph of per-image launch sequences, "
                          "or (auto) whichever dts_autotune_batched measures faster before the warm-up")
+    ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), default=None,
+                    help="run one small case of a kernel's launch plan (for a profiler capture) and print the "
+                         "per-kernel event times instead of the bench line")
     ap.add_argument("--charbonnier-eps", type=float, default=0.0,
                     help="> 0: Charbonnier loss on the target term (the paper's stereo loss uses 0.001)")
     return ap.parse_args()
@@ -853,8 +856,73 @@ def run_sweep(args):
     return lines
 
 
+# Small cases of the large workloads' launch plans, for profiler captures of a few launches on a
+# GPU holding about a gigabyte: (H, W, channels, what runs).  tall: the 10000-row vertical plan;
+# row / rowupd: the 10000-column horizontal plan (plain passes; a 2-iteration solve whose fourth
+# horizontal launch is the first update pass); bwd: a solve and its reverse mode with every pass
+# input kept (the 10000-row adjoint plan); stereo: 2 iterations of the stereo-shaped solve;
+# batched: the first 8 images of the batched workload in one persistent launch.
+NCU_CASES = {"tall": (10000, 2048, 3, "filter"), "row": (2048, 10000, 3, "filter"),
+             "rowupd": (2048, 10000, 3, "solve"), "bwd": (10000, 1024, 3, "backward"),
+             "stereo": (1988, 2880, 3, "solve"), "batched": (0, 0, 3, "batched")}
+
+
+def run_ncu_case(args):
+    import torch
+    from paper_1805_04590_gb300 import dts, workloads
+    H, W, C, what = NCU_CASES[args.ncu_case]
+    dev = torch.device("cuda:0")
+    if what == "batched":
+        wl = workloads.make(3)
+        q = wl.params
+        probs = wl.problems[:8]
+        g = [torch.from_numpy(p.guide).to(dev) for p in probs]
+        t = [torch.from_numpy(p.target).to(dev) for p in probs]
+        c = [torch.from_numpy(p.conf).to(dev) for p in probs]
+        prm = dts.Params(lam=q.lam, sigma_s=q.sigma_s, sigma_r=q.sigma_r, iterations=q.iterations, passes=q.passes)
+        ws = dts.batched_workspace(g, prm)
+        dts.autotune_import("batch 0\n")
+        run = lambda: dts.dts_solve_batched(g, t, c, prm, ws=ws)
+    else:
+        gen = torch.Generator(device=dev).manual_seed(0)
+        g = torch.rand(C, H, W, device=dev, generator=gen)
+        t = torch.rand(H, W, device=dev, generator=gen)
+        c = torch.rand(H, W, device=dev, generator=gen) * 0.9 + 0.1
+        prm = dts.Params(lam=0.99, sigma_s=32.0, sigma_r=0.1, passes=3, iterations=2,
+                         save_checkpoints=2 if what == "backward" else 0)
+        ws = dts.workspace(g, prm, with_backward=what == "backward")
+        gz = torch.randn(H, W, device=dev, generator=gen)
+        if what == "filter":
+            run = lambda: dts.dts_filter(g, t, prm, ws=ws)
+        elif what == "solve":
+            run = lambda: dts.dts_solve(g, t, c, prm, ws=ws)
+        else:
+            run = lambda: (dts.dts_solve(g, t, c, prm, ws=ws), dts.dts_solve_backward(g, t, c, prm, ws, gz))
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    dts.dts_profile(1)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    recs = dts.dts_profile_read()
+    dts.dts_profile(0)
+    status = dts.dts_last_status()
+    agg = {}
+    for name, _, px, fl, ms in recs:
+        a = agg.setdefault(name, [0, 0.0])
+        a[0] += 1
+        a[1] += ms
+    return {"ncu_case": args.ncu_case, "status": status,
+            "kernels_us": {n: round(ms / k * 1e3, 2) for n, (k, ms) in sorted(agg.items(), key=lambda kv: -kv[1][1])}}
+
+
 def main():
     args = parse_args()
+    if args.ncu_case:
+        line = run_ncu_case(args)
+        print(json.dumps(line), flush=True)
+        return 0 if line["status"] == 0 else 1
     if args.sweep:
         for line in run_sweep(args):
             print(json.dumps(line), flush=True)
