@@ -583,50 +583,40 @@ def e2e_of(args, case, world, flush):
     gzh = [x.cpu().pin_memory() for x in case.gz] if case.bwd else []
     n_e2e = max(1, min(args.e2e_steps, args.steps))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the binding's host pipeline overlaps each step's copies with the neighbouring steps' work
+    # (every step still copies its inputs in and its results out)
     if case.bwd:
-        gd = [torch.empty_like(x) for x in case.g]
-        td = [torch.empty_like(x) for x in case.t]
-        cd = [torch.empty_like(x) for x in case.c]
-        gradh = None
+        n = len(case.g)
+        gth = [torch.empty(x.shape, dtype=torch.float32).pin_memory() for x in case.out]
+        gch = [torch.empty(x.shape, dtype=torch.float32).pin_memory() for x in case.out]
+        ggh = [torch.empty(tuple(x.shape), dtype=torch.float32).pin_memory() for x in case.g]
 
-        def e2e_step():
-            nonlocal gradh
-            for dst, src in zip(gd + td + cd + case.gz, gh + th + ch + gzh):
-                dst.copy_(src, non_blocking=True)
+        def solve_flushed(din, dout):
             flush.zero_()
-            case.step(gd, td, cd)
-            for dst, src in zip(zh, case.out):
-                dst.copy_(src, non_blocking=True)
-            grads = [x for gr in case.grads for x in gr if x is not None]
-            if gradh is None:
-                gradh = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in grads]
-            for dst, src in zip(gradh, grads):
-                dst.copy_(src, non_blocking=True)
+            g, t, c, gz = din[:n], din[n:2 * n], din[2 * n:3 * n], din[3 * n:]
+            for i in range(n):
+                dts.dts_solve(g[i], t[i], c[i], case.prm, out=dout[i], ws=case.ws[0])
+                dts.dts_solve_backward(g[i], t[i], c[i], case.prm, case.ws[0], gz[i],
+                                       outs=(dout[n + i], dout[2 * n + i], dout[3 * n + i], None))
 
-        for _ in range(2):
-            e2e_step()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(n_e2e):
-            e2e_step()
-        e1.record(stream)
-        copies = "serial with the solve, asynchronous on its stream (pinned host buffers)"
+        hin, hout = gh + th + ch + gzh, zh + gth + gch + ggh
+        copies = ("dts.HostPipeline: step i+1's host-to-device and step i-1's device-to-host copies (inputs, "
+                  "incoming gradient; result and the target, confidence and guide gradients) overlap step i's "
+                  "solve and backward")
     else:
-        # the binding's host pipeline overlaps each step's copies with the neighbouring steps'
-        # solves (every step still copies its inputs in and its result out)
         def solve_flushed(din, dout):
             flush.zero_()
             case.solve_into(din, dout)
 
-        pipe = dts.HostPipeline(solve_flushed)
         hin, hout = gh + th + ch, zh
-        pipe.run([hin] * 2, [hout] * 2)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        pipe.run([hin] * n_e2e, [hout] * n_e2e, start_event=e0)
-        e1.record(stream)
         copies = ("dts.HostPipeline: step i+1's host-to-device and step i-1's device-to-host copies overlap "
                   "step i's solve")
+    pipe = dts.HostPipeline(solve_flushed)
+    pipe.run([hin] * 2, [hout] * 2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    pipe.run([hin] * n_e2e, [hout] * n_e2e, start_event=e0)
+    e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     if world > 1:

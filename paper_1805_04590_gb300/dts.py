@@ -379,18 +379,30 @@ def dts_solve_noalloc(guide: torch.Tensor, target: torch.Tensor, conf: torch.Ten
 
 def dts_solve_backward(guide: torch.Tensor, target: torch.Tensor, conf: torch.Tensor, params: Params,
                        ws: torch.Tensor, grad_z: torch.Tensor, z_init: Optional[torch.Tensor] = None,
-                       need_guide: bool = True, stream=None):
-    """Gradients (target, conf, guide or None, z_init or None) given dL/dz_K.
+                       need_guide: bool = True, stream=None, outs=None):
+    """Gradients (target, conf, guide or None, z_init or None) given dL/dz_K, into new tensors or
+    into ``outs`` = (target, conf, guide, z_init) gradient tensors (float32, dense; guide and
+    z_init entries may be None when not wanted).
 
     Must follow ``dts_solve`` with ``save_checkpoints`` 1 or 2 on the same workspace."""
     _need_cuda(guide, target, conf, grad_z, z_init)
     _dense(grad_z, "grad_z")
     g = guide_desc(guide)
     dev = target.device
-    gt = torch.empty(target.shape, dtype=torch.float32, device=dev)
-    gc = torch.empty(target.shape, dtype=torch.float32, device=dev)
-    gg = torch.empty((g.C, g.H, g.W), dtype=torch.float32, device=dev) if need_guide else None
-    gz0 = torch.empty(target.shape, dtype=torch.float32, device=dev) if z_init is not None else None
+    if outs is not None:
+        gt, gc, gg, gz0 = outs
+        for x, name in ((gt, "target gradient"), (gc, "confidence gradient"), (gg, "guide gradient"),
+                        (gz0, "z_init gradient")):
+            if x is not None:
+                _need_cuda(x)
+                _dense(x, name)
+        if z_init is None:
+            gz0 = None
+    else:
+        gt = torch.empty(target.shape, dtype=torch.float32, device=dev)
+        gc = torch.empty(target.shape, dtype=torch.float32, device=dev)
+        gg = torch.empty((g.C, g.H, g.W), dtype=torch.float32, device=dev) if need_guide else None
+        gz0 = torch.empty(target.shape, dtype=torch.float32, device=dev) if z_init is not None else None
     p = params.c()
     _check(load().dts_solve_backward(ctypes.byref(g), target.data_ptr(), _TORCH_DTYPE[target.dtype],
                                      conf.data_ptr(), _ptr(z_init), ctypes.byref(p), ws.data_ptr(), ws.numel(),

@@ -322,3 +322,26 @@ def test_backward_chain_shapes(H, items, warps):
     dts.autotune_import("bcol %d %d %d -1\n" % (H, items, warps))
     assert ("bcol %d %d %d -1" % (H, items, warps)) in dts.autotune_export()
     run_case(H, 40, K=2, update=dts.UPDATE_GD, seed=H, keep=2)
+
+
+def test_backward_into_caller_tensors():
+    """dts_solve_backward writing into the caller's gradient tensors gives the same bits as into
+    tensors it allocates (what a pipelined caller reuses step after step); the guide gradient
+    can be left out."""
+    rng = np.random.default_rng(61)
+    H, W = 97, 130
+    g = T(guide_noisy(H, W, 3, 61))
+    t, c = T(rng.random((H, W))), T(rng.uniform(0.1, 1.0, (H, W)))
+    gz = T(rng.standard_normal((H, W)))
+    prm = dts.Params(lam=0.9, sigma_s=8.0, sigma_r=0.3, iterations=3, save_checkpoints=2)
+    ws = dts.workspace(g, prm, with_backward=True)
+    dts.dts_solve(g, t, c, prm, ws=ws)
+    gt, gc, gg, _ = dts.dts_solve_backward(g, t, c, prm, ws, gz)
+    outs = (torch.full_like(t, 7.0), torch.full_like(t, 7.0), torch.full_like(g, 7.0), None)
+    r = dts.dts_solve_backward(g, t, c, prm, ws, gz, outs=outs)
+    assert dts.dts_last_status() == 0
+    assert r[0] is outs[0] and r[1] is outs[1] and r[2] is outs[2]
+    assert torch.equal(outs[0], gt) and torch.equal(outs[1], gc) and torch.equal(outs[2], gg)
+    o2 = (torch.full_like(t, 7.0), torch.full_like(t, 7.0), None, None)
+    dts.dts_solve_backward(g, t, c, prm, ws, gz, outs=o2)
+    assert torch.equal(o2[0], gt) and torch.equal(o2[1], gc)
