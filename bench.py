@@ -254,20 +254,26 @@ def source_hash(path):
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, when that summary was
-    taken on the current source of the kernel's translation unit (its .cu file and the headers it
-    includes), else None."""
+def traffic_key(args):
+    """The workload key of a committed traffic line: workload, guide and target storage, distance
+    storage (each changes what a launch moves)."""
+    return f"{args.workload}:{args.storage}:{args.dist_dtype}"
+
+
+def traffic_for(kernel, key):
+    """DRAM bytes per launch of `kernel` on the workload `key` (traffic_key) from the committed ncu
+    summary, when that summary was taken on the current source of the kernel's translation unit
+    (its .cu file and the headers it includes), else None."""
     sha = source_hash(kernel_source(kernel))
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None
-    pat = re.compile(r"^traffic\s+(\S+)\s+bytes_per_launch=(\d+)\s+source_sha=([0-9a-f]+)", re.M)
+    pat = re.compile(r"^traffic\s+(\S+)\s+workload=(\S+)\s+bytes_per_launch=(\d+)\s+source_sha=([0-9a-f]+)", re.M)
     for fn in sorted(os.listdir(pdir)):
         if fn.endswith((".md", ".txt")):
             for m in pat.finditer(open(os.path.join(pdir, fn)).read()):
-                if m.group(1) == kernel and m.group(3) == sha:
-                    return int(m.group(2))
+                if m.group(1) == kernel and m.group(2) == key and m.group(4) == sha:
+                    return int(m.group(3))
     return None
 
 
@@ -525,7 +531,7 @@ def roofline_of(args, case, recs, total_ms):
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs (copy)",
             "algorithmic_bytes_per_launch": int(alg_bytes), "bytes_per_pixel": round(bpp, 3),
-            "avg_launch_us": round(avg_s * 1e6, 2), "traffic": traffic_for(dom),
+            "avg_launch_us": round(avg_s * 1e6, 2), "traffic": traffic_for(dom, traffic_key(args)),
             "share_of_step": round(kd["ms"] / tot_ms, 4)}
     step_bytes = step_algorithmic_bytes(case, C, s_g)
     step_s = total_ms / args.steps / 1e3

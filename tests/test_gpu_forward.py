@@ -384,11 +384,12 @@ def test_filter_streaming_rows(H, W, items):
 
 
 # the data-term update in the streaming pass: Eq. 3, Eq. 4, the Charbonnier loss (both readings),
-# BF16 target storage, the support-weighted confidence (its chat plane), a caller's z_init; FP16
+# BF16 and FP16 guide and target storage (each a kernel of its own), the support-weighted
+# confidence (its chat plane), a caller's z_init; FP16
 # distances at 8200 (taken) and 8196 (a row of 16-byte units of FP32 but not of FP16: the regular
 # kernel runs)
-@pytest.mark.parametrize("variant", ["gd", "jacobi", "charbonnier_gd", "charbonnier_jacobi", "bf16", "support",
-                                     "zinit", "f16_8200", "f16_8196"])
+@pytest.mark.parametrize("variant", ["gd", "jacobi", "charbonnier_gd", "charbonnier_jacobi", "bf16", "f16target",
+                                     "support", "zinit", "f16_8200", "f16_8196"])
 def test_solve_streaming_rows(variant):
     H, W = (24, 8196) if variant == "f16_8196" else (24, 8200)
     prob = workloads.random_problem(H, W, C=3, seed=31 + len(variant))
@@ -402,6 +403,8 @@ def test_solve_streaming_rows(variant):
         prm.update, prm.charbonnier_eps = dts.UPDATE_JACOBI, 1e-3
     elif variant == "bf16":
         sdt = torch.bfloat16
+    elif variant == "f16target":
+        sdt = torch.float16
     elif variant == "support":
         prm.conf_mode = dts.CONF_SUPPORT
     elif variant == "zinit":
