@@ -448,10 +448,27 @@ constexpr int tall_min_blocks() {
     return ITEMS <= 16 ? 2 : 1;
 }
 
+// Paired halves (pp.paired): a column of up to 32 tiles held by two clusters of CS CTAs, the
+// top half (cluster 2 u) and the bottom half (cluster 2 u + 1) of the strips of unit u, which
+// process the same strips in the same order.  After its cluster's exchange, the top half's last
+// CTA publishes the half's causal map and the bottom half's first CTA the half's anti-causal
+// composition to global slots (alternating by strip parity) under a flag stamped with the
+// launch's base and the strip's round; every CTA of each half waits (bounded) for the other
+// half's stamp and composes.  A half writes a slot for round r + 2 only after it has seen the
+// other half's stamp for round r + 1, which that half publishes after every CTA of it passed its
+// cluster barrier of round r + 1, after its reads of round r.  Both clusters of a unit are
+// resident together: the grid holds only as many clusters as fit at once.
+struct TallPair {
+    unsigned* flags;   // per unit and parity: [top published, bottom published]
+    float* slots;      // per unit and parity: causal map (2 x 32 floats), composition (5 x 32)
+    unsigned base;     // this launch's stamp base (round r stamps base + r + 1)
+    int paired;
+};
+
 template <int ITEMS, bool DHALF, int KIND>
 __global__ void __launch_bounds__(32 * kTallWarps, tall_min_blocks<ITEMS>())
     col_tall_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_d, PassArgs a,
-                    int nstrips, long long timeout, int skip) {
+                    int nstrips, long long timeout, int skip, TallPair pp) {
     using M = ColMode<KIND>;
     using DT = typename std::conditional<DHALF, __half, float>::type;
     constexpr int R = kTallWarps * ITEMS;
@@ -462,12 +479,16 @@ __global__ void __launch_bounds__(32 * kTallWarps, tall_min_blocks<ITEMS>())
     __shared__ ColShared<M, kTallWarps> sh;
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_failed;  // 0, or 1 + the parity of the phase a wait gave up on
+    __shared__ int s_pair_failed;  // a wait for the other half gave up: no more such waits
     cg::cluster_group cluster = cg::this_cluster();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int rank = (int)cluster.block_rank();
     const int CS = (int)cluster.num_blocks();
-    const int tile_row = rank * R;
+    const int half = pp.paired ? (int)(blockIdx.x & 1) : 0;
+    const int unit = pp.paired ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int units = pp.paired ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    const int tile_row = (half * CS + rank) * R;
     const int row0 = tile_row + warp * ITEMS;
     const long long P = a.pitch;
     float* sx = reinterpret_cast<float*>(dsm);
@@ -477,6 +498,7 @@ __global__ void __launch_bounds__(32 * kTallWarps, tall_min_blocks<ITEMS>())
         mbar_init(&bar, 1);
         mbar_init_fence();
         s_failed = 0;
+        s_pair_failed = 0;
     }
     __syncthreads();
     auto issue_d = [&](int strip) {
@@ -497,16 +519,16 @@ __global__ void __launch_bounds__(32 * kTallWarps, tall_min_blocks<ITEMS>())
     // the first tile's distances before the wait for the previous kernel (they were written at
     // the start of the solve, before the horizontal pass that precedes every vertical pass), its
     // positions after it
-    const bool first = threadIdx.x == 0 && (int)blockIdx.x < nstrips && !(skip && blockIdx.x == 0 && rank == 0);
+    const bool first = threadIdx.x == 0 && unit < nstrips && !(skip && blockIdx.x == 0 && rank == 0);
     if (first) {
         mbar_arrive_expect_tx(&bar, kTx);
-        issue_d(blockIdx.x);
+        issue_d(unit);
     }
     wait_predecessor();
-    if (first) issue_x(blockIdx.x);
+    if (first) issue_x(unit);
     int it = 0;
-    for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x, ++it) {
-        const int next = strip + gridDim.x;
+    for (int strip = unit; strip < nstrips; strip += units, ++it) {
+        const int next = strip + units;
         const int col = strip * 32 + lane;
         const bool col_ok = col < a.W;
         // the distance entering the next tile: a plain load, in flight while the stage lands
@@ -547,6 +569,61 @@ __global__ void __launch_bounds__(32 * kTallWarps, tall_min_blocks<ITEMS>())
         typename M::Suf own_suf, suf;
         M::local(x, w, wn, own_pre, own_suf);
         col_exchange_iter<M, kTallWarps>(own_pre, own_suf, lane, warp, kTallWarps, sh, it == 0, pre, suf);
+        if (pp.paired) {
+            const int par = it & 1;
+            const unsigned stamp = pp.base + (unsigned)it + 1u;
+            float* slot = pp.slots + ((size_t)unit * 2 + par) * 32 * 7;
+            unsigned* flag = pp.flags + ((size_t)unit * 2 + par) * 2;
+            if (half == 0 && rank == CS - 1 && warp == kTallWarps - 1) {
+                // the top half's causal map: everything above this last segment, then the segment
+                const typename M::Pre tp = M::pre_compose(pre, own_pre);
+                const float* v = reinterpret_cast<const float*>(&tp);
+#pragma unroll
+                for (int k = 0; k < (int)(sizeof(tp) / 4); ++k) __stcg(slot + k * 32 + lane, v[k]);
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();
+                    st_release_u32(&flag[0], stamp);
+                }
+            }
+            if (half == 1 && rank == 0 && warp == 0) {
+                // the bottom half's composition: this first segment, then everything below it
+                const typename M::Suf ts = M::suf_compose(own_suf, suf);
+                const float* v = reinterpret_cast<const float*>(&ts);
+#pragma unroll
+                for (int k = 0; k < (int)(sizeof(ts) / 4); ++k) __stcg(slot + 64 + k * 32 + lane, v[k]);
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();
+                    st_release_u32(&flag[1], stamp);
+                }
+            }
+            if (threadIdx.x == 0 && !s_pair_failed && ld_acquire_u32(&flag[1 - half]) != stamp) {
+                const long long t0 = clock64();
+                while (ld_acquire_u32(&flag[1 - half]) != stamp) {
+                    if (clock64() - t0 > timeout) {
+                        record_status(a.status, DTS_ERR_TIMEOUT);
+                        s_pair_failed = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __syncthreads();
+            if (half == 0) {
+                typename M::Suf below;
+                float* v = reinterpret_cast<float*>(&below);
+#pragma unroll
+                for (int k = 0; k < (int)(sizeof(below) / 4); ++k) v[k] = __ldcg(slot + 64 + k * 32 + lane);
+                suf = M::suf_compose(suf, below);
+            } else {
+                typename M::Pre above;
+                float* v = reinterpret_cast<float*>(&above);
+#pragma unroll
+                for (int k = 0; k < (int)(sizeof(above) / 4); ++k) v[k] = __ldcg(slot + k * 32 + lane);
+                pre = M::pre_compose(above, pre);
+            }
+        }
         if (next >= nstrips) release_successor();
         M::apply(x, w, wn, own_pre, pre.B, suf);
         col_store<ITEMS, KIND>(a, row0, col, x);
@@ -1013,7 +1090,7 @@ cudaError_t launch_col_tall(const PassArgs& a, int dist_half, int kind, const Co
 cudaError_t launch_col_planned(const PassArgs& a, int dist_half, int kind, const ColPlan& q, cudaStream_t s) {
     if (q.cluster == kColStrip) return launch_col_strip(a, dist_half, q, kind == PASS_TRANSPOSE, s);
     if (q.cluster == kColChain) return launch_col_chain(a, dist_half, kind, q, s);
-    if (q.cluster == kColTall) return launch_col_tall(a, dist_half, kind, q, s);
+    if (q.cluster == kColTall || q.cluster == kColTallPair) return launch_col_tall(a, dist_half, kind, q, s);
     return launch_col_dispatch(a, dist_half, kind, q, s);
 }
 
@@ -1026,7 +1103,7 @@ cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const Co
     const int kid = q.cluster == kColStrip ? (tr ? KID_COL_STRIP_TRANSPOSE : KID_COL_STRIP)
                   : kind == PASS_SUPPORT_CONF ? KID_COL_SUPPORT
                   : q.cluster == kColChain ? (tr ? KID_COL_CHAIN_TRANSPOSE : KID_COL_CHAIN)
-                  : q.cluster == kColTall ? (tr ? KID_COL_TALL_TRANSPOSE : KID_COL_TALL)
+                  : q.cluster == kColTall || q.cluster == kColTallPair ? (tr ? KID_COL_TALL_TRANSPOSE : KID_COL_TALL)
                   : tr ? KID_COL_TRANSPOSE : KID_COL_PLAIN;
     const int flags = dist_half ? kFlagDistHalf : 0;
     const int h = prof_begin(kid, (long long)a.H * a.W, flags, s);
@@ -1079,7 +1156,7 @@ cudaError_t launch_col_strip_t(const PassArgs& a, int nw, bool tr, cudaStream_t 
     // the cluster kernel for the transposed pass
     if (tr) {
         ColPlan q;
-        if (!plan_cols_multi(a.H, &q) || q.cluster == kColTall) {
+        if (!plan_cols_multi(a.H, &q) || q.cluster == kColTall || q.cluster == kColTallPair) {
             // the tall kernel loads through tensor maps too: the cluster kernel, or the chain
             if (!plan_cols_cluster(a.H, &q) && !chain_plan(a.H, &q)) return cudaErrorInvalidValue;
         }
@@ -1174,11 +1251,13 @@ cudaError_t launch_col_chain(const PassArgs& a, int dist_half, int kind, const C
 // persistent TMA clusters for tall columns: ceil(H / R) CTAs per cluster (at most 16), as many
 // clusters as fit at once
 template <int ITEMS, bool DHALF, int KIND>
-cudaError_t launch_tall_t(const PassArgs& a, cudaStream_t s) {
+cudaError_t launch_tall_t(const PassArgs& a, bool paired, cudaStream_t s) {
     auto kernel = col_tall_kernel<ITEMS, DHALF, KIND>;
     constexpr int R = kTallWarps * ITEMS;
-    const int cs = (a.H + R - 1) / R;
-    if (cs > 16) return cudaErrorInvalidValue;
+    const int tiles = (a.H + R - 1) / R;
+    if (tiles > (paired ? 32 : 16) || (paired && tiles < 2)) return cudaErrorInvalidValue;
+    if (paired && (!a.chain_ctl || !a.chain_agg)) return cudaErrorInvalidValue;
+    const int cs = paired ? (tiles + 1) / 2 : tiles;  // CTAs per cluster
     const size_t smem = tall_stage_bytes<ITEMS, DHALF>();
     CUtensorMap tx, td;
     if (!make_box_map(&tx, a.src, false, a.W, a.H, a.pitch, 32, kTallBox) ||
@@ -1186,28 +1265,39 @@ cudaError_t launch_tall_t(const PassArgs& a, cudaStream_t s) {
         return cudaErrorInvalidValue;
     const int nstrips = (a.W + 31) / 32;
     const int mc = max_clusters((const void*)kernel, 32 * kTallWarps, cs, smem);
-    if (mc < 1) return cudaErrorInvalidConfiguration;
-    const int gx = balanced_grid(nstrips, mc);
+    if (mc < (paired ? 2 : 1)) return cudaErrorInvalidConfiguration;
+    // units: clusters, or pairs of clusters (both of a pair resident together: the grid is at
+    // most the clusters that fit at once), at most kTallPairUnits pairs
+    const int units = balanced_grid(nstrips, paired ? std::min(mc / 2, kTallPairUnits) : mc);
+    TallPair pp = {};
+    if (paired) {
+        pp.flags = a.chain_ctl + chain_ctl_words(nstrips);
+        pp.slots = a.chain_agg;
+        pp.base = next_chain_epoch() << 12;  // rounds per launch: at most 512 strips
+        pp.paired = 1;
+    }
     // fault injection (tests): on a single-round grid, CTA 0 of cluster 0 leaves out its first load
-    const bool skip = gx == nstrips && take_injected(DTS_INJECT_TMA_SKIP);
-    return launch_ex_smem(kernel, dim3((unsigned)gx, (unsigned)cs, 1), dim3(32 * kTallWarps), cs, smem, s, tx, td, a,
-                          nstrips, skip ? kInjectedTimeout : default_timeout_cycles(), skip ? 1 : 0);
+    const bool skip = units == nstrips && take_injected(DTS_INJECT_TMA_SKIP);
+    return launch_ex_smem(kernel, dim3((unsigned)(paired ? 2 * units : units), (unsigned)cs, 1), dim3(32 * kTallWarps),
+                          cs, smem, s, tx, td, a, nstrips, skip ? kInjectedTimeout : default_timeout_cycles(),
+                          skip ? 1 : 0, pp);
 }
 
 template <int ITEMS, bool DHALF>
-cudaError_t launch_tall_k(const PassArgs& a, int kind, cudaStream_t s) {
+cudaError_t launch_tall_k(const PassArgs& a, int kind, bool paired, cudaStream_t s) {
     switch (kind) {
-        case PASS_PLAIN: return launch_tall_t<ITEMS, DHALF, PASS_PLAIN>(a, s);
-        case PASS_SUPPORT_CONF: return launch_tall_t<ITEMS, DHALF, PASS_SUPPORT_CONF>(a, s);
-        case PASS_TRANSPOSE: return launch_tall_t<ITEMS, DHALF, PASS_TRANSPOSE>(a, s);
+        case PASS_PLAIN: return launch_tall_t<ITEMS, DHALF, PASS_PLAIN>(a, paired, s);
+        case PASS_SUPPORT_CONF: return launch_tall_t<ITEMS, DHALF, PASS_SUPPORT_CONF>(a, paired, s);
+        case PASS_TRANSPOSE: return launch_tall_t<ITEMS, DHALF, PASS_TRANSPOSE>(a, paired, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_col_tall(const PassArgs& a, int dist_half, int kind, const ColPlan& p, cudaStream_t s) {
-    if (p.items == 16) return dist_half ? launch_tall_k<16, true>(a, kind, s) : launch_tall_k<16, false>(a, kind, s);
-    if (p.items == 32) return dist_half ? launch_tall_k<32, true>(a, kind, s) : launch_tall_k<32, false>(a, kind, s);
-    if (p.items == 40) return dist_half ? launch_tall_k<40, true>(a, kind, s) : launch_tall_k<40, false>(a, kind, s);
+    const bool pr = p.cluster == kColTallPair;
+    if (p.items == 16) return dist_half ? launch_tall_k<16, true>(a, kind, pr, s) : launch_tall_k<16, false>(a, kind, pr, s);
+    if (p.items == 32) return dist_half ? launch_tall_k<32, true>(a, kind, pr, s) : launch_tall_k<32, false>(a, kind, pr, s);
+    if (p.items == 40) return dist_half ? launch_tall_k<40, true>(a, kind, pr, s) : launch_tall_k<40, false>(a, kind, pr, s);
     return cudaErrorInvalidValue;
 }
 
@@ -1271,7 +1361,10 @@ std::string tuned_export() {
     return out;
 }
 
-size_t chain_ctl_bytes(int W) { return (size_t)chain_ctl_words((W + 31) / 32) * sizeof(unsigned); }
+size_t chain_ctl_bytes(int W) {
+    // + the paired tall kernel's flags: 2 per unit and strip parity
+    return ((size_t)chain_ctl_words((W + 31) / 32) + 4 * kTallPairUnits) * sizeof(unsigned);
+}
 size_t chain_agg_bytes(int H, int W) {
     // chunks of at least 64 rows; Pre and Suf of up to 9 floats together (the adjoint's)
     const size_t S = (size_t)(W + 31) / 32, J = (size_t)(H + 63) / 64;
@@ -1294,14 +1387,24 @@ bool chain_plan(int H, ColPlan* p) {
     return chain_shape_fits(H, p->items, p->warps);
 }
 
-// rows per thread of the tall kernel: the fewest whose clusters of at most 16 CTAs of 16 warps
-// hold the column (columns up to 10240 rows)
+// rows per thread of the tall kernel: the most (the smallest clusters, so more of them fit at
+// once) whose clusters of 16 warps hold the column in at most 10 CTAs; else the fewest whose
+// clusters hold it in at most 16 (columns up to 10240 rows).  Measured on GB300 (vertical pass,
+// default against this choice): 4096 x 4096 105.4 -> 74.0 us (clusters of 16 -> 7), 6000 x 3000
+// 85.5 -> 72.2 us (12 -> 10), 2500 x 2500 32.5 -> 27.0 us (10 -> 4); 8192 x 1024 stays at 32
+// rows (16 CTAs, 41.2 us against 46.4 us with 13 CTAs of 40 rows).
 bool tall_plan(int H, ColPlan* p) {
+    p->warps = kTallWarps;
+    p->cluster = kColTall;
+    for (int items : {40, 32, 16}) {
+        if ((H + kTallWarps * items - 1) / (kTallWarps * items) <= 10) {
+            p->items = items;
+            return true;
+        }
+    }
     for (int items : {16, 32, 40}) {
         if ((H + kTallWarps * items - 1) / (kTallWarps * items) <= 16) {
             p->items = items;
-            p->warps = kTallWarps;
-            p->cluster = kColTall;
             return true;
         }
     }
@@ -1320,6 +1423,10 @@ int col_candidates(int H, ColPlan* out, int max_out) {
     for (int items : {16, 32, 40})
         if (H > 1 && (H + kTallWarps * items - 1) / (kTallWarps * items) <= 16 && n < max_out)
             out[n++] = ColPlan{items, kTallWarps, kColTall};
+    for (int items : {32, 40}) {  // paired halves: columns of 3 to 32 tiles
+        const int tiles = (H + kTallWarps * items - 1) / (kTallWarps * items);
+        if (tiles >= 3 && tiles <= 32 && H <= kMaxColRows && n < max_out) out[n++] = ColPlan{items, kTallWarps, kColTallPair};
+    }
     for (const auto& c : kChainShapes)
         if (H > 1 && chain_shape_fits(H, c[0], c[1]) && n < max_out) out[n++] = ColPlan{c[0], c[1], kColChain};
     for (const auto& c : cand) {

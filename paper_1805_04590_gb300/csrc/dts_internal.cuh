@@ -178,6 +178,8 @@ struct ColPlan {
 constexpr int kColStrip = 0;   // one CTA per 8-column strip (col_strip_tma_kernel)
 constexpr int kColChain = -1;  // chained CTAs (col_chain_kernel)
 constexpr int kColTall = -2;   // persistent clusters fed by TMA (col_tall_kernel), ceil(H / rows) CTAs
+constexpr int kColTallPair = -4;  // the same kernel, each column held by a pair of clusters (halves)
+constexpr int kTallPairUnits = 64;  // most cluster pairs of one paired launch
 
 struct RowPlan {
     int items;   // elements per thread

@@ -436,11 +436,13 @@ def test_solve_streaming_rows(variant):
 # (col_chain_kernel: 128-row chunks, 16 rows x 8 warps, by default; 256-row chunks, 16 x 16 and
 # 32 x 8, as tuned shapes); the cluster kernel keeps tall columns for batched solves and as a
 # tuned shape ((40, 16) in clusters of 7 here).  Each non-default shape is set through a tuned plan
-# for a height no other test uses (tuned plans last for the process).  16384 rows is the tallest
-# column.
+# for a height no other test uses (tuned plans last for the process); cluster code -4 holds each
+# column in a pair of clusters (top and bottom halves: 5 tiles of 512 rows as 3 + 3, 7 of 640 as
+# 4 + 4, 16 of 640 as 8 + 8).  16384 rows is the tallest column.
 @pytest.mark.parametrize("H,shape", [(2305, (16, 8, -1)), (2306, (16, 16, -1)), (2307, (32, 8, -1)),
                                      (2308, (16, 16, -2)), (2309, (32, 16, -2)), (2310, (40, 16, -2)),
-                                     (4101, (40, 16, 7)), (10240, None), (12000, None), (16384, None)])
+                                     (4101, (40, 16, 7)), (2313, (32, 16, -4)), (4103, (40, 16, -4)),
+                                     (10001, (40, 16, -4)), (10240, None), (12000, None), (16384, None)])
 def test_filter_chain_and_cluster_shapes(H, shape):
     W = 70 if H < 10000 else 7
     if shape is not None:
@@ -452,6 +454,34 @@ def test_filter_chain_and_cluster_shapes(H, shape):
     assert dts.dts_last_status() == 0
     ref = oracle.filter(prob.guide, prob.target, 40.0, 0.3, passes=3)
     assert_close(out.cpu().numpy(), ref, prob.target, f"filter {H}x{W} shape {shape}")
+
+
+@pytest.mark.parametrize("variant", ["gd", "jacobi", "support", "cg"])
+def test_solve_paired_tall_columns(variant):
+    """Every kind of vertical pass (plain, the support sweep, the transposed pass of conjugate
+    gradients) on the tall kernel with each column held by a pair of clusters."""
+    H, W = 2316, 300
+    dts.autotune_import("col %d 32 16 -4\n" % H)
+    prob = workloads.random_problem(H, W, C=3, seed=79)
+    prm = dts.Params(lam=0.99, sigma_s=24.0, sigma_r=0.2, iterations=3)
+    if variant == "jacobi":
+        prm.update = dts.UPDATE_JACOBI
+    elif variant == "support":
+        prm.conf_mode = dts.CONF_SUPPORT
+    elif variant == "cg":
+        prm.update = dts.UPDATE_CG
+    out = {}
+    names = kernels_of(lambda: out.setdefault("z", dts.dts_solve(to_dev(prob.guide), to_dev(prob.target),
+                                                                 to_dev(prob.conf), prm)))
+    assert dts.dts_last_status() == 0
+    assert "col_tall_kernel" in names, names
+    z = out["z"].cpu().numpy()
+    if variant == "cg":
+        ref = oracle.solve_cg(prob.guide, prob.target, prob.conf, lam=0.99, sigma_s=24.0, sigma_r=0.2,
+                              iterations=3, passes=3)
+    else:
+        ref = oracle_solve(prob.guide, prob.target, prob.conf, prm)
+    assert_close(z, ref, prob.target, f"paired tall columns, {variant}")
 
 
 @pytest.mark.parametrize("update", [dts.UPDATE_GD, dts.UPDATE_JACOBI])
