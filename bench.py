@@ -84,6 +84,13 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3, K=10):
         "col_chain_kernel": 8 + s_d,
         "col_tall_kernel": 8 + s_d,
         "col_bwd_chain_kernel": 24 + s_d,
+        # the two-phase vertical adjoint: chunk totals (pass input, adjoint, distances), then the
+        # replay (those again, the pass output and the distance adjoint read; two planes written)
+        "col_bwd_agg_kernel": 8 + s_d,
+        "col_bwd_apply_kernel": 24 + s_d,
+        # the chunk tuples in and the carries out (nine floats each way per column and chunk of
+        # the default 128 rows): the implementation's bytes, none of the method's
+        "col_bwd_carry_kernel": 72 / 128,
         "row_pass_kernel<support>": s_d + 4,
         "col_pass_kernel<support>": 12 + s_d,
         "row_pass_kernel<update>": 20 + s_t + s_d,
@@ -219,7 +226,8 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
-BACKWARD_KERNELS = ("row_bwd_kernel", "col_bwd_kernel", "col_bwd_chain_kernel", "update_adjoint_kernel",
+BACKWARD_KERNELS = ("row_bwd_kernel", "col_bwd_kernel", "col_bwd_chain_kernel", "col_bwd_agg_kernel",
+                    "col_bwd_apply_kernel", "col_bwd_carry_kernel", "update_adjoint_kernel",
                     "guide_grad_kernel", "axpy_plane_kernel")
 
 

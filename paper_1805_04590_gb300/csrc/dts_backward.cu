@@ -310,6 +310,212 @@ __global__ void __launch_bounds__(32 * NW, bwd_chain_min_blocks<ITEMS, NW>()) co
     col_bwd_finish<ITEMS>(a, row0, col, x, w, wn, G, K, own_pre, pre, suf);
 }
 
+// Two-phase vertical adjoint (no waits): col_bwd_agg_kernel reduces every chunk of NW x ITEMS
+// rows of a 32-column strip to its totals; col_bwd_carry_kernel, one CTA per strip, turns them
+// into every chunk's carries; col_bwd_apply_kernel replays every chunk from its carries.  The
+// three run as consecutive launches.  They move 12 + 28 bytes per position against the chain's
+// 28, but no CTA holds its chunk in registers while it waits for the rest of its column.  Chunk
+// kernels: CTA b takes chunk b mod J of strip b / J.
+//
+// A chunk's totals need six numbers per column: the coupled (h, gJ) tuple (A, B, al, be, ga) and
+// the J map's B (the J and h maps share A, and the h map is (A, B)).  Its carries need four: J
+// and h entering from above (the B of the maps of everything above; their A never reaches an
+// output) and be, ga of everything below (what k_entering reads).  Records (c.agg): S x J x 6 x
+// 32 floats of totals, then S x J x 32 float4 carries.
+constexpr int kSplitRec = 6;
+
+__device__ __forceinline__ float4* split_carries(const ChainArgs& c) {
+    return reinterpret_cast<float4*>(c.agg + (size_t)c.S * c.J * kSplitRec * 32);
+}
+
+// x, w and G of a thread's positions (col_bwd_load without the pass output)
+template <int ITEMS, bool DHALF>
+__device__ __forceinline__ void col_bwd_load3(const BwdArgs& a, int row0, int col, float (&x)[ITEMS],
+                                              float (&w)[ITEMS], float (&G)[ITEMS], float& wn) {
+    const long long P = a.pitch;
+    const bool col_ok = col < a.W;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int r = row0 + j;
+        const bool ok = col_ok && r < a.H;
+        const long long idx = (long long)r * P + col;
+        x[j] = ok ? a.x[idx] : 0.f;
+        w[j] = ok ? load1_d<DHALF>(a.d, idx) : 0.f;
+        G[j] = ok ? a.gin[idx] : 0.f;
+    }
+    const int rn = row0 + ITEMS;
+    wn = (col_ok && rn < a.H) ? ex2(a.k2 * load1_d<DHALF>(a.d, (long long)rn * P + col)) : 0.f;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int r = row0 + j;
+        w[j] = (col_ok && r > 0 && r < a.H) ? ex2(a.k2 * w[j]) : 0.f;
+    }
+}
+
+template <int ITEMS, int NW>
+constexpr int bwd_split_min_blocks() {
+    return ITEMS * NW <= 64 ? 4 : ITEMS * NW <= 128 ? 2 : 1;
+}
+
+template <int ITEMS, int NW, bool DHALF>
+__global__ void __launch_bounds__(32 * NW, bwd_split_min_blocks<ITEMS, NW>()) col_bwd_agg_kernel(BwdArgs a, ChainArgs c) {
+    using M = BackwardMode;
+    __shared__ ChainShared<M, NW> sh;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int strip = (int)blockIdx.x / c.J;
+    const int chunk = (int)blockIdx.x - strip * c.J;
+    const int col = strip * 32 + lane;
+    const int row0 = (chunk * NW + warp) * ITEMS;
+
+    wait_predecessor();
+    float x[ITEMS], w[ITEMS], G[ITEMS], wn;
+    col_bwd_load3<ITEMS, DHALF>(a, row0, col, x, w, G, wn);
+    M::Pre own_pre;
+    M::Suf own_suf;
+    adjoint_local(x, w, wn, G, own_pre, own_suf);
+    sh.pre[warp][lane] = own_pre;
+    sh.suf[warp][lane] = own_suf;
+    __syncthreads();
+    release_successor();
+    float* rec = c.agg + ((size_t)strip * c.J + chunk) * kSplitRec * 32 + lane;
+    // the chunk's totals: its warps' J maps top down, their coupled tuples bottom up
+    if (warp == NW - 1) {
+        Aff t = sh.pre[0][lane].jk;
+        for (int q = 1; q < NW; ++q) t = aff_compose(t, sh.pre[q][lane].jk);
+        __stcg(rec + 5 * 32, t.B);
+    }
+    if (warp == 0) {
+        Coupled t = sh.suf[NW - 1][lane];
+        for (int q = NW - 2; q >= 0; --q) t = coupled_compose(sh.suf[q][lane], t);
+        __stcg(rec, t.A);
+        __stcg(rec + 32, t.B);
+        __stcg(rec + 64, t.al);
+        __stcg(rec + 96, t.be);
+        __stcg(rec + 128, t.ga);
+    }
+}
+
+// One CTA per strip turns the strip's chunk totals into carries.  Warps 0-7 take the prefix
+// direction (top down), warps 8-15 the suffix direction (bottom up), lane = column.  The totals
+// come into shared memory in blocks of kCarryStage chunks (the prefix block from the top, the
+// suffix block from the bottom); each warp takes a run of consecutive chunks of the block,
+// composes the run, takes the other runs' totals before it (and the carry entering the block) as
+// its run's carry, and walks its run writing carries: a serial depth of about 2 kCarryStage / 8 +
+// 7 compositions per block instead of kCarryStage.
+constexpr int kCarryWarps = 8;
+constexpr int kCarryStage = 32;
+
+__global__ void __launch_bounds__(64 * kCarryWarps) col_bwd_carry_kernel(ChainArgs c) {
+    constexpr int NWC = kCarryWarps;
+    constexpr int ST = kCarryStage;
+    __shared__ float pst[ST][3][32];  // A, the J map's B, the h map's B
+    __shared__ float sst[ST][5][32];  // A, B, al, be, ga
+    __shared__ Pre2 bp[NWC][32];
+    __shared__ Coupled bs[NWC][32];
+    __shared__ Pre2 runp[32];    // everything above the current prefix block
+    __shared__ Coupled runs[32];  // everything below the current suffix block
+    wait_predecessor();
+    release_successor();
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const bool prefix = warp < NWC;
+    const int b = warp % NWC;
+    const size_t base = (size_t)blockIdx.x * c.J;
+    const float* rec = c.agg;
+    float4* carry = split_carries(c);
+    if (warp == 0) {
+        runp[lane] = Pre2{aff_identity(), aff_identity()};
+        runs[lane] = coupled_identity();
+    }
+    for (int b0 = 0; b0 < c.J; b0 += ST) {
+        const int nb = min(ST, c.J - b0);
+        const int s0 = c.J - b0 - nb;  // the suffix block: chunks [s0, s0 + nb)
+        for (int i = threadIdx.x; i < nb * 96; i += blockDim.x) {
+            const int j = i / 96, f = (i / 32) % 3;
+            const int field = f == 0 ? 0 : f == 1 ? 5 : 1;
+            pst[j][f][i & 31] = __ldcg(rec + ((base + b0 + j) * kSplitRec + field) * 32 + (i & 31));
+        }
+        for (int i = threadIdx.x; i < nb * 160; i += blockDim.x) {
+            const int j = i / 160, r = i - j * 160;
+            sst[j][r >> 5][r & 31] = __ldcg(rec + (base + s0 + j) * kSplitRec * 32 + r);
+        }
+        __syncthreads();
+        const int per = (nb + NWC - 1) / NWC;
+        const int j0 = min(nb, b * per);
+        const int j1 = min(nb, j0 + per);
+        auto pchunk = [&](int j) {
+            return Pre2{Aff{pst[j][0][lane], pst[j][1][lane]}, Aff{pst[j][0][lane], pst[j][2][lane]}};
+        };
+        auto schunk = [&](int j) {
+            return Coupled{sst[j][0][lane], sst[j][1][lane], sst[j][2][lane], sst[j][3][lane], sst[j][4][lane]};
+        };
+        if (prefix) {
+            Pre2 t = Pre2{aff_identity(), aff_identity()};
+            for (int j = j0; j < j1; ++j) t = BackwardMode::pre_compose(t, pchunk(j));
+            bp[b][lane] = t;
+        } else {
+            Coupled t = coupled_identity();
+            for (int j = j1 - 1; j >= j0; --j) t = coupled_compose(schunk(j), t);
+            bs[b][lane] = t;
+        }
+        __syncthreads();
+        Pre2 pacc;
+        Coupled sacc;
+        if (prefix) {
+            pacc = runp[lane];
+            for (int q = 0; q < b; ++q) pacc = BackwardMode::pre_compose(pacc, bp[q][lane]);
+            for (int j = j0; j < j1; ++j) {
+                __stcg(reinterpret_cast<float2*>(carry + (base + b0 + j) * 32 + lane), make_float2(pacc.jk.B, pacc.hg.B));
+                pacc = BackwardMode::pre_compose(pacc, pchunk(j));
+            }
+        } else {
+            sacc = runs[lane];
+            for (int q = NWC - 1; q > b; --q) sacc = coupled_compose(bs[q][lane], sacc);
+            for (int j = j1 - 1; j >= j0; --j) {
+                __stcg(reinterpret_cast<float2*>(carry + (base + s0 + j) * 32 + lane) + 1, make_float2(sacc.be, sacc.ga));
+                sacc = coupled_compose(schunk(j), sacc);
+            }
+        }
+        __syncthreads();
+        // the carries entering the next blocks: the last prefix run's and the first suffix run's
+        if (prefix && b == NWC - 1) runp[lane] = pacc;
+        if (!prefix && b == 0) runs[lane] = sacc;
+    }
+}
+
+template <int ITEMS, int NW, bool DHALF>
+__global__ void __launch_bounds__(32 * NW, bwd_split_min_blocks<ITEMS, NW>()) col_bwd_apply_kernel(BwdArgs a, ChainArgs c) {
+    using M = BackwardMode;
+    __shared__ ChainShared<M, NW> sh;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int strip = (int)blockIdx.x / c.J;
+    const int chunk = (int)blockIdx.x - strip * c.J;
+    const int col = strip * 32 + lane;
+    const int row0 = (chunk * NW + warp) * ITEMS;
+
+    wait_predecessor();
+    col_bwd_prefetch<ITEMS>(a, row0, strip * 32, lane);
+    const float4 cr = __ldcg(split_carries(c) + ((size_t)strip * c.J + chunk) * 32 + lane);
+    float x[ITEMS], w[ITEMS], G[ITEMS], K[ITEMS], wn;
+    col_bwd_load<ITEMS, DHALF>(a, row0, col, x, w, G, K, wn);
+    M::Pre own_pre;
+    M::Suf own_suf;
+    adjoint_local(x, w, wn, G, own_pre, own_suf);
+    sh.pre[warp][lane] = own_pre;
+    sh.suf[warp][lane] = own_suf;
+    __syncthreads();
+    // everything above the warp's segment (only the B of the maps is used) and everything below
+    M::Pre pre = Pre2{Aff{1.f, cr.x}, Aff{1.f, cr.y}};
+    for (int q = 0; q < warp; ++q) pre = M::pre_compose(pre, sh.pre[q][lane]);
+    M::Suf suf = M::suf_identity();
+    for (int q = warp + 1; q < NW; ++q) suf = M::suf_compose(suf, sh.suf[q][lane]);
+    suf = M::suf_compose(suf, Coupled{1.f, 0.f, 1.f, cr.z, cr.w});
+    release_successor();
+    col_bwd_finish<ITEMS>(a, row0, col, x, w, wn, G, K, own_pre, pre, suf);
+}
+
 // ---------------------------------------------------------------- guide gradient
 // dL/dI_c[y][x] gathers the four distances that involve pixel (y, x):
 //   L1 d = 1 + k sum |D|:          dd/dD = k sign(D)
@@ -502,6 +708,33 @@ cudaError_t launch_col_bwd_chain_t(const BwdArgs& a, cudaStream_t s) {
     return launch_ex_smem(kernel, dim3((unsigned)(c.S * c.J)), dim3(32 * NW), 0, smem, s, a, c);
 }
 
+template <int ITEMS, int NW, bool DHALF>
+cudaError_t launch_col_bwd_split_t(const BwdArgs& a, cudaStream_t s) {
+    ChainArgs c = {};
+    c.ctl = a.chain_ctl;
+    c.agg = a.chain_agg;
+    c.J = (a.H + ITEMS * NW - 1) / (ITEMS * NW);
+    c.S = (a.W + 31) / 32;
+    c.status = a.status;
+    if (!c.ctl || !c.agg || c.J > kChainMaxChunks) return cudaErrorInvalidValue;
+    c.skip_ticket = -1;
+    const dim3 grid((unsigned)(c.S * c.J));
+    const long long px = (long long)a.H * a.W;
+    const int fl = DHALF ? kFlagDistHalf : 0;
+    int h = prof_begin(KID_COL_BWD_AGG, px, fl, s);
+    cudaError_t e = launch_ex(col_bwd_agg_kernel<ITEMS, NW, DHALF>, grid, dim3(32 * NW), 0, s, a, c);
+    prof_end(h, s);
+    if (e != cudaSuccess) return e;
+    h = prof_begin(KID_COL_BWD_CARRY, px, 0, s);
+    e = launch_ex(col_bwd_carry_kernel, dim3((unsigned)c.S), dim3(64 * kCarryWarps), 0, s, c);
+    prof_end(h, s);
+    if (e != cudaSuccess) return e;
+    h = prof_begin(KID_COL_BWD_APPLY, px, fl, s);
+    e = launch_ex(col_bwd_apply_kernel<ITEMS, NW, DHALF>, grid, dim3(32 * NW), 0, s, a, c);
+    prof_end(h, s);
+    return e;
+}
+
 template <int ITEMS, bool DHALF>
 cudaError_t allow_bwd_clusters() {
     return cudaFuncSetAttribute((const void*)col_bwd_kernel<ITEMS, DHALF>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -529,6 +762,10 @@ bool plan_rows_bwd(int W, RowPlan* p) {
 // chain of 256-row chunks waits less for the last chunk of its strip)
 constexpr int kBwdChainShapes[][2] = {{16, 16}, {8, 16}, {8, 8}, {16, 8}, {8, 32}};
 
+// shapes of the two-phase vertical adjoint (rows per thread, warps per CTA), the default first
+constexpr int kBwdSplitShapes[][2] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}, {8, 32}};
+constexpr int kBwdClusterMaxRows = 1536;  // the default plan's cluster limit
+
 std::mutex g_tuned_bwd_mutex;
 std::map<int, ColPlan> g_tuned_bwd_cols;  // H -> vertical adjoint shape
 
@@ -539,13 +776,21 @@ bool valid_bwd_shape(int H, const ColPlan& p) {
                 return (H + p.items * p.warps - 1) / (p.items * p.warps) <= kChainMaxChunks;
         return false;
     }
+    if (p.cluster == kColSplit) {
+        for (const auto& c : kBwdSplitShapes)
+            if (c[0] == p.items && c[1] == p.warps)
+                return (H + p.items * p.warps - 1) / (p.items * p.warps) <= kChainMaxChunks;
+        return false;
+    }
     return (p.items == 8 || p.items == 16) && (p.warps == 8 || p.warps == 16) && p.cluster >= 1 &&
            p.cluster <= 16 && (long long)p.items * p.warps * p.cluster >= H;
 }
 
 // Backward vertical plan: a tuned shape first (set_tuned_bwd_col); else one cluster for columns
-// up to 4096 rows (measured on the 2880 x 1988 stereo workload: 16 rows x 16 warps in clusters of
-// 8 is fastest), a chain above.
+// up to 1536 rows (16 rows x 16 warps in clusters of up to 8 where they fit), the two-phase
+// adjoint in 64-row chunks above.  Measured per vertical adjoint pass on GB300 (cluster or chain
+// against two-phase): 1024 x 8192 84.4 / 87.5 us, 1536 x 4096 66.3 / 66.5, 1988 x 2880 66.1 /
+// 62.8, 2500 x 2500 74.6 / 69.1, 4096 x 4096 218.1 / 148.3, 10000 x 10000 1516.6 (chain) / 789.6.
 bool plan_cols_bwd(int H, ColPlan* p) {
     if (H > kMaxColRows) return false;
     {
@@ -557,6 +802,12 @@ bool plan_cols_bwd(int H, ColPlan* p) {
         }
     }
     static const int cand[][2] = {{16, 16}, {8, 16}, {16, 8}, {8, 8}};
+    if (H > kBwdClusterMaxRows) {
+        p->items = 8;
+        p->warps = 8;
+        p->cluster = kColSplit;
+        return (H + 63) / 64 <= kChainMaxChunks;
+    }
     if (H <= 128) {
         int nw = 1;
         while (nw * 8 < H) nw <<= 1;  // a power of two (the CTA scan works in lane groups)
@@ -577,10 +828,7 @@ bool plan_cols_bwd(int H, ColPlan* p) {
             }
         }
     }
-    p->items = kBwdChainShapes[0][0];
-    p->warps = kBwdChainShapes[0][1];
-    p->cluster = -1;
-    return (H + p->items * p->warps - 1) / (p->items * p->warps) <= kChainMaxChunks;
+    return false;
 }
 
 // records a vertical adjoint shape for columns of H rows (from dts_autotune_import); false when
@@ -615,6 +863,15 @@ cudaError_t launch_row_bwd(const BwdArgs& a, int dist_half, bool final_pass, con
 }
 
 cudaError_t launch_col_bwd(const BwdArgs& a, int dist_half, const ColPlan& p, cudaStream_t s) {
+    if (p.cluster == kColSplit) {  // two launches, each timed on its own
+        const bool dh = dist_half != 0;
+        if (p.items == 8 && p.warps == 16) return dh ? launch_col_bwd_split_t<8, 16, true>(a, s) : launch_col_bwd_split_t<8, 16, false>(a, s);
+        if (p.items == 16 && p.warps == 8) return dh ? launch_col_bwd_split_t<16, 8, true>(a, s) : launch_col_bwd_split_t<16, 8, false>(a, s);
+        if (p.items == 8 && p.warps == 8) return dh ? launch_col_bwd_split_t<8, 8, true>(a, s) : launch_col_bwd_split_t<8, 8, false>(a, s);
+        if (p.items == 16 && p.warps == 16) return dh ? launch_col_bwd_split_t<16, 16, true>(a, s) : launch_col_bwd_split_t<16, 16, false>(a, s);
+        if (p.items == 8 && p.warps == 32) return dh ? launch_col_bwd_split_t<8, 32, true>(a, s) : launch_col_bwd_split_t<8, 32, false>(a, s);
+        return cudaErrorInvalidValue;
+    }
     const int h = prof_begin(p.cluster < 0 ? KID_COL_BWD_CHAIN : KID_COL_BWD, (long long)a.H * a.W,
                              dist_half ? kFlagDistHalf : 0, s);
     cudaError_t e = cudaErrorInvalidValue;

@@ -1366,9 +1366,10 @@ size_t chain_ctl_bytes(int W) {
     return ((size_t)chain_ctl_words((W + 31) / 32) + 4 * kTallPairUnits) * sizeof(unsigned);
 }
 size_t chain_agg_bytes(int H, int W) {
-    // chunks of at least 64 rows; Pre and Suf of up to 9 floats together (the adjoint's)
+    // chunks of at least 64 rows; per column and chunk up to 10 floats (the two-phase adjoint's
+    // six numbers of totals and four of carries; the chain's Pre and Suf take 9 at most)
     const size_t S = (size_t)(W + 31) / 32, J = (size_t)(H + 63) / 64;
-    return S * J * 32 * 9 * sizeof(float);
+    return S * J * 32 * 10 * sizeof(float);
 }
 
 // chain shapes (rows per thread, warps per CTA), the default first

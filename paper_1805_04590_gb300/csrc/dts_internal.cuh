@@ -180,6 +180,7 @@ constexpr int kColChain = -1;  // chained CTAs (col_chain_kernel)
 constexpr int kColTall = -2;   // persistent clusters fed by TMA (col_tall_kernel), ceil(H / rows) CTAs
 constexpr int kColTallPair = -4;  // the same kernel, each column held by a pair of clusters (halves)
 constexpr int kTallPairUnits = 64;  // most cluster pairs of one paired launch
+constexpr int kColSplit = -5;  // vertical adjoint in two launches: chunk totals, then replay
 
 struct RowPlan {
     int items;   // elements per thread
@@ -237,6 +238,9 @@ enum KernelId {
     KID_BATCHED = 35,
     KID_ROW_STREAM = 36,
     KID_ROW_STREAM_UPDATE = 37,
+    KID_COL_BWD_AGG = 38,
+    KID_COL_BWD_APPLY = 39,
+    KID_COL_BWD_CARRY = 40,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16

@@ -131,6 +131,9 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_BATCHED: return "batched_solve_kernel";
         case KID_ROW_STREAM: return "row_stream_kernel";
         case KID_ROW_STREAM_UPDATE: return "row_stream_kernel<update>";
+        case KID_COL_BWD_AGG: return "col_bwd_agg_kernel";
+        case KID_COL_BWD_APPLY: return "col_bwd_apply_kernel";
+        case KID_COL_BWD_CARRY: return "col_bwd_carry_kernel";
         default: return "unknown";
     }
 }

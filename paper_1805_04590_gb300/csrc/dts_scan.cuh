@@ -489,6 +489,75 @@ struct ChainShared {
     typename M::Suf suf[NWMAX][33];
 };
 
+// Turns the J chunk totals of `strip` (Pre tuples at gpre, Suf tuples at gsuf, chunk-major, 32
+// columns each), in place, into every chunk's exclusive carries: everything above it (prefix
+// direction, warp 0, top down) and everything below it (suffix direction, warp 1, bottom up).
+// The tuples come into shared memory (c.stage chunks' worth, dynamic) in blocks loaded by the
+// whole CTA at once: one L2 round trip per block, not one per chunk.  Every thread calls it.
+template <class M>
+__device__ __forceinline__ void chain_compose_strip(const ChainArgs& c, int strip, int lane, int warp,
+                                                    typename M::Pre* gpre, typename M::Suf* gsuf) {
+    using Pre = typename M::Pre;
+    using Suf = typename M::Suf;
+    extern __shared__ __align__(16) float chain_stage[];
+    constexpr int NP = sizeof(Pre) / 4, NS = sizeof(Suf) / 4;
+    float* stp = chain_stage;                              // c.stage x 32 Pre
+    float* sts = chain_stage + (size_t)c.stage * 32 * NP;  // c.stage x 32 Suf
+    Pre pacc = M::pre_identity();
+    Suf sacc = M::suf_identity();
+    const size_t sbase = (size_t)strip * c.J;
+    for (int b0 = 0; b0 < c.J; b0 += c.stage) {
+        const int nb = min(c.stage, c.J - b0);
+        const int s0 = c.J - b0 - nb;  // the suffix block: chunks [s0, s0 + nb), from the bottom
+        const float4* gp = reinterpret_cast<const float4*>(gpre + (sbase + b0) * 32);
+        const float4* gs = reinterpret_cast<const float4*>(gsuf + (sbase + s0) * 32);
+        float4* sp4 = reinterpret_cast<float4*>(stp);
+        float4* ss4 = reinterpret_cast<float4*>(sts);
+        for (int i = threadIdx.x; i < nb * 8 * NP; i += blockDim.x) sp4[i] = __ldcg(gp + i);
+        for (int i = threadIdx.x; i < nb * 8 * NS; i += blockDim.x) ss4[i] = __ldcg(gs + i);
+        __syncthreads();
+        if (warp == 0) {
+            const Pre* sp = reinterpret_cast<const Pre*>(stp);
+            for (int j = 0; j < nb; ++j) {
+                const Pre v = sp[j * 32 + lane];
+                st_cg(gpre + (sbase + b0 + j) * 32 + lane, pacc);
+                pacc = M::pre_compose(pacc, v);
+            }
+        } else if (warp == 1) {
+            const Suf* ss = reinterpret_cast<const Suf*>(sts);
+            for (int j = nb - 1; j >= 0; --j) {
+                const Suf v = ss[j * 32 + lane];
+                st_cg(gsuf + (sbase + s0 + j) * 32 + lane, sacc);
+                sacc = M::suf_compose(v, sacc);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Counts this CTA's arrival at `strip` (its chunk's totals are in place); the CTA whose arrival
+// completes the strip composes the strip's carries (chain_compose_strip), resets the arrival
+// count and returns true.  `count` false leaves the arrival out (fault injection).  Every thread
+// of the CTA calls it.
+template <class M>
+__device__ __forceinline__ bool chain_arrive_compose(const ChainArgs& c, int strip, bool count, int lane, int warp,
+                                                     typename M::Pre* gpre, typename M::Suf* gsuf) {
+    __shared__ int s_combine;
+    unsigned* arrive = c.ctl + kChainCtlHead + strip;
+    if (threadIdx.x == 0) {
+        // the fence publishes the CTA's tuples (ordered before it by the caller's barrier); the
+        // arrival's acquire side makes the other chunks' tuples visible to the composing CTA
+        __threadfence();
+        s_combine = 0;
+        if (count) s_combine = atom_add_acq_rel_u32(arrive, 1u) == (unsigned)c.J - 1u;
+    }
+    __syncthreads();
+    if (!s_combine) return false;
+    chain_compose_strip<M>(c, strip, lane, warp, gpre, gsuf);
+    if (threadIdx.x == 0) atomicExch(arrive, 0u);
+    return true;
+}
+
 // pre / suf: the transforms of everything above / below this warp's segment in its column
 // (warp q of chunk r is segment r NW + q of the column; lane = column).  NW >= 2.
 template <class M, int NWMAX>
@@ -498,7 +567,6 @@ __device__ __forceinline__ void chain_exchange(const typename M::Pre& own_pre, c
                                                typename M::Suf& suf) {
     using Pre = typename M::Pre;
     using Suf = typename M::Suf;
-    __shared__ int s_combine;
     const int strip = ticket / c.J;
     const int chunk = ticket - strip * c.J;
     sh.pre[warp][lane] = own_pre;
@@ -516,58 +584,9 @@ __device__ __forceinline__ void chain_exchange(const typename M::Pre& own_pre, c
         if (warp == NW - 1) st_cg(gpre + mine, M::pre_compose(wpre, own_pre));
         if (warp == 0) st_cg(gsuf + mine, M::suf_compose(own_suf, wsuf));
         __syncthreads();
-        unsigned* arrive = c.ctl + kChainCtlHead + strip;
         unsigned* flag = c.ctl + kChainCtlHead + c.S + strip;
-        if (threadIdx.x == 0) {
-            // the fence publishes the CTA's tuples (ordered before it by the barrier); the
-            // arrival's acquire side makes the other chunks' tuples visible to the composing CTA
-            __threadfence();
-            s_combine = 0;
-            if (ticket != c.skip_ticket) s_combine = atom_add_acq_rel_u32(arrive, 1u) == (unsigned)c.J - 1u;
-        }
-        __syncthreads();
-        if (s_combine) {
-            // every chunk of the strip has published: exclusive carries in place, top down (prefix
-            // direction, warp 0) and bottom up (suffix direction, warp 1).  The tuples come into
-            // shared memory in blocks of c.stage chunks, loaded by the whole CTA at once: one L2
-            // round trip per block, not one per chunk
-            extern __shared__ __align__(16) float chain_stage[];
-            constexpr int NP = sizeof(Pre) / 4, NS = sizeof(Suf) / 4;
-            float* stp = chain_stage;                                  // c.stage x 32 Pre
-            float* sts = chain_stage + (size_t)c.stage * 32 * NP;      // c.stage x 32 Suf
-            Pre pacc = M::pre_identity();
-            Suf sacc = M::suf_identity();
-            const size_t sbase = (size_t)strip * c.J;
-            for (int b0 = 0; b0 < c.J; b0 += c.stage) {
-                const int nb = min(c.stage, c.J - b0);
-                const int s0 = c.J - b0 - nb;  // the suffix block: chunks [s0, s0 + nb), from the bottom
-                const float4* gp = reinterpret_cast<const float4*>(gpre + (sbase + b0) * 32);
-                const float4* gs = reinterpret_cast<const float4*>(gsuf + (sbase + s0) * 32);
-                float4* sp4 = reinterpret_cast<float4*>(stp);
-                float4* ss4 = reinterpret_cast<float4*>(sts);
-                for (int i = threadIdx.x; i < nb * 8 * NP; i += blockDim.x) sp4[i] = __ldcg(gp + i);
-                for (int i = threadIdx.x; i < nb * 8 * NS; i += blockDim.x) ss4[i] = __ldcg(gs + i);
-                __syncthreads();
-                if (warp == 0) {
-                    const Pre* sp = reinterpret_cast<const Pre*>(stp);
-                    for (int j = 0; j < nb; ++j) {
-                        const Pre v = sp[j * 32 + lane];
-                        st_cg(gpre + (sbase + b0 + j) * 32 + lane, pacc);
-                        pacc = M::pre_compose(pacc, v);
-                    }
-                } else if (warp == 1) {
-                    const Suf* ss = reinterpret_cast<const Suf*>(sts);
-                    for (int j = nb - 1; j >= 0; --j) {
-                        const Suf v = ss[j * 32 + lane];
-                        st_cg(gsuf + (sbase + s0 + j) * 32 + lane, sacc);
-                        sacc = M::suf_compose(v, sacc);
-                    }
-                }
-                __syncthreads();
-            }
-            __syncthreads();
+        if (chain_arrive_compose<M>(c, strip, ticket != c.skip_ticket, lane, warp, gpre, gsuf)) {
             if (threadIdx.x == 0) {
-                atomicExch(arrive, 0u);
                 __threadfence();
                 st_release_u32(flag, c.epoch);
             }

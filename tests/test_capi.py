@@ -52,9 +52,9 @@ def test_workspace_size_layout():
     pitch = 64
     plane = 40 * pitch * 4
     # chained vertical passes: 32 + 2 S control words (S = 2 strips of 32 columns) and the paired
-    # tall kernel's 4 x 64 flags, then per strip and 64-row chunk 32 columns of up to 9 floats of
-    # tuples, each region 256-byte aligned
-    split = ((32 + 2 * 2 + 4 * 64) * 4 + 255) // 256 * 256 + 2 * 1 * 32 * 9 * 4
+    # tall kernel's 4 x 64 flags, then per strip and 64-row chunk 32 columns of up to 10 floats of
+    # chunk records, each region 256-byte aligned
+    split = ((32 + 2 * 2 + 4 * 64) * 4 + 255) // 256 * 256 + 2 * 1 * 32 * 10 * 4
     # dY tiled by 8-column strips for the strip kernel: 7 strips of 4 * 2 warps * 9 rows + 1 rows
     # of 8 values (segments of 9 rows, 2 warps for 40 rows), 256-byte aligned
     tiled = (7 * 73 * 8 * 4 + 255) // 256 * 256

@@ -109,9 +109,8 @@ def test_backward_needs_kept_iterates():
         dts.dts_solve_backward(g, t, t, prm, ws, t)
 
 
-# columns over 4096 rows: the vertical adjoint runs on chains of CTAs of 128 rows (one launch,
-# chunk totals composed through global memory); rows over 8192: 16 positions per thread in the
-# row adjoint
+# columns over 1536 rows: the two-phase vertical adjoint (chunk totals of 64 rows, their
+# composition per strip, the replay); rows over 8192: 16 positions per thread in the row adjoint
 @pytest.mark.parametrize("H,W,update", [(4500, 40, dts.UPDATE_GD), (9000, 9, dts.UPDATE_JACOBI),
                                         (5, 9000, dts.UPDATE_GD), (3, 10240, dts.UPDATE_JACOBI)])
 def test_backward_tall_and_wide(H, W, update):
@@ -294,7 +293,7 @@ def test_backward_multispectral_reduced():
 @pytest.mark.parametrize("H,W", [(10000, 64), (64, 10000)])
 def test_backward_multispectral_full_size_slices(H, W):
     """The multispectral generator on slices that run the full 10000 x 10000 image's backward
-    plans (the 10000-row chained vertical adjoint; 10000-column rows), K = 10 with every pass input
+    plans (the 10000-row two-phase vertical adjoint; 10000-column rows), K = 10 with every pass input
     kept, as the bench runs it: every gradient against the oracle's reverse mode."""
     rng = np.random.Generator(np.random.PCG64(1004))
     p = workloads.multispectral_image(H, W, rng, bands=16, gy=max(1, H // 100), gx=max(1, W // 100))
@@ -322,6 +321,37 @@ def test_backward_chain_shapes(H, items, warps):
     dts.autotune_import("bcol %d %d %d -1\n" % (H, items, warps))
     assert ("bcol %d %d %d -1" % (H, items, warps)) in dts.autotune_export()
     run_case(H, 40, K=2, update=dts.UPDATE_GD, seed=H, keep=2)
+
+
+# the two-phase vertical adjoint (chunk totals, strip composition, replay: "bcol H items warps
+# -5"): every shape on a column of several chunks and a ragged last chunk, one chunk alone, FP16
+# distances, and W not a multiple of the 32-column strip
+@pytest.mark.parametrize("H,W,items,warps,dist", [(4511, 40, 8, 16, dts.F32), (4512, 40, 16, 8, dts.F32),
+                                                  (4513, 40, 8, 8, dts.F32), (4514, 40, 16, 16, dts.F32),
+                                                  (4515, 40, 8, 32, dts.F32), (100, 33, 8, 16, dts.F32),
+                                                  (1999, 70, 8, 16, dts.F16)])
+def test_backward_split_shapes(H, W, items, warps, dist):
+    dts.autotune_import("bcol %d %d %d -5\n" % (H, items, warps))
+    assert ("bcol %d %d %d -5" % (H, items, warps)) in dts.autotune_export()
+    if dist == dts.F16:
+        # FP16 distances: the split adjoint against the one-cluster adjoint on the same planes
+        dts.dts_profile(1)
+        z, gt, gc, gg, _, _ = run_case(H, W, K=2, update=dts.UPDATE_JACOBI, seed=H, keep=2, dist=dist)
+        names = {r[0] for r in dts.dts_profile_read()}
+        dts.dts_profile(0)
+        assert {"col_bwd_agg_kernel", "col_bwd_apply_kernel"} <= names
+        dts.autotune_import("bcol %d 16 16 8\n" % H)
+        z2, gt2, gc2, gg2, _, _ = run_case(H, W, K=2, update=dts.UPDATE_JACOBI, seed=H, keep=2, dist=dist)
+        assert torch.equal(z, z2)
+        for a_, b_ in ((gt, gt2), (gc, gc2), (gg, gg2)):
+            scale = float(b_.abs().max()) + 1e-30
+            assert float((a_ - b_).abs().max()) <= 1e-4 * scale
+        return
+    dts.dts_profile(1)
+    run_case(H, W, K=2, update=dts.UPDATE_GD, seed=H, keep=2)
+    names = {r[0] for r in dts.dts_profile_read()}
+    dts.dts_profile(0)
+    assert {"col_bwd_agg_kernel", "col_bwd_apply_kernel"} <= names
 
 
 def test_backward_into_caller_tensors():

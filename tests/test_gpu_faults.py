@@ -69,11 +69,12 @@ def test_pass_wait_reports_timeout_and_recovers(H, W, kind, kernel):
 
 
 def test_chained_adjoint_wait_reports_timeout_and_recovers():
-    """The chained vertical adjoint (columns over 4096 rows; every pass input kept, so the first
-    chained launch after the request is the backward's)."""
+    """The chained vertical adjoint (a tuned plan for this height; every pass input kept, so the
+    first chained launch after the request is the backward's)."""
     d = dev()
     lib = dts.load()
-    H, W = 4500, 40
+    H, W = 4520, 40
+    dts.autotune_import("bcol %d 16 16 -1\n" % H)
     rng = np.random.default_rng(45)
     I = rng.random((3, H, W)).astype(np.float32)
     t = rng.normal(size=(H, W)).astype(np.float32)
