@@ -226,6 +226,19 @@ __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel
         const bool abort = s_abort[it & 1] != 0;  // CTA-uniform (written before the barrier)
         const int ahead = row + 2 * (int)gridDim.x;
         if (tid == 0 && !abort && ahead < a.H) issue(ahead, st);
+        if constexpr (UPD > 0) {
+            // the update operands of that row into L2 as well (a 128-byte line of each per lane
+            // and step), so that the loads after its stage wait hit L2
+            if (!abort && ahead < a.H) {
+                const long long ab = (long long)ahead * P, at = (long long)ahead * W;
+                constexpr int tsz = UPD - 1 == DTS_F32 ? 4 : 2;
+                for (int off = span0 + lane * 32; off < span1; off += 32 * 32) {
+                    prefetch_l2(a.zk + ab + off);
+                    prefetch_l2(static_cast<const char*>(a.t) + (at + off) * tsz);
+                    prefetch_l2(a.c + (a.c_pitched ? ab : at) + off);
+                }
+            }
+        }
         if (abort) {
             // copies still in flight (the one a wait gave up on, the next row's) must land before
             // the CTA's shared memory goes to another CTA
