@@ -406,11 +406,11 @@ __global__ void __launch_bounds__(32 * NW, bwd_split_min_blocks<ITEMS, NW>()) co
 constexpr int kCarryWarps = 8;
 constexpr int kCarryStage = 32;
 
-__global__ void __launch_bounds__(64 * kCarryWarps) col_bwd_carry_kernel(ChainArgs c) {
+__global__ void __launch_bounds__(64 * kCarryWarps, 3) col_bwd_carry_kernel(ChainArgs c) {
     constexpr int NWC = kCarryWarps;
     constexpr int ST = kCarryStage;
-    __shared__ float pst[ST][3][32];  // A, the J map's B, the h map's B
-    __shared__ float sst[ST][5][32];  // A, B, al, be, ga
+    __shared__ __align__(16) float pst[ST][3][32];  // A, B (the h map's), the J map's B
+    __shared__ __align__(16) float sst[ST][5][32];  // A, B, al, be, ga
     __shared__ Pre2 bp[NWC][32];
     __shared__ Coupled bs[NWC][32];
     __shared__ Pre2 runp[32];    // everything above the current prefix block
@@ -431,21 +431,39 @@ __global__ void __launch_bounds__(64 * kCarryWarps) col_bwd_carry_kernel(ChainAr
     for (int b0 = 0; b0 < c.J; b0 += ST) {
         const int nb = min(ST, c.J - b0);
         const int s0 = c.J - b0 - nb;  // the suffix block: chunks [s0, s0 + nb)
-        for (int i = threadIdx.x; i < nb * 96; i += blockDim.x) {
-            const int j = i / 96, f = (i / 32) % 3;
-            const int field = f == 0 ? 0 : f == 1 ? 5 : 1;
-            pst[j][f][i & 31] = __ldcg(rec + ((base + b0 + j) * kSplitRec + field) * 32 + (i & 31));
-        }
-        for (int i = threadIdx.x; i < nb * 160; i += blockDim.x) {
-            const int j = i / 160, r = i - j * 160;
-            sst[j][r >> 5][r & 31] = __ldcg(rec + (base + s0 + j) * kSplitRec * 32 + r);
+        {
+            // 16-byte pieces: per chunk 24 of the prefix block (fields 0-1, then field 5), then per
+            // chunk 40 of the suffix block (fields 0-4); every load of a thread is issued before
+            // its stores
+            constexpr int NT = 64 * NWC;
+            constexpr int U = (ST * 64 + NT - 1) / NT;
+            const float4* r4 = reinterpret_cast<const float4*>(rec);
+            const int np = nb * 24;
+            float4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = (int)threadIdx.x + u * NT;
+                if (k < np) {
+                    const int j = k / 24, r = k - j * 24;
+                    v[u] = __ldcg(r4 + (base + b0 + j) * (kSplitRec * 8) + (r < 16 ? r : r + 24));
+                } else if (k < nb * 64) {
+                    const int j = (k - np) / 40, r = k - np - j * 40;
+                    v[u] = __ldcg(r4 + (base + s0 + j) * (kSplitRec * 8) + r);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = (int)threadIdx.x + u * NT;
+                if (k < np) reinterpret_cast<float4*>(&pst[0][0][0])[k] = v[u];
+                else if (k < nb * 64) reinterpret_cast<float4*>(&sst[0][0][0])[k - np] = v[u];
+            }
         }
         __syncthreads();
         const int per = (nb + NWC - 1) / NWC;
         const int j0 = min(nb, b * per);
         const int j1 = min(nb, j0 + per);
         auto pchunk = [&](int j) {
-            return Pre2{Aff{pst[j][0][lane], pst[j][1][lane]}, Aff{pst[j][0][lane], pst[j][2][lane]}};
+            return Pre2{Aff{pst[j][0][lane], pst[j][2][lane]}, Aff{pst[j][0][lane], pst[j][1][lane]}};
         };
         auto schunk = [&](int j) {
             return Coupled{sst[j][0][lane], sst[j][1][lane], sst[j][2][lane], sst[j][3][lane], sst[j][4][lane]};
