@@ -1157,7 +1157,7 @@ extern "C" int dts_autotune(const dts_guide* guide, const dts_params* params, vo
         RowPlan rp;
         rp.items = items;
         rp.tpr = ((guide->W + items - 1) / items + 31) / 32 * 32;
-        if (items % 2 ? !row_stream_fits(guide->W, items, dh) : rp.tpr > (items >= 32 ? 320 : 1024)) continue;
+        if (items % 2 ? !row_stream_fits(guide->W, items) : rp.tpr > (items >= 32 ? 320 : 1024)) continue;
         rp.rpb = items % 2 || rp.tpr >= 256 ? 1 : 256 / rp.tpr;
         PassArgs r = base_pass(guide, L);
         r.src = u;

@@ -1057,7 +1057,7 @@ cudaError_t launch_row_pass(const PassArgs& a, int dist_half, int kind, const Ro
         // a streaming plan: the plain and update passes on planes the bulk copies can address,
         // else the regular kernel's plan for the row length
         const bool upd = kind == PASS_UPDATE_ROW;
-        if ((kind == PASS_PLAIN || upd) && row_stream_fits(a.W, p.items, dist_half) &&
+        if ((kind == PASS_PLAIN || upd) && row_stream_fits(a.W, p.items) &&
             row_stream_addressable(a, dist_half, upd)) {
             const int h = prof_begin(upd ? KID_ROW_STREAM_UPDATE : KID_ROW_STREAM, (long long)a.H * a.W, flags, s);
             const cudaError_t e = launch_row_stream(a, dist_half, p.items, upd, s);
@@ -1472,11 +1472,11 @@ bool plan_rows(int W, RowPlan* p) {
     const int tuned = tuned_row(W);
     if ((tuned == 8 || tuned == 16 || tuned == 32) && ((W + tuned - 1) / tuned + 31) / 32 * 32 <= (tuned >= 32 ? 320 : 1024))
         row_plan_of(W, tuned, p);
-    else if ((tuned == 17 || tuned == 33) && row_stream_fits(W, tuned, 0))
+    else if ((tuned == 17 || tuned == 33) && row_stream_fits(W, tuned))
         row_plan_of(W, tuned, p);
-    else if (W >= 1024 && row_stream_fits(W, 17, 0))
+    else if (W >= 1024 && row_stream_fits(W, 17))
         row_plan_of(W, 17, p);
-    else if (W >= 1024 && row_stream_fits(W, 33, 0))
+    else if (W >= 1024 && row_stream_fits(W, 33))
         row_plan_of(W, 33, p);
     return true;
 }

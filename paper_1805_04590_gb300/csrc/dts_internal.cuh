@@ -289,7 +289,7 @@ cudaError_t launch_col_pass(const PassArgs& a, int dist_half, int kind, const Co
 bool plan_rows(int W, RowPlan* p);
 bool plan_rows_regular(int W, RowPlan* p);
 // the streaming horizontal pass (dts_rows.cu): plans with an odd segment length (17 or 33)
-bool row_stream_fits(int W, int items, int dist_half);
+bool row_stream_fits(int W, int items);
 bool row_stream_addressable(const PassArgs& a, int dist_half, bool upd);
 cudaError_t launch_row_stream(const PassArgs& a, int dist_half, int items, bool upd, cudaStream_t s);
 cudaError_t prepare_row_stream_kernels();

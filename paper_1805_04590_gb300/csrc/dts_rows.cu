@@ -60,12 +60,15 @@ constexpr int stream_max_threads() {
     return ITEMS >= 33 ? 384 : 512;
 }
 
+// RAG: rows that do not end on a whole 16-byte unit (of the positions, or of FP16 distances).
+// The bulk copies then bring the whole units, the 1-3 positions (1-7 FP16 distances) after them
+// come by plain loads, and the results past the last whole unit leave by plain stores.
 // UPD > 0: the pass with the update, for a target stored as dtype UPD - 1 (DTS_F32, DTS_BF16,
 // DTS_F16).  Waits on a stage are bounded (timeout cycles).  A wait that gives up records DTS_ERR_TIMEOUT;
 // the CTA finishes the row at hand with what it holds (the results are invalid, the status says
 // so), issues no further copies and leaves the row loop after one more bounded wait for each
 // copy of its own still in flight.  skip (fault injection): CTA 0 leaves out its first row's copies.
-template <int ITEMS, bool DHALF, int UPD>
+template <int ITEMS, bool DHALF, int UPD, bool RAG>
 __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel(PassArgs a, long long timeout,
                                                                                   int skip) {
     static_assert(ITEMS % 2 == 1, "odd segment length (bank-conflict-free shared-memory reads)");
@@ -85,7 +88,9 @@ __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel
     const long long P = a.pitch;
     const size_t xb = stream_x_bytes(NW, ITEMS);
     const size_t stage = xb + stream_d_bytes(NW, ITEMS, (int)sizeof(DT));
-    const uint32_t kx = (uint32_t)W * 4u, kd = (uint32_t)W * (uint32_t)sizeof(DT);
+    const int Wx = RAG ? W & ~3 : W;                     // positions the bulk copy brings
+    const int Wd = RAG ? (DHALF ? W & ~7 : W & ~3) : W;  // distances the bulk copy brings
+    const uint32_t kx = (uint32_t)Wx * 4u, kd = (uint32_t)Wd * (uint32_t)sizeof(DT);
     const int e0 = tid * ITEMS;
     const int span0 = warp * 32 * ITEMS;  // this warp's span of the row
     const int span1 = min(span0 + 32 * ITEMS, W);
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
                     const int e = e1 + 128 * g;
-                    if (e < span1) {
+                    if (RAG ? e + 4 <= span1 : e < span1) {
                         load4_f(a.zk, rb + e, zk[g]);
                         if (a.tc_vec) load4_target<UPD - 1>(a.t, tb + e, tt[g]);
                         else {
@@ -146,7 +151,20 @@ __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
                     const int e = e1 + 128 * g;
-                    if (e < span1) {
+                    if constexpr (RAG) {
+                        if (e + 4 > span1 && e < span1) {
+                            // the row's last 1-3 positions (e == Wx): one by one, zbar from the plane
+                            for (int k = 0; e + k < span1; ++k) {
+                                const long long i = rb + e + k;
+                                const float z = dts_update_value(a.zk[i], a.src[i], load_any(a.t, tb + e + k, a.t_dtype),
+                                                                 a.c_pitched ? a.c[i] : a.c[tb + e + k], a.lambda,
+                                                                 a.step, a.update, a.clamp_step, a.eps);
+                                a.zout[i] = z;
+                                sx[e + k] = z;
+                            }
+                        }
+                    }
+                    if (RAG ? e + 4 <= span1 : e < span1) {
                         const float4 zb = *reinterpret_cast<const float4*>(sx + e);
                         const float zbv[4] = {zb.x, zb.y, zb.z, zb.w};
                         float z[4];
@@ -162,6 +180,17 @@ __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel
             __syncwarp();
         }
         float x[ITEMS], w[ITEMS];
+        if constexpr (RAG) {
+            // the thread whose positions (or next distance) reach past the bulk copies: those
+            // positions and distances into the stage from the planes (its own reads only; the
+            // update pass has already written every position of the row into the stage)
+            const int hi = min(e0 + ITEMS + 1, W);
+            for (int e = max(e0, Wd); e < hi; ++e) {
+                if (e == e0 + ITEMS) continue;  // the next thread's position: read below
+                if (UPD == 0 && e >= Wx) sx[e] = a.src[rb + e];
+                const_cast<DT*>(sd)[e] = static_cast<const DT*>(a.d)[rb + e];
+            }
+        }
         if (e0 + ITEMS <= W) {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) {
@@ -177,7 +206,12 @@ __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel
             }
         }
         if (e0 == 0) w[0] = 0.f;  // the row starts here
-        const float wn = e0 + ITEMS < W ? ex2(a.k2 * to_f32<DT>(sd[e0 + ITEMS])) : 0.f;
+        float dn = 0.f;  // the distance entering the next thread's positions
+        if (e0 + ITEMS < W) {
+            if (RAG && e0 + ITEMS >= Wd) dn = load1_d<DHALF>(a.d, rb + e0 + ITEMS);
+            else dn = to_f32<DT>(sd[e0 + ITEMS]);
+        }
+        const float wn = e0 + ITEMS < W ? ex2(a.k2 * dn) : 0.f;
 
         // causal sweep: segment map c -> A c + B, exclusive prefix over the row, replay
         float A = 1.f, B = 0.f;
@@ -217,8 +251,12 @@ __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel
             if (e0 + j < W) sx[e0 + j] = x[j];
         __syncwarp();
         for (int e = span0 + 4 * lane; e < span1; e += 128) {
-            const float4 o = *reinterpret_cast<const float4*>(sx + e);
-            *reinterpret_cast<float4*>(a.dst + rb + e) = o;
+            if (RAG && e + 4 > span1) {
+                for (int k = 0; e + k < span1; ++k) a.dst[rb + e + k] = sx[e + k];
+            } else {
+                const float4 o = *reinterpret_cast<const float4*>(sx + e);
+                *reinterpret_cast<float4*>(a.dst + rb + e) = o;
+            }
         }
         // every thread's reads and writes of the stage come before the next copy into it
         fence_proxy_async_smem();
@@ -251,31 +289,46 @@ __global__ void __launch_bounds__(stream_max_threads<ITEMS>()) row_stream_kernel
     }
 }
 
-template <int ITEMS, bool DHALF, int UPD>
+template <int ITEMS, bool DHALF, int UPD, bool RAG>
 cudaError_t allow_stream_t() {
-    return cudaFuncSetAttribute((const void*)row_stream_kernel<ITEMS, DHALF, UPD>,
+    return cudaFuncSetAttribute((const void*)row_stream_kernel<ITEMS, DHALF, UPD, RAG>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(2 * stream_stage_bytes(stream_max_threads<ITEMS>() / 32, ITEMS, DHALF ? 2 : 4)));
+}
+
+template <int ITEMS, bool DHALF, bool RAG>
+cudaError_t allow_stream_r() {
+    cudaError_t e = cudaSuccess, r;
+    if ((r = allow_stream_t<ITEMS, DHALF, 0, RAG>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<ITEMS, DHALF, 1 + DTS_F32, RAG>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<ITEMS, DHALF, 1 + DTS_BF16, RAG>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_t<ITEMS, DHALF, 1 + DTS_F16, RAG>()) != cudaSuccess) e = r;
+    return e;
 }
 
 template <int ITEMS, bool DHALF>
 cudaError_t allow_stream_k() {
     cudaError_t e = cudaSuccess, r;
-    if ((r = allow_stream_t<ITEMS, DHALF, 0>()) != cudaSuccess) e = r;
-    if ((r = allow_stream_t<ITEMS, DHALF, 1 + DTS_F32>()) != cudaSuccess) e = r;
-    if ((r = allow_stream_t<ITEMS, DHALF, 1 + DTS_BF16>()) != cudaSuccess) e = r;
-    if ((r = allow_stream_t<ITEMS, DHALF, 1 + DTS_F16>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_r<ITEMS, DHALF, false>()) != cudaSuccess) e = r;
+    if ((r = allow_stream_r<ITEMS, DHALF, true>()) != cudaSuccess) e = r;
     return e;
+}
+
+template <int ITEMS, bool DHALF, bool RAG>
+auto stream_kernel_for(const PassArgs& a, bool upd) {
+    return !upd ? row_stream_kernel<ITEMS, DHALF, 0, RAG>
+           : a.t_dtype == DTS_BF16 ? row_stream_kernel<ITEMS, DHALF, 1 + DTS_BF16, RAG>
+           : a.t_dtype == DTS_F16 ? row_stream_kernel<ITEMS, DHALF, 1 + DTS_F16, RAG>
+                                   : row_stream_kernel<ITEMS, DHALF, 1 + DTS_F32, RAG>;
 }
 
 template <int ITEMS, bool DHALF>
 cudaError_t launch_stream_t(const PassArgs& a, bool upd, cudaStream_t s) {
     const int nw = ((a.W + ITEMS - 1) / ITEMS + 31) / 32;
     const size_t smem = 2 * stream_stage_bytes(nw, ITEMS, DHALF ? 2 : 4);
-    auto kernel = !upd ? row_stream_kernel<ITEMS, DHALF, 0>
-                  : a.t_dtype == DTS_BF16 ? row_stream_kernel<ITEMS, DHALF, 1 + DTS_BF16>
-                  : a.t_dtype == DTS_F16 ? row_stream_kernel<ITEMS, DHALF, 1 + DTS_F16>
-                                          : row_stream_kernel<ITEMS, DHALF, 1 + DTS_F32>;
+    // rows that end past their last whole 16-byte unit run the kernel's ragged variant
+    const bool rag = a.W % (DHALF ? 8 : 4) != 0;
+    auto kernel = rag ? stream_kernel_for<ITEMS, DHALF, true>(a, upd) : stream_kernel_for<ITEMS, DHALF, false>(a, upd);
     const int per_sm = blocks_per_sm((const void*)kernel, 32 * nw, smem);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int g = std::min(a.H, per_sm * sm_count());
@@ -288,13 +341,13 @@ cudaError_t launch_stream_t(const PassArgs& a, bool upd, cudaStream_t s) {
 }  // namespace
 
 // Whether the streaming kernel takes this pass with ITEMS positions per thread: rows of at
-// least two warps' spans within its largest CTA, and planes the bulk copies and vector stores
-// can address (16-byte aligned rows, row lengths in whole 16-byte units).
-bool row_stream_fits(int W, int items, int dist_half) {
+// least two warps' spans within its largest CTA, of any length (row_stream_addressable checks
+// that the planes' rows start on 16-byte boundaries).
+bool row_stream_fits(int W, int items) {
     if (items != 17 && items != 33) return false;
     const int nw = ((W + items - 1) / items + 31) / 32;
     const int max_nw = (items >= 33 ? 384 : 512) / 32;
-    return nw >= 2 && nw <= max_nw && W % (dist_half ? 8 : 4) == 0;
+    return nw >= 2 && nw <= max_nw;
 }
 
 bool row_stream_addressable(const PassArgs& a, int dist_half, bool upd) {

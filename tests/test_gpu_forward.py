@@ -341,13 +341,16 @@ def test_solve_multispectral_full_size_slices(H, W, sdt):
 # no other test uses.  700 x 10000: four or five rows per CTA (both stages reused, both barrier
 # parities); 12672: the widest row at 33; 12676 and 1101: not taken (the regular kernel runs);
 # 1092 at 33: two warps, a ragged last segment; 8200 at 17: 16 warps; 1100 at 17: three warps.
+# rows of any length: 1101, 1027, 2882 and 12038 end in 1-3 positions past their whole 16-byte units,
+# which arrive by plain loads and leave by plain stores
 STREAM_SHAPES = [(700, 10000, None), (3, 9000, None), (2, 12672, None), (2, 12676, None), (1500, 1100, 17),
-                 (9, 1092, 33), (40, 2884, 33), (6, 1101, 33), (3, 8200, 17)]
+                 (9, 1092, 33), (40, 2884, 33), (6, 1101, 33), (3, 8200, 17), (7, 1027, None), (4, 2882, 17),
+                 (5, 12038, None)]
 
 
-def stream_fits(W, items, dist_half=False):
+def stream_fits(W, items):
     nw = -(-(-(-W // items)) // 32)
-    return W % (8 if dist_half else 4) == 0 and 2 <= nw <= (12 if items == 33 else 16)
+    return 2 <= nw <= (12 if items == 33 else 16)
 
 
 def stream_taken(W, items=None):
@@ -385,13 +388,16 @@ def test_filter_streaming_rows(H, W, items):
 
 # the data-term update in the streaming pass: Eq. 3, Eq. 4, the Charbonnier loss (both readings),
 # BF16 and FP16 guide and target storage (each a kernel of its own), the support-weighted
-# confidence (its chat plane), a caller's z_init; FP16
-# distances at 8200 (taken) and 8196 (a row of 16-byte units of FP32 but not of FP16: the regular
-# kernel runs)
+# confidence (its chat plane), a caller's z_init; FP16 distances at 8200 and 8196 (a row of
+# 16-byte units of FP32 but not of FP16: its last 4 distances by plain loads); rows that end past
+# their whole 16-byte units (8202: two positions and distances, the update's last group one by
+# one; 8203 with FP16 distances: three of each; 8201 with a BF16 target)
 @pytest.mark.parametrize("variant", ["gd", "jacobi", "charbonnier_gd", "charbonnier_jacobi", "bf16", "f16target",
-                                     "support", "zinit", "f16_8200", "f16_8196"])
+                                     "support", "zinit", "f16_8200", "f16_8196", "ragged_8202", "ragged_f16_8203",
+                                     "ragged_bf16_8201"])
 def test_solve_streaming_rows(variant):
-    H, W = (24, 8196) if variant == "f16_8196" else (24, 8200)
+    H, W = {"f16_8196": (24, 8196), "ragged_8202": (24, 8202), "ragged_f16_8203": (24, 8203),
+            "ragged_bf16_8201": (24, 8201)}.get(variant, (24, 8200))
     prob = workloads.random_problem(H, W, C=3, seed=31 + len(variant))
     prm = dts.Params(lam=0.99, sigma_s=24.0, sigma_r=0.2, iterations=4)
     sdt, kw, z_init = torch.float32, {}, None
@@ -401,7 +407,7 @@ def test_solve_streaming_rows(variant):
         prm.charbonnier_eps = 1.0
     elif variant == "charbonnier_jacobi":
         prm.update, prm.charbonnier_eps = dts.UPDATE_JACOBI, 1e-3
-    elif variant == "bf16":
+    elif variant in ("bf16", "ragged_bf16_8201"):
         sdt = torch.bfloat16
     elif variant == "f16target":
         sdt = torch.float16
@@ -410,16 +416,16 @@ def test_solve_streaming_rows(variant):
     elif variant == "zinit":
         z_init = np.random.default_rng(5).random(prob.target.shape).astype(np.float32)
         kw["z_init"] = z_init.astype(np.float64)
-    elif variant in ("f16_8200", "f16_8196"):
+    elif variant in ("f16_8200", "f16_8196", "ragged_f16_8203"):
         prm.dist_dtype = dts.F16
     g, t = to_dev(prob.guide, sdt), to_dev(prob.target, sdt)
     out = {}
     names = kernels_of(lambda: out.setdefault("z", dts.dts_solve(
         g, t, to_dev(prob.conf), prm, z_init=None if z_init is None else to_dev(z_init))))
     assert dts.dts_last_status() == 0
-    assert ("row_stream_kernel<update>" in names) == (variant != "f16_8196"), names
+    assert "row_stream_kernel<update>" in names, names
     z = out["z"].cpu().numpy()
-    if variant in ("f16_8200", "f16_8196"):
+    if variant in ("f16_8200", "f16_8196", "ragged_f16_8203"):
         dX, dY = oracle.distances(prob.guide, 24.0, 0.2)
         ref = oracle.solve_d(dX.astype(np.float16).astype(np.float64), dY.astype(np.float16).astype(np.float64),
                              prob.target, prob.conf, lam=0.99, sigma_s=24.0, iterations=4)
