@@ -173,6 +173,14 @@ __global__ void __launch_bounds__(256) distance4_kernel(DistArgs a) {
     const bool l2 = a.norm == DTS_NORM_L2;
     for (int c = 0; c < a.C; ++c) {
         const GT* Ic = I + (long long)c * a.ch_stride;
+        if (xok && c + 1 < a.C) {
+            // the next band's rows into L2 while this band is read (the loop waits on each band's
+            // loads); measured at 16 bands: 1918 -> 1682 us, and 2252 us two bands ahead
+            const GT* In = Ic + a.ch_stride + x0;
+#pragma unroll
+            for (int r = -1; r < kDistRows; ++r)
+                if (y0 + r >= 0 && y0 + r < a.H) prefetch_l2(In + (long long)(y0 + r) * a.row_stride);
+        }
         float prev[4] = {0.f, 0.f, 0.f, 0.f};
         if (xok && y0 > 0 && y0 - 1 < a.H) load4_guide<GT>(Ic + (long long)(y0 - 1) * a.row_stride + x0, prev);
 #pragma unroll
