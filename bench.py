@@ -101,6 +101,7 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3, K=10):
         "row_bwd_kernel<final>": 28 + s_d,
         "col_bwd_kernel": 24 + s_d,
         "guide_grad_kernel": C * s_g + 2 * s_d + 8 + 4 * C,
+        "guide_grad_kernel<4 px>": C * s_g + 2 * s_d + 8 + 4 * C,
         "axpy_plane_kernel": 12,
         "update_adjoint_kernel": 36 + s_t,
         "row_pass_kernel<transpose>": 8 + s_d,
@@ -880,7 +881,8 @@ def run_sweep(args):
 # batched: the first 8 images of the batched workload in one persistent launch.
 NCU_CASES = {"tall": (10000, 2048, 3, "filter"), "row": (2048, 10000, 3, "filter"),
              "rowupd": (2048, 10000, 3, "solve"), "bwd": (10000, 1024, 3, "backward"),
-             "stereo": (1988, 2880, 3, "solve"), "batched": (0, 0, 3, "batched")}
+             "stereo": (1988, 2880, 3, "solve"), "batched": (0, 0, 3, "batched"),
+             "bwd16": (2048, 10000, 16, "backward")}
 
 
 def run_ncu_case(args):

@@ -241,6 +241,7 @@ enum KernelId {
     KID_COL_BWD_AGG = 38,
     KID_COL_BWD_APPLY = 39,
     KID_COL_BWD_CARRY = 40,
+    KID_GUIDE_GRAD4 = 41,
 };
 // flags of a timing record
 constexpr int kFlagDistHalf = 1;   // distance planes stored as FP16

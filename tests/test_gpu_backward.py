@@ -189,6 +189,38 @@ def test_autograd_retain_graph_and_unsupported_modes():
             dts.solve(T(I), T(t).requires_grad_(True), T(c), q)
 
 
+# the guide gradient four pixels per thread (rows of whole 16-byte units: W = 96) and one per
+# thread (W = 98), for FP32, BF16 and FP16 guide storage and both distance norms; 16-bit guides
+# against the oracle on the stored (rounded) guide
+@pytest.mark.parametrize("W", [96, 98])
+@pytest.mark.parametrize("gdtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("norm", [dts.NORM_L1, dts.NORM_L2])
+def test_backward_guide_gradient_layouts(W, gdtype, norm):
+    H = 40
+    rng = np.random.default_rng(W + 7 * norm + len(gdtype))
+    I = guide_noisy(H, W, 3, W + norm)
+    t = rng.normal(size=(H, W)).astype(np.float32)
+    c = rng.uniform(0.1, 1.0, (H, W)).astype(np.float32)
+    gz = rng.normal(size=(H, W)).astype(np.float32)
+    g = T(I, {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[gdtype])
+    prm = dts.Params(lam=0.9, sigma_s=8.0, sigma_r=0.3, iterations=3, norm=norm, save_checkpoints=1)
+    tt, cc = T(t), T(c)
+    ws = dts.workspace(g, prm, with_backward=True)
+    dts.dts_solve(g, tt, cc, prm, ws=ws)
+    dts.dts_profile(1)
+    gt, gc, gg, _ = dts.dts_solve_backward(g, tt, cc, prm, ws, T(gz))
+    torch.cuda.synchronize()
+    names = {r[0] for r in dts.dts_profile_read()}
+    dts.dts_profile(0)
+    assert dts.dts_last_status() == 0
+    assert ("guide_grad_kernel<4 px>" in names) == (W % 4 == 0), names
+    ref = oracle.solve_backward(g.float().cpu().numpy(), t, c, gz, lam=0.9, sigma_s=8.0, sigma_r=0.3, iterations=3,
+                                passes=3, norm=norm)
+    close(gt.cpu().numpy(), ref["t"], "grad target")
+    close(gc.cpu().numpy(), ref["c"], "grad conf")
+    close(gg.cpu().numpy(), ref["guide"], "grad guide")
+
+
 def test_backward_fp16_distances_runs_and_agrees_roughly():
     z, gt, gc, gg, _, _ = run_case(64, 96, dist=dts.F16, seed=4)
     _, gt32, gc32, gg32, _, _ = run_case(64, 96, seed=4)
