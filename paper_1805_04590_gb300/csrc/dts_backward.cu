@@ -770,15 +770,28 @@ __global__ void __launch_bounds__(256) update_adjoint_kernel(BwdArgs a) {
 }
 
 // dst[y][x] (pitch dp) += src[y][x] (pitch sp), or = when accumulate is 0
+template <bool VEC>
 __global__ void __launch_bounds__(256) axpy_plane_kernel(const float* src, long long sp, float* dst, long long dp,
                                                          int H, int W, int accumulate) {
     wait_predecessor();
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
-    if (x >= W || y >= H) return;
-    const float v = src[(long long)y * sp + x];
-    float* d = dst + (long long)y * dp + x;
-    *d = accumulate ? *d + v : v;
+    if constexpr (VEC) {  // four elements per thread (W, both pitches and both planes 16-byte aligned)
+        const int x = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+        if (x >= W || y >= H) return;
+        float4 v = *reinterpret_cast<const float4*>(src + (long long)y * sp + x);
+        float4* d = reinterpret_cast<float4*>(dst + (long long)y * dp + x);
+        if (accumulate) {
+            const float4 o = *d;
+            v = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+        }
+        *d = v;
+    } else {
+        const int x = blockIdx.x * blockDim.x + threadIdx.x;
+        if (x >= W || y >= H) return;
+        const float v = src[(long long)y * sp + x];
+        float* d = dst + (long long)y * dp + x;
+        *d = accumulate ? *d + v : v;
+    }
 }
 
 template <int ITEMS, bool DHALF>
@@ -1067,8 +1080,14 @@ cudaError_t launch_axpy_plane(const float* src, long long sp, float* dst, long l
                               cudaStream_t s) {
     const int h = prof_begin(KID_AXPY, (long long)H * W, 0, s);
     const dim3 block(256);
-    const dim3 grid((unsigned)((W + 255) / 256), (unsigned)H);
-    const cudaError_t e = launch_ex(axpy_plane_kernel, grid, block, 0, s, src, sp, dst, dp, H, W, accumulate);
+    auto al16 = [](const void* p) { return (uintptr_t)p % 16 == 0; };
+    cudaError_t e;
+    if (W % 4 == 0 && sp % 4 == 0 && dp % 4 == 0 && al16(src) && al16(dst))
+        e = launch_ex(axpy_plane_kernel<true>, dim3((unsigned)((W / 4 + 255) / 256), (unsigned)H), block, 0, s, src, sp,
+                      dst, dp, H, W, accumulate);
+    else
+        e = launch_ex(axpy_plane_kernel<false>, dim3((unsigned)((W + 255) / 256), (unsigned)H), block, 0, s, src, sp, dst,
+                      dp, H, W, accumulate);
     prof_end(h, s);
     return e;
 }
