@@ -101,7 +101,7 @@ def bytes_per_pixel(name, s_d, s_t, C=3, s_g=4, N=3, K=10):
         "row_bwd_kernel<final>": 28 + s_d,
         "col_bwd_kernel": 24 + s_d,
         "guide_grad_kernel": C * s_g + 2 * s_d + 8 + 4 * C,
-        "guide_grad_kernel<4 px>": C * s_g + 2 * s_d + 8 + 4 * C,
+        "guide_grad_kernel<x4>": C * s_g + 2 * s_d + 8 + 4 * C,
         "axpy_plane_kernel": 12,
         "update_adjoint_kernel": 36 + s_t,
         "row_pass_kernel<transpose>": 8 + s_d,

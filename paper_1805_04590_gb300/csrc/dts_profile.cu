@@ -134,7 +134,7 @@ extern "C" const char* dts_kernel_name(int kernel) {
         case KID_COL_BWD_AGG: return "col_bwd_agg_kernel";
         case KID_COL_BWD_APPLY: return "col_bwd_apply_kernel";
         case KID_COL_BWD_CARRY: return "col_bwd_carry_kernel";
-        case KID_GUIDE_GRAD4: return "guide_grad_kernel<4 px>";
+        case KID_GUIDE_GRAD4: return "guide_grad_kernel<x4>";
         default: return "unknown";
     }
 }

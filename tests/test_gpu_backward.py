@@ -213,7 +213,7 @@ def test_backward_guide_gradient_layouts(W, gdtype, norm):
     names = {r[0] for r in dts.dts_profile_read()}
     dts.dts_profile(0)
     assert dts.dts_last_status() == 0
-    assert ("guide_grad_kernel<4 px>" in names) == (W % 4 == 0), names
+    assert ("guide_grad_kernel<x4>" in names) == (W % 4 == 0), names
     ref = oracle.solve_backward(g.float().cpu().numpy(), t, c, gz, lam=0.9, sigma_s=8.0, sigma_r=0.3, iterations=3,
                                 passes=3, norm=norm)
     close(gt.cpu().numpy(), ref["t"], "grad target")
