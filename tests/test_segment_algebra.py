@@ -11,8 +11,9 @@ sweeps: the normalised pass (causal then anti-causal) and the transposed pass th
 gradients use (unnormalised causal sweep, normalised anti-causal sweep, then a factor 1 - w per
 position), the latter against the oracle's adjoint of one horizontal pass; and the reverse mode
 of a pass as the backward kernels form it (two causal maps and one five-number transform per
-segment), for the input gradient and the distance gradient; and the unnormalised support sweeps
-of the support weighting (a causal map and a two-number suffix per segment).
+segment), for the input gradient and the distance gradient, also with the two-phase vertical
+adjoint's compact chunk records and carries; and the unnormalised support sweeps of the support
+weighting (a causal map and a two-number suffix per segment).
 """
 import numpy as np
 import pytest
@@ -170,6 +171,88 @@ def test_pass_adjoint_is_independent_of_segmentation_and_order(seed):
     gsrc, dXb, _ = oracle.filter_adjoint(d[None, :], np.ones((1, n)), np.array([a]), x[None, :], G[None, :])
     for _ in range(4):
         gx, dd = adjoint_segmented(x, G, K, d, a, rng)
+        np.testing.assert_allclose(gx, gsrc[0], rtol=0, atol=1e-12 * max(1.0, np.abs(gsrc).max()))
+        np.testing.assert_allclose(dd[1:], dXb[0, 1:], rtol=0, atol=1e-12 * max(1.0, np.abs(dXb).max()))
+
+
+def adjoint_two_phase(x, G, K, d, a, rng):
+    """The reverse mode of one pass as the two-phase vertical adjoint forms it: the line in chunks
+    of segments (CTAs of warps).  Each chunk keeps six numbers: the coupled transform of its
+    segments composed (A, B, al, be, ga) and the B of their composed causal map of J; the J and h
+    maps share A, and the h map is the transform's (A, B).  The chunks' carries keep four: J and h
+    entering from above (the B of the composed maps; their A is taken as 1) and be, ga of
+    everything below.  Each segment then composes its chunk's carry with the segments of its own
+    chunk and replays as in adjoint_segmented."""
+    n = len(x)
+    w = [a ** d[j] if j > 0 else 0.0 for j in range(n)]
+    lna = np.log(a)
+
+    def cuts(b, e, k):
+        c = sorted(set(int(v) for v in rng.integers(b + 1, e, size=int(rng.integers(0, k)))) if e - b > 1 else [])
+        return [b] + c + [e]
+
+    chunks = []
+    cb = cuts(0, n, min(n, 10))
+    for b, e in zip(cb[:-1], cb[1:]):
+        segs = []
+        sb = cuts(b, e, min(e - b, 6))
+        for sb0, se0 in zip(sb[:-1], sb[1:]):
+            w_next = w[se0] if se0 < n else 0.0
+            suf = reduce_segment(G[sb0:se0], w[sb0:se0], w_next, normalised=False)
+            q = 0.0
+            for j in range(sb0, se0):
+                q = w[j] * (q - x[j]) + x[j]
+            segs.append((sb0, se0, w_next, (suf[0], q), (suf[0], suf[1]), suf))
+        tot = fold([g[5] for g in segs], coupled, ID5, rng)
+        jk = fold([g[3] for g in segs], aff, ID2, rng)
+        chunks.append((segs, tot + (jk[1],)))  # the six numbers of the chunk
+    # carries from the records alone
+    carries = []
+    for c in range(len(chunks)):
+        pre_jk = fold([(r[0], r[5]) for _, r in chunks[:c]], aff, ID2, rng)
+        pre_hg = fold([(r[0], r[1]) for _, r in chunks[:c]], aff, ID2, rng)
+        after = fold([r[:5] for _, r in chunks[c + 1:]], coupled, ID5, rng)
+        carries.append((pre_jk[1], pre_hg[1], after[3], after[4]))
+    gx, dd = np.empty(n), np.empty(n)
+    for c, (segs, _) in enumerate(chunks):
+        cj, ch, cbe, cga = carries[c]
+        for s, (b, e, w_next, own_jk, own_hg, own) in enumerate(segs):
+            pre_jk = fold([(1.0, cj)] + [g[3] for g in segs[:s]], aff, ID2, rng)
+            pre_hg = fold([(1.0, ch)] + [g[4] for g in segs[:s]], aff, ID2, rng)
+            after = fold([g[5] for g in segs[s + 1:]] + [(1.0, 0.0, 1.0, cbe, cga)], coupled, ID5, rng)
+            jin, hin = pre_jk[1], pre_hg[1]
+            gin = after[3] * (own_hg[0] * hin + own_hg[1]) + after[4]
+            xs, Gs, Ks = list(x[b:e]), list(G[b:e]), list(K[b:e])
+            Jp, hp = jin, hin
+            for j in range(e - b):
+                J = w[b + j] * (Jp - xs[j]) + xs[j]
+                Ks[j] = hp * (Ks[j] - Jp)
+                xs[j] = Jp - xs[j]
+                hp = w[b + j] * hp + Gs[j]
+                Gs[j] = hp
+                Jp = J
+            g = gin
+            for j in range(e - b - 1, -1, -1):
+                wp = w[b + j + 1] if j + 1 < e - b else w_next
+                g = wp * (g - Gs[j]) + Gs[j]
+                dd[b + j] = lna * w[b + j] * (g * xs[j] + Ks[j])
+                gx[b + j] = (1.0 - w[b + j]) * g
+    return gx, dd
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_two_phase_adjoint_records_suffice(seed):
+    """The two-phase vertical adjoint's compact chunk records (six numbers) and carries (four)
+    give the oracle's adjoint of a one-row pass, for any chunking, segmentation and order."""
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(2, 150))
+    x, G = rng.normal(size=n), rng.normal(size=n)
+    d = 1.0 + rng.exponential(3.0, n) * (rng.random(n) < 0.5)
+    a = float(rng.uniform(0.3, 0.995))
+    K = oracle.row_pass(x[None, :], d[None, :], a)[0]
+    gsrc, dXb, _ = oracle.filter_adjoint(d[None, :], np.ones((1, n)), np.array([a]), x[None, :], G[None, :])
+    for _ in range(4):
+        gx, dd = adjoint_two_phase(x, G, K, d, a, rng)
         np.testing.assert_allclose(gx, gsrc[0], rtol=0, atol=1e-12 * max(1.0, np.abs(gsrc).max()))
         np.testing.assert_allclose(dd[1:], dXb[0, 1:], rtol=0, atol=1e-12 * max(1.0, np.abs(dXb).max()))
 
